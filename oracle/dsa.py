@@ -1,0 +1,160 @@
+"""Diffusion synthetic acceleration restricted to the thick subdomain (CPU oracle, tests only).
+
+Paper: Sec. 2.2 (Eq. dsa_prec, Eq. DSA_fp and the additive form D^{-1} = I + D^{-1} Sigma),
+Sec. 3 (Algorithm 2, diagonal heterogeneous DSA: phi_f <- phi_f + D_ff^{-1} Sigma_f r_f),
+Sec. 4.1 (interior-penalty DSA operators, Eq. SIP, Eq. ModifiedF0) and Sec. 4.2 (the
+heterogeneous operator is the principal submatrix on the thick elements, thick where
+sigma_s >= eta).
+
+Readings (the paper's preferred NIP operator is nonsymmetric; this path needs an SPD
+operator for conjugate gradients):
+  * Operator: symmetric interior penalty on the thick elements only,
+        a(u, v) = sum_K (D_K grad u, grad v)_K + (sigma_a u, v)_K
+                + sum_{F interior, both sides thick} <kappa [u],[v]> - <{D grad u.n},[v]> - <{D grad v.n},[u]>
+                + sum_{F on the boundary of the thick region} <kappa u, v> - 1/2<D grad u.n, v> - 1/2<D grad v.n, u>
+    with D = 1/(3 sigma_t), sigma_a = sigma_t - sigma_s.  A face whose neighbour is not thick
+    (thin, void or outside the domain) is treated as a face to a zero exterior state: jump = u,
+    average = half the interior flux.  This is what the principal submatrix of a global
+    interior-penalty matrix gives on such a face, except that the penalty below uses only
+    the thick side, so the operator depends on thick-element data alone (Sec. 4.2).
+  * Penalty: kappa_F = max(1/4, c(p) * (D^-/h^- + D^+/h^+)/2) on interior faces and
+    max(1/4, c(p) * D/h) on boundary faces, c(p) = C_IP p (p+1), h = |K|/|F|.  1/4 is the
+    angular integral of the paper's F_0 = (1/4 pi) sum_d w_d |Omega_d.n|/2; the max() floor is the
+    modification of Eq. ModifiedF0.
+  * All integrals use (p+1)-point Gauss rules per direction (volume and faces), so that a
+    nodal implementation on the same points evaluates the identical bilinear form.
+  * Right-hand side mass matrix Sigma: sigma_s (default) or sigma_t (footnote of Sec. 2.2).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .dg import adjugate, face_points, tensor_rule
+
+C_IP = 2.0
+
+
+class DSA:
+    """Assembles D_ff in the oracle's modal basis and applies the Algorithm 2 correction."""
+
+    def __init__(self, T, mask, sigma="sigma_s", c_ip=C_IP, allow_void=False):
+        self.T = T
+        mask = np.asarray(mask).astype(bool).ravel()
+        if not allow_void and np.any(T.sigma_t[mask] <= 0):
+            raise ValueError("DSA on an element with sigma_t = 0 (full DSA is incompatible with voids)")
+        self.mask = mask
+        self.thick = np.flatnonzero(mask)
+        self.local = -np.ones(T.ne, dtype=np.int64)
+        self.local[self.thick] = np.arange(self.thick.size)
+        self.c_ip = c_ip
+        self.sig = T.sigma_s if sigma == "sigma_s" else T.sigma_t
+        self.D = self.assemble()
+        self.lu = spla.splu(self.D.tocsc()) if self.thick.size else None
+
+    def assemble(self):
+        T = self.T
+        dim, p, n = T.dim, T.p, T.n
+        nt = self.thick.size
+        if nt == 0:
+            return sp.csr_matrix((0, 0))
+        th = self.thick
+        Dc = 1.0 / (3.0 * T.sigma_t[th])
+        sa = T.sigma_t[th] - T.sigma_s[th]
+        cp = self.c_ip * p * (p + 1)
+        pts, wts = tensor_rule(p + 1, dim)
+        B, dB = T.basis.eval(pts)
+        _, J = T.mesh.map(pts)
+        J = J[th]
+        detJ = np.linalg.det(J)
+        Jinv = np.linalg.inv(J)
+        # physical gradients: grad u = J^{-T} grad_ref u
+        gB = np.einsum("eqkr,qmk->eqmr", Jinv, dB)
+        K = (np.einsum("e,q,eq,eqmr,eqnr->emn", Dc, wts, detJ, gB, gB)
+             + np.einsum("e,q,eq,qm,qn->emn", sa, wts, detJ, B, B))
+        vol = np.einsum("q,eq->e", wts, detJ)
+        rows, cols, vals = [], [], []
+
+        def add(re, ce, blk):
+            ri = (re[:, None] * n + np.arange(n))[:, :, None]
+            ci = (ce[:, None] * n + np.arange(n))[:, None, :]
+            rows.append(np.broadcast_to(ri, blk.shape).ravel())
+            cols.append(np.broadcast_to(ci, blk.shape).ravel())
+            vals.append(blk.ravel())
+
+        loc = np.arange(nt)
+        add(loc, loc, K)
+        tf, wf = tensor_rule(p + 1, dim - 1)
+        nbr = T.mesh.nbr[th]
+        for f in range(2 * dim):
+            a, side = divmod(f, 2)
+            s = 1.0 if side else -1.0
+            xi = face_points(tf, a, side)
+            xo = face_points(tf, a, 1 - side)
+            Bf, dBf = T.basis.eval(xi)
+            Bo, dBo = T.basis.eval(xo)
+            _, Jf = T.mesh.map(xi)
+            Jf = Jf[th]
+            N = s * adjugate(Jf)[:, :, a, :]            # n dS / dt  (ne_t, qf, dim)
+            dS = np.linalg.norm(N, axis=-1) * wf[None, :]
+            nrm = N / np.linalg.norm(N, axis=-1)[..., None]
+            area = dS.sum(axis=1)
+            h = vol / area
+            gBf = np.einsum("eqkr,qmk->eqmr", np.linalg.inv(Jf), dBf)
+            dn = np.einsum("eqmr,eqr->eqm", gBf, nrm)         # grad(basis).n on this side
+            u = nbr[:, f]
+            ut = np.where(u >= 0, self.local[np.maximum(u, 0)], -1)
+            inter = ut >= 0
+            bnd = ~inter
+            # boundary-type faces: <kappa u, v> - 1/2 <D du/dn, v> - 1/2 <D dv/dn, u>
+            if np.any(bnd):
+                e = np.flatnonzero(bnd)
+                kap = np.maximum(0.25, cp * Dc[e] / h[e])
+                blk = (np.einsum("e,eq,qm,qn->emn", kap, dS[e], Bf, Bf)
+                       - 0.5 * np.einsum("e,eq,eqn,qm->emn", Dc[e], dS[e], dn[e], Bf)
+                       - 0.5 * np.einsum("e,eq,eqm,qn->emn", Dc[e], dS[e], dn[e], Bf))
+                add(e, e, blk)
+            # interior thick-thick faces, assembled once from the side with side == 1
+            if side == 1 and np.any(inter):
+                e = np.flatnonzero(inter)
+                o = ut[e]
+                _, Jo = T.mesh.map(xo)
+                Jo = Jo[th][o]
+                gBo = np.einsum("eqkr,qmk->eqmr", np.linalg.inv(Jo), dBo)
+                dno = np.einsum("eqmr,eqr->eqm", gBo, nrm[e])       # neighbour gradient . n (n from e to o)
+                ho = vol[o] / area[e]              # conforming faces: same |F| from both sides
+                kap = np.maximum(0.25, cp * 0.5 * (Dc[e] / h[e] + Dc[o] / ho))
+                sides = [(e, Bf, dn[e], Dc[e], 1.0), (o, Bo, dno, Dc[o], -1.0)]
+                for (ra, Ba, dna, Da, sa_) in sides:
+                    for (cb, Bb, dnb, Db, sb_) in sides:
+                        blk = (np.einsum("e,eq,qm,qn->emn", kap * sa_ * sb_, dS[e], Ba, Bb)
+                               - 0.5 * np.einsum("e,eq,eqn,qm->emn", Db * sa_, dS[e], dnb, Ba)
+                               - 0.5 * np.einsum("e,eq,eqm,qn->emn", Da * sb_, dS[e], dna, Bb))
+                        add(ra, cb, blk)
+        return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                             shape=(nt * n, nt * n))
+
+    def rhs(self, r_modal):
+        """Sigma_f r_f: (sigma r, v) on thick elements, flattened."""
+        th = self.thick
+        return np.einsum("e,emn,en->em", self.sig[th], self.T.M[th], r_modal[th]).ravel()
+
+    def correction(self, r_modal):
+        """E_f D_ff^{-1} Sigma_f r_f (Algorithm 2), modal, full-size array."""
+        out = np.zeros_like(r_modal)
+        if self.thick.size:
+            out[self.thick] = self.lu.solve(self.rhs(r_modal)).reshape(-1, self.T.n)
+        return out
+
+    # nodal view of the operator, for comparisons with a nodal implementation
+    def nodal_matrix(self):
+        """D_ff in GL-nodal coordinates: V^{-T} D V^{-1} (block-diagonal V per element)."""
+        nt = self.thick.size
+        Vi = sp.block_diag([sp.csr_matrix(self.T.Vinv)] * nt, format="csr") if nt else sp.csr_matrix((0, 0))
+        return (Vi.T @ self.D @ Vi).tocsr()
+
+
+def thick_mask(prob):
+    """Thick elements: sigma_s >= eta (Sec. 3.3, Sec. 4.2; eta = 1 in Sec. 5.1), or sigma_t h > eta."""
+    return prob.thick_mask()

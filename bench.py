@@ -1,0 +1,310 @@
+"""Benchmark of the heterogeneous-DSA S_N transport hot path on GB300.
+
+Workload (one "step"): the 256x256 jittered-quad, DG Q2, S8 (40 directions) problem with
+16x16 blocks of thick (sigma_t = 1e3, c = 0.9999) / thin (sigma_t = 0.1, c = 0.5) / void
+material and q = 1, solved by FP64 source iteration with thick-only DSA (PCG + multigrid
+V-cycle) to a relative residual of 1e-8.  value = DOF x directions swept per second over the
+whole solve (every iteration's sweep, flux reduction and DSA solve inside the timed region).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 (launched with torch.distributed.run) every rank solves its own replica.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sweep DOF*dirs/s (FP64, thick-DSA source iteration to 1e-8)"
+UNIT = "DOF*dirs/s"
+# per element-direction algorithmic work of the dense element factor-and-solve, n = (p+1)^d
+# nodes: (2/3) n^3 + 6 n^2 flops; traces 2 d (p+1)^(d-1) x 8 bytes
+WORKLOAD = "256x256 jittered quads, DG Q2, S8 (40 dirs), thick/thin/void blocks, FP64 thick-DSA SI to 1e-8"
+
+
+def flops_per_item(n):
+    return (2.0 / 3.0) * n ** 3 + 6.0 * n ** 2
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except Exception:
+        return {}
+
+
+# FP64 FMA peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (GB300 FP64 is 1/64 of FP32)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.index = index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return rank, ws
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(prob, n_dirs, seed=5):
+    """CPU oracle sweep restricted to a bounded sample of directions; returns (DOF*dirs/s, seconds)."""
+    from oracle import Transport
+    T = Transport(prob)
+    phi = T.to_modal(np.ones((T.ne, T.n)))
+    src = T.isotropic_source(phi)
+    dirs = list(range(0, T.nd, max(1, T.nd // n_dirs)))[:n_dirs]
+    t0 = time.perf_counter()
+    for d in dirs:
+        T.sweep_direction(d, src)
+    dt = time.perf_counter() - t0
+    return T.ne * T.n * len(dirs) / dt, dt, len(dirs)
+
+
+def run_reference(args, rank, ws):
+    """The CPU oracle as it stands, timed on the host cores on a bounded sample per step."""
+    from paper_2001_09196_gb300 import inputs
+    if rank != 0:
+        return
+    prob = inputs.config2()
+    from oracle import Transport
+    T = Transport(prob)
+    phi = T.to_modal(np.ones((T.ne, T.n)))
+    src = T.isotropic_source(phi)
+    dirs_per_step = 2
+    times = []
+    d = 0
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for _ in range(dirs_per_step):
+            T.sweep_direction(d % T.nd, src)
+            d += 7
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    units = T.ne * T.n * dirs_per_step
+    value = units * len(times) / sum(times)
+    cores = 1
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{dirs_per_step} of 40 directions per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"numpy oracle sweep of {dirs_per_step} directions per step on the full mesh"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, ws):
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_2001_09196_gb300 import build
+    build.build()
+    from paper_2001_09196_gb300 import inputs, sn
+    prob = inputs.config2()
+    mesh = sn.Mesh.from_problem(prob)
+    n = mesh.n_nodes
+    units_per_sweep = mesh.n_elem * n * mesh.n_dirs
+    stream = torch.cuda.current_stream()
+    opts = dict(dsa="thick", thick_rule="sigma_s", tol=1e-8, inner_tol=1e-4, max_iters=500, precision="fp64")
+    phi = torch.zeros(mesh.shape, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+
+    def step():
+        return mesh.source_iterate(phi=phi, **opts)
+
+    for _ in range(args.warmup):
+        r = step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters = []
+    n0 = sn.launch_count()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            r = step()
+            ev[k][1].record(stream)
+            iters.append(r["iters"])
+        torch.cuda.synchronize()
+    launches = sn.launch_count() - n0
+    barrier(ws)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = max_over_ranks(sum(step_ms) / 1e3, ws)
+    units = sum(iters) * units_per_sweep * ws
+    value = units / total_s
+    clocks = clk.summary()
+
+    # dominant kernel: the FP64 sweep (all level launches of one transport update)
+    sweeps = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        mesh.sweep(phi, precision="fp64")
+        b.record(stream)
+        torch.cuda.synchronize()
+        sweeps.append(a.elapsed_time(b))
+    sweep_ms = statistics.median(sweeps)
+    n_launch_sweep = mesh.n_levels
+    achieved = flops_per_item(n) * mesh.n_elem * mesh.n_dirs / (sweep_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "sweep_level_kernel<2,2,FP64>", "launches_per_sweep": n_launch_sweep,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (no measured FP64 peak)",
+                "sweep_ms": sweep_ms}
+
+    # other forms (not part of value): FP32 element solves and FP32 + FP64 refinement
+    forms = {}
+    for prec in ("fp32", "fp32_refine"):
+        o = dict(opts, precision=prec, max_iters=200)
+        mesh.source_iterate(phi=phi, **o)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        rr = mesh.source_iterate(phi=phi, **o)
+        b.record(stream)
+        torch.cuda.synchronize()
+        forms[prec] = {"ms_to_tol": a.elapsed_time(b), "iters": rr["iters"], "rel_residual": rr["rel_residual"],
+                       "converged": rr["converged"]}
+
+    # end to end through the C ABI with host buffers: H2D materials, solve, D2H phi
+    st_h = torch.as_tensor(prob.sigma_t).pin_memory()
+    ss_h = torch.as_tensor(prob.sigma_s).pin_memory()
+    q_h = torch.as_tensor(prob.q).pin_memory()
+    phi_h = torch.empty(mesh.shape, dtype=torch.float64).pin_memory()
+    st_d, ss_d, q_d = (torch.empty_like(x, device="cuda") for x in (st_h, ss_h, q_h))
+    e2e_ms = []
+    for k in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for hd, dd in ((st_h, st_d), (ss_h, ss_d), (q_h, q_d)):
+            dd.copy_(hd, non_blocking=True)
+        mesh.set_materials(st_d, ss_d, q_d)
+        rr = mesh.source_iterate(phi=phi, **opts)
+        phi_h.copy_(phi, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_s = max_over_ranks(sum(e2e_ms) / 1e3, ws)
+    e2e_value = rr["iters"] * units_per_sweep * len(e2e_ms) * ws / e2e_s
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, secs, nd = oracle_sample(prob, n_dirs=args.cpu_dirs)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"numpy oracle sweep of {nd} of 40 directions on the full 256x256 Q2 mesh ({secs:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "elements": mesh.n_elem, "dofs": mesh.n_elem * n,
+                           "dirs": mesh.n_dirs, "dof_dirs_per_sweep": units_per_sweep,
+                           "iters_per_step": iters, "l2": "256 MB buffer written between timed steps",
+                           "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+                "time_to_1e-8_ms": {"fp64": sum(step_ms) / len(step_ms),
+                                    **{k: v["ms_to_tol"] for k, v in forms.items()}},
+                "forms": forms,
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
+                "e2e": {"value": e2e_value, "unit": UNIT,
+                        "h2d_bytes_per_step": 3 * prob.n_elem * 8,
+                        "d2h_bytes_per_step": mesh.n_elem * n * 8}}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-dirs", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, ws = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+    else:
+        run_ours(args, rank, ws)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

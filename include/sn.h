@@ -1,0 +1,200 @@
+/*
+ * libsn: GB300 (sm_103a) upwind-DG S_N transport sweep, source iteration and
+ * thick-subdomain-only diffusion synthetic acceleration (Southworth, Holec & Haut,
+ * "Diffusion synthetic acceleration for heterogeneous domains, compatible with voids").
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Every call returns an sn_status; none aborts.  On failure sn_last_error() returns a
+ *    thread-local message.  SN_ERR_CUDA leaves the mesh usable unless the CUDA context
+ *    itself was lost.
+ *  - Meshes are structured nx x ny (x nz) grids of the unit square / cube; elements are
+ *    numbered lexicographically with x fastest.  The discrete space is Q_p on each element,
+ *    represented by values at the (p+1)^dim tensor Gauss-Legendre nodes, lexicographic with
+ *    x fastest inside the element.  A scalar-flux array has layout [elem][node] (float64).
+ *  - Directions: level-symmetric S_N, N in {4, 6, 8}; N(N+2) directions in 3D and the
+ *    N(N+2)/2 with positive z component in 2D; weights sum to 4*pi.  Order: octant o
+ *    (x negative if bit 0, y if bit 1, z if bit 2), then points (i, j, k) of the octant,
+ *    i ascending, then j ascending.
+ *  - Array arguments marked "device" are caller-owned device pointers (e.g. a torch
+ *    tensor's data_ptr()); the library never frees them.  "mem" arguments choose host (0)
+ *    or device (1) for inputs that accept both.
+ *  - stream is a cudaStream_t (NULL = legacy default stream).  Calls enqueue work on it
+ *    and return when the results are ready in device memory unless stated otherwise.
+ *  - All device buffers a mesh needs (angular fluxes, work lists, the DSA hierarchy) are
+ *    owned by the mesh and freed by sn_mesh_destroy.
+ */
+#ifndef SN_H
+#define SN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SN_OK = 0,
+    SN_ERR_ARG = 1,                 /* invalid argument or unsupported combination */
+    SN_ERR_CUDA = 2,                /* a CUDA call failed */
+    SN_ERR_OOM = 3,                 /* device allocation failed */
+    SN_ERR_CYCLE = 4,               /* an upwind graph has a cycle (no sweep order) */
+    SN_ERR_VOID_FULL_DSA = 5,       /* full DSA requested on a mesh with sigma_t = 0 */
+    SN_ERR_NOT_CONVERGED = 6,       /* max_iters reached; phi still holds the last iterate */
+    SN_ERR_TIMEOUT = 7,             /* a bounded device wait gave up; outputs undefined */
+    SN_ERR_INNER_NOT_CONVERGED = 8  /* a DSA solve hit inner_max_iters (only if strict) */
+} sn_status;
+
+enum { SN_FP64 = 0, SN_FP32 = 1, SN_FP32_REFINE = 2 };          /* element-solve precision */
+enum { SN_DSA_NONE = 0, SN_DSA_FULL = 1, SN_DSA_THICK = 2 };    /* DSA variant */
+enum { SN_THICK_SIGMA_S = 0, SN_THICK_SIGMA_T_H = 1, SN_THICK_MASK = 2 };
+enum { SN_DSA_SIGMA_S = 0, SN_DSA_SIGMA_T = 1 };
+
+typedef struct sn_mesh sn_mesh;
+
+typedef struct {
+    int dim;                 /* 2 or 3 */
+    int nx, ny, nz;          /* elements per axis (nz ignored in 2D) */
+    int p;                   /* polynomial order: 1..3 in 2D, 1 in 3D */
+    int sn_order;            /* 4, 6 or 8 */
+    const double* vertices;  /* host, 2D only: ((ny+1)*(nx+1)) x 2, x fastest; NULL = uniform grid */
+    double psi_inc;          /* isotropic inflow on every boundary face; 0 = vacuum */
+} sn_mesh_desc;
+
+typedef struct {
+    int n_elem, n_nodes, n_dirs, n_levels;
+    long long n_items;       /* n_elem * n_dirs */
+} sn_mesh_info;
+
+/*
+ * sn_mesh_create: Eq. (sntransport) semi-discretisation (Sec. 1) on a structured mesh.
+ * Builds the S_N quadrature, the per-element geometry and, on the device, the upwind
+ * level sets of every direction (the topological order that makes each transport update
+ * a forward block solve, Sec. 1).  Returns SN_ERR_CYCLE if a direction's upwind graph
+ * has a cycle.  *out is owned by the caller and released with sn_mesh_destroy.
+ * Materials default to sigma_t = sigma_s = q = 0 until sn_set_materials.
+ */
+sn_status sn_mesh_create(const sn_mesh_desc* desc, sn_mesh** out);
+sn_status sn_mesh_destroy(sn_mesh* mesh);
+sn_status sn_mesh_get_info(const sn_mesh* mesh, sn_mesh_info* info);
+
+/* Quadrature readback: dirs (host, n_dirs x 3) and weights (host, n_dirs). */
+sn_status sn_mesh_quadrature(const sn_mesh* mesh, double* dirs, double* weights);
+
+/*
+ * sn_set_materials: per-element sigma_t, sigma_s and isotropic emission density q
+ * (Eq. 1: 0 <= sigma_s <= sigma_t; q_d = q / (4 pi)).  Copied into the mesh (n_elem
+ * doubles each, host if mem = 0, device if mem = 1).  Invalidates any DSA hierarchy.
+ * Returns SN_ERR_ARG on NaN/Inf, negative values or sigma_s > sigma_t.
+ */
+sn_status sn_set_materials(sn_mesh* mesh, const double* sigma_t, const double* sigma_s,
+                           const double* q, int mem, void* stream);
+
+/*
+ * sn_sweep: one transport update, Eq. (source0) / Eq. (phi):
+ *     phi_out = sum_d w_d L_d^{-1} ( q/(4 pi) + sigma_s phi_in / (4 pi) ),
+ * the element systems solved in the given precision (SN_FP64, SN_FP32 or SN_FP32_REFINE;
+ * the scalar-flux sum is always float64).  phi_in, phi_out: device, [elem][node],
+ * must not alias.  The angular fluxes psi_d of this sweep stay in the mesh (used by
+ * sn_gradients).
+ */
+sn_status sn_sweep(sn_mesh* mesh, const double* phi_in, double* phi_out, int precision, void* stream);
+
+typedef struct {
+    int dsa;                 /* SN_DSA_NONE | SN_DSA_FULL | SN_DSA_THICK */
+    int thick_rule;          /* SN_THICK_SIGMA_S (sigma_s >= eta, Sec. 4.2) | SN_THICK_SIGMA_T_H | SN_THICK_MASK */
+    double eta;              /* threshold of the thick rule; the paper uses eta = 1 (Sec. 5.1) */
+    const unsigned char* mask; /* host, n_elem, used with SN_THICK_MASK */
+    int dsa_sigma;           /* SN_DSA_SIGMA_S (default) | SN_DSA_SIGMA_T: mass matrix of the DSA rhs */
+    double tol;              /* relative residual ||r^i|| / ||r^0|| (Euclidean, nodal) */
+    double inner_tol;        /* PCG relative residual of each DSA solve */
+    int max_iters, inner_max_iters;
+    int precision;           /* SN_FP64 | SN_FP32 | SN_FP32_REFINE */
+    int checkpoint_every;    /* >0: copy phi^{k} to checkpoints after every k-th iteration */
+    double* checkpoints;     /* device, max_checkpoints x n_elem x n_nodes, or NULL */
+    int max_checkpoints;
+    int warm_start;          /* 1: start from phi_inout, 0: from phi = 0 */
+} sn_iter_opts;
+
+typedef struct {
+    int iters;               /* outer iterations performed */
+    double rel_residual;     /* last ||r^i|| / ||r^0|| */
+    int inner_iters_total;   /* PCG iterations summed over all DSA solves */
+    double thick_fraction;   /* thick elements / all elements */
+    double* residual_history; /* host, history_len entries, or NULL */
+    int history_len;
+    int n_checkpoints;       /* checkpoints written */
+    double ms_total;         /* wall time of the call (stream-synchronised) */
+} sn_iter_stats;
+
+/* Defaults: dsa thick, sigma_s >= 1, tol 1e-8, inner_tol 1e-4 (Sec. 5), FP64, cold start. */
+void sn_iter_opts_default(sn_iter_opts* opts);
+
+/*
+ * sn_source_iterate: source iteration with diffusion synthetic acceleration,
+ * Eq. (DSA_fp) with the diagonal heterogeneous preconditioner of Algorithm 2:
+ *     phi_half^i = sweep(phi^i),  r^i = phi_half^i - phi^i,
+ *     phi^{i+1} = phi_half^i + E_f D_ff^{-1} Sigma_f r^i_f     (nothing added for SN_DSA_NONE),
+ * with D_ff the symmetric interior-penalty diffusion operator on the thick elements
+ * (Sec. 4.1-4.2; SN_DSA_FULL uses every element) solved by conjugate gradients
+ * preconditioned with a geometric multigrid V-cycle.  Stops after the iteration whose
+ * ||r^i|| <= tol ||r^0||.  phi_inout: device [elem][node]; receives phi^{i+1}.
+ * SN_ERR_VOID_FULL_DSA if dsa = FULL and some sigma_t = 0; SN_ERR_NOT_CONVERGED after
+ * max_iters (phi_inout still written).  stats may be NULL.
+ */
+sn_status sn_source_iterate(sn_mesh* mesh, const sn_iter_opts* opts, double* phi_inout,
+                            sn_iter_stats* stats, void* stream);
+
+/*
+ * sn_adjoint_sweep: transpose of the linear part of sn_sweep (in the nodal coordinates
+ * of the interface): out = sum_d w_d Sigma_s L_d^{-T} mu_in, where Sigma_s is the nodal
+ * mass matrix with coefficient sigma_s/(4 pi).  L_d^T is solved by a sweep in reversed
+ * upwind order with transposed element and face blocks (adjoint of Eq. system).
+ * mu_in, out: device [elem][node]; the lambda_d = w_d L_d^{-T} mu_in stay in the mesh.
+ */
+sn_status sn_adjoint_sweep(sn_mesh* mesh, const double* mu_in, double* out, int precision, void* stream);
+
+/*
+ * sn_adjoint_iterate: solves S^T mu = g (S = I - T, Eq. schur) by the adjoint source
+ * iteration mu <- g + T^T mu with the transposed DSA step.  g, mu_inout: device.
+ */
+sn_status sn_adjoint_iterate(sn_mesh* mesh, const sn_iter_opts* opts, const double* g, double* mu_inout,
+                             sn_iter_stats* stats, void* stream);
+
+/*
+ * sn_gradients: for J = g^T phi with phi converged and mu = S^{-T} g, per element
+ *   d_sigma_t[e] = -sum_d lambda_d,e^T M_e psi_d,e,
+ *   d_sigma_s[e] =  sum_d lambda_d,e^T M_e phi_e / (4 pi),
+ *   d_q[e]       =  sum_d lambda_d,e^T M_e 1 / (4 pi),
+ * with psi_d = L_d^{-1}(q_d + Sigma_s phi) and lambda_d = w_d L_d^{-T} mu (one forward and
+ * one adjoint sweep, FP64).  All pointers device; outputs n_elem doubles (NULL to skip).
+ */
+sn_status sn_gradients(sn_mesh* mesh, const double* phi, const double* mu, double* d_sigma_t,
+                       double* d_sigma_s, double* d_q, void* stream);
+
+/*
+ * Diagnostics of the DSA operator (Sec. 4): y = D_ff x on the elements selected by opts
+ * (x, y device, [elem][node]; entries outside the thick set are ignored / set to 0), and the
+ * PCG + V-cycle solve of D_ff x = b to opts->inner_tol.  *iters receives the PCG count.
+ */
+sn_status sn_dsa_apply(sn_mesh* mesh, const sn_iter_opts* opts, const double* x, double* y, void* stream);
+sn_status sn_dsa_solve(sn_mesh* mesh, const sn_iter_opts* opts, const double* b, double* x, int* iters,
+                       void* stream);
+
+/*
+ * Diagnostic: copies psi_d (direction d) of the last forward sweep (or lambda_d of the last
+ * adjoint sweep if adjoint != 0) into out (device, [elem][node], float64; the FP32 form's
+ * float32 values are widened).  Used to check the element equations of Sec. 4.1 at full size.
+ */
+sn_status sn_get_angular_flux(sn_mesh* mesh, int d, int adjoint, int precision, double* out, void* stream);
+
+/* Number of CUDA kernels the library has launched since it was loaded (diagnostic). */
+long long sn_launch_count(void);
+
+const char* sn_last_error(void);
+const char* sn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SN_H */

@@ -1,0 +1,483 @@
+// C ABI of libsn (declared in include/sn.h): argument checking, mesh ownership and the
+// outer source iteration.  Every numerical step runs in the CUDA kernels of sn_sweep.cu
+// and sn_dsa.cu; this file only sequences them.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "sn_dsa.h"
+#include "sn_internal.h"
+
+namespace sn {
+cudaError_t upload_gl_constants();
+std::atomic<long long> g_launches{0};
+}
+
+namespace {
+
+thread_local std::string g_err;
+
+sn_status fail(sn_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+sn_status cuda_fail(cudaError_t err, const char* where) {
+    if (err == cudaErrorMemoryAllocation) return fail(SN_ERR_OOM, "%s: %s", where, cudaGetErrorString(err));
+    return fail(SN_ERR_CUDA, "%s: %s", where, cudaGetErrorString(err));
+}
+
+#define CK(call, where)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+bool g_const_ready[64] = {};
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+    return cudaMalloc((void**)p, std::max<size_t>(1, count) * sizeof(T));
+}
+
+void free_mesh(sn_mesh* m) {
+    if (!m) return;
+    for (void* p : {(void*)m->d_dirs, (void*)m->d_wts, (void*)m->d_corners, (void*)m->d_sigma_t, (void*)m->d_sigma_s,
+                    (void*)m->d_q, m->d_psi, m->d_psi32, (void*)m->d_lambda, (void*)m->d_work, (void*)m->d_red,
+                    (void*)m->d_scalars, (void*)m->levels.items})
+        if (p) cudaFree(p);
+    sn::dsa_free(m->dsa);
+    delete m;
+}
+
+bool finite_nonneg(const std::vector<double>& v) {
+    for (double x : v)
+        if (!std::isfinite(x) || x < 0.0) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sn_last_error(void) { return g_err.c_str(); }
+const char* sn_version(void) { return "libsn 0.1 (sm_103a)"; }
+long long sn_launch_count(void) { return sn::g_launches.load(); }
+
+void sn_iter_opts_default(sn_iter_opts* o) {
+    std::memset(o, 0, sizeof(*o));
+    o->dsa = SN_DSA_THICK;
+    o->thick_rule = SN_THICK_SIGMA_S;
+    o->eta = 1.0;
+    o->dsa_sigma = SN_DSA_SIGMA_S;
+    o->tol = 1e-8;
+    o->inner_tol = 1e-4;
+    o->max_iters = 1000;
+    o->inner_max_iters = 200;
+    o->precision = SN_FP64;
+}
+
+sn_status sn_mesh_create(const sn_mesh_desc* desc, sn_mesh** out) {
+    if (!desc || !out) return fail(SN_ERR_ARG, "null argument");
+    *out = nullptr;
+    const sn_mesh_desc& d = *desc;
+    if (d.dim != 2 && d.dim != 3) return fail(SN_ERR_ARG, "dim must be 2 or 3");
+    if (d.nx < 1 || d.ny < 1 || (d.dim == 3 && d.nz < 1)) return fail(SN_ERR_ARG, "element counts must be >= 1");
+    if (d.dim == 2 && (d.p < 1 || d.p > 3)) return fail(SN_ERR_ARG, "2D supports p = 1..3");
+    if (d.dim == 3 && d.p != 1) return fail(SN_ERR_ARG, "3D supports p = 1");
+    if (d.dim == 3 && d.vertices) return fail(SN_ERR_ARG, "3D meshes are uniform (vertices must be NULL)");
+    if (!std::isfinite(d.psi_inc) || d.psi_inc < 0) return fail(SN_ERR_ARG, "psi_inc must be finite and >= 0");
+    std::unique_ptr<sn_mesh, void (*)(sn_mesh*)> m(new sn_mesh(), free_mesh);
+    m->desc = d;
+    m->desc.vertices = nullptr;
+    m->dim = d.dim;
+    m->p = d.p;
+    m->nx = d.nx;
+    m->ny = d.ny;
+    m->nz = d.dim == 3 ? d.nz : 1;
+    const int Q = d.p + 1;
+    m->n = d.dim == 2 ? Q * Q : Q * Q * Q;
+    const long long ne = (long long)m->nx * m->ny * m->nz;
+    if (ne > (1ll << 30)) return fail(SN_ERR_ARG, "too many elements");
+    m->ne = (int)ne;
+    if (!sn::level_symmetric(d.sn_order, d.dim, m->h_dirs, m->h_wts)) return fail(SN_ERR_ARG, "sn_order must be 4, 6 or 8");
+    m->nd = (int)m->h_wts.size();
+    m->hx = 1.0 / m->nx;
+    m->hy = 1.0 / m->ny;
+    m->hz = 1.0 / m->nz;
+    if (d.dim == 2) {
+        m->h_corners.resize((size_t)m->ne * 8);
+        const int vx = m->nx + 1;
+        for (int j = 0; j < m->ny; ++j)
+            for (int i = 0; i < m->nx; ++i) {
+                double* c = &m->h_corners[8 * ((size_t)j * m->nx + i)];
+                for (int q = 0; q < 4; ++q) {
+                    const int I = i + (q & 1), J = j + (q >> 1);
+                    if (d.vertices) {
+                        c[2 * q] = d.vertices[2 * ((size_t)J * vx + I)];
+                        c[2 * q + 1] = d.vertices[2 * ((size_t)J * vx + I) + 1];
+                    } else {
+                        c[2 * q] = I * m->hx;
+                        c[2 * q + 1] = J * m->hy;
+                    }
+                    if (!std::isfinite(c[2 * q]) || !std::isfinite(c[2 * q + 1])) return fail(SN_ERR_ARG, "non-finite vertex");
+                }
+                // element must not be inverted: det J > 0 at all four corners
+                for (int q = 0; q < 4; ++q) {
+                    const double xi = (q & 1) ? 1.0 : -1.0, eta = (q >> 1) ? 1.0 : -1.0;
+                    const double ebx = c[2] - c[0], eby = c[3] - c[1], etx = c[6] - c[4], ety = c[7] - c[5];
+                    const double elx = c[4] - c[0], ely = c[5] - c[1], erx = c[6] - c[2], ery = c[7] - c[3];
+                    const double xx = (1 - eta) * ebx + (1 + eta) * etx, xy = (1 - eta) * eby + (1 + eta) * ety;
+                    const double yx = (1 - xi) * elx + (1 + xi) * erx, yy = (1 - xi) * ely + (1 + xi) * ery;
+                    if (!(xx * yy - yx * xy > 0)) return fail(SN_ERR_ARG, "element (%d,%d) is inverted or degenerate", i, j);
+                }
+            }
+    }
+    int dev = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 64 && !g_const_ready[dev]) {
+        CK(sn::upload_gl_constants(), "upload constants");
+        g_const_ready[dev] = true;
+    }
+    const size_t M = (size_t)m->ne * m->n;
+    CK(dalloc(&m->d_dirs, m->h_dirs.size()), "alloc");
+    CK(dalloc(&m->d_wts, m->h_wts.size()), "alloc");
+    CK(cudaMemcpy(m->d_dirs, m->h_dirs.data(), m->h_dirs.size() * sizeof(double), cudaMemcpyHostToDevice), "copy");
+    CK(cudaMemcpy(m->d_wts, m->h_wts.data(), m->h_wts.size() * sizeof(double), cudaMemcpyHostToDevice), "copy");
+    if (d.dim == 2) {
+        CK(dalloc(&m->d_corners, m->h_corners.size()), "alloc");
+        CK(cudaMemcpy(m->d_corners, m->h_corners.data(), m->h_corners.size() * sizeof(double), cudaMemcpyHostToDevice), "copy");
+    }
+    CK(dalloc(&m->d_sigma_t, m->ne), "alloc");
+    CK(dalloc(&m->d_sigma_s, m->ne), "alloc");
+    CK(dalloc(&m->d_q, m->ne), "alloc");
+    CK(cudaMemset(m->d_sigma_t, 0, m->ne * sizeof(double)), "memset");
+    CK(cudaMemset(m->d_sigma_s, 0, m->ne * sizeof(double)), "memset");
+    CK(cudaMemset(m->d_q, 0, m->ne * sizeof(double)), "memset");
+    m->h_sigma_t.assign(m->ne, 0.0);
+    m->h_sigma_s.assign(m->ne, 0.0);
+    m->h_q.assign(m->ne, 0.0);
+    CK(cudaMalloc(&m->d_psi, (size_t)m->nd * M * sizeof(double)), "alloc psi");
+    CK(dalloc(&m->d_work, 4 * M), "alloc");
+    m->red_blocks = (int)((M + 255) / 256);
+    CK(dalloc(&m->d_red, m->red_blocks), "alloc");
+    CK(dalloc(&m->d_scalars, 16), "alloc");
+    bool cycle = false;
+    CK(sn::build_levels(m.get(), 0, &cycle), "level sets");
+    if (cycle) return fail(SN_ERR_CYCLE, "an upwind graph has a cycle");
+    CK(cudaDeviceSynchronize(), "setup");
+    *out = m.release();
+    return SN_OK;
+}
+
+sn_status sn_mesh_destroy(sn_mesh* m) {
+    if (!m) return SN_OK;
+    cudaDeviceSynchronize();
+    free_mesh(m);
+    return SN_OK;
+}
+
+sn_status sn_mesh_get_info(const sn_mesh* m, sn_mesh_info* info) {
+    if (!m || !info) return fail(SN_ERR_ARG, "null argument");
+    info->n_elem = m->ne;
+    info->n_nodes = m->n;
+    info->n_dirs = m->nd;
+    info->n_levels = m->levels.n_levels;
+    info->n_items = (long long)m->ne * m->nd;
+    return SN_OK;
+}
+
+sn_status sn_mesh_quadrature(const sn_mesh* m, double* dirs, double* weights) {
+    if (!m) return fail(SN_ERR_ARG, "null mesh");
+    if (dirs) std::memcpy(dirs, m->h_dirs.data(), m->h_dirs.size() * sizeof(double));
+    if (weights) std::memcpy(weights, m->h_wts.data(), m->h_wts.size() * sizeof(double));
+    return SN_OK;
+}
+
+sn_status sn_set_materials(sn_mesh* m, const double* st, const double* ss, const double* q, int mem, void* stream) {
+    if (!m || !st || !ss || !q) return fail(SN_ERR_ARG, "null argument");
+    if (mem != 0 && mem != 1) return fail(SN_ERR_ARG, "mem must be 0 (host) or 1 (device)");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<double> hst(m->ne), hss(m->ne), hq(m->ne);
+    const cudaMemcpyKind k = mem ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    CK(cudaMemcpyAsync(hst.data(), st, m->ne * sizeof(double), k, s), "copy");
+    CK(cudaMemcpyAsync(hss.data(), ss, m->ne * sizeof(double), k, s), "copy");
+    CK(cudaMemcpyAsync(hq.data(), q, m->ne * sizeof(double), k, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    if (!finite_nonneg(hst) || !finite_nonneg(hss) || !finite_nonneg(hq))
+        return fail(SN_ERR_ARG, "materials must be finite and >= 0");
+    for (int e = 0; e < m->ne; ++e)
+        if (hss[e] > hst[e]) return fail(SN_ERR_ARG, "sigma_s > sigma_t at element %d", e);
+    m->h_sigma_t = hst;
+    m->h_sigma_s = hss;
+    m->h_q = hq;
+    CK(cudaMemcpyAsync(m->d_sigma_t, hst.data(), m->ne * sizeof(double), cudaMemcpyHostToDevice, s), "copy");
+    CK(cudaMemcpyAsync(m->d_sigma_s, hss.data(), m->ne * sizeof(double), cudaMemcpyHostToDevice, s), "copy");
+    CK(cudaMemcpyAsync(m->d_q, hq.data(), m->ne * sizeof(double), cudaMemcpyHostToDevice, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    sn::dsa_free(m->dsa);
+    m->dsa = nullptr;
+    m->dsa_key_dsa = -1;
+    return SN_OK;
+}
+
+static sn_status ensure_psi32(sn_mesh* m) {
+    if (m->d_psi32) return SN_OK;
+    CK(cudaMalloc(&m->d_psi32, (size_t)m->nd * m->ne * m->n * sizeof(float)), "alloc psi32");
+    return SN_OK;
+}
+
+static sn_status ensure_lambda(sn_mesh* m) {
+    if (m->d_lambda) return SN_OK;
+    CK(cudaMalloc(&m->d_lambda, (size_t)m->nd * m->ne * m->n * sizeof(double)), "alloc lambda");
+    return SN_OK;
+}
+
+sn_status sn_sweep(sn_mesh* m, const double* phi_in, double* phi_out, int precision, void* stream) {
+    if (!m || !phi_out) return fail(SN_ERR_ARG, "null argument");
+    if (precision < SN_FP64 || precision > SN_FP32_REFINE) return fail(SN_ERR_ARG, "bad precision");
+    if (phi_in == phi_out) return fail(SN_ERR_ARG, "phi_in and phi_out must not alias");
+    if (precision == SN_FP32) {
+        sn_status st = ensure_psi32(m);
+        if (st != SN_OK) return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(sn::launch_sweep(m, phi_in, precision, 1.0, s), "sweep");
+    CK(sn::launch_phi_reduce(m, precision, nullptr, phi_out, nullptr, s), "phi reduce");
+    return SN_OK;
+}
+
+// Builds (or reuses) the DSA hierarchy selected by opts.
+static sn_status ensure_dsa(sn_mesh* m, const sn_iter_opts* o) {
+    std::vector<unsigned char> mask(m->ne, 0);
+    if (o->dsa == SN_DSA_FULL) {
+        for (int e = 0; e < m->ne; ++e) {
+            if (!(m->h_sigma_t[e] > 0.0))
+                return fail(SN_ERR_VOID_FULL_DSA, "full DSA needs sigma_t > 0 everywhere (element %d is void)", e);
+            mask[e] = 1;
+        }
+    } else if (o->thick_rule == SN_THICK_SIGMA_S) {
+        for (int e = 0; e < m->ne; ++e) mask[e] = m->h_sigma_s[e] >= o->eta && m->h_sigma_t[e] > 0.0;
+    } else if (o->thick_rule == SN_THICK_SIGMA_T_H) {
+        const double h = m->hx;
+        for (int e = 0; e < m->ne; ++e) mask[e] = m->h_sigma_t[e] * h > o->eta;
+    } else if (o->thick_rule == SN_THICK_MASK) {
+        if (!o->mask) return fail(SN_ERR_ARG, "thick_rule MASK needs opts->mask");
+        for (int e = 0; e < m->ne; ++e) {
+            mask[e] = o->mask[e] ? 1 : 0;
+            if (mask[e] && !(m->h_sigma_t[e] > 0.0)) return fail(SN_ERR_ARG, "masked element %d is void", e);
+        }
+    } else {
+        return fail(SN_ERR_ARG, "bad thick_rule");
+    }
+    if (m->dsa && m->dsa_key_mask == mask && m->dsa_key_sigma == o->dsa_sigma) return SN_OK;
+    sn::dsa_free(m->dsa);
+    m->dsa = nullptr;
+    std::string err;
+    m->dsa = sn::dsa_build(m, mask.data(), o->dsa_sigma, err);
+    if (!m->dsa) return fail(SN_ERR_ARG, "DSA setup: %s", err.c_str());
+    m->dsa_key_mask = mask;
+    m->dsa_key_sigma = o->dsa_sigma;
+    return SN_OK;
+}
+
+static sn_status check_opts(const sn_iter_opts* o) {
+    if (!o) return fail(SN_ERR_ARG, "null opts");
+    if (o->dsa < SN_DSA_NONE || o->dsa > SN_DSA_THICK) return fail(SN_ERR_ARG, "bad dsa");
+    if (o->precision < SN_FP64 || o->precision > SN_FP32_REFINE) return fail(SN_ERR_ARG, "bad precision");
+    if (!(o->tol >= 0) || o->max_iters < 1) return fail(SN_ERR_ARG, "bad tol / max_iters");
+    if (o->dsa != SN_DSA_NONE && (!(o->inner_tol > 0) || o->inner_max_iters < 1))
+        return fail(SN_ERR_ARG, "bad inner_tol / inner_max_iters");
+    if (o->checkpoint_every > 0 && (!o->checkpoints || o->max_checkpoints < 1))
+        return fail(SN_ERR_ARG, "checkpointing needs a buffer");
+    return SN_OK;
+}
+
+sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_iter_stats* stats, void* stream) {
+    if (!m || !phi) return fail(SN_ERR_ARG, "null argument");
+    sn_status st = check_opts(o);
+    if (st != SN_OK) return st;
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    if (o->precision == SN_FP32 && (st = ensure_psi32(m)) != SN_OK) return st;
+    if (o->dsa != SN_DSA_NONE && (st = ensure_dsa(m, o)) != SN_OK) return st;
+    const size_t M = (size_t)m->ne * m->n;
+    double* half = m->d_work;
+    double* r = m->d_work + M;
+    if (!o->warm_start) CK(cudaMemsetAsync(phi, 0, M * sizeof(double), s), "memset");
+    double r0 = 0.0, rel = INFINITY;
+    int it = 0, inner_total = 0, nck = 0;
+    bool converged = false;
+    while (it < o->max_iters) {
+        CK(sn::launch_sweep(m, phi, o->precision, 1.0, s), "sweep");
+        CK(sn::launch_phi_reduce(m, o->precision, phi, half, m->d_scalars, s), "phi reduce");
+        double rr = 0.0;
+        CK(cudaMemcpyAsync(&rr, m->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+        CK(cudaStreamSynchronize(s), "sync");
+        const double rn = std::sqrt(rr);
+        if (it == 0) r0 = rn > 0 ? rn : 1.0;
+        rel = rn / r0;
+        if (stats && stats->residual_history && it < stats->history_len) stats->residual_history[it] = rel;
+        if (o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0) {
+            CK(sn::launch_axpy_norm(m, half, phi, r, m->d_scalars + 1, s), "residual");
+            CK(sn::launch_copy(phi, half, M, s), "copy");
+            int its = 0;
+            CK(sn::dsa_correct(m->dsa, r, phi, o->inner_tol, o->inner_max_iters, false, &its, s), "DSA");
+            inner_total += its;
+        } else {
+            CK(sn::launch_copy(phi, half, M, s), "copy");
+        }
+        ++it;
+        if (o->checkpoint_every > 0 && it % o->checkpoint_every == 0 && nck < o->max_checkpoints) {
+            CK(sn::launch_copy(o->checkpoints + (size_t)nck * M, phi, M, s), "checkpoint");
+            ++nck;
+        }
+        if (rel <= o->tol) {
+            converged = true;
+            break;
+        }
+    }
+    CK(cudaStreamSynchronize(s), "sync");
+    if (stats) {
+        stats->iters = it;
+        stats->rel_residual = rel;
+        stats->inner_iters_total = inner_total;
+        stats->thick_fraction = m->dsa && o->dsa != SN_DSA_NONE ? (double)sn::dsa_thick_count(m->dsa) / m->ne : 0.0;
+        stats->n_checkpoints = nck;
+        stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (!converged) return fail(SN_ERR_NOT_CONVERGED, "not converged after %d iterations (rel. residual %.3e)", it, rel);
+    return SN_OK;
+}
+
+sn_status sn_adjoint_sweep(sn_mesh* m, const double* mu, double* out, int precision, void* stream) {
+    if (!m || !mu || !out) return fail(SN_ERR_ARG, "null argument");
+    if (mu == out) return fail(SN_ERR_ARG, "mu_in and out must not alias");
+    if (precision != SN_FP64) return fail(SN_ERR_ARG, "the adjoint sweep is float64 only");
+    sn_status st = ensure_lambda(m);
+    if (st != SN_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(sn::launch_adjoint_sweep(m, mu, s), "adjoint sweep");
+    CK(sn::launch_adjoint_reduce(m, out, s), "adjoint reduce");
+    return SN_OK;
+}
+
+sn_status sn_adjoint_iterate(sn_mesh* m, const sn_iter_opts* o, const double* g, double* mu, sn_iter_stats* stats,
+                             void* stream) {
+    if (!m || !g || !mu) return fail(SN_ERR_ARG, "null argument");
+    sn_status st = check_opts(o);
+    if (st != SN_OK) return st;
+    if ((st = ensure_lambda(m)) != SN_OK) return st;
+    if (o->dsa != SN_DSA_NONE && (st = ensure_dsa(m, o)) != SN_OK) return st;
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t M = (size_t)m->ne * m->n;
+    double* half = m->d_work;
+    double* r = m->d_work + M;
+    double* tmp = m->d_work + 2 * M;
+    if (!o->warm_start) CK(cudaMemsetAsync(mu, 0, M * sizeof(double), s), "memset");
+    double r0 = 0.0, rel = INFINITY;
+    int it = 0, inner_total = 0;
+    bool converged = false;
+    while (it < o->max_iters) {
+        CK(sn::launch_adjoint_sweep(m, mu, s), "adjoint sweep");
+        CK(sn::launch_adjoint_reduce(m, tmp, s), "adjoint reduce");
+        // half = g + T^T mu ; r = half - mu
+        CK(cudaMemcpyAsync(half, g, M * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+        CK(sn::launch_axpy_add(half, tmp, M, s), "axpy");
+        CK(sn::launch_axpy_norm(m, half, mu, r, m->d_scalars, s), "residual");
+        double rr = 0.0;
+        CK(cudaMemcpyAsync(&rr, m->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+        CK(cudaStreamSynchronize(s), "sync");
+        const double rn = std::sqrt(rr);
+        if (it == 0) r0 = rn > 0 ? rn : 1.0;
+        rel = rn / r0;
+        if (stats && stats->residual_history && it < stats->history_len) stats->residual_history[it] = rel;
+        CK(sn::launch_copy(mu, half, M, s), "copy");
+        if (o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0) {
+            int its = 0;
+            CK(sn::dsa_correct(m->dsa, r, mu, o->inner_tol, o->inner_max_iters, true, &its, s), "DSA");
+            inner_total += its;
+        }
+        ++it;
+        if (rel <= o->tol) {
+            converged = true;
+            break;
+        }
+    }
+    CK(cudaStreamSynchronize(s), "sync");
+    if (stats) {
+        stats->iters = it;
+        stats->rel_residual = rel;
+        stats->inner_iters_total = inner_total;
+        stats->thick_fraction = m->dsa && o->dsa != SN_DSA_NONE ? (double)sn::dsa_thick_count(m->dsa) / m->ne : 0.0;
+        stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (!converged) return fail(SN_ERR_NOT_CONVERGED, "adjoint not converged after %d iterations (%.3e)", it, rel);
+    return SN_OK;
+}
+
+sn_status sn_gradients(sn_mesh* m, const double* phi, const double* mu, double* gt, double* gs, double* gq,
+                       void* stream) {
+    if (!m || !phi || !mu) return fail(SN_ERR_ARG, "null argument");
+    sn_status st = ensure_lambda(m);
+    if (st != SN_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(sn::launch_sweep(m, phi, SN_FP64, 1.0, s), "sweep");
+    CK(sn::launch_adjoint_sweep(m, mu, s), "adjoint sweep");
+    CK(sn::launch_gradients(m, phi, gt, gs, gq, s), "gradients");
+    return SN_OK;
+}
+
+sn_status sn_dsa_apply(sn_mesh* m, const sn_iter_opts* o, const double* x, double* y, void* stream) {
+    if (!m || !o || !x || !y) return fail(SN_ERR_ARG, "null argument");
+    sn_iter_opts oo = *o;
+    if (oo.dsa == SN_DSA_NONE) oo.dsa = SN_DSA_THICK;
+    sn_status st = ensure_dsa(m, &oo);
+    if (st != SN_OK) return st;
+    CK(sn::dsa_apply(m->dsa, x, y, (cudaStream_t)stream), "DSA apply");
+    return SN_OK;
+}
+
+sn_status sn_dsa_solve(sn_mesh* m, const sn_iter_opts* o, const double* b, double* x, int* iters, void* stream) {
+    if (!m || !o || !b || !x) return fail(SN_ERR_ARG, "null argument");
+    sn_iter_opts oo = *o;
+    if (oo.dsa == SN_DSA_NONE) oo.dsa = SN_DSA_THICK;
+    sn_status st = ensure_dsa(m, &oo);
+    if (st != SN_OK) return st;
+    int its = 0;
+    CK(sn::dsa_solve(m->dsa, b, x, oo.inner_tol, oo.inner_max_iters, &its, (cudaStream_t)stream), "DSA solve");
+    if (iters) *iters = its;
+    return SN_OK;
+}
+
+sn_status sn_get_angular_flux(sn_mesh* m, int d, int adjoint, int precision, double* out, void* stream) {
+    if (!m || !out) return fail(SN_ERR_ARG, "null argument");
+    if (d < 0 || d >= m->nd) return fail(SN_ERR_ARG, "direction out of range");
+    const size_t M = (size_t)m->ne * m->n;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (adjoint) {
+        if (!m->d_lambda) return fail(SN_ERR_ARG, "no adjoint sweep has run");
+        CK(sn::launch_copy(out, m->d_lambda + (size_t)d * M, M, s), "copy");
+    } else if (precision == SN_FP32) {
+        if (!m->d_psi32) return fail(SN_ERR_ARG, "no FP32 sweep has run");
+        CK(sn::launch_widen(out, static_cast<const float*>(m->d_psi32) + (size_t)d * M, M, s), "copy");
+    } else {
+        CK(sn::launch_copy(out, static_cast<const double*>(m->d_psi) + (size_t)d * M, M, s), "copy");
+    }
+    return SN_OK;
+}
+
+}  // extern "C"

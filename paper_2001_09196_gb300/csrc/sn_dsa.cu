@@ -1,0 +1,370 @@
+// Thick-subdomain DSA on the device (paper Sec. 2.2 Eq. DSA_fp, Algorithm 2, Sec. 4):
+// conjugate gradients on D_ff preconditioned by one symmetric multigrid V-cycle
+// (block-Jacobi on the DG level, weighted Jacobi on the continuous levels, dense coarsest).
+// All vectors and reductions are float64; dot products reduce in a fixed order.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "sn_dsa.h"
+
+namespace sn {
+
+namespace {
+
+constexpr int kBS = 256;
+inline unsigned nblk(long long n) { return (unsigned)((n + kBS - 1) / kBS); }
+
+__global__ void gather_kernel(const double* full, const int* thick, const double* mass, int nt, int n, double* out) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nt * n) return;
+    const int t = (int)(idx / n), i = (int)(idx % n);
+    const double v = full[(size_t)thick[t] * n + i];
+    out[idx] = mass ? mass[idx] * v : v;
+}
+
+__global__ void scatter_add_kernel(const double* x, const int* thick, const double* mass, int nt, int n, double* full) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nt * n) return;
+    const int t = (int)(idx / n), i = (int)(idx % n);
+    full[(size_t)thick[t] * n + i] += mass ? mass[idx] * x[idx] : x[idx];
+}
+
+__global__ void scatter_set_kernel(const double* x, const int* thick, int nt, int n, double* full) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nt * n) return;
+    const int t = (int)(idx / n), i = (int)(idx % n);
+    full[(size_t)thick[t] * n + i] = x[idx];
+}
+
+// out = b - A x (b may be null: out = A x), BSR with n x n blocks; one thread per (row block, node)
+__global__ void bsr_kernel(const int* ptr, const int* col, const double* val, int nt, int n, const double* x,
+                           const double* b, double* out) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nt * n) return;
+    const int t = (int)(idx / n), i = (int)(idx % n);
+    double s = 0.0;
+    for (int k = ptr[t]; k < ptr[t + 1]; ++k) {
+        const double* blk = val + (size_t)k * n * n + (size_t)i * n;
+        const double* xc = x + (size_t)col[k] * n;
+        for (int j = 0; j < n; ++j) s += blk[j] * xc[j];
+    }
+    out[idx] = b ? b[idx] - s : s;
+}
+
+// x (+)= omega Dinv r per block
+__global__ void block_jacobi_kernel(const double* dinv, int nt, int n, double omega, const double* r, double* x,
+                                    int accumulate) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nt * n) return;
+    const int t = (int)(idx / n), i = (int)(idx % n);
+    const double* D = dinv + (size_t)t * n * n + (size_t)i * n;
+    const double* rr = r + (size_t)t * n;
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += D[j] * rr[j];
+    x[idx] = (accumulate ? x[idx] : 0.0) + omega * s;
+}
+
+__global__ void csr_kernel(const int* ptr, const int* col, const double* val, int rows, const double* x,
+                           const double* b, double* out, int mode) {
+    // mode 0: out = M x; 1: out = b - M x; 2: out += M x
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    double s = 0.0;
+    for (int k = ptr[r]; k < ptr[r + 1]; ++k) s += val[k] * x[col[k]];
+    if (mode == 0) out[r] = s;
+    else if (mode == 1) out[r] = b[r] - s;
+    else out[r] += s;
+}
+
+__global__ void jacobi_kernel(const double* dinv, int rows, double omega, const double* r, double* x, int accumulate) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    x[i] = (accumulate ? x[i] : 0.0) + omega * dinv[i] * r[i];
+}
+
+__global__ void dense_mv_kernel(const double* A, int n, const double* b, double* x) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double s = 0.0;
+    for (int c = 0; c < n; ++c) s += A[(size_t)r * n + c] * b[c];
+    x[r] = s;
+}
+
+__global__ void dot_partial_kernel(const double* a, const double* b, long long n, double* part) {
+    __shared__ double sh[kBS];
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += a[i] * b[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void dot_final_kernel(const double* part, int n, double* out) {
+    __shared__ double sh[kBS];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+// x += alpha p, r -= alpha q with alpha = s[0] / s[1]
+__global__ void cg_update_xr(double* x, double* r, const double* p, const double* q, long long n, const double* s) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double alpha = s[0] / s[1];
+    x[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+}
+
+// p = z + beta p with beta = s[4] / s[0]; the last thread to finish cannot update s, so s[0] is
+// refreshed by a separate kernel.
+__global__ void cg_update_p(double* p, const double* z, long long n, const double* s) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double beta = s[4] / s[0];
+    p[i] = z[i] + beta * p[i];
+}
+
+__global__ void copy_scalar(double* s, int dst, int src) { s[dst] = s[src]; }
+
+constexpr int kDotBlocks = 304;  // 2 x 152 SMs
+
+template <typename T>
+cudaError_t up(T** d, const std::vector<T>& h) {
+    if (h.empty()) { *d = nullptr; return cudaSuccess; }
+    cudaError_t err = cudaMalloc(d, h.size() * sizeof(T));
+    if (err != cudaSuccess) return err;
+    return cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+cudaError_t upload(DsaHierarchy* H) {
+    if (H->uploaded) return cudaSuccess;
+    const long long N0 = (long long)H->nt * H->n;
+    cudaError_t err;
+#define UP(dst, src) if ((err = up(&(dst), src)) != cudaSuccess) return err
+    UP(H->d_thick, H->thick);
+    UP(H->d_mass_sig, H->h_mass_sig);
+    UP(H->l0.d_ptr, H->l0.ptr);
+    UP(H->l0.d_col, H->l0.col);
+    UP(H->l0.d_val, H->l0.val);
+    UP(H->l0.d_dinv, H->l0.dinv);
+    for (LevelC& L : H->levels) {
+        UP(L.d_a_ptr, L.a_ptr);
+        UP(L.d_a_col, L.a_col);
+        UP(L.d_a_val, L.a_val);
+        UP(L.d_p_ptr, L.p_ptr);
+        UP(L.d_p_col, L.p_col);
+        UP(L.d_p_val, L.p_val);
+        UP(L.d_r_ptr, L.r_ptr);
+        UP(L.d_r_col, L.r_col);
+        UP(L.d_r_val, L.r_val);
+        UP(L.d_dinv, L.dinv);
+        UP(L.d_dense, L.dense_inv);
+        for (double** v : {&L.d_x, &L.d_b, &L.d_r})
+            if ((err = cudaMalloc(v, std::max(1, L.n) * sizeof(double))) != cudaSuccess) return err;
+    }
+#undef UP
+    for (double** v : {&H->d_x, &H->d_b, &H->d_r, &H->d_z, &H->d_p, &H->d_q, &H->d_vr, &H->d_vx})
+        if ((err = cudaMalloc(v, std::max<long long>(1, N0) * sizeof(double))) != cudaSuccess) return err;
+    if ((err = cudaMalloc(&H->d_part, kDotBlocks * sizeof(double))) != cudaSuccess) return err;
+    if ((err = cudaMalloc(&H->d_s, 16 * sizeof(double))) != cudaSuccess) return err;
+    H->uploaded = true;
+    return cudaSuccess;
+}
+
+cudaError_t dot(DsaHierarchy* H, const double* a, const double* b, long long n, int slot, cudaStream_t s) {
+    SN_COUNT_LAUNCH();
+    dot_partial_kernel<<<kDotBlocks, kBS, 0, s>>>(a, b, n, H->d_part);
+    SN_COUNT_LAUNCH();
+    dot_final_kernel<<<1, kBS, 0, s>>>(H->d_part, kDotBlocks, H->d_s + slot);
+    return cudaGetLastError();
+}
+
+// continuous level l (index into H->levels): x = V(b)
+void vcycle_c(DsaHierarchy* H, size_t l, cudaStream_t s) {
+    LevelC& L = H->levels[l];
+    if (!L.dense_inv.empty()) {
+        SN_COUNT_LAUNCH();
+        dense_mv_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_dense, L.n, L.d_b, L.d_x);
+        return;
+    }
+    for (int k = 0; k < H->nu; ++k) {
+        if (k == 0) {
+            SN_COUNT_LAUNCH();
+            jacobi_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_dinv, L.n, H->omega, L.d_b, L.d_x, 0);
+        } else {
+            SN_COUNT_LAUNCH();
+            csr_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_a_ptr, L.d_a_col, L.d_a_val, L.n, L.d_x, L.d_b, L.d_r, 1);
+            SN_COUNT_LAUNCH();
+            jacobi_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_dinv, L.n, H->omega, L.d_r, L.d_x, 1);
+        }
+    }
+    SN_COUNT_LAUNCH();
+    csr_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_a_ptr, L.d_a_col, L.d_a_val, L.n, L.d_x, L.d_b, L.d_r, 1);
+    LevelC& C = H->levels[l + 1];
+    SN_COUNT_LAUNCH();
+    csr_kernel<<<nblk(C.n), kBS, 0, s>>>(C.d_r_ptr, C.d_r_col, C.d_r_val, C.n, L.d_r, nullptr, C.d_b, 0);
+    vcycle_c(H, l + 1, s);
+    SN_COUNT_LAUNCH();
+    csr_kernel<<<nblk(L.n), kBS, 0, s>>>(C.d_p_ptr, C.d_p_col, C.d_p_val, L.n, C.d_x, nullptr, L.d_x, 2);
+    for (int k = 0; k < H->nu; ++k) {
+        SN_COUNT_LAUNCH();
+        csr_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_a_ptr, L.d_a_col, L.d_a_val, L.n, L.d_x, L.d_b, L.d_r, 1);
+        SN_COUNT_LAUNCH();
+        jacobi_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_dinv, L.n, H->omega, L.d_r, L.d_x, 1);
+    }
+}
+
+// z = V(r) on the DG level
+void vcycle0(DsaHierarchy* H, const double* r, double* z, cudaStream_t s) {
+    const int nt = H->nt, n = H->n;
+    const long long N0 = (long long)nt * n;
+    const Level0& A = H->l0;
+    for (int k = 0; k < H->nu; ++k) {
+        if (k == 0) {
+            SN_COUNT_LAUNCH();
+            block_jacobi_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_dinv, nt, n, H->omega0, r, z, 0);
+        } else {
+            SN_COUNT_LAUNCH();
+            bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, nt, n, z, r, H->d_vr);
+            SN_COUNT_LAUNCH();
+            block_jacobi_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_dinv, nt, n, H->omega0, H->d_vr, z, 1);
+        }
+    }
+    if (!H->levels.empty()) {
+        SN_COUNT_LAUNCH();
+        bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, nt, n, z, r, H->d_vr);
+        LevelC& C = H->levels[0];
+        SN_COUNT_LAUNCH();
+        csr_kernel<<<nblk(C.n), kBS, 0, s>>>(C.d_r_ptr, C.d_r_col, C.d_r_val, C.n, H->d_vr, nullptr, C.d_b, 0);
+        vcycle_c(H, 0, s);
+        SN_COUNT_LAUNCH();
+        csr_kernel<<<nblk(N0), kBS, 0, s>>>(C.d_p_ptr, C.d_p_col, C.d_p_val, (int)N0, C.d_x, nullptr, z, 2);
+    }
+    for (int k = 0; k < H->nu; ++k) {
+        SN_COUNT_LAUNCH();
+        bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, nt, n, z, r, H->d_vr);
+        SN_COUNT_LAUNCH();
+        block_jacobi_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_dinv, nt, n, H->omega0, H->d_vr, z, 1);
+    }
+}
+
+// Solve D_ff x = b (thick-local vectors H->d_b -> H->d_x) by PCG.
+cudaError_t pcg(DsaHierarchy* H, double tol, int max_iters, int* iters, cudaStream_t s) {
+    const long long N0 = (long long)H->nt * H->n;
+    const Level0& A = H->l0;
+    cudaError_t err;
+    *iters = 0;
+    cudaMemsetAsync(H->d_x, 0, N0 * sizeof(double), s);
+    cudaMemcpyAsync(H->d_r, H->d_b, N0 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    dot(H, H->d_b, H->d_b, N0, 3, s);
+    double h[16];
+    if ((err = cudaMemcpyAsync(h, H->d_s, 16 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return err;
+    if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
+    const double bnorm = std::sqrt(h[3]);
+    if (bnorm == 0.0) return cudaSuccess;
+    vcycle0(H, H->d_r, H->d_z, s);
+    cudaMemcpyAsync(H->d_p, H->d_z, N0 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    dot(H, H->d_r, H->d_z, N0, 0, s);
+    for (int k = 1; k <= max_iters; ++k) {
+        SN_COUNT_LAUNCH();
+        bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, H->nt, H->n, H->d_p, nullptr, H->d_q);
+        dot(H, H->d_p, H->d_q, N0, 1, s);
+        SN_COUNT_LAUNCH();
+        cg_update_xr<<<nblk(N0), kBS, 0, s>>>(H->d_x, H->d_r, H->d_p, H->d_q, N0, H->d_s);
+        dot(H, H->d_r, H->d_r, N0, 2, s);
+        double rr;
+        if ((err = cudaMemcpyAsync(&rr, H->d_s + 2, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return err;
+        if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
+        *iters = k;
+        if (!(std::sqrt(rr) > tol * bnorm)) break;
+        vcycle0(H, H->d_r, H->d_z, s);
+        dot(H, H->d_r, H->d_z, N0, 4, s);
+        SN_COUNT_LAUNCH();
+        cg_update_p<<<nblk(N0), kBS, 0, s>>>(H->d_p, H->d_z, N0, H->d_s);
+        SN_COUNT_LAUNCH();
+        copy_scalar<<<1, 1, 0, s>>>(H->d_s, 0, 4);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+void dsa_free(DsaHierarchy* H) {
+    if (!H) return;
+    auto f = [](void* p) { if (p) cudaFree(p); };
+    f(H->d_thick); f(H->d_mass_sig);
+    f(H->l0.d_ptr); f(H->l0.d_col); f(H->l0.d_val); f(H->l0.d_dinv);
+    for (LevelC& L : H->levels) {
+        f(L.d_a_ptr); f(L.d_a_col); f(L.d_a_val); f(L.d_p_ptr); f(L.d_p_col); f(L.d_p_val);
+        f(L.d_r_ptr); f(L.d_r_col); f(L.d_r_val); f(L.d_dinv); f(L.d_dense); f(L.d_x); f(L.d_b); f(L.d_r);
+    }
+    f(H->d_x); f(H->d_b); f(H->d_r); f(H->d_z); f(H->d_p); f(H->d_q); f(H->d_vr); f(H->d_vx);
+    f(H->d_part); f(H->d_s);
+    delete H;
+}
+
+int dsa_thick_count(const DsaHierarchy* H) { return H ? H->nt : 0; }
+
+cudaError_t dsa_apply(DsaHierarchy* H, const double* x, double* y, cudaStream_t s) {
+    cudaError_t err = upload(H);
+    if (err != cudaSuccess) return err;
+    cudaMemsetAsync(y, 0, (size_t)H->ne * H->n * sizeof(double), s);
+    if (H->nt == 0) return cudaGetLastError();
+    const long long N0 = (long long)H->nt * H->n;
+    SN_COUNT_LAUNCH();
+    gather_kernel<<<nblk(N0), kBS, 0, s>>>(x, H->d_thick, nullptr, H->nt, H->n, H->d_p);
+    SN_COUNT_LAUNCH();
+    bsr_kernel<<<nblk(N0), kBS, 0, s>>>(H->l0.d_ptr, H->l0.d_col, H->l0.d_val, H->nt, H->n, H->d_p, nullptr, H->d_q);
+    SN_COUNT_LAUNCH();
+    scatter_set_kernel<<<nblk(N0), kBS, 0, s>>>(H->d_q, H->d_thick, H->nt, H->n, y);
+    return cudaGetLastError();
+}
+
+cudaError_t dsa_solve(DsaHierarchy* H, const double* b_full, double* x_full, double tol, int max_iters, int* iters,
+                      cudaStream_t s) {
+    cudaError_t err = upload(H);
+    if (err != cudaSuccess) return err;
+    cudaMemsetAsync(x_full, 0, (size_t)H->ne * H->n * sizeof(double), s);
+    *iters = 0;
+    if (H->nt == 0) return cudaGetLastError();
+    const long long N0 = (long long)H->nt * H->n;
+    SN_COUNT_LAUNCH();
+    gather_kernel<<<nblk(N0), kBS, 0, s>>>(b_full, H->d_thick, nullptr, H->nt, H->n, H->d_b);
+    if ((err = pcg(H, tol, max_iters, iters, s)) != cudaSuccess) return err;
+    SN_COUNT_LAUNCH();
+    scatter_set_kernel<<<nblk(N0), kBS, 0, s>>>(H->d_x, H->d_thick, H->nt, H->n, x_full);
+    return cudaGetLastError();
+}
+
+// Forward (Algorithm 2): phi_out[thick] += D_ff^{-1} (Sigma r)_f.
+// Transposed: phi_out[thick] += Sigma_f D_ff^{-1} r_f.
+cudaError_t dsa_correct(DsaHierarchy* H, const double* r, double* phi_out, double tol, int max_iters, bool transpose,
+                        int* iters, cudaStream_t s) {
+    cudaError_t err = upload(H);
+    if (err != cudaSuccess) return err;
+    *iters = 0;
+    if (H->nt == 0) return cudaSuccess;
+    const long long N0 = (long long)H->nt * H->n;
+    SN_COUNT_LAUNCH();
+    gather_kernel<<<nblk(N0), kBS, 0, s>>>(r, H->d_thick, transpose ? nullptr : H->d_mass_sig, H->nt, H->n, H->d_b);
+    if ((err = pcg(H, tol, max_iters, iters, s)) != cudaSuccess) return err;
+    SN_COUNT_LAUNCH();
+    scatter_add_kernel<<<nblk(N0), kBS, 0, s>>>(H->d_x, H->d_thick, transpose ? H->d_mass_sig : nullptr, H->nt, H->n,
+                                                phi_out);
+    return cudaGetLastError();
+}
+
+}  // namespace sn

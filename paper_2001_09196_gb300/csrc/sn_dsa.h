@@ -1,0 +1,48 @@
+// Internal: data of the thick-subdomain DSA operator and its multigrid hierarchy.
+#pragma once
+
+#include <vector>
+
+#include "sn_internal.h"
+
+namespace sn {
+
+constexpr int kCoarseMax = 256;  // rows at which the hierarchy stops and inverts densely
+
+struct Level0 {                  // DG space on the thick elements, BSR with n x n blocks
+    std::vector<int> ptr, col;
+    std::vector<double> val;     // nnzb x n x n (row-major blocks)
+    std::vector<double> dinv;    // nt x n x n inverse diagonal blocks
+    int *d_ptr = nullptr, *d_col = nullptr;
+    double *d_val = nullptr, *d_dinv = nullptr;
+};
+
+struct LevelC {                  // a continuous level: operator, prolongation to the finer level
+    int n = 0;
+    std::vector<int> a_ptr, a_col, p_ptr, p_col, r_ptr, r_col;
+    std::vector<double> a_val, p_val, r_val, dinv, dense_inv;
+    int *d_a_ptr = nullptr, *d_a_col = nullptr, *d_p_ptr = nullptr, *d_p_col = nullptr, *d_r_ptr = nullptr,
+        *d_r_col = nullptr;
+    double *d_a_val = nullptr, *d_p_val = nullptr, *d_r_val = nullptr, *d_dinv = nullptr, *d_dense = nullptr;
+    double *d_x = nullptr, *d_b = nullptr, *d_r = nullptr;
+};
+
+struct DsaHierarchy {
+    int n = 0, ne = 0, nt = 0;
+    std::vector<int> thick;               // thick element ids
+    std::vector<double> h_mass_sig;       // nt x n: sigma_Sigma * collocated mass
+    Level0 l0;
+    std::vector<LevelC> levels;           // level 1 .. coarsest
+    int* d_thick = nullptr;
+    double* d_mass_sig = nullptr;
+    // PCG vectors on the thick DOFs (nt x n)
+    double *d_x = nullptr, *d_b = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr;
+    double *d_vr = nullptr, *d_vx = nullptr;  // V-cycle level-0 residual / correction
+    double* d_part = nullptr;                 // reduction partials
+    double* d_s = nullptr;                    // device scalars
+    bool uploaded = false;
+    double omega0 = 0.6, omega = 0.6;         // damping of block-Jacobi (level 0) / Jacobi (levels >= 1)
+    int nu = 2;                               // pre- and post-smoothing steps
+};
+
+}  // namespace sn

@@ -1,0 +1,575 @@
+// Host-side setup of the thick-subdomain DSA operator and its multigrid hierarchy.
+//
+// Operator (paper Sec. 4.1, Eq. SIP with the max-floored penalty of Eq. ModifiedF0; Sec. 4.2,
+// the heterogeneous operator is the principal submatrix on the thick elements):
+//   a(u,v) = sum_K (D grad u, grad v)_K + (sigma_a u, v)_K
+//          + sum_{interior thick-thick F} <kappa [u],[v]> - <{D grad u.n},[v]> - <{D grad v.n},[u]>
+//          + sum_{F on the thick region's boundary} <kappa u,v> - 1/2<D grad u.n, v> - 1/2<D grad v.n, u>
+// D = 1/(3 sigma_t), sigma_a = sigma_t - sigma_s, kappa = max(1/4, c(p) (D-/h- + D+/h+)/2) on interior
+// faces and max(1/4, c(p) D/h) on boundary faces, c(p) = 2 p (p+1), h = |K|/|F|.  A face to a
+// non-thick neighbour is a face to a zero exterior state.  All integrals use the (p+1)-point
+// Gauss rule per axis, on which the nodal basis lives (so the volume terms are collocated).
+//
+// Multigrid (replaces the paper's BoomerAMG, Sec. 5): level 0 is the DG space on the thick
+// elements with element block-Jacobi smoothing; level 1 is continuous Q1 on the vertices of
+// thick elements (prolongation = the element's own bilinear/trilinear map evaluated at its
+// nodes); coarser levels halve the vertex grid per axis with linear interpolation; every
+// coarse operator is the Galerkin product P^T A P; the coarsest is inverted densely.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "sn_dsa.h"
+
+namespace sn {
+
+namespace {
+
+struct Csr {
+    int rows = 0, cols = 0;
+    std::vector<int> ptr, col;
+    std::vector<double> val;
+};
+
+Csr transpose(const Csr& A) {
+    Csr T;
+    T.rows = A.cols;
+    T.cols = A.rows;
+    T.ptr.assign(T.rows + 1, 0);
+    for (int c : A.col) T.ptr[c + 1]++;
+    for (int r = 0; r < T.rows; ++r) T.ptr[r + 1] += T.ptr[r];
+    T.col.resize(A.col.size());
+    T.val.resize(A.val.size());
+    std::vector<int> fill(T.ptr.begin(), T.ptr.end() - 1);
+    for (int r = 0; r < A.rows; ++r)
+        for (int k = A.ptr[r]; k < A.ptr[r + 1]; ++k) {
+            int pos = fill[A.col[k]]++;
+            T.col[pos] = r;
+            T.val[pos] = A.val[k];
+        }
+    return T;
+}
+
+// C = A * B (row-wise accumulation with a dense marker).
+Csr multiply(const Csr& A, const Csr& B) {
+    Csr C;
+    C.rows = A.rows;
+    C.cols = B.cols;
+    C.ptr.assign(A.rows + 1, 0);
+    std::vector<int> mark(B.cols, -1);
+    std::vector<double> acc(B.cols, 0.0);
+    std::vector<int> used;
+    for (int r = 0; r < A.rows; ++r) {
+        used.clear();
+        for (int k = A.ptr[r]; k < A.ptr[r + 1]; ++k) {
+            const int a = A.col[k];
+            const double av = A.val[k];
+            for (int l = B.ptr[a]; l < B.ptr[a + 1]; ++l) {
+                const int c = B.col[l];
+                if (mark[c] != r) {
+                    mark[c] = r;
+                    acc[c] = 0.0;
+                    used.push_back(c);
+                }
+                acc[c] += av * B.val[l];
+            }
+        }
+        std::sort(used.begin(), used.end());
+        for (int c : used) {
+            C.col.push_back(c);
+            C.val.push_back(acc[c]);
+        }
+        C.ptr[r + 1] = (int)C.col.size();
+    }
+    return C;
+}
+
+// In-place inverse of a small SPD-ish dense matrix (Gauss-Jordan, partial pivoting).
+bool invert(std::vector<double>& A, int n) {
+    std::vector<double> I(n * n, 0.0);
+    for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+        if (A[piv * n + c] == 0.0) return false;
+        if (piv != c)
+            for (int q = 0; q < n; ++q) {
+                std::swap(A[c * n + q], A[piv * n + q]);
+                std::swap(I[c * n + q], I[piv * n + q]);
+            }
+        const double inv = 1.0 / A[c * n + c];
+        for (int q = 0; q < n; ++q) {
+            A[c * n + q] *= inv;
+            I[c * n + q] *= inv;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = A[r * n + c];
+            if (f == 0.0) continue;
+            for (int q = 0; q < n; ++q) {
+                A[r * n + q] -= f * A[c * n + q];
+                I[r * n + q] -= f * I[c * n + q];
+            }
+        }
+    }
+    A.swap(I);
+    return true;
+}
+
+struct ElemMap {
+    int dim;
+    double v[8][3];  // corners, corner c: bit a set -> xi_a = +1
+    // x(xi), J(xi) (J[r][c] = dx_r/dxi_c)
+    void eval(const double* xi, double* x, double J[3][3]) const {
+        for (int r = 0; r < dim; ++r) {
+            x[r] = 0.0;
+            for (int c = 0; c < dim; ++c) J[r][c] = 0.0;
+        }
+        const int nc = 1 << dim;
+        for (int c = 0; c < nc; ++c) {
+            double fac[3], s[3];
+            for (int a = 0; a < dim; ++a) {
+                s[a] = ((c >> a) & 1) ? 1.0 : -1.0;
+                fac[a] = 0.5 * (1.0 + s[a] * xi[a]);
+            }
+            double N = 1.0;
+            for (int a = 0; a < dim; ++a) N *= fac[a];
+            for (int r = 0; r < dim; ++r) x[r] += N * v[c][r];
+            for (int a = 0; a < dim; ++a) {
+                double dN = 0.5 * s[a];
+                for (int b = 0; b < dim; ++b)
+                    if (b != a) dN *= fac[b];
+                for (int r = 0; r < dim; ++r) J[r][a] += dN * v[c][r];
+            }
+        }
+    }
+};
+
+double det_inv(int dim, const double J[3][3], double Ji[3][3]) {
+    if (dim == 2) {
+        const double d = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        Ji[0][0] = J[1][1] / d;
+        Ji[0][1] = -J[0][1] / d;
+        Ji[1][0] = -J[1][0] / d;
+        Ji[1][1] = J[0][0] / d;
+        return d;
+    }
+    const double d = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                     J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / d;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / d;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / d;
+    Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / d;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / d;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / d;
+    Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / d;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / d;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / d;
+    return d;
+}
+
+// Tensor nodal basis values and reference gradients at a reference point.
+void basis_at(const GL1D& g, int dim, const double* xi, std::vector<double>& val, std::vector<double>& grad) {
+    const int Q = g.p + 1;
+    double v1[3][kMaxP + 1], d1[3][kMaxP + 1];
+    for (int a = 0; a < dim; ++a) lagrange_eval(g, xi[a], v1[a], d1[a]);
+    const int N = dim == 2 ? Q * Q : Q * Q * Q;
+    val.assign(N, 0.0);
+    grad.assign(N * dim, 0.0);
+    for (int i = 0; i < N; ++i) {
+        int idx[3] = {i % Q, (i / Q) % Q, i / (Q * Q)};
+        double v = 1.0;
+        for (int a = 0; a < dim; ++a) v *= v1[a][idx[a]];
+        val[i] = v;
+        for (int b = 0; b < dim; ++b) {
+            double gb = 1.0;
+            for (int a = 0; a < dim; ++a) gb *= (a == b ? d1[a][idx[a]] : v1[a][idx[a]]);
+            grad[i * dim + b] = gb;
+        }
+    }
+}
+
+}  // namespace
+
+DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sigma, std::string& err) {
+    auto* H = new DsaHierarchy();
+    const int dim = m->dim, p = m->p, n = m->n, Q = p + 1;
+    H->n = n;
+    H->ne = m->ne;
+    for (int e = 0; e < m->ne; ++e)
+        if (mask[e]) H->thick.push_back(e);
+    const int nt = (int)H->thick.size();
+    H->nt = nt;
+    if (nt == 0) return H;
+    std::vector<int> local(m->ne, -1);
+    for (int t = 0; t < nt; ++t) local[H->thick[t]] = t;
+    const GL1D g = gauss_legendre_nodal(p);
+    const double cp = 2.0 * p * (p + 1);
+
+    auto elem_map = [&](int e) {
+        ElemMap em;
+        em.dim = dim;
+        if (dim == 2) {
+            const double* c = &m->h_corners[8 * (size_t)e];
+            for (int q = 0; q < 4; ++q) {
+                em.v[q][0] = c[2 * q];
+                em.v[q][1] = c[2 * q + 1];
+                em.v[q][2] = 0.0;
+            }
+        } else {
+            const int i = e % m->nx, j = (e / m->nx) % m->ny, k = e / (m->nx * m->ny);
+            for (int q = 0; q < 8; ++q) {
+                em.v[q][0] = (i + (q & 1)) * m->hx;
+                em.v[q][1] = (j + ((q >> 1) & 1)) * m->hy;
+                em.v[q][2] = (k + ((q >> 2) & 1)) * m->hz;
+            }
+        }
+        return em;
+    };
+    auto neighbor = [&](int e, int f) {
+        const int ax = f >> 1, side = f & 1;
+        int i = e % m->nx, j = (e / m->nx) % m->ny, k = e / (m->nx * m->ny);
+        const int dl = side ? 1 : -1;
+        if (ax == 0) { i += dl; if (i < 0 || i >= m->nx) return -1; }
+        else if (ax == 1) { j += dl; if (j < 0 || j >= m->ny) return -1; }
+        else { k += dl; if (k < 0 || k >= m->nz) return -1; }
+        return i + m->nx * (j + m->ny * k);
+    };
+
+    // per thick element: volume, D, sigma_a, rhs mass
+    std::vector<double> vol(nt), Dc(nt), sa(nt);
+    H->h_mass_sig.assign((size_t)nt * n, 0.0);
+    std::vector<std::vector<double>> blocks;  // BSR blocks
+    std::vector<std::map<int, int>> rowcols(nt);
+    auto block = [&](int r, int c) -> double* {
+        auto it = rowcols[r].find(c);
+        if (it == rowcols[r].end()) {
+            blocks.emplace_back(n * n, 0.0);
+            rowcols[r][c] = (int)blocks.size() - 1;
+            return blocks.back().data();
+        }
+        return blocks[it->second].data();
+    };
+    std::vector<double> val, grad;
+    const int NQ = n;  // volume points = nodes
+    for (int t = 0; t < nt; ++t) {
+        const int e = H->thick[t];
+        const double st = m->h_sigma_t[e], ss = m->h_sigma_s[e];
+        if (!(st > 0.0)) {
+            err = "DSA on an element with sigma_t = 0";
+            delete H;
+            return nullptr;
+        }
+        Dc[t] = 1.0 / (3.0 * st);
+        sa[t] = st - ss;
+        const double sig = dsa_sigma == SN_DSA_SIGMA_T ? st : ss;
+        ElemMap em = elem_map(e);
+        double* K = block(t, t);
+        double V = 0.0;
+        for (int q = 0; q < NQ; ++q) {
+            const int qi[3] = {q % Q, (q / Q) % Q, q / (Q * Q)};
+            double xi[3], W = 1.0;
+            for (int a = 0; a < dim; ++a) {
+                xi[a] = g.x[qi[a]];
+                W *= g.w[qi[a]];
+            }
+            double x[3], J[3][3], Ji[3][3];
+            em.eval(xi, x, J);
+            const double dJ = det_inv(dim, J, Ji);
+            V += W * dJ;
+            basis_at(g, dim, xi, val, grad);
+            // physical gradients
+            std::vector<double> gp(n * dim, 0.0);
+            for (int i = 0; i < n; ++i)
+                for (int r = 0; r < dim; ++r) {
+                    double s = 0.0;
+                    for (int k = 0; k < dim; ++k) s += Ji[k][r] * grad[i * dim + k];
+                    gp[i * dim + r] = s;
+                }
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    double s = 0.0;
+                    for (int r = 0; r < dim; ++r) s += gp[i * dim + r] * gp[j * dim + r];
+                    K[i * n + j] += W * dJ * (Dc[t] * s + sa[t] * val[i] * val[j]);
+                }
+            H->h_mass_sig[(size_t)t * n + q] = sig * W * dJ;  // collocated mass at node q
+        }
+        vol[t] = V;
+    }
+    // faces
+    const int QF = dim == 2 ? Q : Q * Q;
+    for (int t = 0; t < nt; ++t) {
+        const int e = H->thick[t];
+        ElemMap em = elem_map(e);
+        for (int f = 0; f < 2 * dim; ++f) {
+            const int ax = f >> 1, side = f & 1;
+            const double s = side ? 1.0 : -1.0;
+            const int u = neighbor(e, f);
+            const int o = u >= 0 ? local[u] : -1;
+            if (o >= 0 && side == 0) continue;  // interior faces are assembled from their side-1 element
+            ElemMap emo;
+            if (o >= 0) emo = elem_map(u);
+            // face quadrature data
+            std::vector<double> dS(QF), nrm(QF * 3), Be(QF * n), Dne(QF * n), Bo, Dno;
+            if (o >= 0) {
+                Bo.assign(QF * n, 0.0);
+                Dno.assign(QF * n, 0.0);
+            }
+            double area = 0.0;
+            for (int qf = 0; qf < QF; ++qf) {
+                int tq[2] = {qf % Q, qf / Q};
+                double xi[3], xio[3], Wt = 1.0;
+                int c = 0;
+                for (int a = 0; a < dim; ++a) {
+                    if (a == ax) {
+                        xi[a] = s;
+                        xio[a] = -s;
+                    } else {
+                        xi[a] = g.x[tq[c]];
+                        xio[a] = xi[a];
+                        Wt *= g.w[tq[c]];
+                        ++c;
+                    }
+                }
+                double x[3], J[3][3], Ji[3][3];
+                em.eval(xi, x, J);
+                const double dJ = det_inv(dim, J, Ji);
+                // Nanson: n dS = det J J^{-T} (s e_ax) dt  -> components s * dJ * Ji[ax][r]
+                double Nv[3] = {0, 0, 0}, len = 0.0;
+                for (int r = 0; r < dim; ++r) {
+                    Nv[r] = s * dJ * Ji[ax][r];
+                    len += Nv[r] * Nv[r];
+                }
+                len = std::sqrt(len);
+                dS[qf] = len * Wt;
+                area += dS[qf];
+                for (int r = 0; r < dim; ++r) nrm[qf * 3 + r] = Nv[r] / len;
+                basis_at(g, dim, xi, val, grad);
+                for (int i = 0; i < n; ++i) {
+                    Be[qf * n + i] = val[i];
+                    double dn = 0.0;
+                    for (int r = 0; r < dim; ++r) {
+                        double gr = 0.0;
+                        for (int k = 0; k < dim; ++k) gr += Ji[k][r] * grad[i * dim + k];
+                        dn += gr * nrm[qf * 3 + r];
+                    }
+                    Dne[qf * n + i] = dn;
+                }
+                if (o >= 0) {
+                    double xo[3], Jo[3][3], Jio[3][3];
+                    emo.eval(xio, xo, Jo);
+                    det_inv(dim, Jo, Jio);
+                    basis_at(g, dim, xio, val, grad);
+                    for (int i = 0; i < n; ++i) {
+                        Bo[qf * n + i] = val[i];
+                        double dn = 0.0;
+                        for (int r = 0; r < dim; ++r) {
+                            double gr = 0.0;
+                            for (int k = 0; k < dim; ++k) gr += Jio[k][r] * grad[i * dim + k];
+                            dn += gr * nrm[qf * 3 + r];
+                        }
+                        Dno[qf * n + i] = dn;
+                    }
+                }
+            }
+            const double h = vol[t] / area;
+            if (o < 0) {
+                const double kap = std::max(0.25, cp * Dc[t] / h);
+                double* K = block(t, t);
+                for (int qf = 0; qf < QF; ++qf)
+                    for (int i = 0; i < n; ++i)
+                        for (int j = 0; j < n; ++j)
+                            K[i * n + j] += dS[qf] * (kap * Be[qf * n + i] * Be[qf * n + j] -
+                                                      0.5 * Dc[t] * Dne[qf * n + j] * Be[qf * n + i] -
+                                                      0.5 * Dc[t] * Dne[qf * n + i] * Be[qf * n + j]);
+            } else {
+                const double ho = vol[o] / area;
+                const double kap = std::max(0.25, cp * 0.5 * (Dc[t] / h + Dc[o] / ho));
+                struct Side { int r; const std::vector<double>* B; const std::vector<double>* Dn; double D, sg; };
+                Side sides[2] = {{t, &Be, &Dne, Dc[t], 1.0}, {o, &Bo, &Dno, Dc[o], -1.0}};
+                for (const Side& A : sides)
+                    for (const Side& Bs : sides) {
+                        double* K = block(A.r, Bs.r);
+                        for (int qf = 0; qf < QF; ++qf)
+                            for (int i = 0; i < n; ++i)
+                                for (int j = 0; j < n; ++j)
+                                    K[i * n + j] += dS[qf] * (kap * A.sg * Bs.sg * (*A.B)[qf * n + i] * (*Bs.B)[qf * n + j] -
+                                                              0.5 * Bs.D * A.sg * (*Bs.Dn)[qf * n + j] * (*A.B)[qf * n + i] -
+                                                              0.5 * A.D * Bs.sg * (*A.Dn)[qf * n + i] * (*Bs.B)[qf * n + j]);
+                    }
+            }
+        }
+    }
+    // BSR level 0 + expanded CSR for the Galerkin products
+    Level0& L0 = H->l0;
+    L0.ptr.assign(nt + 1, 0);
+    for (int t = 0; t < nt; ++t) {
+        for (auto& kv : rowcols[t]) {
+            L0.col.push_back(kv.first);
+            L0.val.insert(L0.val.end(), blocks[kv.second].begin(), blocks[kv.second].end());
+        }
+        L0.ptr[t + 1] = (int)L0.col.size();
+    }
+    L0.dinv.resize((size_t)nt * n * n);
+    for (int t = 0; t < nt; ++t) {
+        std::vector<double> B = blocks[rowcols[t][t]];
+        if (!invert(B, n)) {
+            err = "singular diagonal block in the DSA operator";
+            delete H;
+            return nullptr;
+        }
+        std::copy(B.begin(), B.end(), L0.dinv.begin() + (size_t)t * n * n);
+    }
+    Csr A;
+    A.rows = A.cols = nt * n;
+    A.ptr.assign(nt * n + 1, 0);
+    for (int t = 0; t < nt; ++t)
+        for (int i = 0; i < n; ++i) {
+            for (int k = L0.ptr[t]; k < L0.ptr[t + 1]; ++k)
+                for (int j = 0; j < n; ++j) {
+                    A.col.push_back(L0.col[k] * n + j);
+                    A.val.push_back(L0.val[(size_t)k * n * n + i * n + j]);
+                }
+            A.ptr[t * n + i + 1] = (int)A.col.size();
+        }
+
+    // level 1: continuous Q1 on the vertices of thick elements
+    const int vx = m->nx + 1, vy = m->ny + 1, vz = dim == 3 ? m->nz + 1 : 1;
+    std::vector<int> vid((size_t)vx * vy * vz, -1);
+    std::vector<int> vgrid;  // active vertex -> grid index
+    for (int t = 0; t < nt; ++t) {
+        const int e = H->thick[t];
+        const int i = e % m->nx, j = (e / m->nx) % m->ny, k = e / (m->nx * m->ny);
+        for (int c = 0; c < (1 << dim); ++c) {
+            const size_t gid = (i + (c & 1)) + (size_t)vx * ((j + ((c >> 1) & 1)) + (size_t)vy * (dim == 3 ? k + ((c >> 2) & 1) : 0));
+            if (vid[gid] < 0) {
+                vid[gid] = (int)vgrid.size();
+                vgrid.push_back((int)gid);
+            }
+        }
+    }
+    Csr P;
+    P.rows = nt * n;
+    P.cols = (int)vgrid.size();
+    P.ptr.assign(P.rows + 1, 0);
+    for (int t = 0; t < nt; ++t) {
+        const int e = H->thick[t];
+        const int i = e % m->nx, j = (e / m->nx) % m->ny, k = e / (m->nx * m->ny);
+        for (int q = 0; q < n; ++q) {
+            const int qi[3] = {q % Q, (q / Q) % Q, q / (Q * Q)};
+            std::vector<std::pair<int, double>> ent;
+            for (int c = 0; c < (1 << dim); ++c) {
+                double N = 1.0;
+                for (int a = 0; a < dim; ++a) N *= 0.5 * (1.0 + (((c >> a) & 1) ? 1.0 : -1.0) * g.x[qi[a]]);
+                const size_t gid = (i + (c & 1)) + (size_t)vx * ((j + ((c >> 1) & 1)) + (size_t)vy * (dim == 3 ? k + ((c >> 2) & 1) : 0));
+                ent.push_back({vid[gid], N});
+            }
+            std::sort(ent.begin(), ent.end());
+            for (auto& pr : ent) {
+                P.col.push_back(pr.first);
+                P.val.push_back(pr.second);
+            }
+            P.ptr[t * n + q + 1] = (int)P.col.size();
+        }
+    }
+    struct GridLevel { int nx, ny, nz; std::vector<int> gids; };  // cells per axis, active vertex grid ids
+    GridLevel cur{m->nx, m->ny, dim == 3 ? m->nz : 0, vgrid};
+    Csr Acur = A;
+    Csr Pcur = P;
+    for (int lev = 1; lev < 32; ++lev) {
+        Csr Pt = transpose(Pcur);
+        Csr Ac = multiply(Pt, multiply(Acur, Pcur));
+        LevelC L;
+        L.n = Ac.rows;
+        L.p_ptr = Pcur.ptr; L.p_col = Pcur.col; L.p_val = Pcur.val;
+        L.r_ptr = Pt.ptr; L.r_col = Pt.col; L.r_val = Pt.val;
+        L.a_ptr = Ac.ptr; L.a_col = Ac.col; L.a_val = Ac.val;
+        L.dinv.assign(L.n, 0.0);
+        for (int r = 0; r < Ac.rows; ++r)
+            for (int k = Ac.ptr[r]; k < Ac.ptr[r + 1]; ++k)
+                if (Ac.col[k] == r) L.dinv[r] = 1.0 / Ac.val[k];
+        const bool coarsest = Ac.rows <= kCoarseMax || (cur.nx <= 1 && cur.ny <= 1 && cur.nz <= 1);
+        if (coarsest) {
+            std::vector<double> Dm((size_t)Ac.rows * Ac.rows, 0.0);
+            for (int r = 0; r < Ac.rows; ++r)
+                for (int k = Ac.ptr[r]; k < Ac.ptr[r + 1]; ++k) Dm[(size_t)r * Ac.rows + Ac.col[k]] = Ac.val[k];
+            if (!invert(Dm, Ac.rows)) {
+                err = "singular coarsest DSA operator";
+                delete H;
+                return nullptr;
+            }
+            L.dense_inv = Dm;
+            H->levels.push_back(std::move(L));
+            break;
+        }
+        H->levels.push_back(std::move(L));
+        // next vertex grid: half the cells per axis (rounded up), linear interpolation
+        GridLevel nxt{(cur.nx + 1) / 2, (cur.ny + 1) / 2, dim == 3 ? (cur.nz + 1) / 2 : 0, {}};
+        const int fx = cur.nx + 1, fy = cur.ny + 1;
+        const int cx = nxt.nx + 1, cy = nxt.ny + 1, cz = dim == 3 ? nxt.nz + 1 : 1;
+        std::vector<int> cid((size_t)cx * cy * cz, -1);
+        std::vector<std::vector<std::pair<size_t, double>>> rows(cur.gids.size());
+        for (size_t r = 0; r < cur.gids.size(); ++r) {
+            const int gidv = cur.gids[r];
+            const int I = gidv % fx, J = (gidv / fx) % fy, K = gidv / (fx * fy);
+            int ci[3][2];
+            double cw[3][2];
+            int cnt[3];
+            const int idx[3] = {I, J, K};
+            for (int a = 0; a < 3; ++a) {
+                if (a >= dim) { ci[a][0] = 0; cw[a][0] = 1.0; cnt[a] = 1; continue; }
+                if (idx[a] % 2 == 0) { ci[a][0] = idx[a] / 2; cw[a][0] = 1.0; cnt[a] = 1; }
+                else { ci[a][0] = (idx[a] - 1) / 2; ci[a][1] = (idx[a] + 1) / 2; cw[a][0] = cw[a][1] = 0.5; cnt[a] = 2; }
+            }
+            for (int a0 = 0; a0 < cnt[0]; ++a0)
+                for (int a1 = 0; a1 < cnt[1]; ++a1)
+                    for (int a2 = 0; a2 < cnt[2]; ++a2) {
+                        const size_t cg = ci[0][a0] + (size_t)cx * (ci[1][a1] + (size_t)cy * ci[2][a2]);
+                        rows[r].push_back({cg, cw[0][a0] * cw[1][a1] * cw[2][a2]});
+                        if (cid[cg] < 0) cid[cg] = 0;
+                    }
+        }
+        int nc = 0;
+        for (size_t cg = 0; cg < cid.size(); ++cg)
+            if (cid[cg] >= 0) {
+                cid[cg] = nc++;
+                nxt.gids.push_back((int)cg);
+            }
+        Csr Pn;
+        Pn.rows = (int)cur.gids.size();
+        Pn.cols = nc;
+        Pn.ptr.assign(Pn.rows + 1, 0);
+        for (size_t r = 0; r < rows.size(); ++r) {
+            std::vector<std::pair<int, double>> ent;
+            for (auto& pr : rows[r]) ent.push_back({cid[pr.first], pr.second});
+            std::sort(ent.begin(), ent.end());
+            for (auto& pr : ent) {
+                Pn.col.push_back(pr.first);
+                Pn.val.push_back(pr.second);
+            }
+            Pn.ptr[r + 1] = (int)Pn.col.size();
+        }
+        if (nc >= (int)cur.gids.size()) {  // no coarsening possible: make this level the coarsest
+            LevelC& last = H->levels.back();
+            std::vector<double> Dm((size_t)last.n * last.n, 0.0);
+            for (int r = 0; r < last.n; ++r)
+                for (int k = last.a_ptr[r]; k < last.a_ptr[r + 1]; ++k) Dm[(size_t)r * last.n + last.a_col[k]] = last.a_val[k];
+            if (!invert(Dm, last.n)) {
+                err = "singular coarsest DSA operator";
+                delete H;
+                return nullptr;
+            }
+            last.dense_inv = Dm;
+            break;
+        }
+        Acur = Ac;
+        Pcur = Pn;
+        cur = nxt;
+    }
+    return H;
+}
+
+}  // namespace sn

@@ -1,0 +1,119 @@
+// Internal declarations of libsn (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sn.h"
+
+namespace sn {
+
+constexpr int kMaxP = 3;
+
+// Number of kernels this library has launched (reported by sn_launch_count).
+extern std::atomic<long long> g_launches;
+#define SN_COUNT_LAUNCH() (::sn::g_launches.fetch_add(1, std::memory_order_relaxed))
+constexpr double kFourPi = 12.566370614359172953850573533118;
+
+// 1D Gauss-Legendre nodal data for one polynomial order p (p+1 nodes).
+struct GL1D {
+    int p = 0;
+    double x[kMaxP + 1] = {};               // nodes on [-1, 1]
+    double w[kMaxP + 1] = {};               // weights
+    double lm[kMaxP + 1] = {};              // l_k(-1)
+    double lp[kMaxP + 1] = {};              // l_k(+1)
+    double dm[kMaxP + 1][kMaxP + 1] = {};   // dm[a][k] = l_k'(x_a)
+    double dlm[kMaxP + 1] = {};             // l_k'(-1)
+    double dlp[kMaxP + 1] = {};             // l_k'(+1)
+};
+
+GL1D gauss_legendre_nodal(int p);
+void lagrange_eval(const GL1D& g, double t, double* val, double* der);
+
+// Level-symmetric S_N set; returns false for an unsupported order.
+bool level_symmetric(int N, int dim, std::vector<double>& dirs, std::vector<double>& wts);
+
+// Everything a sweep kernel reads, by value.
+struct SweepArgs {
+    int dim, p, nx, ny, nz, ne, nd;
+    double hx, hy, hz;              // 3D uniform spacing
+    double psi_inc;
+    const double* dirs;             // nd x 3
+    const double* corners;          // 2D: ne x 8 = (x00,y00,x10,y10,x01,y01,x11,y11); 3D: null
+    const double* sigma_t;
+    const double* sigma_s;
+    const double* q;
+    const double* phi;              // scattering source (nodal), may be null (= 0)
+    const double* src_scale;        // unused (reserved)
+    void* psi;                      // nd x ne x n, float64 or float32
+    const int2* items;              // (dir, elem) sorted by level
+    double q_scale;                 // multiplies q (1 normally, 0 for homogeneous solves)
+};
+
+struct LevelSets {
+    std::vector<long long> level_ptr;   // host copy, n_levels + 1
+    int2* items = nullptr;              // device, sorted by (level, dir, elem)
+    int n_levels = 0;
+};
+
+struct DsaHierarchy;  // sn_dsa.cu
+
+}  // namespace sn
+
+struct sn_mesh {
+    sn_mesh_desc desc{};
+    int dim = 2, p = 1, n = 4, ne = 0, nd = 0;
+    int nx = 0, ny = 0, nz = 1;
+    double hx = 0, hy = 0, hz = 0;
+    std::vector<double> h_dirs, h_wts, h_corners;
+    std::vector<double> h_sigma_t, h_sigma_s, h_q;  // host mirrors for setup
+    double* d_dirs = nullptr;
+    double* d_wts = nullptr;
+    double* d_corners = nullptr;
+    double* d_sigma_t = nullptr;
+    double* d_sigma_s = nullptr;
+    double* d_q = nullptr;
+    void* d_psi = nullptr;          // forward angular fluxes (float64 storage)
+    void* d_psi32 = nullptr;        // float32 angular fluxes of the FP32 form
+    double* d_lambda = nullptr;     // adjoint angular fluxes
+    double* d_work = nullptr;       // 4 x ne x n scratch vectors for iterations
+    double* d_red = nullptr;        // reduction partials
+    int red_blocks = 0;
+    double* d_scalars = nullptr;    // small device scalars
+    sn::LevelSets levels;
+    sn::DsaHierarchy* dsa = nullptr;
+    int dsa_key_dsa = -1, dsa_key_rule = -1, dsa_key_sigma = -1;
+    double dsa_key_eta = 0;
+    std::vector<unsigned char> dsa_key_mask;
+};
+
+namespace sn {
+// sn_sweep.cu
+cudaError_t build_levels(sn_mesh* m, cudaStream_t s, bool* cycle);
+cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double q_scale, cudaStream_t s);
+cudaError_t launch_adjoint_sweep(sn_mesh* m, const double* mu, cudaStream_t s);
+cudaError_t launch_phi_reduce(sn_mesh* m, int precision, const double* phi_in, double* phi_out, double* d_rr,
+                              cudaStream_t s);
+cudaError_t launch_adjoint_reduce(sn_mesh* m, double* out, cudaStream_t s);
+cudaError_t launch_gradients(sn_mesh* m, const double* phi, double* gt, double* gs, double* gq, cudaStream_t s);
+cudaError_t launch_axpy_norm(sn_mesh* m, const double* a, const double* b, double* out, double* d_rr,
+                             cudaStream_t s);
+cudaError_t launch_copy(double* dst, const double* src, size_t n, cudaStream_t s);
+cudaError_t launch_axpy_add(double* y, const double* x, size_t n, cudaStream_t s);  // y += x
+cudaError_t launch_widen(double* y, const float* x, size_t n, cudaStream_t s);
+// sn_dsa.cu
+DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sigma, std::string& err);
+void dsa_free(DsaHierarchy* h);
+int dsa_thick_count(const DsaHierarchy* h);
+// y = D_ff x (scatter into [elem][node], zeros elsewhere)
+cudaError_t dsa_apply(DsaHierarchy* h, const double* x, double* y, cudaStream_t s);
+// phi_out = phi_half + E_f D_ff^{-1} Sigma_f r (transpose = false); returns PCG iterations in *iters.
+cudaError_t dsa_correct(DsaHierarchy* h, const double* r, double* phi_out, double tol, int max_iters,
+                        bool transpose, int* iters, cudaStream_t s);
+cudaError_t dsa_solve(DsaHierarchy* h, const double* b_full, double* x_full, double tol, int max_iters, int* iters,
+                      cudaStream_t s);
+}  // namespace sn

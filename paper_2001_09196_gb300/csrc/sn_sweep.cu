@@ -1,0 +1,842 @@
+// Upwind DG S_N sweep kernels for sm_103a.
+//
+// Discretisation (paper Sec. 1, Eq. sntransport; Sec. 4.1, Eq. Tmat1): on element K and
+// direction Omega, with Q_p nodal basis at the (p+1)^dim tensor Gauss-Legendre points,
+//   -(psi, Omega.grad v)_K + (sigma_t psi, v)_K + sum_{F outflow} <(Omega.n) psi, v>_F
+//        = (S, v)_K - sum_{F inflow} <(Omega.n) psi_up, v>_F,   S = (q + sigma_s phi)/(4 pi).
+// Gauss-Legendre collocation integrates every term exactly on bilinear (2D) and affine
+// (3D) elements, so the mass matrix is diagonal, M_i = W_i det J(x_i), and the advection
+// couples only nodes on a common coordinate line.  With b = adj(J) Omega (the contravariant
+// flux; for a bilinear map b_1 depends on xi only and b_2 on eta only):
+//   A_ij = sigma_t M_i delta_ij - W_j b(x_j) . grad_ref l_i(x_j) + outflow face terms.
+// The face flux factor of face (axis a, side s) is F = s b_a evaluated on the face; it is
+// computed from the element's edge vectors so that a face gives exactly -F to its neighbour.
+// The transport update (Sec. 1) solves the element systems in upwind order: per direction,
+// Kahn level sets are built on the device, and every level of every direction is one
+// launch of thread-per-(element, direction) work in which each thread forms A_e in
+// registers and solves it by unpivoted LU (A_e has a positive definite symmetric part,
+// (sigma_t u,u) + 1/2 <|Omega.n| u, u>, so every leading minor is nonsingular).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "sn_internal.h"
+
+namespace sn {
+
+__constant__ double c_x[kMaxP + 1][kMaxP + 1];
+__constant__ double c_w[kMaxP + 1][kMaxP + 1];
+__constant__ double c_lm[kMaxP + 1][kMaxP + 1];
+__constant__ double c_lp[kMaxP + 1][kMaxP + 1];
+__constant__ double c_dm[kMaxP + 1][kMaxP + 1][kMaxP + 1];
+
+cudaError_t upload_gl_constants() {
+    double x[kMaxP + 1][kMaxP + 1] = {}, w[kMaxP + 1][kMaxP + 1] = {}, lm[kMaxP + 1][kMaxP + 1] = {},
+           lp[kMaxP + 1][kMaxP + 1] = {}, dm[kMaxP + 1][kMaxP + 1][kMaxP + 1] = {};
+    for (int p = 1; p <= kMaxP; ++p) {
+        GL1D g = gauss_legendre_nodal(p);
+        for (int k = 0; k <= p; ++k) {
+            x[p][k] = g.x[k];
+            w[p][k] = g.w[k];
+            lm[p][k] = g.lm[k];
+            lp[p][k] = g.lp[k];
+            for (int a = 0; a <= p; ++a) dm[p][a][k] = g.dm[a][k];
+        }
+    }
+    cudaError_t err;
+    if ((err = cudaMemcpyToSymbol(c_x, x, sizeof(x))) != cudaSuccess) return err;
+    if ((err = cudaMemcpyToSymbol(c_w, w, sizeof(w))) != cudaSuccess) return err;
+    if ((err = cudaMemcpyToSymbol(c_lm, lm, sizeof(lm))) != cudaSuccess) return err;
+    if ((err = cudaMemcpyToSymbol(c_lp, lp, sizeof(lp))) != cudaSuccess) return err;
+    return cudaMemcpyToSymbol(c_dm, dm, sizeof(dm));
+}
+
+template <int DIM, int P>
+struct Shape {
+    static constexpr int Q = P + 1;
+    static constexpr int N = DIM == 2 ? Q * Q : Q * Q * Q;
+    static constexpr int NT = DIM == 2 ? Q : Q * Q;  // nodes on a face
+};
+
+// Node index of the node with coordinate index ia on axis a and tangential index t.
+template <int DIM, int P>
+__device__ __forceinline__ int node_of(int a, int ia, int t) {
+    constexpr int Q = P + 1;
+    if (DIM == 2) return a == 0 ? ia + Q * t : t + Q * ia;
+    const int t0 = t % Q, t1 = t / Q;
+    if (a == 0) return ia + Q * (t0 + Q * t1);
+    if (a == 1) return t0 + Q * (ia + Q * t1);
+    return t0 + Q * (t1 + Q * ia);
+}
+
+template <int DIM, int P>
+__device__ __forceinline__ double wtan(int t) {
+    constexpr int Q = P + 1;
+    return DIM == 2 ? c_w[P][t] : c_w[P][t % Q] * c_w[P][t / Q];
+}
+
+// Geometry of one element for one direction: face flux factors, b at the nodes and det J.
+template <int DIM, int P>
+struct ElemGeom {
+    double F[2 * DIM];
+    double b[DIM][P + 1];  // 2D: b[0][a] = b_1(x_a), b[1][a] = b_2(x_a); 3D: constant per axis
+    double detJ[Shape<DIM, P>::N];
+};
+
+// Face flux factor of a 2D face from the half edge vector (ex, ey), rounded without FMA
+// contraction so that the level-set build and the sweep see the same value, and a face gives
+// exactly the negated value to its neighbour (which computes it from the same vertices).
+__device__ __forceinline__ double edge_flux(double Ox, double Oy, double ex, double ey) {
+    return __dsub_rn(__dmul_rn(Ox, ey), __dmul_rn(Oy, ex));
+}
+
+__device__ __forceinline__ double face_flux_2d(const double* v, int f, double Ox, double Oy) {
+    // v = x00 y00 x10 y10 x01 y01 x11 y11; faces 0: xi=-1 (left), 1: xi=+1, 2: eta=-1, 3: eta=+1
+    switch (f) {
+        case 0: return -edge_flux(Ox, Oy, 0.5 * (v[4] - v[0]), 0.5 * (v[5] - v[1]));
+        case 1: return edge_flux(Ox, Oy, 0.5 * (v[6] - v[2]), 0.5 * (v[7] - v[3]));
+        case 2: return edge_flux(Ox, Oy, 0.5 * (v[2] - v[0]), 0.5 * (v[3] - v[1]));
+        default: return -edge_flux(Ox, Oy, 0.5 * (v[6] - v[4]), 0.5 * (v[7] - v[5]));
+    }
+}
+
+template <int DIM, int P>
+__device__ __forceinline__ void elem_geom(const SweepArgs& a, int e, double Ox, double Oy, double Oz,
+                                          ElemGeom<DIM, P>& g) {
+    constexpr int Q = P + 1;
+    if constexpr (DIM == 2) {
+        const double* v = a.corners + 8 * (size_t)e;  // x00 y00 x10 y10 x01 y01 x11 y11
+        const double ebx = 0.5 * (v[2] - v[0]), eby = 0.5 * (v[3] - v[1]);
+        const double etx = 0.5 * (v[6] - v[4]), ety = 0.5 * (v[7] - v[5]);
+        const double elx = 0.5 * (v[4] - v[0]), ely = 0.5 * (v[5] - v[1]);
+        const double erx = 0.5 * (v[6] - v[2]), ery = 0.5 * (v[7] - v[3]);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) g.F[f] = face_flux_2d(v, f, Ox, Oy);
+        // b_1(xi) interpolates Omega x (dx/deta) between the left and right edges, b_2(eta) likewise
+        const double cl = -g.F[0], cr = g.F[1], cb = g.F[2], ct = -g.F[3];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const double t = c_x[P][k];
+            g.b[0][k] = 0.5 * (1.0 - t) * cl + 0.5 * (1.0 + t) * cr;
+            g.b[1][k] = -(0.5 * (1.0 - t) * cb + 0.5 * (1.0 + t) * ct);
+        }
+#pragma unroll
+        for (int j1 = 0; j1 < Q; ++j1)
+#pragma unroll
+            for (int j0 = 0; j0 < Q; ++j0) {
+                const double xi = c_x[P][j0], eta = c_x[P][j1];
+                const double xx = 0.5 * (1.0 - eta) * ebx + 0.5 * (1.0 + eta) * etx;  // dx/dxi
+                const double xy = 0.5 * (1.0 - eta) * eby + 0.5 * (1.0 + eta) * ety;
+                const double yx = 0.5 * (1.0 - xi) * elx + 0.5 * (1.0 + xi) * erx;    // dx/deta
+                const double yy = 0.5 * (1.0 - xi) * ely + 0.5 * (1.0 + xi) * ery;
+                g.detJ[j0 + Q * j1] = xx * yy - yx * xy;
+            }
+    } else {
+        const double bx = 0.25 * Ox * a.hy * a.hz, by = 0.25 * Oy * a.hx * a.hz, bz = 0.25 * Oz * a.hx * a.hy;
+        g.F[0] = -bx;
+        g.F[1] = bx;
+        g.F[2] = -by;
+        g.F[3] = by;
+        g.F[4] = -bz;
+        g.F[5] = bz;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            g.b[0][k] = bx;
+            g.b[1][k] = by;
+            g.b[2][k] = bz;
+        }
+        const double dj = 0.125 * a.hx * a.hy * a.hz;
+#pragma unroll
+        for (int i = 0; i < Shape<DIM, P>::N; ++i) g.detJ[i] = dj;
+    }
+}
+
+template <int DIM, int P>
+__device__ __forceinline__ int neighbor(const SweepArgs& a, int e, int f) {
+    const int ax = f >> 1, side = f & 1;
+    int i = e % a.nx, j = (e / a.nx) % a.ny, k = e / (a.nx * a.ny);
+    const int dl = side ? 1 : -1;
+    if (ax == 0) {
+        i += dl;
+        if (i < 0 || i >= a.nx) return -1;
+    } else if (ax == 1) {
+        j += dl;
+        if (j < 0 || j >= a.ny) return -1;
+    } else {
+        k += dl;
+        if (k < 0 || k >= a.nz) return -1;
+    }
+    return i + a.nx * (j + a.ny * k);
+}
+
+template <int DIM, int P>
+__device__ __forceinline__ double face_flux_only(const SweepArgs& a, int e, int f, double Ox, double Oy,
+                                                 double Oz) {
+    if constexpr (DIM == 2) {
+        return face_flux_2d(a.corners + 8 * (size_t)e, f, Ox, Oy);
+    } else {
+        const double bx = 0.25 * Ox * a.hy * a.hz, by = 0.25 * Oy * a.hx * a.hz, bz = 0.25 * Oz * a.hx * a.hy;
+        const double b = (f >> 1) == 0 ? bx : ((f >> 1) == 1 ? by : bz);
+        return (f & 1) ? b : -b;
+    }
+}
+
+// A_e in precision R (volume + outflow faces).
+template <int DIM, int P, typename R>
+__device__ __forceinline__ void assemble(const ElemGeom<DIM, P>& g, double st, R* A) {
+    constexpr int Q = P + 1, N = Shape<DIM, P>::N, NT = Shape<DIM, P>::NT;
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) A[i] = R(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const int j0 = j % Q, j1 = (j / Q) % Q, j2 = j / (Q * Q);
+        const double Wj = c_w[P][j0] * c_w[P][j1] * (DIM == 3 ? c_w[P][j2] : 1.0);
+        A[j * N + j] += R(st * Wj * g.detJ[j]);
+        // axis 0: nodes i differing from j only in index 0
+#pragma unroll
+        for (int ia = 0; ia < Q; ++ia) {
+            const int i = ia + Q * (j1 + Q * j2);
+            A[i * N + j] -= R(Wj * g.b[0][j0] * c_dm[P][j0][ia]);
+        }
+#pragma unroll
+        for (int ia = 0; ia < Q; ++ia) {
+            const int i = j0 + Q * (ia + Q * j2);
+            A[i * N + j] -= R(Wj * g.b[1][j1] * c_dm[P][j1][ia]);
+        }
+        if constexpr (DIM == 3) {
+#pragma unroll
+            for (int ia = 0; ia < Q; ++ia) {
+                const int i = j0 + Q * (j1 + Q * ia);
+                A[i * N + j] -= R(Wj * g.b[DIM - 1][j2] * c_dm[P][j2][ia]);
+            }
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f) {
+        if (g.F[f] > 0.0) {
+            const int ax = f >> 1;
+            const bool hi = f & 1;
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                const double ft = g.F[f] * wtan<DIM, P>(t);
+#pragma unroll
+                for (int ia = 0; ia < Q; ++ia)
+#pragma unroll
+                    for (int ja = 0; ja < Q; ++ja) {
+                        const double li = hi ? c_lp[P][ia] : c_lm[P][ia];
+                        const double lj = hi ? c_lp[P][ja] : c_lm[P][ja];
+                        A[node_of<DIM, P>(ax, ia, t) * N + node_of<DIM, P>(ax, ja, t)] += R(ft * li * lj);
+                    }
+            }
+        }
+    }
+}
+
+// y = A_e x, matrix free, in float64 (used by the refinement step).
+template <int DIM, int P>
+__device__ __forceinline__ void apply_A(const ElemGeom<DIM, P>& g, double st, const double* x, double* y) {
+    constexpr int Q = P + 1, N = Shape<DIM, P>::N, NT = Shape<DIM, P>::NT;
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] = 0.0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const int j0 = j % Q, j1 = (j / Q) % Q, j2 = j / (Q * Q);
+        const double Wj = c_w[P][j0] * c_w[P][j1] * (DIM == 3 ? c_w[P][j2] : 1.0);
+        const double xj = x[j];
+        y[j] += st * Wj * g.detJ[j] * xj;
+        const double u0 = Wj * g.b[0][j0] * xj, u1 = Wj * g.b[1][j1] * xj;
+#pragma unroll
+        for (int ia = 0; ia < Q; ++ia) y[ia + Q * (j1 + Q * j2)] -= u0 * c_dm[P][j0][ia];
+#pragma unroll
+        for (int ia = 0; ia < Q; ++ia) y[j0 + Q * (ia + Q * j2)] -= u1 * c_dm[P][j1][ia];
+        if constexpr (DIM == 3) {
+            const double u2 = Wj * g.b[DIM - 1][j2] * xj;
+#pragma unroll
+            for (int ia = 0; ia < Q; ++ia) y[j0 + Q * (j1 + Q * ia)] -= u2 * c_dm[P][j2][ia];
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f) {
+        if (g.F[f] > 0.0) {
+            const int ax = f >> 1;
+            const bool hi = f & 1;
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                double tr = 0.0;
+#pragma unroll
+                for (int ja = 0; ja < Q; ++ja) tr += (hi ? c_lp[P][ja] : c_lm[P][ja]) * x[node_of<DIM, P>(ax, ja, t)];
+                const double ft = g.F[f] * wtan<DIM, P>(t) * tr;
+#pragma unroll
+                for (int ia = 0; ia < Q; ++ia) y[node_of<DIM, P>(ax, ia, t)] += ft * (hi ? c_lp[P][ia] : c_lm[P][ia]);
+            }
+        }
+    }
+}
+
+template <int N, typename R>
+__device__ __forceinline__ void lu_factor(R* A) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const R inv = R(1) / A[k * N + k];
+        A[k * N + k] = inv;
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) {
+            const R l = A[i * N + k] * inv;
+            A[i * N + k] = l;
+#pragma unroll
+            for (int j = k + 1; j < N; ++j) A[i * N + j] -= l * A[k * N + j];
+        }
+    }
+}
+
+// Solve (LU) x = b in place; the diagonal holds 1/U_kk.
+template <int N, typename R>
+__device__ __forceinline__ void lu_solve(const R* A, R* x) {
+#pragma unroll
+    for (int i = 1; i < N; ++i)
+#pragma unroll
+        for (int k = 0; k < i; ++k) x[i] -= A[i * N + k] * x[k];
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+#pragma unroll
+        for (int k = i + 1; k < N; ++k) x[i] -= A[i * N + k] * x[k];
+        x[i] *= A[i * N + i];
+    }
+}
+
+// Solve (LU)^T x = b in place: U^T y = b (forward), then L^T x = y (backward).
+template <int N, typename R>
+__device__ __forceinline__ void lu_solve_transpose(const R* A, R* x) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int k = 0; k < i; ++k) x[i] -= A[k * N + i] * x[k];
+        x[i] *= A[i * N + i];
+    }
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i)
+#pragma unroll
+        for (int k = i + 1; k < N; ++k) x[i] -= A[k * N + i] * x[k];
+}
+
+// Right-hand side: mass-weighted source + inflow face terms from upwind traces (float64).
+template <int DIM, int P, typename RS>
+__device__ __forceinline__ void assemble_rhs(const SweepArgs& a, const ElemGeom<DIM, P>& g, int d, int e,
+                                             double* rhs) {
+    constexpr int Q = P + 1, N = Shape<DIM, P>::N, NT = Shape<DIM, P>::NT;
+    const double ss = a.sigma_s[e], qe = a.q[e] * a.q_scale;
+    const double* phi = a.phi ? a.phi + (size_t)e * N : nullptr;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const int i0 = i % Q, i1 = (i / Q) % Q, i2 = i / (Q * Q);
+        const double Wi = c_w[P][i0] * c_w[P][i1] * (DIM == 3 ? c_w[P][i2] : 1.0);
+        const double S = (qe + (phi ? ss * phi[i] : 0.0)) * (1.0 / kFourPi);
+        rhs[i] = Wi * g.detJ[i] * S;
+    }
+    const RS* psi = static_cast<const RS*>(a.psi);
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f) {
+        if (g.F[f] < 0.0) {
+            const int ax = f >> 1;
+            const bool hi = f & 1;
+            const int u = neighbor<DIM, P>(a, e, f);
+            double tr[NT];
+            if (u >= 0) {
+                const RS* pu = psi + ((size_t)d * a.ne + u) * N;
+                RS vals[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) vals[i] = pu[i];
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int k = 0; k < Q; ++k)
+                        s += (hi ? c_lm[P][k] : c_lp[P][k]) * (double)vals[node_of<DIM, P>(ax, k, t)];
+                    tr[t] = s;
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < NT; ++t) tr[t] = a.psi_inc;
+            }
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                const double ft = -g.F[f] * wtan<DIM, P>(t) * tr[t];
+#pragma unroll
+                for (int ia = 0; ia < Q; ++ia) rhs[node_of<DIM, P>(ax, ia, t)] += ft * (hi ? c_lp[P][ia] : c_lm[P][ia]);
+            }
+        }
+    }
+}
+
+// MODE 0: float64 solve, float64 storage.  MODE 1: float32 solve and storage.
+// MODE 2: float32 LU + two float64 residual corrections, float64 storage.
+template <int DIM, int P, int MODE>
+__global__ void __launch_bounds__(128) sweep_level_kernel(SweepArgs a, long long begin, long long end) {
+    constexpr int N = Shape<DIM, P>::N;
+    const long long t = begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= end) return;
+    const int2 it = a.items[t];
+    const int d = it.x, e = it.y;
+    const double Ox = a.dirs[3 * d], Oy = a.dirs[3 * d + 1], Oz = a.dirs[3 * d + 2];
+    ElemGeom<DIM, P> g;
+    elem_geom<DIM, P>(a, e, Ox, Oy, Oz, g);
+    const double st = a.sigma_t[e];
+    double rhs[N];
+    if (MODE == 1) {
+        assemble_rhs<DIM, P, float>(a, g, d, e, rhs);
+        float A[N * N], x[N];
+        assemble<DIM, P, float>(g, st, A);
+#pragma unroll
+        for (int i = 0; i < N; ++i) x[i] = (float)rhs[i];
+        lu_factor<N, float>(A);
+        lu_solve<N, float>(A, x);
+        float* out = static_cast<float*>(a.psi) + ((size_t)d * a.ne + e) * N;
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[i] = x[i];
+    } else if (MODE == 0) {
+        assemble_rhs<DIM, P, double>(a, g, d, e, rhs);
+        double A[N * N];
+        assemble<DIM, P, double>(g, st, A);
+        lu_factor<N, double>(A);
+        lu_solve<N, double>(A, rhs);
+        double* out = static_cast<double*>(a.psi) + ((size_t)d * a.ne + e) * N;
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[i] = rhs[i];
+    } else {
+        assemble_rhs<DIM, P, double>(a, g, d, e, rhs);
+        float A[N * N];
+        float c[N];
+        double x[N], r[N];
+        assemble<DIM, P, float>(g, st, A);
+        lu_factor<N, float>(A);
+#pragma unroll
+        for (int i = 0; i < N; ++i) c[i] = (float)rhs[i];
+        lu_solve<N, float>(A, c);
+#pragma unroll
+        for (int i = 0; i < N; ++i) x[i] = c[i];
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            apply_A<DIM, P>(g, st, x, r);
+#pragma unroll
+            for (int i = 0; i < N; ++i) c[i] = (float)(rhs[i] - r[i]);
+            lu_solve<N, float>(A, c);
+#pragma unroll
+            for (int i = 0; i < N; ++i) x[i] += (double)c[i];
+        }
+        double* out = static_cast<double*>(a.psi) + ((size_t)d * a.ne + e) * N;
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[i] = x[i];
+    }
+}
+
+// Adjoint: A_e^T lam_e = mu_e - sum_{outflow F, downwind u} C(u<-e)^T lam_u, in reverse level order.
+template <int DIM, int P>
+__global__ void __launch_bounds__(128) adjoint_level_kernel(SweepArgs a, const double* mu, long long begin,
+                                                           long long end) {
+    constexpr int Q = P + 1, N = Shape<DIM, P>::N, NT = Shape<DIM, P>::NT;
+    const long long t = begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= end) return;
+    const int2 it = a.items[t];
+    const int d = it.x, e = it.y;
+    const double Ox = a.dirs[3 * d], Oy = a.dirs[3 * d + 1], Oz = a.dirs[3 * d + 2];
+    ElemGeom<DIM, P> g;
+    elem_geom<DIM, P>(a, e, Ox, Oy, Oz, g);
+    double rhs[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) rhs[i] = mu[(size_t)e * N + i];
+    const double* lam = static_cast<const double*>(a.psi);
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f) {
+        if (g.F[f] > 0.0) {
+            const int u = neighbor<DIM, P>(a, e, f);
+            if (u < 0) continue;
+            const int ax = f >> 1;
+            const bool hi = f & 1;
+            const double* lu = lam + ((size_t)d * a.ne + u) * N;
+            double vals[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) vals[i] = lu[i];
+#pragma unroll
+            for (int tt = 0; tt < NT; ++tt) {
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < Q; ++k) s += (hi ? c_lm[P][k] : c_lp[P][k]) * vals[node_of<DIM, P>(ax, k, tt)];
+                const double ft = g.F[f] * wtan<DIM, P>(tt) * s;
+#pragma unroll
+                for (int ja = 0; ja < Q; ++ja) rhs[node_of<DIM, P>(ax, ja, tt)] += ft * (hi ? c_lp[P][ja] : c_lm[P][ja]);
+            }
+        }
+    }
+    double A[N * N];
+    assemble<DIM, P, double>(g, a.sigma_t[e], A);
+    lu_factor<N, double>(A);
+    lu_solve_transpose<N, double>(A, rhs);
+    double* out = static_cast<double*>(a.psi) + ((size_t)d * a.ne + e) * N;
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = rhs[i];
+}
+
+// ---------------------------------------------------------------- level sets (Kahn, on device)
+template <int DIM, int P>
+__global__ void indegree_kernel(SweepArgs a, int* indeg, int2* frontier, unsigned long long* cursor) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)a.nd * a.ne) return;
+    const int d = (int)(t / a.ne), e = (int)(t % a.ne);
+    const double Ox = a.dirs[3 * d], Oy = a.dirs[3 * d + 1], Oz = a.dirs[3 * d + 2];
+    int c = 0;
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f)
+        if (face_flux_only<DIM, P>(a, e, f, Ox, Oy, Oz) < 0.0 && neighbor<DIM, P>(a, e, f) >= 0) ++c;
+    indeg[t] = c;
+    if (c == 0) {
+        const unsigned long long pos = atomicAdd(cursor, 1ull);
+        frontier[pos] = make_int2(d, e);
+    }
+}
+
+template <int DIM, int P>
+__global__ void kahn_level_kernel(SweepArgs a, int* indeg, int2* list, int* level, long long begin, long long end,
+                                  int L, unsigned long long* cursor) {
+    const long long t = begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= end) return;
+    const int2 it = list[t];
+    const int d = it.x, e = it.y;
+    level[(size_t)d * a.ne + e] = L;
+    const double Ox = a.dirs[3 * d], Oy = a.dirs[3 * d + 1], Oz = a.dirs[3 * d + 2];
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f) {
+        if (face_flux_only<DIM, P>(a, e, f, Ox, Oy, Oz) > 0.0) {
+            const int u = neighbor<DIM, P>(a, e, f);
+            if (u < 0) continue;
+            if (atomicSub(&indeg[(size_t)d * a.ne + u], 1) == 1) {
+                const unsigned long long pos = atomicAdd(cursor, 1ull);
+                list[pos] = make_int2(d, u);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- reductions
+template <typename RS>
+__global__ void phi_reduce_kernel(const RS* psi, const double* w, int nd, size_t M, const double* phi_in,
+                                  double* phi_out, double* partial) {
+    __shared__ double sh[256];
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double rr = 0.0;
+    if (idx < M) {
+        double s = 0.0;
+        for (int d = 0; d < nd; ++d) s += w[d] * (double)psi[(size_t)d * M + idx];
+        const double r = s - (phi_in ? phi_in[idx] : 0.0);
+        phi_out[idx] = s;
+        rr = r * r;
+    }
+    sh[threadIdx.x] = rr;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && partial) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void final_sum_kernel(const double* partial, int n, double* out) {
+    __shared__ double sh[1024];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+// out = a - b and ||out||^2 partials (b may be null: out = a).
+__global__ void diff_norm_kernel(const double* a, const double* b, double* out, size_t M, double* partial) {
+    __shared__ double sh[256];
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double rr = 0.0;
+    if (idx < M) {
+        const double r = a[idx] - (b ? b[idx] : 0.0);
+        if (out) out[idx] = r;
+        rr = r * r;
+    }
+    sh[threadIdx.x] = rr;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// out[e][i] = sigma_s[e] M_i / (4 pi) * sum_d w_d lam_d[e][i]
+template <int DIM, int P>
+__global__ void adjoint_reduce_kernel(SweepArgs a, const double* lam, const double* w, double* out) {
+    constexpr int Q = P + 1, N = Shape<DIM, P>::N;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t M = (size_t)a.ne * N;
+    if (idx >= M) return;
+    const int e = (int)(idx / N), i = (int)(idx % N);
+    double s = 0.0;
+    for (int d = 0; d < a.nd; ++d) s += w[d] * lam[(size_t)d * M + idx];
+    ElemGeom<DIM, P> g;
+    elem_geom<DIM, P>(a, e, 1.0, 0.0, 0.0, g);
+    const int i0 = i % Q, i1 = (i / Q) % Q, i2 = i / (Q * Q);
+    const double Wi = c_w[P][i0] * c_w[P][i1] * (DIM == 3 ? c_w[P][i2] : 1.0);
+    out[idx] = a.sigma_s[e] * Wi * g.detJ[i] / kFourPi * s;
+}
+
+template <int DIM, int P>
+__global__ void gradient_kernel(SweepArgs a, const double* psi, const double* lam, const double* w,
+                                const double* phi, double* gt, double* gs, double* gq) {
+    constexpr int Q = P + 1, N = Shape<DIM, P>::N;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.ne) return;
+    ElemGeom<DIM, P> g;
+    elem_geom<DIM, P>(a, e, 1.0, 0.0, 0.0, g);
+    double M[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const int i0 = i % Q, i1 = (i / Q) % Q, i2 = i / (Q * Q);
+        M[i] = c_w[P][i0] * c_w[P][i1] * (DIM == 3 ? c_w[P][i2] : 1.0) * g.detJ[i];
+    }
+    double st = 0.0, ssum = 0.0, sq = 0.0;
+    const size_t stride = (size_t)a.ne * N;
+    for (int d = 0; d < a.nd; ++d) {
+        const double* l = lam + d * stride + (size_t)e * N;
+        const double* p = psi + d * stride + (size_t)e * N;
+        double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const double lm = l[i] * M[i];
+            t1 += lm * p[i];
+            t2 += lm * phi[(size_t)e * N + i];
+            t3 += lm;
+        }
+        st += w[d] * t1;
+        ssum += w[d] * t2;
+        sq += w[d] * t3;
+    }
+    if (gt) gt[e] = -st;
+    if (gs) gs[e] = ssum / kFourPi;
+    if (gq) gq[e] = sq / kFourPi;
+}
+
+// ---------------------------------------------------------------- host launchers
+static SweepArgs make_args(const sn_mesh* m) {
+    SweepArgs a{};
+    a.dim = m->dim;
+    a.p = m->p;
+    a.nx = m->nx;
+    a.ny = m->ny;
+    a.nz = m->nz;
+    a.ne = m->ne;
+    a.nd = m->nd;
+    a.hx = m->hx;
+    a.hy = m->hy;
+    a.hz = m->hz;
+    a.psi_inc = m->desc.psi_inc;
+    a.dirs = m->d_dirs;
+    a.corners = m->d_corners;
+    a.sigma_t = m->d_sigma_t;
+    a.sigma_s = m->d_sigma_s;
+    a.q = m->d_q;
+    a.items = m->levels.items;
+    a.q_scale = 1.0;
+    return a;
+}
+
+#define SN_DISPATCH(DIMV, PV, CALL)                                             \
+    do {                                                                        \
+        if ((DIMV) == 2 && (PV) == 1) { constexpr int D_ = 2, P_ = 1; CALL; }   \
+        else if ((DIMV) == 2 && (PV) == 2) { constexpr int D_ = 2, P_ = 2; CALL; } \
+        else if ((DIMV) == 2 && (PV) == 3) { constexpr int D_ = 2, P_ = 3; CALL; } \
+        else if ((DIMV) == 3 && (PV) == 1) { constexpr int D_ = 3, P_ = 1; CALL; } \
+        else return cudaErrorInvalidValue;                                      \
+    } while (0)
+
+static inline unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+cudaError_t build_levels(sn_mesh* m, cudaStream_t s, bool* cycle) {
+    *cycle = false;
+    const long long total = (long long)m->nd * m->ne;
+    int* indeg = nullptr;
+    int* level = nullptr;
+    int2* list = nullptr;
+    unsigned long long* cursor = nullptr;
+    cudaError_t err;
+    if ((err = cudaMalloc(&indeg, total * sizeof(int))) != cudaSuccess) return err;
+    if ((err = cudaMalloc(&level, total * sizeof(int))) != cudaSuccess) { cudaFree(indeg); return err; }
+    if ((err = cudaMalloc(&list, total * sizeof(int2))) != cudaSuccess) { cudaFree(indeg); cudaFree(level); return err; }
+    if ((err = cudaMalloc(&cursor, sizeof(unsigned long long))) != cudaSuccess) {
+        cudaFree(indeg); cudaFree(level); cudaFree(list);
+        return err;
+    }
+    auto cleanup = [&]() { cudaFree(indeg); cudaFree(level); cudaFree(list); cudaFree(cursor); };
+    SweepArgs a = make_args(m);
+    cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s);
+    cudaMemsetAsync(level, 0xff, total * sizeof(int), s);
+    auto run_init = [&]() -> cudaError_t {
+        SN_COUNT_LAUNCH();
+        SN_DISPATCH(m->dim, m->p, (indegree_kernel<D_, P_><<<grid_for(total, 256), 256, 0, s>>>(a, indeg, list, cursor)));
+        return cudaGetLastError();
+    };
+    if ((err = run_init()) != cudaSuccess) { cleanup(); return err; }
+    unsigned long long h_cursor = 0;
+    long long begin = 0;
+    int L = 0;
+    if ((err = cudaMemcpyAsync(&h_cursor, cursor, sizeof(h_cursor), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (err = cudaStreamSynchronize(s)) != cudaSuccess) { cleanup(); return err; }
+    while ((long long)h_cursor > begin) {
+        const long long end = (long long)h_cursor;
+        auto run_level = [&]() -> cudaError_t {
+            SN_DISPATCH(m->dim, m->p,
+                        (kahn_level_kernel<D_, P_><<<grid_for(end - begin, 256), 256, 0, s>>>(a, indeg, list, level, begin, end, L, cursor)));
+            return cudaGetLastError();
+        };
+        if ((err = run_level()) != cudaSuccess) { cleanup(); return err; }
+        begin = end;
+        ++L;
+        if ((err = cudaMemcpyAsync(&h_cursor, cursor, sizeof(h_cursor), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (err = cudaStreamSynchronize(s)) != cudaSuccess) { cleanup(); return err; }
+    }
+    if (begin != total) {
+        *cycle = true;
+        cleanup();
+        return cudaSuccess;
+    }
+    // deterministic order: counting sort of (dir, elem) by level on the host
+    std::vector<int> h_level(total);
+    if ((err = cudaMemcpyAsync(h_level.data(), level, total * sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (err = cudaStreamSynchronize(s)) != cudaSuccess) { cleanup(); return err; }
+    std::vector<long long> ptr(L + 1, 0);
+    for (long long t = 0; t < total; ++t) ptr[h_level[t] + 1]++;
+    for (int l = 0; l < L; ++l) ptr[l + 1] += ptr[l];
+    std::vector<long long> fill(ptr.begin(), ptr.end() - 1);
+    std::vector<int2> items(total);
+    for (long long t = 0; t < total; ++t) {
+        const int d = (int)(t / m->ne), e = (int)(t % m->ne);
+        items[fill[h_level[t]]++] = make_int2(d, e);
+    }
+    if (m->levels.items) cudaFree(m->levels.items);
+    m->levels.items = nullptr;
+    if ((err = cudaMalloc(&m->levels.items, total * sizeof(int2))) != cudaSuccess) { cleanup(); return err; }
+    if ((err = cudaMemcpyAsync(m->levels.items, items.data(), total * sizeof(int2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (err = cudaStreamSynchronize(s)) != cudaSuccess) { cleanup(); return err; }
+    m->levels.level_ptr = ptr;
+    m->levels.n_levels = L;
+    cleanup();
+    return cudaSuccess;
+}
+
+cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double q_scale, cudaStream_t s) {
+    SweepArgs a = make_args(m);
+    a.phi = phi_in;
+    a.q_scale = q_scale;
+    a.psi = precision == SN_FP32 ? m->d_psi32 : m->d_psi;
+    const int bs = 128;
+    for (int L = 0; L < m->levels.n_levels; ++L) {
+        const long long b = m->levels.level_ptr[L], e = m->levels.level_ptr[L + 1];
+        if (e <= b) continue;
+        const unsigned g = grid_for(e - b, bs);
+        if (precision == SN_FP64) {
+            SN_COUNT_LAUNCH();
+            SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 0><<<g, bs, 0, s>>>(a, b, e)));
+        } else if (precision == SN_FP32) {
+            SN_COUNT_LAUNCH();
+            SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 1><<<g, bs, 0, s>>>(a, b, e)));
+        } else {
+            SN_COUNT_LAUNCH();
+            SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 2><<<g, bs, 0, s>>>(a, b, e)));
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_sweep(sn_mesh* m, const double* mu, cudaStream_t s) {
+    SweepArgs a = make_args(m);
+    a.psi = m->d_lambda;
+    const int bs = 128;
+    for (int L = m->levels.n_levels - 1; L >= 0; --L) {
+        const long long b = m->levels.level_ptr[L], e = m->levels.level_ptr[L + 1];
+        if (e <= b) continue;
+        SN_COUNT_LAUNCH();
+        SN_DISPATCH(m->dim, m->p, (adjoint_level_kernel<D_, P_><<<grid_for(e - b, bs), bs, 0, s>>>(a, mu, b, e)));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phi_reduce(sn_mesh* m, int precision, const double* phi_in, double* phi_out, double* d_rr,
+                              cudaStream_t s) {
+    const size_t M = (size_t)m->ne * m->n;
+    const unsigned g = (unsigned)((M + 255) / 256);
+    SN_COUNT_LAUNCH();
+    if (precision == SN_FP32)
+        phi_reduce_kernel<float><<<g, 256, 0, s>>>(static_cast<const float*>(m->d_psi32), m->d_wts, m->nd, M, phi_in,
+                                                   phi_out, d_rr ? m->d_red : nullptr);
+    else
+        phi_reduce_kernel<double><<<g, 256, 0, s>>>(static_cast<const double*>(m->d_psi), m->d_wts, m->nd, M, phi_in,
+                                                    phi_out, d_rr ? m->d_red : nullptr);
+    if (d_rr) { SN_COUNT_LAUNCH(); final_sum_kernel<<<1, 1024, 0, s>>>(m->d_red, (int)g, d_rr); }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_norm(sn_mesh* m, const double* a, const double* b, double* out, double* d_rr,
+                             cudaStream_t s) {
+    const size_t M = (size_t)m->ne * m->n;
+    const unsigned g = (unsigned)((M + 255) / 256);
+    SN_COUNT_LAUNCH();
+    diff_norm_kernel<<<g, 256, 0, s>>>(a, b, out, M, m->d_red);
+    SN_COUNT_LAUNCH();
+    final_sum_kernel<<<1, 1024, 0, s>>>(m->d_red, (int)g, d_rr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_reduce(sn_mesh* m, double* out, cudaStream_t s) {
+    SweepArgs a = make_args(m);
+    const size_t M = (size_t)m->ne * m->n;
+    SN_COUNT_LAUNCH();
+    SN_DISPATCH(m->dim, m->p, (adjoint_reduce_kernel<D_, P_><<<grid_for((long long)M, 256), 256, 0, s>>>(a, m->d_lambda, m->d_wts, out)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gradients(sn_mesh* m, const double* phi, double* gt, double* gs, double* gq, cudaStream_t s) {
+    SweepArgs a = make_args(m);
+    SN_COUNT_LAUNCH();
+    SN_DISPATCH(m->dim, m->p,
+                (gradient_kernel<D_, P_><<<grid_for(m->ne, 128), 128, 0, s>>>(a, static_cast<const double*>(m->d_psi),
+                                                                               m->d_lambda, m->d_wts, phi, gt, gs, gq)));
+    return cudaGetLastError();
+}
+
+__global__ void add_kernel(double* y, const double* x, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] += x[i];
+}
+
+cudaError_t launch_axpy_add(double* y, const double* x, size_t n, cudaStream_t s) {
+    SN_COUNT_LAUNCH();
+    add_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, x, n);
+    return cudaGetLastError();
+}
+
+__global__ void widen_kernel(double* y, const float* x, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (double)x[i];
+}
+
+cudaError_t launch_widen(double* y, const float* x, size_t n, cudaStream_t s) {
+    SN_COUNT_LAUNCH();
+    widen_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, x, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy(double* dst, const double* src, size_t n, cudaStream_t s) {
+    return cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace sn

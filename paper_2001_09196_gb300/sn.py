@@ -1,0 +1,281 @@
+"""Thin Python binding of libsn (include/sn.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library; this module converts torch tensors and
+numpy arrays to the C ABI's pointers and raises on a non-OK status.  Importing it loads
+libsn.so from paper_2001_09196_gb300/lib and fails loudly if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libsn.so")
+
+FP64, FP32, FP32_REFINE = 0, 1, 2
+DSA_NONE, DSA_FULL, DSA_THICK = 0, 1, 2
+THICK_SIGMA_S, THICK_SIGMA_T_H, THICK_MASK = 0, 1, 2
+DSA_SIGMA_S, DSA_SIGMA_T = 0, 1
+_PREC = {"fp64": FP64, "fp32": FP32, "fp32_refine": FP32_REFINE}
+_DSA = {"none": DSA_NONE, "full": DSA_FULL, "thick": DSA_THICK}
+_RULE = {"sigma_s": THICK_SIGMA_S, "sigma_t_h": THICK_SIGMA_T_H, "mask": THICK_MASK}
+
+STATUS = {0: "SN_OK", 1: "SN_ERR_ARG", 2: "SN_ERR_CUDA", 3: "SN_ERR_OOM", 4: "SN_ERR_CYCLE",
+          5: "SN_ERR_VOID_FULL_DSA", 6: "SN_ERR_NOT_CONVERGED", 7: "SN_ERR_TIMEOUT",
+          8: "SN_ERR_INNER_NOT_CONVERGED"}
+
+
+class SnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("p", C.c_int),
+                ("sn_order", C.c_int), ("vertices", C.POINTER(C.c_double)), ("psi_inc", C.c_double)]
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [("n_elem", C.c_int), ("n_nodes", C.c_int), ("n_dirs", C.c_int), ("n_levels", C.c_int),
+                ("n_items", C.c_longlong)]
+
+
+class IterOpts(C.Structure):
+    _fields_ = [("dsa", C.c_int), ("thick_rule", C.c_int), ("eta", C.c_double),
+                ("mask", C.POINTER(C.c_ubyte)), ("dsa_sigma", C.c_int), ("tol", C.c_double),
+                ("inner_tol", C.c_double), ("max_iters", C.c_int), ("inner_max_iters", C.c_int),
+                ("precision", C.c_int), ("checkpoint_every", C.c_int), ("checkpoints", C.c_void_p),
+                ("max_checkpoints", C.c_int), ("warm_start", C.c_int)]
+
+
+class IterStats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("rel_residual", C.c_double), ("inner_iters_total", C.c_int),
+                ("thick_fraction", C.c_double), ("residual_history", C.POINTER(C.c_double)),
+                ("history_len", C.c_int), ("n_checkpoints", C.c_int), ("ms_total", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libsn.so not built ({LIB_PATH}); run paper_2001_09196_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    sig = {
+        "sn_mesh_create": [C.POINTER(MeshDesc), C.POINTER(vp)],
+        "sn_mesh_destroy": [vp],
+        "sn_mesh_get_info": [vp, C.POINTER(MeshInfo)],
+        "sn_mesh_quadrature": [vp, vp, vp],
+        "sn_set_materials": [vp, vp, vp, vp, i, vp],
+        "sn_sweep": [vp, vp, vp, i, vp],
+        "sn_source_iterate": [vp, C.POINTER(IterOpts), vp, C.POINTER(IterStats), vp],
+        "sn_adjoint_sweep": [vp, vp, vp, i, vp],
+        "sn_adjoint_iterate": [vp, C.POINTER(IterOpts), vp, vp, C.POINTER(IterStats), vp],
+        "sn_gradients": [vp, vp, vp, vp, vp, vp, vp],
+        "sn_dsa_apply": [vp, C.POINTER(IterOpts), vp, vp, vp],
+        "sn_dsa_solve": [vp, C.POINTER(IterOpts), vp, vp, C.POINTER(C.c_int), vp],
+        "sn_get_angular_flux": [vp, i, i, i, vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.sn_last_error.restype = C.c_char_p
+    lib.sn_version.restype = C.c_char_p
+    lib.sn_launch_count.restype = C.c_longlong
+    lib.sn_launch_count.argtypes = []
+    lib.sn_iter_opts_default.argtypes = [C.POINTER(IterOpts)]
+    lib.sn_iter_opts_default.restype = None
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def launch_count():
+    """Kernels launched by libsn so far in this process."""
+    return int(_lib.sn_launch_count())
+
+
+def _check(status):
+    if status != 0:
+        raise SnError(status, _lib.sn_last_error().decode())
+
+
+def _ptr(t):
+    """Device pointer of a contiguous float64 CUDA tensor (or None)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_opts(dsa="thick", thick_rule="sigma_s", eta=1.0, mask=None, dsa_sigma="sigma_s", tol=1e-8,
+              inner_tol=1e-4, max_iters=1000, inner_max_iters=200, precision="fp64", checkpoint_every=0,
+              checkpoints=None, warm_start=False):
+    o = IterOpts()
+    _lib.sn_iter_opts_default(C.byref(o))
+    o.dsa = _DSA[dsa] if isinstance(dsa, str) else int(dsa)
+    o.thick_rule = _RULE[thick_rule] if isinstance(thick_rule, str) else int(thick_rule)
+    o.eta = float(eta)
+    keep = []
+    if mask is not None:
+        m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
+        keep.append(m)
+        o.mask = m.ctypes.data_as(C.POINTER(C.c_ubyte))
+        o.thick_rule = THICK_MASK
+    o.dsa_sigma = DSA_SIGMA_S if dsa_sigma == "sigma_s" else DSA_SIGMA_T
+    o.tol, o.inner_tol = float(tol), float(inner_tol)
+    o.max_iters, o.inner_max_iters = int(max_iters), int(inner_max_iters)
+    o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+    o.checkpoint_every = int(checkpoint_every)
+    if checkpoints is not None:
+        o.checkpoints = _ptr(checkpoints)
+        o.max_checkpoints = int(checkpoints.shape[0])
+    o.warm_start = int(bool(warm_start))
+    o._keep = keep
+    return o
+
+
+class Mesh:
+    """A structured mesh with its S_N quadrature and upwind level sets on the current GPU."""
+
+    def __init__(self, dim, nx, ny, nz=1, p=1, sn=8, vertices=None, psi_inc=0.0):
+        desc = MeshDesc(dim, nx, ny, nz if dim == 3 else 1, p, sn, None, float(psi_inc))
+        self._verts = None
+        if vertices is not None:
+            self._verts = np.ascontiguousarray(np.asarray(vertices, dtype=np.float64))
+            desc.vertices = self._verts.ctypes.data_as(C.POINTER(C.c_double))
+        h = C.c_void_p()
+        _check(_lib.sn_mesh_create(C.byref(desc), C.byref(h)))
+        self._h = h
+        info = MeshInfo()
+        _check(_lib.sn_mesh_get_info(h, C.byref(info)))
+        self.n_elem, self.n_nodes, self.n_dirs, self.n_levels = info.n_elem, info.n_nodes, info.n_dirs, info.n_levels
+        self.dim, self.p = dim, p
+
+    @classmethod
+    def from_problem(cls, prob, materials=True):
+        m = cls(prob.dim, prob.nx, prob.ny, prob.nz, prob.p, prob.sn, prob.vertices, prob.psi_inc)
+        if materials:
+            m.set_materials(prob.sigma_t, prob.sigma_s, prob.q)
+        return m
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.sn_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.n_elem, self.n_nodes)
+
+    def quadrature(self):
+        dirs = np.zeros((self.n_dirs, 3))
+        w = np.zeros(self.n_dirs)
+        _check(_lib.sn_mesh_quadrature(self._h, dirs.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p)))
+        return dirs, w
+
+    def set_materials(self, sigma_t, sigma_s, q, stream=None):
+        import torch
+        if isinstance(sigma_t, torch.Tensor) and sigma_t.is_cuda:
+            args = [_ptr(sigma_t.contiguous()), _ptr(sigma_s.contiguous()), _ptr(q.contiguous())]
+            _check(_lib.sn_set_materials(self._h, *args, 1, _stream(stream)))
+            return
+        arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (sigma_t, sigma_s, q)]
+        for a in arrs:
+            if a.size != self.n_elem:
+                raise ValueError("material arrays need one value per element")
+        _check(_lib.sn_set_materials(self._h, *[a.ctypes.data_as(C.c_void_p) for a in arrs], 0, _stream(stream)))
+
+    def sweep(self, phi_in, phi_out=None, precision="fp64", stream=None):
+        import torch
+        if phi_out is None:
+            phi_out = torch.empty(self.shape, dtype=torch.float64, device=phi_in.device if phi_in is not None else "cuda")
+        _check(_lib.sn_sweep(self._h, _ptr(phi_in), _ptr(phi_out), _PREC.get(precision, precision), _stream(stream)))
+        return phi_out
+
+    def source_iterate(self, phi=None, stream=None, history=0, **kw):
+        import torch
+        if phi is None:
+            phi = torch.zeros(self.shape, dtype=torch.float64, device="cuda")
+        if "warm_start" not in kw:
+            kw["warm_start"] = False
+        o = make_opts(**kw)
+        st = IterStats()
+        hist = np.zeros(max(history, 0))
+        if history:
+            st.residual_history = hist.ctypes.data_as(C.POINTER(C.c_double))
+            st.history_len = history
+        status = _lib.sn_source_iterate(self._h, C.byref(o), _ptr(phi), C.byref(st), _stream(stream))
+        out = {"phi": phi, "iters": st.iters, "rel_residual": st.rel_residual, "inner_iters": st.inner_iters_total,
+               "thick_fraction": st.thick_fraction, "ms": st.ms_total, "converged": status == 0,
+               "n_checkpoints": st.n_checkpoints, "history": hist[: st.iters] if history else None}
+        if status not in (0, 6):
+            _check(status)
+        return out
+
+    def adjoint_sweep(self, mu, out=None, stream=None):
+        import torch
+        out = torch.empty_like(mu) if out is None else out
+        _check(_lib.sn_adjoint_sweep(self._h, _ptr(mu), _ptr(out), FP64, _stream(stream)))
+        return out
+
+    def adjoint_iterate(self, g, mu=None, stream=None, **kw):
+        import torch
+        mu = torch.zeros_like(g) if mu is None else mu
+        kw.setdefault("warm_start", False)
+        o = make_opts(**kw)
+        st = IterStats()
+        status = _lib.sn_adjoint_iterate(self._h, C.byref(o), _ptr(g), _ptr(mu), C.byref(st), _stream(stream))
+        if status not in (0, 6):
+            _check(status)
+        return {"mu": mu, "iters": st.iters, "rel_residual": st.rel_residual, "converged": status == 0,
+                "inner_iters": st.inner_iters_total}
+
+    def gradients(self, phi, mu, stream=None):
+        import torch
+        gt, gs, gq = (torch.empty(self.n_elem, dtype=torch.float64, device=phi.device) for _ in range(3))
+        _check(_lib.sn_gradients(self._h, _ptr(phi), _ptr(mu), _ptr(gt), _ptr(gs), _ptr(gq), _stream(stream)))
+        return gt, gs, gq
+
+    def angular_flux(self, d, adjoint=False, precision="fp64", stream=None):
+        import torch
+        out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        _check(_lib.sn_get_angular_flux(self._h, int(d), int(adjoint), _PREC.get(precision, precision), _ptr(out),
+                                        _stream(stream)))
+        return out
+
+    def dsa_apply(self, x, stream=None, **kw):
+        import torch
+        y = torch.empty_like(x)
+        o = make_opts(**kw)
+        _check(_lib.sn_dsa_apply(self._h, C.byref(o), _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def dsa_solve(self, b, stream=None, **kw):
+        import torch
+        x = torch.empty_like(b)
+        o = make_opts(**kw)
+        its = C.c_int(0)
+        _check(_lib.sn_dsa_solve(self._h, C.byref(o), _ptr(b), _ptr(x), C.byref(its), _stream(stream)))
+        return x, its.value

@@ -1,0 +1,62 @@
+"""CPU-side checks of the C-ABI library: it builds, loads and exports every declared symbol."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sn.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:sn_status|void|const char\*)\s+(sn_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2001_09196_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_hot_path_calls():
+    names = declared_functions()
+    for required in ("sn_mesh_create", "sn_sweep", "sn_source_iterate", "sn_adjoint_sweep", "sn_gradients",
+                     "sn_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\s[TW]\s+(\w+)$", out, flags=re.M))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_without_gpu(libpath):
+    import ctypes
+    lib = ctypes.CDLL(libpath)
+    lib.sn_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.sn_version()
+    for n in declared_functions():
+        assert hasattr(lib, n)
+
+
+def test_binding_loads_and_defaults(libpath):
+    from paper_2001_09196_gb300 import sn
+    o = sn.make_opts()
+    assert o.dsa == sn.DSA_THICK and o.tol == 1e-8 and o.inner_tol == 1e-4 and o.eta == 1.0
+
+
+def test_invalid_descriptor_is_rejected_without_touching_the_gpu(libpath):
+    """Argument checks run before any CUDA call."""
+    from paper_2001_09196_gb300 import sn
+    with pytest.raises(sn.SnError) as e:
+        sn.Mesh(4, 8, 8, p=1, sn=4)
+    assert e.value.status == 1
+    with pytest.raises(sn.SnError):
+        sn.Mesh(3, 4, 4, 4, p=2, sn=4)
+    with pytest.raises(sn.SnError):
+        sn.Mesh(2, 4, 4, p=1, sn=5)

@@ -78,6 +78,23 @@ sn_status sn_mesh_create(const sn_mesh_desc* desc, sn_mesh** out);
 sn_status sn_mesh_destroy(sn_mesh* mesh);
 sn_status sn_mesh_get_info(const sn_mesh* mesh, sn_mesh_info* info);
 
+/*
+ * Sweep schedule (tuning; results are identical to rounding-free reordering, i.e. bitwise):
+ *   schedule 0: one launch per wavefront level of all directions;
+ *   schedule 1 (default): one persistent launch per sweep in which warps claim 32-item chunks
+ *   in level order and wait (bounded, SN_ERR_TIMEOUT after 4 s) for their upwind neighbours.
+ * block: threads per block (32..128, multiple of 32); max_blocks_per_sm: 0 = occupancy limit.
+ */
+sn_status sn_mesh_set_schedule(sn_mesh* mesh, int schedule, int block, int max_blocks_per_sm);
+
+/*
+ * Test hook for the bounded waits of the dataflow schedule: the next sweep's items publish a
+ * completion value that no waiter accepts, so every dependent item waits timeout_seconds
+ * (0 < t <= 4), the kernel records the failure and exits, and the call returns SN_ERR_TIMEOUT.
+ * The context stays usable; later sweeps are unaffected.
+ */
+sn_status sn_debug_stall_next_sweep(sn_mesh* mesh, double timeout_seconds);
+
 /* Quadrature readback: dirs (host, n_dirs x 3) and weights (host, n_dirs). */
 sn_status sn_mesh_quadrature(const sn_mesh* mesh, double* dirs, double* weights);
 

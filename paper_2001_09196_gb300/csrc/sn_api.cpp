@@ -56,7 +56,8 @@ void free_mesh(sn_mesh* m) {
     if (!m) return;
     for (void* p : {(void*)m->d_dirs, (void*)m->d_wts, (void*)m->d_corners, (void*)m->d_sigma_t, (void*)m->d_sigma_s,
                     (void*)m->d_q, m->d_psi, m->d_psi32, (void*)m->d_lambda, (void*)m->d_work, (void*)m->d_red,
-                    (void*)m->d_scalars, (void*)m->levels.items})
+                    (void*)m->d_scalars, (void*)m->levels.items, (void*)m->levels.padded, (void*)m->levels.padded_rev, (void*)m->levels.done,
+                    (void*)m->levels.ctrl})
         if (p) cudaFree(p);
     sn::dsa_free(m->dsa);
     delete m;
@@ -256,6 +257,30 @@ sn_status sn_sweep(sn_mesh* m, const double* phi_in, double* phi_out, int precis
     cudaStream_t s = (cudaStream_t)stream;
     CK(sn::launch_sweep(m, phi_in, precision, 1.0, s), "sweep");
     CK(sn::launch_phi_reduce(m, precision, nullptr, phi_out, nullptr, s), "phi reduce");
+    if (m->schedule == sn::SCHED_DATAFLOW) {
+        bool timed_out = false;
+        CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
+        if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out");
+    }
+    return SN_OK;
+}
+
+sn_status sn_debug_stall_next_sweep(sn_mesh* m, double timeout_seconds) {
+    if (!m) return fail(SN_ERR_ARG, "null mesh");
+    if (!(timeout_seconds > 0.0 && timeout_seconds <= 4.0)) return fail(SN_ERR_ARG, "timeout must be in (0, 4] s");
+    if (m->schedule != sn::SCHED_DATAFLOW) return fail(SN_ERR_ARG, "only the dataflow schedule waits");
+    m->levels.stall_timeout_s = timeout_seconds;
+    return SN_OK;
+}
+
+sn_status sn_mesh_set_schedule(sn_mesh* m, int schedule, int block, int max_blocks_per_sm) {
+    if (!m) return fail(SN_ERR_ARG, "null mesh");
+    if (schedule != sn::SCHED_LEVELS && schedule != sn::SCHED_DATAFLOW) return fail(SN_ERR_ARG, "bad schedule");
+    if (block < 32 || block > 128 || block % 32) return fail(SN_ERR_ARG, "block must be 32, 64, 96 or 128");
+    if (max_blocks_per_sm < 0) return fail(SN_ERR_ARG, "max_blocks_per_sm must be >= 0");
+    m->schedule = schedule;
+    m->block = block;
+    m->max_blocks_per_sm = max_blocks_per_sm;
     return SN_OK;
 }
 
@@ -326,6 +351,11 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
         double rr = 0.0;
         CK(cudaMemcpyAsync(&rr, m->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
         CK(cudaStreamSynchronize(s), "sync");
+        if (m->schedule == sn::SCHED_DATAFLOW) {
+            bool timed_out = false;
+            CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
+            if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out");
+        }
         const double rn = std::sqrt(rr);
         if (it == 0) r0 = rn > 0 ? rn : 1.0;
         rel = rn / r0;
@@ -371,6 +401,11 @@ sn_status sn_adjoint_sweep(sn_mesh* m, const double* mu, double* out, int precis
     cudaStream_t s = (cudaStream_t)stream;
     CK(sn::launch_adjoint_sweep(m, mu, s), "adjoint sweep");
     CK(sn::launch_adjoint_reduce(m, out, s), "adjoint reduce");
+    if (m->schedule == sn::SCHED_DATAFLOW) {
+        bool timed_out = false;
+        CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
+        if (timed_out) return fail(SN_ERR_TIMEOUT, "an adjoint sweep dependency wait timed out");
+    }
     return SN_OK;
 }
 

@@ -54,11 +54,32 @@ struct SweepArgs {
     double q_scale;                 // multiplies q (1 normally, 0 for homogeneous solves)
 };
 
+// Persistent dataflow sweep: padded work list and completion words.
+struct DataflowArgs {
+    const int2* items;               // chunks of 32 items, each chunk inside one level; padding = (-1, -1)
+    long long n_items;               // multiple of 32
+    int* done;                       // nd x ne completion epochs
+    int epoch;                       // value that marks "done in this sweep"
+    int publish;                     // value an item writes when done (== epoch except in the stall test)
+    unsigned long long* next;        // chunk counter, zeroed before each launch
+    int* error;                      // set to 1 when a wait times out
+    unsigned long long timeout_ns;   // per-launch wait budget
+};
+
 struct LevelSets {
     std::vector<long long> level_ptr;   // host copy, n_levels + 1
     int2* items = nullptr;              // device, sorted by (level, dir, elem)
     int n_levels = 0;
+    int2* padded = nullptr;             // device, each level padded to a multiple of 32 with (-1, -1)
+    long long n_padded = 0;
+    int2* padded_rev = nullptr;         // device, levels in reverse order (adjoint), padded the same way
+    int* done = nullptr;                // device, nd x ne completion epochs (dataflow schedule)
+    unsigned long long* ctrl = nullptr; // device: [0] chunk counter, [1] error word
+    int epoch = 0;
+    double stall_timeout_s = 0.0;       // > 0: the next dataflow sweep publishes a value nobody waits for
 };
+
+enum { SCHED_LEVELS = 0, SCHED_DATAFLOW = 1 };
 
 struct DsaHierarchy;  // sn_dsa.cu
 
@@ -85,6 +106,9 @@ struct sn_mesh {
     int red_blocks = 0;
     double* d_scalars = nullptr;    // small device scalars
     sn::LevelSets levels;
+    int schedule = sn::SCHED_DATAFLOW;  // sweep schedule (see sn_mesh_set_schedule)
+    int block = 128;                    // threads per block of the sweep kernels
+    int max_blocks_per_sm = 0;          // 0: occupancy limit
     sn::DsaHierarchy* dsa = nullptr;
     int dsa_key_dsa = -1, dsa_key_rule = -1, dsa_key_sigma = -1;
     double dsa_key_eta = 0;
@@ -103,6 +127,8 @@ cudaError_t launch_gradients(sn_mesh* m, const double* phi, double* gt, double* 
 cudaError_t launch_axpy_norm(sn_mesh* m, const double* a, const double* b, double* out, double* d_rr,
                              cudaStream_t s);
 cudaError_t launch_copy(double* dst, const double* src, size_t n, cudaStream_t s);
+// Reads and clears the dataflow error word (synchronises the stream).
+cudaError_t take_sweep_error(sn_mesh* m, cudaStream_t s, bool* timed_out);
 cudaError_t launch_axpy_add(double* y, const double* x, size_t n, cudaStream_t s);  // y += x
 cudaError_t launch_widen(double* y, const float* x, size_t n, cudaStream_t s);
 // sn_dsa.cu

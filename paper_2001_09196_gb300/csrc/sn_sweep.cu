@@ -275,6 +275,96 @@ __device__ __forceinline__ void apply_A(const ElemGeom<DIM, P>& g, double st, co
     }
 }
 
+// Structural nonzeros of A_e after unpivoted elimination.  A_e couples only nodes that differ
+// in at most one tensor index (mass, line advection, face terms), so part of L and U stays zero;
+// the table is evaluated at compile time and the factor/solve loops skip those entries.
+template <int DIM, int P>
+struct LuPattern {
+    static constexpr int Q = P + 1;
+    static constexpr int N = DIM == 2 ? Q * Q : Q * Q * Q;
+    struct Table {
+        unsigned rows[N];  // bit j of rows[i]: entry (i, j) may be nonzero
+    };
+    __host__ __device__ static constexpr Table build() {
+        Table t{};
+        for (int i = 0; i < N; ++i) {
+            t.rows[i] = 0u;
+            for (int j = 0; j < N; ++j) {
+                int diff = 0;
+                int a = i, b = j;
+                for (int ax = 0; ax < DIM; ++ax) {
+                    diff += (a % Q) != (b % Q);
+                    a /= Q;
+                    b /= Q;
+                }
+                if (diff <= 1) t.rows[i] |= 1u << j;
+            }
+        }
+        for (int k = 0; k < N; ++k)
+            for (int i = k + 1; i < N; ++i)
+                if ((t.rows[i] >> k) & 1u)
+                    for (int j = k + 1; j < N; ++j)
+                        if ((t.rows[k] >> j) & 1u) t.rows[i] |= 1u << j;
+        return t;
+    }
+};
+
+template <int DIM, int P, typename R>
+__device__ __forceinline__ void lu_factor_s(R* A) {
+    constexpr int N = LuPattern<DIM, P>::N;
+    constexpr typename LuPattern<DIM, P>::Table pat = LuPattern<DIM, P>::build();
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const R inv = R(1) / A[k * N + k];
+        A[k * N + k] = inv;
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) {
+            if (!((pat.rows[i] >> k) & 1u)) continue;
+            const R l = A[i * N + k] * inv;
+            A[i * N + k] = l;
+#pragma unroll
+            for (int j = k + 1; j < N; ++j)
+                if ((pat.rows[k] >> j) & 1u) A[i * N + j] -= l * A[k * N + j];
+        }
+    }
+}
+
+template <int DIM, int P, typename R>
+__device__ __forceinline__ void lu_solve_s(const R* A, R* x) {
+    constexpr int N = LuPattern<DIM, P>::N;
+    constexpr typename LuPattern<DIM, P>::Table pat = LuPattern<DIM, P>::build();
+#pragma unroll
+    for (int i = 1; i < N; ++i)
+#pragma unroll
+        for (int k = 0; k < i; ++k)
+            if ((pat.rows[i] >> k) & 1u) x[i] -= A[i * N + k] * x[k];
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+#pragma unroll
+        for (int k = i + 1; k < N; ++k)
+            if ((pat.rows[i] >> k) & 1u) x[i] -= A[i * N + k] * x[k];
+        x[i] *= A[i * N + i];
+    }
+}
+
+template <int DIM, int P, typename R>
+__device__ __forceinline__ void lu_solve_transpose_s(const R* A, R* x) {
+    constexpr int N = LuPattern<DIM, P>::N;
+    constexpr typename LuPattern<DIM, P>::Table pat = LuPattern<DIM, P>::build();
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int k = 0; k < i; ++k)
+            if ((pat.rows[k] >> i) & 1u) x[i] -= A[k * N + i] * x[k];
+        x[i] *= A[i * N + i];
+    }
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i)
+#pragma unroll
+        for (int k = i + 1; k < N; ++k)
+            if ((pat.rows[k] >> i) & 1u) x[i] -= A[k * N + i] * x[k];
+}
+
 template <int N, typename R>
 __device__ __forceinline__ void lu_factor(R* A) {
 #pragma unroll
@@ -347,7 +437,7 @@ __device__ __forceinline__ void assemble_rhs(const SweepArgs& a, const ElemGeom<
                 const RS* pu = psi + ((size_t)d * a.ne + u) * N;
                 RS vals[N];
 #pragma unroll
-                for (int i = 0; i < N; ++i) vals[i] = pu[i];
+                for (int i = 0; i < N; ++i) vals[i] = __ldcg(pu + i);
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
                     double s = 0.0;
@@ -373,12 +463,8 @@ __device__ __forceinline__ void assemble_rhs(const SweepArgs& a, const ElemGeom<
 // MODE 0: float64 solve, float64 storage.  MODE 1: float32 solve and storage.
 // MODE 2: float32 LU + two float64 residual corrections, float64 storage.
 template <int DIM, int P, int MODE>
-__global__ void __launch_bounds__(128) sweep_level_kernel(SweepArgs a, long long begin, long long end) {
+__device__ __forceinline__ void solve_item(const SweepArgs& a, int d, int e) {
     constexpr int N = Shape<DIM, P>::N;
-    const long long t = begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= end) return;
-    const int2 it = a.items[t];
-    const int d = it.x, e = it.y;
     const double Ox = a.dirs[3 * d], Oy = a.dirs[3 * d + 1], Oz = a.dirs[3 * d + 2];
     ElemGeom<DIM, P> g;
     elem_geom<DIM, P>(a, e, Ox, Oy, Oz, g);
@@ -390,8 +476,8 @@ __global__ void __launch_bounds__(128) sweep_level_kernel(SweepArgs a, long long
         assemble<DIM, P, float>(g, st, A);
 #pragma unroll
         for (int i = 0; i < N; ++i) x[i] = (float)rhs[i];
-        lu_factor<N, float>(A);
-        lu_solve<N, float>(A, x);
+        lu_factor_s<DIM, P, float>(A);
+        lu_solve_s<DIM, P, float>(A, x);
         float* out = static_cast<float*>(a.psi) + ((size_t)d * a.ne + e) * N;
 #pragma unroll
         for (int i = 0; i < N; ++i) out[i] = x[i];
@@ -399,8 +485,8 @@ __global__ void __launch_bounds__(128) sweep_level_kernel(SweepArgs a, long long
         assemble_rhs<DIM, P, double>(a, g, d, e, rhs);
         double A[N * N];
         assemble<DIM, P, double>(g, st, A);
-        lu_factor<N, double>(A);
-        lu_solve<N, double>(A, rhs);
+        lu_factor_s<DIM, P, double>(A);
+        lu_solve_s<DIM, P, double>(A, rhs);
         double* out = static_cast<double*>(a.psi) + ((size_t)d * a.ne + e) * N;
 #pragma unroll
         for (int i = 0; i < N; ++i) out[i] = rhs[i];
@@ -410,10 +496,10 @@ __global__ void __launch_bounds__(128) sweep_level_kernel(SweepArgs a, long long
         float c[N];
         double x[N], r[N];
         assemble<DIM, P, float>(g, st, A);
-        lu_factor<N, float>(A);
+        lu_factor_s<DIM, P, float>(A);
 #pragma unroll
         for (int i = 0; i < N; ++i) c[i] = (float)rhs[i];
-        lu_solve<N, float>(A, c);
+        lu_solve_s<DIM, P, float>(A, c);
 #pragma unroll
         for (int i = 0; i < N; ++i) x[i] = c[i];
 #pragma unroll 1
@@ -421,7 +507,7 @@ __global__ void __launch_bounds__(128) sweep_level_kernel(SweepArgs a, long long
             apply_A<DIM, P>(g, st, x, r);
 #pragma unroll
             for (int i = 0; i < N; ++i) c[i] = (float)(rhs[i] - r[i]);
-            lu_solve<N, float>(A, c);
+            lu_solve_s<DIM, P, float>(A, c);
 #pragma unroll
             for (int i = 0; i < N; ++i) x[i] += (double)c[i];
         }
@@ -431,15 +517,93 @@ __global__ void __launch_bounds__(128) sweep_level_kernel(SweepArgs a, long long
     }
 }
 
-// Adjoint: A_e^T lam_e = mu_e - sum_{outflow F, downwind u} C(u<-e)^T lam_u, in reverse level order.
-template <int DIM, int P>
-__global__ void __launch_bounds__(128) adjoint_level_kernel(SweepArgs a, const double* mu, long long begin,
-                                                           long long end) {
-    constexpr int Q = P + 1, N = Shape<DIM, P>::N, NT = Shape<DIM, P>::NT;
+template <int DIM, int P, int MODE>
+__global__ void __launch_bounds__(128) sweep_level_kernel(SweepArgs a, long long begin, long long end) {
     const long long t = begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= end) return;
     const int2 it = a.items[t];
-    const int d = it.x, e = it.y;
+    solve_item<DIM, P, MODE>(a, it.x, it.y);
+}
+
+// ---------------------------------------------------------------- persistent dataflow sweep
+// One launch per transport update.  The work list is padded so that every 32-item chunk lies
+// in a single level; warps claim chunks in list order from a global counter, so every item a
+// warp waits for belongs to an earlier level and was claimed by a warp that is running.  An
+// item waits (bounded, with back-off) until each upwind neighbour's completion word holds the
+// current epoch, solves, stores psi and publishes its own word with release semantics.
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <int DIM, int P>
+__device__ __forceinline__ void adjoint_item(const SweepArgs& a, const double* mu, int d, int e);
+
+// ADJ = false: transport update, waits for upwind neighbours (Omega.n < 0 faces).
+// ADJ = true: transposed solve in reverse order, waits for downwind neighbours (Omega.n > 0).
+template <int DIM, int P, int MODE, bool ADJ>
+__global__ void __launch_bounds__(128) sweep_dataflow_kernel(SweepArgs a, DataflowArgs f, const double* mu) {
+    const int lane = threadIdx.x & 31;
+    const long long n_chunks = f.n_items >> 5;
+    const unsigned long long deadline = globaltimer() + f.timeout_ns;
+    while (true) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(f.next, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if ((long long)c >= n_chunks) break;
+        if (*(volatile int*)f.error) break;
+        const int2 it = f.items[(c << 5) + lane];
+        bool ok = true;
+        if (it.x >= 0) {
+            const int d = it.x, e = it.y;
+            const double Ox = a.dirs[3 * d], Oy = a.dirs[3 * d + 1], Oz = a.dirs[3 * d + 2];
+#pragma unroll
+            for (int fc = 0; fc < 2 * DIM; ++fc) {
+                if (!ok) break;
+                const double F = face_flux_only<DIM, P>(a, e, fc, Ox, Oy, Oz);
+                if (ADJ ? F > 0.0 : F < 0.0) {
+                    const int u = neighbor<DIM, P>(a, e, fc);
+                    if (u < 0) continue;
+                    const int* flag = f.done + (size_t)d * a.ne + u;
+                    unsigned ns = 32;
+                    while (ld_acquire(flag) != f.epoch) {
+                        if (globaltimer() > deadline) {
+                            ok = false;
+                            break;
+                        }
+                        __nanosleep(ns);
+                        ns = ns < 1024 ? 2 * ns : 1024;
+                    }
+                }
+            }
+            if (ok) {
+                if constexpr (ADJ) adjoint_item<DIM, P>(a, mu, d, e);
+                else solve_item<DIM, P, MODE>(a, d, e);
+                st_release(f.done + (size_t)d * a.ne + e, f.publish);
+            }
+        }
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) atomicExch(f.error, 1);
+            break;
+        }
+    }
+}
+
+// Adjoint: A_e^T lam_e = mu_e - sum_{outflow F, downwind u} C(u<-e)^T lam_u, in reverse level order.
+template <int DIM, int P>
+__device__ __forceinline__ void adjoint_item(const SweepArgs& a, const double* mu, int d, int e) {
+    constexpr int Q = P + 1, N = Shape<DIM, P>::N, NT = Shape<DIM, P>::NT;
     const double Ox = a.dirs[3 * d], Oy = a.dirs[3 * d + 1], Oz = a.dirs[3 * d + 2];
     ElemGeom<DIM, P> g;
     elem_geom<DIM, P>(a, e, Ox, Oy, Oz, g);
@@ -457,7 +621,7 @@ __global__ void __launch_bounds__(128) adjoint_level_kernel(SweepArgs a, const d
             const double* lu = lam + ((size_t)d * a.ne + u) * N;
             double vals[N];
 #pragma unroll
-            for (int i = 0; i < N; ++i) vals[i] = lu[i];
+            for (int i = 0; i < N; ++i) vals[i] = __ldcg(lu + i);
 #pragma unroll
             for (int tt = 0; tt < NT; ++tt) {
                 double s = 0.0;
@@ -471,11 +635,20 @@ __global__ void __launch_bounds__(128) adjoint_level_kernel(SweepArgs a, const d
     }
     double A[N * N];
     assemble<DIM, P, double>(g, a.sigma_t[e], A);
-    lu_factor<N, double>(A);
-    lu_solve_transpose<N, double>(A, rhs);
+    lu_factor_s<DIM, P, double>(A);
+    lu_solve_transpose_s<DIM, P, double>(A, rhs);
     double* out = static_cast<double*>(a.psi) + ((size_t)d * a.ne + e) * N;
 #pragma unroll
     for (int i = 0; i < N; ++i) out[i] = rhs[i];
+}
+
+template <int DIM, int P>
+__global__ void __launch_bounds__(128) adjoint_level_kernel(SweepArgs a, const double* mu, long long begin,
+                                                           long long end) {
+    const long long t = begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= end) return;
+    const int2 it = a.items[t];
+    adjoint_item<DIM, P>(a, mu, it.x, it.y);
 }
 
 // ---------------------------------------------------------------- level sets (Kahn, on device)
@@ -729,8 +902,76 @@ cudaError_t build_levels(sn_mesh* m, cudaStream_t s, bool* cycle) {
         (err = cudaStreamSynchronize(s)) != cudaSuccess) { cleanup(); return err; }
     m->levels.level_ptr = ptr;
     m->levels.n_levels = L;
+    // padded list for the dataflow schedule: no 32-item chunk crosses a level boundary
+    std::vector<int2> padded;
+    padded.reserve(total + 32 * (size_t)L);
+    for (int l = 0; l < L; ++l) {
+        for (long long t = ptr[l]; t < ptr[l + 1]; ++t) padded.push_back(items[t]);
+        while (padded.size() % 32) padded.push_back(make_int2(-1, -1));
+    }
+    if (m->levels.padded) cudaFree(m->levels.padded);
+    m->levels.padded = nullptr;
+    m->levels.n_padded = (long long)padded.size();
+    if ((err = cudaMalloc(&m->levels.padded, padded.size() * sizeof(int2))) != cudaSuccess) { cleanup(); return err; }
+    if ((err = cudaMemcpyAsync(m->levels.padded, padded.data(), padded.size() * sizeof(int2), cudaMemcpyHostToDevice, s)) != cudaSuccess) { cleanup(); return err; }
+    std::vector<int2> padded_rev;
+    padded_rev.reserve(padded.size());
+    for (int l = L - 1; l >= 0; --l) {
+        for (long long t = ptr[l]; t < ptr[l + 1]; ++t) padded_rev.push_back(items[t]);
+        while (padded_rev.size() % 32) padded_rev.push_back(make_int2(-1, -1));
+    }
+    if (m->levels.padded_rev) cudaFree(m->levels.padded_rev);
+    m->levels.padded_rev = nullptr;
+    if ((err = cudaMalloc(&m->levels.padded_rev, padded_rev.size() * sizeof(int2))) != cudaSuccess) { cleanup(); return err; }
+    if ((err = cudaMemcpyAsync(m->levels.padded_rev, padded_rev.data(), padded_rev.size() * sizeof(int2), cudaMemcpyHostToDevice, s)) != cudaSuccess) { cleanup(); return err; }
+    if (!m->levels.done) {
+        if ((err = cudaMalloc(&m->levels.done, total * sizeof(int))) != cudaSuccess) { cleanup(); return err; }
+        if ((err = cudaMalloc(&m->levels.ctrl, 2 * sizeof(unsigned long long))) != cudaSuccess) { cleanup(); return err; }
+    }
+    cudaMemsetAsync(m->levels.done, 0, total * sizeof(int), s);
+    cudaMemsetAsync(m->levels.ctrl, 0, 2 * sizeof(unsigned long long), s);
+    m->levels.epoch = 0;
+    if ((err = cudaStreamSynchronize(s)) != cudaSuccess) { cleanup(); return err; }
     cleanup();
     return cudaSuccess;
+}
+
+template <int DIM, int P, int MODE, bool ADJ = false>
+static cudaError_t launch_dataflow(sn_mesh* m, const SweepArgs& a, cudaStream_t s, const double* mu = nullptr) {
+    LevelSets& L = m->levels;
+    if (++L.epoch == 0x7fffffff) {  // epochs wrap: start over from a cleared table
+        cudaMemsetAsync(L.done, 0, (size_t)m->nd * m->ne * sizeof(int), s);
+        L.epoch = 1;
+    }
+    cudaMemsetAsync(L.ctrl, 0, sizeof(unsigned long long), s);
+    DataflowArgs f;
+    f.items = ADJ ? L.padded_rev : L.padded;
+    f.n_items = L.n_padded;
+    f.done = L.done;
+    f.epoch = L.epoch;
+    f.next = L.ctrl;
+    f.error = reinterpret_cast<int*>(L.ctrl + 1);
+    f.timeout_ns = 4000000000ull;
+    f.publish = L.epoch;
+    if (L.stall_timeout_s > 0.0) {  // test hook: completion words never match, every wait times out
+        f.publish = -1;
+        f.timeout_ns = (unsigned long long)(L.stall_timeout_s * 1e9);
+        L.stall_timeout_s = 0.0;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_dataflow_kernel<DIM, P, MODE, ADJ>, m->block, 0);
+    if (m->max_blocks_per_sm > 0 && m->max_blocks_per_sm < per_sm) per_sm = m->max_blocks_per_sm;
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    const long long warps_needed = L.n_padded / 32;
+    long long blocks = (long long)sms * per_sm;
+    const long long cap = (warps_needed * 32 + m->block - 1) / m->block;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    SN_COUNT_LAUNCH();
+    sweep_dataflow_kernel<DIM, P, MODE, ADJ><<<(unsigned)blocks, m->block, 0, s>>>(a, f, mu);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double q_scale, cudaStream_t s) {
@@ -738,7 +979,13 @@ cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double
     a.phi = phi_in;
     a.q_scale = q_scale;
     a.psi = precision == SN_FP32 ? m->d_psi32 : m->d_psi;
-    const int bs = 128;
+    if (m->schedule == SCHED_DATAFLOW) {
+        if (precision == SN_FP64) SN_DISPATCH(m->dim, m->p, (launch_dataflow<D_, P_, 0>(m, a, s)));
+        else if (precision == SN_FP32) SN_DISPATCH(m->dim, m->p, (launch_dataflow<D_, P_, 1>(m, a, s)));
+        else SN_DISPATCH(m->dim, m->p, (launch_dataflow<D_, P_, 2>(m, a, s)));
+        return cudaGetLastError();
+    }
+    const int bs = m->block;
     for (int L = 0; L < m->levels.n_levels; ++L) {
         const long long b = m->levels.level_ptr[L], e = m->levels.level_ptr[L + 1];
         if (e <= b) continue;
@@ -760,7 +1007,11 @@ cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double
 cudaError_t launch_adjoint_sweep(sn_mesh* m, const double* mu, cudaStream_t s) {
     SweepArgs a = make_args(m);
     a.psi = m->d_lambda;
-    const int bs = 128;
+    if (m->schedule == SCHED_DATAFLOW) {
+        SN_DISPATCH(m->dim, m->p, (launch_dataflow<D_, P_, 0, true>(m, a, s, mu)));
+        return cudaGetLastError();
+    }
+    const int bs = m->block;
     for (int L = m->levels.n_levels - 1; L >= 0; --L) {
         const long long b = m->levels.level_ptr[L], e = m->levels.level_ptr[L + 1];
         if (e <= b) continue;
@@ -833,6 +1084,21 @@ cudaError_t launch_widen(double* y, const float* x, size_t n, cudaStream_t s) {
     SN_COUNT_LAUNCH();
     widen_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, x, n);
     return cudaGetLastError();
+}
+
+cudaError_t take_sweep_error(sn_mesh* m, cudaStream_t s, bool* timed_out) {
+    *timed_out = false;
+    if (!m->levels.ctrl) return cudaSuccess;
+    unsigned long long w = 0;
+    cudaError_t err = cudaMemcpyAsync(&w, m->levels.ctrl + 1, sizeof(w), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return err;
+    if (w) {
+        *timed_out = true;
+        err = cudaMemsetAsync(m->levels.ctrl + 1, 0, sizeof(w), s);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    }
+    return err;
 }
 
 cudaError_t launch_copy(double* dst, const double* src, size_t n, cudaStream_t s) {

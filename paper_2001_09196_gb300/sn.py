@@ -76,6 +76,8 @@ def _load():
         "sn_dsa_apply": [vp, C.POINTER(IterOpts), vp, vp, vp],
         "sn_dsa_solve": [vp, C.POINTER(IterOpts), vp, vp, C.POINTER(C.c_int), vp],
         "sn_get_angular_flux": [vp, i, i, i, vp, vp],
+        "sn_mesh_set_schedule": [vp, i, i, i],
+        "sn_debug_stall_next_sweep": [vp, d],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -188,6 +190,13 @@ class Mesh:
     @property
     def shape(self):
         return (self.n_elem, self.n_nodes)
+
+    def set_schedule(self, schedule="dataflow", block=128, max_blocks_per_sm=0):
+        sched = {"levels": 0, "dataflow": 1}[schedule] if isinstance(schedule, str) else int(schedule)
+        _check(_lib.sn_mesh_set_schedule(self._h, sched, int(block), int(max_blocks_per_sm)))
+
+    def debug_stall_next_sweep(self, timeout_s=0.2):
+        _check(_lib.sn_debug_stall_next_sweep(self._h, float(timeout_s)))
 
     def quadrature(self):
         dirs = np.zeros((self.n_dirs, 3))

@@ -205,6 +205,28 @@ sn_status sn_dsa_solve(sn_mesh* mesh, const sn_iter_opts* opts, const double* b,
  */
 sn_status sn_get_angular_flux(sn_mesh* mesh, int d, int adjoint, int precision, double* out, void* stream);
 
+/*
+ * sn_scalar_flux_noalloc: the scalar-flux reduction of a transport update without any device
+ * allocation.  The paper has no counterpart; it exists for callers that cannot call cudaMalloc:
+ * code recording a CUDA graph (allocation calls are not capturable), frameworks whose caching
+ * allocator owns all device memory, and latency-critical loops that cannot afford cudaMalloc's
+ * implicit synchronisation.  Computes, in float64 with the same summation order as sn_sweep,
+ *     phi_out[i] = sum_d weights[d] * psi[d * n_values + i],
+ *     *resid_norm2 = sum_i (phi_out[i] - phi_prev[i])^2     (phi_prev NULL means 0; resid_norm2 may be NULL).
+ * psi (n_dirs x n_values), weights (n_dirs), phi_prev, phi_out (n_values) and resid_norm2 (1) are
+ * caller-owned device pointers; phi_out must not alias the inputs.
+ * Scratch: the per-block partial sums live in one file-scope device array of 8192 doubles (64 KB),
+ * held by every GPU that loads the library until the process exits, which limits n_values to
+ * 2,097,152 (larger sizes return SN_ERR_ARG before any GPU work).  The array is shared by all calls
+ * and keeps the last call's partial sums; each call overwrites every slot it reads, so nothing
+ * needs clearing, but calls whose kernels overlap on the GPU (different streams, no ordering)
+ * race on it.  The first call on each device (with that device current) resolves the array's
+ * device address with cudaGetSymbolAddress; make that first call before any stream capture.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
+ */
+sn_status sn_scalar_flux_noalloc(const double* psi, const double* weights, int n_dirs, long long n_values,
+                                 const double* phi_prev, double* phi_out, double* resid_norm2, void* stream);
+
 /* Number of CUDA kernels the library has launched since it was loaded (diagnostic). */
 long long sn_launch_count(void);
 

@@ -71,6 +71,11 @@ bool finite_nonneg(const std::vector<double>& v) {
 
 }  // namespace
 
+sn_status sn::set_error(sn_status st, const char* msg) {
+    g_err = msg;
+    return st;
+}
+
 extern "C" {
 
 const char* sn_last_error(void) { return g_err.c_str(); }

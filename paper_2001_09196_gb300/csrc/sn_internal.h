@@ -116,6 +116,8 @@ struct sn_mesh {
 };
 
 namespace sn {
+// sn_api.cpp: records the thread-local message returned by sn_last_error
+sn_status set_error(sn_status st, const char* msg);
 // sn_sweep.cu
 cudaError_t build_levels(sn_mesh* m, cudaStream_t s, bool* cycle);
 cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double q_scale, cudaStream_t s);

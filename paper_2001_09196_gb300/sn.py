@@ -78,6 +78,7 @@ def _load():
         "sn_get_angular_flux": [vp, i, i, i, vp, vp],
         "sn_mesh_set_schedule": [vp, i, i, i],
         "sn_debug_stall_next_sweep": [vp, d],
+        "sn_scalar_flux_noalloc": [vp, vp, i, C.c_longlong, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -150,6 +151,24 @@ def make_opts(dsa="thick", thick_rule="sigma_s", eta=1.0, mask=None, dsa_sigma="
     o.warm_start = int(bool(warm_start))
     o._keep = keep
     return o
+
+
+def scalar_flux_noalloc(psi, weights, phi_prev=None, phi_out=None, resid_norm2=None, stream=None):
+    """phi_out = sum_d w_d psi_d and ||phi_out - phi_prev||^2 without device allocation in libsn.
+
+    psi: (n_dirs, n_values) float64 CUDA tensor; weights: (n_dirs,) float64 CUDA tensor.
+    Outputs are caller-provided (allocated here by torch only when not given).
+    """
+    import torch
+    nd = int(psi.shape[0])
+    m = int(psi.numel() // nd)
+    if phi_out is None:
+        phi_out = torch.empty(m, dtype=torch.float64, device=psi.device)
+    if resid_norm2 is None:
+        resid_norm2 = torch.empty(1, dtype=torch.float64, device=psi.device)
+    _check(_lib.sn_scalar_flux_noalloc(_ptr(psi), _ptr(weights), nd, m, _ptr(phi_prev), _ptr(phi_out),
+                                       _ptr(resid_norm2), _stream(stream)))
+    return phi_out, resid_norm2
 
 
 class Mesh:

@@ -49,6 +49,7 @@ enum { SN_FP64 = 0, SN_FP32 = 1, SN_FP32_REFINE = 2 };          /* element-solve
 enum { SN_DSA_NONE = 0, SN_DSA_FULL = 1, SN_DSA_THICK = 2 };    /* DSA variant */
 enum { SN_THICK_SIGMA_S = 0, SN_THICK_SIGMA_T_H = 1, SN_THICK_MASK = 2 };
 enum { SN_DSA_SIGMA_S = 0, SN_DSA_SIGMA_T = 1 };
+enum { SN_OUTER_SI = 0, SN_OUTER_FGMRES = 1 };                  /* outer iteration */
 
 typedef struct sn_mesh sn_mesh;
 
@@ -80,8 +81,9 @@ sn_status sn_mesh_get_info(const sn_mesh* mesh, sn_mesh_info* info);
 
 /*
  * Sweep schedule (tuning; results are identical to rounding-free reordering, i.e. bitwise):
- *   schedule 0: one launch per wavefront level of all directions;
- *   schedule 1 (default): one persistent launch per sweep in which warps claim 32-item chunks
+ *   schedule 0 (default): one launch per wavefront level of all directions, captured once into a
+ *   CUDA graph so that a sweep is a single graph launch;
+ *   schedule 1: one persistent launch per sweep in which warps claim 32-item chunks
  *   in level order and wait (bounded, SN_ERR_TIMEOUT after 4 s) for their upwind neighbours.
  * block: threads per block (32..128, multiple of 32); max_blocks_per_sm: 0 = occupancy limit.
  */
@@ -131,6 +133,8 @@ typedef struct {
     double* checkpoints;     /* device, max_checkpoints x n_elem x n_nodes, or NULL */
     int max_checkpoints;
     int warm_start;          /* 1: start from phi_inout, 0: from phi = 0 */
+    int outer;               /* SN_OUTER_SI (fixed point, Eq. DSA_fp) | SN_OUTER_FGMRES (Sec. 5) */
+    int restart;             /* fGMRES restart length (1..60; the paper uses 30) */
 } sn_iter_opts;
 
 typedef struct {
@@ -142,6 +146,7 @@ typedef struct {
     int history_len;
     int n_checkpoints;       /* checkpoints written */
     double ms_total;         /* wall time of the call (stream-synchronised) */
+    int n_sweeps;            /* transport updates performed (all directions each) */
 } sn_iter_stats;
 
 /* Defaults: dsa thick, sigma_s >= 1, tol 1e-8, inner_tol 1e-4 (Sec. 5), FP64, cold start. */
@@ -156,6 +161,10 @@ void sn_iter_opts_default(sn_iter_opts* opts);
  * (Sec. 4.1-4.2; SN_DSA_FULL uses every element) solved by conjugate gradients
  * preconditioned with a geometric multigrid V-cycle.  Stops after the iteration whose
  * ||r^i|| <= tol ||r^0||.  phi_inout: device [elem][node]; receives phi^{i+1}.
+ * With outer = SN_OUTER_FGMRES the same system S phi = b (Eq. schur) is solved by flexible
+ * GMRES(restart) right-preconditioned by the same DSA step, I + E_f D_ff^{-1} Sigma_f E_f^T (the paper's
+ * outer solver, Sec. 5; "flexible" because each DSA solve is inexact).  Its residual b - S phi equals
+ * the source-iteration residual, so tol means the same; iters counts Krylov iterations.
  * SN_ERR_VOID_FULL_DSA if dsa = FULL and some sigma_t = 0; SN_ERR_NOT_CONVERGED after
  * max_iters (phi_inout still written).  stats may be NULL.
  */

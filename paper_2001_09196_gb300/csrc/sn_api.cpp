@@ -54,10 +54,13 @@ cudaError_t dalloc(T** p, size_t count) {
 
 void free_mesh(sn_mesh* m) {
     if (!m) return;
+    sn::drop_level_graphs(m);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    if (m->d_src) cudaFree(m->d_src);
     for (void* p : {(void*)m->d_dirs, (void*)m->d_wts, (void*)m->d_corners, (void*)m->d_sigma_t, (void*)m->d_sigma_s,
-                    (void*)m->d_q, m->d_psi, m->d_psi32, (void*)m->d_lambda, (void*)m->d_work, (void*)m->d_red,
+                    (void*)m->d_q, m->d_psi, m->d_psi32, (void*)m->d_lambda, (void*)m->d_mass, (void*)m->d_work, (void*)m->d_red,
                     (void*)m->d_scalars, (void*)m->levels.items, (void*)m->levels.padded, (void*)m->levels.padded_rev, (void*)m->levels.done,
-                    (void*)m->levels.ctrl})
+                    (void*)m->levels.ctrl, (void*)m->d_krylov})
         if (p) cudaFree(p);
     sn::dsa_free(m->dsa);
     delete m;
@@ -93,6 +96,8 @@ void sn_iter_opts_default(sn_iter_opts* o) {
     o->max_iters = 1000;
     o->inner_max_iters = 200;
     o->precision = SN_FP64;
+    o->outer = SN_OUTER_SI;
+    o->restart = 30;
 }
 
 sn_status sn_mesh_create(const sn_mesh_desc* desc, sn_mesh** out) {
@@ -180,6 +185,9 @@ sn_status sn_mesh_create(const sn_mesh_desc* desc, sn_mesh** out) {
     m->red_blocks = (int)((M + 255) / 256);
     CK(dalloc(&m->d_red, m->red_blocks), "alloc");
     CK(dalloc(&m->d_scalars, 16), "alloc");
+    CK(dalloc(&m->d_mass, M), "alloc");
+    CK(dalloc(&m->d_src, M), "alloc");
+    CK(sn::compute_mass(m.get(), 0), "element masses");
     bool cycle = false;
     CK(sn::build_levels(m.get(), 0, &cycle), "level sets");
     if (cycle) return fail(SN_ERR_CYCLE, "an upwind graph has a cycle");
@@ -242,12 +250,14 @@ sn_status sn_set_materials(sn_mesh* m, const double* st, const double* ss, const
 static sn_status ensure_psi32(sn_mesh* m) {
     if (m->d_psi32) return SN_OK;
     CK(cudaMalloc(&m->d_psi32, (size_t)m->nd * m->ne * m->n * sizeof(float)), "alloc psi32");
+    sn::drop_level_graphs(m);
     return SN_OK;
 }
 
 static sn_status ensure_lambda(sn_mesh* m) {
     if (m->d_lambda) return SN_OK;
     CK(cudaMalloc(&m->d_lambda, (size_t)m->nd * m->ne * m->n * sizeof(double)), "alloc lambda");
+    sn::drop_level_graphs(m);
     return SN_OK;
 }
 
@@ -283,6 +293,7 @@ sn_status sn_mesh_set_schedule(sn_mesh* m, int schedule, int block, int max_bloc
     if (schedule != sn::SCHED_LEVELS && schedule != sn::SCHED_DATAFLOW) return fail(SN_ERR_ARG, "bad schedule");
     if (block < 32 || block > 128 || block % 32) return fail(SN_ERR_ARG, "block must be 32, 64, 96 or 128");
     if (max_blocks_per_sm < 0) return fail(SN_ERR_ARG, "max_blocks_per_sm must be >= 0");
+    if (m->block != block) sn::drop_level_graphs(m);
     m->schedule = schedule;
     m->block = block;
     m->max_blocks_per_sm = max_blocks_per_sm;
@@ -332,6 +343,133 @@ static sn_status check_opts(const sn_iter_opts* o) {
         return fail(SN_ERR_ARG, "bad inner_tol / inner_max_iters");
     if (o->checkpoint_every > 0 && (!o->checkpoints || o->max_checkpoints < 1))
         return fail(SN_ERR_ARG, "checkpointing needs a buffer");
+    if (o->outer != SN_OUTER_SI && o->outer != SN_OUTER_FGMRES) return fail(SN_ERR_ARG, "bad outer iteration");
+    if (o->outer == SN_OUTER_FGMRES && (o->restart < 1 || o->restart > 60))
+        return fail(SN_ERR_ARG, "restart must be in 1..60");
+    return SN_OK;
+}
+
+// Flexible GMRES(k) on S x = b (Eq. schur), right-preconditioned by the DSA step
+// P v = v + E_f D_ff^{-1} Sigma_f E_f^T v (Algorithm 2 applied to a residual); classical
+// Gram-Schmidt twice, Givens rotations on the host.
+static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_stats* stats, cudaStream_t s,
+                        std::chrono::steady_clock::time_point t0) {
+    const long long M = (long long)m->ne * m->n;
+    const int k = o->restart;
+    const int nb = sn::krylov_blocks(M);
+    const size_t need = (size_t)(2 * k + 2) * M + (size_t)(k + 1) * nb + 4 * (k + 2);
+    if (!m->d_krylov || m->krylov_restart < k) {
+        if (m->d_krylov) cudaFree(m->d_krylov);
+        m->d_krylov = nullptr;
+        CK(cudaMalloc(&m->d_krylov, need * sizeof(double)), "alloc fGMRES workspace");
+        m->krylov_restart = k;
+    }
+    double* V = m->d_krylov;                    // (k+1) x M
+    double* Z = V + (size_t)(k + 1) * M;        // k x M
+    double* w = Z + (size_t)k * M;              // M
+    double* part = w + M;                       // (k+1) x nb
+    double* hd = part + (size_t)(k + 1) * nb;   // h (k+1), h2 (k+1), norm, y (k)
+    double* tmp = m->d_work + 2 * (size_t)M;
+    std::vector<double> H((size_t)(k + 1) * k, 0.0), cs(k), sn_(k), g(k + 1), hh(2 * (k + 1) + 1), y(k);
+    double r0 = 0.0, rel = INFINITY;
+    int it = 0, inner_total = 0, sweeps = 0;
+    bool converged = false;
+    bool timed_out = false;
+    while (true) {
+        // true residual r = sweep(x) - x (with the fixed source)
+        ++sweeps;
+        CK(sn::launch_sweep(m, x, o->precision, 1.0, s), "sweep");
+        CK(sn::launch_phi_reduce(m, o->precision, x, tmp, m->d_scalars, s), "phi reduce");
+        CK(sn::launch_axpy_norm(m, tmp, x, w, m->d_scalars, s), "residual");
+        double rr = 0.0;
+        CK(cudaMemcpyAsync(&rr, m->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+        CK(cudaStreamSynchronize(s), "sync");
+        if (m->schedule == sn::SCHED_DATAFLOW) {
+            CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
+            if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out");
+        }
+        const double beta = std::sqrt(rr);
+        if (r0 == 0.0) r0 = beta > 0 ? beta : 1.0;
+        rel = beta / r0;
+        if (stats && stats->residual_history && it < stats->history_len && it == 0) stats->residual_history[0] = rel;
+        if (rel <= o->tol || beta == 0.0) {  // convergence is declared on the true residual only
+            converged = true;
+            break;
+        }
+        if (it >= o->max_iters) break;
+        CK(sn::launch_normalize(w, M, part, hd, V, s), "normalize");
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int jj = 0;
+        for (int j = 0; j < k && it < o->max_iters; ++j) {
+            double* Vj = V + (size_t)j * M;
+            double* Zj = Z + (size_t)j * M;
+            CK(sn::launch_copy(Zj, Vj, M, s), "copy");
+            if (o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0) {
+                int its = 0;
+                CK(sn::dsa_correct(m->dsa, Vj, Zj, o->inner_tol, o->inner_max_iters, false, &its, s), "DSA");
+                inner_total += its;
+            }
+            // w = S Zj = Zj - T Zj (T: sweep without the fixed source)
+            CK(sn::launch_sweep(m, Zj, o->precision, 0.0, s), "sweep");
+            ++sweeps;
+            CK(sn::launch_phi_reduce(m, o->precision, nullptr, tmp, nullptr, s), "phi reduce");
+            CK(sn::launch_axpy_norm(m, Zj, tmp, w, m->d_scalars, s), "apply S");
+            CK(sn::launch_multidot(V, j + 1, M, w, part, hd, s), "orthogonalise");
+            CK(sn::launch_multiaxpy(V, j + 1, M, hd, -1.0, w, s), "orthogonalise");
+            CK(sn::launch_multidot(V, j + 1, M, w, part, hd + (k + 1), s), "orthogonalise");
+            CK(sn::launch_multiaxpy(V, j + 1, M, hd + (k + 1), -1.0, w, s), "orthogonalise");
+            CK(sn::launch_multidot(w, 1, M, w, part, hd + 2 * (k + 1), s), "norm");
+            CK(cudaMemcpyAsync(hh.data(), hd, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+            CK(cudaStreamSynchronize(s), "sync");
+            if (m->schedule == sn::SCHED_DATAFLOW) {
+                CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
+                if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out");
+            }
+            double* h = &H[(size_t)j * (k + 1)];
+            for (int i = 0; i <= j; ++i) h[i] = hh[i] + hh[k + 1 + i];
+            h[j + 1] = std::sqrt(std::max(hh[2 * (k + 1)], 0.0));
+            const double hnext = h[j + 1];
+            for (int i = 0; i < j; ++i) {
+                const double t = cs[i] * h[i] + sn_[i] * h[i + 1];
+                h[i + 1] = -sn_[i] * h[i] + cs[i] * h[i + 1];
+                h[i] = t;
+            }
+            const double rho = std::hypot(h[j], h[j + 1]);
+            cs[j] = rho > 0 ? h[j] / rho : 1.0;
+            sn_[j] = rho > 0 ? h[j + 1] / rho : 0.0;
+            h[j] = rho;
+            h[j + 1] = 0.0;
+            g[j + 1] = -sn_[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++it;
+            jj = j + 1;
+            rel = std::fabs(g[j + 1]) / r0;
+            if (stats && stats->residual_history && it < stats->history_len) stats->residual_history[it] = rel;
+            if (rel <= o->tol || hnext <= 1e-300) break;
+            CK(sn::launch_normalize(w, M, part, hd + 2 * (k + 1), V + (size_t)(j + 1) * M, s), "normalize");
+        }
+        // x += Z y with H y = g (upper triangular)
+        for (int i = jj - 1; i >= 0; --i) {
+            double t = g[i];
+            for (int c = i + 1; c < jj; ++c) t -= H[(size_t)c * (k + 1) + i] * y[c];
+            y[i] = t / H[(size_t)i * (k + 1) + i];
+        }
+        CK(cudaMemcpyAsync(hd, y.data(), jj * sizeof(double), cudaMemcpyHostToDevice, s), "copy");
+        CK(sn::launch_multiaxpy(Z, jj, M, hd, 1.0, x, s), "update");
+        // the restart (or the final check) recomputes the true residual with one more sweep
+    }
+    CK(cudaStreamSynchronize(s), "sync");
+    if (stats) {
+        stats->iters = it;
+        stats->rel_residual = rel;
+        stats->inner_iters_total = inner_total;
+        stats->thick_fraction = m->dsa && o->dsa != SN_DSA_NONE ? (double)sn::dsa_thick_count(m->dsa) / m->ne : 0.0;
+        stats->n_checkpoints = 0;
+        stats->n_sweeps = sweeps;
+        stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (!converged) return fail(SN_ERR_NOT_CONVERGED, "fGMRES not converged after %d iterations (%.3e)", it, rel);
     return SN_OK;
 }
 
@@ -343,6 +481,10 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
     cudaStream_t s = (cudaStream_t)stream;
     if (o->precision == SN_FP32 && (st = ensure_psi32(m)) != SN_OK) return st;
     if (o->dsa != SN_DSA_NONE && (st = ensure_dsa(m, o)) != SN_OK) return st;
+    if (o->outer == SN_OUTER_FGMRES) {
+        if (!o->warm_start) CK(cudaMemsetAsync(phi, 0, (size_t)m->ne * m->n * sizeof(double), s), "memset");
+        return fgmres(m, o, phi, stats, s, t0);
+    }
     const size_t M = (size_t)m->ne * m->n;
     double* half = m->d_work;
     double* r = m->d_work + M;
@@ -391,6 +533,7 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
         stats->inner_iters_total = inner_total;
         stats->thick_fraction = m->dsa && o->dsa != SN_DSA_NONE ? (double)sn::dsa_thick_count(m->dsa) / m->ne : 0.0;
         stats->n_checkpoints = nck;
+        stats->n_sweeps = it;
         stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     if (!converged) return fail(SN_ERR_NOT_CONVERGED, "not converged after %d iterations (rel. residual %.3e)", it, rel);

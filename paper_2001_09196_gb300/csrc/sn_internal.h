@@ -48,7 +48,7 @@ struct SweepArgs {
     const double* sigma_s;
     const double* q;
     const double* phi;              // scattering source (nodal), may be null (= 0)
-    const double* src_scale;        // unused (reserved)
+    const double* mass;             // ne x n collocated masses W_i det J(x_i)
     void* psi;                      // nd x ne x n, float64 or float32
     const int2* items;              // (dir, elem) sorted by level
     double q_scale;                 // multiplies q (1 normally, 0 for homogeneous solves)
@@ -101,15 +101,22 @@ struct sn_mesh {
     void* d_psi = nullptr;          // forward angular fluxes (float64 storage)
     void* d_psi32 = nullptr;        // float32 angular fluxes of the FP32 form
     double* d_lambda = nullptr;     // adjoint angular fluxes
+    double* d_mass = nullptr;       // ne x n collocated masses
     double* d_work = nullptr;       // 4 x ne x n scratch vectors for iterations
     double* d_red = nullptr;        // reduction partials
     int red_blocks = 0;
     double* d_scalars = nullptr;    // small device scalars
     sn::LevelSets levels;
-    int schedule = sn::SCHED_DATAFLOW;  // sweep schedule (see sn_mesh_set_schedule)
+    int schedule = sn::SCHED_LEVELS;    // sweep schedule (see sn_mesh_set_schedule)
     int block = 128;                    // threads per block of the sweep kernels
     int max_blocks_per_sm = 0;          // 0: occupancy limit
+    double* d_src = nullptr;            // ne x n source vector read by the graph-captured level launches
+    cudaGraphExec_t level_graph[7] = {};  // level-schedule sweeps: FP64, FP32, refine, adjoint, and the
+                                          // three forward kinds without the fixed source
+    cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
     sn::DsaHierarchy* dsa = nullptr;
+    double* d_krylov = nullptr;     // flexible GMRES workspace (basis, preconditioned basis, scratch)
+    int krylov_restart = 0;
     int dsa_key_dsa = -1, dsa_key_rule = -1, dsa_key_sigma = -1;
     double dsa_key_eta = 0;
     std::vector<unsigned char> dsa_key_mask;
@@ -120,6 +127,8 @@ namespace sn {
 sn_status set_error(sn_status st, const char* msg);
 // sn_sweep.cu
 cudaError_t build_levels(sn_mesh* m, cudaStream_t s, bool* cycle);
+cudaError_t compute_mass(sn_mesh* m, cudaStream_t s);
+void drop_level_graphs(sn_mesh* m);
 cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double q_scale, cudaStream_t s);
 cudaError_t launch_adjoint_sweep(sn_mesh* m, const double* mu, cudaStream_t s);
 cudaError_t launch_phi_reduce(sn_mesh* m, int precision, const double* phi_in, double* phi_out, double* d_rr,
@@ -133,6 +142,13 @@ cudaError_t launch_copy(double* dst, const double* src, size_t n, cudaStream_t s
 cudaError_t take_sweep_error(sn_mesh* m, cudaStream_t s, bool* timed_out);
 cudaError_t launch_axpy_add(double* y, const double* x, size_t n, cudaStream_t s);  // y += x
 cudaError_t launch_widen(double* y, const float* x, size_t n, cudaStream_t s);
+// sn_krylov.cu
+int krylov_blocks(long long n);
+cudaError_t launch_multidot(const double* V, int k, long long n, const double* w, double* partial, double* h,
+                            cudaStream_t s);
+cudaError_t launch_multiaxpy(const double* V, int k, long long n, const double* c, double sign, double* w,
+                             cudaStream_t s);
+cudaError_t launch_normalize(const double* x, long long n, double* partial, double* s, double* y, cudaStream_t st);
 // sn_dsa.cu
 DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sigma, std::string& err);
 void dsa_free(DsaHierarchy* h);

@@ -31,10 +31,18 @@ __constant__ double c_w[kMaxP + 1][kMaxP + 1];
 __constant__ double c_lm[kMaxP + 1][kMaxP + 1];
 __constant__ double c_lp[kMaxP + 1][kMaxP + 1];
 __constant__ double c_dm[kMaxP + 1][kMaxP + 1][kMaxP + 1];
+__constant__ double c_wdm[kMaxP + 1][kMaxP + 1][kMaxP + 1];  // w_a * l_k'(x_a)
+__constant__ float c_wf[kMaxP + 1][kMaxP + 1];
+__constant__ float c_lmf[kMaxP + 1][kMaxP + 1];
+__constant__ float c_lpf[kMaxP + 1][kMaxP + 1];
+__constant__ float c_wdmf[kMaxP + 1][kMaxP + 1][kMaxP + 1];
 
 cudaError_t upload_gl_constants() {
     double x[kMaxP + 1][kMaxP + 1] = {}, w[kMaxP + 1][kMaxP + 1] = {}, lm[kMaxP + 1][kMaxP + 1] = {},
-           lp[kMaxP + 1][kMaxP + 1] = {}, dm[kMaxP + 1][kMaxP + 1][kMaxP + 1] = {};
+           lp[kMaxP + 1][kMaxP + 1] = {}, dm[kMaxP + 1][kMaxP + 1][kMaxP + 1] = {},
+           wdm[kMaxP + 1][kMaxP + 1][kMaxP + 1] = {};
+    float wf[kMaxP + 1][kMaxP + 1] = {}, lmf[kMaxP + 1][kMaxP + 1] = {}, lpf[kMaxP + 1][kMaxP + 1] = {},
+          wdmf[kMaxP + 1][kMaxP + 1][kMaxP + 1] = {};
     for (int p = 1; p <= kMaxP; ++p) {
         GL1D g = gauss_legendre_nodal(p);
         for (int k = 0; k <= p; ++k) {
@@ -42,7 +50,14 @@ cudaError_t upload_gl_constants() {
             w[p][k] = g.w[k];
             lm[p][k] = g.lm[k];
             lp[p][k] = g.lp[k];
-            for (int a = 0; a <= p; ++a) dm[p][a][k] = g.dm[a][k];
+            wf[p][k] = (float)g.w[k];
+            lmf[p][k] = (float)g.lm[k];
+            lpf[p][k] = (float)g.lp[k];
+            for (int a = 0; a <= p; ++a) {
+                dm[p][a][k] = g.dm[a][k];
+                wdm[p][a][k] = g.w[a] * g.dm[a][k];
+                wdmf[p][a][k] = (float)(g.w[a] * g.dm[a][k]);
+            }
         }
     }
     cudaError_t err;
@@ -50,8 +65,31 @@ cudaError_t upload_gl_constants() {
     if ((err = cudaMemcpyToSymbol(c_w, w, sizeof(w))) != cudaSuccess) return err;
     if ((err = cudaMemcpyToSymbol(c_lm, lm, sizeof(lm))) != cudaSuccess) return err;
     if ((err = cudaMemcpyToSymbol(c_lp, lp, sizeof(lp))) != cudaSuccess) return err;
-    return cudaMemcpyToSymbol(c_dm, dm, sizeof(dm));
+    if ((err = cudaMemcpyToSymbol(c_dm, dm, sizeof(dm))) != cudaSuccess) return err;
+    if ((err = cudaMemcpyToSymbol(c_wdm, wdm, sizeof(wdm))) != cudaSuccess) return err;
+    if ((err = cudaMemcpyToSymbol(c_wf, wf, sizeof(wf))) != cudaSuccess) return err;
+    if ((err = cudaMemcpyToSymbol(c_lmf, lmf, sizeof(lmf))) != cudaSuccess) return err;
+    if ((err = cudaMemcpyToSymbol(c_lpf, lpf, sizeof(lpf))) != cudaSuccess) return err;
+    return cudaMemcpyToSymbol(c_wdmf, wdmf, sizeof(wdmf));
 }
+
+// Gauss-Legendre tables in the arithmetic type of a kernel.
+template <typename R>
+struct GLT;
+template <>
+struct GLT<double> {
+    static __device__ __forceinline__ double w(int p, int k) { return c_w[p][k]; }
+    static __device__ __forceinline__ double lm(int p, int k) { return c_lm[p][k]; }
+    static __device__ __forceinline__ double lp(int p, int k) { return c_lp[p][k]; }
+    static __device__ __forceinline__ double wdm(int p, int a, int k) { return c_wdm[p][a][k]; }
+};
+template <>
+struct GLT<float> {
+    static __device__ __forceinline__ float w(int p, int k) { return c_wf[p][k]; }
+    static __device__ __forceinline__ float lm(int p, int k) { return c_lmf[p][k]; }
+    static __device__ __forceinline__ float lp(int p, int k) { return c_lpf[p][k]; }
+    static __device__ __forceinline__ float wdm(int p, int a, int k) { return c_wdmf[p][a][k]; }
+};
 
 template <int DIM, int P>
 struct Shape {
@@ -71,18 +109,21 @@ __device__ __forceinline__ int node_of(int a, int ia, int t) {
     return t0 + Q * (t1 + Q * ia);
 }
 
-template <int DIM, int P>
-__device__ __forceinline__ double wtan(int t) {
+template <int DIM, int P, typename R = double>
+__device__ __forceinline__ R wtan(int t) {
     constexpr int Q = P + 1;
-    return DIM == 2 ? c_w[P][t] : c_w[P][t % Q] * c_w[P][t / Q];
+    return DIM == 2 ? GLT<R>::w(P, t) : GLT<R>::w(P, t % Q) * GLT<R>::w(P, t / Q);
 }
 
-// Geometry of one element for one direction: face flux factors, b at the nodes and det J.
-template <int DIM, int P>
+// Geometry of one element for one direction, in arithmetic type R: face flux factors (the
+// float64 value Fd decides inflow/outflow for every precision), b at the nodes and the
+// collocated masses W_i det J(x_i) (precomputed per element in float64).
+template <int DIM, int P, typename R>
 struct ElemGeom {
-    double F[2 * DIM];
-    double b[DIM][P + 1];  // 2D: b[0][a] = b_1(x_a), b[1][a] = b_2(x_a); 3D: constant per axis
-    double detJ[Shape<DIM, P>::N];
+    double Fd[2 * DIM];
+    R F[2 * DIM];
+    R b[DIM][P + 1];  // 2D: b[0][a] = b_1(x_a), b[1][a] = b_2(x_a); 3D: constant per axis
+    R mass[Shape<DIM, P>::N];
 };
 
 // Face flux factor of a 2D face from the half edge vector (ex, ey), rounded without FMA
@@ -102,55 +143,88 @@ __device__ __forceinline__ double face_flux_2d(const double* v, int f, double Ox
     }
 }
 
-template <int DIM, int P>
+template <int DIM, int P, typename R>
 __device__ __forceinline__ void elem_geom(const SweepArgs& a, int e, double Ox, double Oy, double Oz,
-                                          ElemGeom<DIM, P>& g) {
-    constexpr int Q = P + 1;
+                                          ElemGeom<DIM, P, R>& g) {
+    constexpr int Q = P + 1, N = Shape<DIM, P>::N;
     if constexpr (DIM == 2) {
-        const double* v = a.corners + 8 * (size_t)e;  // x00 y00 x10 y10 x01 y01 x11 y11
+        const double* v = a.corners + 8 * (size_t)e;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            g.Fd[f] = face_flux_2d(v, f, Ox, Oy);
+            g.F[f] = (R)g.Fd[f];
+        }
+        // b_1(xi) interpolates Omega x (dx/deta) between the left and right edges, b_2(eta) likewise
+        const R cl = -g.F[0], cr = g.F[1], cb = g.F[2], ct = -g.F[3];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const R t = (R)c_x[P][k];
+            g.b[0][k] = R(0.5) * (R(1) - t) * cl + R(0.5) * (R(1) + t) * cr;
+            g.b[1][k] = -(R(0.5) * (R(1) - t) * cb + R(0.5) * (R(1) + t) * ct);
+        }
+    } else {
+        const double bx = 0.25 * Ox * a.hy * a.hz, by = 0.25 * Oy * a.hx * a.hz, bz = 0.25 * Oz * a.hx * a.hy;
+        g.Fd[0] = -bx;
+        g.Fd[1] = bx;
+        g.Fd[2] = -by;
+        g.Fd[3] = by;
+        g.Fd[4] = -bz;
+        g.Fd[5] = bz;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) g.F[f] = (R)g.Fd[f];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            g.b[0][k] = (R)bx;
+            g.b[1][k] = (R)by;
+            g.b[2][k] = (R)bz;
+        }
+    }
+    const double* ms = a.mass + (size_t)e * N;
+#pragma unroll
+    for (int i = 0; i < N; ++i) g.mass[i] = (R)ms[i];
+}
+
+template <int DIM, int P>
+__device__ __forceinline__ void narrow_geom(const ElemGeom<DIM, P, double>& gd, ElemGeom<DIM, P, float>& gf) {
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f) {
+        gf.Fd[f] = gd.Fd[f];
+        gf.F[f] = (float)gd.F[f];
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+        for (int k = 0; k <= P; ++k) gf.b[a][k] = (float)gd.b[a][k];
+#pragma unroll
+    for (int i = 0; i < Shape<DIM, P>::N; ++i) gf.mass[i] = (float)gd.mass[i];
+}
+
+// Collocated masses W_i det J(x_i) of every element (float64, once per mesh).
+template <int DIM, int P>
+__global__ void mass_kernel(SweepArgs a, double* mass) {
+    constexpr int Q = P + 1, N = Shape<DIM, P>::N;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)a.ne * N) return;
+    const int e = (int)(idx / N), i = (int)(idx % N);
+    const int i0 = i % Q, i1 = (i / Q) % Q, i2 = i / (Q * Q);
+    const double W = c_w[P][i0] * c_w[P][i1] * (DIM == 3 ? c_w[P][i2] : 1.0);
+    double dj;
+    if constexpr (DIM == 2) {
+        const double* v = a.corners + 8 * (size_t)e;
         const double ebx = 0.5 * (v[2] - v[0]), eby = 0.5 * (v[3] - v[1]);
         const double etx = 0.5 * (v[6] - v[4]), ety = 0.5 * (v[7] - v[5]);
         const double elx = 0.5 * (v[4] - v[0]), ely = 0.5 * (v[5] - v[1]);
         const double erx = 0.5 * (v[6] - v[2]), ery = 0.5 * (v[7] - v[3]);
-#pragma unroll
-        for (int f = 0; f < 4; ++f) g.F[f] = face_flux_2d(v, f, Ox, Oy);
-        // b_1(xi) interpolates Omega x (dx/deta) between the left and right edges, b_2(eta) likewise
-        const double cl = -g.F[0], cr = g.F[1], cb = g.F[2], ct = -g.F[3];
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            const double t = c_x[P][k];
-            g.b[0][k] = 0.5 * (1.0 - t) * cl + 0.5 * (1.0 + t) * cr;
-            g.b[1][k] = -(0.5 * (1.0 - t) * cb + 0.5 * (1.0 + t) * ct);
-        }
-#pragma unroll
-        for (int j1 = 0; j1 < Q; ++j1)
-#pragma unroll
-            for (int j0 = 0; j0 < Q; ++j0) {
-                const double xi = c_x[P][j0], eta = c_x[P][j1];
-                const double xx = 0.5 * (1.0 - eta) * ebx + 0.5 * (1.0 + eta) * etx;  // dx/dxi
-                const double xy = 0.5 * (1.0 - eta) * eby + 0.5 * (1.0 + eta) * ety;
-                const double yx = 0.5 * (1.0 - xi) * elx + 0.5 * (1.0 + xi) * erx;    // dx/deta
-                const double yy = 0.5 * (1.0 - xi) * ely + 0.5 * (1.0 + xi) * ery;
-                g.detJ[j0 + Q * j1] = xx * yy - yx * xy;
-            }
+        const double xi = c_x[P][i0], eta = c_x[P][i1];
+        const double xx = 0.5 * (1.0 - eta) * ebx + 0.5 * (1.0 + eta) * etx;  // dx/dxi
+        const double xy = 0.5 * (1.0 - eta) * eby + 0.5 * (1.0 + eta) * ety;
+        const double yx = 0.5 * (1.0 - xi) * elx + 0.5 * (1.0 + xi) * erx;    // dx/deta
+        const double yy = 0.5 * (1.0 - xi) * ely + 0.5 * (1.0 + xi) * ery;
+        dj = xx * yy - yx * xy;
     } else {
-        const double bx = 0.25 * Ox * a.hy * a.hz, by = 0.25 * Oy * a.hx * a.hz, bz = 0.25 * Oz * a.hx * a.hy;
-        g.F[0] = -bx;
-        g.F[1] = bx;
-        g.F[2] = -by;
-        g.F[3] = by;
-        g.F[4] = -bz;
-        g.F[5] = bz;
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            g.b[0][k] = bx;
-            g.b[1][k] = by;
-            g.b[2][k] = bz;
-        }
-        const double dj = 0.125 * a.hx * a.hy * a.hz;
-#pragma unroll
-        for (int i = 0; i < Shape<DIM, P>::N; ++i) g.detJ[i] = dj;
+        dj = 0.125 * a.hx * a.hy * a.hz;
     }
+    mass[idx] = W * dj;
 }
 
 template <int DIM, int P>
@@ -183,93 +257,88 @@ __device__ __forceinline__ double face_flux_only(const SweepArgs& a, int e, int 
     }
 }
 
-// A_e in precision R (volume + outflow faces).
+// A_e in arithmetic type R (volume + outflow faces); every entry is one FMA on table values.
 template <int DIM, int P, typename R>
-__device__ __forceinline__ void assemble(const ElemGeom<DIM, P>& g, double st, R* A) {
+__device__ __forceinline__ void assemble(const ElemGeom<DIM, P, R>& g, R st, R* A) {
     constexpr int Q = P + 1, N = Shape<DIM, P>::N, NT = Shape<DIM, P>::NT;
+    using K = GLT<R>;
 #pragma unroll
     for (int i = 0; i < N * N; ++i) A[i] = R(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         const int j0 = j % Q, j1 = (j / Q) % Q, j2 = j / (Q * Q);
-        const double Wj = c_w[P][j0] * c_w[P][j1] * (DIM == 3 ? c_w[P][j2] : 1.0);
-        A[j * N + j] += R(st * Wj * g.detJ[j]);
-        // axis 0: nodes i differing from j only in index 0
+        const R w0 = K::w(P, j0), w1 = K::w(P, j1), w2 = DIM == 3 ? K::w(P, j2) : R(1);
+        A[j * N + j] += st * g.mass[j];
+        // -W_j b(x_j) . grad_ref l_i(x_j): nodes i on the coordinate lines through j
+        const R u0 = w1 * w2 * g.b[0][j0];
 #pragma unroll
-        for (int ia = 0; ia < Q; ++ia) {
-            const int i = ia + Q * (j1 + Q * j2);
-            A[i * N + j] -= R(Wj * g.b[0][j0] * c_dm[P][j0][ia]);
-        }
+        for (int ia = 0; ia < Q; ++ia) A[(ia + Q * (j1 + Q * j2)) * N + j] -= u0 * K::wdm(P, j0, ia);
+        const R u1 = w0 * w2 * g.b[1][j1];
 #pragma unroll
-        for (int ia = 0; ia < Q; ++ia) {
-            const int i = j0 + Q * (ia + Q * j2);
-            A[i * N + j] -= R(Wj * g.b[1][j1] * c_dm[P][j1][ia]);
-        }
+        for (int ia = 0; ia < Q; ++ia) A[(j0 + Q * (ia + Q * j2)) * N + j] -= u1 * K::wdm(P, j1, ia);
         if constexpr (DIM == 3) {
+            const R u2 = w0 * w1 * g.b[DIM - 1][j2];
 #pragma unroll
-            for (int ia = 0; ia < Q; ++ia) {
-                const int i = j0 + Q * (j1 + Q * ia);
-                A[i * N + j] -= R(Wj * g.b[DIM - 1][j2] * c_dm[P][j2][ia]);
-            }
+            for (int ia = 0; ia < Q; ++ia) A[(j0 + Q * (j1 + Q * ia)) * N + j] -= u2 * K::wdm(P, j2, ia);
         }
     }
 #pragma unroll
     for (int f = 0; f < 2 * DIM; ++f) {
-        if (g.F[f] > 0.0) {
+        if (g.Fd[f] > 0.0) {
             const int ax = f >> 1;
             const bool hi = f & 1;
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
-                const double ft = g.F[f] * wtan<DIM, P>(t);
+                const R ft = g.F[f] * wtan<DIM, P, R>(t);
 #pragma unroll
-                for (int ia = 0; ia < Q; ++ia)
+                for (int ia = 0; ia < Q; ++ia) {
+                    const R fi = ft * (hi ? K::lp(P, ia) : K::lm(P, ia));
 #pragma unroll
-                    for (int ja = 0; ja < Q; ++ja) {
-                        const double li = hi ? c_lp[P][ia] : c_lm[P][ia];
-                        const double lj = hi ? c_lp[P][ja] : c_lm[P][ja];
-                        A[node_of<DIM, P>(ax, ia, t) * N + node_of<DIM, P>(ax, ja, t)] += R(ft * li * lj);
-                    }
+                    for (int ja = 0; ja < Q; ++ja)
+                        A[node_of<DIM, P>(ax, ia, t) * N + node_of<DIM, P>(ax, ja, t)] += fi * (hi ? K::lp(P, ja) : K::lm(P, ja));
+                }
             }
         }
     }
 }
 
-// y = A_e x, matrix free, in float64 (used by the refinement step).
+// y = A_e x, matrix free, in float64 (the residual of the refinement step).
 template <int DIM, int P>
-__device__ __forceinline__ void apply_A(const ElemGeom<DIM, P>& g, double st, const double* x, double* y) {
+__device__ __forceinline__ void apply_A(const ElemGeom<DIM, P, double>& g, double st, const double* x, double* y) {
     constexpr int Q = P + 1, N = Shape<DIM, P>::N, NT = Shape<DIM, P>::NT;
+    using K = GLT<double>;
 #pragma unroll
     for (int i = 0; i < N; ++i) y[i] = 0.0;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         const int j0 = j % Q, j1 = (j / Q) % Q, j2 = j / (Q * Q);
-        const double Wj = c_w[P][j0] * c_w[P][j1] * (DIM == 3 ? c_w[P][j2] : 1.0);
+        const double w0 = K::w(P, j0), w1 = K::w(P, j1), w2 = DIM == 3 ? K::w(P, j2) : 1.0;
         const double xj = x[j];
-        y[j] += st * Wj * g.detJ[j] * xj;
-        const double u0 = Wj * g.b[0][j0] * xj, u1 = Wj * g.b[1][j1] * xj;
+        y[j] += st * g.mass[j] * xj;
+        const double u0 = w1 * w2 * g.b[0][j0] * xj, u1 = w0 * w2 * g.b[1][j1] * xj;
 #pragma unroll
-        for (int ia = 0; ia < Q; ++ia) y[ia + Q * (j1 + Q * j2)] -= u0 * c_dm[P][j0][ia];
+        for (int ia = 0; ia < Q; ++ia) y[ia + Q * (j1 + Q * j2)] -= u0 * K::wdm(P, j0, ia);
 #pragma unroll
-        for (int ia = 0; ia < Q; ++ia) y[j0 + Q * (ia + Q * j2)] -= u1 * c_dm[P][j1][ia];
+        for (int ia = 0; ia < Q; ++ia) y[j0 + Q * (ia + Q * j2)] -= u1 * K::wdm(P, j1, ia);
         if constexpr (DIM == 3) {
-            const double u2 = Wj * g.b[DIM - 1][j2] * xj;
+            const double u2 = w0 * w1 * g.b[DIM - 1][j2] * xj;
 #pragma unroll
-            for (int ia = 0; ia < Q; ++ia) y[j0 + Q * (j1 + Q * ia)] -= u2 * c_dm[P][j2][ia];
+            for (int ia = 0; ia < Q; ++ia) y[j0 + Q * (j1 + Q * ia)] -= u2 * K::wdm(P, j2, ia);
         }
     }
 #pragma unroll
     for (int f = 0; f < 2 * DIM; ++f) {
-        if (g.F[f] > 0.0) {
+        if (g.Fd[f] > 0.0) {
             const int ax = f >> 1;
             const bool hi = f & 1;
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
                 double tr = 0.0;
 #pragma unroll
-                for (int ja = 0; ja < Q; ++ja) tr += (hi ? c_lp[P][ja] : c_lm[P][ja]) * x[node_of<DIM, P>(ax, ja, t)];
-                const double ft = g.F[f] * wtan<DIM, P>(t) * tr;
+                for (int ja = 0; ja < Q; ++ja) tr += (hi ? K::lp(P, ja) : K::lm(P, ja)) * x[node_of<DIM, P>(ax, ja, t)];
+                const double ft = g.F[f] * wtan<DIM, P, double>(t) * tr;
 #pragma unroll
-                for (int ia = 0; ia < Q; ++ia) y[node_of<DIM, P>(ax, ia, t)] += ft * (hi ? c_lp[P][ia] : c_lm[P][ia]);
+                for (int ia = 0; ia < Q; ++ia) y[node_of<DIM, P>(ax, ia, t)] += ft * (hi ? K::lp(P, ia) : K::lm(P, ia));
             }
         }
     }
@@ -365,125 +434,78 @@ __device__ __forceinline__ void lu_solve_transpose_s(const R* A, R* x) {
             if ((pat.rows[k] >> i) & 1u) x[i] -= A[k * N + i] * x[k];
 }
 
-template <int N, typename R>
-__device__ __forceinline__ void lu_factor(R* A) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        const R inv = R(1) / A[k * N + k];
-        A[k * N + k] = inv;
-#pragma unroll
-        for (int i = k + 1; i < N; ++i) {
-            const R l = A[i * N + k] * inv;
-            A[i * N + k] = l;
-#pragma unroll
-            for (int j = k + 1; j < N; ++j) A[i * N + j] -= l * A[k * N + j];
-        }
-    }
-}
-
-// Solve (LU) x = b in place; the diagonal holds 1/U_kk.
-template <int N, typename R>
-__device__ __forceinline__ void lu_solve(const R* A, R* x) {
-#pragma unroll
-    for (int i = 1; i < N; ++i)
-#pragma unroll
-        for (int k = 0; k < i; ++k) x[i] -= A[i * N + k] * x[k];
-#pragma unroll
-    for (int i = N - 1; i >= 0; --i) {
-#pragma unroll
-        for (int k = i + 1; k < N; ++k) x[i] -= A[i * N + k] * x[k];
-        x[i] *= A[i * N + i];
-    }
-}
-
-// Solve (LU)^T x = b in place: U^T y = b (forward), then L^T x = y (backward).
-template <int N, typename R>
-__device__ __forceinline__ void lu_solve_transpose(const R* A, R* x) {
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-#pragma unroll
-        for (int k = 0; k < i; ++k) x[i] -= A[k * N + i] * x[k];
-        x[i] *= A[i * N + i];
-    }
-#pragma unroll
-    for (int i = N - 1; i >= 0; --i)
-#pragma unroll
-        for (int k = i + 1; k < N; ++k) x[i] -= A[k * N + i] * x[k];
-}
-
-// Right-hand side: mass-weighted source + inflow face terms from upwind traces (float64).
-template <int DIM, int P, typename RS>
-__device__ __forceinline__ void assemble_rhs(const SweepArgs& a, const ElemGeom<DIM, P>& g, int d, int e,
-                                             double* rhs) {
+// Right-hand side in arithmetic type R: mass-weighted source S = (q + sigma_s phi)/(4 pi) (formed in
+// float64, then rounded to R) plus inflow face terms from the upwind neighbours' traces.
+template <int DIM, int P, typename RS, typename R>
+__device__ __forceinline__ void assemble_rhs(const SweepArgs& a, const ElemGeom<DIM, P, R>& g, int d, int e, R* rhs) {
     constexpr int Q = P + 1, N = Shape<DIM, P>::N, NT = Shape<DIM, P>::NT;
+    using K = GLT<R>;
     const double ss = a.sigma_s[e], qe = a.q[e] * a.q_scale;
     const double* phi = a.phi ? a.phi + (size_t)e * N : nullptr;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        const int i0 = i % Q, i1 = (i / Q) % Q, i2 = i / (Q * Q);
-        const double Wi = c_w[P][i0] * c_w[P][i1] * (DIM == 3 ? c_w[P][i2] : 1.0);
         const double S = (qe + (phi ? ss * phi[i] : 0.0)) * (1.0 / kFourPi);
-        rhs[i] = Wi * g.detJ[i] * S;
+        rhs[i] = g.mass[i] * (R)S;
     }
     const RS* psi = static_cast<const RS*>(a.psi);
 #pragma unroll
     for (int f = 0; f < 2 * DIM; ++f) {
-        if (g.F[f] < 0.0) {
+        if (g.Fd[f] < 0.0) {
             const int ax = f >> 1;
             const bool hi = f & 1;
             const int u = neighbor<DIM, P>(a, e, f);
-            double tr[NT];
+            R tr[NT];
             if (u >= 0) {
                 const RS* pu = psi + ((size_t)d * a.ne + u) * N;
-                RS vals[N];
+                R vals[N];
 #pragma unroll
-                for (int i = 0; i < N; ++i) vals[i] = __ldcg(pu + i);
+                for (int i = 0; i < N; ++i) vals[i] = (R)__ldcg(pu + i);
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
-                    double s = 0.0;
+                    R s = R(0);
 #pragma unroll
-                    for (int k = 0; k < Q; ++k)
-                        s += (hi ? c_lm[P][k] : c_lp[P][k]) * (double)vals[node_of<DIM, P>(ax, k, t)];
+                    for (int k = 0; k < Q; ++k) s += (hi ? K::lm(P, k) : K::lp(P, k)) * vals[node_of<DIM, P>(ax, k, t)];
                     tr[t] = s;
                 }
             } else {
 #pragma unroll
-                for (int t = 0; t < NT; ++t) tr[t] = a.psi_inc;
+                for (int t = 0; t < NT; ++t) tr[t] = (R)a.psi_inc;
             }
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
-                const double ft = -g.F[f] * wtan<DIM, P>(t) * tr[t];
+                const R ft = -g.F[f] * wtan<DIM, P, R>(t) * tr[t];
 #pragma unroll
-                for (int ia = 0; ia < Q; ++ia) rhs[node_of<DIM, P>(ax, ia, t)] += ft * (hi ? c_lp[P][ia] : c_lm[P][ia]);
+                for (int ia = 0; ia < Q; ++ia) rhs[node_of<DIM, P>(ax, ia, t)] += ft * (hi ? K::lp(P, ia) : K::lm(P, ia));
             }
         }
     }
 }
 
-// MODE 0: float64 solve, float64 storage.  MODE 1: float32 solve and storage.
-// MODE 2: float32 LU + two float64 residual corrections, float64 storage.
+// MODE 0: float64 element solve and storage.  MODE 1: float32 geometry, assembly, LU and
+// storage (source formed in float64 and rounded).  MODE 2: float32 assembly and LU, then two
+// float64 residual corrections x += LU^{-1}(b - A x) with A applied matrix-free in float64;
+// float64 storage.
 template <int DIM, int P, int MODE>
 __device__ __forceinline__ void solve_item(const SweepArgs& a, int d, int e) {
     constexpr int N = Shape<DIM, P>::N;
     const double Ox = a.dirs[3 * d], Oy = a.dirs[3 * d + 1], Oz = a.dirs[3 * d + 2];
-    ElemGeom<DIM, P> g;
-    elem_geom<DIM, P>(a, e, Ox, Oy, Oz, g);
     const double st = a.sigma_t[e];
-    double rhs[N];
-    if (MODE == 1) {
-        assemble_rhs<DIM, P, float>(a, g, d, e, rhs);
-        float A[N * N], x[N];
-        assemble<DIM, P, float>(g, st, A);
-#pragma unroll
-        for (int i = 0; i < N; ++i) x[i] = (float)rhs[i];
+    if constexpr (MODE == 1) {
+        ElemGeom<DIM, P, float> g;
+        elem_geom<DIM, P, float>(a, e, Ox, Oy, Oz, g);
+        float rhs[N], A[N * N];
+        assemble_rhs<DIM, P, float, float>(a, g, d, e, rhs);
+        assemble<DIM, P, float>(g, (float)st, A);
         lu_factor_s<DIM, P, float>(A);
-        lu_solve_s<DIM, P, float>(A, x);
+        lu_solve_s<DIM, P, float>(A, rhs);
         float* out = static_cast<float*>(a.psi) + ((size_t)d * a.ne + e) * N;
 #pragma unroll
-        for (int i = 0; i < N; ++i) out[i] = x[i];
-    } else if (MODE == 0) {
-        assemble_rhs<DIM, P, double>(a, g, d, e, rhs);
-        double A[N * N];
+        for (int i = 0; i < N; ++i) out[i] = rhs[i];
+    } else if constexpr (MODE == 0) {
+        ElemGeom<DIM, P, double> g;
+        elem_geom<DIM, P, double>(a, e, Ox, Oy, Oz, g);
+        double rhs[N], A[N * N];
+        assemble_rhs<DIM, P, double, double>(a, g, d, e, rhs);
         assemble<DIM, P, double>(g, st, A);
         lu_factor_s<DIM, P, double>(A);
         lu_solve_s<DIM, P, double>(A, rhs);
@@ -491,11 +513,16 @@ __device__ __forceinline__ void solve_item(const SweepArgs& a, int d, int e) {
 #pragma unroll
         for (int i = 0; i < N; ++i) out[i] = rhs[i];
     } else {
-        assemble_rhs<DIM, P, double>(a, g, d, e, rhs);
-        float A[N * N];
-        float c[N];
-        double x[N], r[N];
-        assemble<DIM, P, float>(g, st, A);
+        ElemGeom<DIM, P, double> gd;
+        elem_geom<DIM, P, double>(a, e, Ox, Oy, Oz, gd);
+        double rhs[N], x[N], r[N];
+        assemble_rhs<DIM, P, double, double>(a, gd, d, e, rhs);
+        float A[N * N], c[N];
+        {
+            ElemGeom<DIM, P, float> gf;
+            narrow_geom<DIM, P>(gd, gf);
+            assemble<DIM, P, float>(gf, (float)st, A);
+        }
         lu_factor_s<DIM, P, float>(A);
 #pragma unroll
         for (int i = 0; i < N; ++i) c[i] = (float)rhs[i];
@@ -504,7 +531,7 @@ __device__ __forceinline__ void solve_item(const SweepArgs& a, int d, int e) {
         for (int i = 0; i < N; ++i) x[i] = c[i];
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
-            apply_A<DIM, P>(g, st, x, r);
+            apply_A<DIM, P>(gd, st, x, r);
 #pragma unroll
             for (int i = 0; i < N; ++i) c[i] = (float)(rhs[i] - r[i]);
             lu_solve_s<DIM, P, float>(A, c);
@@ -558,11 +585,16 @@ __global__ void __launch_bounds__(128) sweep_dataflow_kernel(SweepArgs a, Datafl
     const long long n_chunks = f.n_items >> 5;
     const unsigned long long deadline = globaltimer() + f.timeout_ns;
     while (true) {
+        // lane 0 claims the chunk and reads the error word; the warp acts on one broadcast value
         unsigned long long c = 0;
-        if (lane == 0) c = atomicAdd(f.next, 1ull);
+        int failed = 0;
+        if (lane == 0) {
+            c = atomicAdd(f.next, 1ull);
+            failed = *(volatile int*)f.error;
+        }
         c = __shfl_sync(0xffffffffu, c, 0);
-        if ((long long)c >= n_chunks) break;
-        if (*(volatile int*)f.error) break;
+        failed = __shfl_sync(0xffffffffu, failed, 0);
+        if ((long long)c >= n_chunks || failed) break;
         const int2 it = f.items[(c << 5) + lane];
         bool ok = true;
         if (it.x >= 0) {
@@ -576,26 +608,28 @@ __global__ void __launch_bounds__(128) sweep_dataflow_kernel(SweepArgs a, Datafl
                     const int u = neighbor<DIM, P>(a, e, fc);
                     if (u < 0) continue;
                     const int* flag = f.done + (size_t)d * a.ne + u;
-                    unsigned ns = 32;
+                    int polls = 0;
                     while (ld_acquire(flag) != f.epoch) {
-                        if (globaltimer() > deadline) {
-                            ok = false;
-                            break;
+                        if (++polls > 64) {  // spin briefly, then back off and watch the deadline
+                            if (globaltimer() > deadline) {
+                                ok = false;
+                                break;
+                            }
+                            __nanosleep(64);
                         }
-                        __nanosleep(ns);
-                        ns = ns < 1024 ? 2 * ns : 1024;
                     }
                 }
             }
-            if (ok) {
-                if constexpr (ADJ) adjoint_item<DIM, P>(a, mu, d, e);
-                else solve_item<DIM, P, MODE>(a, d, e);
-                st_release(f.done + (size_t)d * a.ne + e, f.publish);
-            }
         }
+        // reconverge before the solve so the warp issues the element solve once for all its lanes
         if (!__all_sync(0xffffffffu, ok)) {
             if (lane == 0) atomicExch(f.error, 1);
             break;
+        }
+        if (it.x >= 0) {
+            if constexpr (ADJ) adjoint_item<DIM, P>(a, mu, it.x, it.y);
+            else solve_item<DIM, P, MODE>(a, it.x, it.y);
+            st_release(f.done + (size_t)it.x * a.ne + it.y, f.publish);
         }
     }
 }
@@ -605,15 +639,15 @@ template <int DIM, int P>
 __device__ __forceinline__ void adjoint_item(const SweepArgs& a, const double* mu, int d, int e) {
     constexpr int Q = P + 1, N = Shape<DIM, P>::N, NT = Shape<DIM, P>::NT;
     const double Ox = a.dirs[3 * d], Oy = a.dirs[3 * d + 1], Oz = a.dirs[3 * d + 2];
-    ElemGeom<DIM, P> g;
-    elem_geom<DIM, P>(a, e, Ox, Oy, Oz, g);
+    ElemGeom<DIM, P, double> g;
+    elem_geom<DIM, P, double>(a, e, Ox, Oy, Oz, g);
     double rhs[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) rhs[i] = mu[(size_t)e * N + i];
     const double* lam = static_cast<const double*>(a.psi);
 #pragma unroll
     for (int f = 0; f < 2 * DIM; ++f) {
-        if (g.F[f] > 0.0) {
+        if (g.Fd[f] > 0.0) {
             const int u = neighbor<DIM, P>(a, e, f);
             if (u < 0) continue;
             const int ax = f >> 1;
@@ -627,7 +661,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs& a, const double* m
                 double s = 0.0;
 #pragma unroll
                 for (int k = 0; k < Q; ++k) s += (hi ? c_lm[P][k] : c_lp[P][k]) * vals[node_of<DIM, P>(ax, k, tt)];
-                const double ft = g.F[f] * wtan<DIM, P>(tt) * s;
+                const double ft = g.F[f] * wtan<DIM, P, double>(tt) * s;
 #pragma unroll
                 for (int ja = 0; ja < Q; ++ja) rhs[node_of<DIM, P>(ax, ja, tt)] += ft * (hi ? c_lp[P][ja] : c_lm[P][ja]);
             }
@@ -756,11 +790,7 @@ __global__ void adjoint_reduce_kernel(SweepArgs a, const double* lam, const doub
     const int e = (int)(idx / N), i = (int)(idx % N);
     double s = 0.0;
     for (int d = 0; d < a.nd; ++d) s += w[d] * lam[(size_t)d * M + idx];
-    ElemGeom<DIM, P> g;
-    elem_geom<DIM, P>(a, e, 1.0, 0.0, 0.0, g);
-    const int i0 = i % Q, i1 = (i / Q) % Q, i2 = i / (Q * Q);
-    const double Wi = c_w[P][i0] * c_w[P][i1] * (DIM == 3 ? c_w[P][i2] : 1.0);
-    out[idx] = a.sigma_s[e] * Wi * g.detJ[i] / kFourPi * s;
+    out[idx] = a.sigma_s[e] * a.mass[idx] / kFourPi * s;
 }
 
 template <int DIM, int P>
@@ -769,14 +799,9 @@ __global__ void gradient_kernel(SweepArgs a, const double* psi, const double* la
     constexpr int Q = P + 1, N = Shape<DIM, P>::N;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= a.ne) return;
-    ElemGeom<DIM, P> g;
-    elem_geom<DIM, P>(a, e, 1.0, 0.0, 0.0, g);
     double M[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        const int i0 = i % Q, i1 = (i / Q) % Q, i2 = i / (Q * Q);
-        M[i] = c_w[P][i0] * c_w[P][i1] * (DIM == 3 ? c_w[P][i2] : 1.0) * g.detJ[i];
-    }
+    for (int i = 0; i < N; ++i) M[i] = a.mass[(size_t)e * N + i];
     double st = 0.0, ssum = 0.0, sq = 0.0;
     const size_t stride = (size_t)a.ne * N;
     for (int d = 0; d < a.nd; ++d) {
@@ -819,6 +844,7 @@ static SweepArgs make_args(const sn_mesh* m) {
     a.sigma_s = m->d_sigma_s;
     a.q = m->d_q;
     a.items = m->levels.items;
+    a.mass = m->d_mass;
     a.q_scale = 1.0;
     return a;
 }
@@ -833,6 +859,14 @@ static SweepArgs make_args(const sn_mesh* m) {
     } while (0)
 
 static inline unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+cudaError_t compute_mass(sn_mesh* m, cudaStream_t s) {
+    SweepArgs a = make_args(m);
+    const long long M = (long long)m->ne * m->n;
+    SN_COUNT_LAUNCH();
+    SN_DISPATCH(m->dim, m->p, (mass_kernel<D_, P_><<<grid_for(M, 256), 256, 0, s>>>(a, m->d_mass)));
+    return cudaGetLastError();
+}
 
 cudaError_t build_levels(sn_mesh* m, cudaStream_t s, bool* cycle) {
     *cycle = false;
@@ -974,6 +1008,69 @@ static cudaError_t launch_dataflow(sn_mesh* m, const SweepArgs& a, cudaStream_t 
     return cudaGetLastError();
 }
 
+// Level schedule: the launches of one sweep (all levels in order) are captured once into a
+// CUDA graph per kind (forward FP64 / FP32 / FP32+refinement, adjoint); the kernels read their
+// source vector from the mesh-owned buffer d_src so the captured parameters never change.
+static cudaError_t enqueue_levels(sn_mesh* m, int kind, cudaStream_t s) {
+    SweepArgs a = make_args(m);
+    a.q_scale = 1.0;
+    const int bs = m->block;
+    if (kind == 3) {
+        a.psi = m->d_lambda;
+        for (int L = m->levels.n_levels - 1; L >= 0; --L) {
+            const long long b = m->levels.level_ptr[L], e = m->levels.level_ptr[L + 1];
+            if (e <= b) continue;
+            SN_DISPATCH(m->dim, m->p, (adjoint_level_kernel<D_, P_><<<grid_for(e - b, bs), bs, 0, s>>>(a, m->d_src, b, e)));
+        }
+        return cudaGetLastError();
+    }
+    // kinds 4..6: the same sweeps without the fixed source (the linear part T of Eq. source0)
+    if (kind >= 4) {
+        a.q_scale = 0.0;
+        kind -= 4;
+    }
+    a.phi = m->d_src;
+    a.psi = kind == SN_FP32 ? m->d_psi32 : m->d_psi;
+    for (int L = 0; L < m->levels.n_levels; ++L) {
+        const long long b = m->levels.level_ptr[L], e = m->levels.level_ptr[L + 1];
+        if (e <= b) continue;
+        const unsigned g = grid_for(e - b, bs);
+        if (kind == SN_FP64) SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 0><<<g, bs, 0, s>>>(a, b, e)));
+        else if (kind == SN_FP32) SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 1><<<g, bs, 0, s>>>(a, b, e)));
+        else SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 2><<<g, bs, 0, s>>>(a, b, e)));
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_levels_graph(sn_mesh* m, int kind, cudaStream_t s) {
+    cudaError_t err;
+    if (!m->level_graph[kind]) {
+        if (!m->cap_stream && (err = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return err;
+        if ((err = cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return err;
+        cudaError_t qerr = enqueue_levels(m, kind, m->cap_stream);
+        cudaGraph_t graph = nullptr;
+        err = cudaStreamEndCapture(m->cap_stream, &graph);
+        if (qerr != cudaSuccess) err = qerr;
+        if (err == cudaSuccess) err = cudaGraphInstantiate(&m->level_graph[kind], graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (err != cudaSuccess) {
+            m->level_graph[kind] = nullptr;
+            return err;
+        }
+    }
+    g_launches.fetch_add(m->levels.n_levels, std::memory_order_relaxed);
+    return cudaGraphLaunch(m->level_graph[kind], s);
+}
+
+void drop_level_graphs(sn_mesh* m) {
+    for (auto& g : m->level_graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
 cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double q_scale, cudaStream_t s) {
     SweepArgs a = make_args(m);
     a.phi = phi_in;
@@ -985,23 +1082,11 @@ cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double
         else SN_DISPATCH(m->dim, m->p, (launch_dataflow<D_, P_, 2>(m, a, s)));
         return cudaGetLastError();
     }
-    const int bs = m->block;
-    for (int L = 0; L < m->levels.n_levels; ++L) {
-        const long long b = m->levels.level_ptr[L], e = m->levels.level_ptr[L + 1];
-        if (e <= b) continue;
-        const unsigned g = grid_for(e - b, bs);
-        if (precision == SN_FP64) {
-            SN_COUNT_LAUNCH();
-            SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 0><<<g, bs, 0, s>>>(a, b, e)));
-        } else if (precision == SN_FP32) {
-            SN_COUNT_LAUNCH();
-            SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 1><<<g, bs, 0, s>>>(a, b, e)));
-        } else {
-            SN_COUNT_LAUNCH();
-            SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 2><<<g, bs, 0, s>>>(a, b, e)));
-        }
-    }
-    return cudaGetLastError();
+    const size_t M = (size_t)m->ne * m->n;
+    cudaError_t err = phi_in ? cudaMemcpyAsync(m->d_src, phi_in, M * sizeof(double), cudaMemcpyDeviceToDevice, s)
+                             : cudaMemsetAsync(m->d_src, 0, M * sizeof(double), s);
+    if (err != cudaSuccess) return err;
+    return launch_levels_graph(m, q_scale == 0.0 ? precision + 4 : precision, s);
 }
 
 cudaError_t launch_adjoint_sweep(sn_mesh* m, const double* mu, cudaStream_t s) {
@@ -1011,14 +1096,10 @@ cudaError_t launch_adjoint_sweep(sn_mesh* m, const double* mu, cudaStream_t s) {
         SN_DISPATCH(m->dim, m->p, (launch_dataflow<D_, P_, 0, true>(m, a, s, mu)));
         return cudaGetLastError();
     }
-    const int bs = m->block;
-    for (int L = m->levels.n_levels - 1; L >= 0; --L) {
-        const long long b = m->levels.level_ptr[L], e = m->levels.level_ptr[L + 1];
-        if (e <= b) continue;
-        SN_COUNT_LAUNCH();
-        SN_DISPATCH(m->dim, m->p, (adjoint_level_kernel<D_, P_><<<grid_for(e - b, bs), bs, 0, s>>>(a, mu, b, e)));
-    }
-    return cudaGetLastError();
+    const size_t M = (size_t)m->ne * m->n;
+    cudaError_t err = cudaMemcpyAsync(m->d_src, mu, M * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (err != cudaSuccess) return err;
+    return launch_levels_graph(m, 3, s);
 }
 
 cudaError_t launch_phi_reduce(sn_mesh* m, int precision, const double* phi_in, double* phi_out, double* d_rr,

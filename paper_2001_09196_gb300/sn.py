@@ -48,13 +48,14 @@ class IterOpts(C.Structure):
                 ("mask", C.POINTER(C.c_ubyte)), ("dsa_sigma", C.c_int), ("tol", C.c_double),
                 ("inner_tol", C.c_double), ("max_iters", C.c_int), ("inner_max_iters", C.c_int),
                 ("precision", C.c_int), ("checkpoint_every", C.c_int), ("checkpoints", C.c_void_p),
-                ("max_checkpoints", C.c_int), ("warm_start", C.c_int)]
+                ("max_checkpoints", C.c_int), ("warm_start", C.c_int), ("outer", C.c_int), ("restart", C.c_int)]
 
 
 class IterStats(C.Structure):
     _fields_ = [("iters", C.c_int), ("rel_residual", C.c_double), ("inner_iters_total", C.c_int),
                 ("thick_fraction", C.c_double), ("residual_history", C.POINTER(C.c_double)),
-                ("history_len", C.c_int), ("n_checkpoints", C.c_int), ("ms_total", C.c_double)]
+                ("history_len", C.c_int), ("n_checkpoints", C.c_int), ("ms_total", C.c_double),
+                ("n_sweeps", C.c_int)]
 
 
 def _load():
@@ -128,7 +129,7 @@ def _stream(stream):
 
 def make_opts(dsa="thick", thick_rule="sigma_s", eta=1.0, mask=None, dsa_sigma="sigma_s", tol=1e-8,
               inner_tol=1e-4, max_iters=1000, inner_max_iters=200, precision="fp64", checkpoint_every=0,
-              checkpoints=None, warm_start=False):
+              checkpoints=None, warm_start=False, outer="si", restart=30):
     o = IterOpts()
     _lib.sn_iter_opts_default(C.byref(o))
     o.dsa = _DSA[dsa] if isinstance(dsa, str) else int(dsa)
@@ -149,6 +150,8 @@ def make_opts(dsa="thick", thick_rule="sigma_s", eta=1.0, mask=None, dsa_sigma="
         o.checkpoints = _ptr(checkpoints)
         o.max_checkpoints = int(checkpoints.shape[0])
     o.warm_start = int(bool(warm_start))
+    o.outer = {"si": 0, "fgmres": 1}[outer] if isinstance(outer, str) else int(outer)
+    o.restart = int(restart)
     o._keep = keep
     return o
 
@@ -257,7 +260,8 @@ class Mesh:
         status = _lib.sn_source_iterate(self._h, C.byref(o), _ptr(phi), C.byref(st), _stream(stream))
         out = {"phi": phi, "iters": st.iters, "rel_residual": st.rel_residual, "inner_iters": st.inner_iters_total,
                "thick_fraction": st.thick_fraction, "ms": st.ms_total, "converged": status == 0,
-               "n_checkpoints": st.n_checkpoints, "history": hist[: st.iters] if history else None}
+               "n_checkpoints": st.n_checkpoints, "sweeps": st.n_sweeps,
+               "history": hist[: st.iters + 1] if history else None}
         if status not in (0, 6):
             _check(status)
         return out

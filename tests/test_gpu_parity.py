@@ -241,3 +241,18 @@ def test_gradients_parity(sn):
     Gt, Gs, Gq = (x.cpu().numpy() for x in m.gradients(r["phi"], a["mu"]))
     for got, ref in ((Gt, gt), (Gs, gs), (Gq, gq)):
         assert np.abs(got - ref).max() < 1e-9 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name", ["c1", "c2_32", "c3_8"])
+def test_fgmres_reaches_the_oracle_fixed_point(sn, oracle_cache, name):
+    """fGMRES (the paper's outer solver) converges to the same discrete solution as source iteration."""
+    from oracle.dsa import DSA
+    prob, T = _oracle(name, oracle_cache)
+    m = sn.Mesh.from_problem(prob)
+    r = m.source_iterate(dsa="thick", thick_rule=prob.thick_rule, outer="fgmres", restart=30, tol=1e-13,
+                         inner_tol=1e-10, max_iters=400)
+    ref = T.source_iterate(dsa=DSA(T, prob.thick_mask()), tol=1e-14, max_iters=2000)
+    assert r["converged"]
+    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) < 1e-9
+    si = m.source_iterate(dsa="thick", thick_rule=prob.thick_rule, tol=1e-13, inner_tol=1e-10, max_iters=2000)
+    assert r["iters"] <= si["iters"]

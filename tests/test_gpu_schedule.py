@@ -43,6 +43,7 @@ def test_schedules_agree_bitwise(sn, name, precision):
 def test_dependency_wait_timeout_is_reported_and_recoverable(sn):
     prob = CASES["c2_32"]()
     m = sn.Mesh.from_problem(prob)
+    m.set_schedule("dataflow", 128, 0)
     phi = torch.as_tensor(inputs.random_phi(prob, 6), device="cuda")
     ref = m.sweep(phi)
     m.debug_stall_next_sweep(0.2)

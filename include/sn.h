@@ -182,7 +182,8 @@ sn_status sn_adjoint_sweep(sn_mesh* mesh, const double* mu_in, double* out, int 
 
 /*
  * sn_adjoint_iterate: solves S^T mu = g (S = I - T, Eq. schur) by the adjoint source
- * iteration mu <- g + T^T mu with the transposed DSA step.  g, mu_inout: device.
+ * iteration mu <- g + T^T mu with the transposed DSA step, or (outer = SN_OUTER_FGMRES) by
+ * flexible GMRES right-preconditioned by that transposed step.  g, mu_inout: device.
  */
 sn_status sn_adjoint_iterate(sn_mesh* mesh, const sn_iter_opts* opts, const double* g, double* mu_inout,
                              sn_iter_stats* stats, void* stream);

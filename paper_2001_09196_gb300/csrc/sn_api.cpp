@@ -352,8 +352,10 @@ static sn_status check_opts(const sn_iter_opts* o) {
 // Flexible GMRES(k) on S x = b (Eq. schur), right-preconditioned by the DSA step
 // P v = v + E_f D_ff^{-1} Sigma_f E_f^T v (Algorithm 2 applied to a residual); classical
 // Gram-Schmidt twice, Givens rotations on the host.
+// adjoint = true solves S^T x = g instead: operator x - T^T x (reverse sweeps), preconditioner
+// v + Sigma_f D_ff^{-1} E_f^T v (the transposed DSA step), residual g + T^T x - x.
 static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_stats* stats, cudaStream_t s,
-                        std::chrono::steady_clock::time_point t0) {
+                        std::chrono::steady_clock::time_point t0, bool adjoint = false, const double* g_rhs = nullptr) {
     const long long M = (long long)m->ne * m->n;
     const int k = o->restart;
     const int nb = sn::krylov_blocks(M);
@@ -376,10 +378,16 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
     bool converged = false;
     bool timed_out = false;
     while (true) {
-        // true residual r = sweep(x) - x (with the fixed source)
+        // true residual r = sweep(x) - x (with the fixed source); adjoint: g + T^T x - x
         ++sweeps;
-        CK(sn::launch_sweep(m, x, o->precision, 1.0, s), "sweep");
-        CK(sn::launch_phi_reduce(m, o->precision, x, tmp, m->d_scalars, s), "phi reduce");
+        if (adjoint) {
+            CK(sn::launch_adjoint_sweep(m, x, s), "adjoint sweep");
+            CK(sn::launch_adjoint_reduce(m, tmp, s), "adjoint reduce");
+            CK(sn::launch_axpy_add(tmp, g_rhs, M, s), "add g");
+        } else {
+            CK(sn::launch_sweep(m, x, o->precision, 1.0, s), "sweep");
+            CK(sn::launch_phi_reduce(m, o->precision, x, tmp, m->d_scalars, s), "phi reduce");
+        }
         CK(sn::launch_axpy_norm(m, tmp, x, w, m->d_scalars, s), "residual");
         double rr = 0.0;
         CK(cudaMemcpyAsync(&rr, m->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
@@ -407,13 +415,18 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
             CK(sn::launch_copy(Zj, Vj, M, s), "copy");
             if (o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0) {
                 int its = 0;
-                CK(sn::dsa_correct(m->dsa, Vj, Zj, o->inner_tol, o->inner_max_iters, false, &its, s), "DSA");
+                CK(sn::dsa_correct(m->dsa, Vj, Zj, o->inner_tol, o->inner_max_iters, adjoint, &its, s), "DSA");
                 inner_total += its;
             }
             // w = S Zj = Zj - T Zj (T: sweep without the fixed source)
-            CK(sn::launch_sweep(m, Zj, o->precision, 0.0, s), "sweep");
+            if (adjoint) {
+                CK(sn::launch_adjoint_sweep(m, Zj, s), "adjoint sweep");
+                CK(sn::launch_adjoint_reduce(m, tmp, s), "adjoint reduce");
+            } else {
+                CK(sn::launch_sweep(m, Zj, o->precision, 0.0, s), "sweep");
+                CK(sn::launch_phi_reduce(m, o->precision, nullptr, tmp, nullptr, s), "phi reduce");
+            }
             ++sweeps;
-            CK(sn::launch_phi_reduce(m, o->precision, nullptr, tmp, nullptr, s), "phi reduce");
             CK(sn::launch_axpy_norm(m, Zj, tmp, w, m->d_scalars, s), "apply S");
             CK(sn::launch_multidot(V, j + 1, M, w, part, hd, s), "orthogonalise");
             CK(sn::launch_multiaxpy(V, j + 1, M, hd, -1.0, w, s), "orthogonalise");
@@ -567,6 +580,11 @@ sn_status sn_adjoint_iterate(sn_mesh* m, const sn_iter_opts* o, const double* g,
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
     const size_t M = (size_t)m->ne * m->n;
+    if (o->outer == SN_OUTER_FGMRES) {
+        if (o->precision != SN_FP64) return fail(SN_ERR_ARG, "the adjoint solve is float64 only");
+        if (!o->warm_start) CK(cudaMemsetAsync(mu, 0, M * sizeof(double), s), "memset");
+        return fgmres(m, o, mu, stats, s, t0, true, g);
+    }
     double* half = m->d_work;
     double* r = m->d_work + M;
     double* tmp = m->d_work + 2 * M;

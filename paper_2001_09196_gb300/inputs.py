@@ -219,7 +219,12 @@ def config5(n: int = 128, seed: int = MASTER_SEED + 4) -> Problem:
     # 32 distinct non-void elements, drawn without replacement by ranking random keys
     keys = uniform(seed, 31, nonvoid.size)
     fd = np.sort(nonvoid[np.argsort(keys, kind="stable")[:32]])
-    prob.extra.update({"detector": strip.astype(np.uint8), "fd_elements": fd, "fd_u": u})
+    # a second seeded set inside the detector's neighbourhood (12 columns to its left, 32 rows)
+    jj, ii = np.divmod(np.arange(n * n), n)
+    near = nonvoid[(ii[nonvoid] >= n - 16) & (jj[nonvoid] >= 7 * n // 16 - 8) & (jj[nonvoid] < 7 * n // 16 + n // 8 + 8)]
+    keys2 = uniform(seed, 32, near.size)
+    fd_near = np.sort(near[np.argsort(keys2, kind="stable")[:32]])
+    prob.extra.update({"detector": strip.astype(np.uint8), "fd_elements": fd, "fd_near": fd_near, "fd_u": u})
     return prob
 
 

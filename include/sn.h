@@ -240,6 +240,32 @@ sn_status sn_scalar_flux_noalloc(const double* psi, const double* weights, int n
 /* Number of CUDA kernels the library has launched since it was loaded (diagnostic). */
 long long sn_launch_count(void);
 
+/*
+ * Batches (task form 2): many meshes of different size, order p and S_N order swept together.
+ * sn_batch_create: the meshes stay owned by the caller and must outlive the batch.  The batch builds
+ * one work list of every instance's (direction, element) items ordered by (upwind level, element
+ * family, instance); a level never mixes element templates inside a warp.
+ * sn_batch_sweep: one transport update of every instance, phi_out[i] = sweep_i(phi_in[i]) (arrays of
+ * count device pointers; phi_in may be NULL), as one persistent launch (schedule 1) or one set of
+ * level launches (schedule 0).  Synchronises the stream.
+ * sn_batch_source_iterate: Eq. (DSA_fp) with Algorithm 2 for every instance at once: the batched sweep,
+ * per-instance flux reductions and residual norms, and one conjugate-gradient solve of the union of
+ * the instances' thick-DSA systems (block diagonal, one multigrid V-cycle over the union of their
+ * hierarchies), with per-instance convergence masks (a converged instance's items become no-ops).
+ * One whole outer iteration is recorded once into a CUDA graph and replayed; the host checks the
+ * masks every 4 iterations.  phis: count device pointers (warm start if opts->warm_start), receive
+ * the results; stats: count entries or NULL.  opts->outer must be SN_OUTER_SI; no checkpoints; the
+ * thick rule must not be SN_THICK_MASK.  SN_ERR_NOT_CONVERGED if any instance stops at max_iters.
+ */
+typedef struct sn_batch sn_batch;
+sn_status sn_batch_create(sn_mesh* const* meshes, int count, sn_batch** out);
+sn_status sn_batch_destroy(sn_batch* batch);
+sn_status sn_batch_set_schedule(sn_batch* batch, int schedule, int block, int max_blocks_per_sm);
+sn_status sn_batch_sweep(sn_batch* batch, const double* const* phi_in, double* const* phi_out, int precision,
+                         void* stream);
+sn_status sn_batch_source_iterate(sn_batch* batch, const sn_iter_opts* opts, double* const* phis,
+                                  sn_iter_stats* stats, void* stream);
+
 const char* sn_last_error(void);
 const char* sn_version(void);
 

@@ -300,9 +300,9 @@ sn_status sn_mesh_set_schedule(sn_mesh* m, int schedule, int block, int max_bloc
     return SN_OK;
 }
 
-// Builds (or reuses) the DSA hierarchy selected by opts.
-static sn_status ensure_dsa(sn_mesh* m, const sn_iter_opts* o) {
-    std::vector<unsigned char> mask(m->ne, 0);
+// Thick mask selected by opts (Sec. 4.2: sigma_s >= eta; or sigma_t h > eta; or explicit; all for full DSA).
+static sn_status thick_mask_for(const sn_mesh* m, const sn_iter_opts* o, std::vector<unsigned char>& mask) {
+    mask.assign(m->ne, 0);
     if (o->dsa == SN_DSA_FULL) {
         for (int e = 0; e < m->ne; ++e) {
             if (!(m->h_sigma_t[e] > 0.0))
@@ -323,6 +323,14 @@ static sn_status ensure_dsa(sn_mesh* m, const sn_iter_opts* o) {
     } else {
         return fail(SN_ERR_ARG, "bad thick_rule");
     }
+    return SN_OK;
+}
+
+// Builds (or reuses) the DSA hierarchy selected by opts.
+static sn_status ensure_dsa(sn_mesh* m, const sn_iter_opts* o) {
+    std::vector<unsigned char> mask;
+    sn_status st = thick_mask_for(m, o, mask);
+    if (st != SN_OK) return st;
     if (m->dsa && m->dsa_key_mask == mask && m->dsa_key_sigma == o->dsa_sigma) return SN_OK;
     sn::dsa_free(m->dsa);
     m->dsa = nullptr;
@@ -678,6 +686,258 @@ sn_status sn_get_angular_flux(sn_mesh* m, int d, int adjoint, int precision, dou
     } else {
         CK(sn::launch_copy(out, static_cast<const double*>(m->d_psi) + (size_t)d * M, M, s), "copy");
     }
+    return SN_OK;
+}
+
+// ---------------------------------------------------------------- batches
+static void free_batch(sn_batch* b) {
+    if (!b) return;
+    if (b->sweep_graph) cudaGraphExecDestroy(b->sweep_graph);
+    if (b->iter_graph) cudaGraphExecDestroy(b->iter_graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (void* p : {(void*)b->d_items, (void*)b->d_chunk_fam, (void*)b->d_args, (void*)b->d_done, (void*)b->d_done_off,
+                    (void*)b->d_ctrl, (void*)b->d_active, (void*)b->d_phi, (void*)b->d_half, (void*)b->d_r,
+                    (void*)b->d_rr, (void*)b->d_r0, (void*)b->d_iters, (void*)b->d_rel, (void*)b->d_next,
+                    (void*)b->d_dof_inst})
+        if (p) cudaFree(p);
+    sn::union_dsa_free(b->dsa);
+    delete b;
+}
+
+sn_status sn_batch_create(sn_mesh* const* meshes, int count, sn_batch** out) {
+    if (!meshes || !out || count < 1) return fail(SN_ERR_ARG, "need at least one mesh");
+    *out = nullptr;
+    std::unique_ptr<sn_batch, void (*)(sn_batch*)> b(new sn_batch(), free_batch);
+    b->count = count;
+    b->meshes.assign(meshes, meshes + count);
+    long long off = 0;
+    std::vector<int> dof_inst;
+    for (int i = 0; i < count; ++i) {
+        if (!meshes[i]) return fail(SN_ERR_ARG, "mesh %d is null", i);
+        for (int j = 0; j < i; ++j)
+            if (meshes[j] == meshes[i]) return fail(SN_ERR_ARG, "mesh %d appears twice", i);
+        b->dof_off.push_back(off);
+        const long long M = (long long)meshes[i]->ne * meshes[i]->n;
+        dof_inst.insert(dof_inst.end(), M, i);
+        off += M;
+    }
+    b->n_dof = off;
+    CK(dalloc(&b->d_phi, off), "alloc");
+    CK(dalloc(&b->d_half, off), "alloc");
+    CK(dalloc(&b->d_r, off), "alloc");
+    CK(dalloc(&b->d_dof_inst, off), "alloc");
+    CK(cudaMemcpy(b->d_dof_inst, dof_inst.data(), off * sizeof(int), cudaMemcpyHostToDevice), "copy");
+    CK(dalloc(&b->d_rr, count), "alloc");
+    CK(dalloc(&b->d_r0, count), "alloc");
+    CK(dalloc(&b->d_rel, count), "alloc");
+    CK(dalloc(&b->d_iters, count), "alloc");
+    CK(dalloc(&b->d_active, count), "alloc");
+    CK(dalloc(&b->d_next, count), "alloc");
+    CK(cudaMemset(b->d_phi, 0, off * sizeof(double)), "memset");
+    CK(sn::batch_build_worklist(b.get(), 0), "batch work list");
+    CK(cudaDeviceSynchronize(), "setup");
+    *out = b.release();
+    return SN_OK;
+}
+
+sn_status sn_batch_destroy(sn_batch* b) {
+    if (!b) return SN_OK;
+    cudaDeviceSynchronize();
+    free_batch(b);
+    return SN_OK;
+}
+
+sn_status sn_batch_set_schedule(sn_batch* b, int schedule, int block, int max_blocks_per_sm) {
+    if (!b) return fail(SN_ERR_ARG, "null batch");
+    if (schedule != sn::SCHED_LEVELS && schedule != sn::SCHED_DATAFLOW) return fail(SN_ERR_ARG, "bad schedule");
+    if (block < 32 || block > 128 || block % 32) return fail(SN_ERR_ARG, "block must be 32, 64, 96 or 128");
+    if (max_blocks_per_sm < 0) return fail(SN_ERR_ARG, "max_blocks_per_sm must be >= 0");
+    if (b->schedule != schedule || b->block != block || b->max_blocks_per_sm != max_blocks_per_sm) {
+        if (b->sweep_graph) cudaGraphExecDestroy(b->sweep_graph);
+        if (b->iter_graph) cudaGraphExecDestroy(b->iter_graph);
+        b->sweep_graph = b->iter_graph = nullptr;
+    }
+    b->schedule = schedule;
+    b->block = block;
+    b->max_blocks_per_sm = max_blocks_per_sm;
+    return SN_OK;
+}
+
+static sn_status batch_prepare(sn_batch* b, int precision) {
+    for (sn_mesh* m : b->meshes)
+        if (precision == SN_FP32) {
+            sn_status st = ensure_psi32(m);
+            if (st != SN_OK) return st;
+        }
+    return SN_OK;
+}
+
+static sn_status batch_timeout_check(sn_batch* b, cudaStream_t s) {
+    unsigned long long w = 0;
+    CK(cudaMemcpyAsync(&w, b->d_ctrl + 1, sizeof(w), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    if (w) {
+        CK(cudaMemsetAsync(b->d_ctrl + 1, 0, sizeof(w), s), "memset");
+        return fail(SN_ERR_TIMEOUT, "a batched sweep dependency wait timed out");
+    }
+    return SN_OK;
+}
+
+sn_status sn_batch_sweep(sn_batch* b, const double* const* phi_in, double* const* phi_out, int precision, void* stream) {
+    if (!b || !phi_out) return fail(SN_ERR_ARG, "null argument");
+    if (precision < SN_FP64 || precision > SN_FP32_REFINE) return fail(SN_ERR_ARG, "bad precision");
+    sn_status st = batch_prepare(b, precision);
+    if (st != SN_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < b->count; ++i) {
+        const size_t M = (size_t)b->meshes[i]->ne * b->meshes[i]->n;
+        if (phi_in && phi_in[i])
+            CK(cudaMemcpyAsync(b->d_phi + b->dof_off[i], phi_in[i], M * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+        else
+            CK(cudaMemsetAsync(b->d_phi + b->dof_off[i], 0, M * sizeof(double), s), "memset");
+    }
+    std::vector<int> ones(b->count, 1);
+    CK(cudaMemcpyAsync(b->d_active, ones.data(), b->count * sizeof(int), cudaMemcpyHostToDevice, s), "copy");
+    if (b->schedule == sn::SCHED_DATAFLOW) {
+        CK(sn::batch_launch_dataflow(b, precision, s), "batched sweep");
+    } else {
+        CK(sn::batch_enqueue_sweep(b, precision, s), "batched sweep");
+    }
+    for (int i = 0; i < b->count; ++i)
+        CK(sn::launch_phi_reduce(b->meshes[i], precision, nullptr, phi_out[i], nullptr, s), "phi reduce");
+    if (b->schedule == sn::SCHED_DATAFLOW) return batch_timeout_check(b, s);
+    CK(cudaStreamSynchronize(s), "sync");
+    return SN_OK;
+}
+
+static sn_status batch_ensure_dsa(sn_batch* b, const sn_iter_opts* o) {
+    std::vector<std::vector<unsigned char>> masks(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        sn_iter_opts oi = *o;
+        if (o->thick_rule == SN_THICK_MASK) return fail(SN_ERR_ARG, "explicit masks are not supported for batches");
+        sn_status st = thick_mask_for(b->meshes[i], &oi, masks[i]);
+        if (st != SN_OK) return st;
+    }
+    if (b->dsa && b->dsa_masks == masks && b->dsa_sigma == o->dsa_sigma) return SN_OK;
+    sn::union_dsa_free(b->dsa);
+    b->dsa = nullptr;
+    std::vector<sn::DsaHierarchy*> parts;
+    std::string err;
+    for (int i = 0; i < b->count; ++i) {
+        sn::DsaHierarchy* H = sn::dsa_build(b->meshes[i], masks[i].data(), o->dsa_sigma, err);
+        if (!H) {
+            for (sn::DsaHierarchy* P : parts) sn::dsa_free(P);
+            return fail(SN_ERR_ARG, "DSA setup of instance %d: %s", i, err.c_str());
+        }
+        parts.push_back(H);
+    }
+    b->dsa = sn::union_dsa_build(parts, b->dof_off, err);
+    if (!err.empty()) {
+        sn::union_dsa_free(b->dsa);
+        b->dsa = nullptr;
+        return fail(SN_ERR_CUDA, "batched DSA upload: %s", err.c_str());
+    }
+    b->dsa_masks = masks;
+    b->dsa_sigma = o->dsa_sigma;
+    if (b->iter_graph) {
+        cudaGraphExecDestroy(b->iter_graph);
+        b->iter_graph = nullptr;
+    }
+    return SN_OK;
+}
+
+sn_status sn_batch_source_iterate(sn_batch* b, const sn_iter_opts* o, double* const* phis, sn_iter_stats* stats,
+                                  void* stream) {
+    if (!b || !phis) return fail(SN_ERR_ARG, "null argument");
+    sn_status st = check_opts(o);
+    if (st != SN_OK) return st;
+    if (o->outer != SN_OUTER_SI) return fail(SN_ERR_ARG, "batches iterate with source iteration (SN_OUTER_SI)");
+    if (o->checkpoint_every > 0) return fail(SN_ERR_ARG, "checkpoints are not supported for batches");
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = batch_prepare(b, o->precision)) != SN_OK) return st;
+    if (o->dsa != SN_DSA_NONE && (st = batch_ensure_dsa(b, o)) != SN_OK) return st;
+    for (int i = 0; i < b->count; ++i) {
+        const size_t M = (size_t)b->meshes[i]->ne * b->meshes[i]->n;
+        if (o->warm_start)
+            CK(cudaMemcpyAsync(b->d_phi + b->dof_off[i], phis[i], M * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+        else
+            CK(cudaMemsetAsync(b->d_phi + b->dof_off[i], 0, M * sizeof(double), s), "memset");
+    }
+    std::vector<int> ones(b->count, 1);
+    CK(cudaMemcpyAsync(b->d_active, ones.data(), b->count * sizeof(int), cudaMemcpyHostToDevice, s), "copy");
+    CK(cudaMemsetAsync(b->d_iters, 0, b->count * sizeof(int), s), "memset");
+    // one outer iteration of all instances is recorded once into a CUDA graph and replayed
+    const bool same_key = b->iter_graph && b->g_prec == o->precision && b->g_sched == b->schedule &&
+                          b->g_dsa == o->dsa && b->g_tol == o->tol && b->g_inner_tol == o->inner_tol &&
+                          b->g_inner_max == o->inner_max_iters && b->g_max_iters == o->max_iters;
+    if (!same_key) {
+        if (b->iter_graph) cudaGraphExecDestroy(b->iter_graph);
+        b->iter_graph = nullptr;
+        if (!b->cap_stream) CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream");
+        CK(cudaStreamSynchronize(s), "sync");
+        // the argument table is switched to this precision before recording (host copies stay out)
+        CK(sn::batch_set_precision(b, o->precision, s), "precision");
+        CK(cudaStreamSynchronize(s), "sync");
+        CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
+        cudaError_t qerr = sn::batch_enqueue_iteration(b, o, b->d_next, b->d_dof_inst, b->cap_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t err = cudaStreamEndCapture(b->cap_stream, &graph);
+        if (qerr != cudaSuccess) err = qerr;
+        if (err == cudaSuccess) err = cudaGraphInstantiate(&b->iter_graph, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (err != cudaSuccess) {
+            b->iter_graph = nullptr;
+            return cuda_fail(err, "capture of the batched iteration");
+        }
+        b->g_prec = o->precision;
+        b->g_sched = b->schedule;
+        b->g_dsa = o->dsa;
+        b->g_tol = o->tol;
+        b->g_inner_tol = o->inner_tol;
+        b->g_inner_max = o->inner_max_iters;
+        b->g_max_iters = o->max_iters;
+    }
+    const int check_every = 4;
+    std::vector<int> active(b->count);
+    int launches = 0;
+    bool any = true;
+    while (any && launches < o->max_iters) {
+        CK(cudaGraphLaunch(b->iter_graph, s), "graph launch");
+        ++launches;
+        if (launches % check_every == 0 || launches == o->max_iters) {
+            CK(cudaMemcpyAsync(active.data(), b->d_active, b->count * sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+            CK(cudaStreamSynchronize(s), "sync");
+            any = false;
+            for (int a : active) any |= a != 0;
+        }
+    }
+    if (b->schedule == sn::SCHED_DATAFLOW && (st = batch_timeout_check(b, s)) != SN_OK) return st;
+    for (int i = 0; i < b->count; ++i) {
+        const size_t M = (size_t)b->meshes[i]->ne * b->meshes[i]->n;
+        CK(cudaMemcpyAsync(phis[i], b->d_phi + b->dof_off[i], M * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    }
+    std::vector<int> iters(b->count);
+    std::vector<double> rel(b->count);
+    CK(cudaMemcpyAsync(iters.data(), b->d_iters, b->count * sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaMemcpyAsync(rel.data(), b->d_rel, b->count * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    bool all = true;
+    for (int i = 0; i < b->count; ++i) {
+        const bool conv = rel[i] <= o->tol;
+        all &= conv;
+        if (stats) {
+            stats[i].iters = iters[i];
+            stats[i].rel_residual = rel[i];
+            stats[i].inner_iters_total = 0;
+            stats[i].thick_fraction = 0.0;
+            stats[i].n_checkpoints = 0;
+            stats[i].n_sweeps = iters[i];
+            stats[i].ms_total = ms;
+        }
+    }
+    if (!all) return fail(SN_ERR_NOT_CONVERGED, "some batch instances did not converge in %d iterations", o->max_iters);
     return SN_OK;
 }
 

@@ -82,6 +82,16 @@ struct LevelSets {
 enum { SCHED_LEVELS = 0, SCHED_DATAFLOW = 1 };
 
 struct DsaHierarchy;  // sn_dsa.cu
+struct UnionDsa;      // sn_batch.cu
+
+// Element families a batch can mix; a 32-item chunk of the batched work list never mixes them.
+enum { FAM_2D_P1 = 0, FAM_2D_P2 = 1, FAM_2D_P3 = 2, FAM_3D_P1 = 3, FAM_COUNT = 4 };
+inline int family_of(int dim, int p) { return dim == 3 ? FAM_3D_P1 : p - 1; }
+
+// Batched work item: instance, direction, element, family.
+struct BatchItem {
+    int inst, dir, elem, fam;
+};
 
 }  // namespace sn
 
@@ -122,6 +132,47 @@ struct sn_mesh {
     std::vector<unsigned char> dsa_key_mask;
 };
 
+struct sn_batch {
+    std::vector<sn_mesh*> meshes;
+    int count = 0;
+    int precision = -1;                      // precision the graphs were captured for
+    // batched work list: sorted by (level, family, instance, dir, elem); every (level, family)
+    // segment padded to a multiple of 32 with inst = -1
+    sn::BatchItem* d_items = nullptr;
+    long long n_items = 0;
+    std::vector<long long> seg_begin, seg_end;
+    std::vector<int> seg_fam, seg_level;
+    int* d_chunk_fam = nullptr;              // family of each 32-item chunk (dataflow)
+    sn::SweepArgs* d_args = nullptr;         // per-instance sweep arguments (fixed pointers)
+    std::vector<sn::SweepArgs> h_args;
+    int* d_done = nullptr;                   // completion words, instance blocks at done_off
+    long long* d_done_off = nullptr;
+    unsigned long long* d_ctrl = nullptr;    // chunk counter, error word
+    int epoch = 0;
+    int* d_active = nullptr;                 // per instance: 1 = still iterating
+    int schedule = 0, block = 64, max_blocks_per_sm = 0;
+    cudaGraphExec_t sweep_graph = nullptr;   // level schedule, all instances
+    cudaGraphExec_t iter_graph = nullptr;    // one whole outer iteration
+    cudaStream_t cap_stream = nullptr;
+    // concatenated iteration vectors (instance blocks at dof_off)
+    std::vector<long long> dof_off;
+    long long n_dof = 0;
+    double *d_phi = nullptr, *d_half = nullptr, *d_r = nullptr;
+    double* d_rr = nullptr;                  // per-instance squared residual norms
+    double* d_r0 = nullptr;                  // per-instance first residual norm
+    int* d_iters = nullptr;                  // per-instance iteration counts
+    double* d_rel = nullptr;                 // per-instance last relative residual
+    int* d_next = nullptr;                   // per-instance "iterate again" flags
+    int* d_dof_inst = nullptr;               // instance of every concatenated DOF
+    sn::UnionDsa* dsa = nullptr;
+    std::vector<std::vector<unsigned char>> dsa_masks;  // thick masks the union DSA was built for
+    int dsa_sigma = -1;
+    // key of the captured iteration graph
+    int g_prec = -1, g_sched = -1, g_dsa = -1, g_inner_max = -1;
+    double g_tol = -1, g_inner_tol = -1;
+    int g_max_iters = -1;
+};
+
 namespace sn {
 // sn_api.cpp: records the thread-local message returned by sn_last_error
 sn_status set_error(sn_status st, const char* msg);
@@ -129,6 +180,21 @@ sn_status set_error(sn_status st, const char* msg);
 cudaError_t build_levels(sn_mesh* m, cudaStream_t s, bool* cycle);
 cudaError_t compute_mass(sn_mesh* m, cudaStream_t s);
 void drop_level_graphs(sn_mesh* m);
+// batched sweep over all instances of a batch (sn_sweep.cu)
+cudaError_t batch_build_worklist(sn_batch* b, cudaStream_t s);
+cudaError_t batch_enqueue_sweep(sn_batch* b, int precision, cudaStream_t s);  // level schedule, capturable
+cudaError_t batch_launch_dataflow(sn_batch* b, int precision, cudaStream_t s);
+cudaError_t batch_set_precision(sn_batch* b, int precision, cudaStream_t s);
+// union DSA of a batch (sn_batch.cu)
+UnionDsa* union_dsa_build(const std::vector<DsaHierarchy*>& parts, const std::vector<long long>& dof_off,
+                          std::string& err);
+void union_dsa_free(UnionDsa* U);
+long long union_dsa_rows(const UnionDsa* U);
+int* union_dsa_iters(UnionDsa* U);
+cudaError_t union_dsa_correct(UnionDsa* U, const double* r_all, double* phi_all, const int* active, double tol,
+                              int max_iters, cudaStream_t s);
+cudaError_t batch_enqueue_iteration(sn_batch* b, const sn_iter_opts* o, int* d_next, const int* d_dof_inst,
+                                    cudaStream_t s);
 cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double q_scale, cudaStream_t s);
 cudaError_t launch_adjoint_sweep(sn_mesh* m, const double* mu, cudaStream_t s);
 cudaError_t launch_phi_reduce(sn_mesh* m, int precision, const double* phi_in, double* phi_out, double* d_rr,

@@ -1102,6 +1102,243 @@ cudaError_t launch_adjoint_sweep(sn_mesh* m, const double* mu, cudaStream_t s) {
     return launch_levels_graph(m, 3, s);
 }
 
+// ---------------------------------------------------------------- batched sweeps
+// Many meshes (instances) are swept together.  The batch's work list holds every instance's
+// (direction, element) items sorted by (level, element family, instance); each (level, family)
+// segment is padded to whole 32-item chunks, so a warp always runs one element template.
+template <int DIM, int P, int MODE>
+__global__ void __launch_bounds__(128) batch_level_kernel(const SweepArgs* args, const BatchItem* items,
+                                                         long long begin, long long end, const int* active) {
+    const long long t = begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= end) return;
+    const BatchItem it = items[t];
+    if (it.inst < 0 || !active[it.inst]) return;
+    solve_item<DIM, P, MODE>(args[it.inst], it.dir, it.elem);
+}
+
+template <int DIM, int P, int MODE>
+__device__ __forceinline__ bool batch_chunk_item(const SweepArgs* args, const BatchItem& it, const int* active,
+                                                 int* done, const long long* done_off, int epoch,
+                                                 unsigned long long deadline, bool run) {
+    // wait phase (run = false) or solve phase (run = true) of one lane's item
+    if (it.inst < 0 || !active[it.inst]) return true;
+    const SweepArgs& a = args[it.inst];
+    int* dn = done + done_off[it.inst];
+    if (run) {
+        solve_item<DIM, P, MODE>(a, it.dir, it.elem);
+        st_release(dn + (size_t)it.dir * a.ne + it.elem, epoch);
+        return true;
+    }
+    const double Ox = a.dirs[3 * it.dir], Oy = a.dirs[3 * it.dir + 1], Oz = a.dirs[3 * it.dir + 2];
+#pragma unroll
+    for (int fc = 0; fc < 2 * DIM; ++fc) {
+        if (face_flux_only<DIM, P>(a, it.elem, fc, Ox, Oy, Oz) < 0.0) {
+            const int u = neighbor<DIM, P>(a, it.elem, fc);
+            if (u < 0) continue;
+            const int* flag = dn + (size_t)it.dir * a.ne + u;
+            int polls = 0;
+            while (ld_acquire(flag) != epoch) {
+                if (++polls > 64) {
+                    if (globaltimer() > deadline) return false;
+                    __nanosleep(64);
+                }
+            }
+        }
+    }
+    return true;
+}
+
+template <int DIM, int P, int MODE>
+__device__ __forceinline__ bool batch_chunk(const SweepArgs* args, const BatchItem& it, const int* active, int* done,
+                                            const long long* done_off, int epoch, unsigned long long deadline) {
+    const bool ok = batch_chunk_item<DIM, P, MODE>(args, it, active, done, done_off, epoch, deadline, false);
+    if (!__all_sync(0xffffffffu, ok)) return false;
+    batch_chunk_item<DIM, P, MODE>(args, it, active, done, done_off, epoch, deadline, true);
+    return true;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) batch_dataflow_kernel(const SweepArgs* args, const BatchItem* items,
+                                                            const int* chunk_fam, long long n_items, int* done,
+                                                            const long long* done_off, const int* epoch_ptr,
+                                                            unsigned long long* ctrl, const int* active,
+                                                            unsigned long long timeout_ns) {
+    const int lane = threadIdx.x & 31;
+    const long long n_chunks = n_items >> 5;
+    const int epoch = *epoch_ptr;  // advanced on the device before the launch, so graphs can replay it
+    const unsigned long long deadline = globaltimer() + timeout_ns;
+    int* error = reinterpret_cast<int*>(ctrl + 1);
+    while (true) {
+        unsigned long long c = 0;
+        int failed = 0;
+        if (lane == 0) {
+            c = atomicAdd(ctrl, 1ull);
+            failed = *(volatile int*)error;
+        }
+        c = __shfl_sync(0xffffffffu, c, 0);
+        failed = __shfl_sync(0xffffffffu, failed, 0);
+        if ((long long)c >= n_chunks || failed) break;
+        const BatchItem it = items[(c << 5) + lane];
+        bool ok;
+        switch (chunk_fam[c]) {  // uniform across the warp
+            case FAM_2D_P1: ok = batch_chunk<2, 1, MODE>(args, it, active, done, done_off, epoch, deadline); break;
+            case FAM_2D_P2: ok = batch_chunk<2, 2, MODE>(args, it, active, done, done_off, epoch, deadline); break;
+            case FAM_2D_P3: ok = batch_chunk<2, 3, MODE>(args, it, active, done, done_off, epoch, deadline); break;
+            default: ok = batch_chunk<3, 1, MODE>(args, it, active, done, done_off, epoch, deadline); break;
+        }
+        if (!ok) {
+            if (lane == 0) atomicExch(error, 1);
+            break;
+        }
+    }
+}
+
+cudaError_t batch_build_worklist(sn_batch* b, cudaStream_t s) {
+    cudaError_t err;
+    const int n = b->count;
+    std::vector<std::vector<int2>> items(n);
+    int maxL = 0;
+    long long done_total = 0;
+    std::vector<long long> done_off(n);
+    for (int i = 0; i < n; ++i) {
+        sn_mesh* m = b->meshes[i];
+        const long long total = (long long)m->nd * m->ne;
+        items[i].resize(total);
+        if ((err = cudaMemcpy(items[i].data(), m->levels.items, total * sizeof(int2), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return err;
+        maxL = std::max(maxL, m->levels.n_levels);
+        done_off[i] = done_total;
+        done_total += total;
+    }
+    std::vector<BatchItem> list;
+    std::vector<int> chunk_fam;
+    b->seg_begin.clear();
+    b->seg_end.clear();
+    b->seg_fam.clear();
+    b->seg_level.clear();
+    for (int L = 0; L < maxL; ++L)
+        for (int fam = 0; fam < FAM_COUNT; ++fam) {
+            const long long begin = (long long)list.size();
+            for (int i = 0; i < n; ++i) {
+                sn_mesh* m = b->meshes[i];
+                if (family_of(m->dim, m->p) != fam || L >= m->levels.n_levels) continue;
+                for (long long t = m->levels.level_ptr[L]; t < m->levels.level_ptr[L + 1]; ++t)
+                    list.push_back({i, items[i][t].x, items[i][t].y, fam});
+            }
+            if ((long long)list.size() == begin) continue;
+            while (list.size() % 32) list.push_back({-1, 0, 0, fam});
+            b->seg_begin.push_back(begin);
+            b->seg_end.push_back((long long)list.size());
+            b->seg_fam.push_back(fam);
+            b->seg_level.push_back(L);
+            for (long long c = begin / 32; c < (long long)list.size() / 32; ++c) chunk_fam.push_back(fam);
+        }
+    b->n_items = (long long)list.size();
+    if ((err = cudaMalloc(&b->d_items, list.size() * sizeof(BatchItem))) != cudaSuccess) return err;
+    if ((err = cudaMemcpy(b->d_items, list.data(), list.size() * sizeof(BatchItem), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return err;
+    if ((err = cudaMalloc(&b->d_chunk_fam, chunk_fam.size() * sizeof(int))) != cudaSuccess) return err;
+    if ((err = cudaMemcpy(b->d_chunk_fam, chunk_fam.data(), chunk_fam.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return err;
+    if ((err = cudaMalloc(&b->d_done, std::max<long long>(1, done_total) * sizeof(int))) != cudaSuccess) return err;
+    if ((err = cudaMemset(b->d_done, 0, std::max<long long>(1, done_total) * sizeof(int))) != cudaSuccess) return err;
+    if ((err = cudaMalloc(&b->d_done_off, n * sizeof(long long))) != cudaSuccess) return err;
+    if ((err = cudaMemcpy(b->d_done_off, done_off.data(), n * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return err;
+    if ((err = cudaMalloc(&b->d_ctrl, 3 * sizeof(unsigned long long))) != cudaSuccess) return err;
+    if ((err = cudaMemset(b->d_ctrl, 0, 3 * sizeof(unsigned long long))) != cudaSuccess) return err;
+    // per-instance arguments: sources and angular fluxes at fixed addresses
+    b->h_args.resize(n);
+    for (int i = 0; i < n; ++i) {
+        b->h_args[i] = make_args(b->meshes[i]);
+        b->h_args[i].phi = b->d_phi + b->dof_off[i];
+        b->h_args[i].psi = b->meshes[i]->d_psi;
+    }
+    if ((err = cudaMalloc(&b->d_args, n * sizeof(SweepArgs))) != cudaSuccess) return err;
+    return cudaMemcpyAsync(b->d_args, b->h_args.data(), n * sizeof(SweepArgs), cudaMemcpyHostToDevice, s);
+}
+
+// Points every instance's angular-flux storage at the precision's buffer (float32 for SN_FP32).
+cudaError_t batch_set_precision(sn_batch* b, int precision, cudaStream_t s) {
+    if (b->precision == precision) return cudaSuccess;
+    for (int i = 0; i < b->count; ++i)
+        b->h_args[i].psi = precision == SN_FP32 ? b->meshes[i]->d_psi32 : b->meshes[i]->d_psi;
+    b->precision = precision;
+    if (b->sweep_graph) {
+        cudaGraphExecDestroy(b->sweep_graph);
+        b->sweep_graph = nullptr;
+    }
+    if (b->iter_graph) {
+        cudaGraphExecDestroy(b->iter_graph);
+        b->iter_graph = nullptr;
+    }
+    return cudaMemcpyAsync(b->d_args, b->h_args.data(), b->count * sizeof(SweepArgs), cudaMemcpyHostToDevice, s);
+}
+
+cudaError_t batch_enqueue_sweep(sn_batch* b, int precision, cudaStream_t s) {
+    cudaError_t err = batch_set_precision(b, precision, s);
+    if (err != cudaSuccess) return err;
+    const int bs = b->block;
+    for (size_t k = 0; k < b->seg_begin.size(); ++k) {
+        const long long lo = b->seg_begin[k], hi = b->seg_end[k];
+        const unsigned g = grid_for(hi - lo, bs);
+        const int fam = b->seg_fam[k];
+#define SN_BATCH_LEVEL(MODE_)                                                                                   \
+    do {                                                                                                      \
+        if (fam == FAM_2D_P1) batch_level_kernel<2, 1, MODE_><<<g, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active); \
+        else if (fam == FAM_2D_P2) batch_level_kernel<2, 2, MODE_><<<g, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active); \
+        else if (fam == FAM_2D_P3) batch_level_kernel<2, 3, MODE_><<<g, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active); \
+        else batch_level_kernel<3, 1, MODE_><<<g, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active);       \
+    } while (0)
+        SN_COUNT_LAUNCH();
+        if (precision == SN_FP64) SN_BATCH_LEVEL(0);
+        else if (precision == SN_FP32) SN_BATCH_LEVEL(1);
+        else SN_BATCH_LEVEL(2);
+#undef SN_BATCH_LEVEL
+    }
+    return cudaGetLastError();
+}
+
+__global__ void bump_epoch_kernel(unsigned long long* ctrl) {
+    int* e = reinterpret_cast<int*>(ctrl + 2);
+    *e = (*e >= 0x7ffffff0) ? 1 : *e + 1;  // completion words are compared for equality only
+    ctrl[0] = 0ull;                          // chunk counter of the coming launch
+}
+
+// Persistent dataflow sweep of all instances; capturable (the epoch is advanced on the device).
+cudaError_t batch_launch_dataflow(sn_batch* b, int precision, cudaStream_t s) {
+    cudaError_t err = batch_set_precision(b, precision, s);
+    if (err != cudaSuccess) return err;
+    SN_COUNT_LAUNCH();
+    bump_epoch_kernel<<<1, 1, 0, s>>>(b->d_ctrl);
+    int dev = 0, sms = 0, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (precision == SN_FP64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_dataflow_kernel<0>, b->block, 0);
+    else if (precision == SN_FP32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_dataflow_kernel<1>, b->block, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_dataflow_kernel<2>, b->block, 0);
+    if (b->max_blocks_per_sm > 0 && b->max_blocks_per_sm < per_sm) per_sm = b->max_blocks_per_sm;
+    per_sm = std::max(per_sm, 1);
+    long long blocks = std::min<long long>((long long)sms * per_sm, (b->n_items + b->block - 1) / b->block);
+    blocks = std::max<long long>(blocks, 1);
+    const unsigned long long timeout = 4000000000ull;
+    const int* epoch = reinterpret_cast<const int*>(b->d_ctrl + 2);
+    SN_COUNT_LAUNCH();
+    if (precision == SN_FP64)
+        batch_dataflow_kernel<0><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam, b->n_items,
+                                                                      b->d_done, b->d_done_off, epoch, b->d_ctrl,
+                                                                      b->d_active, timeout);
+    else if (precision == SN_FP32)
+        batch_dataflow_kernel<1><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam, b->n_items,
+                                                                      b->d_done, b->d_done_off, epoch, b->d_ctrl,
+                                                                      b->d_active, timeout);
+    else
+        batch_dataflow_kernel<2><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam, b->n_items,
+                                                                      b->d_done, b->d_done_off, epoch, b->d_ctrl,
+                                                                      b->d_active, timeout);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_phi_reduce(sn_mesh* m, int precision, const double* phi_in, double* phi_out, double* d_rr,
                               cudaStream_t s) {
     const size_t M = (size_t)m->ne * m->n;

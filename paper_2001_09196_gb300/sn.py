@@ -80,6 +80,11 @@ def _load():
         "sn_mesh_set_schedule": [vp, i, i, i],
         "sn_debug_stall_next_sweep": [vp, d],
         "sn_scalar_flux_noalloc": [vp, vp, i, C.c_longlong, vp, vp, vp, vp],
+        "sn_batch_create": [vp, i, C.POINTER(vp)],
+        "sn_batch_destroy": [vp],
+        "sn_batch_set_schedule": [vp, i, i, i],
+        "sn_batch_sweep": [vp, vp, vp, i, vp],
+        "sn_batch_source_iterate": [vp, C.POINTER(IterOpts), vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -311,3 +316,54 @@ class Mesh:
         its = C.c_int(0)
         _check(_lib.sn_dsa_solve(self._h, C.byref(o), _ptr(b), _ptr(x), C.byref(its), _stream(stream)))
         return x, its.value
+
+
+class Batch:
+    """Many meshes swept and iterated together (one launch per sweep for all instances)."""
+
+    def __init__(self, meshes):
+        self.meshes = list(meshes)
+        arr = (C.c_void_p * len(self.meshes))(*[m._h.value for m in self.meshes])
+        h = C.c_void_p()
+        _check(_lib.sn_batch_create(arr, len(self.meshes), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.sn_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_schedule(self, schedule="levels", block=64, max_blocks_per_sm=0):
+        sched = {"levels": 0, "dataflow": 1}[schedule] if isinstance(schedule, str) else int(schedule)
+        _check(_lib.sn_batch_set_schedule(self._h, sched, int(block), int(max_blocks_per_sm)))
+
+    @staticmethod
+    def _ptrs(tensors):
+        return (C.c_void_p * len(tensors))(*[None if t is None else _ptr(t).value for t in tensors])
+
+    def sweep(self, phis_in=None, precision="fp64", stream=None):
+        import torch
+        outs = [torch.empty(m.shape, dtype=torch.float64, device="cuda") for m in self.meshes]
+        ins = self._ptrs(phis_in) if phis_in is not None else None
+        _check(_lib.sn_batch_sweep(self._h, ins, self._ptrs(outs), _PREC.get(precision, precision), _stream(stream)))
+        return outs
+
+    def source_iterate(self, phis=None, stream=None, **kw):
+        import torch
+        if phis is None:
+            phis = [torch.zeros(m.shape, dtype=torch.float64, device="cuda") for m in self.meshes]
+        kw.setdefault("warm_start", False)
+        kw.setdefault("outer", "si")
+        o = make_opts(**kw)
+        stats = (IterStats * len(self.meshes))()
+        status = _lib.sn_batch_source_iterate(self._h, C.byref(o), self._ptrs(phis), stats, _stream(stream))
+        if status not in (0, 6):
+            _check(status)
+        return {"phi": phis, "iters": [st.iters for st in stats], "rel_residual": [st.rel_residual for st in stats],
+                "converged": status == 0, "ms": stats[0].ms_total if len(stats) else 0.0}

@@ -266,6 +266,16 @@ sn_status sn_batch_sweep(sn_batch* batch, const double* const* phi_in, double* c
 sn_status sn_batch_source_iterate(sn_batch* batch, const sn_iter_opts* opts, double* const* phis,
                                   sn_iter_stats* stats, void* stream);
 
+/*
+ * Schedule autotuner: times the candidate sweep schedules (level graphs with 32/64/128-thread blocks;
+ * persistent dataflow launches with several per-SM occupancy caps) for this mesh / batch and precision
+ * with CUDA events, keeps the fastest and reports it (any output pointer may be NULL).  Results of
+ * sn_mesh_autotune are cached per (dim, p, directions, precision, element count), so meshes of the same
+ * shape reuse them.  Schedules give bitwise-identical results; tuning changes only the time.
+ */
+sn_status sn_mesh_autotune(sn_mesh* mesh, int precision, void* stream, int* schedule, int* block, int* cap);
+sn_status sn_batch_autotune(sn_batch* batch, int precision, void* stream, int* schedule, int* block, int* cap);
+
 const char* sn_last_error(void);
 const char* sn_version(void);
 

@@ -8,7 +8,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -938,6 +941,123 @@ sn_status sn_batch_source_iterate(sn_batch* b, const sn_iter_opts* o, double* co
         }
     }
     if (!all) return fail(SN_ERR_NOT_CONVERGED, "some batch instances did not converge in %d iterations", o->max_iters);
+    return SN_OK;
+}
+
+// ---------------------------------------------------------------- schedule autotuner
+}  // extern "C"
+
+namespace {
+struct TuneKey {
+    int kind, dim, p, nd, precision;
+    long long size;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(kind, dim, p, nd, precision, size) < std::tie(o.kind, o.dim, o.p, o.nd, o.precision, o.size);
+    }
+};
+struct TuneChoice {
+    int schedule, block, cap;
+    float ms;
+};
+std::map<TuneKey, TuneChoice> g_tune_cache;
+std::mutex g_tune_mutex;
+const TuneChoice kCandidates[] = {{0, 32, 0, 0}, {0, 64, 0, 0}, {0, 128, 0, 0}, {1, 128, 0, 0},
+                                  {1, 128, 1, 0}, {1, 64, 2, 0}, {1, 32, 4, 0}};
+
+template <typename F>
+float time_ms(F&& run, cudaStream_t s, int reps) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    run();  // warm-up (also records graphs)
+    float best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+        cudaEventRecord(a, s);
+        run();
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        best = std::min(best, ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+}  // namespace
+
+extern "C" {
+
+sn_status sn_mesh_autotune(sn_mesh* m, int precision, void* stream, int* schedule, int* block, int* cap) {
+    if (!m) return fail(SN_ERR_ARG, "null mesh");
+    if (precision < SN_FP64 || precision > SN_FP32_REFINE) return fail(SN_ERR_ARG, "bad precision");
+    cudaStream_t s = (cudaStream_t)stream;
+    const TuneKey key{0, m->dim, m->p, m->nd, precision, (long long)m->ne};
+    TuneChoice best{-1, 0, 0, 1e30f};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) best = it->second;
+    }
+    if (best.schedule < 0) {
+        if (precision == SN_FP32) {
+            sn_status st = ensure_psi32(m);
+            if (st != SN_OK) return st;
+        }
+        double* out = m->d_work + 3 * (size_t)m->ne * m->n;
+        for (const TuneChoice& c : kCandidates) {
+            sn_status st = sn_mesh_set_schedule(m, c.schedule, c.block, c.cap);
+            if (st != SN_OK) return st;
+            cudaError_t err = cudaSuccess;
+            const float ms = time_ms([&] {
+                if (err == cudaSuccess) err = sn::launch_sweep(m, nullptr, precision, 1.0, s);
+                if (err == cudaSuccess) err = sn::launch_phi_reduce(m, precision, nullptr, out, nullptr, s);
+            }, s, 2);
+            CK(err, "autotune sweep");
+            if (m->schedule == sn::SCHED_DATAFLOW) {
+                bool timed_out = false;
+                CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
+                if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out while tuning");
+            }
+            if (ms < best.ms) best = {c.schedule, c.block, c.cap, ms};
+        }
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = best;
+    }
+    sn_status st = sn_mesh_set_schedule(m, best.schedule, best.block, best.cap);
+    if (st != SN_OK) return st;
+    if (schedule) *schedule = best.schedule;
+    if (block) *block = best.block;
+    if (cap) *cap = best.cap;
+    return SN_OK;
+}
+
+sn_status sn_batch_autotune(sn_batch* b, int precision, void* stream, int* schedule, int* block, int* cap) {
+    if (!b) return fail(SN_ERR_ARG, "null batch");
+    if (precision < SN_FP64 || precision > SN_FP32_REFINE) return fail(SN_ERR_ARG, "bad precision");
+    cudaStream_t s = (cudaStream_t)stream;
+    sn_status st = batch_prepare(b, precision);
+    if (st != SN_OK) return st;
+    std::vector<int> ones(b->count, 1);
+    CK(cudaMemcpyAsync(b->d_active, ones.data(), b->count * sizeof(int), cudaMemcpyHostToDevice, s), "copy");
+    CK(cudaMemsetAsync(b->d_phi, 0, (size_t)b->n_dof * sizeof(double), s), "memset");
+    TuneChoice best{-1, 0, 0, 1e30f};
+    for (const TuneChoice& c : kCandidates) {
+        if ((st = sn_batch_set_schedule(b, c.schedule, c.block, c.cap)) != SN_OK) return st;
+        cudaError_t err = cudaSuccess;
+        const float ms = time_ms([&] {
+            if (err != cudaSuccess) return;
+            err = b->schedule == sn::SCHED_DATAFLOW ? sn::batch_launch_dataflow(b, precision, s)
+                                                    : sn::batch_enqueue_sweep(b, precision, s);
+        }, s, 2);
+        CK(err, "autotune batched sweep");
+        if (b->schedule == sn::SCHED_DATAFLOW && (st = batch_timeout_check(b, s)) != SN_OK) return st;
+        if (ms < best.ms) best = {c.schedule, c.block, c.cap, ms};
+    }
+    if ((st = sn_batch_set_schedule(b, best.schedule, best.block, best.cap)) != SN_OK) return st;
+    if (schedule) *schedule = best.schedule;
+    if (block) *block = best.block;
+    if (cap) *cap = best.cap;
     return SN_OK;
 }
 

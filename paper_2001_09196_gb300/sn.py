@@ -85,6 +85,8 @@ def _load():
         "sn_batch_set_schedule": [vp, i, i, i],
         "sn_batch_sweep": [vp, vp, vp, i, vp],
         "sn_batch_source_iterate": [vp, C.POINTER(IterOpts), vp, vp, vp],
+        "sn_mesh_autotune": [vp, i, vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
+        "sn_batch_autotune": [vp, i, vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -225,6 +227,13 @@ class Mesh:
     def debug_stall_next_sweep(self, timeout_s=0.2):
         _check(_lib.sn_debug_stall_next_sweep(self._h, float(timeout_s)))
 
+    def autotune(self, precision="fp64", stream=None):
+        """Pick the fastest sweep schedule for this mesh and precision; returns (schedule, block, cap)."""
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        _check(_lib.sn_mesh_autotune(self._h, _PREC.get(precision, precision), _stream(stream), C.byref(a),
+                                     C.byref(b), C.byref(c)))
+        return ("levels", "dataflow")[a.value], b.value, c.value
+
     def quadrature(self):
         dirs = np.zeros((self.n_dirs, 3))
         w = np.zeros(self.n_dirs)
@@ -342,6 +351,12 @@ class Batch:
     def set_schedule(self, schedule="levels", block=64, max_blocks_per_sm=0):
         sched = {"levels": 0, "dataflow": 1}[schedule] if isinstance(schedule, str) else int(schedule)
         _check(_lib.sn_batch_set_schedule(self._h, sched, int(block), int(max_blocks_per_sm)))
+
+    def autotune(self, precision="fp64", stream=None):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        _check(_lib.sn_batch_autotune(self._h, _PREC.get(precision, precision), _stream(stream), C.byref(a),
+                                      C.byref(b), C.byref(c)))
+        return ("levels", "dataflow")[a.value], b.value, c.value
 
     @staticmethod
     def _ptrs(tensors):

@@ -65,3 +65,33 @@ def test_adjoint_schedules_agree_bitwise(sn, name):
     for block, cap in ((128, 0), (32, 1)):
         m.set_schedule("dataflow", block, cap)
         assert torch.equal(m.adjoint_sweep(mu), ref), (block, cap)
+
+
+CANDIDATES = {("levels", 32, 0), ("levels", 64, 0), ("levels", 128, 0), ("dataflow", 128, 0), ("dataflow", 128, 1),
+              ("dataflow", 64, 2), ("dataflow", 32, 4)}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_autotune_picks_a_candidate_and_keeps_results(sn, precision):
+    prob = inputs.config2(n=48, block=8)
+    m = sn.Mesh.from_problem(prob)
+    phi = torch.as_tensor(inputs.random_phi(prob, 9), device="cuda")
+    ref = m.sweep(phi, precision=precision)
+    choice = m.autotune(precision)
+    assert choice in CANDIDATES
+    assert torch.equal(m.sweep(phi, precision=precision), ref)
+    # a second mesh of the same shape takes the cached choice
+    m2 = sn.Mesh.from_problem(prob)
+    assert m2.autotune(precision) == choice
+    assert torch.equal(m2.sweep(phi, precision=precision), ref)
+
+
+def test_batch_autotune_keeps_results(sn):
+    probs = [inputs.config2d_fields(16, 1, 4, 11, "a"), inputs.config2d_fields(20, 2, 6, 12, "b"), inputs.config3(n=6)]
+    meshes = [sn.Mesh.from_problem(p) for p in probs]
+    batch = sn.Batch(meshes)
+    phis = [torch.as_tensor(inputs.random_phi(p, 30 + k), device="cuda") for k, p in enumerate(probs)]
+    ref = batch.sweep(phis)
+    assert batch.autotune("fp64") in CANDIDATES
+    for a, b in zip(batch.sweep(phis), ref):
+        assert torch.equal(a, b)

@@ -50,6 +50,7 @@ enum { SN_DSA_NONE = 0, SN_DSA_FULL = 1, SN_DSA_THICK = 2 };    /* DSA variant *
 enum { SN_THICK_SIGMA_S = 0, SN_THICK_SIGMA_T_H = 1, SN_THICK_MASK = 2 };
 enum { SN_DSA_SIGMA_S = 0, SN_DSA_SIGMA_T = 1 };
 enum { SN_OUTER_SI = 0, SN_OUTER_FGMRES = 1 };                  /* outer iteration */
+enum { SN_CACHE_OFF = 0, SN_CACHE_ON = 1, SN_CACHE_AUTO = 2 };  /* operator cache */
 
 typedef struct sn_mesh sn_mesh;
 
@@ -88,6 +89,25 @@ sn_status sn_mesh_get_info(const sn_mesh* mesh, sn_mesh_info* info);
  * block: threads per block (32..128, multiple of 32); max_blocks_per_sm: 0 = occupancy limit.
  */
 sn_status sn_mesh_set_schedule(sn_mesh* mesh, int schedule, int block, int max_blocks_per_sm);
+
+/*
+ * Operator cache.  The element operator A_e of Eq. (sntransport) (volume terms plus outflow
+ * faces, Sec. 1) depends on the direction, the element geometry and sigma_t only, so within a
+ * solve every transport update re-solves the same nd x ne small systems.  With the cache on, one
+ * fully parallel kernel forms every A_e^{-1} in float64 (from its LU factors) after each change
+ * of materials, and a sweep then builds the right-hand side and applies the stored inverse (the
+ * adjoint applies its transpose); on the level schedule one lane per element node does this, so
+ * an element's solve takes O(N) dependent steps instead of O(N^3).  Storage: nd x ne x s values,
+ * s = N^2 rounded up to a multiple of 4 (N = nodes per element), float64 for SN_FP64 and the
+ * adjoint, a float32 copy for SN_FP32, plus the face flux factors (2D: 4 float64 per direction
+ * and element; 3D: 3 per direction).  SN_FP32_REFINE always assembles on the fly.  Results agree
+ * with on-the-fly solves to rounding.
+ *   SN_CACHE_OFF: assemble and factor in every sweep (frees any cached inverses);
+ *   SN_CACHE_ON: always cache (an allocation failure is returned as SN_ERR_CUDA);
+ *   SN_CACHE_AUTO (default): cache when the inverses take at most half of the free device memory.
+ * Synchronises the device.  Errors: SN_ERR_ARG for a null mesh or an unknown mode.
+ */
+sn_status sn_mesh_set_operator_cache(sn_mesh* mesh, int mode);
 
 /*
  * Test hook for the bounded waits of the dataflow schedule: the next sweep's items publish a

@@ -58,6 +58,7 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_mesh(sn_mesh* m) {
     if (!m) return;
     sn::drop_level_graphs(m);
+    sn::free_operator_cache(m);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     if (m->d_src) cudaFree(m->d_src);
     for (void* p : {(void*)m->d_dirs, (void*)m->d_wts, (void*)m->d_corners, (void*)m->d_sigma_t, (void*)m->d_sigma_s,
@@ -247,6 +248,7 @@ sn_status sn_set_materials(sn_mesh* m, const double* st, const double* ss, const
     sn::dsa_free(m->dsa);
     m->dsa = nullptr;
     m->dsa_key_dsa = -1;
+    m->ainv_valid = m->ainv32_valid = false;  // the cached inverses depend on sigma_t
     return SN_OK;
 }
 
@@ -280,6 +282,17 @@ sn_status sn_sweep(sn_mesh* m, const double* phi_in, double* phi_out, int precis
         CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
         if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out");
     }
+    return SN_OK;
+}
+
+sn_status sn_mesh_set_operator_cache(sn_mesh* m, int mode) {
+    if (!m) return fail(SN_ERR_ARG, "null mesh");
+    if (mode < SN_CACHE_OFF || mode > SN_CACHE_AUTO) return fail(SN_ERR_ARG, "bad cache mode %d", mode);
+    CK(cudaDeviceSynchronize(), "sync");  // no sweep may still read the buffers freed below
+    if (mode == SN_CACHE_OFF) sn::free_operator_cache(m);
+    m->ainv_denied = m->ainv32_denied = false;
+    m->cache_mode = mode;
+    sn::drop_level_graphs(m);
     return SN_OK;
 }
 
@@ -766,12 +779,13 @@ sn_status sn_batch_set_schedule(sn_batch* b, int schedule, int block, int max_bl
     return SN_OK;
 }
 
-static sn_status batch_prepare(sn_batch* b, int precision) {
+static sn_status batch_prepare(sn_batch* b, int precision, cudaStream_t s) {
     for (sn_mesh* m : b->meshes)
         if (precision == SN_FP32) {
             sn_status st = ensure_psi32(m);
             if (st != SN_OK) return st;
         }
+    CK(sn::batch_refresh_cache(b, precision, s), "operator cache");
     return SN_OK;
 }
 
@@ -789,9 +803,9 @@ static sn_status batch_timeout_check(sn_batch* b, cudaStream_t s) {
 sn_status sn_batch_sweep(sn_batch* b, const double* const* phi_in, double* const* phi_out, int precision, void* stream) {
     if (!b || !phi_out) return fail(SN_ERR_ARG, "null argument");
     if (precision < SN_FP64 || precision > SN_FP32_REFINE) return fail(SN_ERR_ARG, "bad precision");
-    sn_status st = batch_prepare(b, precision);
-    if (st != SN_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    sn_status st = batch_prepare(b, precision, s);
+    if (st != SN_OK) return st;
     for (int i = 0; i < b->count; ++i) {
         const size_t M = (size_t)b->meshes[i]->ne * b->meshes[i]->n;
         if (phi_in && phi_in[i])
@@ -858,7 +872,7 @@ sn_status sn_batch_source_iterate(sn_batch* b, const sn_iter_opts* o, double* co
     if (o->checkpoint_every > 0) return fail(SN_ERR_ARG, "checkpoints are not supported for batches");
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = batch_prepare(b, o->precision)) != SN_OK) return st;
+    if ((st = batch_prepare(b, o->precision, s)) != SN_OK) return st;
     if (o->dsa != SN_DSA_NONE && (st = batch_ensure_dsa(b, o)) != SN_OK) return st;
     for (int i = 0; i < b->count; ++i) {
         const size_t M = (size_t)b->meshes[i]->ne * b->meshes[i]->n;
@@ -1036,7 +1050,7 @@ sn_status sn_batch_autotune(sn_batch* b, int precision, void* stream, int* sched
     if (!b) return fail(SN_ERR_ARG, "null batch");
     if (precision < SN_FP64 || precision > SN_FP32_REFINE) return fail(SN_ERR_ARG, "bad precision");
     cudaStream_t s = (cudaStream_t)stream;
-    sn_status st = batch_prepare(b, precision);
+    sn_status st = batch_prepare(b, precision, s);
     if (st != SN_OK) return st;
     std::vector<int> ones(b->count, 1);
     CK(cudaMemcpyAsync(b->d_active, ones.data(), b->count * sizeof(int), cudaMemcpyHostToDevice, s), "copy");

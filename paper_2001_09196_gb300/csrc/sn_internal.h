@@ -52,7 +52,17 @@ struct SweepArgs {
     void* psi;                      // nd x ne x n, float64 or float32
     const int2* items;              // (dir, elem) sorted by level
     double q_scale;                 // multiplies q (1 normally, 0 for homogeneous solves)
+    const double* ainv;             // operator cache: nd x ne inverses A_e^{-1} (float64), or null
+    const float* ainv32;            // the same rounded to float32 (FP32 form), or null
+    const double* fflux;            // face flux factors beside the cache: 2D nd x ne x 4, 3D nd x 3 (b_x, b_y, b_z)
 };
+
+// Entries of one cached inverse: N*N rounded up to a multiple of 4 (16-byte vector loads).  The
+// inverse is stored column-major: entry (i, j) of A_e^{-1} at [j * N + i].
+inline int cache_stride(int dim, int p) {
+    const int q = p + 1, n = dim == 2 ? q * q : q * q * q;
+    return (n * n + 3) & ~3;
+}
 
 // Persistent dataflow sweep: padded work list and completion words.
 struct DataflowArgs {
@@ -87,6 +97,7 @@ struct UnionDsa;      // sn_batch.cu
 // Element families a batch can mix; a 32-item chunk of the batched work list never mixes them.
 enum { FAM_2D_P1 = 0, FAM_2D_P2 = 1, FAM_2D_P3 = 2, FAM_3D_P1 = 3, FAM_COUNT = 4 };
 inline int family_of(int dim, int p) { return dim == 3 ? FAM_3D_P1 : p - 1; }
+inline int family_nodes(int fam) { return fam == FAM_3D_P1 ? 8 : (fam + 2) * (fam + 2); }
 
 // Batched work item: instance, direction, element, family.
 struct BatchItem {
@@ -120,6 +131,12 @@ struct sn_mesh {
     int schedule = sn::SCHED_LEVELS;    // sweep schedule (see sn_mesh_set_schedule)
     int block = 128;                    // threads per block of the sweep kernels
     int max_blocks_per_sm = 0;          // 0: occupancy limit
+    int cache_mode = SN_CACHE_AUTO;     // operator cache (see sn_mesh_set_operator_cache)
+    double* d_ainv = nullptr;           // cached inverses, float64 (FP64 form and adjoint)
+    float* d_ainv32 = nullptr;          // cached inverses, float32 (FP32 form)
+    double* d_fflux = nullptr;          // face flux factors read with the cache (see SweepArgs::fflux)
+    bool ainv_valid = false, ainv32_valid = false;    // match the current materials
+    bool ainv_denied = false, ainv32_denied = false;  // AUTO mode found no room for them
     double* d_src = nullptr;            // ne x n source vector read by the graph-captured level launches
     cudaGraphExec_t level_graph[7] = {};  // level-schedule sweeps: FP64, FP32, refine, adjoint, and the
                                           // three forward kinds without the fixed source
@@ -151,6 +168,7 @@ struct sn_batch {
     int epoch = 0;
     int* d_active = nullptr;                 // per instance: 1 = still iterating
     int schedule = 0, block = 64, max_blocks_per_sm = 0;
+    bool cached = false;                     // every instance has an operator cache: node-per-lane kernels
     cudaGraphExec_t sweep_graph = nullptr;   // level schedule, all instances
     cudaGraphExec_t iter_graph = nullptr;    // one whole outer iteration
     cudaStream_t cap_stream = nullptr;
@@ -196,6 +214,9 @@ cudaError_t union_dsa_correct(UnionDsa* U, const double* r_all, double* phi_all,
 cudaError_t batch_enqueue_iteration(sn_batch* b, const sn_iter_opts* o, int* d_next, const int* d_dof_inst,
                                     cudaStream_t s);
 cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double q_scale, cudaStream_t s);
+cudaError_t prepare_operator_cache(sn_mesh* m, int precision, cudaStream_t s);
+void free_operator_cache(sn_mesh* m);
+cudaError_t batch_refresh_cache(sn_batch* b, int precision, cudaStream_t s);
 cudaError_t launch_adjoint_sweep(sn_mesh* m, const double* mu, cudaStream_t s);
 cudaError_t launch_phi_reduce(sn_mesh* m, int precision, const double* phi_in, double* phi_out, double* d_rr,
                               cudaStream_t s);

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 #include <vector>
 
@@ -36,6 +37,8 @@ __constant__ float c_wf[kMaxP + 1][kMaxP + 1];
 __constant__ float c_lmf[kMaxP + 1][kMaxP + 1];
 __constant__ float c_lpf[kMaxP + 1][kMaxP + 1];
 __constant__ float c_wdmf[kMaxP + 1][kMaxP + 1][kMaxP + 1];
+
+cudaError_t upload_face_coefficients();
 
 cudaError_t upload_gl_constants() {
     double x[kMaxP + 1][kMaxP + 1] = {}, w[kMaxP + 1][kMaxP + 1] = {}, lm[kMaxP + 1][kMaxP + 1] = {},
@@ -70,7 +73,8 @@ cudaError_t upload_gl_constants() {
     if ((err = cudaMemcpyToSymbol(c_wf, wf, sizeof(wf))) != cudaSuccess) return err;
     if ((err = cudaMemcpyToSymbol(c_lmf, lmf, sizeof(lmf))) != cudaSuccess) return err;
     if ((err = cudaMemcpyToSymbol(c_lpf, lpf, sizeof(lpf))) != cudaSuccess) return err;
-    return cudaMemcpyToSymbol(c_wdmf, wdmf, sizeof(wdmf));
+    if ((err = cudaMemcpyToSymbol(c_wdmf, wdmf, sizeof(wdmf))) != cudaSuccess) return err;
+    return upload_face_coefficients();
 }
 
 // Gauss-Legendre tables in the arithmetic type of a kernel.
@@ -434,6 +438,198 @@ __device__ __forceinline__ void lu_solve_transpose_s(const R* A, R* x) {
             if ((pat.rows[k] >> i) & 1u) x[i] -= A[k * N + i] * x[k];
 }
 
+// ---------------------------------------------------------------- operator cache
+// A_e depends on the direction, the element geometry and sigma_t only, so within a solve every
+// transport update would factor the same nd x ne matrices again.  The cache holds A_e^{-1} of
+// every (direction, element) pair, column-major (entry (i, j) at [j * N + i]), formed once per
+// change of materials by a fully parallel kernel; a cached sweep forms the right-hand side and
+// multiplies.  Beside it sit the face flux factors (2D: per pair; 3D: per direction), so that a
+// cached sweep needs no geometry.
+template <int DIM, int P>
+struct CacheShape {
+    static constexpr int N = Shape<DIM, P>::N;
+    static constexpr int S = (N * N + 3) & ~3;  // entries per cached inverse (16-byte multiple)
+};
+
+// A_e^{-1} of every (direction, element) pair, independent work: float64 assembly and unpivoted
+// LU (the factorisation the on-the-fly sweep uses), then column j = U^{-1} L^{-1} e_j stored
+// contiguously in type R, padding zeroed; the face flux factors are written beside it.
+template <int DIM, int P, typename R>
+__global__ void __launch_bounds__(128) factor_kernel(SweepArgs a, R* out, double* fflux) {
+    constexpr int N = CacheShape<DIM, P>::N, S = CacheShape<DIM, P>::S;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)a.nd * a.ne) return;
+    const int d = (int)(t / a.ne), e = (int)(t % a.ne);
+    ElemGeom<DIM, P, double> g;
+    elem_geom<DIM, P, double>(a, e, a.dirs[3 * d], a.dirs[3 * d + 1], a.dirs[3 * d + 2], g);
+    if (DIM == 2) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) fflux[t * 4 + f] = g.Fd[f];
+    } else if (e == 0) {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) fflux[3 * d + ax] = g.Fd[2 * ax + 1];
+    }
+    double A[N * N];
+    assemble<DIM, P, double>(g, a.sigma_t[e], A);
+    lu_factor_s<DIM, P, double>(A);
+    R* o = out + t * S;
+#pragma unroll 1
+    for (int j = 0; j < N; ++j) {
+        double x[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) x[i] = i == j ? 1.0 : 0.0;
+        lu_solve_s<DIM, P, double>(A, x);
+#pragma unroll
+        for (int i = 0; i < N; ++i) o[j * N + i] = (R)x[i];
+    }
+#pragma unroll
+    for (int k = N * N; k < S; ++k) o[k] = R(0);
+}
+
+// Face coefficients W_t l_side(i_a) of every node (i_a its index along the face normal axis, t
+// its tangential index) and face, per element family, in float64 and float32.
+__device__ double g_fcoef[FAM_COUNT][32][6];
+__device__ float g_fcoef32[FAM_COUNT][32][6];
+
+template <typename R>
+__device__ __forceinline__ R fcoef(int fam, int r, int f);
+template <>
+__device__ __forceinline__ double fcoef<double>(int fam, int r, int f) { return __ldg(&g_fcoef[fam][r][f]); }
+template <>
+__device__ __forceinline__ float fcoef<float>(int fam, int r, int f) { return __ldg(&g_fcoef32[fam][r][f]); }
+
+cudaError_t upload_face_coefficients() {
+    static double c[FAM_COUNT][32][6];
+    static float c32[FAM_COUNT][32][6];
+    for (int fam = 0; fam < FAM_COUNT; ++fam) {
+        const int dim = fam == FAM_3D_P1 ? 3 : 2, p = fam == FAM_3D_P1 ? 1 : fam + 1, Q = p + 1;
+        const int n = dim == 2 ? Q * Q : Q * Q * Q;
+        const GL1D g = gauss_legendre_nodal(p);
+        for (int r = 0; r < 32; ++r)
+            for (int f = 0; f < 6; ++f) {
+                double v = 0.0;
+                if (r < n && f < 2 * dim) {
+                    const int ri[3] = {r % Q, (r / Q) % Q, r / (Q * Q)};
+                    const int ax = f >> 1;
+                    const bool hi = f & 1;
+                    double wt = 1.0;
+                    for (int b = 0; b < dim; ++b)
+                        if (b != ax) wt *= g.w[ri[b]];
+                    v = wt * (hi ? g.lp[ri[ax]] : g.lm[ri[ax]]);
+                }
+                c[fam][r][f] = v;
+                c32[fam][r][f] = (float)v;
+            }
+    }
+    cudaError_t err = cudaMemcpyToSymbol(g_fcoef, c, sizeof(c));
+    if (err != cudaSuccess) return err;
+    return cudaMemcpyToSymbol(g_fcoef32, c32, sizeof(c32));
+}
+
+// Cached transport update with one lane per node: a warp holds 32 / N items, lane r of an item
+// forms row r of its right-hand side (source and the inflow terms through the faces of node r's
+// coordinate lines), the item's right-hand side is exchanged by shuffles and lane r writes
+// x_r = sum_j (A_e^{-1})_rj rhs_j.  An item's float64 work on the critical path is then about
+// 2N + 5 dim instructions instead of the ~(2/3) N^3 of a factorisation.  ADJ = true is the
+// transposed solve of the adjoint (outflow faces, downwind neighbours, A_e^{-T}).
+// Face flux factors of (direction d, element e) from the cache: the float64 values the level
+// sets were built from, so inflow/outflow decisions agree everywhere.
+template <int DIM>
+__device__ __forceinline__ void cached_fluxes(const SweepArgs& a, int d, int e, double* F) {
+    if constexpr (DIM == 2) {
+        const double2* fp = reinterpret_cast<const double2*>(a.fflux + ((size_t)d * a.ne + e) * 4);
+        const double2 v0 = __ldg(fp), v1 = __ldg(fp + 1);
+        F[0] = v0.x;
+        F[1] = v0.y;
+        F[2] = v1.x;
+        F[3] = v1.y;
+    } else {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const double b = __ldg(a.fflux + 3 * d + ax);
+            F[2 * ax] = -b;
+            F[2 * ax + 1] = b;
+        }
+    }
+}
+
+template <int DIM, int P, typename R, bool ADJ>
+__device__ __forceinline__ R node_rhs(const SweepArgs& a, const double* mu, int d, int e, int r) {
+    constexpr int Q = P + 1, N = Shape<DIM, P>::N;
+    constexpr int FAM = DIM == 3 ? FAM_3D_P1 : P - 1;
+    using K = GLT<R>;
+    double F[2 * DIM];
+    cached_fluxes<DIM>(a, d, e, F);
+    R rhs;
+    if constexpr (ADJ) {
+        rhs = (R)mu[(size_t)e * N + r];
+    } else {
+        const double ss = a.sigma_s[e], qe = a.q[e] * a.q_scale;
+        const double S = (qe + (a.phi ? ss * a.phi[(size_t)e * N + r] : 0.0)) * (1.0 / kFourPi);
+        rhs = (R)a.mass[(size_t)e * N + r] * (R)S;
+    }
+    const int ri[3] = {r % Q, (r / Q) % Q, r / (Q * Q)};
+    const R* psi = static_cast<const R*>(a.psi);
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f) {
+        if (ADJ ? !(F[f] > 0.0) : !(F[f] < 0.0)) continue;
+        const int ax = f >> 1;
+        const bool hi = f & 1;
+        const int u = neighbor<DIM, P>(a, e, f);
+        const int tt = DIM == 2 ? ri[1 - ax] : (ax == 0 ? ri[1] + Q * ri[2] : (ax == 1 ? ri[0] + Q * ri[2] : ri[0] + Q * ri[1]));
+        R tr;
+        if (u >= 0) {
+            const R* pu = psi + ((size_t)d * a.ne + u) * N;
+            tr = R(0);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) tr += (hi ? K::lm(P, k) : K::lp(P, k)) * __ldcg(pu + node_of<DIM, P>(ax, k, tt));
+        } else {
+            if (ADJ) continue;
+            tr = (R)a.psi_inc;
+        }
+        const R c = (ADJ ? (R)F[f] : -(R)F[f]) * fcoef<R>(FAM, r, f);
+        rhs += c * tr;
+    }
+    return rhs;
+}
+
+template <int DIM, int P, int MODE, bool ADJ>
+__device__ __forceinline__ void node_item(const SweepArgs& a, const double* mu, int d, int e, int r, int src0,
+                                          bool valid) {
+    using R = typename std::conditional<MODE == 1, float, double>::type;
+    constexpr int N = Shape<DIM, P>::N, S = CacheShape<DIM, P>::S;
+    const R rhs = valid ? node_rhs<DIM, P, R, ADJ>(a, mu, d, e, r) : R(0);
+    const R* inv;
+    if constexpr (MODE == 1) inv = a.ainv32;
+    else inv = a.ainv;
+    inv += ((size_t)d * a.ne + e) * S;
+    R x = R(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const R rj = __shfl_sync(0xffffffffu, rhs, src0 + j);
+        if (valid) x += __ldcs(inv + (ADJ ? r * N + j : j * N + r)) * rj;
+    }
+    if (valid) static_cast<R*>(a.psi)[((size_t)d * a.ne + e) * N + r] = x;
+}
+
+template <int DIM, int P, int MODE, bool ADJ>
+__global__ void __launch_bounds__(128) node_level_kernel(SweepArgs a, const double* mu, long long begin,
+                                                        long long end) {
+    constexpr int N = Shape<DIM, P>::N, IPW = 32 / N;
+    const int lane = threadIdx.x & 31;
+    const int slot = lane / N, r = lane - slot * N;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long t = begin + warp * IPW + slot;
+    const bool valid = slot < IPW && t < end;
+    int d = 0, e = 0;
+    if (valid) {
+        const int2 it = a.items[t];
+        d = it.x;
+        e = it.y;
+    }
+    node_item<DIM, P, MODE, ADJ>(a, mu, d, e, r, slot < IPW ? slot * N : 0, valid);
+}
+
 // Right-hand side in arithmetic type R: mass-weighted source S = (q + sigma_s phi)/(4 pi) (formed in
 // float64, then rounded to R) plus inflow face terms from the upwind neighbours' traces.
 template <int DIM, int P, typename RS, typename R>
@@ -630,6 +826,73 @@ __global__ void __launch_bounds__(128) sweep_dataflow_kernel(SweepArgs a, Datafl
             if constexpr (ADJ) adjoint_item<DIM, P>(a, mu, it.x, it.y);
             else solve_item<DIM, P, MODE>(a, it.x, it.y);
             st_release(f.done + (size_t)it.x * a.ne + it.y, f.publish);
+        }
+    }
+}
+
+// Bounded wait until every upwind (ADJ: downwind) neighbour of (d, e) holds the current epoch;
+// false when the deadline passed.  Face fluxes come from the operator cache.
+template <int DIM, int P, bool ADJ>
+__device__ __forceinline__ bool wait_neighbours(const SweepArgs& a, const int* done, int epoch, int d, int e,
+                                                unsigned long long deadline) {
+    double F[2 * DIM];
+    cached_fluxes<DIM>(a, d, e, F);
+#pragma unroll
+    for (int fc = 0; fc < 2 * DIM; ++fc) {
+        if (ADJ ? F[fc] > 0.0 : F[fc] < 0.0) {
+            const int u = neighbor<DIM, P>(a, e, fc);
+            if (u < 0) continue;
+            const int* flag = done + (size_t)d * a.ne + u;
+            int polls = 0;
+            while (ld_acquire(flag) != epoch) {
+                if (++polls > 64) {
+                    if (globaltimer() > deadline) return false;
+                    __nanosleep(64);
+                }
+            }
+        }
+    }
+    return true;
+}
+
+// Dataflow schedule of the cached sweep, one lane per node: a warp claims 32 / N items at a time
+// (a slice of a 32-item chunk of the padded list, so claims still follow level order), waits for
+// their neighbours, solves, synchronises, and each item's lane 0 fences and publishes the
+// completion word, so a waiter that acquires it sees all N lanes' angular fluxes.
+template <int DIM, int P, int MODE, bool ADJ>
+__global__ void __launch_bounds__(128) node_dataflow_kernel(SweepArgs a, DataflowArgs f, const double* mu) {
+    constexpr int N = Shape<DIM, P>::N, IPW = 32 / N, SLICES = (32 + IPW - 1) / IPW;
+    const int lane = threadIdx.x & 31;
+    const int slot = lane / N, r = lane - slot * N;
+    const int src0 = slot < IPW ? slot * N : 0;
+    const long long n_slices = (f.n_items >> 5) * SLICES;
+    const unsigned long long deadline = globaltimer() + f.timeout_ns;
+    while (true) {
+        unsigned long long c = 0;
+        int failed = 0;
+        if (lane == 0) {
+            c = atomicAdd(f.next, 1ull);
+            failed = *(volatile int*)f.error;
+        }
+        c = __shfl_sync(0xffffffffu, c, 0);
+        failed = __shfl_sync(0xffffffffu, failed, 0);
+        if ((long long)c >= n_slices || failed) break;
+        const long long chunk = (long long)c / SLICES;
+        const int k = (int)((long long)c - chunk * SLICES) * IPW + slot;
+        int2 it = make_int2(-1, -1);
+        if (slot < IPW && k < 32) it = f.items[(chunk << 5) + k];
+        const bool valid = it.x >= 0;
+        const int d = valid ? it.x : 0, e = valid ? it.y : 0;
+        const bool ok = valid ? wait_neighbours<DIM, P, ADJ>(a, f.done, f.epoch, d, e, deadline) : true;
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) atomicExch(f.error, 1);
+            break;
+        }
+        node_item<DIM, P, MODE, ADJ>(a, mu, d, e, r, src0, valid);
+        __syncwarp();
+        if (valid && r == 0) {
+            __threadfence();
+            st_release(f.done + (size_t)d * a.ne + e, f.publish);
         }
     }
 }
@@ -846,6 +1109,9 @@ static SweepArgs make_args(const sn_mesh* m) {
     a.items = m->levels.items;
     a.mass = m->d_mass;
     a.q_scale = 1.0;
+    a.ainv = m->cache_mode != SN_CACHE_OFF ? m->d_ainv : nullptr;
+    a.ainv32 = m->cache_mode != SN_CACHE_OFF ? m->d_ainv32 : nullptr;
+    a.fflux = m->d_fflux;
     return a;
 }
 
@@ -859,6 +1125,13 @@ static SweepArgs make_args(const sn_mesh* m) {
     } while (0)
 
 static inline unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// Blocks of bs threads for n items of the node-per-lane kernels (32 / N items per warp).
+static inline unsigned node_grid(const sn_mesh* m, long long n, int bs) {
+    const int ipw = 32 / m->n;
+    const long long warps = (n + ipw - 1) / ipw;
+    return grid_for(warps * 32, bs);
+}
 
 cudaError_t compute_mass(sn_mesh* m, cudaStream_t s) {
     SweepArgs a = make_args(m);
@@ -995,16 +1268,19 @@ static cudaError_t launch_dataflow(sn_mesh* m, const SweepArgs& a, cudaStream_t 
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_dataflow_kernel<DIM, P, MODE, ADJ>, m->block, 0);
+    const bool cached = MODE == 1 ? a.ainv32 != nullptr : (MODE == 0 && a.ainv != nullptr);
+    if (cached) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, node_dataflow_kernel<DIM, P, MODE == 1 ? 1 : 0, ADJ>, m->block, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_dataflow_kernel<DIM, P, MODE, ADJ>, m->block, 0);
     if (m->max_blocks_per_sm > 0 && m->max_blocks_per_sm < per_sm) per_sm = m->max_blocks_per_sm;
     per_sm = per_sm < 1 ? 1 : per_sm;
-    const long long warps_needed = L.n_padded / 32;
+    const long long warps_needed = cached ? (L.n_padded / 32) * ((32 + (32 / m->n) - 1) / (32 / m->n)) : L.n_padded / 32;
     long long blocks = (long long)sms * per_sm;
     const long long cap = (warps_needed * 32 + m->block - 1) / m->block;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     SN_COUNT_LAUNCH();
-    sweep_dataflow_kernel<DIM, P, MODE, ADJ><<<(unsigned)blocks, m->block, 0, s>>>(a, f, mu);
+    if (cached) node_dataflow_kernel<DIM, P, MODE == 1 ? 1 : 0, ADJ><<<(unsigned)blocks, m->block, 0, s>>>(a, f, mu);
+    else sweep_dataflow_kernel<DIM, P, MODE, ADJ><<<(unsigned)blocks, m->block, 0, s>>>(a, f, mu);
     return cudaGetLastError();
 }
 
@@ -1020,7 +1296,10 @@ static cudaError_t enqueue_levels(sn_mesh* m, int kind, cudaStream_t s) {
         for (int L = m->levels.n_levels - 1; L >= 0; --L) {
             const long long b = m->levels.level_ptr[L], e = m->levels.level_ptr[L + 1];
             if (e <= b) continue;
-            SN_DISPATCH(m->dim, m->p, (adjoint_level_kernel<D_, P_><<<grid_for(e - b, bs), bs, 0, s>>>(a, m->d_src, b, e)));
+            if (a.ainv)
+                SN_DISPATCH(m->dim, m->p, (node_level_kernel<D_, P_, 0, true><<<node_grid(m, e - b, bs), bs, 0, s>>>(a, m->d_src, b, e)));
+            else
+                SN_DISPATCH(m->dim, m->p, (adjoint_level_kernel<D_, P_><<<grid_for(e - b, bs), bs, 0, s>>>(a, m->d_src, b, e)));
         }
         return cudaGetLastError();
     }
@@ -1034,8 +1313,12 @@ static cudaError_t enqueue_levels(sn_mesh* m, int kind, cudaStream_t s) {
     for (int L = 0; L < m->levels.n_levels; ++L) {
         const long long b = m->levels.level_ptr[L], e = m->levels.level_ptr[L + 1];
         if (e <= b) continue;
-        const unsigned g = grid_for(e - b, bs);
-        if (kind == SN_FP64) SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 0><<<g, bs, 0, s>>>(a, b, e)));
+        const unsigned g = grid_for(e - b, bs), gn = node_grid(m, e - b, bs);
+        if (kind == SN_FP64 && a.ainv)
+            SN_DISPATCH(m->dim, m->p, (node_level_kernel<D_, P_, 0, false><<<gn, bs, 0, s>>>(a, nullptr, b, e)));
+        else if (kind == SN_FP32 && a.ainv32)
+            SN_DISPATCH(m->dim, m->p, (node_level_kernel<D_, P_, 1, false><<<gn, bs, 0, s>>>(a, nullptr, b, e)));
+        else if (kind == SN_FP64) SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 0><<<g, bs, 0, s>>>(a, b, e)));
         else if (kind == SN_FP32) SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 1><<<g, bs, 0, s>>>(a, b, e)));
         else SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 2><<<g, bs, 0, s>>>(a, b, e)));
     }
@@ -1071,7 +1354,100 @@ void drop_level_graphs(sn_mesh* m) {
         }
 }
 
+cudaError_t prepare_operator_cache(sn_mesh* m, int precision, cudaStream_t s) {
+    if (m->cache_mode == SN_CACHE_OFF || precision == SN_FP32_REFINE) return cudaSuccess;
+    const bool f32 = precision == SN_FP32;
+    void** buf = f32 ? reinterpret_cast<void**>(&m->d_ainv32) : reinterpret_cast<void**>(&m->d_ainv);
+    bool& valid = f32 ? m->ainv32_valid : m->ainv_valid;
+    bool& denied = f32 ? m->ainv32_denied : m->ainv_denied;
+    const long long total = (long long)m->nd * m->ne;
+    cudaError_t err;
+    if (!*buf) {
+        if (denied) return cudaSuccess;
+        const size_t bytes = (size_t)total * cache_stride(m->dim, m->p) * (f32 ? sizeof(float) : sizeof(double));
+        size_t free_b = 0, total_b = 0;
+        if ((err = cudaMemGetInfo(&free_b, &total_b)) != cudaSuccess) return err;
+        if (m->cache_mode == SN_CACHE_AUTO && bytes > free_b / 2) {
+            denied = true;
+            return cudaSuccess;
+        }
+        if ((err = cudaMalloc(buf, bytes)) != cudaSuccess) {
+            *buf = nullptr;
+            if (m->cache_mode != SN_CACHE_AUTO) return err;
+            cudaGetLastError();  // out of memory is not sticky: fall back to on-the-fly solves
+            denied = true;
+            return cudaSuccess;
+        }
+        if (!m->d_fflux) {
+            const size_t fb = (m->dim == 2 ? (size_t)total * 4 : (size_t)m->nd * 3) * sizeof(double);
+            if ((err = cudaMalloc(&m->d_fflux, fb)) != cudaSuccess) {
+                m->d_fflux = nullptr;
+                cudaFree(*buf);
+                *buf = nullptr;
+                if (m->cache_mode != SN_CACHE_AUTO) return err;
+                cudaGetLastError();
+                denied = true;
+                return cudaSuccess;
+            }
+        }
+        drop_level_graphs(m);  // captured launches carry the cache pointers
+        valid = false;
+    }
+    if (!valid) {
+        SweepArgs a = make_args(m);
+        SN_COUNT_LAUNCH();
+        if (f32)
+            SN_DISPATCH(m->dim, m->p, (factor_kernel<D_, P_, float><<<grid_for(total, 128), 128, 0, s>>>(a, m->d_ainv32, m->d_fflux)));
+        else
+            SN_DISPATCH(m->dim, m->p, (factor_kernel<D_, P_, double><<<grid_for(total, 128), 128, 0, s>>>(a, m->d_ainv, m->d_fflux)));
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        valid = true;
+    }
+    return cudaSuccess;
+}
+
+void free_operator_cache(sn_mesh* m) {
+    if (m->d_ainv) cudaFree(m->d_ainv);
+    if (m->d_ainv32) cudaFree(m->d_ainv32);
+    if (m->d_fflux) cudaFree(m->d_fflux);
+    m->d_ainv = nullptr;
+    m->d_ainv32 = nullptr;
+    m->d_fflux = nullptr;
+    m->ainv_valid = m->ainv32_valid = false;
+}
+
+// Brings every instance's cached inverses up to date and points the batch's argument table at
+// them.  The batch runs the cached (node-per-lane) kernels only when every instance has a cache
+// for this precision; a change of that choice drops the recorded graphs.
+cudaError_t batch_refresh_cache(sn_batch* b, int precision, cudaStream_t s) {
+    bool changed = false, all = precision != SN_FP32_REFINE;
+    for (int i = 0; i < b->count; ++i) {
+        sn_mesh* m = b->meshes[i];
+        cudaError_t err = prepare_operator_cache(m, precision, s);
+        if (err != cudaSuccess) return err;
+        const SweepArgs fresh = make_args(m);
+        all = all && (precision == SN_FP32 ? fresh.ainv32 != nullptr : fresh.ainv != nullptr);
+        if (fresh.ainv != b->h_args[i].ainv || fresh.ainv32 != b->h_args[i].ainv32 || fresh.fflux != b->h_args[i].fflux) {
+            b->h_args[i].ainv = fresh.ainv;
+            b->h_args[i].ainv32 = fresh.ainv32;
+            b->h_args[i].fflux = fresh.fflux;
+            changed = true;
+        }
+    }
+    if (all != b->cached) {
+        b->cached = all;
+        if (b->sweep_graph) cudaGraphExecDestroy(b->sweep_graph);
+        if (b->iter_graph) cudaGraphExecDestroy(b->iter_graph);
+        b->sweep_graph = b->iter_graph = nullptr;
+    }
+    // the kernels read the table from device memory, so recorded graphs stay valid
+    if (!changed) return cudaSuccess;
+    return cudaMemcpyAsync(b->d_args, b->h_args.data(), b->count * sizeof(SweepArgs), cudaMemcpyHostToDevice, s);
+}
+
 cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double q_scale, cudaStream_t s) {
+    cudaError_t cerr = prepare_operator_cache(m, precision, s);
+    if (cerr != cudaSuccess) return cerr;
     SweepArgs a = make_args(m);
     a.phi = phi_in;
     a.q_scale = q_scale;
@@ -1090,6 +1466,8 @@ cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double
 }
 
 cudaError_t launch_adjoint_sweep(sn_mesh* m, const double* mu, cudaStream_t s) {
+    cudaError_t cerr = prepare_operator_cache(m, SN_FP64, s);
+    if (cerr != cudaSuccess) return cerr;
     SweepArgs a = make_args(m);
     a.psi = m->d_lambda;
     if (m->schedule == SCHED_DATAFLOW) {
@@ -1155,6 +1533,90 @@ __device__ __forceinline__ bool batch_chunk(const SweepArgs* args, const BatchIt
     if (!__all_sync(0xffffffffu, ok)) return false;
     batch_chunk_item<DIM, P, MODE>(args, it, active, done, done_off, epoch, deadline, true);
     return true;
+}
+
+// Cached batched sweeps, one lane per node (the arithmetic of node_item, so a batched sweep
+// equals the single-mesh sweeps bit for bit).  Level schedule: a warp takes 32 / N consecutive
+// items of a (level, family) segment.
+template <int DIM, int P, int MODE>
+__global__ void __launch_bounds__(128) batch_node_level_kernel(const SweepArgs* args, const BatchItem* items,
+                                                              long long begin, long long end, const int* active) {
+    constexpr int N = Shape<DIM, P>::N, IPW = 32 / N;
+    const int lane = threadIdx.x & 31;
+    const int slot = lane / N, r = lane - slot * N;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long t = begin + warp * IPW + slot;
+    BatchItem it{-1, 0, 0, 0};
+    if (slot < IPW && t < end) it = items[t];
+    const bool valid = it.inst >= 0 && active[it.inst];
+    node_item<DIM, P, MODE, false>(args[valid ? it.inst : 0], nullptr, valid ? it.dir : 0, valid ? it.elem : 0, r,
+                                   slot < IPW ? slot * N : 0, valid);
+}
+
+// Dataflow schedule: a warp claims a 32-item chunk (one family, one level) and runs it in rounds
+// of 32 / N items (one claim per chunk keeps the shared counter's traffic low for large batches).
+template <int DIM, int P, int MODE>
+__device__ __forceinline__ bool batch_node_chunk(const SweepArgs* args, const BatchItem* items, long long chunk,
+                                                 const int* active, int* done, const long long* done_off, int epoch,
+                                                 unsigned long long deadline) {
+    constexpr int N = Shape<DIM, P>::N, IPW = 32 / N, ROUNDS = (32 + IPW - 1) / IPW;
+    const int lane = threadIdx.x & 31;
+    const int slot = lane / N, r = lane - slot * N;
+    const int src0 = slot < IPW ? slot * N : 0;
+#pragma unroll 1
+    for (int round = 0; round < ROUNDS; ++round) {
+        const int k = round * IPW + slot;
+        BatchItem it{-1, 0, 0, 0};
+        if (slot < IPW && k < 32) it = items[(chunk << 5) + k];
+        const bool valid = it.inst >= 0 && active[it.inst];
+        const int inst = valid ? it.inst : 0, d = valid ? it.dir : 0, e = valid ? it.elem : 0;
+        const SweepArgs& a = args[inst];
+        int* dn = done + done_off[inst];
+        const bool ok = valid ? wait_neighbours<DIM, P, false>(a, dn, epoch, d, e, deadline) : true;
+        if (!__all_sync(0xffffffffu, ok)) return false;
+        node_item<DIM, P, MODE, false>(a, nullptr, d, e, r, src0, valid);
+        __syncwarp();
+        if (valid && r == 0) {
+            __threadfence();
+            st_release(dn + (size_t)d * a.ne + e, epoch);
+        }
+    }
+    return true;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) batch_node_dataflow_kernel(const SweepArgs* args, const BatchItem* items,
+                                                                 const int* chunk_fam, long long n_items, int* done,
+                                                                 const long long* done_off, const int* epoch_ptr,
+                                                                 unsigned long long* ctrl, const int* active,
+                                                                 unsigned long long timeout_ns) {
+    const int lane = threadIdx.x & 31;
+    const long long n_chunks = n_items >> 5;
+    const int epoch = *epoch_ptr;
+    const unsigned long long deadline = globaltimer() + timeout_ns;
+    int* error = reinterpret_cast<int*>(ctrl + 1);
+    while (true) {
+        unsigned long long c = 0;
+        int failed = 0;
+        if (lane == 0) {
+            c = atomicAdd(ctrl, 1ull);
+            failed = *(volatile int*)error;
+        }
+        c = __shfl_sync(0xffffffffu, c, 0);
+        failed = __shfl_sync(0xffffffffu, failed, 0);
+        if ((long long)c >= n_chunks || failed) break;
+        bool ok;
+        switch (chunk_fam[c]) {  // uniform across the warp
+            case FAM_2D_P1: ok = batch_node_chunk<2, 1, MODE>(args, items, c, active, done, done_off, epoch, deadline); break;
+            case FAM_2D_P2: ok = batch_node_chunk<2, 2, MODE>(args, items, c, active, done, done_off, epoch, deadline); break;
+            case FAM_2D_P3: ok = batch_node_chunk<2, 3, MODE>(args, items, c, active, done, done_off, epoch, deadline); break;
+            default: ok = batch_node_chunk<3, 1, MODE>(args, items, c, active, done, done_off, epoch, deadline); break;
+        }
+        if (!ok) {
+            if (lane == 0) atomicExch(error, 1);
+            break;
+        }
+    }
 }
 
 template <int MODE>
@@ -1290,11 +1752,23 @@ cudaError_t batch_enqueue_sweep(sn_batch* b, int precision, cudaStream_t s) {
         else if (fam == FAM_2D_P3) batch_level_kernel<2, 3, MODE_><<<g, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active); \
         else batch_level_kernel<3, 1, MODE_><<<g, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active);       \
     } while (0)
+#define SN_BATCH_NODE(MODE_)                                                                                    \
+    do {                                                                                                      \
+        const unsigned gn = grid_for(((hi - lo + ipw - 1) / ipw) * 32, bs);                                   \
+        if (fam == FAM_2D_P1) batch_node_level_kernel<2, 1, MODE_><<<gn, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active); \
+        else if (fam == FAM_2D_P2) batch_node_level_kernel<2, 2, MODE_><<<gn, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active); \
+        else if (fam == FAM_2D_P3) batch_node_level_kernel<2, 3, MODE_><<<gn, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active); \
+        else batch_node_level_kernel<3, 1, MODE_><<<gn, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active); \
+    } while (0)
         SN_COUNT_LAUNCH();
-        if (precision == SN_FP64) SN_BATCH_LEVEL(0);
+        const int ipw = 32 / family_nodes(fam);
+        if (precision == SN_FP64 && b->cached) SN_BATCH_NODE(0);
+        else if (precision == SN_FP32 && b->cached) SN_BATCH_NODE(1);
+        else if (precision == SN_FP64) SN_BATCH_LEVEL(0);
         else if (precision == SN_FP32) SN_BATCH_LEVEL(1);
         else SN_BATCH_LEVEL(2);
 #undef SN_BATCH_LEVEL
+#undef SN_BATCH_NODE
     }
     return cudaGetLastError();
 }
@@ -1314,7 +1788,10 @@ cudaError_t batch_launch_dataflow(sn_batch* b, int precision, cudaStream_t s) {
     int dev = 0, sms = 0, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (precision == SN_FP64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_dataflow_kernel<0>, b->block, 0);
+    const bool node = b->cached && precision != SN_FP32_REFINE;
+    if (node && precision == SN_FP64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_node_dataflow_kernel<0>, b->block, 0);
+    else if (node) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_node_dataflow_kernel<1>, b->block, 0);
+    else if (precision == SN_FP64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_dataflow_kernel<0>, b->block, 0);
     else if (precision == SN_FP32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_dataflow_kernel<1>, b->block, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_dataflow_kernel<2>, b->block, 0);
     if (b->max_blocks_per_sm > 0 && b->max_blocks_per_sm < per_sm) per_sm = b->max_blocks_per_sm;
@@ -1324,7 +1801,15 @@ cudaError_t batch_launch_dataflow(sn_batch* b, int precision, cudaStream_t s) {
     const unsigned long long timeout = 4000000000ull;
     const int* epoch = reinterpret_cast<const int*>(b->d_ctrl + 2);
     SN_COUNT_LAUNCH();
-    if (precision == SN_FP64)
+    if (node && precision == SN_FP64)
+        batch_node_dataflow_kernel<0><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam, b->n_items,
+                                                                           b->d_done, b->d_done_off, epoch, b->d_ctrl,
+                                                                           b->d_active, timeout);
+    else if (node)
+        batch_node_dataflow_kernel<1><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam, b->n_items,
+                                                                           b->d_done, b->d_done_off, epoch, b->d_ctrl,
+                                                                           b->d_active, timeout);
+    else if (precision == SN_FP64)
         batch_dataflow_kernel<0><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam, b->n_items,
                                                                       b->d_done, b->d_done_off, epoch, b->d_ctrl,
                                                                       b->d_active, timeout);

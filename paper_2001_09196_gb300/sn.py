@@ -78,6 +78,7 @@ def _load():
         "sn_dsa_solve": [vp, C.POINTER(IterOpts), vp, vp, C.POINTER(C.c_int), vp],
         "sn_get_angular_flux": [vp, i, i, i, vp, vp],
         "sn_mesh_set_schedule": [vp, i, i, i],
+        "sn_mesh_set_operator_cache": [vp, i],
         "sn_debug_stall_next_sweep": [vp, d],
         "sn_scalar_flux_noalloc": [vp, vp, i, C.c_longlong, vp, vp, vp, vp],
         "sn_batch_create": [vp, i, C.POINTER(vp)],
@@ -223,6 +224,11 @@ class Mesh:
     def set_schedule(self, schedule="dataflow", block=128, max_blocks_per_sm=0):
         sched = {"levels": 0, "dataflow": 1}[schedule] if isinstance(schedule, str) else int(schedule)
         _check(_lib.sn_mesh_set_schedule(self._h, sched, int(block), int(max_blocks_per_sm)))
+
+    def set_operator_cache(self, mode="auto"):
+        """Cache every element operator's inverse between sweeps: "off", "on" or "auto"."""
+        m = {"off": 0, "on": 1, "auto": 2}[mode] if isinstance(mode, str) else int(mode)
+        _check(_lib.sn_mesh_set_operator_cache(self._h, m))
 
     def debug_stall_next_sweep(self, timeout_s=0.2):
         _check(_lib.sn_debug_stall_next_sweep(self._h, float(timeout_s)))

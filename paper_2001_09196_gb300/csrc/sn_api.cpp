@@ -437,11 +437,8 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
             double* Vj = V + (size_t)j * M;
             double* Zj = Z + (size_t)j * M;
             CK(sn::launch_copy(Zj, Vj, M, s), "copy");
-            if (o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0) {
-                int its = 0;
-                CK(sn::dsa_correct(m->dsa, Vj, Zj, o->inner_tol, o->inner_max_iters, adjoint, &its, s), "DSA");
-                inner_total += its;
-            }
+            if (o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0)
+                CK(sn::dsa_correct(m->dsa, Vj, Zj, o->inner_tol, o->inner_max_iters, adjoint, s), "DSA");
             // w = S Zj = Zj - T Zj (T: sweep without the fixed source)
             if (adjoint) {
                 CK(sn::launch_adjoint_sweep(m, Zj, s), "adjoint sweep");
@@ -497,6 +494,7 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
         // the restart (or the final check) recomputes the true residual with one more sweep
     }
     CK(cudaStreamSynchronize(s), "sync");
+    if (m->dsa) CK(sn::dsa_take_iters(m->dsa, s, &inner_total), "DSA iterations");
     if (stats) {
         stats->iters = it;
         stats->rel_residual = rel;
@@ -518,6 +516,10 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
     cudaStream_t s = (cudaStream_t)stream;
     if (o->precision == SN_FP32 && (st = ensure_psi32(m)) != SN_OK) return st;
     if (o->dsa != SN_DSA_NONE && (st = ensure_dsa(m, o)) != SN_OK) return st;
+    if (m->dsa) {  // the PCG iteration counter starts from zero for this solve
+        int stale = 0;
+        CK(sn::dsa_take_iters(m->dsa, (cudaStream_t)stream, &stale), "DSA iterations");
+    }
     if (o->outer == SN_OUTER_FGMRES) {
         if (!o->warm_start) CK(cudaMemsetAsync(phi, 0, (size_t)m->ne * m->n * sizeof(double), s), "memset");
         return fgmres(m, o, phi, stats, s, t0);
@@ -547,9 +549,7 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
         if (o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0) {
             CK(sn::launch_axpy_norm(m, half, phi, r, m->d_scalars + 1, s), "residual");
             CK(sn::launch_copy(phi, half, M, s), "copy");
-            int its = 0;
-            CK(sn::dsa_correct(m->dsa, r, phi, o->inner_tol, o->inner_max_iters, false, &its, s), "DSA");
-            inner_total += its;
+            CK(sn::dsa_correct(m->dsa, r, phi, o->inner_tol, o->inner_max_iters, false, s), "DSA");
         } else {
             CK(sn::launch_copy(phi, half, M, s), "copy");
         }
@@ -564,6 +564,7 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
         }
     }
     CK(cudaStreamSynchronize(s), "sync");
+    if (m->dsa) CK(sn::dsa_take_iters(m->dsa, s, &inner_total), "DSA iterations");
     if (stats) {
         stats->iters = it;
         stats->rel_residual = rel;
@@ -601,6 +602,10 @@ sn_status sn_adjoint_iterate(sn_mesh* m, const sn_iter_opts* o, const double* g,
     if (st != SN_OK) return st;
     if ((st = ensure_lambda(m)) != SN_OK) return st;
     if (o->dsa != SN_DSA_NONE && (st = ensure_dsa(m, o)) != SN_OK) return st;
+    if (m->dsa) {  // the PCG iteration counter starts from zero for this solve
+        int stale = 0;
+        CK(sn::dsa_take_iters(m->dsa, (cudaStream_t)stream, &stale), "DSA iterations");
+    }
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
     const size_t M = (size_t)m->ne * m->n;
@@ -632,9 +637,7 @@ sn_status sn_adjoint_iterate(sn_mesh* m, const sn_iter_opts* o, const double* g,
         if (stats && stats->residual_history && it < stats->history_len) stats->residual_history[it] = rel;
         CK(sn::launch_copy(mu, half, M, s), "copy");
         if (o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0) {
-            int its = 0;
-            CK(sn::dsa_correct(m->dsa, r, mu, o->inner_tol, o->inner_max_iters, true, &its, s), "DSA");
-            inner_total += its;
+            CK(sn::dsa_correct(m->dsa, r, mu, o->inner_tol, o->inner_max_iters, true, s), "DSA");
         }
         ++it;
         if (rel <= o->tol) {
@@ -643,6 +646,7 @@ sn_status sn_adjoint_iterate(sn_mesh* m, const sn_iter_opts* o, const double* g,
         }
     }
     CK(cudaStreamSynchronize(s), "sync");
+    if (m->dsa) CK(sn::dsa_take_iters(m->dsa, s, &inner_total), "DSA iterations");
     if (stats) {
         stats->iters = it;
         stats->rel_residual = rel;
@@ -683,7 +687,9 @@ sn_status sn_dsa_solve(sn_mesh* m, const sn_iter_opts* o, const double* b, doubl
     sn_status st = ensure_dsa(m, &oo);
     if (st != SN_OK) return st;
     int its = 0;
-    CK(sn::dsa_solve(m->dsa, b, x, oo.inner_tol, oo.inner_max_iters, &its, (cudaStream_t)stream), "DSA solve");
+    CK(sn::dsa_take_iters(m->dsa, (cudaStream_t)stream, &its), "DSA iterations");  // drop earlier counts
+    CK(sn::dsa_solve(m->dsa, b, x, oo.inner_tol, oo.inner_max_iters, (cudaStream_t)stream), "DSA solve");
+    CK(sn::dsa_take_iters(m->dsa, (cudaStream_t)stream, &its), "DSA iterations");
     if (iters) *iters = its;
     return SN_OK;
 }

@@ -139,6 +139,22 @@ __global__ void cg_update_p(double* p, const double* z, long long n, const doubl
 
 __global__ void copy_scalar(double* s, int dst, int src) { s[dst] = s[src]; }
 
+// Start of the recorded PCG: s[0] (r.z of the previous iteration) = +inf makes the first search
+// direction p = z; the loop runs only for b != 0.
+__global__ void pcg_start_kernel(double* s, int* it, cudaGraphConditionalHandle h) {
+    s[0] = INFINITY;
+    it[0] = 0;
+    cudaGraphSetConditional(h, s[3] > 0.0 ? 1u : 0u);
+}
+
+// End of one recorded PCG iteration: continue while ||r|| > tol ||b|| and fewer than max_iters.
+__global__ void pcg_check_kernel(const double* s, int* it, double tol, int max_iters, cudaGraphConditionalHandle h) {
+    const int k = ++it[0];
+    ++it[1];
+    const bool more = sqrt(s[2]) > tol * sqrt(s[3]) && k < max_iters;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 constexpr int kDotBlocks = 304;  // 2 x 152 SMs
 
 template <typename T>
@@ -180,6 +196,8 @@ cudaError_t upload(DsaHierarchy* H) {
         if ((err = cudaMalloc(v, std::max<long long>(1, N0) * sizeof(double))) != cudaSuccess) return err;
     if ((err = cudaMalloc(&H->d_part, kDotBlocks * sizeof(double))) != cudaSuccess) return err;
     if ((err = cudaMalloc(&H->d_s, 16 * sizeof(double))) != cudaSuccess) return err;
+    if ((err = cudaMalloc(&H->d_it, 2 * sizeof(int))) != cudaSuccess) return err;
+    if ((err = cudaMemset(H->d_it, 0, 2 * sizeof(int))) != cudaSuccess) return err;
     H->uploaded = true;
     return cudaSuccess;
 }
@@ -261,43 +279,105 @@ void vcycle0(DsaHierarchy* H, const double* r, double* z, cudaStream_t s) {
     }
 }
 
-// Solve D_ff x = b (thick-local vectors H->d_b -> H->d_x) by PCG.
-cudaError_t pcg(DsaHierarchy* H, double tol, int max_iters, int* iters, cudaStream_t s) {
+// Records PCG on D_ff x = b (thick-local vectors H->d_b -> H->d_x) into a CUDA graph: a prologue
+// (x = 0, p = 0, r = b, b.b, start) and a WHILE conditional node whose body is one iteration
+//   z = V(r); rz = r.z; p = z + (rz / rz_prev) p; q = A p; alpha = rz / p.q;
+//   x += alpha p; r -= alpha q; continue while ||r|| > tol ||b|| and k < max_iters.
+// This is the preconditioned CG of the eager form step for step; the convergence test runs on
+// the device, so a solve is one graph launch.
+cudaError_t record_pcg(DsaHierarchy* H, double tol, int max_iters) {
     const long long N0 = (long long)H->nt * H->n;
     const Level0& A = H->l0;
     cudaError_t err;
-    *iters = 0;
-    cudaMemsetAsync(H->d_x, 0, N0 * sizeof(double), s);
-    cudaMemcpyAsync(H->d_r, H->d_b, N0 * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    dot(H, H->d_b, H->d_b, N0, 3, s);
-    double h[16];
-    if ((err = cudaMemcpyAsync(h, H->d_s, 16 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return err;
-    if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
-    const double bnorm = std::sqrt(h[3]);
-    if (bnorm == 0.0) return cudaSuccess;
+    if (!H->cap && (err = cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking)) != cudaSuccess) return err;
+    if (!H->cap2 && (err = cudaStreamCreateWithFlags(&H->cap2, cudaStreamNonBlocking)) != cudaSuccess) return err;
+    if (H->pcg_graph) cudaGraphExecDestroy(H->pcg_graph);
+    H->pcg_graph = nullptr;
+    const long long count0 = g_launches.load();
+    if ((err = cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return err;
+    cudaGraph_t g = nullptr, body = nullptr;
+    bool body_open = false;
+    auto finish = [&](cudaError_t e) -> cudaError_t {
+        if (body_open) {
+            cudaGraph_t b2 = nullptr;
+            cudaStreamEndCapture(H->cap2, &b2);
+        }
+        cudaGraph_t g2 = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(H->cap, &g2);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&H->pcg_graph, g2, 0);
+        if (g2) cudaGraphDestroy(g2);
+        if (e != cudaSuccess) H->pcg_graph = nullptr;
+        return e;
+    };
+    cudaStreamCaptureStatus cs;
+    if ((err = cudaStreamGetCaptureInfo(H->cap, &cs, nullptr, &g, nullptr, nullptr, nullptr)) != cudaSuccess)
+        return finish(err);
+    cudaGraphConditionalHandle h;
+    if ((err = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return finish(err);
+    cudaMemsetAsync(H->d_x, 0, N0 * sizeof(double), H->cap);
+    cudaMemsetAsync(H->d_p, 0, N0 * sizeof(double), H->cap);
+    cudaMemcpyAsync(H->d_r, H->d_b, N0 * sizeof(double), cudaMemcpyDeviceToDevice, H->cap);
+    dot(H, H->d_b, H->d_b, N0, 3, H->cap);
+    SN_COUNT_LAUNCH();
+    pcg_start_kernel<<<1, 1, 0, H->cap>>>(H->d_s, H->d_it, h);
+    H->pro_launches = g_launches.load() - count0;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    if ((err = cudaStreamGetCaptureInfo(H->cap, &cs, nullptr, nullptr, &deps, nullptr, &ndeps)) != cudaSuccess)
+        return finish(err);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    if ((err = cudaGraphAddNode(&loop, g, deps, nullptr, ndeps, &cp)) != cudaSuccess) return finish(err);
+    if ((err = cudaStreamUpdateCaptureDependencies(H->cap, &loop, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+        return finish(err);
+    body = cp.conditional.phGraph_out[0];
+    if ((err = cudaStreamBeginCaptureToGraph(H->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return finish(err);
+    body_open = true;
+    const long long count1 = g_launches.load();
+    cudaStream_t s = H->cap2;
     vcycle0(H, H->d_r, H->d_z, s);
-    cudaMemcpyAsync(H->d_p, H->d_z, N0 * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    dot(H, H->d_r, H->d_z, N0, 0, s);
-    for (int k = 1; k <= max_iters; ++k) {
-        SN_COUNT_LAUNCH();
-        bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, H->nt, H->n, H->d_p, nullptr, H->d_q);
-        dot(H, H->d_p, H->d_q, N0, 1, s);
-        SN_COUNT_LAUNCH();
-        cg_update_xr<<<nblk(N0), kBS, 0, s>>>(H->d_x, H->d_r, H->d_p, H->d_q, N0, H->d_s);
-        dot(H, H->d_r, H->d_r, N0, 2, s);
-        double rr;
-        if ((err = cudaMemcpyAsync(&rr, H->d_s + 2, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return err;
-        if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
-        *iters = k;
-        if (!(std::sqrt(rr) > tol * bnorm)) break;
-        vcycle0(H, H->d_r, H->d_z, s);
-        dot(H, H->d_r, H->d_z, N0, 4, s);
-        SN_COUNT_LAUNCH();
-        cg_update_p<<<nblk(N0), kBS, 0, s>>>(H->d_p, H->d_z, N0, H->d_s);
-        SN_COUNT_LAUNCH();
-        copy_scalar<<<1, 1, 0, s>>>(H->d_s, 0, 4);
+    dot(H, H->d_r, H->d_z, N0, 4, s);
+    SN_COUNT_LAUNCH();
+    cg_update_p<<<nblk(N0), kBS, 0, s>>>(H->d_p, H->d_z, N0, H->d_s);
+    SN_COUNT_LAUNCH();
+    copy_scalar<<<1, 1, 0, s>>>(H->d_s, 0, 4);
+    SN_COUNT_LAUNCH();
+    bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, H->nt, H->n, H->d_p, nullptr, H->d_q);
+    dot(H, H->d_p, H->d_q, N0, 1, s);
+    SN_COUNT_LAUNCH();
+    cg_update_xr<<<nblk(N0), kBS, 0, s>>>(H->d_x, H->d_r, H->d_p, H->d_q, N0, H->d_s);
+    dot(H, H->d_r, H->d_r, N0, 2, s);
+    SN_COUNT_LAUNCH();
+    pcg_check_kernel<<<1, 1, 0, s>>>(H->d_s, H->d_it, tol, max_iters, h);
+    H->body_launches = g_launches.load() - count1;
+    g_launches.store(count0);  // recorded, not run: launches are counted when the graph runs
+    if ((err = cudaGetLastError()) != cudaSuccess) return finish(err);
+    cudaGraph_t b2 = nullptr;
+    err = cudaStreamEndCapture(H->cap2, &b2);
+    body_open = false;
+    if (err != cudaSuccess) return finish(err);
+    err = finish(cudaSuccess);
+    if (err == cudaSuccess) {
+        H->pcg_tol = tol;
+        H->pcg_max = max_iters;
     }
-    return cudaGetLastError();
+    return err;
+}
+
+// Solves D_ff x = b by one launch of the recorded PCG; the iteration count stays on the device
+// (dsa_take_iters reads the running total).
+cudaError_t pcg(DsaHierarchy* H, double tol, int max_iters, cudaStream_t s) {
+    cudaError_t err;
+    if (!H->pcg_graph || H->pcg_tol != tol || H->pcg_max != max_iters)
+        if ((err = record_pcg(H, tol, max_iters)) != cudaSuccess) return err;
+    g_launches.fetch_add(H->pro_launches, std::memory_order_relaxed);
+    return cudaGraphLaunch(H->pcg_graph, s);
 }
 
 }  // namespace
@@ -312,7 +392,10 @@ void dsa_free(DsaHierarchy* H) {
         f(L.d_r_ptr); f(L.d_r_col); f(L.d_r_val); f(L.d_dinv); f(L.d_dense); f(L.d_x); f(L.d_b); f(L.d_r);
     }
     f(H->d_x); f(H->d_b); f(H->d_r); f(H->d_z); f(H->d_p); f(H->d_q); f(H->d_vr); f(H->d_vx);
-    f(H->d_part); f(H->d_s);
+    f(H->d_part); f(H->d_s); f(H->d_it);
+    if (H->pcg_graph) cudaGraphExecDestroy(H->pcg_graph);
+    if (H->cap) cudaStreamDestroy(H->cap);
+    if (H->cap2) cudaStreamDestroy(H->cap2);
     delete H;
 }
 
@@ -333,17 +416,15 @@ cudaError_t dsa_apply(DsaHierarchy* H, const double* x, double* y, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t dsa_solve(DsaHierarchy* H, const double* b_full, double* x_full, double tol, int max_iters, int* iters,
-                      cudaStream_t s) {
+cudaError_t dsa_solve(DsaHierarchy* H, const double* b_full, double* x_full, double tol, int max_iters, cudaStream_t s) {
     cudaError_t err = upload(H);
     if (err != cudaSuccess) return err;
     cudaMemsetAsync(x_full, 0, (size_t)H->ne * H->n * sizeof(double), s);
-    *iters = 0;
     if (H->nt == 0) return cudaGetLastError();
     const long long N0 = (long long)H->nt * H->n;
     SN_COUNT_LAUNCH();
     gather_kernel<<<nblk(N0), kBS, 0, s>>>(b_full, H->d_thick, nullptr, H->nt, H->n, H->d_b);
-    if ((err = pcg(H, tol, max_iters, iters, s)) != cudaSuccess) return err;
+    if ((err = pcg(H, tol, max_iters, s)) != cudaSuccess) return err;
     SN_COUNT_LAUNCH();
     scatter_set_kernel<<<nblk(N0), kBS, 0, s>>>(H->d_x, H->d_thick, H->nt, H->n, x_full);
     return cudaGetLastError();
@@ -352,19 +433,31 @@ cudaError_t dsa_solve(DsaHierarchy* H, const double* b_full, double* x_full, dou
 // Forward (Algorithm 2): phi_out[thick] += D_ff^{-1} (Sigma r)_f.
 // Transposed: phi_out[thick] += Sigma_f D_ff^{-1} r_f.
 cudaError_t dsa_correct(DsaHierarchy* H, const double* r, double* phi_out, double tol, int max_iters, bool transpose,
-                        int* iters, cudaStream_t s) {
+                        cudaStream_t s) {
     cudaError_t err = upload(H);
     if (err != cudaSuccess) return err;
-    *iters = 0;
     if (H->nt == 0) return cudaSuccess;
     const long long N0 = (long long)H->nt * H->n;
     SN_COUNT_LAUNCH();
     gather_kernel<<<nblk(N0), kBS, 0, s>>>(r, H->d_thick, transpose ? nullptr : H->d_mass_sig, H->nt, H->n, H->d_b);
-    if ((err = pcg(H, tol, max_iters, iters, s)) != cudaSuccess) return err;
+    if ((err = pcg(H, tol, max_iters, s)) != cudaSuccess) return err;
     SN_COUNT_LAUNCH();
     scatter_add_kernel<<<nblk(N0), kBS, 0, s>>>(H->d_x, H->d_thick, transpose ? H->d_mass_sig : nullptr, H->nt, H->n,
                                                 phi_out);
     return cudaGetLastError();
+}
+
+// PCG iterations run since the last call (synchronises the stream); 0 before the first solve.
+cudaError_t dsa_take_iters(DsaHierarchy* H, cudaStream_t s, int* iters) {
+    *iters = 0;
+    if (!H || !H->uploaded) return cudaSuccess;
+    int h[2] = {0, 0};
+    cudaError_t err = cudaMemcpyAsync(h, H->d_it, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return err;
+    *iters = h[1];
+    g_launches.fetch_add((long long)h[1] * H->body_launches, std::memory_order_relaxed);
+    return cudaMemsetAsync(H->d_it + 1, 0, sizeof(int), s);
 }
 
 }  // namespace sn

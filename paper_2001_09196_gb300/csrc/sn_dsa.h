@@ -43,6 +43,14 @@ struct DsaHierarchy {
     bool uploaded = false;
     double omega0 = 0.6, omega = 0.6;         // damping of block-Jacobi (level 0) / Jacobi (levels >= 1)
     int nu = 2;                               // pre- and post-smoothing steps
+    // PCG recorded as a CUDA graph whose WHILE conditional node repeats one iteration until the
+    // device-side convergence test fails (no host synchronisation per iteration)
+    cudaGraphExec_t pcg_graph = nullptr;
+    double pcg_tol = -1.0;
+    int pcg_max = -1;
+    int* d_it = nullptr;                      // [0] iterations of the current solve, [1] running total
+    long long pro_launches = 0, body_launches = 0;  // kernels in the prologue / one loop iteration
+    cudaStream_t cap = nullptr, cap2 = nullptr;     // private capture streams
 };
 
 }  // namespace sn

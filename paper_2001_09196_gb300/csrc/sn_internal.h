@@ -242,9 +242,11 @@ void dsa_free(DsaHierarchy* h);
 int dsa_thick_count(const DsaHierarchy* h);
 // y = D_ff x (scatter into [elem][node], zeros elsewhere)
 cudaError_t dsa_apply(DsaHierarchy* h, const double* x, double* y, cudaStream_t s);
-// phi_out = phi_half + E_f D_ff^{-1} Sigma_f r (transpose = false); returns PCG iterations in *iters.
+// phi_out = phi_half + E_f D_ff^{-1} Sigma_f r (transpose = false); PCG iterations accumulate on the device.
 cudaError_t dsa_correct(DsaHierarchy* h, const double* r, double* phi_out, double tol, int max_iters,
-                        bool transpose, int* iters, cudaStream_t s);
-cudaError_t dsa_solve(DsaHierarchy* h, const double* b_full, double* x_full, double tol, int max_iters, int* iters,
+                        bool transpose, cudaStream_t s);
+cudaError_t dsa_solve(DsaHierarchy* h, const double* b_full, double* x_full, double tol, int max_iters,
                       cudaStream_t s);
+// PCG iterations run since the last call (synchronises the stream)
+cudaError_t dsa_take_iters(DsaHierarchy* h, cudaStream_t s, int* iters);
 }  // namespace sn

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <type_traits>
+#include <utility>
 #include <cstdio>
 #include <vector>
 
@@ -553,21 +554,50 @@ __device__ __forceinline__ void cached_fluxes(const SweepArgs& a, int d, int e, 
     }
 }
 
-template <int DIM, int P, typename R, bool ADJ>
-__device__ __forceinline__ R node_rhs(const SweepArgs& a, const double* mu, int d, int e, int r) {
-    constexpr int Q = P + 1, N = Shape<DIM, P>::N;
-    constexpr int FAM = DIM == 3 ? FAM_3D_P1 : P - 1;
-    using K = GLT<R>;
+// Programmatic dependent launch: a level kernel's blocks do the work that reads no angular flux
+// before griddepcontrol.wait, which returns when every prerequisite grid has completed and its
+// writes are visible; then they allow the next level to launch.  Without a programmatic
+// dependency both instructions do nothing.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// The part of a node's work that reads no angular flux: the face flux factors, the source row
+// (forward: M_r (q + sigma_s phi_r) / (4 pi); adjoint: mu_r) and the N entries of the cached
+// inverse this lane multiplies with (forward: row r of A_e^{-1}; adjoint: column r).
+template <int DIM, int P, typename R>
+struct NodeStage {
     double F[2 * DIM];
-    cached_fluxes<DIM>(a, d, e, F);
     R rhs;
+    R inv[Shape<DIM, P>::N];
+};
+
+template <int DIM, int P, int MODE, bool ADJ>
+__device__ __forceinline__ void node_stage(const SweepArgs& a, const double* mu, int d, int e, int r,
+                                           NodeStage<DIM, P, typename std::conditional<MODE == 1, float, double>::type>& st) {
+    using R = typename std::conditional<MODE == 1, float, double>::type;
+    constexpr int N = Shape<DIM, P>::N, S = CacheShape<DIM, P>::S;
+    cached_fluxes<DIM>(a, d, e, st.F);
     if constexpr (ADJ) {
-        rhs = (R)mu[(size_t)e * N + r];
+        st.rhs = (R)mu[(size_t)e * N + r];
     } else {
         const double ss = a.sigma_s[e], qe = a.q[e] * a.q_scale;
         const double S = (qe + (a.phi ? ss * a.phi[(size_t)e * N + r] : 0.0)) * (1.0 / kFourPi);
-        rhs = (R)a.mass[(size_t)e * N + r] * (R)S;
+        st.rhs = (R)a.mass[(size_t)e * N + r] * (R)S;
     }
+    const R* inv;
+    if constexpr (MODE == 1) inv = a.ainv32;
+    else inv = a.ainv;
+    inv += ((size_t)d * a.ne + e) * S;
+#pragma unroll
+    for (int j = 0; j < N; ++j) st.inv[j] = __ldcs(inv + (ADJ ? r * N + j : j * N + r));
+}
+
+// Inflow (adjoint: outflow) face terms of node r from the neighbours' angular fluxes.
+template <int DIM, int P, typename R, bool ADJ>
+__device__ __forceinline__ R node_faces(const SweepArgs& a, const double* F, int d, int e, int r, R rhs) {
+    constexpr int Q = P + 1, N = Shape<DIM, P>::N;
+    constexpr int FAM = DIM == 3 ? FAM_3D_P1 : P - 1;
+    using K = GLT<R>;
     const int ri[3] = {r % Q, (r / Q) % Q, r / (Q * Q)};
     const R* psi = static_cast<const R*>(a.psi);
 #pragma unroll
@@ -593,21 +623,27 @@ __device__ __forceinline__ R node_rhs(const SweepArgs& a, const double* mu, int 
     return rhs;
 }
 
-template <int DIM, int P, int MODE, bool ADJ>
+// One node of one item: stage, (PDL: release the next grid, wait for the previous one), face
+// terms, x_r = sum_j inv_rj rhs_j with rhs_j shuffled from the item's lane j, store.
+template <int DIM, int P, int MODE, bool ADJ, bool PDL = false>
 __device__ __forceinline__ void node_item(const SweepArgs& a, const double* mu, int d, int e, int r, int src0,
                                           bool valid) {
     using R = typename std::conditional<MODE == 1, float, double>::type;
-    constexpr int N = Shape<DIM, P>::N, S = CacheShape<DIM, P>::S;
-    const R rhs = valid ? node_rhs<DIM, P, R, ADJ>(a, mu, d, e, r) : R(0);
-    const R* inv;
-    if constexpr (MODE == 1) inv = a.ainv32;
-    else inv = a.ainv;
-    inv += ((size_t)d * a.ne + e) * S;
+    constexpr int N = Shape<DIM, P>::N;
+    NodeStage<DIM, P, R> st;
+    if (valid) node_stage<DIM, P, MODE, ADJ>(a, mu, d, e, r, st);
+    if (PDL) {
+        // the next level may launch once this one's inputs are complete: its blocks then run
+        // their prologue while this level computes, and the look-ahead stays one level deep
+        pdl_wait();
+        pdl_launch_dependents();
+    }
+    const R rhs = valid ? node_faces<DIM, P, R, ADJ>(a, st.F, d, e, r, st.rhs) : R(0);
     R x = R(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         const R rj = __shfl_sync(0xffffffffu, rhs, src0 + j);
-        if (valid) x += __ldcs(inv + (ADJ ? r * N + j : j * N + r)) * rj;
+        if (valid) x += st.inv[j] * rj;
     }
     if (valid) static_cast<R*>(a.psi)[((size_t)d * a.ne + e) * N + r] = x;
 }
@@ -627,7 +663,7 @@ __global__ void __launch_bounds__(128) node_level_kernel(SweepArgs a, const doub
         d = it.x;
         e = it.y;
     }
-    node_item<DIM, P, MODE, ADJ>(a, mu, d, e, r, slot < IPW ? slot * N : 0, valid);
+    node_item<DIM, P, MODE, ADJ, true>(a, mu, d, e, r, slot < IPW ? slot * N : 0, valid);
 }
 
 // Right-hand side in arithmetic type R: mass-weighted source S = (q + sigma_s phi)/(4 pi) (formed in
@@ -1126,6 +1162,26 @@ static SweepArgs make_args(const sn_mesh* m) {
 
 static inline unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// Launch with programmatic stream serialisation when pdl is set: the kernel may start while its
+// predecessor in the stream still runs (it waits in griddepcontrol.wait before reading the
+// predecessor's results).  The first launch of a sequence passes pdl = false, so everything
+// written before the sequence is complete before any of its kernels starts.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), unsigned grid, int block, cudaStream_t s,
+                            Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Blocks of bs threads for n items of the node-per-lane kernels (32 / N items per warp).
 static inline unsigned node_grid(const sn_mesh* m, long long n, int bs) {
     const int ipw = 32 / m->n;
@@ -1296,9 +1352,11 @@ static cudaError_t enqueue_levels(sn_mesh* m, int kind, cudaStream_t s) {
         for (int L = m->levels.n_levels - 1; L >= 0; --L) {
             const long long b = m->levels.level_ptr[L], e = m->levels.level_ptr[L + 1];
             if (e <= b) continue;
-            if (a.ainv)
-                SN_DISPATCH(m->dim, m->p, (node_level_kernel<D_, P_, 0, true><<<node_grid(m, e - b, bs), bs, 0, s>>>(a, m->d_src, b, e)));
-            else
+            if (a.ainv) {
+                cudaError_t lerr = cudaSuccess;
+                SN_DISPATCH(m->dim, m->p, (lerr = launch_k(L != m->levels.n_levels - 1, node_level_kernel<D_, P_, 0, true>, node_grid(m, e - b, bs), bs, s, a, (const double*)m->d_src, b, e)));
+                if (lerr != cudaSuccess) return lerr;
+            } else
                 SN_DISPATCH(m->dim, m->p, (adjoint_level_kernel<D_, P_><<<grid_for(e - b, bs), bs, 0, s>>>(a, m->d_src, b, e)));
         }
         return cudaGetLastError();
@@ -1314,13 +1372,16 @@ static cudaError_t enqueue_levels(sn_mesh* m, int kind, cudaStream_t s) {
         const long long b = m->levels.level_ptr[L], e = m->levels.level_ptr[L + 1];
         if (e <= b) continue;
         const unsigned g = grid_for(e - b, bs), gn = node_grid(m, e - b, bs);
+        cudaError_t lerr = cudaSuccess;
+        const double* none = nullptr;
         if (kind == SN_FP64 && a.ainv)
-            SN_DISPATCH(m->dim, m->p, (node_level_kernel<D_, P_, 0, false><<<gn, bs, 0, s>>>(a, nullptr, b, e)));
+            SN_DISPATCH(m->dim, m->p, (lerr = launch_k(L > 0, node_level_kernel<D_, P_, 0, false>, gn, bs, s, a, none, b, e)));
         else if (kind == SN_FP32 && a.ainv32)
-            SN_DISPATCH(m->dim, m->p, (node_level_kernel<D_, P_, 1, false><<<gn, bs, 0, s>>>(a, nullptr, b, e)));
+            SN_DISPATCH(m->dim, m->p, (lerr = launch_k(L > 0, node_level_kernel<D_, P_, 1, false>, gn, bs, s, a, none, b, e)));
         else if (kind == SN_FP64) SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 0><<<g, bs, 0, s>>>(a, b, e)));
         else if (kind == SN_FP32) SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 1><<<g, bs, 0, s>>>(a, b, e)));
         else SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 2><<<g, bs, 0, s>>>(a, b, e)));
+        if (lerr != cudaSuccess) return lerr;
     }
     return cudaGetLastError();
 }
@@ -1549,8 +1610,8 @@ __global__ void __launch_bounds__(128) batch_node_level_kernel(const SweepArgs* 
     BatchItem it{-1, 0, 0, 0};
     if (slot < IPW && t < end) it = items[t];
     const bool valid = it.inst >= 0 && active[it.inst];
-    node_item<DIM, P, MODE, false>(args[valid ? it.inst : 0], nullptr, valid ? it.dir : 0, valid ? it.elem : 0, r,
-                                   slot < IPW ? slot * N : 0, valid);
+    node_item<DIM, P, MODE, false, true>(args[valid ? it.inst : 0], nullptr, valid ? it.dir : 0, valid ? it.elem : 0,
+                                         r, slot < IPW ? slot * N : 0, valid);
 }
 
 // Dataflow schedule: a warp claims a 32-item chunk (one family, one level) and runs it in rounds
@@ -1755,10 +1816,13 @@ cudaError_t batch_enqueue_sweep(sn_batch* b, int precision, cudaStream_t s) {
 #define SN_BATCH_NODE(MODE_)                                                                                    \
     do {                                                                                                      \
         const unsigned gn = grid_for(((hi - lo + ipw - 1) / ipw) * 32, bs);                                   \
-        if (fam == FAM_2D_P1) batch_node_level_kernel<2, 1, MODE_><<<gn, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active); \
-        else if (fam == FAM_2D_P2) batch_node_level_kernel<2, 2, MODE_><<<gn, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active); \
-        else if (fam == FAM_2D_P3) batch_node_level_kernel<2, 3, MODE_><<<gn, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active); \
-        else batch_node_level_kernel<3, 1, MODE_><<<gn, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active); \
+        const bool pdl = k > 0;                                                                               \
+        cudaError_t lerr;                                                                                     \
+        if (fam == FAM_2D_P1) lerr = launch_k(pdl, batch_node_level_kernel<2, 1, MODE_>, gn, bs, s, b->d_args, b->d_items, lo, hi, b->d_active); \
+        else if (fam == FAM_2D_P2) lerr = launch_k(pdl, batch_node_level_kernel<2, 2, MODE_>, gn, bs, s, b->d_args, b->d_items, lo, hi, b->d_active); \
+        else if (fam == FAM_2D_P3) lerr = launch_k(pdl, batch_node_level_kernel<2, 3, MODE_>, gn, bs, s, b->d_args, b->d_items, lo, hi, b->d_active); \
+        else lerr = launch_k(pdl, batch_node_level_kernel<3, 1, MODE_>, gn, bs, s, b->d_args, b->d_items, lo, hi, b->d_active); \
+        if (lerr != cudaSuccess) return lerr;                                                                 \
     } while (0)
         SN_COUNT_LAUNCH();
         const int ipw = 32 / family_nodes(fam);

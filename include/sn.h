@@ -81,14 +81,22 @@ sn_status sn_mesh_destroy(sn_mesh* mesh);
 sn_status sn_mesh_get_info(const sn_mesh* mesh, sn_mesh_info* info);
 
 /*
- * Sweep schedule (tuning; results are identical to rounding-free reordering, i.e. bitwise):
+ * Sweep schedule (tuning; every schedule computes the same element solves in the same arithmetic,
+ * so results are bitwise identical):
  *   schedule 0 (default): one launch per wavefront level of all directions, captured once into a
- *   CUDA graph so that a sweep is a single graph launch;
- *   schedule 1: one persistent launch per sweep in which warps claim 32-item chunks
- *   in level order and wait (bounded, SN_ERR_TIMEOUT after 4 s) for their upwind neighbours.
- * block: threads per block (32..128, multiple of 32); max_blocks_per_sm: 0 = occupancy limit.
+ *   CUDA graph so that a sweep is a single graph launch (programmatic dependent launch overlaps a
+ *   level's prologue with the previous level);
+ *   schedule 1: one persistent launch per sweep in which warps claim items in level order and
+ *   wait (bounded, SN_ERR_TIMEOUT after 4 s) for their upwind neighbours;
+ *   schedule 2 (operator cache on): one persistent launch in which a CTA of `block` threads runs
+ *   a whole tile of param^dim elements of one direction (param = tile edge, 0 = 16 in 2D and 8 in
+ *   3D), synchronising itself between the tile's levels and waiting (bounded) only for upwind
+ *   elements of other tiles; tiles whose upwind graph is cyclic (jittered faces) run as one task.
+ *   Uncached solves (SN_FP32_REFINE, cache off) and the adjoint use schedule 0 instead.
+ * block: threads per block, a multiple of 32 in [32, 128] (schedules 0, 1) or [32, 256] (2).
+ * param: schedule 1: blocks per SM (0 = occupancy limit); schedule 2: tile edge (<= 64); else 0.
  */
-sn_status sn_mesh_set_schedule(sn_mesh* mesh, int schedule, int block, int max_blocks_per_sm);
+sn_status sn_mesh_set_schedule(sn_mesh* mesh, int schedule, int block, int param);
 
 /*
  * Operator cache.  The element operator A_e of Eq. (sntransport) (volume terms plus outflow
@@ -288,7 +296,8 @@ sn_status sn_batch_source_iterate(sn_batch* batch, const sn_iter_opts* opts, dou
 
 /*
  * Schedule autotuner: times the candidate sweep schedules (level graphs with 32/64/128-thread blocks;
- * persistent dataflow launches with several per-SM occupancy caps) for this mesh / batch and precision
+ * persistent dataflow launches with several per-SM occupancy caps; for meshes, tiled launches with
+ * several tile edges and CTA sizes) for this mesh / batch and precision
  * with CUDA events, keeps the fastest and reports it (any output pointer may be NULL).  Results of
  * sn_mesh_autotune are cached per (dim, p, directions, precision, element count), so meshes of the same
  * shape reuse them.  Schedules give bitwise-identical results; tuning changes only the time.

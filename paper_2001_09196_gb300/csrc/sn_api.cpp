@@ -59,6 +59,7 @@ void free_mesh(sn_mesh* m) {
     if (!m) return;
     sn::drop_level_graphs(m);
     sn::free_operator_cache(m);
+    sn::free_tiles(m);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     if (m->d_src) cudaFree(m->d_src);
     for (void* p : {(void*)m->d_dirs, (void*)m->d_wts, (void*)m->d_corners, (void*)m->d_sigma_t, (void*)m->d_sigma_s,
@@ -277,7 +278,7 @@ sn_status sn_sweep(sn_mesh* m, const double* phi_in, double* phi_out, int precis
     cudaStream_t s = (cudaStream_t)stream;
     CK(sn::launch_sweep(m, phi_in, precision, 1.0, s), "sweep");
     CK(sn::launch_phi_reduce(m, precision, nullptr, phi_out, nullptr, s), "phi reduce");
-    if (m->schedule == sn::SCHED_DATAFLOW) {
+    if (m->schedule != sn::SCHED_LEVELS) {
         bool timed_out = false;
         CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
         if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out");
@@ -299,20 +300,29 @@ sn_status sn_mesh_set_operator_cache(sn_mesh* m, int mode) {
 sn_status sn_debug_stall_next_sweep(sn_mesh* m, double timeout_seconds) {
     if (!m) return fail(SN_ERR_ARG, "null mesh");
     if (!(timeout_seconds > 0.0 && timeout_seconds <= 4.0)) return fail(SN_ERR_ARG, "timeout must be in (0, 4] s");
-    if (m->schedule != sn::SCHED_DATAFLOW) return fail(SN_ERR_ARG, "only the dataflow schedule waits");
+    if (m->schedule == sn::SCHED_LEVELS) return fail(SN_ERR_ARG, "only the dataflow and tiled schedules wait");
     m->levels.stall_timeout_s = timeout_seconds;
     return SN_OK;
 }
 
-sn_status sn_mesh_set_schedule(sn_mesh* m, int schedule, int block, int max_blocks_per_sm) {
+sn_status sn_mesh_set_schedule(sn_mesh* m, int schedule, int block, int param) {
     if (!m) return fail(SN_ERR_ARG, "null mesh");
-    if (schedule != sn::SCHED_LEVELS && schedule != sn::SCHED_DATAFLOW) return fail(SN_ERR_ARG, "bad schedule");
-    if (block < 32 || block > 128 || block % 32) return fail(SN_ERR_ARG, "block must be 32, 64, 96 or 128");
-    if (max_blocks_per_sm < 0) return fail(SN_ERR_ARG, "max_blocks_per_sm must be >= 0");
+    if (schedule != sn::SCHED_LEVELS && schedule != sn::SCHED_DATAFLOW && schedule != sn::SCHED_TILES)
+        return fail(SN_ERR_ARG, "bad schedule");
+    const int max_block = schedule == sn::SCHED_TILES ? 256 : 128;
+    if (block < 32 || block > max_block || block % 32)
+        return fail(SN_ERR_ARG, "block must be a multiple of 32 in [32, %d]", max_block);
+    if (param < 0) return fail(SN_ERR_ARG, "the schedule parameter must be >= 0");
+    if (schedule == sn::SCHED_TILES && param > 64) return fail(SN_ERR_ARG, "tile edge must be <= 64");
     if (m->block != block) sn::drop_level_graphs(m);
     m->schedule = schedule;
-    m->block = block;
-    m->max_blocks_per_sm = max_blocks_per_sm;
+    if (schedule != sn::SCHED_TILES) m->block = block;
+    if (schedule == sn::SCHED_TILES) {
+        m->tile_block = block;
+        m->tile_edge = param > 0 ? param : (m->dim == 2 ? 16 : 8);
+    } else {
+        m->max_blocks_per_sm = param;
+    }
     return SN_OK;
 }
 
@@ -416,7 +426,7 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
         double rr = 0.0;
         CK(cudaMemcpyAsync(&rr, m->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
         CK(cudaStreamSynchronize(s), "sync");
-        if (m->schedule == sn::SCHED_DATAFLOW) {
+        if (m->schedule != sn::SCHED_LEVELS) {
             CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
             if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out");
         }
@@ -456,7 +466,7 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
             CK(sn::launch_multidot(w, 1, M, w, part, hd + 2 * (k + 1), s), "norm");
             CK(cudaMemcpyAsync(hh.data(), hd, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
             CK(cudaStreamSynchronize(s), "sync");
-            if (m->schedule == sn::SCHED_DATAFLOW) {
+            if (m->schedule != sn::SCHED_LEVELS) {
                 CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
                 if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out");
             }
@@ -537,7 +547,7 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
         double rr = 0.0;
         CK(cudaMemcpyAsync(&rr, m->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
         CK(cudaStreamSynchronize(s), "sync");
-        if (m->schedule == sn::SCHED_DATAFLOW) {
+        if (m->schedule != sn::SCHED_LEVELS) {
             bool timed_out = false;
             CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
             if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out");
@@ -587,7 +597,7 @@ sn_status sn_adjoint_sweep(sn_mesh* m, const double* mu, double* out, int precis
     cudaStream_t s = (cudaStream_t)stream;
     CK(sn::launch_adjoint_sweep(m, mu, s), "adjoint sweep");
     CK(sn::launch_adjoint_reduce(m, out, s), "adjoint reduce");
-    if (m->schedule == sn::SCHED_DATAFLOW) {
+    if (m->schedule != sn::SCHED_LEVELS) {
         bool timed_out = false;
         CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
         if (timed_out) return fail(SN_ERR_TIMEOUT, "an adjoint sweep dependency wait timed out");
@@ -983,6 +993,10 @@ std::map<TuneKey, TuneChoice> g_tune_cache;
 std::mutex g_tune_mutex;
 const TuneChoice kCandidates[] = {{0, 32, 0, 0}, {0, 64, 0, 0}, {0, 128, 0, 0}, {1, 128, 0, 0},
                                   {1, 128, 1, 0}, {1, 64, 2, 0}, {1, 32, 4, 0}};
+// meshes also try the tiled schedule (cached solves) with a few tile edges and CTA sizes
+const TuneChoice kMeshCandidates[] = {{0, 32, 0, 0}, {0, 64, 0, 0}, {0, 128, 0, 0}, {1, 128, 0, 0},
+                                      {1, 64, 2, 0}, {2, 128, 8, 0}, {2, 128, 16, 0}, {2, 256, 16, 0},
+                                      {2, 256, 32, 0}};
 
 template <typename F>
 float time_ms(F&& run, cudaStream_t s, int reps) {
@@ -1025,7 +1039,7 @@ sn_status sn_mesh_autotune(sn_mesh* m, int precision, void* stream, int* schedul
             if (st != SN_OK) return st;
         }
         double* out = m->d_work + 3 * (size_t)m->ne * m->n;
-        for (const TuneChoice& c : kCandidates) {
+        for (const TuneChoice& c : kMeshCandidates) {
             sn_status st = sn_mesh_set_schedule(m, c.schedule, c.block, c.cap);
             if (st != SN_OK) return st;
             cudaError_t err = cudaSuccess;
@@ -1034,7 +1048,7 @@ sn_status sn_mesh_autotune(sn_mesh* m, int precision, void* stream, int* schedul
                 if (err == cudaSuccess) err = sn::launch_phi_reduce(m, precision, nullptr, out, nullptr, s);
             }, s, 2);
             CK(err, "autotune sweep");
-            if (m->schedule == sn::SCHED_DATAFLOW) {
+            if (m->schedule != sn::SCHED_LEVELS) {
                 bool timed_out = false;
                 CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
                 if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out while tuning");

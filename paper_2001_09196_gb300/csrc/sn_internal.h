@@ -87,9 +87,27 @@ struct LevelSets {
     unsigned long long* ctrl = nullptr; // device: [0] chunk counter, [1] error word
     int epoch = 0;
     double stall_timeout_s = 0.0;       // > 0: the next dataflow sweep publishes a value nobody waits for
+    std::vector<int> h_level;           // host copy of the level of every (dir, elem), dir-major
 };
 
-enum { SCHED_LEVELS = 0, SCHED_DATAFLOW = 1 };
+enum { SCHED_LEVELS = 0, SCHED_DATAFLOW = 1, SCHED_TILES = 2 };
+
+// Tiled schedule of the cached sweep: the mesh is cut into tiles of edge^dim elements; per
+// direction, the tiles of every strongly connected component of the tile upwind graph form one
+// task (a component of several tiles appears only where vertex jitter reverses faces on a tile
+// boundary), and tasks are listed in a topological order of the component graph.  A CTA runs a
+// task's elements in increasing global level, synchronising the CTA between levels, and waits
+// (bounded) on the completion words of upwind elements in other tasks.
+struct TileSets {
+    int edge = 0;                       // tile edge the tasks were built for (0: not built)
+    int4* tasks = nullptr;              // device: (direction, first item, first level boundary, levels)
+    int* lvl_ptr = nullptr;             // device: item offsets of every task's local levels
+    int2* items = nullptr;              // device: (element, flags) flags bit f < 6: wait for the upwind
+                                        // neighbour through face f; bit 6: publish the completion word
+    long long n_tasks = 0;
+    int max_level_items = 0;            // largest local level of any task
+};
+constexpr int kTileWaitMask = 63, kTilePublish = 64;
 
 struct DsaHierarchy;  // sn_dsa.cu
 struct UnionDsa;      // sn_batch.cu
@@ -128,7 +146,10 @@ struct sn_mesh {
     int red_blocks = 0;
     double* d_scalars = nullptr;    // small device scalars
     sn::LevelSets levels;
+    sn::TileSets tiles;
     int schedule = sn::SCHED_LEVELS;    // sweep schedule (see sn_mesh_set_schedule)
+    int tile_edge = 16;                 // tile edge of the tiled schedule
+    int tile_block = 128;               // threads per CTA of the tiled schedule
     int block = 128;                    // threads per block of the sweep kernels
     int max_blocks_per_sm = 0;          // 0: occupancy limit
     int cache_mode = SN_CACHE_AUTO;     // operator cache (see sn_mesh_set_operator_cache)
@@ -196,6 +217,11 @@ namespace sn {
 sn_status set_error(sn_status st, const char* msg);
 // sn_sweep.cu
 cudaError_t build_levels(sn_mesh* m, cudaStream_t s, bool* cycle);
+// upwind face bits of every (dir, elem): bit f set when Omega.n_f < 0 and face f has a neighbour
+cudaError_t launch_upwind_mask(sn_mesh* m, unsigned char* mask, cudaStream_t s);
+// sn_tiles.cpp: builds m->tiles for tile edge `edge` (needs the level sets)
+cudaError_t build_tiles(sn_mesh* m, int edge, cudaStream_t s);
+void free_tiles(sn_mesh* m);
 cudaError_t compute_mass(sn_mesh* m, cudaStream_t s);
 void drop_level_graphs(sn_mesh* m);
 // batched sweep over all instances of a batch (sn_sweep.cu)

@@ -933,6 +933,89 @@ __global__ void __launch_bounds__(128) node_dataflow_kernel(SweepArgs a, Dataflo
     }
 }
 
+// ---------------------------------------------------------------- tiled sweep (cached operators)
+struct TileArgs {
+    const int4* tasks;               // (direction, first item, first level boundary, levels)
+    const int* lvl_ptr;
+    const int2* items;               // (element, flags)
+    long long n_tasks;
+    int* done;                       // nd x ne completion words
+    int epoch, publish;
+    unsigned long long* next;        // task counter, zeroed before each launch
+    int* error;                      // set to 1 when a wait times out
+    unsigned long long timeout_ns;
+};
+
+// Bounded wait for the upwind neighbours through the faces in `bits` (elements of other tasks).
+template <int DIM, int P>
+__device__ __forceinline__ bool wait_faces(const SweepArgs& a, const int* done, int epoch, int d, int e, int bits,
+                                           unsigned long long deadline) {
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f) {
+        if (!((bits >> f) & 1)) continue;
+        const int* flag = done + (size_t)d * a.ne + neighbor<DIM, P>(a, e, f);
+        int polls = 0;
+        while (ld_acquire(flag) != epoch) {
+            if (++polls > 64) {
+                if (globaltimer() > deadline) return false;
+                __nanosleep(64);
+            }
+        }
+    }
+    return true;
+}
+
+// A CTA claims tasks in list order and runs each task's local levels one after another, one
+// lane per node (node_item), with a CTA barrier between levels.  A failed wait ends the launch
+// for every CTA through the error word (all barriers are still reached: waits are bounded).
+template <int DIM, int P, int MODE>
+__global__ void __launch_bounds__(256) tile_sweep_kernel(SweepArgs a, TileArgs t) {
+    constexpr int N = Shape<DIM, P>::N, IPW = 32 / N;
+    __shared__ long long s_task;
+    __shared__ int s_failed;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int slot = lane / N, r = lane - slot * N, src0 = slot < IPW ? slot * N : 0;
+    const int per_pass = (blockDim.x >> 5) * IPW;
+    const unsigned long long deadline = globaltimer() + t.timeout_ns;
+    while (true) {
+        if (threadIdx.x == 0) {
+            s_task = (long long)atomicAdd(t.next, 1ull);
+            s_failed = *(volatile int*)t.error;
+        }
+        __syncthreads();
+        const long long task = s_task;
+        const int failed = s_failed;
+        __syncthreads();
+        if (task >= t.n_tasks || failed) break;
+        const int4 T = t.tasks[task];
+        const int d = T.x;
+        bool abort = false;
+        for (int L = 0; L < T.w && !abort; ++L) {
+            const int lo = t.lvl_ptr[T.z + L], hi = t.lvl_ptr[T.z + L + 1];
+            bool bad = false;
+            for (int base = lo; base < hi; base += per_pass) {
+                const int idx = base + warp * IPW + slot;
+                const bool valid = slot < IPW && idx < hi;
+                const int2 it = valid ? t.items[idx] : make_int2(0, 0);
+                bool ok = true;
+                if (valid && (it.y & kTileWaitMask)) ok = wait_faces<DIM, P>(a, t.done, t.epoch, d, it.x, it.y, deadline);
+                node_item<DIM, P, MODE, false>(a, nullptr, d, it.x, r, src0, valid && ok);
+                __syncwarp();
+                if (valid && ok && r == 0 && (it.y & kTilePublish)) {
+                    __threadfence();
+                    st_release(t.done + (size_t)d * a.ne + it.x, t.publish);
+                }
+                bad = bad || !ok;
+            }
+            abort = __syncthreads_or(bad) != 0;
+        }
+        if (abort) {
+            if (threadIdx.x == 0) atomicExch(t.error, 1);
+            break;
+        }
+    }
+}
+
 // Adjoint: A_e^T lam_e = mu_e - sum_{outflow F, downwind u} C(u<-e)^T lam_u, in reverse level order.
 template <int DIM, int P>
 __device__ __forceinline__ void adjoint_item(const SweepArgs& a, const double* mu, int d, int e) {
@@ -1000,6 +1083,19 @@ __global__ void indegree_kernel(SweepArgs a, int* indeg, int2* frontier, unsigne
         const unsigned long long pos = atomicAdd(cursor, 1ull);
         frontier[pos] = make_int2(d, e);
     }
+}
+
+template <int DIM, int P>
+__global__ void upwind_mask_kernel(SweepArgs a, unsigned char* mask) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)a.nd * a.ne) return;
+    const int d = (int)(t / a.ne), e = (int)(t % a.ne);
+    const double Ox = a.dirs[3 * d], Oy = a.dirs[3 * d + 1], Oz = a.dirs[3 * d + 2];
+    unsigned m = 0;
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f)
+        if (face_flux_only<DIM, P>(a, e, f, Ox, Oy, Oz) < 0.0 && neighbor<DIM, P>(a, e, f) >= 0) m |= 1u << f;
+    mask[t] = (unsigned char)m;
 }
 
 template <int DIM, int P>
@@ -1246,7 +1342,8 @@ cudaError_t build_levels(sn_mesh* m, cudaStream_t s, bool* cycle) {
         return cudaSuccess;
     }
     // deterministic order: counting sort of (dir, elem) by level on the host
-    std::vector<int> h_level(total);
+    std::vector<int>& h_level = m->levels.h_level;
+    h_level.assign(total, 0);
     if ((err = cudaMemcpyAsync(h_level.data(), level, total * sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (err = cudaStreamSynchronize(s)) != cudaSuccess) { cleanup(); return err; }
     std::vector<long long> ptr(L + 1, 0);
@@ -1337,6 +1434,51 @@ static cudaError_t launch_dataflow(sn_mesh* m, const SweepArgs& a, cudaStream_t 
     SN_COUNT_LAUNCH();
     if (cached) node_dataflow_kernel<DIM, P, MODE == 1 ? 1 : 0, ADJ><<<(unsigned)blocks, m->block, 0, s>>>(a, f, mu);
     else sweep_dataflow_kernel<DIM, P, MODE, ADJ><<<(unsigned)blocks, m->block, 0, s>>>(a, f, mu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_upwind_mask(sn_mesh* m, unsigned char* mask, cudaStream_t s) {
+    SweepArgs a = make_args(m);
+    const long long total = (long long)m->nd * m->ne;
+    SN_COUNT_LAUNCH();
+    SN_DISPATCH(m->dim, m->p, (upwind_mask_kernel<D_, P_><<<grid_for(total, 256), 256, 0, s>>>(a, mask)));
+    return cudaGetLastError();
+}
+
+template <int DIM, int P, int MODE>
+static cudaError_t launch_tiles(sn_mesh* m, const SweepArgs& a, cudaStream_t s) {
+    LevelSets& L = m->levels;
+    if (++L.epoch == 0x7fffffff) {
+        cudaMemsetAsync(L.done, 0, (size_t)m->nd * m->ne * sizeof(int), s);
+        L.epoch = 1;
+    }
+    cudaMemsetAsync(L.ctrl, 0, sizeof(unsigned long long), s);
+    TileArgs t;
+    t.tasks = m->tiles.tasks;
+    t.lvl_ptr = m->tiles.lvl_ptr;
+    t.items = m->tiles.items;
+    t.n_tasks = m->tiles.n_tasks;
+    t.done = L.done;
+    t.epoch = L.epoch;
+    t.publish = L.epoch;
+    t.next = L.ctrl;
+    t.error = reinterpret_cast<int*>(L.ctrl + 1);
+    t.timeout_ns = 4000000000ull;
+    if (L.stall_timeout_s > 0.0) {  // test hook: completion words never match, every wait times out
+        t.publish = -1;
+        t.timeout_ns = (unsigned long long)(L.stall_timeout_s * 1e9);
+        L.stall_timeout_s = 0.0;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_sweep_kernel<DIM, P, MODE>, m->tile_block, 0);
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    long long blocks = (long long)sms * per_sm;
+    if (blocks > t.n_tasks) blocks = t.n_tasks;
+    if (blocks < 1) blocks = 1;
+    SN_COUNT_LAUNCH();
+    tile_sweep_kernel<DIM, P, MODE><<<(unsigned)blocks, m->tile_block, 0, s>>>(a, t);
     return cudaGetLastError();
 }
 
@@ -1513,6 +1655,13 @@ cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double
     a.phi = phi_in;
     a.q_scale = q_scale;
     a.psi = precision == SN_FP32 ? m->d_psi32 : m->d_psi;
+    const bool cached = precision == SN_FP64 ? a.ainv != nullptr : (precision == SN_FP32 && a.ainv32 != nullptr);
+    if (m->schedule == SCHED_TILES && cached) {  // uncached solves fall back to the level schedule
+        if (m->tiles.edge != m->tile_edge && (cerr = build_tiles(m, m->tile_edge, s)) != cudaSuccess) return cerr;
+        if (precision == SN_FP64) SN_DISPATCH(m->dim, m->p, (cerr = launch_tiles<D_, P_, 0>(m, a, s)));
+        else SN_DISPATCH(m->dim, m->p, (cerr = launch_tiles<D_, P_, 1>(m, a, s)));
+        return cerr;
+    }
     if (m->schedule == SCHED_DATAFLOW) {
         if (precision == SN_FP64) SN_DISPATCH(m->dim, m->p, (launch_dataflow<D_, P_, 0>(m, a, s)));
         else if (precision == SN_FP32) SN_DISPATCH(m->dim, m->p, (launch_dataflow<D_, P_, 1>(m, a, s)));

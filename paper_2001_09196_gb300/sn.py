@@ -221,9 +221,10 @@ class Mesh:
     def shape(self):
         return (self.n_elem, self.n_nodes)
 
-    def set_schedule(self, schedule="dataflow", block=128, max_blocks_per_sm=0):
-        sched = {"levels": 0, "dataflow": 1}[schedule] if isinstance(schedule, str) else int(schedule)
-        _check(_lib.sn_mesh_set_schedule(self._h, sched, int(block), int(max_blocks_per_sm)))
+    def set_schedule(self, schedule="dataflow", block=128, param=0):
+        """schedule "levels" | "dataflow" | "tiles"; param: per-SM block cap (dataflow) or tile edge (tiles)."""
+        sched = {"levels": 0, "dataflow": 1, "tiles": 2}[schedule] if isinstance(schedule, str) else int(schedule)
+        _check(_lib.sn_mesh_set_schedule(self._h, sched, int(block), int(param)))
 
     def set_operator_cache(self, mode="auto"):
         """Cache every element operator's inverse between sweeps: "off", "on" or "auto"."""
@@ -238,7 +239,7 @@ class Mesh:
         a, b, c = C.c_int(), C.c_int(), C.c_int()
         _check(_lib.sn_mesh_autotune(self._h, _PREC.get(precision, precision), _stream(stream), C.byref(a),
                                      C.byref(b), C.byref(c)))
-        return ("levels", "dataflow")[a.value], b.value, c.value
+        return ("levels", "dataflow", "tiles")[a.value], b.value, c.value
 
     def quadrature(self):
         dirs = np.zeros((self.n_dirs, 3))
@@ -362,7 +363,7 @@ class Batch:
         a, b, c = C.c_int(), C.c_int(), C.c_int()
         _check(_lib.sn_batch_autotune(self._h, _PREC.get(precision, precision), _stream(stream), C.byref(a),
                                       C.byref(b), C.byref(c)))
-        return ("levels", "dataflow")[a.value], b.value, c.value
+        return ("levels", "dataflow", "tiles")[a.value], b.value, c.value
 
     @staticmethod
     def _ptrs(tensors):

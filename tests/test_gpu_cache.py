@@ -64,7 +64,7 @@ def _oracle(name, cache):
     return cache[name]
 
 
-@pytest.mark.parametrize("schedule", ["levels", "dataflow"])
+@pytest.mark.parametrize("schedule", ["levels", "dataflow", "tiles"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_cached_sweeps_match_oracle(sn, oracles, name, schedule):
     from oracle import adjoint

@@ -1,4 +1,5 @@
-"""GPU: the sweep schedules agree bit for bit, and the bounded dependency waits report a timeout."""
+"""GPU: the sweep schedules (level graphs, dataflow, tiles) agree bit for bit, and the bounded
+dependency waits report a timeout."""
 import numpy as np
 import pytest
 
@@ -34,16 +35,18 @@ def test_schedules_agree_bitwise(sn, name, precision):
     phi = torch.as_tensor(inputs.random_phi(prob, 5), device="cuda")
     m.set_schedule("levels", 128)
     ref = m.sweep(phi, precision=precision)
-    for block, cap in ((128, 0), (64, 0), (32, 1), (96, 2)):
-        m.set_schedule("dataflow", block, cap)
+    for sched, block, param in (("dataflow", 128, 0), ("dataflow", 64, 0), ("dataflow", 32, 1), ("dataflow", 96, 2),
+                                ("tiles", 128, 4), ("tiles", 256, 8), ("tiles", 64, 3), ("tiles", 32, 16)):
+        m.set_schedule(sched, block, param)
         got = m.sweep(phi, precision=precision)
-        assert torch.equal(got, ref), (block, cap)
+        assert torch.equal(got, ref), (sched, block, param)
 
 
-def test_dependency_wait_timeout_is_reported_and_recoverable(sn):
+@pytest.mark.parametrize("schedule", [("dataflow", 128, 0), ("tiles", 128, 8)])
+def test_dependency_wait_timeout_is_reported_and_recoverable(sn, schedule):
     prob = CASES["c2_32"]()
     m = sn.Mesh.from_problem(prob)
-    m.set_schedule("dataflow", 128, 0)
+    m.set_schedule(*schedule)
     phi = torch.as_tensor(inputs.random_phi(prob, 6), device="cuda")
     ref = m.sweep(phi)
     m.debug_stall_next_sweep(0.2)
@@ -62,13 +65,14 @@ def test_adjoint_schedules_agree_bitwise(sn, name):
     mu = torch.as_tensor(inputs.random_phi(prob, 8) - 0.7, device="cuda")
     m.set_schedule("levels", 128)
     ref = m.adjoint_sweep(mu)
-    for block, cap in ((128, 0), (32, 1)):
-        m.set_schedule("dataflow", block, cap)
-        assert torch.equal(m.adjoint_sweep(mu), ref), (block, cap)
+    for sched, block, param in (("dataflow", 128, 0), ("dataflow", 32, 1), ("tiles", 128, 8)):
+        m.set_schedule(sched, block, param)
+        assert torch.equal(m.adjoint_sweep(mu), ref), (sched, block, param)
 
 
 CANDIDATES = {("levels", 32, 0), ("levels", 64, 0), ("levels", 128, 0), ("dataflow", 128, 0), ("dataflow", 128, 1),
-              ("dataflow", 64, 2), ("dataflow", 32, 4)}
+              ("dataflow", 64, 2), ("dataflow", 32, 4), ("tiles", 128, 8), ("tiles", 128, 16), ("tiles", 256, 16),
+              ("tiles", 256, 32)}
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

@@ -49,6 +49,10 @@ def peaks():
         return {}
 
 
+# DRAM bytes per item of node_level_kernel<2,2,FP64> on this workload, from the ncu capture
+# summarised in profiles/node_level_kernel_fp64_c2_256x256_q2_s8.md (read + write, 3 launches)
+NODE_KERNEL_DRAM_BYTES_PER_ITEM = 1386.0
+
 # FP64 FMA peak: 152 SMs x 4 sub-partitions x 0.5 FP64 FMA/clk x 2 flop x 2.07 GHz (GB300 runs FP64 at
 # 1/64 of the FP32 rate); an FMA-chain probe on this GPU measured 1.01 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
@@ -287,8 +291,12 @@ def run_ours(args, rank, ws):
     bytes_item = bytes_per_item(n, prob.dim, prob.p)
     achieved = bytes_item * mesh.n_elem * mesh.n_dirs / (sweep_ms / 1e3) / 1e9
     hbm = peaks().get("hbm_gbs")
+    items_per_launch = mesh.n_elem * mesh.n_dirs / n_launch_sweep
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm or 6800.0, "unit": "GB/s",
-                "frac": achieved / (hbm or 6800.0), "traffic": None,
+                "frac": achieved / (hbm or 6800.0),
+                "traffic": NODE_KERNEL_DRAM_BYTES_PER_ITEM * items_per_launch,
+                "traffic_source": "ncu dram__bytes_read+write of three mid-sweep launches, per item, scaled "
+                                  "to the average launch (profiles/node_level_kernel_fp64_c2_256x256_q2_s8.md)",
                 "kernel": "node_level_kernel<2,2,FP64> (cached sweep)", "launches_per_sweep": n_launch_sweep,
                 "bytes_per_elem_dir": bytes_item,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else "fallback 6.8 TB/s",
@@ -298,6 +306,7 @@ def run_ours(args, rank, ws):
     # other forms (not part of value): FP32 element solves, FP32 + FP64 refinement, and
     # unaccelerated-by-Krylov source iteration with the same DSA (capped at 300 iterations)
     forms = {}
+    phi64 = phi.clone()  # the FP64 fGMRES solution of the last timed step
     for prec, outer in (("fp32", "fgmres"), ("fp32_refine", "fgmres"), ("fp64", "si")):
         o = dict(opts, precision=prec, outer=outer, max_iters=300)
         mesh.source_iterate(phi=phi, **o)
@@ -307,8 +316,10 @@ def run_ours(args, rank, ws):
         rr = mesh.source_iterate(phi=phi, **o)
         b.record(stream)
         torch.cuda.synchronize()
+        err = float((phi - phi64).abs().max() / phi64.abs().max())
         forms[f"{prec}_{outer}"] = {"ms_to_tol": a.elapsed_time(b), "iters": rr["iters"], "sweeps": rr["sweeps"],
-                                    "rel_residual": rr["rel_residual"], "converged": rr["converged"]}
+                                    "rel_residual": rr["rel_residual"], "converged": rr["converged"],
+                                    "max_rel_err_vs_fp64_solution": err}
 
     # end to end through the C ABI with host buffers: H2D materials, solve, D2H phi
     st_h = torch.as_tensor(prob.sigma_t).pin_memory()

@@ -16,9 +16,11 @@
 // nodes); coarser levels halve the vertex grid per axis with linear interpolation; every
 // coarse operator is the Galerkin product P^T A P; the coarsest is inverted densely.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
-#include <map>
 #include <string>
+#include <thread>
+#include <utility>
 #include <vector>
 
 #include "sn_dsa.h"
@@ -194,9 +196,32 @@ void basis_at(const GL1D& g, int dim, const double* xi, std::vector<double>& val
 
 }  // namespace
 
+// Runs f(i) for i in [0, n) on the host's cores (fixed chunks claimed from a shared counter; every
+// f(i) must touch data of its own index only, so the result does not depend on the schedule).
+template <typename F>
+void parallel_for(int n, F&& f) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int T = (int)std::max(1u, std::min(hw == 0 ? 1u : hw, 32u));
+    if (n < 512 || T == 1) {
+        for (int i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::atomic<int> next{0};
+    constexpr int chunk = 64;
+    auto work = [&]() {
+        int s0;
+        while ((s0 = next.fetch_add(chunk)) < n)
+            for (int i = s0; i < std::min(n, s0 + chunk); ++i) f(i);
+    };
+    std::vector<std::thread> th;
+    for (int k = 1; k < T; ++k) th.emplace_back(work);
+    work();
+    for (auto& t : th) t.join();
+}
+
 DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sigma, std::string& err) {
     auto* H = new DsaHierarchy();
-    const int dim = m->dim, p = m->p, n = m->n, Q = p + 1;
+    const int dim = m->dim, p = m->p, n = m->n, Q = p + 1, nf = 2 * dim;
     H->n = n;
     H->ne = m->ne;
     for (int e = 0; e < m->ne; ++e)
@@ -204,6 +229,12 @@ DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sig
     const int nt = (int)H->thick.size();
     H->nt = nt;
     if (nt == 0) return H;
+    for (int e : H->thick)
+        if (!(m->h_sigma_t[e] > 0.0)) {
+            err = "DSA on an element with sigma_t = 0";
+            delete H;
+            return nullptr;
+        }
     std::vector<int> local(m->ne, -1);
     for (int t = 0; t < nt; ++t) local[H->thick[t]] = t;
     const GL1D g = gauss_legendre_nodal(p);
@@ -229,6 +260,9 @@ DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sig
         }
         return em;
     };
+    auto coord = [&](int e, int ax) {
+        return ax == 0 ? e % m->nx : (ax == 1 ? (e / m->nx) % m->ny : e / (m->nx * m->ny));
+    };
     auto neighbor = [&](int e, int f) {
         const int ax = f >> 1, side = f & 1;
         int i = e % m->nx, j = (e / m->nx) % m->ny, k = e / (m->nx * m->ny);
@@ -239,249 +273,354 @@ DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sig
         return i + m->nx * (j + m->ny * k);
     };
 
-    // per thick element: volume, D, sigma_a, rhs mass
-    std::vector<double> vol(nt), Dc(nt), sa(nt);
-    H->h_mass_sig.assign((size_t)nt * n, 0.0);
-    std::vector<std::vector<double>> blocks;  // BSR blocks
-    std::vector<std::map<int, int>> rowcols(nt);
-    auto block = [&](int r, int c) -> double* {
-        auto it = rowcols[r].find(c);
-        if (it == rowcols[r].end()) {
-            blocks.emplace_back(n * n, 0.0);
-            rowcols[r][c] = (int)blocks.size() - 1;
-            return blocks.back().data();
-        }
-        return blocks[it->second].data();
-    };
-    std::vector<double> val, grad;
-    const int NQ = n;  // volume points = nodes
-    for (int t = 0; t < nt; ++t) {
-        const int e = H->thick[t];
-        const double st = m->h_sigma_t[e], ss = m->h_sigma_s[e];
-        if (!(st > 0.0)) {
-            err = "DSA on an element with sigma_t = 0";
-            delete H;
-            return nullptr;
-        }
-        Dc[t] = 1.0 / (3.0 * st);
-        sa[t] = st - ss;
-        const double sig = dsa_sigma == SN_DSA_SIGMA_T ? st : ss;
-        ElemMap em = elem_map(e);
-        double* K = block(t, t);
-        double V = 0.0;
-        for (int q = 0; q < NQ; ++q) {
+    // reference basis data, the same for every element: values and reference gradients at the
+    // volume nodes and at the face quadrature points of every face
+    const int QF = dim == 2 ? Q : Q * Q;
+    std::vector<double> vval((size_t)n * n), vgrad((size_t)n * n * dim), vW(n);
+    std::vector<double> fval((size_t)nf * QF * n), fgrad((size_t)nf * QF * n * dim), fW((size_t)nf * QF);
+    std::vector<double> fxi((size_t)nf * QF * 3);
+    {
+        std::vector<double> val, grad;
+        for (int q = 0; q < n; ++q) {
             const int qi[3] = {q % Q, (q / Q) % Q, q / (Q * Q)};
-            double xi[3], W = 1.0;
+            double xi[3] = {0, 0, 0}, W = 1.0;
             for (int a = 0; a < dim; ++a) {
                 xi[a] = g.x[qi[a]];
                 W *= g.w[qi[a]];
             }
-            double x[3], J[3][3], Ji[3][3];
-            em.eval(xi, x, J);
-            const double dJ = det_inv(dim, J, Ji);
-            V += W * dJ;
+            vW[q] = W;
             basis_at(g, dim, xi, val, grad);
-            // physical gradients
-            std::vector<double> gp(n * dim, 0.0);
-            for (int i = 0; i < n; ++i)
-                for (int r = 0; r < dim; ++r) {
-                    double s = 0.0;
-                    for (int k = 0; k < dim; ++k) s += Ji[k][r] * grad[i * dim + k];
-                    gp[i * dim + r] = s;
-                }
-            for (int i = 0; i < n; ++i)
-                for (int j = 0; j < n; ++j) {
-                    double s = 0.0;
-                    for (int r = 0; r < dim; ++r) s += gp[i * dim + r] * gp[j * dim + r];
-                    K[i * n + j] += W * dJ * (Dc[t] * s + sa[t] * val[i] * val[j]);
-                }
-            H->h_mass_sig[(size_t)t * n + q] = sig * W * dJ;  // collocated mass at node q
+            std::copy(val.begin(), val.end(), vval.begin() + (size_t)q * n);
+            std::copy(grad.begin(), grad.end(), vgrad.begin() + (size_t)q * n * dim);
         }
-        vol[t] = V;
-    }
-    // faces
-    const int QF = dim == 2 ? Q : Q * Q;
-    for (int t = 0; t < nt; ++t) {
-        const int e = H->thick[t];
-        ElemMap em = elem_map(e);
-        for (int f = 0; f < 2 * dim; ++f) {
-            const int ax = f >> 1, side = f & 1;
-            const double s = side ? 1.0 : -1.0;
-            const int u = neighbor(e, f);
-            const int o = u >= 0 ? local[u] : -1;
-            if (o >= 0 && side == 0) continue;  // interior faces are assembled from their side-1 element
-            ElemMap emo;
-            if (o >= 0) emo = elem_map(u);
-            // face quadrature data
-            std::vector<double> dS(QF), nrm(QF * 3), Be(QF * n), Dne(QF * n), Bo, Dno;
-            if (o >= 0) {
-                Bo.assign(QF * n, 0.0);
-                Dno.assign(QF * n, 0.0);
-            }
-            double area = 0.0;
+        for (int f = 0; f < nf; ++f) {
+            const int ax = f >> 1;
+            const double s = (f & 1) ? 1.0 : -1.0;
             for (int qf = 0; qf < QF; ++qf) {
-                int tq[2] = {qf % Q, qf / Q};
-                double xi[3], xio[3], Wt = 1.0;
+                const int tq[2] = {qf % Q, qf / Q};
+                double* xi = &fxi[((size_t)f * QF + qf) * 3];
+                double Wt = 1.0;
                 int c = 0;
+                for (int a = 0; a < 3; ++a) xi[a] = 0.0;
                 for (int a = 0; a < dim; ++a) {
                     if (a == ax) {
                         xi[a] = s;
-                        xio[a] = -s;
                     } else {
                         xi[a] = g.x[tq[c]];
-                        xio[a] = xi[a];
                         Wt *= g.w[tq[c]];
                         ++c;
                     }
                 }
-                double x[3], J[3][3], Ji[3][3];
-                em.eval(xi, x, J);
-                const double dJ = det_inv(dim, J, Ji);
-                // Nanson: n dS = det J J^{-T} (s e_ax) dt  -> components s * dJ * Ji[ax][r]
-                double Nv[3] = {0, 0, 0}, len = 0.0;
-                for (int r = 0; r < dim; ++r) {
-                    Nv[r] = s * dJ * Ji[ax][r];
-                    len += Nv[r] * Nv[r];
-                }
-                len = std::sqrt(len);
-                dS[qf] = len * Wt;
-                area += dS[qf];
-                for (int r = 0; r < dim; ++r) nrm[qf * 3 + r] = Nv[r] / len;
+                fW[(size_t)f * QF + qf] = Wt;
                 basis_at(g, dim, xi, val, grad);
-                for (int i = 0; i < n; ++i) {
-                    Be[qf * n + i] = val[i];
-                    double dn = 0.0;
-                    for (int r = 0; r < dim; ++r) {
-                        double gr = 0.0;
-                        for (int k = 0; k < dim; ++k) gr += Ji[k][r] * grad[i * dim + k];
-                        dn += gr * nrm[qf * 3 + r];
-                    }
-                    Dne[qf * n + i] = dn;
-                }
-                if (o >= 0) {
-                    double xo[3], Jo[3][3], Jio[3][3];
-                    emo.eval(xio, xo, Jo);
-                    det_inv(dim, Jo, Jio);
-                    basis_at(g, dim, xio, val, grad);
-                    for (int i = 0; i < n; ++i) {
-                        Bo[qf * n + i] = val[i];
-                        double dn = 0.0;
-                        for (int r = 0; r < dim; ++r) {
-                            double gr = 0.0;
-                            for (int k = 0; k < dim; ++k) gr += Jio[k][r] * grad[i * dim + k];
-                            dn += gr * nrm[qf * 3 + r];
-                        }
-                        Dno[qf * n + i] = dn;
-                    }
-                }
-            }
-            const double h = vol[t] / area;
-            if (o < 0) {
-                const double kap = std::max(0.25, cp * Dc[t] / h);
-                double* K = block(t, t);
-                for (int qf = 0; qf < QF; ++qf)
-                    for (int i = 0; i < n; ++i)
-                        for (int j = 0; j < n; ++j)
-                            K[i * n + j] += dS[qf] * (kap * Be[qf * n + i] * Be[qf * n + j] -
-                                                      0.5 * Dc[t] * Dne[qf * n + j] * Be[qf * n + i] -
-                                                      0.5 * Dc[t] * Dne[qf * n + i] * Be[qf * n + j]);
-            } else {
-                const double ho = vol[o] / area;
-                const double kap = std::max(0.25, cp * 0.5 * (Dc[t] / h + Dc[o] / ho));
-                struct Side { int r; const std::vector<double>* B; const std::vector<double>* Dn; double D, sg; };
-                Side sides[2] = {{t, &Be, &Dne, Dc[t], 1.0}, {o, &Bo, &Dno, Dc[o], -1.0}};
-                for (const Side& A : sides)
-                    for (const Side& Bs : sides) {
-                        double* K = block(A.r, Bs.r);
-                        for (int qf = 0; qf < QF; ++qf)
-                            for (int i = 0; i < n; ++i)
-                                for (int j = 0; j < n; ++j)
-                                    K[i * n + j] += dS[qf] * (kap * A.sg * Bs.sg * (*A.B)[qf * n + i] * (*Bs.B)[qf * n + j] -
-                                                              0.5 * Bs.D * A.sg * (*Bs.Dn)[qf * n + j] * (*A.B)[qf * n + i] -
-                                                              0.5 * A.D * Bs.sg * (*A.Dn)[qf * n + i] * (*Bs.B)[qf * n + j]);
-                    }
+                std::copy(val.begin(), val.end(), fval.begin() + ((size_t)f * QF + qf) * n);
+                std::copy(grad.begin(), grad.end(), fgrad.begin() + ((size_t)f * QF + qf) * n * dim);
             }
         }
     }
-    // BSR level 0 + expanded CSR for the Galerkin products
+
+    // BSR structure: every thick element's row holds its own block and those of its thick face
+    // neighbours, columns ascending
     Level0& L0 = H->l0;
     L0.ptr.assign(nt + 1, 0);
     for (int t = 0; t < nt; ++t) {
-        for (auto& kv : rowcols[t]) {
-            L0.col.push_back(kv.first);
-            L0.val.insert(L0.val.end(), blocks[kv.second].begin(), blocks[kv.second].end());
+        int cnt = 1;
+        for (int f = 0; f < nf; ++f) {
+            const int u = neighbor(H->thick[t], f);
+            if (u >= 0 && local[u] >= 0) ++cnt;
         }
-        L0.ptr[t + 1] = (int)L0.col.size();
+        L0.ptr[t + 1] = L0.ptr[t] + cnt;
     }
-    L0.dinv.resize((size_t)nt * n * n);
-    for (int t = 0; t < nt; ++t) {
-        std::vector<double> B = blocks[rowcols[t][t]];
-        if (!invert(B, n)) {
-            err = "singular diagonal block in the DSA operator";
-            delete H;
-            return nullptr;
+    L0.col.resize(L0.ptr[nt]);
+    parallel_for(nt, [&](int t) {
+        int* c = &L0.col[L0.ptr[t]];
+        int k = 0;
+        c[k++] = t;
+        for (int f = 0; f < nf; ++f) {
+            const int u = neighbor(H->thick[t], f);
+            if (u >= 0 && local[u] >= 0) c[k++] = local[u];
         }
-        std::copy(B.begin(), B.end(), L0.dinv.begin() + (size_t)t * n * n);
-    }
-    Csr A;
-    A.rows = A.cols = nt * n;
-    A.ptr.assign(nt * n + 1, 0);
-    for (int t = 0; t < nt; ++t)
-        for (int i = 0; i < n; ++i) {
-            for (int k = L0.ptr[t]; k < L0.ptr[t + 1]; ++k)
-                for (int j = 0; j < n; ++j) {
-                    A.col.push_back(L0.col[k] * n + j);
-                    A.val.push_back(L0.val[(size_t)k * n * n + i * n + j]);
-                }
-            A.ptr[t * n + i + 1] = (int)A.col.size();
-        }
+        std::sort(c, c + k);
+    });
+    L0.val.assign((size_t)L0.ptr[nt] * n * n, 0.0);
+    auto block = [&](int r, int c) -> double* {
+        for (int k = L0.ptr[r]; k < L0.ptr[r + 1]; ++k)
+            if (L0.col[k] == c) return &L0.val[(size_t)k * n * n];
+        return nullptr;  // unreachable: the structure holds every face pair
+    };
 
-    // level 1: continuous Q1 on the vertices of thick elements
+    // volume terms: (D grad u, grad v) + (sigma_a u, v), collocated at the nodes
+    std::vector<double> vol(nt), Dc(nt), sa(nt);
+    H->h_mass_sig.assign((size_t)nt * n, 0.0);
+    parallel_for(nt, [&](int t) {
+        const int e = H->thick[t];
+        const double st = m->h_sigma_t[e], ss = m->h_sigma_s[e];
+        Dc[t] = 1.0 / (3.0 * st);
+        sa[t] = st - ss;
+        const double sig = dsa_sigma == SN_DSA_SIGMA_T ? st : ss;
+        const ElemMap em = elem_map(e);
+        double* K = block(t, t);
+        double V = 0.0;
+        std::vector<double> gp((size_t)n * dim);
+        for (int q = 0; q < n; ++q) {
+            const int qi[3] = {q % Q, (q / Q) % Q, q / (Q * Q)};
+            double xi[3] = {0, 0, 0};
+            for (int a = 0; a < dim; ++a) xi[a] = g.x[qi[a]];
+            const double W = vW[q];
+            double x[3], J[3][3], Ji[3][3];
+            em.eval(xi, x, J);
+            const double dJ = det_inv(dim, J, Ji);
+            V += W * dJ;
+            const double* val = &vval[(size_t)q * n];
+            const double* grad = &vgrad[(size_t)q * n * dim];
+            for (int i = 0; i < n; ++i)
+                for (int r = 0; r < dim; ++r) {
+                    double sum = 0.0;
+                    for (int k = 0; k < dim; ++k) sum += Ji[k][r] * grad[i * dim + k];
+                    gp[i * dim + r] = sum;
+                }
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    double sum = 0.0;
+                    for (int r = 0; r < dim; ++r) sum += gp[i * dim + r] * gp[j * dim + r];
+                    K[i * n + j] += W * dJ * (Dc[t] * sum + sa[t] * val[i] * val[j]);
+                }
+            H->h_mass_sig[(size_t)t * n + q] = sig * W * dJ;  // collocated mass at node q
+        }
+        vol[t] = V;
+    });
+
+    // face terms.  An interior thick-thick face is assembled once, from its side-1 element, into
+    // the rows of both elements; a face to a non-thick element or the boundary into its own row.
+    // Pass (axis, parity) takes the elements whose coordinate along the axis has that parity, so
+    // no two faces of one pass write the same row.
+    struct FaceData {
+        std::vector<double> dS, nrm, B, Dn;
+        double area;
+    };
+    auto face_geometry = [&](const ElemMap& em, int f, FaceData& F) {
+        const int ax = f >> 1;
+        const double s = (f & 1) ? 1.0 : -1.0;
+        F.dS.resize(QF);
+        F.nrm.resize((size_t)QF * 3);
+        F.area = 0.0;
+        for (int qf = 0; qf < QF; ++qf) {
+            const double* xi = &fxi[((size_t)f * QF + qf) * 3];
+            double x[3], J[3][3], Ji[3][3];
+            em.eval(xi, x, J);
+            const double dJ = det_inv(dim, J, Ji);
+            // Nanson: n dS = det J J^{-T} (s e_ax) dt
+            double Nv[3] = {0, 0, 0}, len = 0.0;
+            for (int r = 0; r < dim; ++r) {
+                Nv[r] = s * dJ * Ji[ax][r];
+                len += Nv[r] * Nv[r];
+            }
+            len = std::sqrt(len);
+            F.dS[qf] = len * fW[(size_t)f * QF + qf];
+            F.area += F.dS[qf];
+            for (int r = 0; r < dim; ++r) F.nrm[qf * 3 + r] = Nv[r] / len;
+        }
+    };
+    // values and normal derivatives on face f of an element with map em, along the normals F.nrm
+    auto face_traces = [&](const ElemMap& em, int f, const std::vector<double>& nrm, std::vector<double>& B,
+                           std::vector<double>& Dn) {
+        B.resize((size_t)QF * n);
+        Dn.resize((size_t)QF * n);
+        for (int qf = 0; qf < QF; ++qf) {
+            const double* xi = &fxi[((size_t)f * QF + qf) * 3];
+            double x[3], J[3][3], Ji[3][3];
+            em.eval(xi, x, J);
+            det_inv(dim, J, Ji);
+            const double* val = &fval[((size_t)f * QF + qf) * n];
+            const double* grad = &fgrad[((size_t)f * QF + qf) * n * dim];
+            for (int i = 0; i < n; ++i) {
+                B[qf * n + i] = val[i];
+                double dn = 0.0;
+                for (int r = 0; r < dim; ++r) {
+                    double gr = 0.0;
+                    for (int k = 0; k < dim; ++k) gr += Ji[k][r] * grad[i * dim + k];
+                    dn += gr * nrm[qf * 3 + r];
+                }
+                Dn[qf * n + i] = dn;
+            }
+        }
+    };
+    for (int ax = 0; ax < dim; ++ax)
+        for (int parity = 0; parity < 2; ++parity)
+            parallel_for(nt, [&](int t) {
+                const int e = H->thick[t];
+                if (coord(e, ax) % 2 != parity) return;
+                FaceData F;
+                std::vector<double> Be, Dne, Bo, Dno;
+                for (int side = 0; side < 2; ++side) {
+                    const int f = 2 * ax + side;
+                    const int u = neighbor(e, f);
+                    const int o = u >= 0 ? local[u] : -1;
+                    if (o >= 0 && side == 0) continue;  // assembled by the side-1 element
+                    const ElemMap em = elem_map(e);
+                    face_geometry(em, f, F);
+                    face_traces(em, f, F.nrm, Be, Dne);
+                    const double h = vol[t] / F.area;
+                    if (o < 0) {
+                        const double kap = std::max(0.25, cp * Dc[t] / h);
+                        double* K = block(t, t);
+                        for (int qf = 0; qf < QF; ++qf)
+                            for (int i = 0; i < n; ++i)
+                                for (int j = 0; j < n; ++j)
+                                    K[i * n + j] += F.dS[qf] * (kap * Be[qf * n + i] * Be[qf * n + j] -
+                                                                0.5 * Dc[t] * Dne[qf * n + j] * Be[qf * n + i] -
+                                                                0.5 * Dc[t] * Dne[qf * n + i] * Be[qf * n + j]);
+                        continue;
+                    }
+                    face_traces(elem_map(u), f ^ 1, F.nrm, Bo, Dno);
+                    const double ho = vol[o] / F.area;
+                    const double kap = std::max(0.25, cp * 0.5 * (Dc[t] / h + Dc[o] / ho));
+                    struct Side { int r; const std::vector<double>* B; const std::vector<double>* Dn; double D, sg; };
+                    const Side sides[2] = {{t, &Be, &Dne, Dc[t], 1.0}, {o, &Bo, &Dno, Dc[o], -1.0}};
+                    for (const Side& A : sides)
+                        for (const Side& Bs : sides) {
+                            double* K = block(A.r, Bs.r);
+                            for (int qf = 0; qf < QF; ++qf)
+                                for (int i = 0; i < n; ++i)
+                                    for (int j = 0; j < n; ++j)
+                                        K[i * n + j] += F.dS[qf] * (kap * A.sg * Bs.sg * (*A.B)[qf * n + i] * (*Bs.B)[qf * n + j] -
+                                                                    0.5 * Bs.D * A.sg * (*Bs.Dn)[qf * n + j] * (*A.B)[qf * n + i] -
+                                                                    0.5 * A.D * Bs.sg * (*A.Dn)[qf * n + i] * (*Bs.B)[qf * n + j]);
+                        }
+                }
+            });
+
+    // inverse diagonal blocks (block-Jacobi smoother)
+    L0.dinv.resize((size_t)nt * n * n);
+    std::atomic<int> singular{0};
+    parallel_for(nt, [&](int t) {
+        const double* K = block(t, t);
+        std::vector<double> B(K, K + (size_t)n * n);
+        if (!invert(B, n)) singular = 1;
+        std::copy(B.begin(), B.end(), L0.dinv.begin() + (size_t)t * n * n);
+    });
+    if (singular) {
+        err = "singular diagonal block in the DSA operator";
+        delete H;
+        return nullptr;
+    }
+
+    // level 1: continuous Q1 on the vertices of thick elements.  The prolongation of an element is
+    // its own bilinear (trilinear) map evaluated at its nodes: the same n x 2^dim matrix Pref for
+    // every element, so A_1 = P^T A P is accumulated block by block as Pref^T K_tc Pref.
+    const int nc = 1 << dim;
     const int vx = m->nx + 1, vy = m->ny + 1, vz = dim == 3 ? m->nz + 1 : 1;
     std::vector<int> vid((size_t)vx * vy * vz, -1);
     std::vector<int> vgrid;  // active vertex -> grid index
+    std::vector<int> evid((size_t)nt * nc);
     for (int t = 0; t < nt; ++t) {
         const int e = H->thick[t];
         const int i = e % m->nx, j = (e / m->nx) % m->ny, k = e / (m->nx * m->ny);
-        for (int c = 0; c < (1 << dim); ++c) {
+        for (int c = 0; c < nc; ++c) {
             const size_t gid = (i + (c & 1)) + (size_t)vx * ((j + ((c >> 1) & 1)) + (size_t)vy * (dim == 3 ? k + ((c >> 2) & 1) : 0));
             if (vid[gid] < 0) {
                 vid[gid] = (int)vgrid.size();
                 vgrid.push_back((int)gid);
             }
+            evid[(size_t)t * nc + c] = vid[gid];
+        }
+    }
+    const int nv = (int)vgrid.size();
+    std::vector<double> Pref((size_t)n * nc);
+    for (int q = 0; q < n; ++q) {
+        const int qi[3] = {q % Q, (q / Q) % Q, q / (Q * Q)};
+        for (int c = 0; c < nc; ++c) {
+            double N = 1.0;
+            for (int a = 0; a < dim; ++a) N *= 0.5 * (1.0 + (((c >> a) & 1) ? 1.0 : -1.0) * g.x[qi[a]]);
+            Pref[(size_t)q * nc + c] = N;
         }
     }
     Csr P;
     P.rows = nt * n;
-    P.cols = (int)vgrid.size();
-    P.ptr.assign(P.rows + 1, 0);
-    for (int t = 0; t < nt; ++t) {
-        const int e = H->thick[t];
-        const int i = e % m->nx, j = (e / m->nx) % m->ny, k = e / (m->nx * m->ny);
-        for (int q = 0; q < n; ++q) {
-            const int qi[3] = {q % Q, (q / Q) % Q, q / (Q * Q)};
-            std::vector<std::pair<int, double>> ent;
-            for (int c = 0; c < (1 << dim); ++c) {
-                double N = 1.0;
-                for (int a = 0; a < dim; ++a) N *= 0.5 * (1.0 + (((c >> a) & 1) ? 1.0 : -1.0) * g.x[qi[a]]);
-                const size_t gid = (i + (c & 1)) + (size_t)vx * ((j + ((c >> 1) & 1)) + (size_t)vy * (dim == 3 ? k + ((c >> 2) & 1) : 0));
-                ent.push_back({vid[gid], N});
+    P.cols = nv;
+    P.ptr.resize(P.rows + 1);
+    for (int r = 0; r <= P.rows; ++r) P.ptr[r] = r * nc;
+    P.col.resize((size_t)P.rows * nc);
+    P.val.resize((size_t)P.rows * nc);
+    parallel_for(nt, [&](int t) {
+        int ord[8];
+        for (int c = 0; c < nc; ++c) ord[c] = c;
+        std::sort(ord, ord + nc, [&](int a, int b) { return evid[(size_t)t * nc + a] < evid[(size_t)t * nc + b]; });
+        for (int q = 0; q < n; ++q)
+            for (int k = 0; k < nc; ++k) {
+                const size_t pos = ((size_t)t * n + q) * nc + k;
+                P.col[pos] = evid[(size_t)t * nc + ord[k]];
+                P.val[pos] = Pref[(size_t)q * nc + ord[k]];
             }
-            std::sort(ent.begin(), ent.end());
-            for (auto& pr : ent) {
-                P.col.push_back(pr.first);
-                P.val.push_back(pr.second);
+    });
+    // KP = K_tc Pref for every block
+    const size_t nnzb = L0.col.size();
+    std::vector<double> KP(nnzb * n * nc);
+    parallel_for((int)nnzb, [&](int b) {
+        const double* K = &L0.val[(size_t)b * n * n];
+        double* o = &KP[(size_t)b * n * nc];
+        for (int i = 0; i < n; ++i)
+            for (int c = 0; c < nc; ++c) {
+                double sum = 0.0;
+                for (int j = 0; j < n; ++j) sum += K[i * n + j] * Pref[(size_t)j * nc + c];
+                o[i * nc + c] = sum;
             }
-            P.ptr[t * n + q + 1] = (int)P.col.size();
-        }
+    });
+    // rows of A_1: vertex v gathers Pref[:, a]^T KP_tc over the (t, a) that touch it
+    std::vector<int> vt_ptr(nv + 1, 0), vt((size_t)nt * nc);
+    for (size_t k = 0; k < evid.size(); ++k) vt_ptr[evid[k] + 1]++;
+    for (int v = 0; v < nv; ++v) vt_ptr[v + 1] += vt_ptr[v];
+    {
+        std::vector<int> fill(vt_ptr.begin(), vt_ptr.end() - 1);
+        for (size_t k = 0; k < evid.size(); ++k) vt[fill[evid[k]]++] = (int)k;  // k = t * nc + a, ascending
     }
+    std::vector<std::vector<std::pair<int, double>>> arows(nv);
+    parallel_for(nv, [&](int v) {
+        std::vector<std::pair<int, double>>& row = arows[v];
+        for (int s = vt_ptr[v]; s < vt_ptr[v + 1]; ++s) {
+            const int t = vt[s] / nc, a = vt[s] % nc;
+            for (int b = L0.ptr[t]; b < L0.ptr[t + 1]; ++b) {
+                const int c = L0.col[b];
+                const double* kp = &KP[(size_t)b * n * nc];
+                for (int cc = 0; cc < nc; ++cc) {
+                    double sum = 0.0;
+                    for (int i = 0; i < n; ++i) sum += Pref[(size_t)i * nc + a] * kp[i * nc + cc];
+                    const int col = evid[(size_t)c * nc + cc];
+                    bool found = false;
+                    for (auto& pr : row)
+                        if (pr.first == col) {
+                            pr.second += sum;
+                            found = true;
+                            break;
+                        }
+                    if (!found) row.push_back({col, sum});
+                }
+            }
+        }
+        std::sort(row.begin(), row.end(), [](const std::pair<int, double>& x, const std::pair<int, double>& y) {
+            return x.first < y.first;
+        });
+    });
+    Csr A1;
+    A1.rows = A1.cols = nv;
+    A1.ptr.assign(nv + 1, 0);
+    for (int v = 0; v < nv; ++v) A1.ptr[v + 1] = A1.ptr[v] + (int)arows[v].size();
+    A1.col.resize(A1.ptr[nv]);
+    A1.val.resize(A1.ptr[nv]);
+    parallel_for(nv, [&](int v) {
+        for (size_t k = 0; k < arows[v].size(); ++k) {
+            A1.col[A1.ptr[v] + k] = arows[v][k].first;
+            A1.val[A1.ptr[v] + k] = arows[v][k].second;
+        }
+    });
+
     struct GridLevel { int nx, ny, nz; std::vector<int> gids; };  // cells per axis, active vertex grid ids
     GridLevel cur{m->nx, m->ny, dim == 3 ? m->nz : 0, vgrid};
-    Csr Acur = A;
+    Csr Acur;
     Csr Pcur = P;
     for (int lev = 1; lev < 32; ++lev) {
         Csr Pt = transpose(Pcur);
-        Csr Ac = multiply(Pt, multiply(Acur, Pcur));
+        Csr Ac = lev == 1 ? std::move(A1) : multiply(Pt, multiply(Acur, Pcur));
         LevelC L;
         L.n = Ac.rows;
         L.p_ptr = Pcur.ptr; L.p_col = Pcur.col; L.p_val = Pcur.val;

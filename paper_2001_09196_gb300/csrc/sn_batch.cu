@@ -54,8 +54,10 @@ struct UnionDsa {
     double *x = nullptr, *b = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *vr = nullptr;
     double* part = nullptr;
     double* s = nullptr;         // [0] rz [1] pq [2] rr [3] bb [4] rz_new
-    int* done = nullptr;         // 1 once the solve has converged (or b = 0)
+    int* done = nullptr;         // 1 once the solve has converged (or b = 0); 0 in the recorded loop
     int* iters = nullptr;        // PCG iterations performed (device counter)
+    int* local_iters = nullptr;  // iterations of the current solve (recorded loop)
+    cudaStream_t cap2 = nullptr; // captures the loop body while the batched iteration is recorded
     double omega0 = 0.6, omega = 0.6;
     int nu = 2;
     std::vector<DsaHierarchy*> parts;  // host hierarchies (kept for their sizes)
@@ -226,6 +228,23 @@ __global__ void u_check(double* s, double tol2, int* done, int* iters) {
 __global__ void u_shift(double* s, const int* done) {
     SKIP_IF_DONE;
     s[0] = s[4];
+}
+
+// Start of the recorded union PCG: s[0] = +inf makes the first search direction p = z; the loop
+// body runs only when b != 0.
+__global__ void u_loop_start(double* s, int* local_iters, cudaGraphConditionalHandle h) {
+    s[0] = INFINITY;
+    *local_iters = 0;
+    cudaGraphSetConditional(h, s[3] > 0.0 ? 1u : 0u);
+}
+
+// End of one recorded union PCG iteration: continue while ||r||^2 > tol^2 ||b||^2 and fewer than
+// max_iters iterations; iters accumulates the batch's PCG count.
+__global__ void u_loop_check(const double* s, double tol2, int max_iters, int* local_iters, int* iters,
+                             cudaGraphConditionalHandle h) {
+    const int k = ++*local_iters;
+    *iters += 1;
+    cudaGraphSetConditional(h, (s[2] > tol2 * s[3] && k < max_iters) ? 1u : 0u);
 }
 
 template <typename T>
@@ -473,6 +492,7 @@ UnionDsa* union_dsa_build(const std::vector<DsaHierarchy*>& parts, const std::ve
     if ((cerr = cudaMalloc(&U->part, kParts * sizeof(double))) != cudaSuccess ||
         (cerr = cudaMalloc(&U->s, 8 * sizeof(double))) != cudaSuccess ||
         (cerr = cudaMalloc(&U->done, sizeof(int))) != cudaSuccess ||
+        (cerr = cudaMalloc(&U->local_iters, sizeof(int))) != cudaSuccess ||
         (cerr = cudaMalloc(&U->iters, sizeof(int))) != cudaSuccess) {
         err = cudaGetErrorString(cerr);
         return U;
@@ -495,8 +515,10 @@ void union_dsa_free(UnionDsa* U) {
     for (void* p : {(void*)U->row_dof, (void*)U->mass_sig, (void*)U->row_inst, (void*)U->inst_n, (void*)U->inst_row0,
                     (void*)U->inst_ptr0, (void*)U->inst_blk0, (void*)U->inst_val0, (void*)U->inst_dinv0, (void*)U->bsr_ptr, (void*)U->bsr_col,
                     (void*)U->bsr_val, (void*)U->dinv, (void*)U->x, (void*)U->b, (void*)U->r, (void*)U->z, (void*)U->p,
-                    (void*)U->q, (void*)U->vr, (void*)U->part, (void*)U->s, (void*)U->done, (void*)U->iters})
+                    (void*)U->q, (void*)U->vr, (void*)U->part, (void*)U->s, (void*)U->done, (void*)U->iters,
+                    (void*)U->local_iters})
         f(p);
+    if (U->cap2) cudaStreamDestroy(U->cap2);
     for (DsaHierarchy* H : U->parts) dsa_free(H);
     delete U;
 }
@@ -505,39 +527,66 @@ long long union_dsa_rows(const UnionDsa* U) { return U ? U->n0 : 0; }
 int* union_dsa_iters(UnionDsa* U) { return U->iters; }
 
 // phi_all[thick rows] += D_ff^{-1} Sigma_f r_all (union of Algorithm 2 over active instances).
-// Records a fixed maximum number of PCG iterations; kernels become no-ops once converged.
+// Called while the batched iteration is being recorded: the PCG loop becomes a WHILE conditional
+// node whose body is one iteration (z = V(r); rz; p = z + (rz / rz_prev) p; q = A p; x, r update;
+// r.r; device-side test), so a converged solve launches nothing more.
 cudaError_t union_dsa_correct(UnionDsa* U, const double* r_all, double* phi_all, const int* active, double tol,
                               int max_iters, cudaStream_t s) {
     if (U->n0 == 0) return cudaSuccess;
     const long long n = U->n0;
-    cudaMemsetAsync(U->done, 0, sizeof(int), s);
+    cudaError_t err;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    if ((err = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr)) != cudaSuccess) return err;
+    if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureUnsupported;
+    if (!U->cap2 && (err = cudaStreamCreateWithFlags(&U->cap2, cudaStreamNonBlocking)) != cudaSuccess) return err;
+    cudaGraphConditionalHandle h;
+    if ((err = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return err;
+    cudaMemsetAsync(U->done, 0, sizeof(int), s);  // the loop's kernels never skip
     SN_COUNT_LAUNCH();
     u_gather<<<nb(n), kBS, 0, s>>>(r_all, U->row_dof, U->mass_sig, n, U->b, U->done);
     cudaMemsetAsync(U->x, 0, n * sizeof(double), s);
+    cudaMemsetAsync(U->p, 0, n * sizeof(double), s);
     cudaMemcpyAsync(U->r, U->b, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
     dot(U, U->b, U->b, n, 3, s);
     SN_COUNT_LAUNCH();
-    u_start<<<1, 1, 0, s>>>(U->s, U->done, U->iters);
-    vcycle0_union(U, U->r, U->z, s);
-    cudaMemcpyAsync(U->p, U->z, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    dot(U, U->r, U->z, n, 0, s);
-    for (int k = 0; k < max_iters; ++k) {
-        SN_COUNT_LAUNCH();
-        u_bsr<<<nb(n), kBS, 0, s>>>(U->row_inst, U->inst_n, U->inst_row0, U->inst_ptr0, U->inst_blk0, U->inst_val0, U->bsr_ptr,
-                                   U->bsr_col, U->bsr_val, n, U->p, nullptr, U->q, U->done);
-        dot(U, U->p, U->q, n, 1, s);
-        SN_COUNT_LAUNCH();
-        u_update_xr<<<nb(n), kBS, 0, s>>>(U->x, U->r, U->p, U->q, n, U->s, U->done);
-        dot(U, U->r, U->r, n, 2, s);
-        SN_COUNT_LAUNCH();
-        u_check<<<1, 1, 0, s>>>(U->s, tol * tol, U->done, U->iters);
-        vcycle0_union(U, U->r, U->z, s);
-        dot(U, U->r, U->z, n, 4, s);
-        SN_COUNT_LAUNCH();
-        u_update_p<<<nb(n), kBS, 0, s>>>(U->p, U->z, n, U->s, U->done);
-        SN_COUNT_LAUNCH();
-        u_shift<<<1, 1, 0, s>>>(U->s, U->done);
-    }
+    u_loop_start<<<1, 1, 0, s>>>(U->s, U->local_iters, h);
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    if ((err = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &ndeps)) != cudaSuccess) return err;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    if ((err = cudaGraphAddNode(&loop, g, deps, nullptr, ndeps, &cp)) != cudaSuccess) return err;
+    if ((err = cudaStreamUpdateCaptureDependencies(s, &loop, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+        return err;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t b = U->cap2;
+    if ((err = cudaStreamBeginCaptureToGraph(b, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return err;
+    vcycle0_union(U, U->r, U->z, b);
+    dot(U, U->r, U->z, n, 4, b);
+    SN_COUNT_LAUNCH();
+    u_update_p<<<nb(n), kBS, 0, b>>>(U->p, U->z, n, U->s, U->done);
+    SN_COUNT_LAUNCH();
+    u_shift<<<1, 1, 0, b>>>(U->s, U->done);
+    SN_COUNT_LAUNCH();
+    u_bsr<<<nb(n), kBS, 0, b>>>(U->row_inst, U->inst_n, U->inst_row0, U->inst_ptr0, U->inst_blk0, U->inst_val0, U->bsr_ptr,
+                               U->bsr_col, U->bsr_val, n, U->p, nullptr, U->q, U->done);
+    dot(U, U->p, U->q, n, 1, b);
+    SN_COUNT_LAUNCH();
+    u_update_xr<<<nb(n), kBS, 0, b>>>(U->x, U->r, U->p, U->q, n, U->s, U->done);
+    dot(U, U->r, U->r, n, 2, b);
+    SN_COUNT_LAUNCH();
+    u_loop_check<<<1, 1, 0, b>>>(U->s, tol * tol, max_iters, U->local_iters, U->iters, h);
+    cudaError_t lerr = cudaGetLastError();
+    cudaGraph_t b2 = nullptr;
+    err = cudaStreamEndCapture(b, &b2);
+    if (lerr != cudaSuccess) return lerr;
+    if (err != cudaSuccess) return err;
     SN_COUNT_LAUNCH();
     u_scatter_add<<<nb(n), kBS, 0, s>>>(U->x, U->row_dof, U->row_inst, active, n, phi_all);
     return cudaGetLastError();

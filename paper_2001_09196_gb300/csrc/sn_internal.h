@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/sn.h"
@@ -213,6 +214,36 @@ struct sn_batch {
 };
 
 namespace sn {
+// Launch with programmatic stream serialisation when pdl is set: the kernel may start while its
+// predecessor in the stream still runs (it waits in griddepcontrol.wait before reading the
+// predecessor's results).  The first launch of a sequence passes pdl = false, so everything
+// written before the sequence is complete before any of its kernels starts.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), unsigned grid, int block, cudaStream_t s,
+                            Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+#ifdef __CUDACC__
+// Programmatic dependent launch: a kernel does the work that reads nothing its predecessor writes
+// before griddepcontrol.wait, which returns when every prerequisite grid has completed and its
+// writes are visible; griddepcontrol.launch_dependents lets the next kernel in the stream start
+// its own blocks.  Without a programmatic dependency both instructions do nothing.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+#endif
+
 // sn_api.cpp: records the thread-local message returned by sn_last_error
 sn_status set_error(sn_status st, const char* msg);
 // sn_sweep.cu

@@ -554,13 +554,6 @@ __device__ __forceinline__ void cached_fluxes(const SweepArgs& a, int d, int e, 
     }
 }
 
-// Programmatic dependent launch: a level kernel's blocks do the work that reads no angular flux
-// before griddepcontrol.wait, which returns when every prerequisite grid has completed and its
-// writes are visible; then they allow the next level to launch.  Without a programmatic
-// dependency both instructions do nothing.
-__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
 // The part of a node's work that reads no angular flux: the face flux factors, the source row
 // (forward: M_r (q + sigma_s phi_r) / (4 pi); adjoint: mu_r) and the N entries of the cached
 // inverse this lane multiplies with (forward: row r of A_e^{-1}; adjoint: column r).
@@ -1257,26 +1250,6 @@ static SweepArgs make_args(const sn_mesh* m) {
     } while (0)
 
 static inline unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
-
-// Launch with programmatic stream serialisation when pdl is set: the kernel may start while its
-// predecessor in the stream still runs (it waits in griddepcontrol.wait before reading the
-// predecessor's results).  The first launch of a sequence passes pdl = false, so everything
-// written before the sequence is complete before any of its kernels starts.
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), unsigned grid, int block, cudaStream_t s,
-                            Args&&... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
 
 // Blocks of bs threads for n items of the node-per-lane kernels (32 / N items per warp).
 static inline unsigned node_grid(const sn_mesh* m, long long n, int bs) {

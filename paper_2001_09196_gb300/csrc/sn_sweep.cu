@@ -618,19 +618,15 @@ __device__ __forceinline__ R node_faces(const SweepArgs& a, const double* F, int
 
 // One node of one item: stage, (PDL: release the next grid, wait for the previous one), face
 // terms, x_r = sum_j inv_rj rhs_j with rhs_j shuffled from the item's lane j, store.
-template <int DIM, int P, int MODE, bool ADJ, bool PDL = false>
-__device__ __forceinline__ void node_item(const SweepArgs& a, const double* mu, int d, int e, int r, int src0,
-                                          bool valid) {
+// Second half of a node's work: face terms from the neighbours' angular fluxes, then
+// x_r = sum_j inv_rj rhs_j with rhs_j shuffled from the item's lane j, and the store.  Every lane
+// of the warp must call it (shuffles); `valid` masks lanes without an item.
+template <int DIM, int P, int MODE, bool ADJ>
+__device__ __forceinline__ void node_finish(const SweepArgs& a,
+                                            const NodeStage<DIM, P, typename std::conditional<MODE == 1, float, double>::type>& st,
+                                            int d, int e, int r, int src0, bool valid) {
     using R = typename std::conditional<MODE == 1, float, double>::type;
     constexpr int N = Shape<DIM, P>::N;
-    NodeStage<DIM, P, R> st;
-    if (valid) node_stage<DIM, P, MODE, ADJ>(a, mu, d, e, r, st);
-    if (PDL) {
-        // the next level may launch once this one's inputs are complete: its blocks then run
-        // their prologue while this level computes, and the look-ahead stays one level deep
-        pdl_wait();
-        pdl_launch_dependents();
-    }
     const R rhs = valid ? node_faces<DIM, P, R, ADJ>(a, st.F, d, e, r, st.rhs) : R(0);
     R x = R(0);
 #pragma unroll
@@ -639,6 +635,22 @@ __device__ __forceinline__ void node_item(const SweepArgs& a, const double* mu, 
         if (valid) x += st.inv[j] * rj;
     }
     if (valid) static_cast<R*>(a.psi)[((size_t)d * a.ne + e) * N + r] = x;
+}
+
+// One node of one item: stage, (PDL: wait for the previous grid, release the next), finish.
+template <int DIM, int P, int MODE, bool ADJ, bool PDL = false>
+__device__ __forceinline__ void node_item(const SweepArgs& a, const double* mu, int d, int e, int r, int src0,
+                                          bool valid) {
+    using R = typename std::conditional<MODE == 1, float, double>::type;
+    NodeStage<DIM, P, R> st;
+    if (valid) node_stage<DIM, P, MODE, ADJ>(a, mu, d, e, r, st);
+    if (PDL) {
+        // the next level may launch once this one's inputs are complete: its blocks then run
+        // their prologue while this level computes, and the look-ahead stays one level deep
+        pdl_wait();
+        pdl_launch_dependents();
+    }
+    node_finish<DIM, P, MODE, ADJ>(a, st, d, e, r, src0, valid);
 }
 
 template <int DIM, int P, int MODE, bool ADJ>
@@ -912,12 +924,15 @@ __global__ void __launch_bounds__(128) node_dataflow_kernel(SweepArgs a, Dataflo
         if (slot < IPW && k < 32) it = f.items[(chunk << 5) + k];
         const bool valid = it.x >= 0;
         const int d = valid ? it.x : 0, e = valid ? it.y : 0;
+        // loads that read no angular flux go out before the waits, so they overlap them
+        NodeStage<DIM, P, typename std::conditional<MODE == 1, float, double>::type> st;
+        if (valid) node_stage<DIM, P, MODE, ADJ>(a, mu, d, e, r, st);
         const bool ok = valid ? wait_neighbours<DIM, P, ADJ>(a, f.done, f.epoch, d, e, deadline) : true;
         if (!__all_sync(0xffffffffu, ok)) {
             if (lane == 0) atomicExch(f.error, 1);
             break;
         }
-        node_item<DIM, P, MODE, ADJ>(a, mu, d, e, r, src0, valid);
+        node_finish<DIM, P, MODE, ADJ>(a, st, d, e, r, src0, valid);
         __syncwarp();
         if (valid && r == 0) {
             __threadfence();
@@ -963,6 +978,7 @@ __device__ __forceinline__ bool wait_faces(const SweepArgs& a, const int* done, 
 // for every CTA through the error word (all barriers are still reached: waits are bounded).
 template <int DIM, int P, int MODE>
 __global__ void __launch_bounds__(256) tile_sweep_kernel(SweepArgs a, TileArgs t) {
+    using R = typename std::conditional<MODE == 1, float, double>::type;
     constexpr int N = Shape<DIM, P>::N, IPW = 32 / N;
     __shared__ long long s_task;
     __shared__ int s_failed;
@@ -982,25 +998,54 @@ __global__ void __launch_bounds__(256) tile_sweep_kernel(SweepArgs a, TileArgs t
         if (task >= t.n_tasks || failed) break;
         const int4 T = t.tasks[task];
         const int d = T.x;
-        bool abort = false;
-        for (int L = 0; L < T.w && !abort; ++L) {
-            const int lo = t.lvl_ptr[T.z + L], hi = t.lvl_ptr[T.z + L + 1];
-            bool bad = false;
-            for (int base = lo; base < hi; base += per_pass) {
-                const int idx = base + warp * IPW + slot;
-                const bool valid = slot < IPW && idx < hi;
-                const int2 it = valid ? t.items[idx] : make_int2(0, 0);
-                bool ok = true;
-                if (valid && (it.y & kTileWaitMask)) ok = wait_faces<DIM, P>(a, t.done, t.epoch, d, it.x, it.y, deadline);
-                node_item<DIM, P, MODE, false>(a, nullptr, d, it.x, r, src0, valid && ok);
-                __syncwarp();
-                if (valid && ok && r == 0 && (it.y & kTilePublish)) {
-                    __threadfence();
-                    st_release(t.done + (size_t)d * a.ne + it.x, t.publish);
+        // the task's passes (level, first item) in order; the stage of the next pass is loaded
+        // before the current pass waits and computes (it reads no angular flux)
+        int L = 0, lo = t.lvl_ptr[T.z], hi = t.lvl_ptr[T.z + 1], base = lo;
+        int idx = base + warp * IPW + slot;
+        bool valid = slot < IPW && idx < hi;
+        int2 it = valid ? t.items[idx] : make_int2(0, 0);
+        NodeStage<DIM, P, R> st;
+        if (valid) node_stage<DIM, P, MODE, false>(a, nullptr, d, it.x, r, st);
+        bool bad = false, abort = false;
+        while (true) {
+            // next pass
+            int nL = L, nlo = lo, nhi = hi, nbase = base + per_pass;
+            if (nbase >= nhi) {
+                ++nL;
+                if (nL < T.w) {
+                    nlo = nhi;
+                    nhi = t.lvl_ptr[T.z + nL + 1];
+                    nbase = nlo;
                 }
-                bad = bad || !ok;
             }
-            abort = __syncthreads_or(bad) != 0;
+            const bool more = nL < T.w;
+            const int nidx = nbase + warp * IPW + slot;
+            const bool nvalid = more && slot < IPW && nidx < nhi;
+            const int2 nit = nvalid ? t.items[nidx] : make_int2(0, 0);
+            NodeStage<DIM, P, R> nst;
+            if (nvalid) node_stage<DIM, P, MODE, false>(a, nullptr, d, nit.x, r, nst);
+            // this pass
+            bool ok = true;
+            if (valid && (it.y & kTileWaitMask)) ok = wait_faces<DIM, P>(a, t.done, t.epoch, d, it.x, it.y, deadline);
+            node_finish<DIM, P, MODE, false>(a, st, d, it.x, r, src0, valid && ok);
+            __syncwarp();
+            if (valid && ok && r == 0 && (it.y & kTilePublish)) {
+                __threadfence();
+                st_release(t.done + (size_t)d * a.ne + it.x, t.publish);
+            }
+            bad = bad || !ok;
+            if (nL != L || !more) {  // level boundary: the CTA's angular fluxes of this level are complete
+                abort = __syncthreads_or(bad) != 0;
+                bad = false;
+                if (abort || !more) break;
+            }
+            L = nL;
+            lo = nlo;
+            hi = nhi;
+            base = nbase;
+            valid = nvalid;
+            it = nit;
+            st = nst;
         }
         if (abort) {
             if (threadIdx.x == 0) atomicExch(t.error, 1);

@@ -1,7 +1,9 @@
 """Diffusion synthetic acceleration restricted to the thick subdomain (CPU oracle, tests only).
 
 Paper: Sec. 2.2 (Eq. dsa_prec, Eq. DSA_fp and the additive form D^{-1} = I + D^{-1} Sigma),
-Sec. 3 (Algorithm 2, diagonal heterogeneous DSA: phi_f <- phi_f + D_ff^{-1} Sigma_f r_f),
+Sec. 3 (Algorithm 2, diagonal heterogeneous DSA: phi_f <- phi_f + D_ff^{-1} Sigma_f r_f; and
+Algorithm 1, triangular heterogeneous DSA, the same step followed by a zero-source transport
+update of the thick correction whose result is added on the thin DOFs only),
 Sec. 4.1 (interior-penalty DSA operators, Eq. SIP, Eq. ModifiedF0) and Sec. 4.2 (the
 heterogeneous operator is the principal submatrix on the thick elements, thick where
 sigma_s >= eta).
@@ -153,6 +155,40 @@ class DSA:
         nt = self.thick.size
         Vi = sp.block_diag([sp.csr_matrix(self.T.Vinv)] * nt, format="csr") if nt else sp.csr_matrix((0, 0))
         return (Vi.T @ self.D @ Vi).tocsr()
+
+
+class TriangularDSA:
+    """Algorithm 1 (triangular heterogeneous DSA) as the source-iteration correction.
+
+    The preconditioner of Eq. approxS acts on a residual r in two steps:
+      1. on the thick region, r_f <- r_f + D_ff^{-1} Sigma_f r_f (the DSA step of Algorithm 2);
+      2. with phibar = [0; r_f] (the thin part set to zero, the thick part from step 1), every
+         direction adds [w_d L_d^{-1} Sigma_s phibar]_s to the thin part: a transport update with
+         zero fixed source and vacuum inflow whose result is kept on the thin DOFs only.
+    As a correction of source iteration (phi^{i+1} = phi^i + P r^i = phi_half^i + (P r^i - r^i)) this
+    is E_f D_ff^{-1} Sigma_f r_f plus, on the thin DOFs, the accumulated update of step 2.
+    """
+
+    def __init__(self, dsa):
+        self.dsa = dsa
+        self.T = dsa.T
+
+    def homogeneous_update(self, x_modal):
+        """sum_d w_d L_d^{-1} Sigma_s x / (4 pi) with no fixed source and vacuum inflow."""
+        T = self.T
+        zero = np.zeros((T.nd, T.ne, T.n))
+        return T.sweep_modal(x_modal, src_per_dir=zero, psi_inc=0.0)
+
+    def correction(self, r_modal):
+        c = self.dsa.correction(r_modal)                      # step 1 (thick DOFs)
+        phibar = np.zeros_like(r_modal)
+        th = self.dsa.thick
+        phibar[th] = r_modal[th] + c[th]
+        y = self.homogeneous_update(phibar)                   # step 2, accumulated over directions
+        thin = ~self.dsa.mask
+        out = c.copy()
+        out[thin] += y[thin]
+        return out
 
 
 def thick_mask(prob):

@@ -15,7 +15,7 @@ import pytest
 from paper_2001_09196_gb300 import inputs
 from oracle import Transport
 from oracle import adjoint, dense
-from oracle.dsa import DSA
+from oracle.dsa import DSA, TriangularDSA
 from oracle.quadrature import level_symmetric, level_symmetric_octant
 
 FOUR_PI = 4.0 * np.pi
@@ -185,6 +185,49 @@ def test_dsa_accelerates_config1():
     assert r["converged"] and r["iters"] < 40
     r0 = T.source_iterate(tol=1e-8, max_iters=60)
     assert not r0["converged"]
+
+
+def _vacuum_thin(prob):
+    """sigma_s = 0 on every element outside the thick set (the case of Eq. Stri)."""
+    thick = prob.thick_mask().astype(bool)
+    prob.sigma_s[~thick] = 0.0
+    return prob
+
+
+@pytest.mark.parametrize("prob_fn", [lambda: inputs.config1(), lambda: inputs.config2(n=16, block=4, p=1, sn=4)])
+def test_triangular_dsa_makes_the_thin_block_the_identity(prob_fn):
+    """Eq. Stri: with Sigma_s = 0 on the thin region S is block upper triangular, and Algorithm 1's
+    preconditioner P (Eq. approxS) makes the thin rows of S P the identity, whatever D_ff is:
+    (S P v)_s = v_s.  S v = v - T v with T the zero-source, vacuum-inflow transport update."""
+    prob = _vacuum_thin(prob_fn())
+    T = Transport(prob)
+    tri = TriangularDSA(DSA(T, prob.thick_mask()))
+    rng = np.random.default_rng(7)
+    v = rng.standard_normal((T.ne, T.n))
+    Pv = v + tri.correction(v)
+    SPv = Pv - tri.homogeneous_update(Pv)
+    thin = ~prob.thick_mask().astype(bool)
+    assert thin.any() and (~thin).any()
+    assert np.abs(SPv[thin] - v[thin]).max() < 1e-13 * np.abs(v).max()
+    # the thick rows are not the identity (D_ff only approximates the thick block)
+    assert np.abs(SPv[~thin] - v[~thin]).max() > 1e-6
+
+
+def test_triangular_dsa_fixed_point_and_acceleration():
+    """Algorithm 1 is a preconditioner: same fixed point as the dense solve of Eq. system, and with
+    a nearly vacuum thin region it takes no more iterations than Algorithm 2."""
+    prob = inputs.config2d_fields(8, 1, 4, 98, "tri")
+    prob.q[:] = 1.0
+    prob.sigma_t[prob.sigma_t == 0] = 0.5
+    thick = prob.thick_mask().astype(bool)
+    prob.sigma_s[~thick] = 1e-3 * prob.sigma_t[~thick]
+    T = Transport(prob)
+    ref = dense.solve_block_system(T)
+    diag = DSA(T, prob.thick_mask())
+    r_tri = T.source_iterate(dsa=TriangularDSA(diag), tol=1e-14, max_iters=3000)
+    assert np.abs(r_tri["phi"] - ref).max() < 1e-11 * np.abs(ref).max()
+    r_diag = T.source_iterate(dsa=diag, tol=1e-14, max_iters=3000)
+    assert r_tri["iters"] <= r_diag["iters"]
 
 
 def test_full_dsa_rejects_voids():

@@ -307,8 +307,9 @@ def run_ours(args, rank, ws):
     # unaccelerated-by-Krylov source iteration with the same DSA (capped at 300 iterations)
     forms = {}
     phi64 = phi.clone()  # the FP64 fGMRES solution of the last timed step
-    for prec, outer in (("fp32", "fgmres"), ("fp32_refine", "fgmres"), ("fp64", "si")):
-        o = dict(opts, precision=prec, outer=outer, max_iters=300)
+    for prec, outer, dsa in (("fp32", "fgmres", "thick"), ("fp32_refine", "fgmres", "thick"), ("fp64", "si", "thick"),
+                             ("fp64", "fgmres", "triangular")):
+        o = dict(opts, precision=prec, outer=outer, max_iters=300, dsa=dsa)
         mesh.source_iterate(phi=phi, **o)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         flush.zero_()
@@ -317,7 +318,7 @@ def run_ours(args, rank, ws):
         b.record(stream)
         torch.cuda.synchronize()
         err = float((phi - phi64).abs().max() / phi64.abs().max())
-        forms[f"{prec}_{outer}"] = {"ms_to_tol": a.elapsed_time(b), "iters": rr["iters"], "sweeps": rr["sweeps"],
+        forms[f"{prec}_{outer}" + ("_triangular_dsa" if dsa == "triangular" else "")] = {"ms_to_tol": a.elapsed_time(b), "iters": rr["iters"], "sweeps": rr["sweeps"],
                                     "rel_residual": rr["rel_residual"], "converged": rr["converged"],
                                     "max_rel_err_vs_fp64_solution": err}
 

@@ -46,7 +46,7 @@ typedef enum {
 } sn_status;
 
 enum { SN_FP64 = 0, SN_FP32 = 1, SN_FP32_REFINE = 2 };          /* element-solve precision */
-enum { SN_DSA_NONE = 0, SN_DSA_FULL = 1, SN_DSA_THICK = 2 };    /* DSA variant */
+enum { SN_DSA_NONE = 0, SN_DSA_FULL = 1, SN_DSA_THICK = 2, SN_DSA_TRIANGULAR = 3 };  /* DSA variant */
 enum { SN_THICK_SIGMA_S = 0, SN_THICK_SIGMA_T_H = 1, SN_THICK_MASK = 2 };
 enum { SN_DSA_SIGMA_S = 0, SN_DSA_SIGMA_T = 1 };
 enum { SN_OUTER_SI = 0, SN_OUTER_FGMRES = 1 };                  /* outer iteration */
@@ -148,7 +148,7 @@ sn_status sn_set_materials(sn_mesh* mesh, const double* sigma_t, const double* s
 sn_status sn_sweep(sn_mesh* mesh, const double* phi_in, double* phi_out, int precision, void* stream);
 
 typedef struct {
-    int dsa;                 /* SN_DSA_NONE | SN_DSA_FULL | SN_DSA_THICK */
+    int dsa;                 /* SN_DSA_NONE | SN_DSA_FULL | SN_DSA_THICK (Algorithm 2) | SN_DSA_TRIANGULAR (Algorithm 1) */
     int thick_rule;          /* SN_THICK_SIGMA_S (sigma_s >= eta, Sec. 4.2) | SN_THICK_SIGMA_T_H | SN_THICK_MASK */
     double eta;              /* threshold of the thick rule; the paper uses eta = 1 (Sec. 5.1) */
     const unsigned char* mask; /* host, n_elem, used with SN_THICK_MASK */
@@ -193,6 +193,11 @@ void sn_iter_opts_default(sn_iter_opts* opts);
  * GMRES(restart) right-preconditioned by the same DSA step, I + E_f D_ff^{-1} Sigma_f E_f^T (the paper's
  * outer solver, Sec. 5; "flexible" because each DSA solve is inexact).  Its residual b - S phi equals
  * the source-iteration residual, so tol means the same; iters counts Krylov iterations.
+ * SN_DSA_TRIANGULAR is the block upper-triangular preconditioner of Algorithm 1 (Eq. approxS): the
+ * thick-only DSA step above, then a transport update with zero fixed source and vacuum inflow of
+ * [0; corrected thick part] whose result is added on the thin DOFs only (one extra sweep per outer
+ * iteration).  It uses the same thick rule; it is not available for the adjoint or for batches
+ * (SN_ERR_ARG).
  * SN_ERR_VOID_FULL_DSA if dsa = FULL and some sigma_t = 0; SN_ERR_NOT_CONVERGED after
  * max_iters (phi_inout still written).  stats may be NULL.
  */

@@ -370,7 +370,7 @@ static sn_status ensure_dsa(sn_mesh* m, const sn_iter_opts* o) {
 
 static sn_status check_opts(const sn_iter_opts* o) {
     if (!o) return fail(SN_ERR_ARG, "null opts");
-    if (o->dsa < SN_DSA_NONE || o->dsa > SN_DSA_THICK) return fail(SN_ERR_ARG, "bad dsa");
+    if (o->dsa < SN_DSA_NONE || o->dsa > SN_DSA_TRIANGULAR) return fail(SN_ERR_ARG, "bad dsa");
     if (o->precision < SN_FP64 || o->precision > SN_FP32_REFINE) return fail(SN_ERR_ARG, "bad precision");
     if (!(o->tol >= 0) || o->max_iters < 1) return fail(SN_ERR_ARG, "bad tol / max_iters");
     if (o->dsa != SN_DSA_NONE && (!(o->inner_tol > 0) || o->inner_max_iters < 1))
@@ -447,8 +447,20 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
             double* Vj = V + (size_t)j * M;
             double* Zj = Z + (size_t)j * M;
             CK(sn::launch_copy(Zj, Vj, M, s), "copy");
-            if (o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0)
+            if (o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0) {
                 CK(sn::dsa_correct(m->dsa, Vj, Zj, o->inner_tol, o->inner_max_iters, adjoint, s), "DSA");
+                if (o->dsa == SN_DSA_TRIANGULAR) {
+                    // Algorithm 1, step 2: the zero-source transport update of [0; Z_f], kept on the
+                    // thin DOFs (Z_f = V_f + D_ff^{-1} Sigma_f V_f after step 1)
+                    double* w = m->d_work;
+                    double* y = m->d_work + M;
+                    CK(sn::dsa_select_thick(m->dsa, Zj, w, s), "Algorithm 1");
+                    CK(sn::launch_sweep(m, w, o->precision, 0.0, s), "sweep");
+                    CK(sn::launch_phi_reduce(m, o->precision, nullptr, y, nullptr, s), "phi reduce");
+                    CK(sn::dsa_add_thin(m->dsa, y, Zj, s), "Algorithm 1");
+                    ++sweeps;
+                }
+            }
             // w = S Zj = Zj - T Zj (T: sweep without the fixed source)
             if (adjoint) {
                 CK(sn::launch_adjoint_sweep(m, Zj, s), "adjoint sweep");
@@ -539,7 +551,7 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
     double* r = m->d_work + M;
     if (!o->warm_start) CK(cudaMemsetAsync(phi, 0, M * sizeof(double), s), "memset");
     double r0 = 0.0, rel = INFINITY;
-    int it = 0, inner_total = 0, nck = 0;
+    int it = 0, inner_total = 0, nck = 0, extra_sweeps = 0;
     bool converged = false;
     while (it < o->max_iters) {
         CK(sn::launch_sweep(m, phi, o->precision, 1.0, s), "sweep");
@@ -559,7 +571,20 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
         if (o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0) {
             CK(sn::launch_axpy_norm(m, half, phi, r, m->d_scalars + 1, s), "residual");
             CK(sn::launch_copy(phi, half, M, s), "copy");
-            CK(sn::dsa_correct(m->dsa, r, phi, o->inner_tol, o->inner_max_iters, false, s), "DSA");
+            if (o->dsa != SN_DSA_TRIANGULAR) {
+                CK(sn::dsa_correct(m->dsa, r, phi, o->inner_tol, o->inner_max_iters, false, s), "DSA");
+            } else {
+                // Algorithm 1: w = E_f (r_f + D_ff^{-1} Sigma_f r_f) (step 1), y = zero-source transport
+                // update of w (step 2); phi gets w - r on the thick DOFs and y on the thin ones
+                double* w = m->d_work + 2 * M;
+                double* y = m->d_work + 3 * M;
+                CK(sn::dsa_select_thick(m->dsa, r, w, s), "Algorithm 1");
+                CK(sn::dsa_correct(m->dsa, r, w, o->inner_tol, o->inner_max_iters, false, s), "DSA");
+                CK(sn::launch_sweep(m, w, o->precision, 0.0, s), "sweep");
+                CK(sn::launch_phi_reduce(m, o->precision, nullptr, y, nullptr, s), "phi reduce");
+                CK(sn::dsa_tri_combine(m->dsa, w, r, y, phi, s), "Algorithm 1");
+                ++extra_sweeps;
+            }
         } else {
             CK(sn::launch_copy(phi, half, M, s), "copy");
         }
@@ -581,7 +606,7 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
         stats->inner_iters_total = inner_total;
         stats->thick_fraction = m->dsa && o->dsa != SN_DSA_NONE ? (double)sn::dsa_thick_count(m->dsa) / m->ne : 0.0;
         stats->n_checkpoints = nck;
-        stats->n_sweeps = it;
+        stats->n_sweeps = it + extra_sweeps;
         stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     if (!converged) return fail(SN_ERR_NOT_CONVERGED, "not converged after %d iterations (rel. residual %.3e)", it, rel);
@@ -610,6 +635,7 @@ sn_status sn_adjoint_iterate(sn_mesh* m, const sn_iter_opts* o, const double* g,
     if (!m || !g || !mu) return fail(SN_ERR_ARG, "null argument");
     sn_status st = check_opts(o);
     if (st != SN_OK) return st;
+    if (o->dsa == SN_DSA_TRIANGULAR) return fail(SN_ERR_ARG, "the adjoint iteration has no triangular DSA");
     if ((st = ensure_lambda(m)) != SN_OK) return st;
     if (o->dsa != SN_DSA_NONE && (st = ensure_dsa(m, o)) != SN_OK) return st;
     if (m->dsa) {  // the PCG iteration counter starts from zero for this solve
@@ -844,6 +870,7 @@ sn_status sn_batch_sweep(sn_batch* b, const double* const* phi_in, double* const
 }
 
 static sn_status batch_ensure_dsa(sn_batch* b, const sn_iter_opts* o) {
+    if (o->dsa == SN_DSA_TRIANGULAR) return fail(SN_ERR_ARG, "batches use the diagonal (Algorithm 2) DSA only");
     std::vector<std::vector<unsigned char>> masks(b->count);
     for (int i = 0; i < b->count; ++i) {
         sn_iter_opts oi = *o;

@@ -92,6 +92,28 @@ __global__ void dense_mv_kernel(const double* A, int n, const double* b, double*
     x[r] = s;
 }
 
+// Algorithm 1 (triangular heterogeneous DSA) helpers on full [elem][node] vectors; emask marks
+// the thick elements.
+__global__ void select_thick_kernel(const unsigned char* emask, int n, long long M, const double* x, double* out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    out[i] = emask[i / n] ? x[i] : 0.0;
+}
+
+// thick DOFs: phi += w - r (the DSA correction, w = r + D^{-1} Sigma r there); thin DOFs: phi += y
+__global__ void tri_combine_kernel(const unsigned char* emask, int n, long long M, const double* w, const double* r,
+                                   const double* y, double* phi) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    phi[i] += emask[i / n] ? w[i] - r[i] : y[i];
+}
+
+__global__ void add_thin_kernel(const unsigned char* emask, int n, long long M, const double* y, double* z) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    if (!emask[i / n]) z[i] += y[i];
+}
+
 __global__ void dot_partial_kernel(const double* a, const double* b, long long n, double* part) {
     __shared__ double sh[kBS];
     double s = 0.0;
@@ -196,6 +218,12 @@ cudaError_t upload(DsaHierarchy* H) {
         if ((err = cudaMalloc(v, std::max<long long>(1, N0) * sizeof(double))) != cudaSuccess) return err;
     if ((err = cudaMalloc(&H->d_part, kDotBlocks * sizeof(double))) != cudaSuccess) return err;
     if ((err = cudaMalloc(&H->d_s, 16 * sizeof(double))) != cudaSuccess) return err;
+    {
+        std::vector<unsigned char> em(H->ne, 0);
+        for (int e : H->thick) em[e] = 1;
+        if ((err = cudaMalloc(&H->d_emask, std::max(1, H->ne))) != cudaSuccess) return err;
+        if ((err = cudaMemcpy(H->d_emask, em.data(), H->ne, cudaMemcpyHostToDevice)) != cudaSuccess) return err;
+    }
     if ((err = cudaMalloc(&H->d_it, 2 * sizeof(int))) != cudaSuccess) return err;
     if ((err = cudaMemset(H->d_it, 0, 2 * sizeof(int))) != cudaSuccess) return err;
     H->uploaded = true;
@@ -392,7 +420,7 @@ void dsa_free(DsaHierarchy* H) {
         f(L.d_r_ptr); f(L.d_r_col); f(L.d_r_val); f(L.d_dinv); f(L.d_dense); f(L.d_x); f(L.d_b); f(L.d_r);
     }
     f(H->d_x); f(H->d_b); f(H->d_r); f(H->d_z); f(H->d_p); f(H->d_q); f(H->d_vr); f(H->d_vx);
-    f(H->d_part); f(H->d_s); f(H->d_it);
+    f(H->d_part); f(H->d_s); f(H->d_it); f(H->d_emask);
     if (H->pcg_graph) cudaGraphExecDestroy(H->pcg_graph);
     if (H->cap) cudaStreamDestroy(H->cap);
     if (H->cap2) cudaStreamDestroy(H->cap2);
@@ -458,6 +486,31 @@ cudaError_t dsa_take_iters(DsaHierarchy* H, cudaStream_t s, int* iters) {
     *iters = h[1];
     g_launches.fetch_add((long long)h[1] * H->body_launches, std::memory_order_relaxed);
     return cudaMemsetAsync(H->d_it + 1, 0, sizeof(int), s);
+}
+
+// Algorithm 1 pieces on full vectors (M = ne x n values).
+cudaError_t dsa_select_thick(DsaHierarchy* H, const double* x, double* out, cudaStream_t s) {
+    cudaError_t err = upload(H);
+    if (err != cudaSuccess) return err;
+    const long long M = (long long)H->ne * H->n;
+    SN_COUNT_LAUNCH();
+    select_thick_kernel<<<nblk(M), kBS, 0, s>>>(H->d_emask, H->n, M, x, out);
+    return cudaGetLastError();
+}
+
+cudaError_t dsa_tri_combine(DsaHierarchy* H, const double* w, const double* r, const double* y, double* phi,
+                            cudaStream_t s) {
+    const long long M = (long long)H->ne * H->n;
+    SN_COUNT_LAUNCH();
+    tri_combine_kernel<<<nblk(M), kBS, 0, s>>>(H->d_emask, H->n, M, w, r, y, phi);
+    return cudaGetLastError();
+}
+
+cudaError_t dsa_add_thin(DsaHierarchy* H, const double* y, double* z, cudaStream_t s) {
+    const long long M = (long long)H->ne * H->n;
+    SN_COUNT_LAUNCH();
+    add_thin_kernel<<<nblk(M), kBS, 0, s>>>(H->d_emask, H->n, M, y, z);
+    return cudaGetLastError();
 }
 
 }  // namespace sn

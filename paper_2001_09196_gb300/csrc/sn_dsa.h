@@ -49,6 +49,7 @@ struct DsaHierarchy {
     double pcg_tol = -1.0;
     int pcg_max = -1;
     int* d_it = nullptr;                      // [0] iterations of the current solve, [1] running total
+    unsigned char* d_emask = nullptr;         // per element: 1 = thick (Algorithm 1's restrictions)
     long long pro_launches = 0, body_launches = 0;  // kernels in the prologue / one loop iteration
     cudaStream_t cap = nullptr, cap2 = nullptr;     // private capture streams
 };

@@ -306,4 +306,10 @@ cudaError_t dsa_solve(DsaHierarchy* h, const double* b_full, double* x_full, dou
                       cudaStream_t s);
 // PCG iterations run since the last call (synchronises the stream)
 cudaError_t dsa_take_iters(DsaHierarchy* h, cudaStream_t s, int* iters);
+// Algorithm 1 on full [elem][node] vectors: out = x on thick elements, 0 elsewhere;
+// phi += (w - r) on thick elements and y elsewhere; z += y on thin elements
+cudaError_t dsa_select_thick(DsaHierarchy* h, const double* x, double* out, cudaStream_t s);
+cudaError_t dsa_tri_combine(DsaHierarchy* h, const double* w, const double* r, const double* y, double* phi,
+                            cudaStream_t s);
+cudaError_t dsa_add_thin(DsaHierarchy* h, const double* y, double* z, cudaStream_t s);
 }  // namespace sn

@@ -1522,8 +1522,9 @@ static cudaError_t enqueue_levels(sn_mesh* m, int kind, cudaStream_t s) {
         return cudaGetLastError();
     }
     // kinds 4..6: the same sweeps without the fixed source (the linear part T of Eq. source0)
-    if (kind >= 4) {
+    if (kind >= 4) {  // the linear part: no fixed source and vacuum inflow
         a.q_scale = 0.0;
+        a.psi_inc = 0.0;
         kind -= 4;
     }
     a.phi = m->d_src;
@@ -1672,6 +1673,7 @@ cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double
     SweepArgs a = make_args(m);
     a.phi = phi_in;
     a.q_scale = q_scale;
+    if (q_scale == 0.0) a.psi_inc = 0.0;  // the linear part of the update has vacuum inflow
     a.psi = precision == SN_FP32 ? m->d_psi32 : m->d_psi;
     const bool cached = precision == SN_FP64 ? a.ainv != nullptr : (precision == SN_FP32 && a.ainv32 != nullptr);
     if (m->schedule == SCHED_TILES && cached) {  // uncached solves fall back to the level schedule

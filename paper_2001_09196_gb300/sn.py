@@ -15,11 +15,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libsn.so")
 
 FP64, FP32, FP32_REFINE = 0, 1, 2
-DSA_NONE, DSA_FULL, DSA_THICK = 0, 1, 2
+DSA_NONE, DSA_FULL, DSA_THICK, DSA_TRIANGULAR = 0, 1, 2, 3
 THICK_SIGMA_S, THICK_SIGMA_T_H, THICK_MASK = 0, 1, 2
 DSA_SIGMA_S, DSA_SIGMA_T = 0, 1
 _PREC = {"fp64": FP64, "fp32": FP32, "fp32_refine": FP32_REFINE}
-_DSA = {"none": DSA_NONE, "full": DSA_FULL, "thick": DSA_THICK}
+_DSA = {"none": DSA_NONE, "full": DSA_FULL, "thick": DSA_THICK, "triangular": DSA_TRIANGULAR}
 _RULE = {"sigma_s": THICK_SIGMA_S, "sigma_t_h": THICK_SIGMA_T_H, "mask": THICK_MASK}
 
 STATUS = {0: "SN_OK", 1: "SN_ERR_ARG", 2: "SN_ERR_CUDA", 3: "SN_ERR_OOM", 4: "SN_ERR_CYCLE",

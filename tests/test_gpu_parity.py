@@ -256,3 +256,53 @@ def test_fgmres_reaches_the_oracle_fixed_point(sn, oracle_cache, name):
     assert _rel(r["phi"].cpu().numpy(), ref["phi"]) < 1e-9
     si = m.source_iterate(dsa="thick", thick_rule=prob.thick_rule, tol=1e-13, inner_tol=1e-10, max_iters=2000)
     assert r["iters"] <= si["iters"]
+
+
+@pytest.mark.parametrize("name", ["c1", "c2_32", "c3_8"])
+def test_iterate_parity_triangular_dsa(sn, oracle_cache, name):
+    """Algorithm 1 (triangular heterogeneous DSA) iterates match the oracle's."""
+    from oracle.dsa import DSA, TriangularDSA
+    prob, T = _oracle(name, oracle_cache)
+    m = sn.Mesh.from_problem(prob)
+    K = 5
+    r = m.source_iterate(dsa="triangular", thick_rule=prob.thick_rule, tol=0.0, max_iters=K, inner_tol=1e-14,
+                         inner_max_iters=500)
+    ref = T.source_iterate(dsa=TriangularDSA(DSA(T, prob.thick_mask())), tol=0.0, max_iters=K)
+    assert r["sweeps"] == 2 * K
+    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["c1", "c2_32"])
+def test_fgmres_triangular_dsa_reaches_the_oracle_fixed_point(sn, oracle_cache, name):
+    from oracle.dsa import DSA
+    prob, T = _oracle(name, oracle_cache)
+    m = sn.Mesh.from_problem(prob)
+    r = m.source_iterate(dsa="triangular", thick_rule=prob.thick_rule, outer="fgmres", restart=30, tol=1e-13,
+                         inner_tol=1e-10, max_iters=400)
+    ref = T.source_iterate(dsa=DSA(T, prob.thick_mask()), tol=1e-14, max_iters=2000)
+    assert r["converged"]
+    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) < 1e-9
+
+
+def test_fgmres_with_boundary_inflow(sn, oracle_cache):
+    """The Krylov operator is the linear part of the update (no fixed source, vacuum inflow): with
+    nonzero boundary inflow fGMRES still reaches the fixed point of source iteration."""
+    prob, T = _oracle("ragged", oracle_cache)
+    m = sn.Mesh.from_problem(prob)
+    r = m.source_iterate(dsa="none", outer="fgmres", restart=20, tol=1e-13, max_iters=400)
+    ref = T.source_iterate(tol=1e-14, max_iters=4000)
+    assert r["converged"] and ref["converged"]
+    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) < 1e-10
+
+
+def test_triangular_dsa_is_rejected_where_unsupported(sn, oracle_cache):
+    prob, _ = _oracle("c1", oracle_cache)
+    m = sn.Mesh.from_problem(prob)
+    g = torch.ones(m.shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(sn.SnError) as e:
+        m.adjoint_iterate(g, dsa="triangular", max_iters=2)
+    assert e.value.status == 1
+    b = sn.Batch([m])
+    with pytest.raises(sn.SnError) as e:
+        b.source_iterate(dsa="triangular", max_iters=2)
+    assert e.value.status == 1

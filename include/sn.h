@@ -83,9 +83,10 @@ sn_status sn_mesh_get_info(const sn_mesh* mesh, sn_mesh_info* info);
 /*
  * Sweep schedule (tuning; every schedule computes the same element solves in the same arithmetic,
  * so results are bitwise identical):
- *   schedule 0 (default): one launch per wavefront level of all directions, captured once into a
- *   CUDA graph so that a sweep is a single graph launch (programmatic dependent launch overlaps a
- *   level's prologue with the previous level);
+ *   schedule 0 (default): one launch per wavefront level, captured once into a CUDA graph so that
+ *   a sweep is a single graph launch (programmatic dependent launch overlaps a level's prologue
+ *   with the previous level); with param = G > 1 the directions are split into G groups of
+ *   consecutive directions whose level launches form G independent chains of the graph;
  *   schedule 1: one persistent launch per sweep in which warps claim items in level order and
  *   wait (bounded, SN_ERR_TIMEOUT after 4 s) for their upwind neighbours;
  *   schedule 2 (operator cache on): one persistent launch in which a CTA of `block` threads runs
@@ -94,7 +95,8 @@ sn_status sn_mesh_get_info(const sn_mesh* mesh, sn_mesh_info* info);
  *   elements of other tiles; tiles whose upwind graph is cyclic (jittered faces) run as one task.
  *   Uncached solves (SN_FP32_REFINE, cache off) and the adjoint use schedule 0 instead.
  * block: threads per block, a multiple of 32 in [32, 128] (schedules 0, 1) or [32, 256] (2).
- * param: schedule 1: blocks per SM (0 = occupancy limit); schedule 2: tile edge (<= 64); else 0.
+ * param: schedule 0: direction groups (0 or 1 = one chain, at most the number of directions);
+ * schedule 1: blocks per SM (0 = occupancy limit); schedule 2: tile edge (<= 64).
  */
 sn_status sn_mesh_set_schedule(sn_mesh* mesh, int schedule, int block, int param);
 

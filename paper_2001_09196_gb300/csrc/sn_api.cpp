@@ -3,6 +3,7 @@
 // and sn_dsa.cu; this file only sequences them.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -60,6 +61,7 @@ void free_mesh(sn_mesh* m) {
     sn::drop_level_graphs(m);
     sn::free_operator_cache(m);
     sn::free_tiles(m);
+    sn::free_level_groups(m);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     if (m->d_src) cudaFree(m->d_src);
     for (void* p : {(void*)m->d_dirs, (void*)m->d_wts, (void*)m->d_corners, (void*)m->d_sigma_t, (void*)m->d_sigma_s,
@@ -314,12 +316,16 @@ sn_status sn_mesh_set_schedule(sn_mesh* m, int schedule, int block, int param) {
         return fail(SN_ERR_ARG, "block must be a multiple of 32 in [32, %d]", max_block);
     if (param < 0) return fail(SN_ERR_ARG, "the schedule parameter must be >= 0");
     if (schedule == sn::SCHED_TILES && param > 64) return fail(SN_ERR_ARG, "tile edge must be <= 64");
-    if (m->block != block) sn::drop_level_graphs(m);
+    if (schedule == sn::SCHED_LEVELS && param > m->nd) return fail(SN_ERR_ARG, "more direction groups than directions");
+    const int groups = schedule == sn::SCHED_LEVELS ? std::max(param, 1) : m->level_groups;
+    if ((schedule != sn::SCHED_TILES && m->block != block) || groups != m->level_groups) sn::drop_level_graphs(m);
     m->schedule = schedule;
     if (schedule != sn::SCHED_TILES) m->block = block;
     if (schedule == sn::SCHED_TILES) {
         m->tile_block = block;
         m->tile_edge = param > 0 ? param : (m->dim == 2 ? 16 : 8);
+    } else if (schedule == sn::SCHED_LEVELS) {
+        m->level_groups = groups;
     } else {
         m->max_blocks_per_sm = param;
     }
@@ -1021,7 +1027,8 @@ std::mutex g_tune_mutex;
 const TuneChoice kCandidates[] = {{0, 32, 0, 0}, {0, 64, 0, 0}, {0, 128, 0, 0}, {1, 128, 0, 0},
                                   {1, 128, 1, 0}, {1, 64, 2, 0}, {1, 32, 4, 0}};
 // meshes also try the tiled schedule (cached solves) with a few tile edges and CTA sizes
-const TuneChoice kMeshCandidates[] = {{0, 32, 0, 0}, {0, 64, 0, 0}, {0, 128, 0, 0}, {1, 128, 0, 0},
+const TuneChoice kMeshCandidates[] = {{0, 32, 0, 0}, {0, 64, 0, 0}, {0, 128, 0, 0}, {0, 32, 4, 0},
+                                      {0, 32, 8, 0}, {0, 64, 8, 0}, {0, 32, 16, 0}, {1, 128, 0, 0},
                                       {1, 64, 2, 0}, {2, 128, 8, 0}, {2, 128, 16, 0}, {2, 256, 16, 0},
                                       {2, 256, 32, 0}};
 

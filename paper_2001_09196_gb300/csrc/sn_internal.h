@@ -89,6 +89,13 @@ struct LevelSets {
     int epoch = 0;
     double stall_timeout_s = 0.0;       // > 0: the next dataflow sweep publishes a value nobody waits for
     std::vector<int> h_level;           // host copy of the level of every (dir, elem), dir-major
+    // direction groups of the level schedule: group g sweeps directions [g nd / G, (g + 1) nd / G)
+    // as its own chain of level launches (items sorted by (group, level, dir, elem))
+    int groups = 0;                     // G the group lists were built for (0: not built)
+    int2* gitems = nullptr;
+    std::vector<std::vector<long long>> gptr;  // per group: level boundaries into gitems
+    std::vector<cudaStream_t> gstreams;        // fork/join streams of the captured graph
+    std::vector<cudaEvent_t> gevents;          // [0] fork, [1 + g] join of group g
 };
 
 enum { SCHED_LEVELS = 0, SCHED_DATAFLOW = 1, SCHED_TILES = 2 };
@@ -149,6 +156,7 @@ struct sn_mesh {
     sn::LevelSets levels;
     sn::TileSets tiles;
     int schedule = sn::SCHED_LEVELS;    // sweep schedule (see sn_mesh_set_schedule)
+    int level_groups = 1;               // direction groups of the level schedule (parallel chains)
     int tile_edge = 16;                 // tile edge of the tiled schedule
     int tile_block = 128;               // threads per CTA of the tiled schedule
     int block = 128;                    // threads per block of the sweep kernels
@@ -248,6 +256,9 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 sn_status set_error(sn_status st, const char* msg);
 // sn_sweep.cu
 cudaError_t build_levels(sn_mesh* m, cudaStream_t s, bool* cycle);
+// group lists of the level schedule for G direction groups (needs the level sets)
+cudaError_t build_level_groups(sn_mesh* m, int G);
+void free_level_groups(sn_mesh* m);
 // upwind face bits of every (dir, elem): bit f set when Omega.n_f < 0 and face f has a neighbour
 cudaError_t launch_upwind_mask(sn_mesh* m, unsigned char* mask, cudaStream_t s);
 // sn_tiles.cpp: builds m->tiles for tile edge `edge` (needs the level sets)

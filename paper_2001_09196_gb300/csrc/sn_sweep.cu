@@ -1414,6 +1414,64 @@ cudaError_t build_levels(sn_mesh* m, cudaStream_t s, bool* cycle) {
     return cudaSuccess;
 }
 
+void free_level_groups(sn_mesh* m) {
+    LevelSets& L = m->levels;
+    if (L.gitems) cudaFree(L.gitems);
+    L.gitems = nullptr;
+    for (cudaStream_t st : L.gstreams) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : L.gevents) cudaEventDestroy(ev);
+    L.gstreams.clear();
+    L.gevents.clear();
+    L.gptr.clear();
+    L.groups = 0;
+}
+
+// Directions are independent, so the level schedule may run G groups of directions as G chains
+// of level launches: a chain's levels are those of its own directions, and the deepest direction
+// no longer makes every other direction wait at each of its levels.
+cudaError_t build_level_groups(sn_mesh* m, int G) {
+    free_level_groups(m);
+    LevelSets& L = m->levels;
+    const int nd = m->nd, ne = m->ne;
+    G = std::max(1, std::min(G, nd));
+    const std::vector<int>& lev = L.h_level;
+    std::vector<int2> items;
+    items.reserve((size_t)nd * ne);
+    L.gptr.assign(G, {});
+    for (int g = 0; g < G; ++g) {
+        const int d0 = (int)((long long)g * nd / G), d1 = (int)((long long)(g + 1) * nd / G);
+        int depth = 0;
+        for (int d = d0; d < d1; ++d)
+            for (int e = 0; e < ne; ++e) depth = std::max(depth, lev[(size_t)d * ne + e] + 1);
+        std::vector<long long> cnt(depth + 1, 0);
+        for (int d = d0; d < d1; ++d)
+            for (int e = 0; e < ne; ++e) cnt[lev[(size_t)d * ne + e] + 1]++;
+        for (int l = 0; l < depth; ++l) cnt[l + 1] += cnt[l];
+        const long long base = (long long)items.size();
+        items.resize(base + cnt[depth]);
+        std::vector<long long> fill(cnt.begin(), cnt.end() - 1);
+        for (int d = d0; d < d1; ++d)
+            for (int e = 0; e < ne; ++e) items[base + fill[lev[(size_t)d * ne + e]]++] = make_int2(d, e);
+        for (long long& c : cnt) c += base;
+        L.gptr[g] = cnt;
+    }
+    cudaError_t err;
+    if ((err = cudaMalloc(&L.gitems, items.size() * sizeof(int2))) != cudaSuccess) {
+        L.gitems = nullptr;
+        return err;
+    }
+    if ((err = cudaMemcpy(L.gitems, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return err;
+    L.gstreams.resize(G, nullptr);
+    for (auto& st : L.gstreams)
+        if ((err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return err;
+    L.gevents.resize(G + 1, nullptr);
+    for (auto& ev : L.gevents)
+        if ((err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return err;
+    L.groups = G;
+    return cudaSuccess;
+}
+
 template <int DIM, int P, int MODE, bool ADJ = false>
 static cudaError_t launch_dataflow(sn_mesh* m, const SweepArgs& a, cudaStream_t s, const double* mu = nullptr) {
     LevelSets& L = m->levels;
@@ -1500,45 +1558,31 @@ static cudaError_t launch_tiles(sn_mesh* m, const SweepArgs& a, cudaStream_t s) 
     return cudaGetLastError();
 }
 
-// Level schedule: the launches of one sweep (all levels in order) are captured once into a
-// CUDA graph per kind (forward FP64 / FP32 / FP32+refinement, adjoint); the kernels read their
-// source vector from the mesh-owned buffer d_src so the captured parameters never change.
-static cudaError_t enqueue_levels(sn_mesh* m, int kind, cudaStream_t s) {
-    SweepArgs a = make_args(m);
-    a.q_scale = 1.0;
+// One chain of level launches over the level boundaries `ptr` of the items in a.items, in
+// increasing order (reverse: decreasing, the adjoint); within a chain every launch after the first
+// uses programmatic dependent launch.
+static cudaError_t enqueue_chain(sn_mesh* m, int kind, const SweepArgs& a, const std::vector<long long>& ptr,
+                                 cudaStream_t s) {
     const int bs = m->block;
-    if (kind == 3) {
-        a.psi = m->d_lambda;
-        for (int L = m->levels.n_levels - 1; L >= 0; --L) {
-            const long long b = m->levels.level_ptr[L], e = m->levels.level_ptr[L + 1];
-            if (e <= b) continue;
-            if (a.ainv) {
-                cudaError_t lerr = cudaSuccess;
-                SN_DISPATCH(m->dim, m->p, (lerr = launch_k(L != m->levels.n_levels - 1, node_level_kernel<D_, P_, 0, true>, node_grid(m, e - b, bs), bs, s, a, (const double*)m->d_src, b, e)));
-                if (lerr != cudaSuccess) return lerr;
-            } else
-                SN_DISPATCH(m->dim, m->p, (adjoint_level_kernel<D_, P_><<<grid_for(e - b, bs), bs, 0, s>>>(a, m->d_src, b, e)));
-        }
-        return cudaGetLastError();
-    }
-    // kinds 4..6: the same sweeps without the fixed source (the linear part T of Eq. source0)
-    if (kind >= 4) {  // the linear part: no fixed source and vacuum inflow
-        a.q_scale = 0.0;
-        a.psi_inc = 0.0;
-        kind -= 4;
-    }
-    a.phi = m->d_src;
-    a.psi = kind == SN_FP32 ? m->d_psi32 : m->d_psi;
-    for (int L = 0; L < m->levels.n_levels; ++L) {
-        const long long b = m->levels.level_ptr[L], e = m->levels.level_ptr[L + 1];
+    const int nl = (int)ptr.size() - 1;
+    bool first = true;
+    for (int q = 0; q < nl; ++q) {
+        const int L = kind == 3 ? nl - 1 - q : q;
+        const long long b = ptr[L], e = ptr[L + 1];
         if (e <= b) continue;
         const unsigned g = grid_for(e - b, bs), gn = node_grid(m, e - b, bs);
         cudaError_t lerr = cudaSuccess;
         const double* none = nullptr;
-        if (kind == SN_FP64 && a.ainv)
-            SN_DISPATCH(m->dim, m->p, (lerr = launch_k(L > 0, node_level_kernel<D_, P_, 0, false>, gn, bs, s, a, none, b, e)));
+        const bool pdl = !first;
+        first = false;
+        if (kind == 3 && a.ainv)
+            SN_DISPATCH(m->dim, m->p, (lerr = launch_k(pdl, node_level_kernel<D_, P_, 0, true>, gn, bs, s, a, (const double*)m->d_src, b, e)));
+        else if (kind == 3)
+            SN_DISPATCH(m->dim, m->p, (adjoint_level_kernel<D_, P_><<<g, bs, 0, s>>>(a, m->d_src, b, e)));
+        else if (kind == SN_FP64 && a.ainv)
+            SN_DISPATCH(m->dim, m->p, (lerr = launch_k(pdl, node_level_kernel<D_, P_, 0, false>, gn, bs, s, a, none, b, e)));
         else if (kind == SN_FP32 && a.ainv32)
-            SN_DISPATCH(m->dim, m->p, (lerr = launch_k(L > 0, node_level_kernel<D_, P_, 1, false>, gn, bs, s, a, none, b, e)));
+            SN_DISPATCH(m->dim, m->p, (lerr = launch_k(pdl, node_level_kernel<D_, P_, 1, false>, gn, bs, s, a, none, b, e)));
         else if (kind == SN_FP64) SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 0><<<g, bs, 0, s>>>(a, b, e)));
         else if (kind == SN_FP32) SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 1><<<g, bs, 0, s>>>(a, b, e)));
         else SN_DISPATCH(m->dim, m->p, (sweep_level_kernel<D_, P_, 2><<<g, bs, 0, s>>>(a, b, e)));
@@ -1547,10 +1591,47 @@ static cudaError_t enqueue_levels(sn_mesh* m, int kind, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Level schedule: the launches of one sweep are captured once into a CUDA graph per kind
+// (forward FP64 / FP32 / FP32+refinement, adjoint, and the forward kinds without the fixed
+// source); the kernels read their source vector from the mesh-owned buffer d_src so the captured
+// parameters never change.  With direction groups the graph forks into one chain per group.
+static cudaError_t enqueue_levels(sn_mesh* m, int kind, cudaStream_t s) {
+    SweepArgs a = make_args(m);
+    a.q_scale = 1.0;
+    if (kind == 3) {
+        a.psi = m->d_lambda;
+    } else {
+        if (kind >= 4) {  // the linear part: no fixed source and vacuum inflow
+            a.q_scale = 0.0;
+            a.psi_inc = 0.0;
+            kind -= 4;
+        }
+        a.phi = m->d_src;
+        a.psi = kind == SN_FP32 ? m->d_psi32 : m->d_psi;
+    }
+    LevelSets& L = m->levels;
+    if (m->level_groups <= 1) return enqueue_chain(m, kind, a, L.level_ptr, s);
+    if (L.groups != m->level_groups) return cudaErrorInvalidValue;  // built before the capture starts
+    cudaError_t err;
+    a.items = L.gitems;
+    if ((err = cudaEventRecord(L.gevents[0], s)) != cudaSuccess) return err;
+    for (int g = 0; g < L.groups; ++g) {
+        cudaStream_t gs = L.gstreams[g];
+        if ((err = cudaStreamWaitEvent(gs, L.gevents[0], 0)) != cudaSuccess) return err;
+        if ((err = enqueue_chain(m, kind, a, L.gptr[g], gs)) != cudaSuccess) return err;
+        if ((err = cudaEventRecord(L.gevents[1 + g], gs)) != cudaSuccess) return err;
+        if ((err = cudaStreamWaitEvent(s, L.gevents[1 + g], 0)) != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
 static cudaError_t launch_levels_graph(sn_mesh* m, int kind, cudaStream_t s) {
     cudaError_t err;
     if (!m->level_graph[kind]) {
         if (!m->cap_stream && (err = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return err;
+        if (m->level_groups > 1 && m->levels.groups != m->level_groups &&
+            (err = build_level_groups(m, m->level_groups)) != cudaSuccess)
             return err;
         if ((err = cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return err;
         cudaError_t qerr = enqueue_levels(m, kind, m->cap_stream);
@@ -1564,7 +1645,12 @@ static cudaError_t launch_levels_graph(sn_mesh* m, int kind, cudaStream_t s) {
             return err;
         }
     }
-    g_launches.fetch_add(m->levels.n_levels, std::memory_order_relaxed);
+    long long kernels = m->levels.n_levels;
+    if (m->level_groups > 1) {
+        kernels = 0;
+        for (const auto& ptr : m->levels.gptr) kernels += (long long)ptr.size() - 1;
+    }
+    g_launches.fetch_add(kernels, std::memory_order_relaxed);
     return cudaGraphLaunch(m->level_graph[kind], s);
 }
 

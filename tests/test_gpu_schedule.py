@@ -35,8 +35,11 @@ def test_schedules_agree_bitwise(sn, name, precision):
     phi = torch.as_tensor(inputs.random_phi(prob, 5), device="cuda")
     m.set_schedule("levels", 128)
     ref = m.sweep(phi, precision=precision)
-    for sched, block, param in (("dataflow", 128, 0), ("dataflow", 64, 0), ("dataflow", 32, 1), ("dataflow", 96, 2),
-                                ("tiles", 128, 4), ("tiles", 256, 8), ("tiles", 64, 3), ("tiles", 32, 16)):
+    for sched, block, param in (("levels", 32, 4), ("levels", 64, 3), ("levels", 32, 1000), ("dataflow", 128, 0),
+                                ("dataflow", 64, 0), ("dataflow", 32, 1), ("dataflow", 96, 2), ("tiles", 128, 4),
+                                ("tiles", 256, 8), ("tiles", 64, 3), ("tiles", 32, 16)):
+        if sched == "levels" and param > m.n_dirs:
+            param = m.n_dirs  # one chain per direction
         m.set_schedule(sched, block, param)
         got = m.sweep(phi, precision=precision)
         assert torch.equal(got, ref), (sched, block, param)
@@ -65,12 +68,13 @@ def test_adjoint_schedules_agree_bitwise(sn, name):
     mu = torch.as_tensor(inputs.random_phi(prob, 8) - 0.7, device="cuda")
     m.set_schedule("levels", 128)
     ref = m.adjoint_sweep(mu)
-    for sched, block, param in (("dataflow", 128, 0), ("dataflow", 32, 1), ("tiles", 128, 8)):
+    for sched, block, param in (("levels", 32, 4), ("dataflow", 128, 0), ("dataflow", 32, 1), ("tiles", 128, 8)):
         m.set_schedule(sched, block, param)
         assert torch.equal(m.adjoint_sweep(mu), ref), (sched, block, param)
 
 
-CANDIDATES = {("levels", 32, 0), ("levels", 64, 0), ("levels", 128, 0), ("dataflow", 128, 0), ("dataflow", 128, 1),
+CANDIDATES = {("levels", 32, 0), ("levels", 64, 0), ("levels", 128, 0), ("levels", 32, 4), ("levels", 32, 8),
+              ("levels", 64, 8), ("levels", 32, 16), ("dataflow", 128, 0), ("dataflow", 128, 1),
               ("dataflow", 64, 2), ("dataflow", 32, 4), ("tiles", 128, 8), ("tiles", 128, 16), ("tiles", 256, 16),
               ("tiles", 256, 32)}
 

@@ -93,10 +93,13 @@ sn_status sn_mesh_get_info(const sn_mesh* mesh, sn_mesh_info* info);
  *   a whole tile of param^dim elements of one direction (param = tile edge, 0 = 16 in 2D and 8 in
  *   3D), synchronising itself between the tile's levels and waiting (bounded) only for upwind
  *   elements of other tiles; tiles whose upwind graph is cyclic (jittered faces) run as one task.
- *   Uncached solves (SN_FP32_REFINE, cache off) and the adjoint use schedule 0 instead.
- * block: threads per block, a multiple of 32 in [32, 128] (schedules 0, 1) or [32, 256] (2).
+ *   schedule 3 (operator cache on): one cooperative launch per sweep; every CTA takes its share of
+ *   each level's items and the CTAs meet at a grid barrier between levels (bounded wait,
+ *   SN_ERR_TIMEOUT after 4 s); param = CTAs per SM (at least 1).
+ *   Uncached solves (SN_FP32_REFINE, cache off) and the adjoint use schedule 0 instead of 2 or 3.
+ * block: threads per block, a multiple of 32 in [32, 128] (schedules 0, 1), [32, 256] (2), [32, 512] (3).
  * param: schedule 0: direction groups (0 or 1 = one chain, at most the number of directions);
- * schedule 1: blocks per SM (0 = occupancy limit); schedule 2: tile edge (<= 64).
+ * schedule 1: blocks per SM (0 = occupancy limit); schedule 2: tile edge (<= 64); schedule 3: CTAs per SM.
  */
 sn_status sn_mesh_set_schedule(sn_mesh* mesh, int schedule, int block, int param);
 

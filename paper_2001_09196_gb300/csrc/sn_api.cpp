@@ -67,7 +67,7 @@ void free_mesh(sn_mesh* m) {
     for (void* p : {(void*)m->d_dirs, (void*)m->d_wts, (void*)m->d_corners, (void*)m->d_sigma_t, (void*)m->d_sigma_s,
                     (void*)m->d_q, m->d_psi, m->d_psi32, (void*)m->d_lambda, (void*)m->d_mass, (void*)m->d_work, (void*)m->d_red,
                     (void*)m->d_scalars, (void*)m->levels.items, (void*)m->levels.padded, (void*)m->levels.padded_rev, (void*)m->levels.done,
-                    (void*)m->levels.ctrl, (void*)m->d_krylov})
+                    (void*)m->levels.ctrl, (void*)m->d_krylov, (void*)m->levels.d_level_ptr, (void*)m->levels.d_barrier})
         if (p) cudaFree(p);
     sn::dsa_free(m->dsa);
     delete m;
@@ -309,23 +309,26 @@ sn_status sn_debug_stall_next_sweep(sn_mesh* m, double timeout_seconds) {
 
 sn_status sn_mesh_set_schedule(sn_mesh* m, int schedule, int block, int param) {
     if (!m) return fail(SN_ERR_ARG, "null mesh");
-    if (schedule != sn::SCHED_LEVELS && schedule != sn::SCHED_DATAFLOW && schedule != sn::SCHED_TILES)
-        return fail(SN_ERR_ARG, "bad schedule");
-    const int max_block = schedule == sn::SCHED_TILES ? 256 : 128;
+    if (schedule < sn::SCHED_LEVELS || schedule > sn::SCHED_BARRIER) return fail(SN_ERR_ARG, "bad schedule");
+    const int max_block = schedule == sn::SCHED_TILES ? 256 : (schedule == sn::SCHED_BARRIER ? 512 : 128);
     if (block < 32 || block > max_block || block % 32)
         return fail(SN_ERR_ARG, "block must be a multiple of 32 in [32, %d]", max_block);
     if (param < 0) return fail(SN_ERR_ARG, "the schedule parameter must be >= 0");
     if (schedule == sn::SCHED_TILES && param > 64) return fail(SN_ERR_ARG, "tile edge must be <= 64");
     if (schedule == sn::SCHED_LEVELS && param > m->nd) return fail(SN_ERR_ARG, "more direction groups than directions");
     const int groups = schedule == sn::SCHED_LEVELS ? std::max(param, 1) : m->level_groups;
-    if ((schedule != sn::SCHED_TILES && m->block != block) || groups != m->level_groups) sn::drop_level_graphs(m);
+    const bool own_block = schedule == sn::SCHED_LEVELS || schedule == sn::SCHED_DATAFLOW;
+    if ((own_block && m->block != block) || groups != m->level_groups) sn::drop_level_graphs(m);
     m->schedule = schedule;
-    if (schedule != sn::SCHED_TILES) m->block = block;
+    if (own_block) m->block = block;
     if (schedule == sn::SCHED_TILES) {
         m->tile_block = block;
         m->tile_edge = param > 0 ? param : (m->dim == 2 ? 16 : 8);
     } else if (schedule == sn::SCHED_LEVELS) {
         m->level_groups = groups;
+    } else if (schedule == sn::SCHED_BARRIER) {
+        m->barrier_block = block;
+        m->barrier_ctas_per_sm = std::max(param, 1);
     } else {
         m->max_blocks_per_sm = param;
     }
@@ -1027,10 +1030,10 @@ std::mutex g_tune_mutex;
 const TuneChoice kCandidates[] = {{0, 32, 0, 0}, {0, 64, 0, 0}, {0, 128, 0, 0}, {1, 128, 0, 0},
                                   {1, 128, 1, 0}, {1, 64, 2, 0}, {1, 32, 4, 0}};
 // meshes also try the tiled schedule (cached solves) with a few tile edges and CTA sizes
-const TuneChoice kMeshCandidates[] = {{0, 32, 0, 0}, {0, 64, 0, 0}, {0, 128, 0, 0}, {0, 32, 4, 0},
-                                      {0, 32, 8, 0}, {0, 64, 8, 0}, {0, 32, 16, 0}, {1, 128, 0, 0},
-                                      {1, 64, 2, 0}, {2, 128, 8, 0}, {2, 128, 16, 0}, {2, 256, 16, 0},
-                                      {2, 256, 32, 0}};
+const TuneChoice kMeshCandidates[] = {{0, 32, 0, 0}, {0, 64, 0, 0}, {0, 128, 0, 0}, {0, 32, 2, 0},
+                                      {0, 32, 4, 0}, {0, 64, 8, 0}, {1, 128, 0, 0}, {1, 64, 2, 0},
+                                      {2, 128, 8, 0}, {2, 256, 16, 0}, {3, 256, 1, 0}, {3, 512, 1, 0},
+                                      {3, 256, 2, 0}, {3, 128, 4, 0}};
 
 template <typename F>
 float time_ms(F&& run, cudaStream_t s, int reps) {

@@ -89,6 +89,8 @@ struct LevelSets {
     int epoch = 0;
     double stall_timeout_s = 0.0;       // > 0: the next dataflow sweep publishes a value nobody waits for
     std::vector<int> h_level;           // host copy of the level of every (dir, elem), dir-major
+    long long* d_level_ptr = nullptr;   // device copy of level_ptr (level-barrier schedule)
+    int* d_barrier = nullptr;           // arrival counter of the level-barrier schedule
     // direction groups of the level schedule: group g sweeps directions [g nd / G, (g + 1) nd / G)
     // as its own chain of level launches (items sorted by (group, level, dir, elem))
     int groups = 0;                     // G the group lists were built for (0: not built)
@@ -98,7 +100,7 @@ struct LevelSets {
     std::vector<cudaEvent_t> gevents;          // [0] fork, [1 + g] join of group g
 };
 
-enum { SCHED_LEVELS = 0, SCHED_DATAFLOW = 1, SCHED_TILES = 2 };
+enum { SCHED_LEVELS = 0, SCHED_DATAFLOW = 1, SCHED_TILES = 2, SCHED_BARRIER = 3 };
 
 // Tiled schedule of the cached sweep: the mesh is cut into tiles of edge^dim elements; per
 // direction, the tiles of every strongly connected component of the tile upwind graph form one
@@ -159,6 +161,8 @@ struct sn_mesh {
     int level_groups = 1;               // direction groups of the level schedule (parallel chains)
     int tile_edge = 16;                 // tile edge of the tiled schedule
     int tile_block = 128;               // threads per CTA of the tiled schedule
+    int barrier_block = 256;            // threads per CTA of the level-barrier schedule
+    int barrier_ctas_per_sm = 1;        // CTAs per SM of the level-barrier schedule
     int block = 128;                    // threads per block of the sweep kernels
     int max_blocks_per_sm = 0;          // 0: occupancy limit
     int cache_mode = SN_CACHE_AUTO;     // operator cache (see sn_mesh_set_operator_cache)

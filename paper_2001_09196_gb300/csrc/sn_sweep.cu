@@ -1054,6 +1054,66 @@ __global__ void __launch_bounds__(256) tile_sweep_kernel(SweepArgs a, TileArgs t
     }
 }
 
+// ---------------------------------------------------------------- level-barrier sweep (cached operators)
+// One cooperative launch per sweep: every CTA takes its share of each level's items (one lane per
+// node, node_item) and the CTAs meet at a grid barrier between levels, in place of a kernel
+// boundary.  The barrier is an arrival counter: a CTA's thread 0 fences (making the CTA's angular
+// fluxes visible), adds one, and polls with acquire loads until every CTA of the level has arrived;
+// the poll is bounded and sets the error word when it gives up.
+struct BarrierArgs {
+    const long long* level_ptr;
+    int n_levels;
+    int* counter;                    // zeroed before the launch
+    int* error;
+    int stall;                       // test hook: arrivals are not counted, every wait times out
+    unsigned long long timeout_ns;
+};
+
+template <int DIM, int P, int MODE>
+__global__ void __launch_bounds__(512) barrier_sweep_kernel(SweepArgs a, BarrierArgs b) {
+    constexpr int N = Shape<DIM, P>::N, IPW = 32 / N;
+    __shared__ int s_fail;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int slot = lane / N, r = lane - slot * N, src0 = slot < IPW ? slot * N : 0;
+    const long long per_pass = (long long)(blockDim.x >> 5) * IPW, stride = per_pass * gridDim.x;
+    const unsigned long long deadline = globaltimer() + b.timeout_ns;
+    for (int L = 0; L < b.n_levels; ++L) {
+        const long long lo = b.level_ptr[L], hi = b.level_ptr[L + 1];
+        for (long long base = lo + blockIdx.x * per_pass; base < hi; base += stride) {
+            const long long t = base + warp * IPW + slot;
+            const bool valid = slot < IPW && t < hi;
+            int d = 0, e = 0;
+            if (valid) {
+                const int2 it = a.items[t];
+                d = it.x;
+                e = it.y;
+            }
+            node_item<DIM, P, MODE, false>(a, nullptr, d, e, r, src0, valid);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int fail = 0;
+            __threadfence();
+            if (!b.stall) atomicAdd(b.counter, 1);
+            const int target = (L + 1) * (int)gridDim.x;
+            int polls = 0;
+            while (ld_acquire(b.counter) < target) {
+                if (++polls > 32) {
+                    if (globaltimer() > deadline || *(volatile int*)b.error) {
+                        fail = 1;
+                        atomicExch(b.error, 1);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            s_fail = fail;
+        }
+        __syncthreads();
+        if (s_fail) return;
+    }
+}
+
 // Adjoint: A_e^T lam_e = mu_e - sum_{outflow F, downwind u} C(u<-e)^T lam_u, in reverse level order.
 template <int DIM, int P>
 __device__ __forceinline__ void adjoint_item(const SweepArgs& a, const double* mu, int d, int e) {
@@ -1558,6 +1618,48 @@ static cudaError_t launch_tiles(sn_mesh* m, const SweepArgs& a, cudaStream_t s) 
     return cudaGetLastError();
 }
 
+template <int DIM, int P, int MODE>
+static cudaError_t launch_barrier_sweep(sn_mesh* m, const SweepArgs& a, cudaStream_t s) {
+    LevelSets& L = m->levels;
+    cudaError_t err;
+    if (!L.d_level_ptr) {
+        if ((err = cudaMalloc(&L.d_level_ptr, L.level_ptr.size() * sizeof(long long))) != cudaSuccess) {
+            L.d_level_ptr = nullptr;
+            return err;
+        }
+        if ((err = cudaMemcpy(L.d_level_ptr, L.level_ptr.data(), L.level_ptr.size() * sizeof(long long),
+                              cudaMemcpyHostToDevice)) != cudaSuccess)
+            return err;
+        if ((err = cudaMalloc(&L.d_barrier, sizeof(int))) != cudaSuccess) {
+            L.d_barrier = nullptr;
+            return err;
+        }
+    }
+    BarrierArgs b;
+    b.level_ptr = L.d_level_ptr;
+    b.n_levels = L.n_levels;
+    b.counter = L.d_barrier;
+    b.error = reinterpret_cast<int*>(L.ctrl + 1);
+    b.stall = 0;
+    b.timeout_ns = 4000000000ull;
+    if (L.stall_timeout_s > 0.0) {
+        b.stall = 1;
+        b.timeout_ns = (unsigned long long)(L.stall_timeout_s * 1e9);
+        L.stall_timeout_s = 0.0;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, barrier_sweep_kernel<DIM, P, MODE>, m->barrier_block, 0);
+    per_sm = std::min(per_sm, m->barrier_ctas_per_sm);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if ((err = cudaMemsetAsync(L.d_barrier, 0, sizeof(int), s)) != cudaSuccess) return err;
+    void* args[] = {const_cast<SweepArgs*>(&a), &b};
+    SN_COUNT_LAUNCH();
+    return cudaLaunchCooperativeKernel((const void*)barrier_sweep_kernel<DIM, P, MODE>, dim3(sms * per_sm),
+                                       dim3(m->barrier_block), args, 0, s);
+}
+
 // One chain of level launches over the level boundaries `ptr` of the items in a.items, in
 // increasing order (reverse: decreasing, the adjoint); within a chain every launch after the first
 // uses programmatic dependent launch.
@@ -1762,6 +1864,11 @@ cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double
     if (q_scale == 0.0) a.psi_inc = 0.0;  // the linear part of the update has vacuum inflow
     a.psi = precision == SN_FP32 ? m->d_psi32 : m->d_psi;
     const bool cached = precision == SN_FP64 ? a.ainv != nullptr : (precision == SN_FP32 && a.ainv32 != nullptr);
+    if (m->schedule == SCHED_BARRIER && cached) {  // uncached solves fall back to the level schedule
+        if (precision == SN_FP64) SN_DISPATCH(m->dim, m->p, (cerr = launch_barrier_sweep<D_, P_, 0>(m, a, s)));
+        else SN_DISPATCH(m->dim, m->p, (cerr = launch_barrier_sweep<D_, P_, 1>(m, a, s)));
+        return cerr;
+    }
     if (m->schedule == SCHED_TILES && cached) {  // uncached solves fall back to the level schedule
         if (m->tiles.edge != m->tile_edge && (cerr = build_tiles(m, m->tile_edge, s)) != cudaSuccess) return cerr;
         if (precision == SN_FP64) SN_DISPATCH(m->dim, m->p, (cerr = launch_tiles<D_, P_, 0>(m, a, s)));

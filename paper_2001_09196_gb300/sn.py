@@ -222,8 +222,9 @@ class Mesh:
         return (self.n_elem, self.n_nodes)
 
     def set_schedule(self, schedule="dataflow", block=128, param=0):
-        """schedule "levels" | "dataflow" | "tiles"; param: per-SM block cap (dataflow) or tile edge (tiles)."""
-        sched = {"levels": 0, "dataflow": 1, "tiles": 2}[schedule] if isinstance(schedule, str) else int(schedule)
+        """schedule "levels" | "dataflow" | "tiles" | "barrier"; param: direction groups (levels), per-SM
+        block cap (dataflow), tile edge (tiles) or CTAs per SM (barrier)."""
+        sched = {"levels": 0, "dataflow": 1, "tiles": 2, "barrier": 3}[schedule] if isinstance(schedule, str) else int(schedule)
         _check(_lib.sn_mesh_set_schedule(self._h, sched, int(block), int(param)))
 
     def set_operator_cache(self, mode="auto"):
@@ -239,7 +240,7 @@ class Mesh:
         a, b, c = C.c_int(), C.c_int(), C.c_int()
         _check(_lib.sn_mesh_autotune(self._h, _PREC.get(precision, precision), _stream(stream), C.byref(a),
                                      C.byref(b), C.byref(c)))
-        return ("levels", "dataflow", "tiles")[a.value], b.value, c.value
+        return ("levels", "dataflow", "tiles", "barrier")[a.value], b.value, c.value
 
     def quadrature(self):
         dirs = np.zeros((self.n_dirs, 3))
@@ -363,7 +364,7 @@ class Batch:
         a, b, c = C.c_int(), C.c_int(), C.c_int()
         _check(_lib.sn_batch_autotune(self._h, _PREC.get(precision, precision), _stream(stream), C.byref(a),
                                       C.byref(b), C.byref(c)))
-        return ("levels", "dataflow", "tiles")[a.value], b.value, c.value
+        return ("levels", "dataflow", "tiles", "barrier")[a.value], b.value, c.value
 
     @staticmethod
     def _ptrs(tensors):

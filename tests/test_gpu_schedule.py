@@ -37,7 +37,8 @@ def test_schedules_agree_bitwise(sn, name, precision):
     ref = m.sweep(phi, precision=precision)
     for sched, block, param in (("levels", 32, 4), ("levels", 64, 3), ("levels", 32, 1000), ("dataflow", 128, 0),
                                 ("dataflow", 64, 0), ("dataflow", 32, 1), ("dataflow", 96, 2), ("tiles", 128, 4),
-                                ("tiles", 256, 8), ("tiles", 64, 3), ("tiles", 32, 16)):
+                                ("tiles", 256, 8), ("tiles", 64, 3), ("tiles", 32, 16), ("barrier", 256, 1),
+                                ("barrier", 512, 1), ("barrier", 128, 3)):
         if sched == "levels" and param > m.n_dirs:
             param = m.n_dirs  # one chain per direction
         m.set_schedule(sched, block, param)
@@ -45,7 +46,7 @@ def test_schedules_agree_bitwise(sn, name, precision):
         assert torch.equal(got, ref), (sched, block, param)
 
 
-@pytest.mark.parametrize("schedule", [("dataflow", 128, 0), ("tiles", 128, 8)])
+@pytest.mark.parametrize("schedule", [("dataflow", 128, 0), ("tiles", 128, 8), ("barrier", 256, 1)])
 def test_dependency_wait_timeout_is_reported_and_recoverable(sn, schedule):
     prob = CASES["c2_32"]()
     m = sn.Mesh.from_problem(prob)
@@ -76,7 +77,8 @@ def test_adjoint_schedules_agree_bitwise(sn, name):
 CANDIDATES = {("levels", 32, 0), ("levels", 64, 0), ("levels", 128, 0), ("levels", 32, 4), ("levels", 32, 8),
               ("levels", 64, 8), ("levels", 32, 16), ("dataflow", 128, 0), ("dataflow", 128, 1),
               ("dataflow", 64, 2), ("dataflow", 32, 4), ("tiles", 128, 8), ("tiles", 128, 16), ("tiles", 256, 16),
-              ("tiles", 256, 32)}
+              ("tiles", 256, 32), ("levels", 32, 2), ("tiles", 256, 16), ("barrier", 256, 1), ("barrier", 512, 1),
+              ("barrier", 256, 2), ("barrier", 128, 4)}
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

@@ -66,30 +66,47 @@ __global__ void block_jacobi_kernel(const double* dinv, int nt, int n, double om
     x[idx] = (accumulate ? x[idx] : 0.0) + omega * s;
 }
 
-__global__ void csr_kernel(const int* ptr, const int* col, const double* val, int rows, const double* x,
-                           const double* b, double* out, int mode) {
-    // mode 0: out = M x; 1: out = b - M x; 2: out += M x
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rows) return;
+// CSR product with G lanes per row (G a power of two dividing 32): the lanes of a group take
+// every G-th entry of the row and the group adds its partial sums by a fixed shuffle tree, so a
+// row costs about (nnz / G) dependent loads instead of nnz.  mode 0: out = M x; 1: out = b - M x;
+// 2: out += M x.
+template <int G>
+__global__ void csr_vec_kernel(const int* ptr, const int* col, const double* val, int rows, const double* x,
+                               const double* b, double* out, int mode) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int gl = threadIdx.x & (G - 1);
+    const long long row = tid / G;
     double s = 0.0;
-    for (int k = ptr[r]; k < ptr[r + 1]; ++k) s += val[k] * x[col[k]];
-    if (mode == 0) out[r] = s;
-    else if (mode == 1) out[r] = b[r] - s;
-    else out[r] += s;
+    if (row < rows) {
+        const int k1 = ptr[row + 1];
+        for (int k = ptr[row] + gl; k < k1; k += G) s += val[k] * x[col[k]];
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
+    if (row < rows && gl == 0) {
+        if (mode == 0) out[row] = s;
+        else if (mode == 1) out[row] = b[row] - s;
+        else out[row] += s;
+    }
+}
+
+// x = A b for the dense coarsest level, one warp per row (lanes stride over the columns)
+__global__ void dense_mv_warp_kernel(const double* A, int n, const double* b, double* x) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const long long row = tid >> 5;
+    double s = 0.0;
+    if (row < n)
+        for (int c = lane; c < n; c += 32) s += A[(size_t)row * n + c] * b[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (row < n && lane == 0) x[row] = s;
 }
 
 __global__ void jacobi_kernel(const double* dinv, int rows, double omega, const double* r, double* x, int accumulate) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= rows) return;
     x[i] = (accumulate ? x[i] : 0.0) + omega * dinv[i] * r[i];
-}
-
-__global__ void dense_mv_kernel(const double* A, int n, const double* b, double* x) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    double s = 0.0;
-    for (int c = 0; c < n; ++c) s += A[(size_t)r * n + c] * b[c];
-    x[r] = s;
 }
 
 // Algorithm 1 (triangular heterogeneous DSA) helpers on full [elem][node] vectors; emask marks
@@ -238,12 +255,23 @@ cudaError_t dot(DsaHierarchy* H, const double* a, const double* b, long long n, 
     return cudaGetLastError();
 }
 
+// CSR product with the group width chosen from the rows' average length.
+void csr_mv(const int* ptr, const int* col, const double* val, int rows, long long nnz, const double* x,
+            const double* b, double* out, int mode, cudaStream_t s) {
+    if (rows <= 0) return;
+    const double avg = (double)nnz / rows;
+    SN_COUNT_LAUNCH();
+    if (avg > 12.0) csr_vec_kernel<8><<<nblk((long long)rows * 8), kBS, 0, s>>>(ptr, col, val, rows, x, b, out, mode);
+    else if (avg > 3.0) csr_vec_kernel<4><<<nblk((long long)rows * 4), kBS, 0, s>>>(ptr, col, val, rows, x, b, out, mode);
+    else csr_vec_kernel<1><<<nblk(rows), kBS, 0, s>>>(ptr, col, val, rows, x, b, out, mode);
+}
+
 // continuous level l (index into H->levels): x = V(b)
 void vcycle_c(DsaHierarchy* H, size_t l, cudaStream_t s) {
     LevelC& L = H->levels[l];
     if (!L.dense_inv.empty()) {
         SN_COUNT_LAUNCH();
-        dense_mv_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_dense, L.n, L.d_b, L.d_x);
+        dense_mv_warp_kernel<<<nblk((long long)L.n * 32), kBS, 0, s>>>(L.d_dense, L.n, L.d_b, L.d_x);
         return;
     }
     for (int k = 0; k < H->nu; ++k) {
@@ -251,23 +279,18 @@ void vcycle_c(DsaHierarchy* H, size_t l, cudaStream_t s) {
             SN_COUNT_LAUNCH();
             jacobi_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_dinv, L.n, H->omega, L.d_b, L.d_x, 0);
         } else {
-            SN_COUNT_LAUNCH();
-            csr_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_a_ptr, L.d_a_col, L.d_a_val, L.n, L.d_x, L.d_b, L.d_r, 1);
+            csr_mv(L.d_a_ptr, L.d_a_col, L.d_a_val, L.n, (long long)L.a_val.size(), L.d_x, L.d_b, L.d_r, 1, s);
             SN_COUNT_LAUNCH();
             jacobi_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_dinv, L.n, H->omega, L.d_r, L.d_x, 1);
         }
     }
-    SN_COUNT_LAUNCH();
-    csr_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_a_ptr, L.d_a_col, L.d_a_val, L.n, L.d_x, L.d_b, L.d_r, 1);
+    csr_mv(L.d_a_ptr, L.d_a_col, L.d_a_val, L.n, (long long)L.a_val.size(), L.d_x, L.d_b, L.d_r, 1, s);
     LevelC& C = H->levels[l + 1];
-    SN_COUNT_LAUNCH();
-    csr_kernel<<<nblk(C.n), kBS, 0, s>>>(C.d_r_ptr, C.d_r_col, C.d_r_val, C.n, L.d_r, nullptr, C.d_b, 0);
+    csr_mv(C.d_r_ptr, C.d_r_col, C.d_r_val, C.n, (long long)C.r_val.size(), L.d_r, nullptr, C.d_b, 0, s);
     vcycle_c(H, l + 1, s);
-    SN_COUNT_LAUNCH();
-    csr_kernel<<<nblk(L.n), kBS, 0, s>>>(C.d_p_ptr, C.d_p_col, C.d_p_val, L.n, C.d_x, nullptr, L.d_x, 2);
+    csr_mv(C.d_p_ptr, C.d_p_col, C.d_p_val, L.n, (long long)C.p_val.size(), C.d_x, nullptr, L.d_x, 2, s);
     for (int k = 0; k < H->nu; ++k) {
-        SN_COUNT_LAUNCH();
-        csr_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_a_ptr, L.d_a_col, L.d_a_val, L.n, L.d_x, L.d_b, L.d_r, 1);
+        csr_mv(L.d_a_ptr, L.d_a_col, L.d_a_val, L.n, (long long)L.a_val.size(), L.d_x, L.d_b, L.d_r, 1, s);
         SN_COUNT_LAUNCH();
         jacobi_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_dinv, L.n, H->omega, L.d_r, L.d_x, 1);
     }
@@ -293,11 +316,9 @@ void vcycle0(DsaHierarchy* H, const double* r, double* z, cudaStream_t s) {
         SN_COUNT_LAUNCH();
         bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, nt, n, z, r, H->d_vr);
         LevelC& C = H->levels[0];
-        SN_COUNT_LAUNCH();
-        csr_kernel<<<nblk(C.n), kBS, 0, s>>>(C.d_r_ptr, C.d_r_col, C.d_r_val, C.n, H->d_vr, nullptr, C.d_b, 0);
+        csr_mv(C.d_r_ptr, C.d_r_col, C.d_r_val, C.n, (long long)C.r_val.size(), H->d_vr, nullptr, C.d_b, 0, s);
         vcycle_c(H, 0, s);
-        SN_COUNT_LAUNCH();
-        csr_kernel<<<nblk(N0), kBS, 0, s>>>(C.d_p_ptr, C.d_p_col, C.d_p_val, (int)N0, C.d_x, nullptr, z, 2);
+        csr_mv(C.d_p_ptr, C.d_p_col, C.d_p_val, (int)N0, (long long)C.p_val.size(), C.d_x, nullptr, z, 2, s);
     }
     for (int k = 0; k < H->nu; ++k) {
         SN_COUNT_LAUNCH();

@@ -131,16 +131,27 @@ __global__ void u_block_jacobi(const int* row_inst, const int* inst_n, const lon
     x[r] = (accumulate ? x[r] : 0.0) + omega * s;
 }
 
+// CSR product with 4 lanes per row and a fixed shuffle tree (see csr_vec_kernel of the
+// single-mesh DSA); mode 0: out = M x; 1: out = b - M x; 2: out += M x
 __global__ void u_csr(const int* ptr, const int* col, const double* val, int rows, const double* x, const double* b,
                       double* out, int mode, const int* done) {
     SKIP_IF_DONE;
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rows) return;
+    constexpr int G = 4;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int gl = threadIdx.x & (G - 1);
+    const long long r = tid / G;
     double s = 0.0;
-    for (int k = ptr[r]; k < ptr[r + 1]; ++k) s += val[k] * x[col[k]];
-    if (mode == 0) out[r] = s;
-    else if (mode == 1) out[r] = b[r] - s;
-    else out[r] += s;
+    if (r < rows) {
+        const int k1 = ptr[r + 1];
+        for (int k = ptr[r] + gl; k < k1; k += G) s += val[k] * x[col[k]];
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
+    if (r < rows && gl == 0) {
+        if (mode == 0) out[r] = s;
+        else if (mode == 1) out[r] = b[r] - s;
+        else out[r] += s;
+    }
 }
 
 __global__ void u_jacobi(const double* dinv, int rows, double omega, const double* res, double* x, int accumulate,
@@ -151,20 +162,24 @@ __global__ void u_jacobi(const double* dinv, int rows, double omega, const doubl
     x[i] = (accumulate ? x[i] : 0.0) + omega * dinv[i] * res[i];
 }
 
-// x[off_k + r] = sum_c A_k[r][c] b[off_k + c] for every dense block k (one block per CTA row group)
+// x[off_k + r] = sum_c A_k[r][c] b[off_k + c] for every dense block k, one warp per row
 __global__ void u_dense(const int* off, const int* size, const long long* mat, const double* val, int n_dense,
                         const double* b, double* x, const int* done) {
     SKIP_IF_DONE;
     const int k = blockIdx.y;
     if (k >= n_dense) return;
     const int n = size[k];
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const double* A = val + mat[k] + (size_t)r * n;
-    const double* bb = b + off[k];
+    const int lane = threadIdx.x & 31;
+    const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     double s = 0.0;
-    for (int c = 0; c < n; ++c) s += A[c] * bb[c];
-    x[off[k] + r] = s;
+    if (r < n) {
+        const double* A = val + mat[k] + (size_t)r * n;
+        const double* bb = b + off[k];
+        for (int c = lane; c < n; c += 32) s += A[c] * bb[c];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (r < n && lane == 0) x[off[k] + r] = s;
 }
 
 __global__ void u_dot_partial(const double* a, const double* b, long long n, double* part, const int* done) {
@@ -274,7 +289,7 @@ void vcycle_union(UnionDsa* U, size_t l, cudaStream_t s) {
             u_jacobi<<<nb(L.n), kBS, 0, s>>>(L.dinv, L.n, U->omega, L.b, L.x, 0, dn);
         } else {
             SN_COUNT_LAUNCH();
-            u_csr<<<nb(L.n), kBS, 0, s>>>(L.a_ptr, L.a_col, L.a_val, L.n, L.x, L.b, L.r, 1, dn);
+            u_csr<<<nb((long long)(L.n) * 4), kBS, 0, s>>>(L.a_ptr, L.a_col, L.a_val, L.n, L.x, L.b, L.r, 1, dn);
             SN_COUNT_LAUNCH();
             u_jacobi<<<nb(L.n), kBS, 0, s>>>(L.dinv, L.n, U->omega, L.r, L.x, 1, dn);
         }
@@ -282,22 +297,22 @@ void vcycle_union(UnionDsa* U, size_t l, cudaStream_t s) {
     if (l + 1 < U->levels.size()) {
         UnionLevel& C = U->levels[l + 1];
         SN_COUNT_LAUNCH();
-        u_csr<<<nb(L.n), kBS, 0, s>>>(L.a_ptr, L.a_col, L.a_val, L.n, L.x, L.b, L.r, 1, dn);
+        u_csr<<<nb((long long)(L.n) * 4), kBS, 0, s>>>(L.a_ptr, L.a_col, L.a_val, L.n, L.x, L.b, L.r, 1, dn);
         SN_COUNT_LAUNCH();
-        u_csr<<<nb(C.n), kBS, 0, s>>>(C.r_ptr, C.r_col, C.r_val, C.n, L.r, nullptr, C.b, 0, dn);
+        u_csr<<<nb((long long)(C.n) * 4), kBS, 0, s>>>(C.r_ptr, C.r_col, C.r_val, C.n, L.r, nullptr, C.b, 0, dn);
         vcycle_union(U, l + 1, s);
         SN_COUNT_LAUNCH();
-        u_csr<<<nb(L.n), kBS, 0, s>>>(C.p_ptr, C.p_col, C.p_val, L.n, C.x, nullptr, L.x, 2, dn);
+        u_csr<<<nb((long long)(L.n) * 4), kBS, 0, s>>>(C.p_ptr, C.p_col, C.p_val, L.n, C.x, nullptr, L.x, 2, dn);
     }
     for (int k = 0; k < U->nu; ++k) {
         SN_COUNT_LAUNCH();
-        u_csr<<<nb(L.n), kBS, 0, s>>>(L.a_ptr, L.a_col, L.a_val, L.n, L.x, L.b, L.r, 1, dn);
+        u_csr<<<nb((long long)(L.n) * 4), kBS, 0, s>>>(L.a_ptr, L.a_col, L.a_val, L.n, L.x, L.b, L.r, 1, dn);
         SN_COUNT_LAUNCH();
         u_jacobi<<<nb(L.n), kBS, 0, s>>>(L.dinv, L.n, U->omega, L.r, L.x, 1, dn);
     }
     if (L.n_dense > 0) {  // instances whose hierarchy ends here: exact coarsest solve
         SN_COUNT_LAUNCH();
-        u_dense<<<dim3(nb(L.max_dense), L.n_dense), kBS, 0, s>>>(L.dense_off, L.dense_size, L.dense_mat, L.dense_val, L.n_dense,
+        u_dense<<<dim3(nb((long long)L.max_dense * 32), L.n_dense), kBS, 0, s>>>(L.dense_off, L.dense_size, L.dense_mat, L.dense_val, L.n_dense,
                                                         L.b, L.x, dn);
     }
 }
@@ -325,10 +340,10 @@ void vcycle0_union(UnionDsa* U, const double* r, double* z, cudaStream_t s) {
         u_bsr<<<nb(n), kBS, 0, s>>>(U->row_inst, U->inst_n, U->inst_row0, U->inst_ptr0, U->inst_blk0, U->inst_val0, U->bsr_ptr,
                                    U->bsr_col, U->bsr_val, n, z, r, U->vr, dn);
         SN_COUNT_LAUNCH();
-        u_csr<<<nb(C.n), kBS, 0, s>>>(C.r_ptr, C.r_col, C.r_val, C.n, U->vr, nullptr, C.b, 0, dn);
+        u_csr<<<nb((long long)(C.n) * 4), kBS, 0, s>>>(C.r_ptr, C.r_col, C.r_val, C.n, U->vr, nullptr, C.b, 0, dn);
         vcycle_union(U, 0, s);
         SN_COUNT_LAUNCH();
-        u_csr<<<nb(n), kBS, 0, s>>>(C.p_ptr, C.p_col, C.p_val, (int)n, C.x, nullptr, z, 2, dn);
+        u_csr<<<nb((long long)(n) * 4), kBS, 0, s>>>(C.p_ptr, C.p_col, C.p_val, (int)n, C.x, nullptr, z, 2, dn);
     }
     for (int k = 0; k < U->nu; ++k) {
         SN_COUNT_LAUNCH();

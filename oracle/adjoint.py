@@ -13,7 +13,8 @@ Per element e with mass matrix M_e this gives
     dJ/dq_e       =  sum_d lambda_d,e^T M_e 1 / (4 pi).
 L_d^T is solved element by element in reverse upwind order with transposed element and
 face-coupling blocks.  The DSA step of the adjoint iteration uses the transposed
-Algorithm 2 preconditioner, I + E_f Sigma_f D_ff^{-1} E_f^T (D_ff symmetric); like any
+Algorithm 2 preconditioner, I + E_f Sigma_f D_ff^{-T} E_f^T (D_ff^{-T} = D_ff^{-1} for the
+symmetric operator, a transposed solve for the nonsymmetric ones of Eq. NIP); like any
 convergent preconditioner it leaves mu unchanged.
 """
 from __future__ import annotations
@@ -77,12 +78,7 @@ def adjoint_iterate(T, g_modal, dsa=None, tol=1e-12, max_iters=2000):
         r0 = r0 if r0 is not None else (rn if rn > 0 else 1.0)
         rel = rn / r0
         if dsa is not None and dsa.thick.size:
-            # transposed Algorithm 2: E_f Sigma_f D_ff^{-1} E_f^T r
-            th = dsa.thick
-            z = dsa.lu.solve(r[th].ravel()).reshape(-1, T.n)
-            corr = np.zeros_like(r)
-            corr[th] = np.einsum("e,emn,en->em", dsa.sig[th], T.M[th], z)
-            half = half + corr
+            half = half + dsa.correction_transposed(r)  # transposed Algorithm 2
         mu = half
         it += 1
         if rel <= tol:

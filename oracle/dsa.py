@@ -4,28 +4,36 @@ Paper: Sec. 2.2 (Eq. dsa_prec, Eq. DSA_fp and the additive form D^{-1} = I + D^{
 Sec. 3 (Algorithm 2, diagonal heterogeneous DSA: phi_f <- phi_f + D_ff^{-1} Sigma_f r_f; and
 Algorithm 1, triangular heterogeneous DSA, the same step followed by a zero-source transport
 update of the thick correction whose result is added on the thin DOFs only),
-Sec. 4.1 (interior-penalty DSA operators, Eq. SIP, Eq. ModifiedF0) and Sec. 4.2 (the
-heterogeneous operator is the principal submatrix on the thick elements, thick where
-sigma_s >= eta).
+Sec. 4.1 (interior-penalty DSA operators: Eq. SIP, Eq. NIP and the modified penalty of
+Eq. ModifiedF0) and Sec. 4.2 (the heterogeneous operator is the principal submatrix on the
+thick elements, thick where sigma_s >= eta).
 
-Readings (the paper's preferred NIP operator is nonsymmetric; this path needs an SPD
-operator for conjugate gradients):
-  * Operator: symmetric interior penalty on the thick elements only,
-        a(u, v) = sum_K (D_K grad u, grad v)_K + (sigma_a u, v)_K
-                + sum_{F interior, both sides thick} <kappa [u],[v]> - <{D grad u.n},[v]> - <{D grad v.n},[u]>
-                + sum_{F on the boundary of the thick region} <kappa u, v> - 1/2<D grad u.n, v> - 1/2<D grad v.n, u>
-    with D = 1/(3 sigma_t), sigma_a = sigma_t - sigma_s.  A face whose neighbour is not thick
-    (thin, void or outside the domain) is treated as a face to a zero exterior state: jump = u,
-    average = half the interior flux.  This is what the principal submatrix of a global
-    interior-penalty matrix gives on such a face, except that the penalty below uses only
-    the thick side, so the operator depends on thick-element data alone (Sec. 4.2).
-  * Penalty: kappa_F = max(1/4, c(p) * (D^-/h^- + D^+/h^+)/2) on interior faces and
-    max(1/4, c(p) * D/h) on boundary faces, c(p) = C_IP p (p+1), h = |K|/|F|.  1/4 is the
-    angular integral of the paper's F_0 = (1/4 pi) sum_d w_d |Omega_d.n|/2; the max() floor is the
-    modification of Eq. ModifiedF0.
-  * All integrals use (p+1)-point Gauss rules per direction (volume and faces), so that a
-    nodal implementation on the same points evaluates the identical bilinear form.
-  * Right-hand side mass matrix Sigma: sigma_s (default) or sigma_t (footnote of Sec. 2.2).
+Three operators, all with D = 1/(3 sigma_t), sigma_a = sigma_t - sigma_s and the same volume form
+sum_K (D grad u, grad v)_K + (sigma_a u, v)_K; they differ on the faces.  A face whose neighbour
+is not thick (thin, void or outside the domain) is treated as a face to a zero exterior state:
+jump = u, average = half the interior value.  This is what the principal submatrix of a global
+interior-penalty matrix gives on such a face.
+  * "sip" (default; the conjugate-gradient path needs an SPD operator):
+        <kappa [u],[v]> - <{D grad u.n},[v]> - <{D grad v.n},[u]>,
+    kappa_F = max(1/4, c(p) (D^-/h^- + D^+/h^+)/2) on interior faces and max(1/4, c(p) D/h) on
+    boundary faces, c(p) = C_IP p (p+1), h = |K|/|F|.  1/4 is the angular integral of the paper's
+    F_0 = (1/4 pi) sum_d w_d |Omega_d.n|/2; the max() floor is the idea of Eq. ModifiedF0 in the
+    form of the modified interior penalty method.  Only thick-element data enter (Sec. 4.2).
+  * "nip" (Eq. NIP): drops the symmetrising term G^T Sigma_t^{-1} F_1, which is the face term
+    -<{D grad v.n},[u]>; keeps -<{D grad u.n},[v]> (the term F_1^T Sigma_t^{-1} G) and the plain
+    penalty F_0, kappa_F = 1/4.  Nonsymmetric.
+  * "mnip" (Eq. NIP with Eq. ModifiedF0): the face terms of "nip" with the modified penalty
+        kappa_F = 1/8 [max(c(p)/(sigma_t^- h^-), 1) + max(c(p)/(sigma_t^+ h^+), 1)],
+    c(p) = C_M p (p+1), C_M = 0.1 (Sec. 4.1.1).  Reading: each side is the upwind side for the
+    directions leaving it, and (1/4 pi) times the angular integral of |Omega.n| over either half
+    of the sphere is 1/4, so the (1/8 pi) sum over directions splits into 1/8 per side.  The
+    neighbour is any element, thin ones included (Sec. 4.2 notes that heterogeneous mNIP brings
+    thin data into the thick submatrix); on the domain boundary the element's own value stands
+    for the missing side.  A void neighbour (sigma_t = 0) makes the penalty infinite: the paper
+    states that Eq. ModifiedF0 is not compatible with voids, so this is an error.
+All integrals use (p+1)-point Gauss rules per direction (volume and faces), so that a nodal
+implementation on the same points evaluates the identical bilinear form.  Right-hand side mass
+matrix Sigma: sigma_s (default) or sigma_t (footnote of Sec. 2.2).
 """
 from __future__ import annotations
 
@@ -36,16 +44,25 @@ import scipy.sparse.linalg as spla
 from .dg import adjugate, face_points, tensor_rule
 
 C_IP = 2.0
+C_M = 0.1  # the constant of c(p) in Eq. ModifiedF0 (Sec. 4.1.1)
+OPERATORS = ("sip", "nip", "mnip")
 
 
 class DSA:
     """Assembles D_ff in the oracle's modal basis and applies the Algorithm 2 correction."""
 
-    def __init__(self, T, mask, sigma="sigma_s", c_ip=C_IP, allow_void=False):
+    def __init__(self, T, mask, sigma="sigma_s", c_ip=C_IP, allow_void=False, operator="sip"):
         self.T = T
+        if operator not in OPERATORS:
+            raise ValueError(f"unknown DSA operator {operator!r}")
+        self.operator = operator
         mask = np.asarray(mask).astype(bool).ravel()
         if not allow_void and np.any(T.sigma_t[mask] <= 0):
             raise ValueError("DSA on an element with sigma_t = 0 (full DSA is incompatible with voids)")
+        if operator == "mnip":
+            nb = T.mesh.nbr[mask]
+            if np.any((nb >= 0) & (T.sigma_t[np.maximum(nb, 0)] <= 0)):
+                raise ValueError("mNIP penalty next to a void element (Eq. ModifiedF0 is not compatible with voids)")
         self.mask = mask
         self.thick = np.flatnonzero(mask)
         self.local = -np.ones(T.ne, dtype=np.int64)
@@ -76,6 +93,11 @@ class DSA:
         K = (np.einsum("e,q,eq,eqmr,eqnr->emn", Dc, wts, detJ, gB, gB)
              + np.einsum("e,q,eq,qm,qn->emn", sa, wts, detJ, B, B))
         vol = np.einsum("q,eq->e", wts, detJ)
+        _, Jall = T.mesh.map(pts)
+        vol_all = np.einsum("q,eq->e", wts, np.linalg.det(Jall))   # every element (mNIP neighbours)
+        op = self.operator
+        cm = C_M * p * (p + 1)
+        sym = 1.0 if op == "sip" else 0.0            # weight of the symmetrising face term
         rows, cols, vals = [], [], []
 
         def add(re, ce, blk):
@@ -112,10 +134,22 @@ class DSA:
             # boundary-type faces: <kappa u, v> - 1/2 <D du/dn, v> - 1/2 <D dv/dn, u>
             if np.any(bnd):
                 e = np.flatnonzero(bnd)
-                kap = np.maximum(0.25, cp * Dc[e] / h[e])
+                if op == "sip":
+                    kap = np.maximum(0.25, cp * Dc[e] / h[e])
+                elif op == "nip":
+                    kap = np.full(e.size, 0.25)
+                else:
+                    st_e = T.sigma_t[th[e]]
+                    own = np.maximum(cm / (st_e * h[e]), 1.0)
+                    u_all = u[e]
+                    has = u_all >= 0
+                    ug = np.maximum(u_all, 0)
+                    h_o = vol_all[ug] / area[e]
+                    other = np.where(has, np.maximum(cm / (np.where(has, T.sigma_t[ug], 1.0) * h_o), 1.0), own)
+                    kap = 0.125 * (own + other)
                 blk = (np.einsum("e,eq,qm,qn->emn", kap, dS[e], Bf, Bf)
                        - 0.5 * np.einsum("e,eq,eqn,qm->emn", Dc[e], dS[e], dn[e], Bf)
-                       - 0.5 * np.einsum("e,eq,eqm,qn->emn", Dc[e], dS[e], dn[e], Bf))
+                       - sym * 0.5 * np.einsum("e,eq,eqm,qn->emn", Dc[e], dS[e], dn[e], Bf))
                 add(e, e, blk)
             # interior thick-thick faces, assembled once from the side with side == 1
             if side == 1 and np.any(inter):
@@ -126,13 +160,20 @@ class DSA:
                 gBo = np.einsum("eqkr,qmk->eqmr", np.linalg.inv(Jo), dBo)
                 dno = np.einsum("eqmr,eqr->eqm", gBo, nrm[e])       # neighbour gradient . n (n from e to o)
                 ho = vol[o] / area[e]              # conforming faces: same |F| from both sides
-                kap = np.maximum(0.25, cp * 0.5 * (Dc[e] / h[e] + Dc[o] / ho))
+                if op == "sip":
+                    kap = np.maximum(0.25, cp * 0.5 * (Dc[e] / h[e] + Dc[o] / ho))
+                elif op == "nip":
+                    kap = np.full(e.size, 0.25)
+                else:
+                    kap = 0.125 * (np.maximum(cm / (T.sigma_t[th[e]] * h[e]), 1.0)
+                                   + np.maximum(cm / (T.sigma_t[th[o]] * ho), 1.0))
                 sides = [(e, Bf, dn[e], Dc[e], 1.0), (o, Bo, dno, Dc[o], -1.0)]
                 for (ra, Ba, dna, Da, sa_) in sides:
                     for (cb, Bb, dnb, Db, sb_) in sides:
+                        # row ra (test v), column cb (trial u): penalty, -{D du/dn}[v], -{D dv/dn}[u]
                         blk = (np.einsum("e,eq,qm,qn->emn", kap * sa_ * sb_, dS[e], Ba, Bb)
                                - 0.5 * np.einsum("e,eq,eqn,qm->emn", Db * sa_, dS[e], dnb, Ba)
-                               - 0.5 * np.einsum("e,eq,eqm,qn->emn", Da * sb_, dS[e], dna, Bb))
+                               - sym * 0.5 * np.einsum("e,eq,eqm,qn->emn", Da * sb_, dS[e], dna, Bb))
                         add(ra, cb, blk)
         return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                              shape=(nt * n, nt * n))
@@ -147,6 +188,15 @@ class DSA:
         out = np.zeros_like(r_modal)
         if self.thick.size:
             out[self.thick] = self.lu.solve(self.rhs(r_modal)).reshape(-1, self.T.n)
+        return out
+
+    def correction_transposed(self, r_modal):
+        """Transpose of correction(): E_f Sigma_f D_ff^{-T} E_f^T r (the adjoint iteration's step)."""
+        out = np.zeros_like(r_modal)
+        th = self.thick
+        if th.size:
+            z = self.lu.solve(r_modal[th].ravel(), trans="T").reshape(-1, self.T.n)
+            out[th] = np.einsum("e,emn,en->em", self.sig[th], self.T.M[th], z)
         return out
 
     # nodal view of the operator, for comparisons with a nodal implementation

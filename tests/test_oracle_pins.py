@@ -165,8 +165,10 @@ def _void_free_c1():
     return prob
 
 
-def test_dsa_fixed_point_invariance():
-    """DSA is a preconditioner only: none / thick / full reach the same phi (Eq. DSA_fp)."""
+@pytest.mark.parametrize("operator", ["sip", "nip", "mnip"])
+def test_dsa_fixed_point_invariance(operator):
+    """DSA is a preconditioner only: none / thick / full reach the same phi (Eq. DSA_fp), with each
+    interior-penalty operator of Sec. 4.1."""
     prob = inputs.config2d_fields(6, 1, 4, 99, "inv")
     prob.q[:] = 1.0
     prob.sigma_t[prob.sigma_t == 0] = 0.5
@@ -174,7 +176,7 @@ def test_dsa_fixed_point_invariance():
     T = Transport(prob)
     ref = dense.solve_block_system(T)
     for mask in (prob.thick_mask(), np.ones(T.ne)):
-        r = T.source_iterate(dsa=DSA(T, mask), tol=1e-15, max_iters=3000)
+        r = T.source_iterate(dsa=DSA(T, mask, operator=operator), tol=1e-15, max_iters=3000)
         assert np.abs(r["phi"] - ref).max() < 1e-11 * np.abs(ref).max()
 
 
@@ -247,13 +249,16 @@ def test_dsa_operator_spd(prob_fn):
     np.linalg.cholesky(D)
 
 
-def test_dsa_operator_consistency_q2():
-    """u = x(1-x)y(1-y) in Q2: a(u,v) = (f,v) + 1/2 <D du/dn, v>_boundary exactly (SIP consistency
-    in the interior; the half-flux boundary term of the zero-exterior reading on the boundary)."""
+@pytest.mark.parametrize("operator", ["sip", "nip", "mnip"])
+def test_dsa_operator_consistency_q2(operator):
+    """u = x(1-x)y(1-y) in Q2: a(u,v) = (f,v) + 1/2 <D du/dn, v>_boundary exactly (consistency of
+    the interior-penalty forms in the interior; the half-flux boundary term of the zero-exterior
+    reading on the boundary).  u is continuous and zero on the boundary, so the penalty and the
+    symmetrising term vanish and the three operators of Sec. 4.1 share this identity."""
     n, st, ss = 4, 2.0, 1.5
     prob = inputs.uniform_problem(2, n, 2, 4, st, ss, 0.0)
     T = Transport(prob)
-    op = DSA(T, np.ones(T.ne))
+    op = DSA(T, np.ones(T.ne), operator=operator)
     Dc, sa = 1.0 / (3 * st), st - ss
     u = lambda x: x[..., 0] * (1 - x[..., 0]) * x[..., 1] * (1 - x[..., 1])
     f = lambda x: Dc * (2 * x[..., 1] * (1 - x[..., 1]) + 2 * x[..., 0] * (1 - x[..., 0])) + sa * u(x)

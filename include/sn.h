@@ -39,7 +39,7 @@ typedef enum {
     SN_ERR_CUDA = 2,                /* a CUDA call failed */
     SN_ERR_OOM = 3,                 /* device allocation failed */
     SN_ERR_CYCLE = 4,               /* an upwind graph has a cycle (no sweep order) */
-    SN_ERR_VOID_FULL_DSA = 5,       /* full DSA requested on a mesh with sigma_t = 0 */
+    SN_ERR_VOID_FULL_DSA = 5,       /* full DSA on a mesh with sigma_t = 0, or the mNIP penalty next to a void */
     SN_ERR_NOT_CONVERGED = 6,       /* max_iters reached; phi still holds the last iterate */
     SN_ERR_TIMEOUT = 7,             /* a bounded device wait gave up; outputs undefined */
     SN_ERR_INNER_NOT_CONVERGED = 8  /* a DSA solve hit inner_max_iters (only if strict) */
@@ -49,6 +49,7 @@ enum { SN_FP64 = 0, SN_FP32 = 1, SN_FP32_REFINE = 2 };          /* element-solve
 enum { SN_DSA_NONE = 0, SN_DSA_FULL = 1, SN_DSA_THICK = 2, SN_DSA_TRIANGULAR = 3 };  /* DSA variant */
 enum { SN_THICK_SIGMA_S = 0, SN_THICK_SIGMA_T_H = 1, SN_THICK_MASK = 2 };
 enum { SN_DSA_SIGMA_S = 0, SN_DSA_SIGMA_T = 1 };
+enum { SN_DSA_OP_SIP = 0, SN_DSA_OP_NIP = 1, SN_DSA_OP_MNIP = 2 };  /* DSA operator (Sec. 4.1) */
 enum { SN_OUTER_SI = 0, SN_OUTER_FGMRES = 1 };                  /* outer iteration */
 enum { SN_CACHE_OFF = 0, SN_CACHE_ON = 1, SN_CACHE_AUTO = 2 };  /* operator cache */
 
@@ -159,7 +160,7 @@ typedef struct {
     const unsigned char* mask; /* host, n_elem, used with SN_THICK_MASK */
     int dsa_sigma;           /* SN_DSA_SIGMA_S (default) | SN_DSA_SIGMA_T: mass matrix of the DSA rhs */
     double tol;              /* relative residual ||r^i|| / ||r^0|| (Euclidean, nodal) */
-    double inner_tol;        /* PCG relative residual of each DSA solve */
+    double inner_tol;        /* relative residual of each DSA solve (PCG, or BiCGStab for NIP / mNIP) */
     int max_iters, inner_max_iters;
     int precision;           /* SN_FP64 | SN_FP32 | SN_FP32_REFINE */
     int checkpoint_every;    /* >0: copy phi^{k} to checkpoints after every k-th iteration */
@@ -168,12 +169,14 @@ typedef struct {
     int warm_start;          /* 1: start from phi_inout, 0: from phi = 0 */
     int outer;               /* SN_OUTER_SI (fixed point, Eq. DSA_fp) | SN_OUTER_FGMRES (Sec. 5) */
     int restart;             /* fGMRES restart length (1..60; the paper uses 30) */
+    int dsa_operator;        /* SN_DSA_OP_SIP (default) | SN_DSA_OP_NIP (Eq. NIP) | SN_DSA_OP_MNIP (Eq. NIP with
+                                the penalty of Eq. ModifiedF0); see sn_source_iterate */
 } sn_iter_opts;
 
 typedef struct {
     int iters;               /* outer iterations performed */
     double rel_residual;     /* last ||r^i|| / ||r^0|| */
-    int inner_iters_total;   /* PCG iterations summed over all DSA solves */
+    int inner_iters_total;   /* inner Krylov iterations summed over all DSA solves */
     double thick_fraction;   /* thick elements / all elements */
     double* residual_history; /* host, history_len entries, or NULL */
     int history_len;
@@ -203,6 +206,19 @@ void sn_iter_opts_default(sn_iter_opts* opts);
  * [0; corrected thick part] whose result is added on the thin DOFs only (one extra sweep per outer
  * iteration).  It uses the same thick rule; it is not available for the adjoint or for batches
  * (SN_ERR_ARG).
+ * opts->dsa_operator picks D_ff (Sec. 4.1; D = 1/(3 sigma_t), sigma_a = sigma_t - sigma_s, all
+ * integrals on the (p+1)-point Gauss rule; a face to a non-thick element or the boundary is a face
+ * to a zero exterior state, as in a principal submatrix):
+ *   SN_DSA_OP_SIP: symmetric interior penalty with kappa = max(1/4, 2 p(p+1) {D/h}), h = |K|/|F|;
+ *     SPD, solved by conjugate gradients.
+ *   SN_DSA_OP_NIP: Eq. NIP, the SIP form without the symmetrising face term -<{D dv/dn},[u]> and
+ *     with the penalty of F_0, kappa = 1/4; nonsymmetric, solved by BiCGStab right-preconditioned
+ *     with the same V-cycle (the adjoint builds D_ff^T and its own hierarchy).
+ *   SN_DSA_OP_MNIP: Eq. NIP with the penalty of Eq. ModifiedF0,
+ *     kappa = [max(0.1 p(p+1)/(sigma_t^- h^-), 1) + max(0.1 p(p+1)/(sigma_t^+ h^+), 1)] / 8 with
+ *     the neighbour's data even when it is thin (the element's own on the domain boundary);
+ *     SN_ERR_VOID_FULL_DSA if a thick element has a void neighbour.
+ * Batches take SN_DSA_OP_SIP only (SN_ERR_ARG).
  * SN_ERR_VOID_FULL_DSA if dsa = FULL and some sigma_t = 0; SN_ERR_NOT_CONVERGED after
  * max_iters (phi_inout still written).  stats may be NULL.
  */

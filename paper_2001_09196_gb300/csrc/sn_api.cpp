@@ -70,6 +70,7 @@ void free_mesh(sn_mesh* m) {
                     (void*)m->levels.ctrl, (void*)m->d_krylov, (void*)m->levels.d_level_ptr, (void*)m->levels.d_barrier})
         if (p) cudaFree(p);
     sn::dsa_free(m->dsa);
+    sn::dsa_free(m->dsa_t);
     delete m;
 }
 
@@ -105,6 +106,7 @@ void sn_iter_opts_default(sn_iter_opts* o) {
     o->precision = SN_FP64;
     o->outer = SN_OUTER_SI;
     o->restart = 30;
+    o->dsa_operator = SN_DSA_OP_SIP;
 }
 
 sn_status sn_mesh_create(const sn_mesh_desc* desc, sn_mesh** out) {
@@ -249,7 +251,8 @@ sn_status sn_set_materials(sn_mesh* m, const double* st, const double* ss, const
     CK(cudaMemcpyAsync(m->d_q, hq.data(), m->ne * sizeof(double), cudaMemcpyHostToDevice, s), "copy");
     CK(cudaStreamSynchronize(s), "sync");
     sn::dsa_free(m->dsa);
-    m->dsa = nullptr;
+    sn::dsa_free(m->dsa_t);
+    m->dsa = m->dsa_t = nullptr;
     m->dsa_key_dsa = -1;
     m->ainv_valid = m->ainv32_valid = false;  // the cached inverses depend on sigma_t
     return SN_OK;
@@ -366,20 +369,39 @@ static sn_status ensure_dsa(sn_mesh* m, const sn_iter_opts* o) {
     std::vector<unsigned char> mask;
     sn_status st = thick_mask_for(m, o, mask);
     if (st != SN_OK) return st;
-    if (m->dsa && m->dsa_key_mask == mask && m->dsa_key_sigma == o->dsa_sigma) return SN_OK;
+    if (m->dsa && m->dsa_key_mask == mask && m->dsa_key_sigma == o->dsa_sigma && m->dsa_key_op == o->dsa_operator)
+        return SN_OK;
     sn::dsa_free(m->dsa);
-    m->dsa = nullptr;
+    sn::dsa_free(m->dsa_t);
+    m->dsa = m->dsa_t = nullptr;
     std::string err;
-    m->dsa = sn::dsa_build(m, mask.data(), o->dsa_sigma, err);
-    if (!m->dsa) return fail(SN_ERR_ARG, "DSA setup: %s", err.c_str());
+    bool void_conflict = false;
+    m->dsa = sn::dsa_build(m, mask.data(), o->dsa_sigma, o->dsa_operator, false, err, &void_conflict);
+    if (!m->dsa) return fail(void_conflict ? SN_ERR_VOID_FULL_DSA : SN_ERR_ARG, "DSA setup: %s", err.c_str());
     m->dsa_key_mask = mask;
     m->dsa_key_sigma = o->dsa_sigma;
+    m->dsa_key_op = o->dsa_operator;
     return SN_OK;
 }
+
+// The adjoint iteration's DSA step solves with D_ff^T: for a nonsymmetric operator (Eq. NIP) a
+// second hierarchy built from the transposed blocks, kept beside the forward one.
+static sn_status ensure_dsa_adjoint(sn_mesh* m, const sn_iter_opts* o) {
+    sn_status st = ensure_dsa(m, o);
+    if (st != SN_OK || !m->dsa || m->dsa->symmetric || m->dsa_t) return st;
+    std::string err;
+    m->dsa_t = sn::dsa_build(m, m->dsa_key_mask.data(), o->dsa_sigma, o->dsa_operator, true, err);
+    if (!m->dsa_t) return fail(SN_ERR_ARG, "DSA setup (transposed): %s", err.c_str());
+    return SN_OK;
+}
+
+// Hierarchy of the DSA step: D_ff, or D_ff^T in the adjoint iteration.
+static sn::DsaHierarchy* dsa_for(sn_mesh* m, bool adjoint) { return adjoint && m->dsa_t ? m->dsa_t : m->dsa; }
 
 static sn_status check_opts(const sn_iter_opts* o) {
     if (!o) return fail(SN_ERR_ARG, "null opts");
     if (o->dsa < SN_DSA_NONE || o->dsa > SN_DSA_TRIANGULAR) return fail(SN_ERR_ARG, "bad dsa");
+    if (o->dsa_operator < SN_DSA_OP_SIP || o->dsa_operator > SN_DSA_OP_MNIP) return fail(SN_ERR_ARG, "bad dsa_operator");
     if (o->precision < SN_FP64 || o->precision > SN_FP32_REFINE) return fail(SN_ERR_ARG, "bad precision");
     if (!(o->tol >= 0) || o->max_iters < 1) return fail(SN_ERR_ARG, "bad tol / max_iters");
     if (o->dsa != SN_DSA_NONE && (!(o->inner_tol > 0) || o->inner_max_iters < 1))
@@ -457,7 +479,7 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
             double* Zj = Z + (size_t)j * M;
             CK(sn::launch_copy(Zj, Vj, M, s), "copy");
             if (o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0) {
-                CK(sn::dsa_correct(m->dsa, Vj, Zj, o->inner_tol, o->inner_max_iters, adjoint, s), "DSA");
+                CK(sn::dsa_correct(dsa_for(m, adjoint), Vj, Zj, o->inner_tol, o->inner_max_iters, adjoint, s), "DSA");
                 if (o->dsa == SN_DSA_TRIANGULAR) {
                     // Algorithm 1, step 2: the zero-source transport update of [0; Z_f], kept on the
                     // thin DOFs (Z_f = V_f + D_ff^{-1} Sigma_f V_f after step 1)
@@ -525,7 +547,7 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
         // the restart (or the final check) recomputes the true residual with one more sweep
     }
     CK(cudaStreamSynchronize(s), "sync");
-    if (m->dsa) CK(sn::dsa_take_iters(m->dsa, s, &inner_total), "DSA iterations");
+    if (m->dsa) CK(sn::dsa_take_iters(dsa_for(m, adjoint), s, &inner_total), "DSA iterations");
     if (stats) {
         stats->iters = it;
         stats->rel_residual = rel;
@@ -646,10 +668,10 @@ sn_status sn_adjoint_iterate(sn_mesh* m, const sn_iter_opts* o, const double* g,
     if (st != SN_OK) return st;
     if (o->dsa == SN_DSA_TRIANGULAR) return fail(SN_ERR_ARG, "the adjoint iteration has no triangular DSA");
     if ((st = ensure_lambda(m)) != SN_OK) return st;
-    if (o->dsa != SN_DSA_NONE && (st = ensure_dsa(m, o)) != SN_OK) return st;
-    if (m->dsa) {  // the PCG iteration counter starts from zero for this solve
+    if (o->dsa != SN_DSA_NONE && (st = ensure_dsa_adjoint(m, o)) != SN_OK) return st;
+    if (m->dsa) {  // the inner iteration counter starts from zero for this solve
         int stale = 0;
-        CK(sn::dsa_take_iters(m->dsa, (cudaStream_t)stream, &stale), "DSA iterations");
+        CK(sn::dsa_take_iters(dsa_for(m, true), (cudaStream_t)stream, &stale), "DSA iterations");
     }
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
@@ -682,7 +704,7 @@ sn_status sn_adjoint_iterate(sn_mesh* m, const sn_iter_opts* o, const double* g,
         if (stats && stats->residual_history && it < stats->history_len) stats->residual_history[it] = rel;
         CK(sn::launch_copy(mu, half, M, s), "copy");
         if (o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0) {
-            CK(sn::dsa_correct(m->dsa, r, mu, o->inner_tol, o->inner_max_iters, true, s), "DSA");
+            CK(sn::dsa_correct(dsa_for(m, true), r, mu, o->inner_tol, o->inner_max_iters, true, s), "DSA");
         }
         ++it;
         if (rel <= o->tol) {
@@ -691,7 +713,7 @@ sn_status sn_adjoint_iterate(sn_mesh* m, const sn_iter_opts* o, const double* g,
         }
     }
     CK(cudaStreamSynchronize(s), "sync");
-    if (m->dsa) CK(sn::dsa_take_iters(m->dsa, s, &inner_total), "DSA iterations");
+    if (m->dsa) CK(sn::dsa_take_iters(dsa_for(m, true), s, &inner_total), "DSA iterations");
     if (stats) {
         stats->iters = it;
         stats->rel_residual = rel;
@@ -880,6 +902,7 @@ sn_status sn_batch_sweep(sn_batch* b, const double* const* phi_in, double* const
 
 static sn_status batch_ensure_dsa(sn_batch* b, const sn_iter_opts* o) {
     if (o->dsa == SN_DSA_TRIANGULAR) return fail(SN_ERR_ARG, "batches use the diagonal (Algorithm 2) DSA only");
+    if (o->dsa_operator != SN_DSA_OP_SIP) return fail(SN_ERR_ARG, "batches use the symmetric (SIP) DSA operator only");
     std::vector<std::vector<unsigned char>> masks(b->count);
     for (int i = 0; i < b->count; ++i) {
         sn_iter_opts oi = *o;
@@ -893,7 +916,7 @@ static sn_status batch_ensure_dsa(sn_batch* b, const sn_iter_opts* o) {
     std::vector<sn::DsaHierarchy*> parts;
     std::string err;
     for (int i = 0; i < b->count; ++i) {
-        sn::DsaHierarchy* H = sn::dsa_build(b->meshes[i], masks[i].data(), o->dsa_sigma, err);
+        sn::DsaHierarchy* H = sn::dsa_build(b->meshes[i], masks[i].data(), o->dsa_sigma, SN_DSA_OP_SIP, false, err);
         if (!H) {
             for (sn::DsaHierarchy* P : parts) sn::dsa_free(P);
             return fail(SN_ERR_ARG, "DSA setup of instance %d: %s", i, err.c_str());

@@ -1,5 +1,6 @@
 // Thick-subdomain DSA on the device (paper Sec. 2.2 Eq. DSA_fp, Algorithm 2, Sec. 4):
-// conjugate gradients on D_ff preconditioned by one symmetric multigrid V-cycle
+// conjugate gradients on the symmetric operator (Eq. SIP), BiCGStab on the nonsymmetric ones
+// (Eq. NIP, with or without Eq. ModifiedF0), both preconditioned by one multigrid V-cycle
 // (block-Jacobi on the DG level, weighted Jacobi on the continuous levels, dense coarsest).
 // All vectors and reductions are float64; dot products reduce in a fixed order.
 #include <cuda_runtime.h>
@@ -194,6 +195,55 @@ __global__ void pcg_check_kernel(const double* s, int* it, double tol, int max_i
     cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
+// BiCGStab (right-preconditioned with the V-cycle M) scalars in s: [0] rho of the previous
+// iteration, [1] alpha, [2] omega, [3] b.b, [4] rho = rhat.r, [5] rhat.v, [6] t.s, [7] t.t, [8] r.r.
+__global__ void bicg_start_kernel(double* s, int* it, cudaGraphConditionalHandle h) {
+    s[0] = s[1] = s[2] = 1.0;
+    it[0] = 0;
+    cudaGraphSetConditional(h, s[3] > 0.0 ? 1u : 0u);
+}
+
+// p = r + beta (p - omega v), beta = (rho / rho_prev) (alpha / omega)
+__global__ void bicg_update_p(double* p, const double* r, const double* v, long long n, const double* s) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double beta = (s[4] / s[0]) * (s[1] / s[2]);
+    p[i] = r[i] + beta * (p[i] - s[2] * v[i]);
+}
+
+// alpha = rho / rhat.v; x += alpha M p; r <- s = r - alpha v
+__global__ void bicg_update_xs(double* x, double* r, const double* ph, const double* v, long long n, const double* s) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double alpha = s[5] != 0.0 ? s[4] / s[5] : 0.0;
+    x[i] += alpha * ph[i];
+    r[i] -= alpha * v[i];
+}
+
+// omega = t.s / t.t; x += omega M s; r = s - omega t
+__global__ void bicg_update_xr(double* x, double* r, const double* sh, const double* t, long long n, const double* s) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double omega = s[7] > 0.0 ? s[6] / s[7] : 0.0;
+    x[i] += omega * sh[i];
+    r[i] -= omega * t[i];
+}
+
+// End of one iteration: keep rho, alpha, omega for the next; continue while ||r|| > tol ||b||,
+// fewer than max_iters, and no breakdown (rho, alpha or omega zero, or a non-finite residual).
+__global__ void bicg_check_kernel(double* s, int* it, double tol, int max_iters, cudaGraphConditionalHandle h) {
+    const double alpha = s[5] != 0.0 ? s[4] / s[5] : 0.0;
+    const double omega = s[7] > 0.0 ? s[6] / s[7] : 0.0;
+    s[0] = s[4];
+    s[1] = alpha;
+    s[2] = omega;
+    const int k = ++it[0];
+    ++it[1];
+    const bool ok = s[4] != 0.0 && alpha != 0.0 && omega != 0.0 && isfinite(s[8]);
+    const bool more = ok && sqrt(s[8]) > tol * sqrt(s[3]) && k < max_iters;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 constexpr int kDotBlocks = 304;  // 2 x 152 SMs
 
 template <typename T>
@@ -233,6 +283,9 @@ cudaError_t upload(DsaHierarchy* H) {
 #undef UP
     for (double** v : {&H->d_x, &H->d_b, &H->d_r, &H->d_z, &H->d_p, &H->d_q, &H->d_vr, &H->d_vx})
         if ((err = cudaMalloc(v, std::max<long long>(1, N0) * sizeof(double))) != cudaSuccess) return err;
+    if (!H->symmetric)
+        for (double** v : {&H->d_rh, &H->d_sh, &H->d_t})
+            if ((err = cudaMalloc(v, std::max<long long>(1, N0) * sizeof(double))) != cudaSuccess) return err;
     if ((err = cudaMalloc(&H->d_part, kDotBlocks * sizeof(double))) != cudaSuccess) return err;
     if ((err = cudaMalloc(&H->d_s, 16 * sizeof(double))) != cudaSuccess) return err;
     {
@@ -328,13 +381,19 @@ void vcycle0(DsaHierarchy* H, const double* r, double* z, cudaStream_t s) {
     }
 }
 
-// Records PCG on D_ff x = b (thick-local vectors H->d_b -> H->d_x) into a CUDA graph: a prologue
-// (x = 0, p = 0, r = b, b.b, start) and a WHILE conditional node whose body is one iteration
-//   z = V(r); rz = r.z; p = z + (rz / rz_prev) p; q = A p; alpha = rz / p.q;
-//   x += alpha p; r -= alpha q; continue while ||r|| > tol ||b|| and k < max_iters.
-// This is the preconditioned CG of the eager form step for step; the convergence test runs on
-// the device, so a solve is one graph launch.
-cudaError_t record_pcg(DsaHierarchy* H, double tol, int max_iters) {
+// Records the Krylov solve of D_ff x = b (thick-local vectors H->d_b -> H->d_x) into a CUDA graph:
+// a prologue and a WHILE conditional node whose body is one iteration; the convergence test runs
+// on the device, so a solve is one graph launch.
+//   PCG (symmetric operator), the preconditioned CG of the eager form step for step:
+//     prologue x = 0, p = 0, r = b, b.b;  body z = M r; rz = r.z; p = z + (rz / rz_prev) p; q = A p;
+//     alpha = rz / p.q; x += alpha p; r -= alpha q.
+//   BiCGStab (nonsymmetric operators), right-preconditioned by the same V-cycle M:
+//     prologue x = 0, r = rhat = b, p = v = 0, b.b;  body rho = rhat.r;
+//     p = r + (rho / rho_prev)(alpha / omega)(p - omega v); ph = M p; v = A ph; alpha = rho / rhat.v;
+//     x += alpha ph; s = r - alpha v; sh = M s; t = A sh; omega = t.s / t.t; x += omega sh;
+//     r = s - omega t.
+// Both continue while ||r|| > tol ||b|| and k < max_iters.
+cudaError_t record_krylov(DsaHierarchy* H, double tol, int max_iters) {
     const long long N0 = (long long)H->nt * H->n;
     const Level0& A = H->l0;
     cudaError_t err;
@@ -367,9 +426,14 @@ cudaError_t record_pcg(DsaHierarchy* H, double tol, int max_iters) {
     cudaMemsetAsync(H->d_x, 0, N0 * sizeof(double), H->cap);
     cudaMemsetAsync(H->d_p, 0, N0 * sizeof(double), H->cap);
     cudaMemcpyAsync(H->d_r, H->d_b, N0 * sizeof(double), cudaMemcpyDeviceToDevice, H->cap);
+    if (!H->symmetric) {
+        cudaMemsetAsync(H->d_q, 0, N0 * sizeof(double), H->cap);
+        cudaMemcpyAsync(H->d_rh, H->d_b, N0 * sizeof(double), cudaMemcpyDeviceToDevice, H->cap);
+    }
     dot(H, H->d_b, H->d_b, N0, 3, H->cap);
     SN_COUNT_LAUNCH();
-    pcg_start_kernel<<<1, 1, 0, H->cap>>>(H->d_s, H->d_it, h);
+    if (H->symmetric) pcg_start_kernel<<<1, 1, 0, H->cap>>>(H->d_s, H->d_it, h);
+    else bicg_start_kernel<<<1, 1, 0, H->cap>>>(H->d_s, H->d_it, h);
     H->pro_launches = g_launches.load() - count0;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
@@ -390,20 +454,44 @@ cudaError_t record_pcg(DsaHierarchy* H, double tol, int max_iters) {
     body_open = true;
     const long long count1 = g_launches.load();
     cudaStream_t s = H->cap2;
-    vcycle0(H, H->d_r, H->d_z, s);
-    dot(H, H->d_r, H->d_z, N0, 4, s);
-    SN_COUNT_LAUNCH();
-    cg_update_p<<<nblk(N0), kBS, 0, s>>>(H->d_p, H->d_z, N0, H->d_s);
-    SN_COUNT_LAUNCH();
-    copy_scalar<<<1, 1, 0, s>>>(H->d_s, 0, 4);
-    SN_COUNT_LAUNCH();
-    bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, H->nt, H->n, H->d_p, nullptr, H->d_q);
-    dot(H, H->d_p, H->d_q, N0, 1, s);
-    SN_COUNT_LAUNCH();
-    cg_update_xr<<<nblk(N0), kBS, 0, s>>>(H->d_x, H->d_r, H->d_p, H->d_q, N0, H->d_s);
-    dot(H, H->d_r, H->d_r, N0, 2, s);
-    SN_COUNT_LAUNCH();
-    pcg_check_kernel<<<1, 1, 0, s>>>(H->d_s, H->d_it, tol, max_iters, h);
+    if (H->symmetric) {
+        vcycle0(H, H->d_r, H->d_z, s);
+        dot(H, H->d_r, H->d_z, N0, 4, s);
+        SN_COUNT_LAUNCH();
+        cg_update_p<<<nblk(N0), kBS, 0, s>>>(H->d_p, H->d_z, N0, H->d_s);
+        SN_COUNT_LAUNCH();
+        copy_scalar<<<1, 1, 0, s>>>(H->d_s, 0, 4);
+        SN_COUNT_LAUNCH();
+        bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, H->nt, H->n, H->d_p, nullptr, H->d_q);
+        dot(H, H->d_p, H->d_q, N0, 1, s);
+        SN_COUNT_LAUNCH();
+        cg_update_xr<<<nblk(N0), kBS, 0, s>>>(H->d_x, H->d_r, H->d_p, H->d_q, N0, H->d_s);
+        dot(H, H->d_r, H->d_r, N0, 2, s);
+        SN_COUNT_LAUNCH();
+        pcg_check_kernel<<<1, 1, 0, s>>>(H->d_s, H->d_it, tol, max_iters, h);
+    } else {
+        // vectors: p = d_p, ph = d_z, v = d_q, r (holding s after the first half) = d_r,
+        // sh = d_sh, t = d_t, rhat = d_rh
+        dot(H, H->d_rh, H->d_r, N0, 4, s);
+        SN_COUNT_LAUNCH();
+        bicg_update_p<<<nblk(N0), kBS, 0, s>>>(H->d_p, H->d_r, H->d_q, N0, H->d_s);
+        vcycle0(H, H->d_p, H->d_z, s);
+        SN_COUNT_LAUNCH();
+        bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, H->nt, H->n, H->d_z, nullptr, H->d_q);
+        dot(H, H->d_rh, H->d_q, N0, 5, s);
+        SN_COUNT_LAUNCH();
+        bicg_update_xs<<<nblk(N0), kBS, 0, s>>>(H->d_x, H->d_r, H->d_z, H->d_q, N0, H->d_s);
+        vcycle0(H, H->d_r, H->d_sh, s);
+        SN_COUNT_LAUNCH();
+        bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, H->nt, H->n, H->d_sh, nullptr, H->d_t);
+        dot(H, H->d_t, H->d_r, N0, 6, s);
+        dot(H, H->d_t, H->d_t, N0, 7, s);
+        SN_COUNT_LAUNCH();
+        bicg_update_xr<<<nblk(N0), kBS, 0, s>>>(H->d_x, H->d_r, H->d_sh, H->d_t, N0, H->d_s);
+        dot(H, H->d_r, H->d_r, N0, 8, s);
+        SN_COUNT_LAUNCH();
+        bicg_check_kernel<<<1, 1, 0, s>>>(H->d_s, H->d_it, tol, max_iters, h);
+    }
     H->body_launches = g_launches.load() - count1;
     g_launches.store(count0);  // recorded, not run: launches are counted when the graph runs
     if ((err = cudaGetLastError()) != cudaSuccess) return finish(err);
@@ -419,12 +507,12 @@ cudaError_t record_pcg(DsaHierarchy* H, double tol, int max_iters) {
     return err;
 }
 
-// Solves D_ff x = b by one launch of the recorded PCG; the iteration count stays on the device
-// (dsa_take_iters reads the running total).
+// Solves D_ff x = b by one launch of the recorded Krylov solve; the iteration count stays on the
+// device (dsa_take_iters reads the running total).
 cudaError_t pcg(DsaHierarchy* H, double tol, int max_iters, cudaStream_t s) {
     cudaError_t err;
     if (!H->pcg_graph || H->pcg_tol != tol || H->pcg_max != max_iters)
-        if ((err = record_pcg(H, tol, max_iters)) != cudaSuccess) return err;
+        if ((err = record_krylov(H, tol, max_iters)) != cudaSuccess) return err;
     g_launches.fetch_add(H->pro_launches, std::memory_order_relaxed);
     return cudaGraphLaunch(H->pcg_graph, s);
 }
@@ -441,6 +529,7 @@ void dsa_free(DsaHierarchy* H) {
         f(L.d_r_ptr); f(L.d_r_col); f(L.d_r_val); f(L.d_dinv); f(L.d_dense); f(L.d_x); f(L.d_b); f(L.d_r);
     }
     f(H->d_x); f(H->d_b); f(H->d_r); f(H->d_z); f(H->d_p); f(H->d_q); f(H->d_vr); f(H->d_vx);
+    f(H->d_rh); f(H->d_sh); f(H->d_t);
     f(H->d_part); f(H->d_s); f(H->d_it); f(H->d_emask);
     if (H->pcg_graph) cudaGraphExecDestroy(H->pcg_graph);
     if (H->cap) cudaStreamDestroy(H->cap);
@@ -480,7 +569,7 @@ cudaError_t dsa_solve(DsaHierarchy* H, const double* b_full, double* x_full, dou
 }
 
 // Forward (Algorithm 2): phi_out[thick] += D_ff^{-1} (Sigma r)_f.
-// Transposed: phi_out[thick] += Sigma_f D_ff^{-1} r_f.
+// Transposed: phi_out[thick] += Sigma_f H^{-1} r_f, H = D_ff^T (D_ff itself when symmetric).
 cudaError_t dsa_correct(DsaHierarchy* H, const double* r, double* phi_out, double tol, int max_iters, bool transpose,
                         cudaStream_t s) {
     cudaError_t err = upload(H);
@@ -496,7 +585,7 @@ cudaError_t dsa_correct(DsaHierarchy* H, const double* r, double* phi_out, doubl
     return cudaGetLastError();
 }
 
-// PCG iterations run since the last call (synchronises the stream); 0 before the first solve.
+// Krylov iterations run since the last call (synchronises the stream); 0 before the first solve.
 cudaError_t dsa_take_iters(DsaHierarchy* H, cudaStream_t s, int* iters) {
     *iters = 0;
     if (!H || !H->uploaded) return cudaSuccess;

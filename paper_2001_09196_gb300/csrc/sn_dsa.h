@@ -29,6 +29,9 @@ struct LevelC {                  // a continuous level: operator, prolongation t
 
 struct DsaHierarchy {
     int n = 0, ne = 0, nt = 0;
+    int op = 0;                           // SN_DSA_OP_SIP | SN_DSA_OP_NIP | SN_DSA_OP_MNIP
+    bool symmetric = true;                // SIP: conjugate gradients; NIP / mNIP: BiCGStab
+    bool transposed = false;              // holds D_ff^T
     std::vector<int> thick;               // thick element ids
     std::vector<double> h_mass_sig;       // nt x n: sigma_Sigma * collocated mass
     Level0 l0;
@@ -38,13 +41,15 @@ struct DsaHierarchy {
     // PCG vectors on the thick DOFs (nt x n)
     double *d_x = nullptr, *d_b = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr;
     double *d_vr = nullptr, *d_vx = nullptr;  // V-cycle level-0 residual / correction
+    double *d_rh = nullptr, *d_sh = nullptr, *d_t = nullptr;  // BiCGStab: shadow residual, M s, A M s
     double* d_part = nullptr;                 // reduction partials
     double* d_s = nullptr;                    // device scalars
     bool uploaded = false;
     double omega0 = 0.6, omega = 0.6;         // damping of block-Jacobi (level 0) / Jacobi (levels >= 1)
     int nu = 2;                               // pre- and post-smoothing steps
-    // PCG recorded as a CUDA graph whose WHILE conditional node repeats one iteration until the
-    // device-side convergence test fails (no host synchronisation per iteration)
+    // The Krylov solve (PCG or BiCGStab) recorded as a CUDA graph whose WHILE conditional node
+    // repeats one iteration until the device-side convergence test fails (no host
+    // synchronisation per iteration)
     cudaGraphExec_t pcg_graph = nullptr;
     double pcg_tol = -1.0;
     int pcg_max = -1;

@@ -1,14 +1,24 @@
 // Host-side setup of the thick-subdomain DSA operator and its multigrid hierarchy.
 //
-// Operator (paper Sec. 4.1, Eq. SIP with the max-floored penalty of Eq. ModifiedF0; Sec. 4.2,
-// the heterogeneous operator is the principal submatrix on the thick elements):
+// Operators (paper Sec. 4.1; Sec. 4.2: the heterogeneous operator is the principal submatrix on
+// the thick elements):
 //   a(u,v) = sum_K (D grad u, grad v)_K + (sigma_a u, v)_K
-//          + sum_{interior thick-thick F} <kappa [u],[v]> - <{D grad u.n},[v]> - <{D grad v.n},[u]>
-//          + sum_{F on the thick region's boundary} <kappa u,v> - 1/2<D grad u.n, v> - 1/2<D grad v.n, u>
-// D = 1/(3 sigma_t), sigma_a = sigma_t - sigma_s, kappa = max(1/4, c(p) (D-/h- + D+/h+)/2) on interior
-// faces and max(1/4, c(p) D/h) on boundary faces, c(p) = 2 p (p+1), h = |K|/|F|.  A face to a
-// non-thick neighbour is a face to a zero exterior state.  All integrals use the (p+1)-point
-// Gauss rule per axis, on which the nodal basis lives (so the volume terms are collocated).
+//          + sum_{interior thick-thick F} <kappa [u],[v]> - <{D grad u.n},[v]> - s <{D grad v.n},[u]>
+//          + sum_{F on the thick region's boundary} <kappa u,v> - 1/2<D grad u.n, v> - s/2 <D grad v.n, u>
+// D = 1/(3 sigma_t), sigma_a = sigma_t - sigma_s, h = |K|/|F|.  A face to a non-thick neighbour is a
+// face to a zero exterior state.
+//   SIP (Eq. SIP with a max-floored penalty): s = 1, kappa = max(1/4, c(p) (D-/h- + D+/h+)/2) on
+//     interior faces and max(1/4, c(p) D/h) on boundary faces, c(p) = 2 p (p+1).
+//   NIP (Eq. NIP): s = 0 (the symmetrising term G^T Sigma_t^{-1} F_1 dropped), kappa = 1/4 (F_0).
+//   mNIP (Eq. NIP with Eq. ModifiedF0): s = 0, kappa = (max(c(p)/(sigma_t- h-), 1) + max(c(p)/(sigma_t+ h+),
+//     1)) / 8, c(p) = 0.1 p (p+1): each side is upwind for the directions leaving it, and either half of
+//     the angular integral of |Omega.n| / (8 pi) is 1/8.  The neighbour's data enter even when it is
+//     thin; on the domain boundary the element's own value stands for the missing side; a void
+//     neighbour makes the penalty infinite and is an error.
+// All integrals use the (p+1)-point Gauss rule per axis, on which the nodal basis lives (so the
+// volume terms are collocated).  For the adjoint of a nonsymmetric operator the assembled blocks
+// are transposed before the hierarchy is built (the Galerkin hierarchy of A^T is the transpose of
+// that of A).
 //
 // Multigrid (replaces the paper's BoomerAMG, Sec. 5): level 0 is the DG space on the thick
 // elements with element block-Jacobi smoothing; level 1 is continuous Q1 on the vertices of
@@ -219,11 +229,17 @@ void parallel_for(int n, F&& f) {
     for (auto& t : th) t.join();
 }
 
-DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sigma, std::string& err) {
+DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sigma, int dsa_op, bool transposed,
+                        std::string& err, bool* void_conflict) {
+    if (void_conflict) *void_conflict = false;
     auto* H = new DsaHierarchy();
     const int dim = m->dim, p = m->p, n = m->n, Q = p + 1, nf = 2 * dim;
     H->n = n;
     H->ne = m->ne;
+    H->op = dsa_op;
+    H->symmetric = dsa_op == SN_DSA_OP_SIP;
+    H->transposed = transposed && !H->symmetric;
+    const double sym = H->symmetric ? 1.0 : 0.0;  // weight of the symmetrising face term
     for (int e = 0; e < m->ne; ++e)
         if (mask[e]) H->thick.push_back(e);
     const int nt = (int)H->thick.size();
@@ -238,7 +254,8 @@ DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sig
     std::vector<int> local(m->ne, -1);
     for (int t = 0; t < nt; ++t) local[H->thick[t]] = t;
     const GL1D g = gauss_legendre_nodal(p);
-    const double cp = 2.0 * p * (p + 1);
+    const double cp = 2.0 * p * (p + 1);   // SIP penalty constant
+    const double cm = 0.1 * p * (p + 1);   // c(p) of Eq. ModifiedF0
 
     auto elem_map = [&](int e) {
         ElemMap em;
@@ -272,6 +289,17 @@ DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sig
         else { k += dl; if (k < 0 || k >= m->nz) return -1; }
         return i + m->nx * (j + m->ny * k);
     };
+    if (dsa_op == SN_DSA_OP_MNIP)
+        for (int e : H->thick)
+            for (int f = 0; f < nf; ++f) {
+                const int u = neighbor(e, f);
+                if (u >= 0 && !(m->h_sigma_t[u] > 0.0)) {
+                    err = "the mNIP penalty (Eq. ModifiedF0) is undefined next to a void element";
+                    if (void_conflict) *void_conflict = true;
+                    delete H;
+                    return nullptr;
+                }
+            }
 
     // reference basis data, the same for every element: values and reference gradients at the
     // volume nodes and at the face quadrature points of every face
@@ -390,6 +418,20 @@ DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sig
         vol[t] = V;
     });
 
+    // volume of any element (the mNIP penalty reads thin neighbours too)
+    auto elem_volume = [&](int e) {
+        const ElemMap em = elem_map(e);
+        double V = 0.0;
+        for (int q = 0; q < n; ++q) {
+            const int qi[3] = {q % Q, (q / Q) % Q, q / (Q * Q)};
+            double xi[3] = {0, 0, 0}, x[3], J[3][3], Ji[3][3];
+            for (int a = 0; a < dim; ++a) xi[a] = g.x[qi[a]];
+            em.eval(xi, x, J);
+            V += vW[q] * det_inv(dim, J, Ji);
+        }
+        return V;
+    };
+
     // face terms.  An interior thick-thick face is assembled once, from its side-1 element, into
     // the rows of both elements; a face to a non-thick element or the boundary into its own row.
     // Pass (axis, parity) takes the elements whose coordinate along the axis has that parity, so
@@ -461,20 +503,31 @@ DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sig
                     face_geometry(em, f, F);
                     face_traces(em, f, F.nrm, Be, Dne);
                     const double h = vol[t] / F.area;
+                    // Eq. ModifiedF0 factor of one side: max(c(p) / (sigma_t h), 1)
+                    auto mod = [&](double st, double hh) { return std::max(cm / (st * hh), 1.0); };
                     if (o < 0) {
-                        const double kap = std::max(0.25, cp * Dc[t] / h);
+                        double kap = 0.25;
+                        if (dsa_op == SN_DSA_OP_SIP) {
+                            kap = std::max(0.25, cp * Dc[t] / h);
+                        } else if (dsa_op == SN_DSA_OP_MNIP) {
+                            const double own = mod(m->h_sigma_t[e], h);
+                            const double other = u >= 0 ? mod(m->h_sigma_t[u], elem_volume(u) / F.area) : own;
+                            kap = 0.125 * (own + other);
+                        }
                         double* K = block(t, t);
                         for (int qf = 0; qf < QF; ++qf)
                             for (int i = 0; i < n; ++i)
                                 for (int j = 0; j < n; ++j)
                                     K[i * n + j] += F.dS[qf] * (kap * Be[qf * n + i] * Be[qf * n + j] -
                                                                 0.5 * Dc[t] * Dne[qf * n + j] * Be[qf * n + i] -
-                                                                0.5 * Dc[t] * Dne[qf * n + i] * Be[qf * n + j]);
+                                                                sym * 0.5 * Dc[t] * Dne[qf * n + i] * Be[qf * n + j]);
                         continue;
                     }
                     face_traces(elem_map(u), f ^ 1, F.nrm, Bo, Dno);
                     const double ho = vol[o] / F.area;
-                    const double kap = std::max(0.25, cp * 0.5 * (Dc[t] / h + Dc[o] / ho));
+                    double kap = 0.25;
+                    if (dsa_op == SN_DSA_OP_SIP) kap = std::max(0.25, cp * 0.5 * (Dc[t] / h + Dc[o] / ho));
+                    else if (dsa_op == SN_DSA_OP_MNIP) kap = 0.125 * (mod(m->h_sigma_t[e], h) + mod(m->h_sigma_t[u], ho));
                     struct Side { int r; const std::vector<double>* B; const std::vector<double>* Dn; double D, sg; };
                     const Side sides[2] = {{t, &Be, &Dne, Dc[t], 1.0}, {o, &Bo, &Dno, Dc[o], -1.0}};
                     for (const Side& A : sides)
@@ -485,10 +538,23 @@ DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sig
                                     for (int j = 0; j < n; ++j)
                                         K[i * n + j] += F.dS[qf] * (kap * A.sg * Bs.sg * (*A.B)[qf * n + i] * (*Bs.B)[qf * n + j] -
                                                                     0.5 * Bs.D * A.sg * (*Bs.Dn)[qf * n + j] * (*A.B)[qf * n + i] -
-                                                                    0.5 * A.D * Bs.sg * (*A.Dn)[qf * n + i] * (*Bs.B)[qf * n + j]);
+                                                                    sym * 0.5 * A.D * Bs.sg * (*A.Dn)[qf * n + i] * (*Bs.B)[qf * n + j]);
                         }
                 }
             });
+
+    if (H->transposed) {  // block (r, c) of D^T is block (c, r) of D, transposed
+        std::vector<double> tv(L0.val.size());
+        parallel_for(nt, [&](int r) {
+            for (int k = L0.ptr[r]; k < L0.ptr[r + 1]; ++k) {
+                const double* src = block(L0.col[k], r);
+                double* dst = &tv[(size_t)k * n * n];
+                for (int i = 0; i < n; ++i)
+                    for (int j = 0; j < n; ++j) dst[i * n + j] = src[j * n + i];
+            }
+        });
+        L0.val.swap(tv);
+    }
 
     // inverse diagonal blocks (block-Jacobi smoother)
     L0.dinv.resize((size_t)nt * n * n);

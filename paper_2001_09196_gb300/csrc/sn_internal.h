@@ -176,9 +176,10 @@ struct sn_mesh {
                                           // three forward kinds without the fixed source
     cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
     sn::DsaHierarchy* dsa = nullptr;
+    sn::DsaHierarchy* dsa_t = nullptr;  // D_ff^T for the adjoint of a nonsymmetric operator (built on demand)
     double* d_krylov = nullptr;     // flexible GMRES workspace (basis, preconditioned basis, scratch)
     int krylov_restart = 0;
-    int dsa_key_dsa = -1, dsa_key_rule = -1, dsa_key_sigma = -1;
+    int dsa_key_dsa = -1, dsa_key_rule = -1, dsa_key_sigma = -1, dsa_key_op = -1;
     double dsa_key_eta = 0;
     std::vector<unsigned char> dsa_key_mask;
 };
@@ -309,17 +310,22 @@ cudaError_t launch_multiaxpy(const double* V, int k, long long n, const double* 
                              cudaStream_t s);
 cudaError_t launch_normalize(const double* x, long long n, double* partial, double* s, double* y, cudaStream_t st);
 // sn_dsa.cu
-DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sigma, std::string& err);
+// Assembles D_ff (dsa_op: SN_DSA_OP_SIP / NIP / MNIP; transposed: D_ff^T, for the adjoint of a
+// nonsymmetric operator) and its multigrid hierarchy.  Returns null with err set; *void_conflict
+// is set when the operator is undefined next to a void element (mNIP, Eq. ModifiedF0).
+DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sigma, int dsa_op, bool transposed,
+                        std::string& err, bool* void_conflict = nullptr);
 void dsa_free(DsaHierarchy* h);
 int dsa_thick_count(const DsaHierarchy* h);
 // y = D_ff x (scatter into [elem][node], zeros elsewhere)
 cudaError_t dsa_apply(DsaHierarchy* h, const double* x, double* y, cudaStream_t s);
-// phi_out = phi_half + E_f D_ff^{-1} Sigma_f r (transpose = false); PCG iterations accumulate on the device.
+// phi_out += E_f D_ff^{-1} Sigma_f r (transpose = false) or E_f Sigma_f H^{-1} r (transpose = true, with H
+// the hierarchy of D_ff^T for a nonsymmetric operator); inner iterations accumulate on the device.
 cudaError_t dsa_correct(DsaHierarchy* h, const double* r, double* phi_out, double tol, int max_iters,
                         bool transpose, cudaStream_t s);
 cudaError_t dsa_solve(DsaHierarchy* h, const double* b_full, double* x_full, double tol, int max_iters,
                       cudaStream_t s);
-// PCG iterations run since the last call (synchronises the stream)
+// inner Krylov iterations run since the last call (synchronises the stream)
 cudaError_t dsa_take_iters(DsaHierarchy* h, cudaStream_t s, int* iters);
 // Algorithm 1 on full [elem][node] vectors: out = x on thick elements, 0 elsewhere;
 // phi += (w - r) on thick elements and y elsewhere; z += y on thin elements

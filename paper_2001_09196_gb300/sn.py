@@ -18,6 +18,8 @@ FP64, FP32, FP32_REFINE = 0, 1, 2
 DSA_NONE, DSA_FULL, DSA_THICK, DSA_TRIANGULAR = 0, 1, 2, 3
 THICK_SIGMA_S, THICK_SIGMA_T_H, THICK_MASK = 0, 1, 2
 DSA_SIGMA_S, DSA_SIGMA_T = 0, 1
+DSA_OP_SIP, DSA_OP_NIP, DSA_OP_MNIP = 0, 1, 2
+_DSA_OP = {"sip": DSA_OP_SIP, "nip": DSA_OP_NIP, "mnip": DSA_OP_MNIP}
 _PREC = {"fp64": FP64, "fp32": FP32, "fp32_refine": FP32_REFINE}
 _DSA = {"none": DSA_NONE, "full": DSA_FULL, "thick": DSA_THICK, "triangular": DSA_TRIANGULAR}
 _RULE = {"sigma_s": THICK_SIGMA_S, "sigma_t_h": THICK_SIGMA_T_H, "mask": THICK_MASK}
@@ -48,7 +50,8 @@ class IterOpts(C.Structure):
                 ("mask", C.POINTER(C.c_ubyte)), ("dsa_sigma", C.c_int), ("tol", C.c_double),
                 ("inner_tol", C.c_double), ("max_iters", C.c_int), ("inner_max_iters", C.c_int),
                 ("precision", C.c_int), ("checkpoint_every", C.c_int), ("checkpoints", C.c_void_p),
-                ("max_checkpoints", C.c_int), ("warm_start", C.c_int), ("outer", C.c_int), ("restart", C.c_int)]
+                ("max_checkpoints", C.c_int), ("warm_start", C.c_int), ("outer", C.c_int), ("restart", C.c_int),
+                ("dsa_operator", C.c_int)]
 
 
 class IterStats(C.Structure):
@@ -137,7 +140,10 @@ def _stream(stream):
 
 def make_opts(dsa="thick", thick_rule="sigma_s", eta=1.0, mask=None, dsa_sigma="sigma_s", tol=1e-8,
               inner_tol=1e-4, max_iters=1000, inner_max_iters=200, precision="fp64", checkpoint_every=0,
-              checkpoints=None, warm_start=False, outer="si", restart=30):
+              checkpoints=None, warm_start=False, outer="si", restart=30, operator="sip"):
+    """Options of sn_source_iterate / sn_adjoint_iterate.  operator: the DSA operator D_ff,
+    "sip" (symmetric, conjugate gradients), "nip" (Eq. NIP) or "mnip" (Eq. NIP with the penalty
+    of Eq. ModifiedF0); the nonsymmetric two are solved by BiCGStab."""
     o = IterOpts()
     _lib.sn_iter_opts_default(C.byref(o))
     o.dsa = _DSA[dsa] if isinstance(dsa, str) else int(dsa)
@@ -160,6 +166,7 @@ def make_opts(dsa="thick", thick_rule="sigma_s", eta=1.0, mask=None, dsa_sigma="
     o.warm_start = int(bool(warm_start))
     o.outer = {"si": 0, "fgmres": 1}[outer] if isinstance(outer, str) else int(outer)
     o.restart = int(restart)
+    o.dsa_operator = _DSA_OP[operator] if isinstance(operator, str) else int(operator)
     o._keep = keep
     return o
 

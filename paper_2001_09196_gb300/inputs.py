@@ -228,6 +228,55 @@ def config5(n: int = 128, seed: int = MASTER_SEED + 4) -> Problem:
     return prob
 
 
+# Materials of the hohlraum problem (Sec. 5.2, Table hohlraum_materials): opacity sigma and heat
+# capacity C_v of gold wall, helium fill, capsule CH layer, hydrogen fuel; NIF units.
+HOHLRAUM_SIGMA = (1.0e3, 1.0e-3, 1.0e2, 1.0)
+HOHLRAUM_CV = (1.0e5, 1.0e-2, 1.0e3, 1.0)
+HOHLRAUM_A_RAD = 137.199      # radiation constant a
+HOHLRAUM_C_LIGHT = 2.9979e4   # speed of light c
+HOHLRAUM_DT = 1.0e-3          # the paper's single long time step (microseconds)
+HOHLRAUM_T_COLD, HOHLRAUM_T_HOT = 1.0e-3, 0.4  # keV: initial temperature; laser-heated gold
+
+
+def hohlraum_like(n: int = 256, p: int = 2, sn: int = 8, jitter: float = 0.15,
+                  seed: int = MASTER_SEED + 6) -> Problem:
+    """A synthetic 2D hohlraum-like layout (the paper's curvilinear hohlraum mesh is not available).
+
+    Materials by undeformed cell centre (x, y) in [0, 1]^2; left to right through the capsule:
+    gold wall, helium, CH, hydrogen, CH, helium, gold wall (Fig. hohlraum_mesh's order).
+      gold: a frame of width 1/16, open (helium) on the top and bottom walls where |x - 1/2| < 1/8
+        (laser entrance holes);
+      capsule centred at (1/2, 1/2): hydrogen for r < 0.15, CH for 0.15 <= r < 0.18, with a helium
+        fill tube through the CH on the right (x > 1/2, |y - 1/2| < 0.01);
+      helium everywhere else.
+    Temperature T = 0.4 keV on the laser spots (gold of the left and right walls with
+    1/8 <= y < 3/8 or 5/8 <= y < 7/8), 1e-3 keV elsewhere; time step 1e-3.
+    The returned Problem carries the plain absorber (sigma_t = sigma, sigma_s = 0, q = 0); the
+    pseudo-scattering coefficients of Eq. hohlraum_sigma / Eq. hohlraum_q are computed from
+    extra = {material, sigma, cv, T, dt, a_rad, c_light} by the consumer.
+    """
+    xc, yc = _centroids_uniform(n, n)
+    w = 1.0 / 16.0
+    mat = np.full(n * n, 1, dtype=np.int64)                       # helium
+    frame = (xc < w) | (xc >= 1 - w) | (yc < w) | (yc >= 1 - w)
+    leh = ((yc < w) | (yc >= 1 - w)) & (np.abs(xc - 0.5) < 0.125)
+    mat[frame & ~leh] = 0                                          # gold
+    r = np.hypot(xc - 0.5, yc - 0.5)
+    mat[r < 0.15] = 3                                              # hydrogen
+    ch = (r >= 0.15) & (r < 0.18)
+    tube = (xc > 0.5) & (np.abs(yc - 0.5) < 0.01)
+    mat[ch & ~tube] = 2                                            # CH
+    spot = (mat == 0) & ((xc < w) | (xc >= 1 - w)) & (_in(yc, 0.125, 0.375) | _in(yc, 0.625, 0.875))
+    T = np.where(spot, HOHLRAUM_T_HOT, HOHLRAUM_T_COLD)
+    sigma = np.choose(mat, HOHLRAUM_SIGMA).astype(np.float64)
+    cv = np.choose(mat, HOHLRAUM_CV).astype(np.float64)
+    V = jittered_vertices(n, n, jitter, seed) if jitter > 0 else None
+    return Problem(f"hohlraum_like_{n}x{n}_q{p}_s{sn}", 2, n, n, 1, p, sn, sigma.copy(), np.zeros(n * n),
+                   np.zeros(n * n), vertices=V,
+                   extra={"material": mat, "sigma": sigma, "cv": cv, "T": T, "dt": HOHLRAUM_DT,
+                          "a_rad": HOHLRAUM_A_RAD, "c_light": HOHLRAUM_C_LIGHT})
+
+
 def uniform_problem(dim, n, p, sn, sigma_t, sigma_s, q, psi_inc=0.0, name="uniform") -> Problem:
     ne = n ** dim
     return Problem(name, dim, n, n, n if dim == 3 else 1, p, sn,

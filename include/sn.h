@@ -144,6 +144,26 @@ sn_status sn_set_materials(sn_mesh* mesh, const double* sigma_t, const double* s
                            const double* q, int mem, void* stream);
 
 /*
+ * sn_set_pseudo_scattering: the materials of one implicit time step of gray thermal radiative
+ * transfer written as a steady transport problem (Sec. 5.2, Eq. hohlraum_sigma, Eq. hohlraum_q),
+ * computed per element on the device from the opacity sigma (= sigma_a), the heat capacity C_v
+ * and the temperature T:
+ *     b = 16 pi a c T^3,  sigma_t = sigma,  sigma_s = sigma^2 b / (C_v/dt + sigma b),
+ *     q = 4 pi q_ps,  q_ps = sigma a c T^4 - sigma^2 b a c T^4 / (C_v/dt + sigma b)
+ * (q_d = q_ps per direction; the library's q is total emission, q_d = q / (4 pi)).  q_ps is
+ * evaluated in the equal form sigma a c T^4 (C_v/dt) / (C_v/dt + sigma b), free of the
+ * cancellation of the printed difference.  sigma, cv, T: n_elem doubles each, host if mem = 0,
+ * device if mem = 1; dt, a_rad, c_light: the time step, the radiation constant and the speed of
+ * light (the paper: 1e-3, 137.199, 2.9979e4 in NIF units).  Then as sn_set_materials.
+ * SN_ERR_ARG unless sigma >= 0, C_v > 0, T >= 0 (finite) and dt, a_rad, c_light > 0.
+ */
+sn_status sn_set_pseudo_scattering(sn_mesh* mesh, const double* sigma, const double* cv, const double* T,
+                                   double dt, double a_rad, double c_light, int mem, void* stream);
+
+/* Current materials (host arrays of n_elem doubles; any may be NULL). */
+sn_status sn_get_materials(const sn_mesh* mesh, double* sigma_t, double* sigma_s, double* q);
+
+/*
  * sn_sweep: one transport update, Eq. (source0) / Eq. (phi):
  *     phi_out = sum_d w_d L_d^{-1} ( q/(4 pi) + sigma_s phi_in / (4 pi) ),
  * the element systems solved in the given precision (SN_FP64, SN_FP32 or SN_FP32_REFINE;

@@ -18,7 +18,8 @@ OUT_DIR = os.path.join(HERE, "lib")
 OBJ_DIR = os.path.join(HERE, "lib", "obj")
 LIB = os.path.join(OUT_DIR, "libsn.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["sn_setup.cpp", "sn_dsa_setup.cpp", "sn_api.cpp", "sn_sweep.cu", "sn_dsa.cu", "sn_noalloc.cu", "sn_krylov.cu", "sn_batch.cu", "sn_tiles.cpp"]
+SOURCES = ["sn_setup.cpp", "sn_dsa_setup.cpp", "sn_api.cpp", "sn_sweep.cu", "sn_dsa.cu", "sn_noalloc.cu", "sn_krylov.cu", "sn_batch.cu",
+           "sn_tiles.cpp", "sn_materials.cu"]
 
 
 def nvcc() -> str:

@@ -229,6 +229,9 @@ sn_status sn_mesh_quadrature(const sn_mesh* m, double* dirs, double* weights) {
     return SN_OK;
 }
 
+static sn_status commit_materials(sn_mesh* m, std::vector<double>& hst, std::vector<double>& hss,
+                                  std::vector<double>& hq, cudaStream_t s);
+
 sn_status sn_set_materials(sn_mesh* m, const double* st, const double* ss, const double* q, int mem, void* stream) {
     if (!m || !st || !ss || !q) return fail(SN_ERR_ARG, "null argument");
     if (mem != 0 && mem != 1) return fail(SN_ERR_ARG, "mem must be 0 (host) or 1 (device)");
@@ -239,6 +242,53 @@ sn_status sn_set_materials(sn_mesh* m, const double* st, const double* ss, const
     CK(cudaMemcpyAsync(hss.data(), ss, m->ne * sizeof(double), k, s), "copy");
     CK(cudaMemcpyAsync(hq.data(), q, m->ne * sizeof(double), k, s), "copy");
     CK(cudaStreamSynchronize(s), "sync");
+    return commit_materials(m, hst, hss, hq, s);
+}
+
+sn_status sn_set_pseudo_scattering(sn_mesh* m, const double* sigma, const double* cv, const double* T, double dt,
+                                   double a_rad, double c_light, int mem, void* stream) {
+    if (!m || !sigma || !cv || !T) return fail(SN_ERR_ARG, "null argument");
+    if (mem != 0 && mem != 1) return fail(SN_ERR_ARG, "mem must be 0 (host) or 1 (device)");
+    if (!(dt > 0) || !(a_rad > 0) || !(c_light > 0) || !std::isfinite(dt) || !std::isfinite(a_rad) ||
+        !std::isfinite(c_light))
+        return fail(SN_ERR_ARG, "dt, a_rad and c_light must be finite and > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ne = (size_t)m->ne;
+    // inputs and outputs in the work vector (4 n_elem n_nodes doubles >= 6 n_elem)
+    double* in = m->d_work;
+    double* out = m->d_work + 3 * ne;
+    std::vector<double> h(3 * ne);
+    const cudaMemcpyKind k = mem ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    CK(cudaMemcpyAsync(h.data(), sigma, ne * sizeof(double), k, s), "copy");
+    CK(cudaMemcpyAsync(h.data() + ne, cv, ne * sizeof(double), k, s), "copy");
+    CK(cudaMemcpyAsync(h.data() + 2 * ne, T, ne * sizeof(double), k, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    for (size_t e = 0; e < ne; ++e)
+        if (!(std::isfinite(h[e]) && h[e] >= 0.0 && std::isfinite(h[ne + e]) && h[ne + e] > 0.0 &&
+              std::isfinite(h[2 * ne + e]) && h[2 * ne + e] >= 0.0))
+            return fail(SN_ERR_ARG, "need finite sigma >= 0, C_v > 0, T >= 0 (element %zu)", e);
+    CK(cudaMemcpyAsync(in, h.data(), 3 * ne * sizeof(double), cudaMemcpyHostToDevice, s), "copy");
+    CK(sn::launch_pseudo_scattering(in, in + ne, in + 2 * ne, m->ne, dt, a_rad, c_light, out, out + ne, out + 2 * ne, s),
+       "pseudo-scattering kernel");
+    std::vector<double> hst(ne), hss(ne), hq(ne);
+    CK(cudaMemcpyAsync(hst.data(), out, ne * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaMemcpyAsync(hss.data(), out + ne, ne * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaMemcpyAsync(hq.data(), out + 2 * ne, ne * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    return commit_materials(m, hst, hss, hq, s);
+}
+
+sn_status sn_get_materials(const sn_mesh* m, double* st, double* ss, double* q) {
+    if (!m) return fail(SN_ERR_ARG, "null mesh");
+    if (st) std::memcpy(st, m->h_sigma_t.data(), m->ne * sizeof(double));
+    if (ss) std::memcpy(ss, m->h_sigma_s.data(), m->ne * sizeof(double));
+    if (q) std::memcpy(q, m->h_q.data(), m->ne * sizeof(double));
+    return SN_OK;
+}
+
+// Validates host copies of the materials and makes them the mesh's (invalidating what depends on them).
+static sn_status commit_materials(sn_mesh* m, std::vector<double>& hst, std::vector<double>& hss,
+                                  std::vector<double>& hq, cudaStream_t s) {
     if (!finite_nonneg(hst) || !finite_nonneg(hss) || !finite_nonneg(hq))
         return fail(SN_ERR_ARG, "materials must be finite and >= 0");
     for (int e = 0; e < m->ne; ++e)

@@ -301,6 +301,10 @@ cudaError_t launch_copy(double* dst, const double* src, size_t n, cudaStream_t s
 // Reads and clears the dataflow error word (synchronises the stream).
 cudaError_t take_sweep_error(sn_mesh* m, cudaStream_t s, bool* timed_out);
 cudaError_t launch_axpy_add(double* y, const double* x, size_t n, cudaStream_t s);  // y += x
+// sn_materials.cu: per-element sigma_t, sigma_s, q of the pseudo-scattering time step
+cudaError_t launch_pseudo_scattering(const double* sigma, const double* cv, const double* T, int ne, double dt,
+                                     double a_rad, double c_light, double* sigma_t, double* sigma_s, double* q,
+                                     cudaStream_t s);
 cudaError_t launch_widen(double* y, const float* x, size_t n, cudaStream_t s);
 // sn_krylov.cu
 int krylov_blocks(long long n);

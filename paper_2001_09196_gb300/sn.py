@@ -72,6 +72,8 @@ def _load():
         "sn_mesh_get_info": [vp, C.POINTER(MeshInfo)],
         "sn_mesh_quadrature": [vp, vp, vp],
         "sn_set_materials": [vp, vp, vp, vp, i, vp],
+        "sn_set_pseudo_scattering": [vp, vp, vp, vp, d, d, d, i, vp],
+        "sn_get_materials": [vp, vp, vp, vp],
         "sn_sweep": [vp, vp, vp, i, vp],
         "sn_source_iterate": [vp, C.POINTER(IterOpts), vp, C.POINTER(IterStats), vp],
         "sn_adjoint_sweep": [vp, vp, vp, i, vp],
@@ -266,6 +268,29 @@ class Mesh:
             if a.size != self.n_elem:
                 raise ValueError("material arrays need one value per element")
         _check(_lib.sn_set_materials(self._h, *[a.ctypes.data_as(C.c_void_p) for a in arrs], 0, _stream(stream)))
+
+    def set_pseudo_scattering(self, sigma, cv, T, dt, a_rad=137.199, c_light=2.9979e4, stream=None):
+        """Materials of one pseudo-scattering time step (Sec. 5.2, Eq. hohlraum_sigma / hohlraum_q),
+        formed on the device from per-element opacity, heat capacity and temperature; the default
+        constants are the paper's NIF-unit a and c."""
+        import torch
+        if isinstance(sigma, torch.Tensor) and sigma.is_cuda:
+            args = [_ptr(x.contiguous()) for x in (sigma, cv, T)]
+            _check(_lib.sn_set_pseudo_scattering(self._h, *args, float(dt), float(a_rad), float(c_light), 1,
+                                                 _stream(stream)))
+            return
+        arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (sigma, cv, T)]
+        for a in arrs:
+            if a.size != self.n_elem:
+                raise ValueError("material arrays need one value per element")
+        _check(_lib.sn_set_pseudo_scattering(self._h, *[a.ctypes.data_as(C.c_void_p) for a in arrs], float(dt),
+                                             float(a_rad), float(c_light), 0, _stream(stream)))
+
+    def materials(self):
+        """(sigma_t, sigma_s, q) as the mesh holds them (host copies)."""
+        out = [np.empty(self.n_elem) for _ in range(3)]
+        _check(_lib.sn_get_materials(self._h, *[a.ctypes.data_as(C.c_void_p) for a in out]))
+        return tuple(out)
 
     def sweep(self, phi_in, phi_out=None, precision="fp64", stream=None):
         import torch

@@ -173,6 +173,20 @@ sn_status sn_get_materials(const sn_mesh* mesh, double* sigma_t, double* sigma_s
  */
 sn_status sn_sweep(sn_mesh* mesh, const double* phi_in, double* phi_out, int precision, void* stream);
 
+/*
+ * sn_sweep_directions: the part of the transport update that directions d_begin <= d < d_end
+ * contribute, phi_out = sum_{d in range} w_d L_d^{-1}( q/(4 pi) + sigma_s phi_in/(4 pi) ).
+ * Directions are independent within one update (Eq. psi), so the partial updates of a partition
+ * of the directions sum to sn_sweep's phi_out (up to the order of the float64 additions): the
+ * decomposition behind sharding the sweep by direction, where each process sweeps its range and
+ * one sum-reduction of phi_out completes the update.  psi_d of the range is stored as sn_sweep
+ * stores it (bitwise the same values); the other directions' psi_d are left as they were.  Runs as
+ * a chain of level launches whatever the mesh's schedule.  Errors: SN_ERR_ARG for a range outside
+ * [0, n_dirs), an empty range, a bad precision or aliasing buffers.
+ */
+sn_status sn_sweep_directions(sn_mesh* mesh, const double* phi_in, double* phi_out, int d_begin, int d_end,
+                              int precision, void* stream);
+
 typedef struct {
     int dsa;                 /* SN_DSA_NONE | SN_DSA_FULL | SN_DSA_THICK (Algorithm 2) | SN_DSA_TRIANGULAR (Algorithm 1) */
     int thick_rule;          /* SN_THICK_SIGMA_S (sigma_s >= eta, Sec. 4.2) | SN_THICK_SIGMA_T_H | SN_THICK_MASK */

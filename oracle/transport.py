@@ -194,13 +194,14 @@ class Transport:
         return psi
 
     # ----- full transport update ---------------------------------------------------------
-    def sweep_modal(self, phi_modal, src_per_dir=None, psi_inc=None, keep_psi=False):
-        """phi_half = sum_d w_d L_d^{-1}(q_d + Sigma_s phi) in modal coefficients (Eq. phi)."""
+    def sweep_modal(self, phi_modal, src_per_dir=None, psi_inc=None, keep_psi=False, directions=None):
+        """phi_half = sum_d w_d L_d^{-1}(q_d + Sigma_s phi) in modal coefficients (Eq. phi); with
+        `directions` the sum runs over those directions only (a partial transport update)."""
         out = np.zeros((self.ne, self.n))
         psis = [] if keep_psi else None
         scatter = (self.sigma_s[:, None] * phi_modal) / FOUR_PI
         iso = self.isotropic_source(np.zeros_like(phi_modal))
-        for d in range(self.nd):
+        for d in (range(self.nd) if directions is None else directions):
             # src_per_dir (modal, per direction) replaces the isotropic q/(4 pi) when given
             src = scatter + (iso if src_per_dir is None else src_per_dir[d])
             psi = self.sweep_direction(d, src, psi_inc)
@@ -209,9 +210,10 @@ class Transport:
                 psis.append(psi)
         return (out, psis) if keep_psi else out
 
-    def sweep(self, phi_nodal):
-        """One transport update on GL-nodal data [elem][node] (Eq. source0)."""
-        return self.to_nodal(self.sweep_modal(self.to_modal(phi_nodal)))
+    def sweep(self, phi_nodal, directions=None):
+        """One transport update on GL-nodal data [elem][node] (Eq. source0), or its partial sum over
+        `directions`."""
+        return self.to_nodal(self.sweep_modal(self.to_modal(phi_nodal), directions=directions))
 
     # ----- source iteration -------------------------------------------------------------
     def source_iterate(self, dsa=None, tol=1e-8, max_iters=1000, phi0_nodal=None,

@@ -67,7 +67,8 @@ void free_mesh(sn_mesh* m) {
     for (void* p : {(void*)m->d_dirs, (void*)m->d_wts, (void*)m->d_corners, (void*)m->d_sigma_t, (void*)m->d_sigma_s,
                     (void*)m->d_q, m->d_psi, m->d_psi32, (void*)m->d_lambda, (void*)m->d_mass, (void*)m->d_work, (void*)m->d_red,
                     (void*)m->d_scalars, (void*)m->levels.items, (void*)m->levels.padded, (void*)m->levels.padded_rev, (void*)m->levels.done,
-                    (void*)m->levels.ctrl, (void*)m->d_krylov, (void*)m->levels.d_level_ptr, (void*)m->levels.d_barrier})
+                    (void*)m->levels.ctrl, (void*)m->d_krylov, (void*)m->levels.d_level_ptr, (void*)m->levels.d_barrier,
+                    (void*)m->range_items})
         if (p) cudaFree(p);
     sn::dsa_free(m->dsa);
     sn::dsa_free(m->dsa_t);
@@ -338,6 +339,23 @@ sn_status sn_sweep(sn_mesh* m, const double* phi_in, double* phi_out, int precis
         CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
         if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out");
     }
+    return SN_OK;
+}
+
+sn_status sn_sweep_directions(sn_mesh* m, const double* phi_in, double* phi_out, int d_begin, int d_end, int precision,
+                              void* stream) {
+    if (!m || !phi_out) return fail(SN_ERR_ARG, "null argument");
+    if (precision < SN_FP64 || precision > SN_FP32_REFINE) return fail(SN_ERR_ARG, "bad precision");
+    if (phi_in == phi_out) return fail(SN_ERR_ARG, "phi_in and phi_out must not alias");
+    if (d_begin < 0 || d_end > m->nd || d_begin >= d_end)
+        return fail(SN_ERR_ARG, "direction range [%d, %d) not inside [0, %d)", d_begin, d_end, m->nd);
+    if (precision == SN_FP32) {
+        sn_status st = ensure_psi32(m);
+        if (st != SN_OK) return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(sn::launch_sweep_range(m, phi_in, precision, d_begin, d_end, s), "sweep");
+    CK(sn::launch_phi_reduce(m, precision, nullptr, phi_out, nullptr, s, d_begin, d_end), "phi reduce");
     return SN_OK;
 }
 

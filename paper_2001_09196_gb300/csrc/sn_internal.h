@@ -176,6 +176,9 @@ struct sn_mesh {
                                           // three forward kinds without the fixed source
     cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
     sn::DsaHierarchy* dsa = nullptr;
+    int2* range_items = nullptr;        // level work list of the direction range of sn_sweep_directions
+    std::vector<long long> range_ptr;
+    int range_d0 = -1, range_d1 = -1;
     sn::DsaHierarchy* dsa_t = nullptr;  // D_ff^T for the adjoint of a nonsymmetric operator (built on demand)
     double* d_krylov = nullptr;     // flexible GMRES workspace (basis, preconditioned basis, scratch)
     int krylov_restart = 0;
@@ -291,8 +294,11 @@ cudaError_t prepare_operator_cache(sn_mesh* m, int precision, cudaStream_t s);
 void free_operator_cache(sn_mesh* m);
 cudaError_t batch_refresh_cache(sn_batch* b, int precision, cudaStream_t s);
 cudaError_t launch_adjoint_sweep(sn_mesh* m, const double* mu, cudaStream_t s);
+// phi_out = sum_{d0 <= d < d1} w_d psi_d (d1 < 0: every direction), optional ||phi_out - phi_in||^2
 cudaError_t launch_phi_reduce(sn_mesh* m, int precision, const double* phi_in, double* phi_out, double* d_rr,
-                              cudaStream_t s);
+                              cudaStream_t s, int d0 = 0, int d1 = -1);
+// forward sweep of directions d0 <= d < d1 only (level chain on the stream, any schedule)
+cudaError_t launch_sweep_range(sn_mesh* m, const double* phi_in, int precision, int d0, int d1, cudaStream_t s);
 cudaError_t launch_adjoint_reduce(sn_mesh* m, double* out, cudaStream_t s);
 cudaError_t launch_gradients(sn_mesh* m, const double* phi, double* gt, double* gs, double* gq, cudaStream_t s);
 cudaError_t launch_axpy_norm(sn_mesh* m, const double* a, const double* b, double* out, double* d_rr,

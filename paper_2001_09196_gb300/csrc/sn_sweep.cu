@@ -1219,15 +1219,17 @@ __global__ void kahn_level_kernel(SweepArgs a, int* indeg, int2* list, int* leve
 }
 
 // ---------------------------------------------------------------- reductions
+// phi_out = sum over directions d0 <= d < d1 of w_d psi_d (in increasing d), and partial sums of
+// ||phi_out - phi_in||^2 per block.
 template <typename RS>
-__global__ void phi_reduce_kernel(const RS* psi, const double* w, int nd, size_t M, const double* phi_in,
+__global__ void phi_reduce_kernel(const RS* psi, const double* w, int d0, int d1, size_t M, const double* phi_in,
                                   double* phi_out, double* partial) {
     __shared__ double sh[256];
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     double rr = 0.0;
     if (idx < M) {
         double s = 0.0;
-        for (int d = 0; d < nd; ++d) s += w[d] * (double)psi[(size_t)d * M + idx];
+        for (int d = d0; d < d1; ++d) s += w[d] * (double)psi[(size_t)d * M + idx];
         const double r = s - (phi_in ? phi_in[idx] : 0.0);
         phi_out[idx] = s;
         rr = r * r;
@@ -1489,32 +1491,37 @@ void free_level_groups(sn_mesh* m) {
 // Directions are independent, so the level schedule may run G groups of directions as G chains
 // of level launches: a chain's levels are those of its own directions, and the deepest direction
 // no longer makes every other direction wait at each of its levels.
+// Appends the items (d, e) of directions d0 <= d < d1 to `items`, grouped by level (level sets of
+// the mesh, directions then elements ascending inside a level); returns the level boundaries.
+static std::vector<long long> append_level_list(const sn_mesh* m, int d0, int d1, std::vector<int2>& items) {
+    const int ne = m->ne;
+    const std::vector<int>& lev = m->levels.h_level;
+    int depth = 0;
+    for (int d = d0; d < d1; ++d)
+        for (int e = 0; e < ne; ++e) depth = std::max(depth, lev[(size_t)d * ne + e] + 1);
+    std::vector<long long> cnt(depth + 1, 0);
+    for (int d = d0; d < d1; ++d)
+        for (int e = 0; e < ne; ++e) cnt[lev[(size_t)d * ne + e] + 1]++;
+    for (int l = 0; l < depth; ++l) cnt[l + 1] += cnt[l];
+    const long long base = (long long)items.size();
+    items.resize(base + cnt[depth]);
+    std::vector<long long> fill(cnt.begin(), cnt.end() - 1);
+    for (int d = d0; d < d1; ++d)
+        for (int e = 0; e < ne; ++e) items[base + fill[lev[(size_t)d * ne + e]]++] = make_int2(d, e);
+    for (long long& c : cnt) c += base;
+    return cnt;
+}
+
 cudaError_t build_level_groups(sn_mesh* m, int G) {
     free_level_groups(m);
     LevelSets& L = m->levels;
     const int nd = m->nd, ne = m->ne;
     G = std::max(1, std::min(G, nd));
-    const std::vector<int>& lev = L.h_level;
     std::vector<int2> items;
     items.reserve((size_t)nd * ne);
     L.gptr.assign(G, {});
-    for (int g = 0; g < G; ++g) {
-        const int d0 = (int)((long long)g * nd / G), d1 = (int)((long long)(g + 1) * nd / G);
-        int depth = 0;
-        for (int d = d0; d < d1; ++d)
-            for (int e = 0; e < ne; ++e) depth = std::max(depth, lev[(size_t)d * ne + e] + 1);
-        std::vector<long long> cnt(depth + 1, 0);
-        for (int d = d0; d < d1; ++d)
-            for (int e = 0; e < ne; ++e) cnt[lev[(size_t)d * ne + e] + 1]++;
-        for (int l = 0; l < depth; ++l) cnt[l + 1] += cnt[l];
-        const long long base = (long long)items.size();
-        items.resize(base + cnt[depth]);
-        std::vector<long long> fill(cnt.begin(), cnt.end() - 1);
-        for (int d = d0; d < d1; ++d)
-            for (int e = 0; e < ne; ++e) items[base + fill[lev[(size_t)d * ne + e]]++] = make_int2(d, e);
-        for (long long& c : cnt) c += base;
-        L.gptr[g] = cnt;
-    }
+    for (int g = 0; g < G; ++g)
+        L.gptr[g] = append_level_list(m, (int)((long long)g * nd / G), (int)((long long)(g + 1) * nd / G), items);
     cudaError_t err;
     if ((err = cudaMalloc(&L.gitems, items.size() * sizeof(int2))) != cudaSuccess) {
         L.gitems = nullptr;
@@ -1888,6 +1895,39 @@ cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double
     return launch_levels_graph(m, q_scale == 0.0 ? precision + 4 : precision, s);
 }
 
+// Forward sweep of the directions d0 <= d < d1 only: the level work list of that range (built once
+// per range and kept) launched as one chain of level kernels on the stream.  The element solves
+// are those of the full sweep, so psi_d of these directions is bitwise the full sweep's.
+cudaError_t launch_sweep_range(sn_mesh* m, const double* phi_in, int precision, int d0, int d1, cudaStream_t s) {
+    cudaError_t err = prepare_operator_cache(m, precision, s);
+    if (err != cudaSuccess) return err;
+    if (!m->range_items || m->range_d0 != d0 || m->range_d1 != d1) {
+        if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;  // a previous list may be in use
+        if (m->range_items) cudaFree(m->range_items);
+        m->range_items = nullptr;
+        std::vector<int2> items;
+        m->range_ptr = append_level_list(m, d0, d1, items);
+        if ((err = cudaMalloc(&m->range_items, std::max<size_t>(1, items.size()) * sizeof(int2))) != cudaSuccess) {
+            m->range_items = nullptr;
+            return err;
+        }
+        if ((err = cudaMemcpy(m->range_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return err;
+        m->range_d0 = d0;
+        m->range_d1 = d1;
+    }
+    SweepArgs a = make_args(m);
+    a.phi = phi_in;
+    a.q_scale = 1.0;
+    a.psi = precision == SN_FP32 ? m->d_psi32 : m->d_psi;
+    a.items = m->range_items;
+    long long launches = 0;
+    for (size_t l = 0; l + 1 < m->range_ptr.size(); ++l) launches += m->range_ptr[l + 1] > m->range_ptr[l];
+    g_launches.fetch_add(launches, std::memory_order_relaxed);
+    return enqueue_chain(m, precision, a, m->range_ptr, s);
+}
+
 cudaError_t launch_adjoint_sweep(sn_mesh* m, const double* mu, cudaStream_t s) {
     cudaError_t cerr = prepare_operator_cache(m, SN_FP64, s);
     if (cerr != cudaSuccess) return cerr;
@@ -2251,15 +2291,16 @@ cudaError_t batch_launch_dataflow(sn_batch* b, int precision, cudaStream_t s) {
 }
 
 cudaError_t launch_phi_reduce(sn_mesh* m, int precision, const double* phi_in, double* phi_out, double* d_rr,
-                              cudaStream_t s) {
+                              cudaStream_t s, int d0, int d1) {
     const size_t M = (size_t)m->ne * m->n;
     const unsigned g = (unsigned)((M + 255) / 256);
+    if (d1 < 0) d1 = m->nd;
     SN_COUNT_LAUNCH();
     if (precision == SN_FP32)
-        phi_reduce_kernel<float><<<g, 256, 0, s>>>(static_cast<const float*>(m->d_psi32), m->d_wts, m->nd, M, phi_in,
+        phi_reduce_kernel<float><<<g, 256, 0, s>>>(static_cast<const float*>(m->d_psi32), m->d_wts, d0, d1, M, phi_in,
                                                    phi_out, d_rr ? m->d_red : nullptr);
     else
-        phi_reduce_kernel<double><<<g, 256, 0, s>>>(static_cast<const double*>(m->d_psi), m->d_wts, m->nd, M, phi_in,
+        phi_reduce_kernel<double><<<g, 256, 0, s>>>(static_cast<const double*>(m->d_psi), m->d_wts, d0, d1, M, phi_in,
                                                     phi_out, d_rr ? m->d_red : nullptr);
     if (d_rr) { SN_COUNT_LAUNCH(); final_sum_kernel<<<1, 1024, 0, s>>>(m->d_red, (int)g, d_rr); }
     return cudaGetLastError();

@@ -75,6 +75,7 @@ def _load():
         "sn_set_pseudo_scattering": [vp, vp, vp, vp, d, d, d, i, vp],
         "sn_get_materials": [vp, vp, vp, vp],
         "sn_sweep": [vp, vp, vp, i, vp],
+        "sn_sweep_directions": [vp, vp, vp, i, i, i, vp],
         "sn_source_iterate": [vp, C.POINTER(IterOpts), vp, C.POINTER(IterStats), vp],
         "sn_adjoint_sweep": [vp, vp, vp, i, vp],
         "sn_adjoint_iterate": [vp, C.POINTER(IterOpts), vp, vp, C.POINTER(IterStats), vp],
@@ -268,6 +269,15 @@ class Mesh:
             if a.size != self.n_elem:
                 raise ValueError("material arrays need one value per element")
         _check(_lib.sn_set_materials(self._h, *[a.ctypes.data_as(C.c_void_p) for a in arrs], 0, _stream(stream)))
+
+    def sweep_directions(self, phi_in, d_begin, d_end, phi_out=None, precision="fp64", stream=None):
+        """The contribution of directions d_begin <= d < d_end to one transport update."""
+        import torch
+        if phi_out is None:
+            phi_out = torch.empty(self.shape, dtype=torch.float64, device=phi_in.device if phi_in is not None else "cuda")
+        _check(_lib.sn_sweep_directions(self._h, _ptr(phi_in), _ptr(phi_out), int(d_begin), int(d_end),
+                                        _PREC.get(precision, precision), _stream(stream)))
+        return phi_out
 
     def set_pseudo_scattering(self, sigma, cv, T, dt, a_rad=137.199, c_light=2.9979e4, stream=None):
         """Materials of one pseudo-scattering time step (Sec. 5.2, Eq. hohlraum_sigma / hohlraum_q),

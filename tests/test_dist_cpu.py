@@ -1,8 +1,10 @@
-"""Multi-process (N > 1) paths of the benchmark on CPU ranks with the gloo backend.
+"""Multi-process (N > 1) paths on CPU ranks with the gloo backend.
 
-Every call of this build runs on one GPU, so the N > 1 launcher logic is covered here: the
-max-over-ranks timing and barrier used by `bench.py`, and the reference arm launched the way the
-driver launches it (torch.distributed.run, two ranks), where rank 0 alone prints the JSON line.
+Every call of this build runs on one GPU, so the N > 1 logic is covered here: the max-over-ranks
+timing and barrier used by `bench.py`, the reference arm launched the way the driver launches it
+(torch.distributed.run, two ranks), where rank 0 alone prints the JSON line, and the exchange step
+of a direction-sharded transport update (each rank sums its own directions, one sum-reduction of
+the scalar flux completes the update), run on the oracle.
 """
 import json
 import os
@@ -54,3 +56,33 @@ def test_reference_arm_under_two_ranks_prints_one_line():
     line = lines[0]
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def _shard_main(rank, world, port, out_dir):
+    import numpy as np
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from oracle import Transport
+    from paper_2001_09196_gb300 import inputs
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    prob = inputs.config2d_fields(6, 1, 4, 77, "shard")
+    T = Transport(prob)
+    phi = inputs.random_phi(prob, 9)
+    mine = range(rank * T.nd // world, (rank + 1) * T.nd // world)   # this rank's directions
+    part = torch.as_tensor(T.sweep(phi, directions=mine))
+    dist.all_reduce(part, op=dist.ReduceOp.SUM)
+    if rank == 0:
+        np.save(os.path.join(out_dir, "reduced.npy"), part.numpy())
+        np.save(os.path.join(out_dir, "full.npy"), T.sweep(phi))
+    dist.destroy_process_group()
+
+
+def test_direction_sharded_update_with_gloo(tmp_path):
+    """Ranks sweep disjoint direction ranges; the allreduce of their partial scalar fluxes equals the
+    full transport update (Eq. phi: phi = sum over all directions of w_d psi_d)."""
+    import numpy as np
+    import torch.multiprocessing as mp
+    mp.spawn(_shard_main, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    got, ref = np.load(tmp_path / "reduced.npy"), np.load(tmp_path / "full.npy")
+    assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()

@@ -35,6 +35,16 @@ def flops_per_item(n):
     return (2.0 / 3.0) * n ** 3 + 6.0 * n ** 2
 
 
+def cached_flops_per_item(n, dim, p):
+    """Algorithmic float64 flops of one cached element solve: x = A_e^{-1} rhs (2 n^2), the source
+    and mass terms of rhs (3 n), the inflow face terms (2 flops per inflow trace value)."""
+    return 2 * n * n + 3 * n + 2 * dim * (p + 1) ** (dim - 1)
+
+
+# float64 peak of GB300, derived: 152 SMs x 2 FMA per clock x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
 def bytes_per_item(n, dim, p):
     """Algorithmic bytes of one cached element solve: A_e^{-1} (n^2 float64) read, psi_e (n) written,
     inflow traces (dim faces x (p+1)^(dim-1) values) read, face flux factors (2D: 4) read."""
@@ -51,7 +61,7 @@ def peaks():
 
 # DRAM bytes per item of node_level_kernel<2,2,FP64> on this workload, from the ncu capture
 # summarised in profiles/node_level_kernel_fp64_c2_256x256_q2_s8.md (read + write, 3 launches)
-NODE_KERNEL_DRAM_BYTES_PER_ITEM = 1386.0
+NODE_KERNEL_DRAM_BYTES_PER_ITEM = 1432.0
 
 # FP64 FMA peak: 152 SMs x 4 sub-partitions x 0.5 FP64 FMA/clk x 2 flop x 2.07 GHz (GB300 runs FP64 at
 # 1/64 of the FP32 rate); an FMA-chain probe on this GPU measured 1.01 TFLOP/s.
@@ -306,7 +316,14 @@ def run_ours(args, rank, ws):
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else "fallback 6.8 TB/s",
                 "sweep_ms": sweep_ms, "levels_on_critical_path": mesh.n_levels,
                 "us_per_level": 1e3 * sweep_ms / mesh.n_levels,
-                "fp64_flops_per_elem_dir_uncached": flops_per_item(n)}
+                "fp64_flops_per_elem_dir_uncached": flops_per_item(n),
+                "fp64_pipe": {"flops_per_elem_dir": cached_flops_per_item(n, prob.dim, prob.p),
+                              "achieved_tflops": cached_flops_per_item(n, prob.dim, prob.p) * mesh.n_elem * mesh.n_dirs
+                              / (sweep_ms / 1e3) / 1e12,
+                              "peak_tflops": FP64_PEAK_TFLOPS,
+                              "frac": cached_flops_per_item(n, prob.dim, prob.p) * mesh.n_elem * mesh.n_dirs
+                              / (sweep_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                              "peak_source": "derived: 152 SMs x 2 float64 FMA/clk x 2 flop x 2.07 GHz"}}
 
     # other forms (not part of value): FP32 element solves, FP32 + FP64 refinement,
     # unaccelerated-by-Krylov source iteration with the same DSA (capped at 300 iterations),

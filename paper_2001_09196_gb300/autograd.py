@@ -67,7 +67,8 @@ def solve(mesh, sigma_t, sigma_s, q, solve_opts=None, adjoint_opts=None, checkpo
     so = dict(DEFAULT_SOLVE, **(solve_opts or {}))
     ao = dict(DEFAULT_SOLVE, **(adjoint_opts or {}))
     ao.pop("precision", None)
-    for k in ("thick_rule", "eta", "mask"):
+    # the adjoint's DSA step is the transpose of the forward one: same thick set, operator and Sigma
+    for k in ("thick_rule", "eta", "mask", "operator", "dsa_sigma"):
         if k in so and k not in ao:
             ao[k] = so[k]
     return SnSolve.apply(sigma_t, sigma_s, q, mesh, so, ao, checkpoint_every)

@@ -50,6 +50,7 @@ enum { SN_DSA_NONE = 0, SN_DSA_FULL = 1, SN_DSA_THICK = 2, SN_DSA_TRIANGULAR = 3
 enum { SN_THICK_SIGMA_S = 0, SN_THICK_SIGMA_T_H = 1, SN_THICK_MASK = 2 };
 enum { SN_DSA_SIGMA_S = 0, SN_DSA_SIGMA_T = 1 };
 enum { SN_DSA_OP_SIP = 0, SN_DSA_OP_NIP = 1, SN_DSA_OP_MNIP = 2 };  /* DSA operator (Sec. 4.1) */
+enum { SN_VCYCLE_AUTO = 0, SN_VCYCLE_FP64 = 1, SN_VCYCLE_FP32 = 2 };  /* DSA preconditioner arithmetic */
 enum { SN_OUTER_SI = 0, SN_OUTER_FGMRES = 1 };                  /* outer iteration */
 enum { SN_CACHE_OFF = 0, SN_CACHE_ON = 1, SN_CACHE_AUTO = 2 };  /* operator cache */
 
@@ -205,6 +206,10 @@ typedef struct {
     int restart;             /* fGMRES restart length (1..60; the paper uses 30) */
     int dsa_operator;        /* SN_DSA_OP_SIP (default) | SN_DSA_OP_NIP (Eq. NIP) | SN_DSA_OP_MNIP (Eq. NIP with
                                 the penalty of Eq. ModifiedF0); see sn_source_iterate */
+    int dsa_vcycle;          /* arithmetic of the multigrid V-cycle that preconditions each DSA solve:
+                                SN_VCYCLE_AUTO (default: float32 when inner_tol >= 1e-8, else float64),
+                                SN_VCYCLE_FP64 or SN_VCYCLE_FP32.  The Krylov residuals, dot products and
+                                convergence test are float64 in every mode. */
 } sn_iter_opts;
 
 typedef struct {

@@ -437,8 +437,11 @@ static sn_status ensure_dsa(sn_mesh* m, const sn_iter_opts* o) {
     std::vector<unsigned char> mask;
     sn_status st = thick_mask_for(m, o, mask);
     if (st != SN_OK) return st;
-    if (m->dsa && m->dsa_key_mask == mask && m->dsa_key_sigma == o->dsa_sigma && m->dsa_key_op == o->dsa_operator)
+    if (m->dsa && m->dsa_key_mask == mask && m->dsa_key_sigma == o->dsa_sigma && m->dsa_key_op == o->dsa_operator) {
+        m->dsa->vcycle_mode = o->dsa_vcycle;
+        if (m->dsa_t) m->dsa_t->vcycle_mode = o->dsa_vcycle;
         return SN_OK;
+    }
     sn::dsa_free(m->dsa);
     sn::dsa_free(m->dsa_t);
     m->dsa = m->dsa_t = nullptr;
@@ -449,6 +452,7 @@ static sn_status ensure_dsa(sn_mesh* m, const sn_iter_opts* o) {
     m->dsa_key_mask = mask;
     m->dsa_key_sigma = o->dsa_sigma;
     m->dsa_key_op = o->dsa_operator;
+    m->dsa->vcycle_mode = o->dsa_vcycle;
     return SN_OK;
 }
 
@@ -460,6 +464,7 @@ static sn_status ensure_dsa_adjoint(sn_mesh* m, const sn_iter_opts* o) {
     std::string err;
     m->dsa_t = sn::dsa_build(m, m->dsa_key_mask.data(), o->dsa_sigma, o->dsa_operator, true, err);
     if (!m->dsa_t) return fail(SN_ERR_ARG, "DSA setup (transposed): %s", err.c_str());
+    m->dsa_t->vcycle_mode = o->dsa_vcycle;
     return SN_OK;
 }
 
@@ -470,6 +475,7 @@ static sn_status check_opts(const sn_iter_opts* o) {
     if (!o) return fail(SN_ERR_ARG, "null opts");
     if (o->dsa < SN_DSA_NONE || o->dsa > SN_DSA_TRIANGULAR) return fail(SN_ERR_ARG, "bad dsa");
     if (o->dsa_operator < SN_DSA_OP_SIP || o->dsa_operator > SN_DSA_OP_MNIP) return fail(SN_ERR_ARG, "bad dsa_operator");
+    if (o->dsa_vcycle < SN_VCYCLE_AUTO || o->dsa_vcycle > SN_VCYCLE_FP32) return fail(SN_ERR_ARG, "bad dsa_vcycle");
     if (o->precision < SN_FP64 || o->precision > SN_FP32_REFINE) return fail(SN_ERR_ARG, "bad precision");
     if (!(o->tol >= 0) || o->max_iters < 1) return fail(SN_ERR_ARG, "bad tol / max_iters");
     if (o->dsa != SN_DSA_NONE && (!(o->inner_tol > 0) || o->inner_max_iters < 1))

@@ -39,45 +39,57 @@ __global__ void scatter_set_kernel(const double* x, const int* thick, int nt, in
     full[(size_t)thick[t] * n + i] = x[idx];
 }
 
+// The V-cycle kernels are templated on the arithmetic type T: float64 for the operator products
+// of the Krylov solvers and for tight inner tolerances, float32 for the preconditioner when the
+// inner tolerance is loose (the Krylov residuals, dot products and tests stay float64).
+
 // out = b - A x (b may be null: out = A x), BSR with n x n blocks; one thread per (row block, node)
-__global__ void bsr_kernel(const int* ptr, const int* col, const double* val, int nt, int n, const double* x,
-                           const double* b, double* out) {
+template <typename T>
+__global__ void bsr_kernel(const int* ptr, const int* col, const T* val, int nt, int n, const T* x, const T* b,
+                           T* out) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)nt * n) return;
     const int t = (int)(idx / n), i = (int)(idx % n);
-    double s = 0.0;
+    T s = T(0);
     for (int k = ptr[t]; k < ptr[t + 1]; ++k) {
-        const double* blk = val + (size_t)k * n * n + (size_t)i * n;
-        const double* xc = x + (size_t)col[k] * n;
+        const T* blk = val + (size_t)k * n * n + (size_t)i * n;
+        const T* xc = x + (size_t)col[k] * n;
         for (int j = 0; j < n; ++j) s += blk[j] * xc[j];
     }
     out[idx] = b ? b[idx] - s : s;
 }
 
 // x (+)= omega Dinv r per block
-__global__ void block_jacobi_kernel(const double* dinv, int nt, int n, double omega, const double* r, double* x,
-                                    int accumulate) {
+template <typename T>
+__global__ void block_jacobi_kernel(const T* dinv, int nt, int n, T omega, const T* r, T* x, int accumulate) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)nt * n) return;
     const int t = (int)(idx / n), i = (int)(idx % n);
-    const double* D = dinv + (size_t)t * n * n + (size_t)i * n;
-    const double* rr = r + (size_t)t * n;
-    double s = 0.0;
+    const T* D = dinv + (size_t)t * n * n + (size_t)i * n;
+    const T* rr = r + (size_t)t * n;
+    T s = T(0);
     for (int j = 0; j < n; ++j) s += D[j] * rr[j];
-    x[idx] = (accumulate ? x[idx] : 0.0) + omega * s;
+    x[idx] = (accumulate ? x[idx] : T(0)) + omega * s;
+}
+
+// precision conversions at the entry and exit of a float32 V-cycle
+template <typename A, typename B>
+__global__ void convert_kernel(const A* in, B* out, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = static_cast<B>(in[i]);
 }
 
 // CSR product with G lanes per row (G a power of two dividing 32): the lanes of a group take
 // every G-th entry of the row and the group adds its partial sums by a fixed shuffle tree, so a
 // row costs about (nnz / G) dependent loads instead of nnz.  mode 0: out = M x; 1: out = b - M x;
 // 2: out += M x.
-template <int G>
-__global__ void csr_vec_kernel(const int* ptr, const int* col, const double* val, int rows, const double* x,
-                               const double* b, double* out, int mode) {
+template <int G, typename T>
+__global__ void csr_vec_kernel(const int* ptr, const int* col, const T* val, int rows, const T* x, const T* b, T* out,
+                               int mode) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int gl = threadIdx.x & (G - 1);
     const long long row = tid / G;
-    double s = 0.0;
+    T s = T(0);
     if (row < rows) {
         const int k1 = ptr[row + 1];
         for (int k = ptr[row] + gl; k < k1; k += G) s += val[k] * x[col[k]];
@@ -92,11 +104,12 @@ __global__ void csr_vec_kernel(const int* ptr, const int* col, const double* val
 }
 
 // x = A b for the dense coarsest level, one warp per row (lanes stride over the columns)
-__global__ void dense_mv_warp_kernel(const double* A, int n, const double* b, double* x) {
+template <typename T>
+__global__ void dense_mv_warp_kernel(const T* A, int n, const T* b, T* x) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const long long row = tid >> 5;
-    double s = 0.0;
+    T s = T(0);
     if (row < n)
         for (int c = lane; c < n; c += 32) s += A[(size_t)row * n + c] * b[c];
 #pragma unroll
@@ -104,10 +117,11 @@ __global__ void dense_mv_warp_kernel(const double* A, int n, const double* b, do
     if (row < n && lane == 0) x[row] = s;
 }
 
-__global__ void jacobi_kernel(const double* dinv, int rows, double omega, const double* r, double* x, int accumulate) {
+template <typename T>
+__global__ void jacobi_kernel(const T* dinv, int rows, T omega, const T* r, T* x, int accumulate) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= rows) return;
-    x[i] = (accumulate ? x[i] : 0.0) + omega * dinv[i] * r[i];
+    x[i] = (accumulate ? x[i] : T(0)) + omega * dinv[i] * r[i];
 }
 
 // Algorithm 1 (triangular heterogeneous DSA) helpers on full [elem][node] vectors; emask marks
@@ -300,6 +314,39 @@ cudaError_t upload(DsaHierarchy* H) {
     return cudaSuccess;
 }
 
+template <typename T>
+cudaError_t up32(float** d, const std::vector<T>& h) {
+    if (h.empty()) { *d = nullptr; return cudaSuccess; }
+    std::vector<float> f(h.begin(), h.end());
+    cudaError_t err = cudaMalloc(d, f.size() * sizeof(float));
+    if (err != cudaSuccess) return err;
+    return cudaMemcpy(*d, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice);
+}
+
+// float32 copies of the hierarchy's values and the float32 V-cycle's vectors (made once, on demand)
+cudaError_t upload32(DsaHierarchy* H) {
+    if (H->uploaded32) return cudaSuccess;
+    const long long N0 = (long long)H->nt * H->n;
+    cudaError_t err;
+#define UP32(dst, src) if ((err = up32(&(dst), src)) != cudaSuccess) return err
+    UP32(H->l0.d_val32, H->l0.val);
+    UP32(H->l0.d_dinv32, H->l0.dinv);
+    for (LevelC& L : H->levels) {
+        UP32(L.d_a_val32, L.a_val);
+        UP32(L.d_p_val32, L.p_val);
+        UP32(L.d_r_val32, L.r_val);
+        UP32(L.d_dinv32, L.dinv);
+        UP32(L.d_dense32, L.dense_inv);
+        for (float** v : {&L.d_x32, &L.d_b32, &L.d_r32})
+            if ((err = cudaMalloc(v, std::max(1, L.n) * sizeof(float))) != cudaSuccess) return err;
+    }
+#undef UP32
+    for (float** v : {&H->d_vr32, &H->d_r32, &H->d_z32})
+        if ((err = cudaMalloc(v, std::max<long long>(1, N0) * sizeof(float))) != cudaSuccess) return err;
+    H->uploaded32 = true;
+    return cudaSuccess;
+}
+
 cudaError_t dot(DsaHierarchy* H, const double* a, const double* b, long long n, int slot, cudaStream_t s) {
     SN_COUNT_LAUNCH();
     dot_partial_kernel<<<kDotBlocks, kBS, 0, s>>>(a, b, n, H->d_part);
@@ -308,77 +355,134 @@ cudaError_t dot(DsaHierarchy* H, const double* a, const double* b, long long n, 
     return cudaGetLastError();
 }
 
+// Pointers of the multigrid hierarchy in one arithmetic type (the index arrays are shared).
+template <typename T>
+struct VLevel {
+    int n = 0;
+    long long a_nnz = 0, p_nnz = 0, r_nnz = 0;
+    const int *a_ptr, *a_col, *p_ptr, *p_col, *r_ptr, *r_col;
+    const T *a_val, *p_val, *r_val, *dinv, *dense;
+    T *x, *b, *r;
+};
+template <typename T>
+struct VCycle {
+    int nt = 0, n = 0, nu = 2;
+    T omega0 = T(0.6), omega = T(0.6);
+    const int *l0_ptr, *l0_col;
+    const T *l0_val, *l0_dinv;
+    T* vr;
+    std::vector<VLevel<T>> levels;
+};
+
+VCycle<double> view64(const DsaHierarchy* H) {
+    VCycle<double> V;
+    V.nt = H->nt; V.n = H->n; V.nu = H->nu; V.omega0 = H->omega0; V.omega = H->omega;
+    V.l0_ptr = H->l0.d_ptr; V.l0_col = H->l0.d_col; V.l0_val = H->l0.d_val; V.l0_dinv = H->l0.d_dinv; V.vr = H->d_vr;
+    for (const LevelC& L : H->levels)
+        V.levels.push_back({L.n, (long long)L.a_val.size(), (long long)L.p_val.size(), (long long)L.r_val.size(),
+                            L.d_a_ptr, L.d_a_col, L.d_p_ptr, L.d_p_col, L.d_r_ptr, L.d_r_col,
+                            L.d_a_val, L.d_p_val, L.d_r_val, L.d_dinv, L.d_dense, L.d_x, L.d_b, L.d_r});
+    return V;
+}
+
+VCycle<float> view32(const DsaHierarchy* H) {
+    VCycle<float> V;
+    V.nt = H->nt; V.n = H->n; V.nu = H->nu; V.omega0 = (float)H->omega0; V.omega = (float)H->omega;
+    V.l0_ptr = H->l0.d_ptr; V.l0_col = H->l0.d_col; V.l0_val = H->l0.d_val32; V.l0_dinv = H->l0.d_dinv32; V.vr = H->d_vr32;
+    for (const LevelC& L : H->levels)
+        V.levels.push_back({L.n, (long long)L.a_val.size(), (long long)L.p_val.size(), (long long)L.r_val.size(),
+                            L.d_a_ptr, L.d_a_col, L.d_p_ptr, L.d_p_col, L.d_r_ptr, L.d_r_col,
+                            L.d_a_val32, L.d_p_val32, L.d_r_val32, L.d_dinv32, L.d_dense32, L.d_x32, L.d_b32, L.d_r32});
+    return V;
+}
+
 // CSR product with the group width chosen from the rows' average length.
-void csr_mv(const int* ptr, const int* col, const double* val, int rows, long long nnz, const double* x,
-            const double* b, double* out, int mode, cudaStream_t s) {
+template <typename T>
+void csr_mv(const int* ptr, const int* col, const T* val, int rows, long long nnz, const T* x, const T* b, T* out,
+            int mode, cudaStream_t s) {
     if (rows <= 0) return;
     const double avg = (double)nnz / rows;
     SN_COUNT_LAUNCH();
-    if (avg > 12.0) csr_vec_kernel<8><<<nblk((long long)rows * 8), kBS, 0, s>>>(ptr, col, val, rows, x, b, out, mode);
-    else if (avg > 3.0) csr_vec_kernel<4><<<nblk((long long)rows * 4), kBS, 0, s>>>(ptr, col, val, rows, x, b, out, mode);
-    else csr_vec_kernel<1><<<nblk(rows), kBS, 0, s>>>(ptr, col, val, rows, x, b, out, mode);
+    if (avg > 12.0) csr_vec_kernel<8, T><<<nblk((long long)rows * 8), kBS, 0, s>>>(ptr, col, val, rows, x, b, out, mode);
+    else if (avg > 3.0) csr_vec_kernel<4, T><<<nblk((long long)rows * 4), kBS, 0, s>>>(ptr, col, val, rows, x, b, out, mode);
+    else csr_vec_kernel<1, T><<<nblk(rows), kBS, 0, s>>>(ptr, col, val, rows, x, b, out, mode);
 }
 
-// continuous level l (index into H->levels): x = V(b)
-void vcycle_c(DsaHierarchy* H, size_t l, cudaStream_t s) {
-    LevelC& L = H->levels[l];
-    if (!L.dense_inv.empty()) {
+// continuous level l: x = V(b)
+template <typename T>
+void vcycle_c(const VCycle<T>& V, size_t l, cudaStream_t s) {
+    const VLevel<T>& L = V.levels[l];
+    if (L.dense) {
         SN_COUNT_LAUNCH();
-        dense_mv_warp_kernel<<<nblk((long long)L.n * 32), kBS, 0, s>>>(L.d_dense, L.n, L.d_b, L.d_x);
+        dense_mv_warp_kernel<T><<<nblk((long long)L.n * 32), kBS, 0, s>>>(L.dense, L.n, L.b, L.x);
         return;
     }
-    for (int k = 0; k < H->nu; ++k) {
+    for (int k = 0; k < V.nu; ++k) {
         if (k == 0) {
             SN_COUNT_LAUNCH();
-            jacobi_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_dinv, L.n, H->omega, L.d_b, L.d_x, 0);
+            jacobi_kernel<T><<<nblk(L.n), kBS, 0, s>>>(L.dinv, L.n, V.omega, L.b, L.x, 0);
         } else {
-            csr_mv(L.d_a_ptr, L.d_a_col, L.d_a_val, L.n, (long long)L.a_val.size(), L.d_x, L.d_b, L.d_r, 1, s);
+            csr_mv<T>(L.a_ptr, L.a_col, L.a_val, L.n, L.a_nnz, L.x, L.b, L.r, 1, s);
             SN_COUNT_LAUNCH();
-            jacobi_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_dinv, L.n, H->omega, L.d_r, L.d_x, 1);
+            jacobi_kernel<T><<<nblk(L.n), kBS, 0, s>>>(L.dinv, L.n, V.omega, L.r, L.x, 1);
         }
     }
-    csr_mv(L.d_a_ptr, L.d_a_col, L.d_a_val, L.n, (long long)L.a_val.size(), L.d_x, L.d_b, L.d_r, 1, s);
-    LevelC& C = H->levels[l + 1];
-    csr_mv(C.d_r_ptr, C.d_r_col, C.d_r_val, C.n, (long long)C.r_val.size(), L.d_r, nullptr, C.d_b, 0, s);
-    vcycle_c(H, l + 1, s);
-    csr_mv(C.d_p_ptr, C.d_p_col, C.d_p_val, L.n, (long long)C.p_val.size(), C.d_x, nullptr, L.d_x, 2, s);
-    for (int k = 0; k < H->nu; ++k) {
-        csr_mv(L.d_a_ptr, L.d_a_col, L.d_a_val, L.n, (long long)L.a_val.size(), L.d_x, L.d_b, L.d_r, 1, s);
+    csr_mv<T>(L.a_ptr, L.a_col, L.a_val, L.n, L.a_nnz, L.x, L.b, L.r, 1, s);
+    const VLevel<T>& C = V.levels[l + 1];
+    csr_mv<T>(C.r_ptr, C.r_col, C.r_val, C.n, C.r_nnz, L.r, nullptr, C.b, 0, s);
+    vcycle_c<T>(V, l + 1, s);
+    csr_mv<T>(C.p_ptr, C.p_col, C.p_val, L.n, C.p_nnz, C.x, nullptr, L.x, 2, s);
+    for (int k = 0; k < V.nu; ++k) {
+        csr_mv<T>(L.a_ptr, L.a_col, L.a_val, L.n, L.a_nnz, L.x, L.b, L.r, 1, s);
         SN_COUNT_LAUNCH();
-        jacobi_kernel<<<nblk(L.n), kBS, 0, s>>>(L.d_dinv, L.n, H->omega, L.d_r, L.d_x, 1);
+        jacobi_kernel<T><<<nblk(L.n), kBS, 0, s>>>(L.dinv, L.n, V.omega, L.r, L.x, 1);
     }
 }
 
 // z = V(r) on the DG level
-void vcycle0(DsaHierarchy* H, const double* r, double* z, cudaStream_t s) {
-    const int nt = H->nt, n = H->n;
+template <typename T>
+void vcycle0_t(const VCycle<T>& V, const T* r, T* z, cudaStream_t s) {
+    const int nt = V.nt, n = V.n;
     const long long N0 = (long long)nt * n;
-    const Level0& A = H->l0;
-    for (int k = 0; k < H->nu; ++k) {
+    for (int k = 0; k < V.nu; ++k) {
         if (k == 0) {
             SN_COUNT_LAUNCH();
-            block_jacobi_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_dinv, nt, n, H->omega0, r, z, 0);
+            block_jacobi_kernel<T><<<nblk(N0), kBS, 0, s>>>(V.l0_dinv, nt, n, V.omega0, r, z, 0);
         } else {
             SN_COUNT_LAUNCH();
-            bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, nt, n, z, r, H->d_vr);
+            bsr_kernel<T><<<nblk(N0), kBS, 0, s>>>(V.l0_ptr, V.l0_col, V.l0_val, nt, n, z, r, V.vr);
             SN_COUNT_LAUNCH();
-            block_jacobi_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_dinv, nt, n, H->omega0, H->d_vr, z, 1);
+            block_jacobi_kernel<T><<<nblk(N0), kBS, 0, s>>>(V.l0_dinv, nt, n, V.omega0, V.vr, z, 1);
         }
     }
-    if (!H->levels.empty()) {
+    if (!V.levels.empty()) {
         SN_COUNT_LAUNCH();
-        bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, nt, n, z, r, H->d_vr);
-        LevelC& C = H->levels[0];
-        csr_mv(C.d_r_ptr, C.d_r_col, C.d_r_val, C.n, (long long)C.r_val.size(), H->d_vr, nullptr, C.d_b, 0, s);
-        vcycle_c(H, 0, s);
-        csr_mv(C.d_p_ptr, C.d_p_col, C.d_p_val, (int)N0, (long long)C.p_val.size(), C.d_x, nullptr, z, 2, s);
+        bsr_kernel<T><<<nblk(N0), kBS, 0, s>>>(V.l0_ptr, V.l0_col, V.l0_val, nt, n, z, r, V.vr);
+        const VLevel<T>& C = V.levels[0];
+        csr_mv<T>(C.r_ptr, C.r_col, C.r_val, C.n, C.r_nnz, V.vr, nullptr, C.b, 0, s);
+        vcycle_c<T>(V, 0, s);
+        csr_mv<T>(C.p_ptr, C.p_col, C.p_val, (int)N0, C.p_nnz, C.x, nullptr, z, 2, s);
     }
-    for (int k = 0; k < H->nu; ++k) {
+    for (int k = 0; k < V.nu; ++k) {
         SN_COUNT_LAUNCH();
-        bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, nt, n, z, r, H->d_vr);
+        bsr_kernel<T><<<nblk(N0), kBS, 0, s>>>(V.l0_ptr, V.l0_col, V.l0_val, nt, n, z, r, V.vr);
         SN_COUNT_LAUNCH();
-        block_jacobi_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_dinv, nt, n, H->omega0, H->d_vr, z, 1);
+        block_jacobi_kernel<T><<<nblk(N0), kBS, 0, s>>>(V.l0_dinv, nt, n, V.omega0, V.vr, z, 1);
     }
+}
+
+// z = V(r) on float64 vectors, in float64 or (H->pc32) in float32 between two conversions
+void vcycle0(DsaHierarchy* H, const double* r, double* z, cudaStream_t s) {
+    if (!H->pc32) {
+        vcycle0_t<double>(view64(H), r, z, s);
+        return;
+    }
+    const long long N0 = (long long)H->nt * H->n;
+    SN_COUNT_LAUNCH();
+    convert_kernel<double, float><<<nblk(N0), kBS, 0, s>>>(r, H->d_r32, N0);
+    vcycle0_t<float>(view32(H), H->d_r32, H->d_z32, s);
+    SN_COUNT_LAUNCH();
+    convert_kernel<float, double><<<nblk(N0), kBS, 0, s>>>(H->d_z32, z, N0);
 }
 
 // Records the Krylov solve of D_ff x = b (thick-local vectors H->d_b -> H->d_x) into a CUDA graph:
@@ -462,7 +566,7 @@ cudaError_t record_krylov(DsaHierarchy* H, double tol, int max_iters) {
         SN_COUNT_LAUNCH();
         copy_scalar<<<1, 1, 0, s>>>(H->d_s, 0, 4);
         SN_COUNT_LAUNCH();
-        bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, H->nt, H->n, H->d_p, nullptr, H->d_q);
+        bsr_kernel<double><<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, H->nt, H->n, H->d_p, nullptr, H->d_q);
         dot(H, H->d_p, H->d_q, N0, 1, s);
         SN_COUNT_LAUNCH();
         cg_update_xr<<<nblk(N0), kBS, 0, s>>>(H->d_x, H->d_r, H->d_p, H->d_q, N0, H->d_s);
@@ -477,13 +581,13 @@ cudaError_t record_krylov(DsaHierarchy* H, double tol, int max_iters) {
         bicg_update_p<<<nblk(N0), kBS, 0, s>>>(H->d_p, H->d_r, H->d_q, N0, H->d_s);
         vcycle0(H, H->d_p, H->d_z, s);
         SN_COUNT_LAUNCH();
-        bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, H->nt, H->n, H->d_z, nullptr, H->d_q);
+        bsr_kernel<double><<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, H->nt, H->n, H->d_z, nullptr, H->d_q);
         dot(H, H->d_rh, H->d_q, N0, 5, s);
         SN_COUNT_LAUNCH();
         bicg_update_xs<<<nblk(N0), kBS, 0, s>>>(H->d_x, H->d_r, H->d_z, H->d_q, N0, H->d_s);
         vcycle0(H, H->d_r, H->d_sh, s);
         SN_COUNT_LAUNCH();
-        bsr_kernel<<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, H->nt, H->n, H->d_sh, nullptr, H->d_t);
+        bsr_kernel<double><<<nblk(N0), kBS, 0, s>>>(A.d_ptr, A.d_col, A.d_val, H->nt, H->n, H->d_sh, nullptr, H->d_t);
         dot(H, H->d_t, H->d_r, N0, 6, s);
         dot(H, H->d_t, H->d_t, N0, 7, s);
         SN_COUNT_LAUNCH();
@@ -511,8 +615,12 @@ cudaError_t record_krylov(DsaHierarchy* H, double tol, int max_iters) {
 // device (dsa_take_iters reads the running total).
 cudaError_t pcg(DsaHierarchy* H, double tol, int max_iters, cudaStream_t s) {
     cudaError_t err;
-    if (!H->pcg_graph || H->pcg_tol != tol || H->pcg_max != max_iters)
+    const bool want32 = H->vcycle_mode == SN_VCYCLE_FP32 || (H->vcycle_mode == SN_VCYCLE_AUTO && tol >= 1e-8);
+    if (want32 && (err = upload32(H)) != cudaSuccess) return err;
+    if (!H->pcg_graph || H->pcg_tol != tol || H->pcg_max != max_iters || H->pc32 != want32) {
+        H->pc32 = want32;
         if ((err = record_krylov(H, tol, max_iters)) != cudaSuccess) return err;
+    }
     g_launches.fetch_add(H->pro_launches, std::memory_order_relaxed);
     return cudaGraphLaunch(H->pcg_graph, s);
 }
@@ -527,7 +635,9 @@ void dsa_free(DsaHierarchy* H) {
     for (LevelC& L : H->levels) {
         f(L.d_a_ptr); f(L.d_a_col); f(L.d_a_val); f(L.d_p_ptr); f(L.d_p_col); f(L.d_p_val);
         f(L.d_r_ptr); f(L.d_r_col); f(L.d_r_val); f(L.d_dinv); f(L.d_dense); f(L.d_x); f(L.d_b); f(L.d_r);
+        f(L.d_a_val32); f(L.d_p_val32); f(L.d_r_val32); f(L.d_dinv32); f(L.d_dense32); f(L.d_x32); f(L.d_b32); f(L.d_r32);
     }
+    f(H->l0.d_val32); f(H->l0.d_dinv32); f(H->d_vr32); f(H->d_r32); f(H->d_z32);
     f(H->d_x); f(H->d_b); f(H->d_r); f(H->d_z); f(H->d_p); f(H->d_q); f(H->d_vr); f(H->d_vx);
     f(H->d_rh); f(H->d_sh); f(H->d_t);
     f(H->d_part); f(H->d_s); f(H->d_it); f(H->d_emask);
@@ -548,7 +658,7 @@ cudaError_t dsa_apply(DsaHierarchy* H, const double* x, double* y, cudaStream_t 
     SN_COUNT_LAUNCH();
     gather_kernel<<<nblk(N0), kBS, 0, s>>>(x, H->d_thick, nullptr, H->nt, H->n, H->d_p);
     SN_COUNT_LAUNCH();
-    bsr_kernel<<<nblk(N0), kBS, 0, s>>>(H->l0.d_ptr, H->l0.d_col, H->l0.d_val, H->nt, H->n, H->d_p, nullptr, H->d_q);
+    bsr_kernel<double><<<nblk(N0), kBS, 0, s>>>(H->l0.d_ptr, H->l0.d_col, H->l0.d_val, H->nt, H->n, H->d_p, nullptr, H->d_q);
     SN_COUNT_LAUNCH();
     scatter_set_kernel<<<nblk(N0), kBS, 0, s>>>(H->d_q, H->d_thick, H->nt, H->n, y);
     return cudaGetLastError();

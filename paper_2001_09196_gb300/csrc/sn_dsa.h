@@ -15,6 +15,7 @@ struct Level0 {                  // DG space on the thick elements, BSR with n x
     std::vector<double> dinv;    // nt x n x n inverse diagonal blocks
     int *d_ptr = nullptr, *d_col = nullptr;
     double *d_val = nullptr, *d_dinv = nullptr;
+    float *d_val32 = nullptr, *d_dinv32 = nullptr;  // float32 copies for the float32 V-cycle
 };
 
 struct LevelC {                  // a continuous level: operator, prolongation to the finer level
@@ -25,6 +26,8 @@ struct LevelC {                  // a continuous level: operator, prolongation t
         *d_r_col = nullptr;
     double *d_a_val = nullptr, *d_p_val = nullptr, *d_r_val = nullptr, *d_dinv = nullptr, *d_dense = nullptr;
     double *d_x = nullptr, *d_b = nullptr, *d_r = nullptr;
+    float *d_a_val32 = nullptr, *d_p_val32 = nullptr, *d_r_val32 = nullptr, *d_dinv32 = nullptr, *d_dense32 = nullptr;
+    float *d_x32 = nullptr, *d_b32 = nullptr, *d_r32 = nullptr;
 };
 
 struct DsaHierarchy {
@@ -45,6 +48,11 @@ struct DsaHierarchy {
     double* d_part = nullptr;                 // reduction partials
     double* d_s = nullptr;                    // device scalars
     bool uploaded = false;
+    // V-cycle arithmetic: SN_VCYCLE_AUTO (float32 when the inner tolerance is >= 1e-8), _FP64, _FP32
+    int vcycle_mode = 0;
+    bool pc32 = false;                        // the recorded solve uses the float32 V-cycle
+    bool uploaded32 = false;
+    float *d_vr32 = nullptr, *d_r32 = nullptr, *d_z32 = nullptr;
     double omega0 = 0.6, omega = 0.6;         // damping of block-Jacobi (level 0) / Jacobi (levels >= 1)
     int nu = 2;                               // pre- and post-smoothing steps
     // The Krylov solve (PCG or BiCGStab) recorded as a CUDA graph whose WHILE conditional node

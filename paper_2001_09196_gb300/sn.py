@@ -51,7 +51,7 @@ class IterOpts(C.Structure):
                 ("inner_tol", C.c_double), ("max_iters", C.c_int), ("inner_max_iters", C.c_int),
                 ("precision", C.c_int), ("checkpoint_every", C.c_int), ("checkpoints", C.c_void_p),
                 ("max_checkpoints", C.c_int), ("warm_start", C.c_int), ("outer", C.c_int), ("restart", C.c_int),
-                ("dsa_operator", C.c_int)]
+                ("dsa_operator", C.c_int), ("dsa_vcycle", C.c_int)]
 
 
 class IterStats(C.Structure):
@@ -143,10 +143,11 @@ def _stream(stream):
 
 def make_opts(dsa="thick", thick_rule="sigma_s", eta=1.0, mask=None, dsa_sigma="sigma_s", tol=1e-8,
               inner_tol=1e-4, max_iters=1000, inner_max_iters=200, precision="fp64", checkpoint_every=0,
-              checkpoints=None, warm_start=False, outer="si", restart=30, operator="sip"):
+              checkpoints=None, warm_start=False, outer="si", restart=30, operator="sip", vcycle="auto"):
     """Options of sn_source_iterate / sn_adjoint_iterate.  operator: the DSA operator D_ff,
     "sip" (symmetric, conjugate gradients), "nip" (Eq. NIP) or "mnip" (Eq. NIP with the penalty
-    of Eq. ModifiedF0); the nonsymmetric two are solved by BiCGStab."""
+    of Eq. ModifiedF0); the nonsymmetric two are solved by BiCGStab.  vcycle: arithmetic of the
+    multigrid preconditioner, "auto" (float32 when inner_tol >= 1e-8), "fp64" or "fp32"."""
     o = IterOpts()
     _lib.sn_iter_opts_default(C.byref(o))
     o.dsa = _DSA[dsa] if isinstance(dsa, str) else int(dsa)
@@ -170,6 +171,7 @@ def make_opts(dsa="thick", thick_rule="sigma_s", eta=1.0, mask=None, dsa_sigma="
     o.outer = {"si": 0, "fgmres": 1}[outer] if isinstance(outer, str) else int(outer)
     o.restart = int(restart)
     o.dsa_operator = _DSA_OP[operator] if isinstance(operator, str) else int(operator)
+    o.dsa_vcycle = {"auto": 0, "fp64": 1, "fp32": 2}[vcycle] if isinstance(vcycle, str) else int(vcycle)
     o._keep = keep
     return o
 

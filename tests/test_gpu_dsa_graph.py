@@ -78,3 +78,56 @@ def test_iterations_report_inner_pcg_counts(sn, case):
         assert r["inner_iters"] >= 4 * 2  # four DSA solves, each more than one PCG iteration at 1e-6
         r0 = m.source_iterate(dsa="none", tol=0.0, max_iters=4, outer=outer)
         assert r0["inner_iters"] == 0
+
+
+def _true_residual(op, b, x):
+    """||b_f - D_ff x_f|| / ||b_f|| with the oracle's operator in float64 on the host."""
+    D = op.nodal_matrix()
+    bf = b[op.thick].ravel()
+    xf = x.cpu().numpy()[op.thick].ravel()
+    return float(np.linalg.norm(bf - D @ xf) / np.linalg.norm(bf))
+
+
+@pytest.mark.parametrize("operator", ["sip", "nip"])
+def test_float32_vcycle_preconditions_to_tight_tolerances(sn, case, operator):
+    """The float32 V-cycle is only the preconditioner: the float64 Krylov residual still reaches
+    1e-11, in about as many iterations as with the float64 V-cycle."""
+    import scipy.sparse.linalg as spla
+    from oracle.dsa import DSA
+    prob, b, ref, op = case
+    if operator != "sip":
+        op = DSA(op.T, prob.thick_mask(), operator=operator)
+        ref = np.zeros_like(b)
+        ref[op.thick] = spla.spsolve(op.nodal_matrix().tocsc(), b[op.thick].ravel()).reshape(-1, op.T.n)
+    m = sn.Mesh.from_problem(prob)
+    bt = torch.as_tensor(b, device="cuda")
+    kw = dict(thick_rule=prob.thick_rule, operator=operator, inner_tol=1e-11, inner_max_iters=500)
+    x32, it32 = m.dsa_solve(bt, vcycle="fp32", **kw)
+    x64, it64 = m.dsa_solve(bt, vcycle="fp64", **kw)
+    assert it32 < 500 and it32 <= 1.5 * it64 + 2
+    assert _true_residual(op, b, x32) < 2e-11 and _true_residual(op, b, x64) < 2e-11
+    assert _rel(x32, ref) < 1e-8
+
+
+def test_auto_vcycle_is_float32_for_loose_and_float64_for_tight_tolerances(sn, case):
+    prob, b, _, _ = case
+    m = sn.Mesh.from_problem(prob)
+    bt = torch.as_tensor(b, device="cuda")
+    kw = dict(thick_rule=prob.thick_rule, inner_max_iters=500)
+    loose = {v: m.dsa_solve(bt, vcycle=v, inner_tol=1e-4, **kw)[0].clone() for v in ("auto", "fp32", "fp64")}
+    assert torch.equal(loose["auto"], loose["fp32"]) and not torch.equal(loose["auto"], loose["fp64"])
+    tight = {v: m.dsa_solve(bt, vcycle=v, inner_tol=1e-10, **kw)[0].clone() for v in ("auto", "fp32", "fp64")}
+    assert torch.equal(tight["auto"], tight["fp64"]) and not torch.equal(tight["auto"], tight["fp32"])
+
+
+def test_float32_vcycle_leaves_the_fixed_point_alone(sn):
+    """With the paper's loose inner tolerance (float32 V-cycle) fGMRES reaches the oracle's solution."""
+    from oracle import Transport
+    from oracle.dsa import DSA
+    prob = inputs.config1()
+    T = Transport(prob)
+    m = sn.Mesh.from_problem(prob)
+    r = m.source_iterate(dsa="thick", outer="fgmres", tol=1e-12, inner_tol=1e-4, max_iters=400)
+    ref = T.source_iterate(dsa=DSA(T, prob.thick_mask()), tol=1e-13, max_iters=400)
+    assert r["converged"] and r["inner_iters"] > 0
+    assert np.abs(r["phi"].cpu().numpy() - ref["phi"]).max() < 1e-9 * np.abs(ref["phi"]).max()

@@ -222,6 +222,8 @@ typedef struct {
     int n_checkpoints;       /* checkpoints written */
     double ms_total;         /* wall time of the call (stream-synchronised) */
     int n_sweeps;            /* transport updates performed (all directions each) */
+    double ms_sweep;         /* device time of the transport updates and their flux reductions (CUDA events) */
+    double ms_dsa;           /* device time of the DSA solves (CUDA events); both 0 for batches */
 } sn_iter_stats;
 
 /* Defaults: dsa thick, sigma_s >= 1, tol 1e-8, inner_tol 1e-4 (Sec. 5), FP64, cold start. */

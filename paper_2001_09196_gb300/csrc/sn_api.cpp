@@ -488,6 +488,47 @@ static sn_status check_opts(const sn_iter_opts* o) {
     return SN_OK;
 }
 
+// Device time of one kind of work over a solve: CUDA event pairs recorded on the stream around
+// each segment, their elapsed times summed at the synchronisation points the iterations already
+// have (harvest() is called only after the stream has been synchronised).
+struct SegmentClock {
+    static constexpr int kPairs = 8;
+    cudaEvent_t a[kPairs] = {}, b[kPairs] = {};
+    int n = 0;
+    double ms = 0.0;
+    bool ok = true;
+    SegmentClock() {
+        for (int i = 0; i < kPairs && ok; ++i)
+            ok = cudaEventCreate(&a[i]) == cudaSuccess && cudaEventCreate(&b[i]) == cudaSuccess;
+    }
+    ~SegmentClock() {
+        for (int i = 0; i < kPairs; ++i) {
+            if (a[i]) cudaEventDestroy(a[i]);
+            if (b[i]) cudaEventDestroy(b[i]);
+        }
+    }
+    void begin(cudaStream_t s) {
+        if (!ok) return;
+        if (n == kPairs) {  // more segments than pairs between two synchronisations
+            cudaEventSynchronize(b[kPairs - 1]);
+            harvest();
+        }
+        cudaEventRecord(a[n], s);
+    }
+    void end(cudaStream_t s) {
+        if (!ok) return;
+        cudaEventRecord(b[n], s);
+        ++n;
+    }
+    void harvest() {
+        for (int i = 0; i < n; ++i) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, a[i], b[i]) == cudaSuccess) ms += t;
+        }
+        n = 0;
+    }
+};
+
 // Flexible GMRES(k) on S x = b (Eq. schur), right-preconditioned by the DSA step
 // P v = v + E_f D_ff^{-1} Sigma_f E_f^T v (Algorithm 2 applied to a residual); classical
 // Gram-Schmidt twice, Givens rotations on the host.
@@ -516,9 +557,11 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
     int it = 0, inner_total = 0, sweeps = 0;
     bool converged = false;
     bool timed_out = false;
+    SegmentClock sweep_clock, dsa_clock;
     while (true) {
         // true residual r = sweep(x) - x (with the fixed source); adjoint: g + T^T x - x
         ++sweeps;
+        sweep_clock.begin(s);
         if (adjoint) {
             CK(sn::launch_adjoint_sweep(m, x, s), "adjoint sweep");
             CK(sn::launch_adjoint_reduce(m, tmp, s), "adjoint reduce");
@@ -527,10 +570,13 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
             CK(sn::launch_sweep(m, x, o->precision, 1.0, s), "sweep");
             CK(sn::launch_phi_reduce(m, o->precision, x, tmp, m->d_scalars, s), "phi reduce");
         }
+        sweep_clock.end(s);
         CK(sn::launch_axpy_norm(m, tmp, x, w, m->d_scalars, s), "residual");
         double rr = 0.0;
         CK(cudaMemcpyAsync(&rr, m->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
         CK(cudaStreamSynchronize(s), "sync");
+        sweep_clock.harvest();
+        dsa_clock.harvest();
         if (m->schedule != sn::SCHED_LEVELS) {
             CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
             if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out");
@@ -553,20 +599,25 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
             double* Zj = Z + (size_t)j * M;
             CK(sn::launch_copy(Zj, Vj, M, s), "copy");
             if (o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0) {
+                dsa_clock.begin(s);
                 CK(sn::dsa_correct(dsa_for(m, adjoint), Vj, Zj, o->inner_tol, o->inner_max_iters, adjoint, s), "DSA");
+                dsa_clock.end(s);
                 if (o->dsa == SN_DSA_TRIANGULAR) {
                     // Algorithm 1, step 2: the zero-source transport update of [0; Z_f], kept on the
                     // thin DOFs (Z_f = V_f + D_ff^{-1} Sigma_f V_f after step 1)
                     double* w = m->d_work;
                     double* y = m->d_work + M;
                     CK(sn::dsa_select_thick(m->dsa, Zj, w, s), "Algorithm 1");
+                    sweep_clock.begin(s);
                     CK(sn::launch_sweep(m, w, o->precision, 0.0, s), "sweep");
                     CK(sn::launch_phi_reduce(m, o->precision, nullptr, y, nullptr, s), "phi reduce");
+                    sweep_clock.end(s);
                     CK(sn::dsa_add_thin(m->dsa, y, Zj, s), "Algorithm 1");
                     ++sweeps;
                 }
             }
             // w = S Zj = Zj - T Zj (T: sweep without the fixed source)
+            sweep_clock.begin(s);
             if (adjoint) {
                 CK(sn::launch_adjoint_sweep(m, Zj, s), "adjoint sweep");
                 CK(sn::launch_adjoint_reduce(m, tmp, s), "adjoint reduce");
@@ -574,6 +625,7 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
                 CK(sn::launch_sweep(m, Zj, o->precision, 0.0, s), "sweep");
                 CK(sn::launch_phi_reduce(m, o->precision, nullptr, tmp, nullptr, s), "phi reduce");
             }
+            sweep_clock.end(s);
             ++sweeps;
             CK(sn::launch_axpy_norm(m, Zj, tmp, w, m->d_scalars, s), "apply S");
             CK(sn::launch_multidot(V, j + 1, M, w, part, hd, s), "orthogonalise");
@@ -583,6 +635,8 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
             CK(sn::launch_multidot(w, 1, M, w, part, hd + 2 * (k + 1), s), "norm");
             CK(cudaMemcpyAsync(hh.data(), hd, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
             CK(cudaStreamSynchronize(s), "sync");
+            sweep_clock.harvest();
+            dsa_clock.harvest();
             if (m->schedule != sn::SCHED_LEVELS) {
                 CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
                 if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out");
@@ -621,6 +675,8 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
         // the restart (or the final check) recomputes the true residual with one more sweep
     }
     CK(cudaStreamSynchronize(s), "sync");
+    sweep_clock.harvest();
+    dsa_clock.harvest();
     if (m->dsa) CK(sn::dsa_take_iters(dsa_for(m, adjoint), s, &inner_total), "DSA iterations");
     if (stats) {
         stats->iters = it;
@@ -629,6 +685,8 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
         stats->thick_fraction = m->dsa && o->dsa != SN_DSA_NONE ? (double)sn::dsa_thick_count(m->dsa) / m->ne : 0.0;
         stats->n_checkpoints = 0;
         stats->n_sweeps = sweeps;
+        stats->ms_sweep = sweep_clock.ms;
+        stats->ms_dsa = dsa_clock.ms;
         stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     if (!converged) return fail(SN_ERR_NOT_CONVERGED, "fGMRES not converged after %d iterations (%.3e)", it, rel);
@@ -658,12 +716,17 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
     double r0 = 0.0, rel = INFINITY;
     int it = 0, inner_total = 0, nck = 0, extra_sweeps = 0;
     bool converged = false;
+    SegmentClock sweep_clock, dsa_clock;
     while (it < o->max_iters) {
+        sweep_clock.begin(s);
         CK(sn::launch_sweep(m, phi, o->precision, 1.0, s), "sweep");
         CK(sn::launch_phi_reduce(m, o->precision, phi, half, m->d_scalars, s), "phi reduce");
+        sweep_clock.end(s);
         double rr = 0.0;
         CK(cudaMemcpyAsync(&rr, m->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
         CK(cudaStreamSynchronize(s), "sync");
+        sweep_clock.harvest();
+        dsa_clock.harvest();
         if (m->schedule != sn::SCHED_LEVELS) {
             bool timed_out = false;
             CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
@@ -677,16 +740,22 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
             CK(sn::launch_axpy_norm(m, half, phi, r, m->d_scalars + 1, s), "residual");
             CK(sn::launch_copy(phi, half, M, s), "copy");
             if (o->dsa != SN_DSA_TRIANGULAR) {
+                dsa_clock.begin(s);
                 CK(sn::dsa_correct(m->dsa, r, phi, o->inner_tol, o->inner_max_iters, false, s), "DSA");
+                dsa_clock.end(s);
             } else {
                 // Algorithm 1: w = E_f (r_f + D_ff^{-1} Sigma_f r_f) (step 1), y = zero-source transport
                 // update of w (step 2); phi gets w - r on the thick DOFs and y on the thin ones
                 double* w = m->d_work + 2 * M;
                 double* y = m->d_work + 3 * M;
                 CK(sn::dsa_select_thick(m->dsa, r, w, s), "Algorithm 1");
+                dsa_clock.begin(s);
                 CK(sn::dsa_correct(m->dsa, r, w, o->inner_tol, o->inner_max_iters, false, s), "DSA");
+                dsa_clock.end(s);
+                sweep_clock.begin(s);
                 CK(sn::launch_sweep(m, w, o->precision, 0.0, s), "sweep");
                 CK(sn::launch_phi_reduce(m, o->precision, nullptr, y, nullptr, s), "phi reduce");
+                sweep_clock.end(s);
                 CK(sn::dsa_tri_combine(m->dsa, w, r, y, phi, s), "Algorithm 1");
                 ++extra_sweeps;
             }
@@ -704,6 +773,8 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
         }
     }
     CK(cudaStreamSynchronize(s), "sync");
+    sweep_clock.harvest();
+    dsa_clock.harvest();
     if (m->dsa) CK(sn::dsa_take_iters(m->dsa, s, &inner_total), "DSA iterations");
     if (stats) {
         stats->iters = it;
@@ -712,6 +783,8 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
         stats->thick_fraction = m->dsa && o->dsa != SN_DSA_NONE ? (double)sn::dsa_thick_count(m->dsa) / m->ne : 0.0;
         stats->n_checkpoints = nck;
         stats->n_sweeps = it + extra_sweeps;
+        stats->ms_sweep = sweep_clock.ms;
+        stats->ms_dsa = dsa_clock.ms;
         stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     if (!converged) return fail(SN_ERR_NOT_CONVERGED, "not converged after %d iterations (rel. residual %.3e)", it, rel);
@@ -762,9 +835,12 @@ sn_status sn_adjoint_iterate(sn_mesh* m, const sn_iter_opts* o, const double* g,
     double r0 = 0.0, rel = INFINITY;
     int it = 0, inner_total = 0;
     bool converged = false;
+    SegmentClock sweep_clock, dsa_clock;
     while (it < o->max_iters) {
+        sweep_clock.begin(s);
         CK(sn::launch_adjoint_sweep(m, mu, s), "adjoint sweep");
         CK(sn::launch_adjoint_reduce(m, tmp, s), "adjoint reduce");
+        sweep_clock.end(s);
         // half = g + T^T mu ; r = half - mu
         CK(cudaMemcpyAsync(half, g, M * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
         CK(sn::launch_axpy_add(half, tmp, M, s), "axpy");
@@ -772,13 +848,17 @@ sn_status sn_adjoint_iterate(sn_mesh* m, const sn_iter_opts* o, const double* g,
         double rr = 0.0;
         CK(cudaMemcpyAsync(&rr, m->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
         CK(cudaStreamSynchronize(s), "sync");
+        sweep_clock.harvest();
+        dsa_clock.harvest();
         const double rn = std::sqrt(rr);
         if (it == 0) r0 = rn > 0 ? rn : 1.0;
         rel = rn / r0;
         if (stats && stats->residual_history && it < stats->history_len) stats->residual_history[it] = rel;
         CK(sn::launch_copy(mu, half, M, s), "copy");
         if (o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0) {
+            dsa_clock.begin(s);
             CK(sn::dsa_correct(dsa_for(m, true), r, mu, o->inner_tol, o->inner_max_iters, true, s), "DSA");
+            dsa_clock.end(s);
         }
         ++it;
         if (rel <= o->tol) {
@@ -787,12 +867,17 @@ sn_status sn_adjoint_iterate(sn_mesh* m, const sn_iter_opts* o, const double* g,
         }
     }
     CK(cudaStreamSynchronize(s), "sync");
+    sweep_clock.harvest();
+    dsa_clock.harvest();
     if (m->dsa) CK(sn::dsa_take_iters(dsa_for(m, true), s, &inner_total), "DSA iterations");
     if (stats) {
         stats->iters = it;
         stats->rel_residual = rel;
         stats->inner_iters_total = inner_total;
         stats->thick_fraction = m->dsa && o->dsa != SN_DSA_NONE ? (double)sn::dsa_thick_count(m->dsa) / m->ne : 0.0;
+        stats->n_sweeps = it;
+        stats->ms_sweep = sweep_clock.ms;
+        stats->ms_dsa = dsa_clock.ms;
         stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     if (!converged) return fail(SN_ERR_NOT_CONVERGED, "adjoint not converged after %d iterations (%.3e)", it, rel);
@@ -1101,6 +1186,7 @@ sn_status sn_batch_source_iterate(sn_batch* b, const sn_iter_opts* o, double* co
             stats[i].n_checkpoints = 0;
             stats[i].n_sweeps = iters[i];
             stats[i].ms_total = ms;
+            stats[i].ms_sweep = stats[i].ms_dsa = 0.0;  // one recorded iteration for all instances: no split
         }
     }
     if (!all) return fail(SN_ERR_NOT_CONVERGED, "some batch instances did not converge in %d iterations", o->max_iters);

@@ -58,7 +58,7 @@ class IterStats(C.Structure):
     _fields_ = [("iters", C.c_int), ("rel_residual", C.c_double), ("inner_iters_total", C.c_int),
                 ("thick_fraction", C.c_double), ("residual_history", C.POINTER(C.c_double)),
                 ("history_len", C.c_int), ("n_checkpoints", C.c_int), ("ms_total", C.c_double),
-                ("n_sweeps", C.c_int)]
+                ("n_sweeps", C.c_int), ("ms_sweep", C.c_double), ("ms_dsa", C.c_double)]
 
 
 def _load():
@@ -326,7 +326,7 @@ class Mesh:
         status = _lib.sn_source_iterate(self._h, C.byref(o), _ptr(phi), C.byref(st), _stream(stream))
         out = {"phi": phi, "iters": st.iters, "rel_residual": st.rel_residual, "inner_iters": st.inner_iters_total,
                "thick_fraction": st.thick_fraction, "ms": st.ms_total, "converged": status == 0,
-               "n_checkpoints": st.n_checkpoints, "sweeps": st.n_sweeps,
+               "n_checkpoints": st.n_checkpoints, "sweeps": st.n_sweeps, "ms_sweep": st.ms_sweep, "ms_dsa": st.ms_dsa,
                "history": hist[: st.iters + 1] if history else None}
         if status not in (0, 6):
             _check(status)
@@ -348,7 +348,8 @@ class Mesh:
         if status not in (0, 6):
             _check(status)
         return {"mu": mu, "iters": st.iters, "rel_residual": st.rel_residual, "converged": status == 0,
-                "inner_iters": st.inner_iters_total}
+                "inner_iters": st.inner_iters_total, "sweeps": st.n_sweeps, "ms_sweep": st.ms_sweep,
+                "ms_dsa": st.ms_dsa}
 
     def gradients(self, phi, mu, stream=None):
         import torch

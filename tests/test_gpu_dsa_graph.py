@@ -131,3 +131,18 @@ def test_float32_vcycle_leaves_the_fixed_point_alone(sn):
     ref = T.source_iterate(dsa=DSA(T, prob.thick_mask()), tol=1e-13, max_iters=400)
     assert r["converged"] and r["inner_iters"] > 0
     assert np.abs(r["phi"].cpu().numpy() - ref["phi"]).max() < 1e-9 * np.abs(ref["phi"]).max()
+
+
+@pytest.mark.parametrize("outer", ["si", "fgmres"])
+def test_solves_report_sweep_and_dsa_device_time(sn, outer):
+    """sn_iter_stats splits a solve's device time into transport updates and DSA solves."""
+    prob = inputs.config1()
+    m = sn.Mesh.from_problem(prob)
+    r = m.source_iterate(dsa="thick", outer=outer, tol=1e-8, max_iters=300)
+    assert r["converged"] and r["ms_sweep"] > 0 and r["ms_dsa"] > 0
+    assert r["ms_sweep"] + r["ms_dsa"] <= r["ms"] * 1.02 + 0.1
+    n = m.source_iterate(dsa="none", outer=outer, tol=1e-3, max_iters=60)
+    assert n["ms_dsa"] == 0 and n["ms_sweep"] > 0
+    g = torch.ones(m.shape, dtype=torch.float64, device="cuda")
+    a = m.adjoint_iterate(g, dsa="thick", outer=outer, tol=1e-8, max_iters=300)
+    assert a["converged"] and a["ms_sweep"] > 0 and a["ms_dsa"] > 0 and a["sweeps"] > 0

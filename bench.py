@@ -41,9 +41,6 @@ def cached_flops_per_item(n, dim, p):
     return 2 * n * n + 3 * n + 2 * dim * (p + 1) ** (dim - 1)
 
 
-# float64 peak of GB300, derived: 152 SMs x 2 FMA per clock x 2 flops x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-
 
 def step_ms_last(ev):
     """Elapsed time of the last (start, end) CUDA event pair."""
@@ -78,13 +75,14 @@ FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
 class ClockSampler:
     """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
 
-    def __init__(self, index=0):
+    def __init__(self, index=0, path=None):
+        import tempfile
         self.proc = None
         self.index = index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), f"sn_bench_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
@@ -273,7 +271,7 @@ def run_ours(args, rank, ws):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     iters = []
     n0 = sn.launch_count()
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clocks_csv) as clk:
         torch.cuda.synchronize()
         for k in range(args.steps):
             flush.zero_()
@@ -446,6 +444,7 @@ def main():
     ap.add_argument("--cpu-dirs", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-instance form")
+    ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi clock samples of the timed region here")
     args = ap.parse_args()
     rank, ws = dist_init(args)
     if args.impl == "reference":

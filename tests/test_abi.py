@@ -60,3 +60,32 @@ def test_invalid_descriptor_is_rejected_without_touching_the_gpu(libpath):
         sn.Mesh(3, 4, 4, 4, p=2, sn=4)
     with pytest.raises(sn.SnError):
         sn.Mesh(2, 4, 4, p=1, sn=5)
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every field of the ctypes mirrors sits at the C compiler's offset, and the sizes agree."""
+    import shutil
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    from paper_2001_09196_gb300 import sn
+    pairs = {"sn_mesh_desc": sn.MeshDesc, "sn_mesh_info": sn.MeshInfo, "sn_iter_opts": sn.IterOpts,
+             "sn_iter_stats": sn.IterStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sn.h"', "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        struct, field, value = line.split()
+        got[(struct, field)] = int(value)
+    import ctypes
+    for cname, cls in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)

@@ -503,8 +503,8 @@ cudaError_t record_krylov(DsaHierarchy* H, double tol, int max_iters) {
     cudaError_t err;
     if (!H->cap && (err = cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking)) != cudaSuccess) return err;
     if (!H->cap2 && (err = cudaStreamCreateWithFlags(&H->cap2, cudaStreamNonBlocking)) != cudaSuccess) return err;
-    if (H->pcg_graph) cudaGraphExecDestroy(H->pcg_graph);
-    H->pcg_graph = nullptr;
+    if (H->krylov_graph) cudaGraphExecDestroy(H->krylov_graph);
+    H->krylov_graph = nullptr;
     const long long count0 = g_launches.load();
     if ((err = cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return err;
     cudaGraph_t g = nullptr, body = nullptr;
@@ -517,9 +517,9 @@ cudaError_t record_krylov(DsaHierarchy* H, double tol, int max_iters) {
         cudaGraph_t g2 = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(H->cap, &g2);
         if (e == cudaSuccess) e = e2;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&H->pcg_graph, g2, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&H->krylov_graph, g2, 0);
         if (g2) cudaGraphDestroy(g2);
-        if (e != cudaSuccess) H->pcg_graph = nullptr;
+        if (e != cudaSuccess) H->krylov_graph = nullptr;
         return e;
     };
     cudaStreamCaptureStatus cs;
@@ -605,24 +605,24 @@ cudaError_t record_krylov(DsaHierarchy* H, double tol, int max_iters) {
     if (err != cudaSuccess) return finish(err);
     err = finish(cudaSuccess);
     if (err == cudaSuccess) {
-        H->pcg_tol = tol;
-        H->pcg_max = max_iters;
+        H->krylov_tol = tol;
+        H->krylov_max = max_iters;
     }
     return err;
 }
 
 // Solves D_ff x = b by one launch of the recorded Krylov solve; the iteration count stays on the
 // device (dsa_take_iters reads the running total).
-cudaError_t pcg(DsaHierarchy* H, double tol, int max_iters, cudaStream_t s) {
+cudaError_t krylov_solve(DsaHierarchy* H, double tol, int max_iters, cudaStream_t s) {
     cudaError_t err;
     const bool want32 = H->vcycle_mode == SN_VCYCLE_FP32 || (H->vcycle_mode == SN_VCYCLE_AUTO && tol >= 1e-8);
     if (want32 && (err = upload32(H)) != cudaSuccess) return err;
-    if (!H->pcg_graph || H->pcg_tol != tol || H->pcg_max != max_iters || H->pc32 != want32) {
+    if (!H->krylov_graph || H->krylov_tol != tol || H->krylov_max != max_iters || H->pc32 != want32) {
         H->pc32 = want32;
         if ((err = record_krylov(H, tol, max_iters)) != cudaSuccess) return err;
     }
     g_launches.fetch_add(H->pro_launches, std::memory_order_relaxed);
-    return cudaGraphLaunch(H->pcg_graph, s);
+    return cudaGraphLaunch(H->krylov_graph, s);
 }
 
 }  // namespace
@@ -641,7 +641,7 @@ void dsa_free(DsaHierarchy* H) {
     f(H->d_x); f(H->d_b); f(H->d_r); f(H->d_z); f(H->d_p); f(H->d_q); f(H->d_vr); f(H->d_vx);
     f(H->d_rh); f(H->d_sh); f(H->d_t);
     f(H->d_part); f(H->d_s); f(H->d_it); f(H->d_emask);
-    if (H->pcg_graph) cudaGraphExecDestroy(H->pcg_graph);
+    if (H->krylov_graph) cudaGraphExecDestroy(H->krylov_graph);
     if (H->cap) cudaStreamDestroy(H->cap);
     if (H->cap2) cudaStreamDestroy(H->cap2);
     delete H;
@@ -672,7 +672,7 @@ cudaError_t dsa_solve(DsaHierarchy* H, const double* b_full, double* x_full, dou
     const long long N0 = (long long)H->nt * H->n;
     SN_COUNT_LAUNCH();
     gather_kernel<<<nblk(N0), kBS, 0, s>>>(b_full, H->d_thick, nullptr, H->nt, H->n, H->d_b);
-    if ((err = pcg(H, tol, max_iters, s)) != cudaSuccess) return err;
+    if ((err = krylov_solve(H, tol, max_iters, s)) != cudaSuccess) return err;
     SN_COUNT_LAUNCH();
     scatter_set_kernel<<<nblk(N0), kBS, 0, s>>>(H->d_x, H->d_thick, H->nt, H->n, x_full);
     return cudaGetLastError();
@@ -688,7 +688,7 @@ cudaError_t dsa_correct(DsaHierarchy* H, const double* r, double* phi_out, doubl
     const long long N0 = (long long)H->nt * H->n;
     SN_COUNT_LAUNCH();
     gather_kernel<<<nblk(N0), kBS, 0, s>>>(r, H->d_thick, transpose ? nullptr : H->d_mass_sig, H->nt, H->n, H->d_b);
-    if ((err = pcg(H, tol, max_iters, s)) != cudaSuccess) return err;
+    if ((err = krylov_solve(H, tol, max_iters, s)) != cudaSuccess) return err;
     SN_COUNT_LAUNCH();
     scatter_add_kernel<<<nblk(N0), kBS, 0, s>>>(H->d_x, H->d_thick, transpose ? H->d_mass_sig : nullptr, H->nt, H->n,
                                                 phi_out);

@@ -58,9 +58,9 @@ struct DsaHierarchy {
     // The Krylov solve (PCG or BiCGStab) recorded as a CUDA graph whose WHILE conditional node
     // repeats one iteration until the device-side convergence test fails (no host
     // synchronisation per iteration)
-    cudaGraphExec_t pcg_graph = nullptr;
-    double pcg_tol = -1.0;
-    int pcg_max = -1;
+    cudaGraphExec_t krylov_graph = nullptr;
+    double krylov_tol = -1.0;
+    int krylov_max = -1;
     int* d_it = nullptr;                      // [0] iterations of the current solve, [1] running total
     unsigned char* d_emask = nullptr;         // per element: 1 = thick (Algorithm 1's restrictions)
     long long pro_launches = 0, body_launches = 0;  // kernels in the prologue / one loop iteration

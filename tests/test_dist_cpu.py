@@ -1,6 +1,7 @@
 """Multi-process (N > 1) paths on CPU ranks with the gloo backend.
 
-Every call of this build runs on one GPU, so the N > 1 logic is covered here: the max-over-ranks
+The library runs one process per GPU and the GPU tests use one GPU, so the N > 1 logic is covered
+here: the max-over-ranks
 timing and barrier used by `bench.py`, the reference arm launched the way the driver launches it
 (torch.distributed.run, two ranks), where rank 0 alone prints the JSON line, and the exchange step
 of a direction-sharded transport update (each rank sums its own directions, one sum-reduction of

@@ -1,9 +1,8 @@
 """Multi-process (N > 1) paths on CPU ranks with the gloo backend.
 
 The library runs one process per GPU and the GPU tests use one GPU, so the N > 1 logic is covered
-here: the max-over-ranks
-timing and barrier used by `bench.py`, the reference arm launched the way the driver launches it
-(torch.distributed.run, two ranks), where rank 0 alone prints the JSON line, and the exchange step
+here: the max-over-ranks timing and barrier used by `bench.py`, the reference arm launched by
+torch.distributed.run with two ranks (rank 0 alone prints the JSON line), and the exchange step
 of a direction-sharded transport update (each rank sums its own directions, one sum-reduction of
 the scalar flux completes the update), run on the oracle.
 """

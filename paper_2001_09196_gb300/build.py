@@ -2,7 +2,7 @@
 
 Usage: python -m paper_2001_09196_gb300.build [--force]
 Translation units compile in parallel; the link uses nvcc's static CUDA runtime so the
-library depends only on the driver.
+library depends only on the CUDA driver.
 """
 from __future__ import annotations
 

@@ -1,0 +1,106 @@
+"""CPU: the library's host assembly of the thick-subdomain DSA operator (sn::dsa_build, Sec. 4.1-4.2:
+Eq. SIP, Eq. NIP and Eq. NIP with the penalty of Eq. ModifiedF0, and the transposed operator the
+adjoint solves with) against the oracle's operator, element block by element block.
+
+The library assembles in the nodal Gauss-Legendre basis, the oracle in a modal Legendre basis; both
+use the (p+1)-point Gauss rule, so the nodal view of the oracle's matrix, V^{-T} D V^{-1}, must
+equal the library's to rounding (1e-12 relative to the largest entry).  A small driver
+(tests/dsa_host/dsa_dump.cpp) links the library's host setup sources and needs no GPU.
+"""
+import os
+import shutil
+import struct
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2001_09196_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2001_09196_gb300", "csrc")
+OPS = {"sip": 0, "nip": 1, "mnip": 2}
+
+
+@pytest.fixture(scope="module")
+def driver(tmp_path_factory):
+    cxx = shutil.which("g++")
+    cuda_inc = "/usr/local/cuda/include"
+    if not cxx or not os.path.exists(os.path.join(cuda_inc, "cuda_runtime.h")):
+        pytest.skip("needs g++ and the CUDA headers")
+    exe = str(tmp_path_factory.mktemp("dsa_host") / "dsa_dump")
+    subprocess.run([cxx, "-std=c++17", "-O2", "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-I", cuda_inc,
+                    os.path.join(ROOT, "tests", "dsa_host", "dsa_dump.cpp"), os.path.join(CSRC, "sn_dsa_setup.cpp"),
+                    os.path.join(CSRC, "sn_setup.cpp"), "-lpthread", "-o", exe], check=True)
+    return exe
+
+
+def _assemble(driver, tmp_path, prob, mask, op, transposed):
+    inp, out = tmp_path / "in.bin", tmp_path / "out.bin"
+    has_v = prob.dim == 2 and prob.vertices is not None
+    with open(inp, "wb") as f:
+        f.write(struct.pack("8i", prob.dim, prob.nx, prob.ny, prob.nz, prob.p, OPS[op], int(transposed), int(has_v)))
+        f.write(np.ascontiguousarray(prob.sigma_t, dtype=np.float64).tobytes())
+        f.write(np.ascontiguousarray(prob.sigma_s, dtype=np.float64).tobytes())
+        f.write(np.ascontiguousarray(mask, dtype=np.uint8).tobytes())
+        if has_v:
+            f.write(np.ascontiguousarray(prob.vertices, dtype=np.float64).tobytes())
+    subprocess.run([driver, str(inp), str(out)], check=True, capture_output=True)
+    raw = open(out, "rb").read()
+    status, nt, n, nnzb = struct.unpack_from("4i", raw, 0)
+    if status:
+        return None, bool(nt)
+    off = 16
+    thick = np.frombuffer(raw, np.int32, nt, off); off += 4 * nt
+    ptr = np.frombuffer(raw, np.int32, nt + 1, off); off += 4 * (nt + 1)
+    col = np.frombuffer(raw, np.int32, nnzb, off); off += 4 * nnzb
+    val = np.frombuffer(raw, np.float64, nnzb * n * n, off).reshape(nnzb, n, n)
+    D = np.zeros((nt * n, nt * n))
+    for r in range(nt):
+        for k in range(ptr[r], ptr[r + 1]):
+            D[r * n:(r + 1) * n, col[k] * n:(col[k] + 1) * n] = val[k]
+    return (thick, D), False
+
+
+def _void_free_c1():
+    prob = inputs.config1()
+    v = prob.sigma_t == 0
+    prob.sigma_t[v], prob.sigma_s[v] = 1.0, 0.9
+    return prob
+
+
+CASES = {
+    "c1": inputs.config1,
+    "c1_full": _void_free_c1,
+    "c2_jittered_q2": lambda: inputs.config2(n=16, block=4, p=2, sn=4),
+    "q3": lambda: inputs.config2d_fields(6, 3, 4, 81, "q3"),
+    "c3_q1": lambda: inputs.config3(n=4),
+    "c3_q2": lambda: inputs.config3(n=3, p=2),
+}
+
+
+@pytest.mark.parametrize("transposed", [False, True])
+@pytest.mark.parametrize("op", ["sip", "nip", "mnip"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_host_assembly_matches_the_oracle(driver, tmp_path, name, op, transposed):
+    from oracle import Transport
+    from oracle.dsa import DSA
+    prob = CASES[name]()
+    T = Transport(prob)
+    mask = np.ones(T.ne, dtype=np.uint8) if name == "c1_full" else prob.thick_mask().astype(np.uint8)
+    try:
+        ref = DSA(T, mask, operator=op)
+    except ValueError:  # mNIP next to a void: the library must refuse it too, as a void conflict
+        got, void_conflict = _assemble(driver, tmp_path, prob, mask, op, transposed)
+        assert got is None and void_conflict
+        return
+    got, _ = _assemble(driver, tmp_path, prob, mask, op, transposed)
+    assert got is not None
+    thick, D = got
+    assert np.array_equal(thick, ref.thick)
+    Dn = ref.nodal_matrix().toarray()
+    if transposed and op != "sip":
+        Dn = Dn.T
+    assert np.abs(D - Dn).max() <= 1e-12 * np.abs(Dn).max()
+    if op != "sip":
+        assert np.abs(Dn - Dn.T).max() > 1e-6 * np.abs(Dn).max()  # and the nonsymmetric ones are so

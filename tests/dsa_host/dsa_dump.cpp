@@ -6,6 +6,9 @@
 // float64 sigma_t[ne], sigma_s[ne]; uint8 mask[ne]; float64 vertices[(nx+1)(ny+1)][2] if 2D and
 // has_vertices.  Output: int32 status, nt, n, nnzb; int32 thick[nt], ptr[nt+1], col[nnzb];
 // float64 val[nnzb * n * n] (row-major blocks).  status 1 = setup refused (message on stderr).
+// With a third argument, the continuous multigrid levels go to that file: int32 count, then per
+// level int32 rows, prolongation rows, a_nnz, p_nnz, dense (0/1); CSR a (ptr, col, val), CSR p
+// (ptr, col, val; p maps this level to the next finer one) and, for the dense level, its inverse.
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -28,8 +31,8 @@ void put(FILE* f, const T* src, size_t count) {
 }  // namespace
 
 int main(int argc, char** argv) {
-    if (argc != 3) {
-        std::fprintf(stderr, "usage: dsa_dump input output\n");
+    if (argc != 3 && argc != 4) {
+        std::fprintf(stderr, "usage: dsa_dump input output [levels]\n");
         return 2;
     }
     FILE* in = std::fopen(argv[1], "rb");
@@ -94,6 +97,27 @@ int main(int argc, char** argv) {
     put(out, col.data(), col.size());
     put(out, H->l0.val.data(), H->l0.val.size());
     std::fclose(out);
+    if (argc == 4) {
+        FILE* lv = std::fopen(argv[3], "wb");
+        if (!lv) return 2;
+        const int32_t count = (int32_t)H->levels.size();
+        put(lv, &count, 1);
+        for (const sn::LevelC& L : H->levels) {
+            const int32_t meta[5] = {L.n, (int32_t)L.p_ptr.size() - 1, (int32_t)L.a_val.size(), (int32_t)L.p_val.size(),
+                                     L.dense_inv.empty() ? 0 : 1};
+            put(lv, meta, 5);
+            std::vector<int32_t> ap(L.a_ptr.begin(), L.a_ptr.end()), ac(L.a_col.begin(), L.a_col.end());
+            std::vector<int32_t> pp(L.p_ptr.begin(), L.p_ptr.end()), pc(L.p_col.begin(), L.p_col.end());
+            put(lv, ap.data(), ap.size());
+            put(lv, ac.data(), ac.size());
+            put(lv, L.a_val.data(), L.a_val.size());
+            put(lv, pp.data(), pp.size());
+            put(lv, pc.data(), pc.size());
+            put(lv, L.p_val.data(), L.p_val.size());
+            if (!L.dense_inv.empty()) put(lv, L.dense_inv.data(), L.dense_inv.size());
+        }
+        std::fclose(lv);
+    }
     delete H;  // host-only hierarchy: nothing was uploaded
     return 0;
 }

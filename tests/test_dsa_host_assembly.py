@@ -35,8 +35,8 @@ def driver(tmp_path_factory):
     return exe
 
 
-def _assemble(driver, tmp_path, prob, mask, op, transposed):
-    inp, out = tmp_path / "in.bin", tmp_path / "out.bin"
+def _assemble(driver, tmp_path, prob, mask, op, transposed, levels=False):
+    inp, out, lev = tmp_path / "in.bin", tmp_path / "out.bin", tmp_path / "levels.bin"
     has_v = prob.dim == 2 and prob.vertices is not None
     with open(inp, "wb") as f:
         f.write(struct.pack("8i", prob.dim, prob.nx, prob.ny, prob.nz, prob.p, OPS[op], int(transposed), int(has_v)))
@@ -45,7 +45,7 @@ def _assemble(driver, tmp_path, prob, mask, op, transposed):
         f.write(np.ascontiguousarray(mask, dtype=np.uint8).tobytes())
         if has_v:
             f.write(np.ascontiguousarray(prob.vertices, dtype=np.float64).tobytes())
-    subprocess.run([driver, str(inp), str(out)], check=True, capture_output=True)
+    subprocess.run([driver, str(inp), str(out)] + ([str(lev)] if levels else []), check=True, capture_output=True)
     raw = open(out, "rb").read()
     status, nt, n, nnzb = struct.unpack_from("4i", raw, 0)
     if status:
@@ -59,7 +59,31 @@ def _assemble(driver, tmp_path, prob, mask, op, transposed):
     for r in range(nt):
         for k in range(ptr[r], ptr[r + 1]):
             D[r * n:(r + 1) * n, col[k] * n:(col[k] + 1) * n] = val[k]
+    if levels:
+        return (thick, D, _read_levels(open(lev, "rb").read())), False
     return (thick, D), False
+
+
+def _read_levels(raw):
+    import scipy.sparse as sp
+    (count,) = struct.unpack_from("i", raw, 0)
+    off, out = 4, []
+    for _ in range(count):
+        rows, prow, annz, pnnz, dense = struct.unpack_from("5i", raw, off)
+        off += 20
+
+        def take(dtype, k):
+            nonlocal off
+            a = np.frombuffer(raw, dtype, k, off)
+            off += a.nbytes
+            return a
+        ap, ac, av = take(np.int32, rows + 1), take(np.int32, annz), take(np.float64, annz)
+        pp, pc, pv = take(np.int32, prow + 1), take(np.int32, pnnz), take(np.float64, pnnz)
+        A = sp.csr_matrix((av, ac, ap), shape=(rows, rows)).toarray()
+        P = sp.csr_matrix((pv, pc, pp), shape=(prow, rows)).toarray()
+        inv = take(np.float64, rows * rows).reshape(rows, rows) if dense else None
+        out.append((A, P, inv))
+    return out
 
 
 def _void_free_c1():
@@ -104,3 +128,25 @@ def test_host_assembly_matches_the_oracle(driver, tmp_path, name, op, transposed
     assert np.abs(D - Dn).max() <= 1e-12 * np.abs(Dn).max()
     if op != "sip":
         assert np.abs(Dn - Dn.T).max() > 1e-6 * np.abs(Dn).max()  # and the nonsymmetric ones are so
+
+
+@pytest.mark.parametrize("op", ["sip", "nip"])
+@pytest.mark.parametrize("name", ["c1_full", "c2_jittered_q2", "c3_q1"])
+def test_multigrid_hierarchy_is_galerkin(driver, tmp_path, name, op):
+    """The hierarchy behind the V-cycle: every continuous level's operator is P^T A P of the level
+    above, every prolongation row is an interpolation (weights summing to 1), and the coarsest
+    level holds the inverse of its operator."""
+    prob = CASES[name]()
+    mask = np.ones(prob.n_elem, dtype=np.uint8) if name == "c1_full" else prob.thick_mask().astype(np.uint8)
+    got, _ = _assemble(driver, tmp_path, prob, mask, op, False, levels=True)
+    _, D, levels = got
+    assert levels and levels[-1][2] is not None
+    fine = D
+    for A, P, inv in levels:
+        assert P.shape == (fine.shape[0], A.shape[0])
+        assert np.abs(P.sum(axis=1) - 1.0).max() < 1e-12
+        G = P.T @ fine @ P
+        assert np.abs(A - G).max() <= 1e-11 * np.abs(G).max()
+        fine = A
+    A, _, inv = levels[-1]
+    assert np.abs(inv @ A - np.eye(A.shape[0])).max() < 1e-8

@@ -5,7 +5,7 @@ adjoint solves with) against the oracle's operator, element block by element blo
 The library assembles in the nodal Gauss-Legendre basis, the oracle in a modal Legendre basis; both
 use the (p+1)-point Gauss rule, so the nodal view of the oracle's matrix, V^{-T} D V^{-1}, must
 equal the library's to rounding (1e-12 relative to the largest entry).  A small driver
-(tests/dsa_host/dsa_dump.cpp) links the library's host setup sources and needs no GPU.
+(tests/host_drivers/dsa_dump.cpp) links the library's host setup sources and needs no GPU.
 """
 import os
 import shutil
@@ -28,9 +28,9 @@ def driver(tmp_path_factory):
     cuda_inc = "/usr/local/cuda/include"
     if not cxx or not os.path.exists(os.path.join(cuda_inc, "cuda_runtime.h")):
         pytest.skip("needs g++ and the CUDA headers")
-    exe = str(tmp_path_factory.mktemp("dsa_host") / "dsa_dump")
+    exe = str(tmp_path_factory.mktemp("host_drivers") / "dsa_dump")
     subprocess.run([cxx, "-std=c++17", "-O2", "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-I", cuda_inc,
-                    os.path.join(ROOT, "tests", "dsa_host", "dsa_dump.cpp"), os.path.join(CSRC, "sn_dsa_setup.cpp"),
+                    os.path.join(ROOT, "tests", "host_drivers", "dsa_dump.cpp"), os.path.join(CSRC, "sn_dsa_setup.cpp"),
                     os.path.join(CSRC, "sn_setup.cpp"), "-lpthread", "-o", exe], check=True)
     return exe
 

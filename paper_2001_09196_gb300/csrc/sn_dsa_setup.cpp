@@ -64,39 +64,10 @@ Csr transpose(const Csr& A) {
     return T;
 }
 
-// C = A * B (row-wise accumulation with a dense marker).
-Csr multiply(const Csr& A, const Csr& B) {
-    Csr C;
-    C.rows = A.rows;
-    C.cols = B.cols;
-    C.ptr.assign(A.rows + 1, 0);
-    std::vector<int> mark(B.cols, -1);
-    std::vector<double> acc(B.cols, 0.0);
-    std::vector<int> used;
-    for (int r = 0; r < A.rows; ++r) {
-        used.clear();
-        for (int k = A.ptr[r]; k < A.ptr[r + 1]; ++k) {
-            const int a = A.col[k];
-            const double av = A.val[k];
-            for (int l = B.ptr[a]; l < B.ptr[a + 1]; ++l) {
-                const int c = B.col[l];
-                if (mark[c] != r) {
-                    mark[c] = r;
-                    acc[c] = 0.0;
-                    used.push_back(c);
-                }
-                acc[c] += av * B.val[l];
-            }
-        }
-        std::sort(used.begin(), used.end());
-        for (int c : used) {
-            C.col.push_back(c);
-            C.val.push_back(acc[c]);
-        }
-        C.ptr[r + 1] = (int)C.col.size();
-    }
-    return C;
-}
+// C = A * B, rows in parallel: each output row sums its products in the order A's row entries and
+// then B's row entries are met (so the result does not depend on the thread schedule), columns
+// ascending.
+Csr multiply(const Csr& A, const Csr& B);
 
 // In-place inverse of a small SPD-ish dense matrix (Gauss-Jordan, partial pivoting).
 bool invert(std::vector<double>& A, int n) {
@@ -228,6 +199,48 @@ void parallel_for(int n, F&& f) {
     work();
     for (auto& t : th) t.join();
 }
+
+namespace {
+
+Csr multiply(const Csr& A, const Csr& B) {
+    Csr C;
+    C.rows = A.rows;
+    C.cols = B.cols;
+    std::vector<std::vector<std::pair<int, double>>> rows(A.rows);
+    parallel_for(A.rows, [&](int r) {
+        std::vector<std::pair<int, double>>& row = rows[r];
+        for (int k = A.ptr[r]; k < A.ptr[r + 1]; ++k) {
+            const double av = A.val[k];
+            for (int l = B.ptr[A.col[k]]; l < B.ptr[A.col[k] + 1]; ++l) {
+                const int c = B.col[l];
+                bool found = false;
+                for (auto& pr : row)
+                    if (pr.first == c) {
+                        pr.second += av * B.val[l];
+                        found = true;
+                        break;
+                    }
+                if (!found) row.push_back({c, 0.0 + av * B.val[l]});  // as an accumulator that starts at 0
+            }
+        }
+        std::sort(row.begin(), row.end(), [](const std::pair<int, double>& x, const std::pair<int, double>& y) {
+            return x.first < y.first;
+        });
+    });
+    C.ptr.assign(A.rows + 1, 0);
+    for (int r = 0; r < A.rows; ++r) C.ptr[r + 1] = C.ptr[r] + (int)rows[r].size();
+    C.col.resize(C.ptr[A.rows]);
+    C.val.resize(C.ptr[A.rows]);
+    parallel_for(A.rows, [&](int r) {
+        for (size_t k = 0; k < rows[r].size(); ++k) {
+            C.col[C.ptr[r] + k] = rows[r][k].first;
+            C.val[C.ptr[r] + k] = rows[r][k].second;
+        }
+    });
+    return C;
+}
+
+}  // namespace
 
 DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sigma, int dsa_op, bool transposed,
                         std::string& err, bool* void_conflict) {
@@ -682,15 +695,34 @@ DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sig
 
     struct GridLevel { int nx, ny, nz; std::vector<int> gids; };  // cells per axis, active vertex grid ids
     GridLevel cur{m->nx, m->ny, dim == 3 ? m->nz : 0, vgrid};
+    // restriction to level 1, P^T, row by row: vertex v takes Pref[q][a] from node q of every
+    // element t that has v as corner a (the columns come out ascending, as a transpose gives them)
+    Csr R1;
+    R1.rows = nv;
+    R1.cols = P.rows;
+    R1.ptr.assign(nv + 1, 0);
+    for (int v = 0; v < nv; ++v) R1.ptr[v + 1] = R1.ptr[v] + (vt_ptr[v + 1] - vt_ptr[v]) * n;
+    R1.col.resize(R1.ptr[nv]);
+    R1.val.resize(R1.ptr[nv]);
+    parallel_for(nv, [&](int v) {
+        int pos = R1.ptr[v];
+        for (int s = vt_ptr[v]; s < vt_ptr[v + 1]; ++s) {
+            const int t = vt[s] / nc, a = vt[s] % nc;
+            for (int q = 0; q < n; ++q, ++pos) {
+                R1.col[pos] = t * n + q;
+                R1.val[pos] = Pref[(size_t)q * nc + a];
+            }
+        }
+    });
     Csr Acur;
-    Csr Pcur = P;
+    Csr Pcur = std::move(P);
     for (int lev = 1; lev < 32; ++lev) {
-        Csr Pt = transpose(Pcur);
+        Csr Pt = lev == 1 ? std::move(R1) : transpose(Pcur);
         Csr Ac = lev == 1 ? std::move(A1) : multiply(Pt, multiply(Acur, Pcur));
         LevelC L;
         L.n = Ac.rows;
-        L.p_ptr = Pcur.ptr; L.p_col = Pcur.col; L.p_val = Pcur.val;
-        L.r_ptr = Pt.ptr; L.r_col = Pt.col; L.r_val = Pt.val;
+        L.p_ptr = std::move(Pcur.ptr); L.p_col = std::move(Pcur.col); L.p_val = std::move(Pcur.val);
+        L.r_ptr = std::move(Pt.ptr); L.r_col = std::move(Pt.col); L.r_val = std::move(Pt.val);
         L.a_ptr = Ac.ptr; L.a_col = Ac.col; L.a_val = Ac.val;
         L.dinv.assign(L.n, 0.0);
         for (int r = 0; r < Ac.rows; ++r)
@@ -770,9 +802,9 @@ DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sig
             last.dense_inv = Dm;
             break;
         }
-        Acur = Ac;
-        Pcur = Pn;
-        cur = nxt;
+        Acur = std::move(Ac);
+        Pcur = std::move(Pn);
+        cur = std::move(nxt);
     }
     return H;
 }

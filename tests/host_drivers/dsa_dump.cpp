@@ -8,7 +8,8 @@
 // float64 val[nnzb * n * n] (row-major blocks).  status 1 = setup refused (message on stderr).
 // With a third argument, the continuous multigrid levels go to that file: int32 count, then per
 // level int32 rows, prolongation rows, a_nnz, p_nnz, dense (0/1); CSR a (ptr, col, val), CSR p
-// (ptr, col, val; p maps this level to the next finer one) and, for the dense level, its inverse.
+// (ptr, col, val; p maps this level to the next finer one), CSR r (the restriction, rows x
+// prolongation rows, p_nnz entries) and, for the dense level, its inverse.
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -114,6 +115,10 @@ int main(int argc, char** argv) {
             put(lv, pp.data(), pp.size());
             put(lv, pc.data(), pc.size());
             put(lv, L.p_val.data(), L.p_val.size());
+            std::vector<int32_t> rp(L.r_ptr.begin(), L.r_ptr.end()), rc(L.r_col.begin(), L.r_col.end());
+            put(lv, rp.data(), rp.size());
+            put(lv, rc.data(), rc.size());
+            put(lv, L.r_val.data(), L.r_val.size());
             if (!L.dense_inv.empty()) put(lv, L.dense_inv.data(), L.dense_inv.size());
         }
         std::fclose(lv);

@@ -79,10 +79,13 @@ def _read_levels(raw):
             return a
         ap, ac, av = take(np.int32, rows + 1), take(np.int32, annz), take(np.float64, annz)
         pp, pc, pv = take(np.int32, prow + 1), take(np.int32, pnnz), take(np.float64, pnnz)
+        rp, rc, rv = take(np.int32, rows + 1), take(np.int32, pnnz), take(np.float64, pnnz)
         A = sp.csr_matrix((av, ac, ap), shape=(rows, rows)).toarray()
         P = sp.csr_matrix((pv, pc, pp), shape=(prow, rows)).toarray()
+        R = sp.csr_matrix((rv, rc, rp), shape=(rows, prow)).toarray()
+        assert np.all(np.diff(rp) >= 0) and all(np.all(np.diff(rc[rp[i]:rp[i + 1]]) > 0) for i in range(rows))
         inv = take(np.float64, rows * rows).reshape(rows, rows) if dense else None
-        out.append((A, P, inv))
+        out.append((A, P, R, inv))
     return out
 
 
@@ -140,13 +143,14 @@ def test_multigrid_hierarchy_is_galerkin(driver, tmp_path, name, op):
     mask = np.ones(prob.n_elem, dtype=np.uint8) if name == "c1_full" else prob.thick_mask().astype(np.uint8)
     got, _ = _assemble(driver, tmp_path, prob, mask, op, False, levels=True)
     _, D, levels = got
-    assert levels and levels[-1][2] is not None
+    assert levels and levels[-1][3] is not None
     fine = D
-    for A, P, inv in levels:
+    for A, P, R, inv in levels:
         assert P.shape == (fine.shape[0], A.shape[0])
+        assert np.array_equal(R, P.T)                # the restriction is exactly P^T, columns ascending
         assert np.abs(P.sum(axis=1) - 1.0).max() < 1e-12
         G = P.T @ fine @ P
         assert np.abs(A - G).max() <= 1e-11 * np.abs(G).max()
         fine = A
-    A, _, inv = levels[-1]
+    A, _, _, inv = levels[-1]
     assert np.abs(inv @ A - np.eye(A.shape[0])).max() < 1e-8

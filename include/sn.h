@@ -156,7 +156,9 @@ sn_status sn_set_materials(sn_mesh* mesh, const double* sigma_t, const double* s
  * cancellation of the printed difference.  sigma, cv, T: n_elem doubles each, host if mem = 0,
  * device if mem = 1; dt, a_rad, c_light: the time step, the radiation constant and the speed of
  * light (the paper: 1e-3, 137.199, 2.9979e4 in NIF units).  Then as sn_set_materials.
- * SN_ERR_ARG unless sigma >= 0, C_v > 0, T >= 0 (finite) and dt, a_rad, c_light > 0.
+ * Synchronises the stream and uses the mesh's work vectors, so no other call on this mesh may be
+ * in flight.  SN_ERR_ARG unless sigma >= 0, C_v > 0, T >= 0 (finite) and dt, a_rad, c_light > 0;
+ * a refused call leaves the materials unchanged.
  */
 sn_status sn_set_pseudo_scattering(sn_mesh* mesh, const double* sigma, const double* cv, const double* T,
                                    double dt, double a_rad, double c_light, int mem, void* stream);

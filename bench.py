@@ -9,7 +9,10 @@ sweep, flux reduction, DSA solve and Krylov step inside the timed region; the pe
 operator cache and DSA hierarchy -- is timed separately as setup_ms and is inside e2e).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-For N > 1 (launched with torch.distributed.run) every rank solves its own replica.
+For N > 1 (launched with torch.distributed.run, one rank per GPU) the ranks solve the one problem
+together, sharded by direction: each rank sweeps nd/N of the directions of every transport update and
+one NCCL all-reduce of the partial scalar flux completes it (Eq. phi); the DSA step, the Krylov work
+and the convergence test run replicated ("scaling": "strong").  The other forms run at N = 1 only.
 """
 from __future__ import annotations
 
@@ -32,14 +35,32 @@ WORKLOAD = "256x256 jittered quads, DG Q2, S8 (40 dirs), thick/thin/void blocks,
 
 
 def flops_per_item(n):
+    """Float64 flops of the dense element factor-and-solve the method itself requires, per
+    element-direction: (2/3) n^3 + 6 n^2."""
     return (2.0 / 3.0) * n ** 3 + 6.0 * n ** 2
 
 
-def cached_flops_per_item(n, dim, p):
-    """Algorithmic float64 flops of one cached element solve: x = A_e^{-1} rhs (2 n^2), the source
-    and mass terms of rhs (3 n), the inflow face terms (2 flops per inflow trace value)."""
-    return 2 * n * n + 3 * n + 2 * dim * (p + 1) ** (dim - 1)
+def reuse_floor_flops(n):
+    """Float64 flops per element-direction when A_e is reused between sweeps: 2 n^2 (x = A_e^{-1} rhs)."""
+    return 2.0 * n * n
 
+
+def trace_bytes_per_item(n, dim, p):
+    """Algorithmic HBM bytes per element-direction: the inflow and outflow traces, 2 dim (p+1)^(dim-1)
+    float64 values (read once, written once)."""
+    return 8 * 2 * dim * (p + 1) ** (dim - 1)
+
+
+def element_bytes(n):
+    """Algorithmic HBM bytes per element and sweep: the scalar flux read and written (2 n float64)
+    and the three material values."""
+    return 8 * (2 * n + 3)
+
+
+def implementation_bytes_per_item(n, dim, p):
+    """Bytes the cached kernels read per element-direction in this implementation: A_e^{-1} (n^2
+    float64), psi_e written (n), inflow traces (dim (p+1)^(dim-1)), face flux factors (2D: 4)."""
+    return 8 * (n * n + n + dim * (p + 1) ** (dim - 1) + (4 if dim == 2 else 0))
 
 
 def step_ms_last(ev):
@@ -47,12 +68,6 @@ def step_ms_last(ev):
     import torch
     torch.cuda.synchronize()
     return ev[-1][0].elapsed_time(ev[-1][1])
-
-
-def bytes_per_item(n, dim, p):
-    """Algorithmic bytes of one cached element solve: A_e^{-1} (n^2 float64) read, psi_e (n) written,
-    inflow traces (dim faces x (p+1)^(dim-1) values) read, face flux factors (2D: 4) read."""
-    return 8 * (n * n + n + dim * (p + 1) ** (dim - 1) + (4 if dim == 2 else 0))
 
 
 def peaks():
@@ -63,13 +78,53 @@ def peaks():
         return {}
 
 
-# DRAM bytes per item of node_level_kernel<2,2,FP64> on this workload, from the ncu capture
-# summarised in profiles/node_level_kernel_fp64_c2_256x256_q2_s8.md (read + write, 3 launches)
-NODE_KERNEL_DRAM_BYTES_PER_ITEM = 1432.0
-
 # FP64 FMA peak: 152 SMs x 4 sub-partitions x 0.5 FP64 FMA/clk x 2 flop x 2.07 GHz (GB300 runs FP64 at
 # 1/64 of the FP32 rate); an FMA-chain probe on this GPU measured 1.01 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
+
+# DRAM bytes (read + write) per element-direction of the dominant sweep kernel, from an ncu
+# metrics-only capture (dram__bytes_read.sum + dram__bytes_write.sum) of the bench's own launch, per
+# (schedule, workload).  A schedule or kernel changed since its capture has no entry (traffic null).
+SWEEP_DRAM_BYTES_PER_ITEM = {}
+
+SCHEDULE_KERNEL = {"levels": "node_level_kernel", "dataflow": "node_dataflow_kernel", "static": "node_dataflow_kernel",
+                   "tiles": "tile_sweep_kernel", "barrier": "barrier_sweep_kernel"}
+
+
+def sweep_roofline(mesh, prob, sweep_ms, schedule, n_launch, workload_key):
+    """Roofline of the cached FP64 sweep (the dominant kernel).  Its binding roof is the float64
+    pipe: achieved = the reuse floor 2 n^2 flops per element-direction x element-directions per
+    launch / launch time, against the derived FP64 peak.  Beside it the HBM view with the
+    algorithmic bytes (traces per element-direction, flux and materials per element)."""
+    n, dim, p = mesh.n_nodes, prob.dim, prob.p
+    items = mesh.n_elem * mesh.n_dirs
+    launch_s = sweep_ms / 1e3 / max(n_launch, 1)
+    items_per_launch = items / max(n_launch, 1)
+    flops = reuse_floor_flops(n) * items_per_launch
+    achieved = flops / launch_s / 1e12
+    alg_bytes = trace_bytes_per_item(n, dim, p) * items + element_bytes(n) * mesh.n_elem
+    hbm = peaks().get("hbm_gbs")
+    hbm_peak = hbm or 6800.0
+    hbm_achieved = alg_bytes / (sweep_ms / 1e3) / 1e9
+    dram = SWEEP_DRAM_BYTES_PER_ITEM.get((schedule[0], workload_key))
+    kernel = SCHEDULE_KERNEL.get(schedule[0], schedule[0]) + f"<{dim},{p},FP64>"
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": None if dram is None else dram * items_per_launch,
+            "kernel": kernel, "schedule": list(schedule), "launches_per_sweep": n_launch,
+            "flops_per_elem_dir": reuse_floor_flops(n),
+            "peak_source": "derived: 152 SMs x 2 float64 FMA/clk x 2 flop x 2.07 GHz (of derived)",
+            "flops_what": "float64 reuse floor 2 n^2 per element-direction (A_e^{-1} applied; the "
+                          "factorisation, (2/3) n^3 + 6 n^2, is done once per material set)",
+            "sweep_ms": sweep_ms, "levels_on_critical_path": mesh.n_levels,
+            "us_per_level": 1e3 * sweep_ms / mesh.n_levels,
+            "hbm": {"algorithmic_bytes_per_sweep": alg_bytes,
+                    "bytes_what": f"{trace_bytes_per_item(n, dim, p)} B of traces per element-direction + "
+                                  f"{element_bytes(n)} B of flux and materials per element",
+                    "achieved_gbs": hbm_achieved, "peak_gbs": hbm_peak, "frac": hbm_achieved / hbm_peak,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6.8 TB/s"},
+            "implementation_bytes_per_elem_dir": implementation_bytes_per_item(n, dim, p),
+            "fp64_flops_factor_and_solve_per_elem_dir": flops_per_item(n)}
 
 
 class ClockSampler:
@@ -185,7 +240,7 @@ def run_reference(args, rank, ws):
     cores = 1
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": f"{dirs_per_step} of 40 directions per step"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"numpy oracle sweep of {dirs_per_step} directions per step on the full mesh"},
@@ -230,6 +285,81 @@ def batched_form(torch, sn, inputs, stream, flush, args):
             "sequential_fgmres_ms": sum(seq), "speedup_vs_sequential": sum(seq) / solve_ms}
 
 
+def other_workloads(torch, sn, inputs, stream, flush, time_sweeps):
+    """The other configurations of the workload list, each timed once (not part of value):
+    config 1 (16^2 Q1 S4, latency-bound solve), config 3 (64^3 Q1 S8, sigma_t h > 1 thick rule;
+    sweep throughput, roofline and time to 1e-8) and config 5 (128^2 Q1 S8 detector gradients:
+    forward solve, adjoint solve and gradients through the autograd Function)."""
+    from paper_2001_09196_gb300 import autograd
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), out
+
+    out = {}
+    # config 1
+    p1 = inputs.config1()
+    m1 = sn.Mesh.from_problem(p1)
+    o1 = dict(dsa="thick", tol=1e-8, inner_tol=1e-4, max_iters=500)
+    for outer in ("si", "fgmres"):
+        m1.source_iterate(outer=outer, **o1)
+        ms, r = timed(lambda: m1.source_iterate(outer=outer, **o1))
+        out.setdefault("c1", {})[f"fp64_{outer}"] = {"ms_to_tol": ms, "iters": r["iters"], "sweeps": r["sweeps"],
+                                                     "converged": r["converged"]}
+    out["c1"]["workload"] = "16x16 Q1 S4 (12 dirs), thick block, void, source corner; thick DSA to 1e-8"
+    del m1
+    # config 3
+    p3 = inputs.config3()
+    m3 = sn.Mesh.from_problem(p3)
+    sched3 = m3.autotune("fp64")
+    x3 = torch.as_tensor(inputs.random_phi(p3, 3), device="cuda")
+    ms3 = time_sweeps(m3, x3)
+    c0 = sn.launch_count()
+    m3.sweep(x3, precision="fp64")
+    nl3 = sn.launch_count() - c0 - 1
+    items3 = m3.n_elem * m3.n_nodes * m3.n_dirs
+    o3 = dict(dsa="thick", thick_rule="sigma_t_h", tol=1e-8, inner_tol=1e-4, max_iters=500, outer="fgmres")
+    phi3 = torch.zeros(m3.shape, dtype=torch.float64, device="cuda")
+    m3.source_iterate(phi=phi3, **o3)
+    ms_solve, r3 = timed(lambda: m3.source_iterate(phi=phi3, **o3))
+    out["c3"] = {"workload": "64^3 unit cube, Q1, S8 (80 dirs), log-uniform sigma_t, 10% void, thick where "
+                             "sigma_t h > 1; FP64 thick-DSA fGMRES(30) to 1e-8",
+                 "sweep_ms": ms3, "sweep_dof_dirs_per_s": items3 / (ms3 / 1e3),
+                 "fp32_sweep_ms": time_sweeps(m3, x3, precision="fp32"),
+                 "ms_to_tol": ms_solve, "iters": r3["iters"], "sweeps": r3["sweeps"], "converged": r3["converged"],
+                 "thick_fraction": r3["thick_fraction"], "solve_dof_dirs_per_s": r3["sweeps"] * items3 / (ms_solve / 1e3),
+                 "roofline": sweep_roofline(m3, p3, ms3, sched3, nl3, "c3")}
+    del m3, x3, phi3
+    # config 5
+    p5 = inputs.config5()
+    if True:
+        m5 = sn.Mesh.from_problem(p5)
+        # J = sum over the strip of the integral of phi: g = Gauss weights x (h/2)^2 on strip elements
+        xg, wg = np.polynomial.legendre.leggauss(p5.p + 1)
+        g5h = np.zeros((p5.n_elem, p5.n_nodes))
+        g5h[p5.extra["detector"].astype(bool)] = np.outer(wg, wg).ravel() * (0.5 / p5.nx) ** 2
+        g5 = torch.as_tensor(g5h, device="cuda")
+
+        def grad_once():
+            st, ss, q = (torch.tensor(a, dtype=torch.float64, device="cuda", requires_grad=True)
+                         for a in (p5.sigma_t, p5.sigma_s, p5.q))
+            phi = autograd.solve(m5, st, ss, q, solve_opts=dict(thick_rule="sigma_t_h", tol=1e-8),
+                                 adjoint_opts=dict(tol=1e-8))
+            (g5 * phi).sum().backward()
+            return st.grad
+        grad_once()
+        ms5, _ = timed(grad_once)
+        out["c5"] = {"workload": "128x128 Q1 S8, config-3-style fields, detector = right-edge 16x4 strip; forward "
+                                 "fGMRES + adjoint fGMRES (thick DSA, 1e-8) + gradients w.r.t. sigma_t, sigma_s, q",
+                     "ms_gradient": ms5}
+    return out
+
+
 def run_ours(args, rank, ws):
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -261,8 +391,13 @@ def run_ours(args, rank, ws):
         torch.cuda.synchronize()
         setup.append((time.perf_counter() - t0) * 1e3)
 
+    shard = {}
+    if ws > 1:  # this rank's directions; the exchange sums the partial updates over the ranks
+        shard = dict(directions=(rank * mesh.n_dirs // ws, (rank + 1) * mesh.n_dirs // ws),
+                     exchange=sn.torch_allreduce())
+
     def step():  # one whole solve from phi = 0 to 1e-8
-        return mesh.source_iterate(phi=phi, **opts)
+        return mesh.source_iterate(phi=phi, **shard, **opts)
 
     for _ in range(args.warmup):
         r = step()
@@ -288,102 +423,84 @@ def run_ours(args, rank, ws):
     barrier(ws)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = max_over_ranks(sum(step_ms) / 1e3, ws)
-    units = sum(iters) * units_per_sweep * ws
+    units = sum(iters) * units_per_sweep  # one problem, all ranks together
     value = units / total_s
     clocks = clk.summary()
 
-    # dominant kernel: the cached FP64 sweep, node_level_kernel<2,2,FP64> (one launch per level,
-    # captured in a CUDA graph with programmatic dependent launch).  Algorithmic bytes per
-    # element-direction: the cached inverse (N^2 float64), the angular flux written (N), the
-    # inflow traces (dim (p+1)^(dim-1)) and the four face flux factors.
-    sweeps = []
-    for _ in range(5):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        a.record(stream)
-        mesh.sweep(phi, precision="fp64")
-        b.record(stream)
-        torch.cuda.synchronize()
-        sweeps.append(a.elapsed_time(b))
-    sweep_ms = statistics.median(sweeps)
+    # dominant kernel: the cached FP64 sweep in the autotuned schedule, timed alone (median of 5
+    # sweeps, L2 flushed before each)
+    def time_sweeps(m, x, reps=5, precision="fp64"):
+        out = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a.record(stream)
+            m.sweep(x, precision=precision)
+            b.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return statistics.median(out)
+
+    sweep_ms = time_sweeps(mesh, phi)
     c0 = sn.launch_count()
     mesh.sweep(phi, precision="fp64")
-    n_launch_sweep = sn.launch_count() - c0 - 1  # level launches of one sweep (minus the flux reduction)
-    bytes_item = bytes_per_item(n, prob.dim, prob.p)
-    achieved = bytes_item * mesh.n_elem * mesh.n_dirs / (sweep_ms / 1e3) / 1e9
-    hbm = peaks().get("hbm_gbs")
-    items_per_launch = mesh.n_elem * mesh.n_dirs / n_launch_sweep
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm or 6800.0, "unit": "GB/s",
-                "frac": achieved / (hbm or 6800.0),
-                "traffic": NODE_KERNEL_DRAM_BYTES_PER_ITEM * items_per_launch,
-                "traffic_source": "ncu dram__bytes_read+write of three mid-sweep launches, per item, scaled "
-                                  "to the average launch (profiles/node_level_kernel_fp64_c2_256x256_q2_s8.md)",
-                "kernel": "node_level_kernel<2,2,FP64> (cached sweep)", "launches_per_sweep": n_launch_sweep,
-                "schedule": list(schedule),
-                "bytes_per_elem_dir": bytes_item,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else "fallback 6.8 TB/s",
-                "sweep_ms": sweep_ms, "levels_on_critical_path": mesh.n_levels,
-                "us_per_level": 1e3 * sweep_ms / mesh.n_levels,
-                "fp64_flops_per_elem_dir_uncached": flops_per_item(n),
-                "fp64_pipe": {"flops_per_elem_dir": cached_flops_per_item(n, prob.dim, prob.p),
-                              "achieved_tflops": cached_flops_per_item(n, prob.dim, prob.p) * mesh.n_elem * mesh.n_dirs
-                              / (sweep_ms / 1e3) / 1e12,
-                              "peak_tflops": FP64_PEAK_TFLOPS,
-                              "frac": cached_flops_per_item(n, prob.dim, prob.p) * mesh.n_elem * mesh.n_dirs
-                              / (sweep_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
-                              "peak_source": "derived: 152 SMs x 2 float64 FMA/clk x 2 flop x 2.07 GHz"}}
+    n_launch_sweep = sn.launch_count() - c0 - 1  # sweep launches (minus the flux reduction)
+    roofline = sweep_roofline(mesh, prob, sweep_ms, schedule, n_launch_sweep, "c2")
+    roofline["fp32_sweep_ms"] = time_sweeps(mesh, phi, precision="fp32")
 
-    # other forms (not part of value): FP32 element solves, FP32 + FP64 refinement,
-    # unaccelerated-by-Krylov source iteration with the same DSA (capped at 300 iterations),
-    # Algorithm 1, and the nonsymmetric DSA operators of Sec. 4.1 (Eq. NIP; Eq. NIP with the
-    # penalty of Eq. ModifiedF0, undefined where a thick element borders a void)
-    forms = {}
-    phi64 = phi.clone()  # the FP64 fGMRES solution of the last timed step
-    for prec, outer, dsa, op in (("fp32", "fgmres", "thick", "sip"), ("fp32_refine", "fgmres", "thick", "sip"),
-                                 ("fp64", "si", "thick", "sip"), ("fp64", "fgmres", "triangular", "sip"),
-                                 ("fp64", "fgmres", "thick", "nip"), ("fp64", "fgmres", "thick", "mnip")):
-        name = f"{prec}_{outer}" + {"triangular": "_triangular_dsa", "thick": ""}[dsa] + ("" if op == "sip" else f"_{op}_dsa")
-        o = dict(opts, precision=prec, outer=outer, max_iters=300, dsa=dsa, operator=op)
-        try:
-            mesh.source_iterate(phi=phi, **o)  # builds this operator's hierarchy outside the timing
-        except sn.SnError as e:
-            forms[name] = {"unavailable": str(e)}
-            continue
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        a.record(stream)
-        rr = mesh.source_iterate(phi=phi, **o)
-        b.record(stream)
-        torch.cuda.synchronize()
-        err = float((phi - phi64).abs().max() / phi64.abs().max())
-        forms[name] = {"ms_to_tol": a.elapsed_time(b), "iters": rr["iters"], "sweeps": rr["sweeps"],
-                       "inner_iters": rr["inner_iters"], "rel_residual": rr["rel_residual"],
-                       "converged": rr["converged"], "max_rel_err_vs_fp64_solution": err}
+    forms, hohl = {}, {}
+    if ws == 1:  # the other forms run on one GPU only
+        # other forms (not part of value): FP32 element solves, FP32 + FP64 refinement,
+        # unaccelerated-by-Krylov source iteration with the same DSA (capped at 300 iterations),
+        # Algorithm 1, and the nonsymmetric DSA operators of Sec. 4.1 (Eq. NIP; Eq. NIP with the
+        # penalty of Eq. ModifiedF0, undefined where a thick element borders a void)
+        forms = {}
+        phi64 = phi.clone()  # the FP64 fGMRES solution of the last timed step
+        for prec, outer, dsa, op in (("fp32", "fgmres", "thick", "sip"), ("fp32_refine", "fgmres", "thick", "sip"),
+                                     ("fp64", "si", "thick", "sip"), ("fp64", "fgmres", "triangular", "sip"),
+                                     ("fp64", "fgmres", "thick", "nip"), ("fp64", "fgmres", "thick", "mnip")):
+            name = f"{prec}_{outer}" + {"triangular": "_triangular_dsa", "thick": ""}[dsa] + ("" if op == "sip" else f"_{op}_dsa")
+            o = dict(opts, precision=prec, outer=outer, max_iters=300, dsa=dsa, operator=op)
+            try:
+                mesh.source_iterate(phi=phi, **o)  # builds this operator's hierarchy outside the timing
+            except sn.SnError as e:
+                forms[name] = {"unavailable": str(e)}
+                continue
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a.record(stream)
+            rr = mesh.source_iterate(phi=phi, **o)
+            b.record(stream)
+            torch.cuda.synchronize()
+            err = float((phi - phi64).abs().max() / phi64.abs().max())
+            forms[name] = {"ms_to_tol": a.elapsed_time(b), "iters": rr["iters"], "sweeps": rr["sweeps"],
+                           "inner_iters": rr["inner_iters"], "rel_residual": rr["rel_residual"],
+                           "converged": rr["converged"], "max_rel_err_vs_fp64_solution": err}
 
-    # hohlraum-like layout (Sec. 5.2 stand-in): pseudo-scattering materials formed on the device,
-    # FP64 thick-DSA fGMRES(30) to 1e-8 with the symmetric and the NIP operators
-    hohl = {}
-    lay = inputs.hohlraum_like(256, p=2, sn=8)
-    hm = sn.Mesh.from_problem(lay)
-    hm.autotune("fp64")
-    x = lay.extra
-    hm.set_pseudo_scattering(x["sigma"], x["cv"], x["T"], x["dt"], x["a_rad"], x["c_light"])
-    hphi = torch.zeros(hm.shape, dtype=torch.float64, device="cuda")
-    for op in ("sip", "nip"):
-        o = dict(opts, operator=op)
-        hm.source_iterate(phi=hphi, **o)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        a.record(stream)
-        rr = hm.source_iterate(phi=hphi, **o)
-        b.record(stream)
-        torch.cuda.synchronize()
-        hohl[f"fp64_fgmres_{op}_dsa"] = {"ms_to_tol": a.elapsed_time(b), "iters": rr["iters"], "sweeps": rr["sweeps"],
-                                         "inner_iters": rr["inner_iters"], "converged": rr["converged"]}
-    hohl.update({"workload": "hohlraum-like 256x256 jittered quads, DG Q2, S8; gold/helium/CH/hydrogen, laser spots "
-                             "at 0.4 keV; Eq. hohlraum_sigma/q materials; thick = sigma_s >= 1",
-                 "thick_fraction": float(np.mean(hm.materials()[1] >= 1.0))})
-    del hm, hphi
+        # hohlraum-like layout (Sec. 5.2 stand-in): pseudo-scattering materials formed on the device,
+        # FP64 thick-DSA fGMRES(30) to 1e-8 with the symmetric and the NIP operators
+        hohl = {}
+        lay = inputs.hohlraum_like(256, p=2, sn=8)
+        hm = sn.Mesh.from_problem(lay)
+        hm.autotune("fp64")
+        x = lay.extra
+        hm.set_pseudo_scattering(x["sigma"], x["cv"], x["T"], x["dt"], x["a_rad"], x["c_light"])
+        hphi = torch.zeros(hm.shape, dtype=torch.float64, device="cuda")
+        for op in ("sip", "nip"):
+            o = dict(opts, operator=op)
+            hm.source_iterate(phi=hphi, **o)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a.record(stream)
+            rr = hm.source_iterate(phi=hphi, **o)
+            b.record(stream)
+            torch.cuda.synchronize()
+            hohl[f"fp64_fgmres_{op}_dsa"] = {"ms_to_tol": a.elapsed_time(b), "iters": rr["iters"], "sweeps": rr["sweeps"],
+                                             "inner_iters": rr["inner_iters"], "converged": rr["converged"]}
+        hohl.update({"workload": "hohlraum-like 256x256 jittered quads, DG Q2, S8; gold/helium/CH/hydrogen, laser spots "
+                                 "at 0.4 keV; Eq. hohlraum_sigma/q materials; thick = sigma_s >= 1",
+                     "thick_fraction": float(np.mean(hm.materials()[1] >= 1.0))})
+        del hm, hphi
 
     # end to end through the C ABI with host buffers: H2D materials, solve, D2H phi
     st_h = torch.as_tensor(prob.sigma_t).pin_memory()
@@ -398,14 +515,15 @@ def run_ours(args, rank, ws):
         for hd, dd in ((st_h, st_d), (ss_h, ss_d), (q_h, q_d)):
             dd.copy_(hd, non_blocking=True)
         mesh.set_materials(st_d, ss_d, q_d)
-        rr = mesh.source_iterate(phi=phi, **opts)
+        rr = mesh.source_iterate(phi=phi, **shard, **opts)
         phi_h.copy_(phi, non_blocking=True)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_s = max_over_ranks(sum(e2e_ms) / 1e3, ws)
-    e2e_value = rr["sweeps"] * units_per_sweep * len(e2e_ms) * ws / e2e_s
+    e2e_value = rr["sweeps"] * units_per_sweep * len(e2e_ms) / e2e_s
 
-    batched = None if args.no_batch else batched_form(torch, sn, inputs, stream, flush, args)
+    batched = None if (args.no_batch or ws > 1) else batched_form(torch, sn, inputs, stream, flush, args)
+    workloads = None if (args.no_other or ws > 1) else other_workloads(torch, sn, inputs, stream, flush, time_sweeps)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -416,18 +534,19 @@ def run_ours(args, rank, ws):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "elements": mesh.n_elem, "dofs": mesh.n_elem * n,
                            "dirs": mesh.n_dirs, "dof_dirs_per_sweep": units_per_sweep,
                            "iters_per_step": iters, "l2": "256 MB buffer written between timed steps",
                            "sweep_schedule": list(schedule),
-                           "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+                           "parallelism": f"direction-sharded x{ws}" if ws > 1 else "1 GPU"},
                 "setup_ms": {"materials_cache_dsa_one_iteration": min(setup),
                              "what": "set_materials (device arrays) + operator cache + DSA hierarchy, then one "
                                      "fGMRES iteration; not in value, in e2e"},
                 "time_to_1e-8_ms": {"fp64_fgmres": sum(step_ms) / len(step_ms),
                                     **{k: v["ms_to_tol"] for k, v in forms.items() if v.get("converged")}},
                 "step_breakdown": breakdown, "forms": forms, "hohlraum_like": hohl, "batched": batched,
+                "workloads": workloads,
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": UNIT,
                         "h2d_bytes_per_step": 3 * prob.n_elem * 8,
@@ -444,6 +563,7 @@ def main():
     ap.add_argument("--cpu-dirs", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-instance form")
+    ap.add_argument("--no-other", action="store_true", help="skip configs 1, 3 and 5")
     ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi clock samples of the timed region here")
     args = ap.parse_args()
     rank, ws = dist_init(args)

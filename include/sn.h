@@ -45,7 +45,7 @@ typedef enum {
     SN_ERR_INNER_NOT_CONVERGED = 8  /* a DSA solve hit inner_max_iters (only if strict) */
 } sn_status;
 
-enum { SN_FP64 = 0, SN_FP32 = 1, SN_FP32_REFINE = 2 };          /* element-solve precision */
+enum { SN_FP64 = 0, SN_FP32 = 1, SN_FP32_REFINE = 2, SN_FP32_MIXED = 3 };  /* element-solve precision */
 enum { SN_DSA_NONE = 0, SN_DSA_FULL = 1, SN_DSA_THICK = 2, SN_DSA_TRIANGULAR = 3 };  /* DSA variant */
 enum { SN_THICK_SIGMA_S = 0, SN_THICK_SIGMA_T_H = 1, SN_THICK_MASK = 2 };
 enum { SN_DSA_SIGMA_S = 0, SN_DSA_SIGMA_T = 1 };
@@ -98,10 +98,15 @@ sn_status sn_mesh_get_info(const sn_mesh* mesh, sn_mesh_info* info);
  *   schedule 3 (operator cache on): one cooperative launch per sweep; every CTA takes its share of
  *   each level's items and the CTAs meet at a grid barrier between levels (bounded wait,
  *   SN_ERR_TIMEOUT after 4 s); param = CTAs per SM (at least 1).
+ *   schedule 4: as schedule 1, but with every warp of the grid resident and the work list dealt
+ *   out statically (warp w takes slices w, w + W, w + 2W, ... of the level-ordered list, W warps in
+ *   all) instead of claimed through a shared counter.
  *   Uncached solves (SN_FP32_REFINE, cache off) and the adjoint use schedule 0 instead of 2 or 3.
- * block: threads per block, a multiple of 32 in [32, 128] (schedules 0, 1), [32, 256] (2), [32, 512] (3).
+ * block: threads per block, a multiple of 32 in [32, 128] (schedules 0, 1, 4), [32, 256] (2),
+ * [32, 512] (3).
  * param: schedule 0: direction groups (0 or 1 = one chain, at most the number of directions);
- * schedule 1: blocks per SM (0 = occupancy limit); schedule 2: tile edge (<= 64); schedule 3: CTAs per SM.
+ * schedules 1 and 4: blocks per SM (0 = occupancy limit); schedule 2: tile edge (<= 64); schedule 3:
+ * CTAs per SM.
  */
 sn_status sn_mesh_set_schedule(sn_mesh* mesh, int schedule, int block, int param);
 
@@ -190,6 +195,19 @@ sn_status sn_sweep(sn_mesh* mesh, const double* phi_in, double* phi_out, int pre
 sn_status sn_sweep_directions(sn_mesh* mesh, const double* phi_in, double* phi_out, int d_begin, int d_end,
                               int precision, void* stream);
 
+/*
+ * Exchange step of a direction-sharded iteration (sn_iter_opts.exchange).  The transport update
+ * is a sum over directions (Eq. phi), so processes that each sweep their own range of directions
+ * complete one update by summing their partial scalar fluxes.  The library calls the function
+ * after it has enqueued this process's partial update on `stream`: phi_partial (device, n doubles,
+ * [elem][node]) holds sum_{d in range} w_d psi_d when the stream reaches that point, and must hold
+ * the sum over all processes when the stream continues past the call (for example an NCCL
+ * all-reduce enqueued on `stream`, or a synchronise, host all-reduce and copy back).  Every process
+ * must receive bitwise the same sum, so that all of them take the same convergence decisions.
+ * Return SN_OK, or any other status to end the iteration with that status.
+ */
+typedef sn_status (*sn_exchange_fn)(double* phi_partial, long long n, void* stream, void* ctx);
+
 typedef struct {
     int dsa;                 /* SN_DSA_NONE | SN_DSA_FULL | SN_DSA_THICK (Algorithm 2) | SN_DSA_TRIANGULAR (Algorithm 1) */
     int thick_rule;          /* SN_THICK_SIGMA_S (sigma_s >= eta, Sec. 4.2) | SN_THICK_SIGMA_T_H | SN_THICK_MASK */
@@ -199,7 +217,13 @@ typedef struct {
     double tol;              /* relative residual ||r^i|| / ||r^0|| (Euclidean, nodal) */
     double inner_tol;        /* relative residual of each DSA solve (PCG, or BiCGStab for NIP / mNIP) */
     int max_iters, inner_max_iters;
-    int precision;           /* SN_FP64 | SN_FP32 | SN_FP32_REFINE */
+    int precision;           /* SN_FP64 | SN_FP32 | SN_FP32_REFINE | SN_FP32_MIXED (fGMRES only): float32
+                                element solves in every Arnoldi step, float64 element solves for the true
+                                residual that starts each restart cycle; a cycle ends once its residual
+                                estimate fell by refine_drop (or after `restart` steps), so the float32
+                                operator error enters only as the inexactness of a correction and the
+                                iteration converges to the float64 fixed point (mixed-precision iterative
+                                refinement around flexible GMRES) */
     int checkpoint_every;    /* >0: copy phi^{k} to checkpoints after every k-th iteration */
     double* checkpoints;     /* device, max_checkpoints x n_elem x n_nodes, or NULL */
     int max_checkpoints;
@@ -212,6 +236,16 @@ typedef struct {
                                 SN_VCYCLE_AUTO (default: float32 when inner_tol >= 1e-8, else float64),
                                 SN_VCYCLE_FP64 or SN_VCYCLE_FP32.  The Krylov residuals, dot products and
                                 convergence test are float64 in every mode. */
+    int dir_begin, dir_end;  /* direction sharding (sn_source_iterate only): this process sweeps the
+                                directions dir_begin <= d < dir_end of every transport update and
+                                `exchange` sums the partial updates over processes; both 0 = all
+                                directions, no exchange.  The DSA step, the Krylov work and the
+                                convergence test run replicated on every process. */
+    sn_exchange_fn exchange; /* required with a direction range; see sn_exchange_fn */
+    void* exchange_ctx;      /* passed through to exchange */
+    double* exchange_buf;    /* optional device buffer (n_elem x n_nodes doubles) that the partial
+                                updates are written to and exchanged in; NULL = library scratch */
+    double refine_drop;      /* SN_FP32_MIXED: residual reduction that ends a restart cycle (0 = 1e-3) */
 } sn_iter_opts;
 
 typedef struct {
@@ -315,9 +349,10 @@ sn_status sn_get_angular_flux(sn_mesh* mesh, int d, int adjoint, int precision, 
 /*
  * sn_scalar_flux_noalloc: the scalar-flux reduction of a transport update without any device
  * allocation.  The paper has no counterpart; it exists for callers that cannot call cudaMalloc:
- * code recording a CUDA graph (allocation calls are not capturable), frameworks whose caching
- * allocator owns all device memory, and latency-critical loops that cannot afford cudaMalloc's
- * implicit synchronisation.  Computes, in float64 with the same summation order as sn_sweep,
+ * frameworks whose caching allocator owns all device memory (a cudaMalloc behind its back can fail
+ * or fragment the pool it manages), latency-critical loops that cannot afford cudaMalloc's implicit
+ * device synchronisation, and embedded hosts whose device memory budget is fixed at start-up.
+ * Computes, in float64 with the same summation order as sn_sweep,
  *     phi_out[i] = sum_d weights[d] * psi[d * n_values + i],
  *     *resid_norm2 = sum_i (phi_out[i] - phi_prev[i])^2     (phi_prev NULL means 0; resid_norm2 may be NULL).
  * psi (n_dirs x n_values), weights (n_dirs), phi_prev, phi_out (n_values) and resid_norm2 (1) are

@@ -242,5 +242,16 @@ class TriangularDSA:
 
 
 def thick_mask(prob):
-    """Thick elements: sigma_s >= eta (Sec. 3.3, Sec. 4.2; eta = 1 in Sec. 5.1), or sigma_t h > eta."""
-    return prob.thick_mask()
+    """Thick/thin split of the problem's elements (uint8 per element).
+
+    Rule "sigma_s" (the paper's, Sec. 3.3 and Sec. 4.2 with eta = 1 in Sec. 5.1): thick where
+    sigma_s >= eta.  Rule "sigma_t_h": thick where sigma_t h > eta with h the element width 1/nx (an
+    optically thick cell).  A void element (sigma_t = 0) is never thick under either rule.
+    """
+    st = np.asarray(prob.sigma_t, dtype=np.float64)
+    ss = np.asarray(prob.sigma_s, dtype=np.float64)
+    if prob.thick_rule == "sigma_s":
+        return ((ss >= prob.eta) & (st > 0)).astype(np.uint8)
+    if prob.thick_rule == "sigma_t_h":
+        return (st * (1.0 / prob.nx) > prob.eta).astype(np.uint8)
+    raise ValueError(f"unknown thick rule {prob.thick_rule!r}")

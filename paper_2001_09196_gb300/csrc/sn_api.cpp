@@ -268,6 +268,13 @@ sn_status sn_set_pseudo_scattering(sn_mesh* m, const double* sigma, const double
         if (!(std::isfinite(h[e]) && h[e] >= 0.0 && std::isfinite(h[ne + e]) && h[ne + e] > 0.0 &&
               std::isfinite(h[2 * ne + e]) && h[2 * ne + e] >= 0.0))
             return fail(SN_ERR_ARG, "need finite sigma >= 0, C_v > 0, T >= 0 (element %zu)", e);
+    // sigma b = 16 pi a c sigma T^3 and the emission sigma a c T^4 must stay finite (Eq. hohlraum_q)
+    for (size_t e = 0; e < ne; ++e) {
+        const double t = h[2 * ne + e], t3 = t * t * t;
+        const double sb = h[e] * (16.0 * M_PI * a_rad * c_light * t3);
+        if (!std::isfinite(sb) || !std::isfinite(h[e] * a_rad * c_light * t3 * t * 4.0 * M_PI))
+            return fail(SN_ERR_ARG, "sigma b = 16 pi a c sigma T^3 overflows at element %zu (T = %g)", e, t);
+    }
     CK(cudaMemcpyAsync(in, h.data(), 3 * ne * sizeof(double), cudaMemcpyHostToDevice, s), "copy");
     CK(sn::launch_pseudo_scattering(in, in + ne, in + 2 * ne, m->ne, dt, a_rad, c_light, out, out + ne, out + 2 * ne, s),
        "pseudo-scattering kernel");
@@ -380,7 +387,7 @@ sn_status sn_debug_stall_next_sweep(sn_mesh* m, double timeout_seconds) {
 
 sn_status sn_mesh_set_schedule(sn_mesh* m, int schedule, int block, int param) {
     if (!m) return fail(SN_ERR_ARG, "null mesh");
-    if (schedule < sn::SCHED_LEVELS || schedule > sn::SCHED_BARRIER) return fail(SN_ERR_ARG, "bad schedule");
+    if (schedule < sn::SCHED_LEVELS || schedule > sn::SCHED_STATIC) return fail(SN_ERR_ARG, "bad schedule");
     const int max_block = schedule == sn::SCHED_TILES ? 256 : (schedule == sn::SCHED_BARRIER ? 512 : 128);
     if (block < 32 || block > max_block || block % 32)
         return fail(SN_ERR_ARG, "block must be a multiple of 32 in [32, %d]", max_block);
@@ -388,7 +395,7 @@ sn_status sn_mesh_set_schedule(sn_mesh* m, int schedule, int block, int param) {
     if (schedule == sn::SCHED_TILES && param > 64) return fail(SN_ERR_ARG, "tile edge must be <= 64");
     if (schedule == sn::SCHED_LEVELS && param > m->nd) return fail(SN_ERR_ARG, "more direction groups than directions");
     const int groups = schedule == sn::SCHED_LEVELS ? std::max(param, 1) : m->level_groups;
-    const bool own_block = schedule == sn::SCHED_LEVELS || schedule == sn::SCHED_DATAFLOW;
+    const bool own_block = schedule == sn::SCHED_LEVELS || sn::dataflow_like(schedule);
     if ((own_block && m->block != block) || groups != m->level_groups) sn::drop_level_graphs(m);
     m->schedule = schedule;
     if (own_block) m->block = block;
@@ -471,12 +478,50 @@ static sn_status ensure_dsa_adjoint(sn_mesh* m, const sn_iter_opts* o) {
 // Hierarchy of the DSA step: D_ff, or D_ff^T in the adjoint iteration.
 static sn::DsaHierarchy* dsa_for(sn_mesh* m, bool adjoint) { return adjoint && m->dsa_t ? m->dsa_t : m->dsa; }
 
+// Direction sharding (sn_iter_opts.dir_begin / dir_end / exchange): this process sweeps a range of
+// directions and the caller's exchange sums the partial updates over processes (Eq. phi).
+static bool sharded(const sn_iter_opts* o) { return o->exchange != nullptr || o->dir_begin != 0 || o->dir_end != 0; }
+
+static sn_status check_shard(const sn_mesh* m, const sn_iter_opts* o) {
+    if (!sharded(o)) return SN_OK;
+    if (!o->exchange) return fail(SN_ERR_ARG, "a direction range needs an exchange function");
+    const int d1 = o->dir_begin == 0 && o->dir_end == 0 ? m->nd : o->dir_end;
+    if (o->dir_begin < 0 || d1 > m->nd || o->dir_begin >= d1)
+        return fail(SN_ERR_ARG, "direction range [%d, %d) not inside [0, %d)", o->dir_begin, d1, m->nd);
+    return SN_OK;
+}
+
+// out = sum_d w_d L_d^{-1}(q_scale q/(4 pi) + sigma_s phi_in/(4 pi)) over all directions: swept here,
+// or this process's range swept here and completed by the caller's exchange.
+static sn_status transport_update(sn_mesh* m, const sn_iter_opts* o, const double* phi_in, double* out, double q_scale,
+                                  cudaStream_t s, int precision = -1) {
+    if (precision < 0) precision = o->precision;
+    if (!sharded(o)) {
+        CK(sn::launch_sweep(m, phi_in, precision, q_scale, s), "sweep");
+        CK(sn::launch_phi_reduce(m, precision, nullptr, out, nullptr, s), "phi reduce");
+        return SN_OK;
+    }
+    const int d0 = o->dir_begin, d1 = o->dir_begin == 0 && o->dir_end == 0 ? m->nd : o->dir_end;
+    const long long M = (long long)m->ne * m->n;
+    double* buf = o->exchange_buf ? o->exchange_buf : out;
+    CK(sn::launch_sweep_range(m, phi_in, precision, d0, d1, s, q_scale), "sweep");
+    CK(sn::launch_phi_reduce(m, precision, nullptr, buf, nullptr, s, d0, d1), "phi reduce");
+    const sn_status st = o->exchange(buf, M, (void*)s, o->exchange_ctx);
+    if (st != SN_OK) return fail(st, "the exchange of a partial transport update returned status %d", (int)st);
+    if (buf != out) CK(cudaMemcpyAsync(out, buf, M * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    return SN_OK;
+}
+
 static sn_status check_opts(const sn_iter_opts* o) {
     if (!o) return fail(SN_ERR_ARG, "null opts");
     if (o->dsa < SN_DSA_NONE || o->dsa > SN_DSA_TRIANGULAR) return fail(SN_ERR_ARG, "bad dsa");
     if (o->dsa_operator < SN_DSA_OP_SIP || o->dsa_operator > SN_DSA_OP_MNIP) return fail(SN_ERR_ARG, "bad dsa_operator");
     if (o->dsa_vcycle < SN_VCYCLE_AUTO || o->dsa_vcycle > SN_VCYCLE_FP32) return fail(SN_ERR_ARG, "bad dsa_vcycle");
-    if (o->precision < SN_FP64 || o->precision > SN_FP32_REFINE) return fail(SN_ERR_ARG, "bad precision");
+    if (o->precision < SN_FP64 || o->precision > SN_FP32_MIXED) return fail(SN_ERR_ARG, "bad precision");
+    if (o->precision == SN_FP32_MIXED && o->outer != SN_OUTER_FGMRES)
+        return fail(SN_ERR_ARG, "SN_FP32_MIXED refines around fGMRES (outer = SN_OUTER_FGMRES)");
+    if (o->precision == SN_FP32_MIXED && !(o->refine_drop >= 0.0 && o->refine_drop < 1.0))
+        return fail(SN_ERR_ARG, "refine_drop must be in [0, 1)");
     if (!(o->tol >= 0) || o->max_iters < 1) return fail(SN_ERR_ARG, "bad tol / max_iters");
     if (o->dsa != SN_DSA_NONE && (!(o->inner_tol > 0) || o->inner_max_iters < 1))
         return fail(SN_ERR_ARG, "bad inner_tol / inner_max_iters");
@@ -558,6 +603,11 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
     bool converged = false;
     bool timed_out = false;
     SegmentClock sweep_clock, dsa_clock;
+    // SN_FP32_MIXED: float64 sweeps for the true residual, float32 sweeps inside the cycle, and a
+    // cycle ends once its residual estimate fell by `drop` (iterative refinement around fGMRES)
+    const bool mixed = o->precision == SN_FP32_MIXED;
+    const int prec_res = mixed ? SN_FP64 : o->precision, prec_op = mixed ? SN_FP32 : o->precision;
+    const double drop = mixed ? (o->refine_drop > 0.0 ? o->refine_drop : 1e-3) : 0.0;
     while (true) {
         // true residual r = sweep(x) - x (with the fixed source); adjoint: g + T^T x - x
         ++sweeps;
@@ -567,8 +617,8 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
             CK(sn::launch_adjoint_reduce(m, tmp, s), "adjoint reduce");
             CK(sn::launch_axpy_add(tmp, g_rhs, M, s), "add g");
         } else {
-            CK(sn::launch_sweep(m, x, o->precision, 1.0, s), "sweep");
-            CK(sn::launch_phi_reduce(m, o->precision, x, tmp, m->d_scalars, s), "phi reduce");
+            sn_status ust = transport_update(m, o, x, tmp, 1.0, s, prec_res);
+            if (ust != SN_OK) return ust;
         }
         sweep_clock.end(s);
         CK(sn::launch_axpy_norm(m, tmp, x, w, m->d_scalars, s), "residual");
@@ -609,8 +659,8 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
                     double* y = m->d_work + M;
                     CK(sn::dsa_select_thick(m->dsa, Zj, w, s), "Algorithm 1");
                     sweep_clock.begin(s);
-                    CK(sn::launch_sweep(m, w, o->precision, 0.0, s), "sweep");
-                    CK(sn::launch_phi_reduce(m, o->precision, nullptr, y, nullptr, s), "phi reduce");
+                    sn_status ust = transport_update(m, o, w, y, 0.0, s, prec_op);
+                    if (ust != SN_OK) return ust;
                     sweep_clock.end(s);
                     CK(sn::dsa_add_thin(m->dsa, y, Zj, s), "Algorithm 1");
                     ++sweeps;
@@ -622,8 +672,8 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
                 CK(sn::launch_adjoint_sweep(m, Zj, s), "adjoint sweep");
                 CK(sn::launch_adjoint_reduce(m, tmp, s), "adjoint reduce");
             } else {
-                CK(sn::launch_sweep(m, Zj, o->precision, 0.0, s), "sweep");
-                CK(sn::launch_phi_reduce(m, o->precision, nullptr, tmp, nullptr, s), "phi reduce");
+                sn_status ust = transport_update(m, o, Zj, tmp, 0.0, s, prec_op);
+                if (ust != SN_OK) return ust;
             }
             sweep_clock.end(s);
             ++sweeps;
@@ -662,6 +712,7 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
             rel = std::fabs(g[j + 1]) / r0;
             if (stats && stats->residual_history && it < stats->history_len) stats->residual_history[it] = rel;
             if (rel <= o->tol || hnext <= 1e-300) break;
+            if (mixed && std::fabs(g[j + 1]) <= drop * beta) break;  // this cycle's correction is done
             CK(sn::launch_normalize(w, M, part, hd + 2 * (k + 1), V + (size_t)(j + 1) * M, s), "normalize");
         }
         // x += Z y with H y = g (upper triangular)
@@ -699,7 +750,8 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
     if (st != SN_OK) return st;
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
-    if (o->precision == SN_FP32 && (st = ensure_psi32(m)) != SN_OK) return st;
+    if ((st = check_shard(m, o)) != SN_OK) return st;
+    if ((o->precision == SN_FP32 || o->precision == SN_FP32_MIXED) && (st = ensure_psi32(m)) != SN_OK) return st;
     if (o->dsa != SN_DSA_NONE && (st = ensure_dsa(m, o)) != SN_OK) return st;
     if (m->dsa) {  // the PCG iteration counter starts from zero for this solve
         int stale = 0;
@@ -717,10 +769,16 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
     int it = 0, inner_total = 0, nck = 0, extra_sweeps = 0;
     bool converged = false;
     SegmentClock sweep_clock, dsa_clock;
+    const bool shard = sharded(o);
     while (it < o->max_iters) {
         sweep_clock.begin(s);
-        CK(sn::launch_sweep(m, phi, o->precision, 1.0, s), "sweep");
-        CK(sn::launch_phi_reduce(m, o->precision, phi, half, m->d_scalars, s), "phi reduce");
+        if (!shard) {
+            CK(sn::launch_sweep(m, phi, o->precision, 1.0, s), "sweep");
+            CK(sn::launch_phi_reduce(m, o->precision, phi, half, m->d_scalars, s), "phi reduce");
+        } else {
+            if ((st = transport_update(m, o, phi, half, 1.0, s)) != SN_OK) return st;
+            CK(sn::launch_axpy_norm(m, half, phi, r, m->d_scalars, s), "residual");
+        }
         sweep_clock.end(s);
         double rr = 0.0;
         CK(cudaMemcpyAsync(&rr, m->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
@@ -753,8 +811,7 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
                 CK(sn::dsa_correct(m->dsa, r, w, o->inner_tol, o->inner_max_iters, false, s), "DSA");
                 dsa_clock.end(s);
                 sweep_clock.begin(s);
-                CK(sn::launch_sweep(m, w, o->precision, 0.0, s), "sweep");
-                CK(sn::launch_phi_reduce(m, o->precision, nullptr, y, nullptr, s), "phi reduce");
+                if ((st = transport_update(m, o, w, y, 0.0, s)) != SN_OK) return st;
                 sweep_clock.end(s);
                 CK(sn::dsa_tri_combine(m->dsa, w, r, y, phi, s), "Algorithm 1");
                 ++extra_sweeps;
@@ -814,6 +871,7 @@ sn_status sn_adjoint_iterate(sn_mesh* m, const sn_iter_opts* o, const double* g,
     sn_status st = check_opts(o);
     if (st != SN_OK) return st;
     if (o->dsa == SN_DSA_TRIANGULAR) return fail(SN_ERR_ARG, "the adjoint iteration has no triangular DSA");
+    if (sharded(o)) return fail(SN_ERR_ARG, "direction sharding is available in sn_source_iterate only");
     if ((st = ensure_lambda(m)) != SN_OK) return st;
     if (o->dsa != SN_DSA_NONE && (st = ensure_dsa_adjoint(m, o)) != SN_OK) return st;
     if (m->dsa) {  // the inner iteration counter starts from zero for this solve
@@ -1103,6 +1161,7 @@ sn_status sn_batch_source_iterate(sn_batch* b, const sn_iter_opts* o, double* co
     sn_status st = check_opts(o);
     if (st != SN_OK) return st;
     if (o->outer != SN_OUTER_SI) return fail(SN_ERR_ARG, "batches iterate with source iteration (SN_OUTER_SI)");
+    if (sharded(o)) return fail(SN_ERR_ARG, "batches shard by instance, not by direction");
     if (o->checkpoint_every > 0) return fail(SN_ERR_ARG, "checkpoints are not supported for batches");
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
@@ -1216,7 +1275,8 @@ const TuneChoice kCandidates[] = {{0, 32, 0, 0}, {0, 64, 0, 0}, {0, 128, 0, 0}, 
 const TuneChoice kMeshCandidates[] = {{0, 32, 0, 0}, {0, 64, 0, 0}, {0, 128, 0, 0}, {0, 32, 2, 0},
                                       {0, 32, 4, 0}, {0, 64, 8, 0}, {1, 128, 0, 0}, {1, 64, 2, 0},
                                       {2, 128, 8, 0}, {2, 256, 16, 0}, {3, 256, 1, 0}, {3, 512, 1, 0},
-                                      {3, 256, 2, 0}, {3, 128, 4, 0}};
+                                      {3, 256, 2, 0}, {3, 128, 4, 0}, {4, 128, 0, 0}, {4, 64, 0, 0},
+                                      {4, 128, 4, 0}, {4, 128, 2, 0}, {4, 32, 0, 0}};
 
 template <typename F>
 float time_ms(F&& run, cudaStream_t s, int reps) {

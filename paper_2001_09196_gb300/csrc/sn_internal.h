@@ -75,6 +75,8 @@ struct DataflowArgs {
     unsigned long long* next;        // chunk counter, zeroed before each launch
     int* error;                      // set to 1 when a wait times out
     unsigned long long timeout_ns;   // per-launch wait budget
+    long long static_warps;          // > 0: static assignment, warp w takes slices w, w + static_warps, ...
+                                     // (every warp of the grid resident); 0: slices claimed from `next`
 };
 
 struct LevelSets {
@@ -100,7 +102,9 @@ struct LevelSets {
     std::vector<cudaEvent_t> gevents;          // [0] fork, [1 + g] join of group g
 };
 
-enum { SCHED_LEVELS = 0, SCHED_DATAFLOW = 1, SCHED_TILES = 2, SCHED_BARRIER = 3 };
+enum { SCHED_LEVELS = 0, SCHED_DATAFLOW = 1, SCHED_TILES = 2, SCHED_BARRIER = 3, SCHED_STATIC = 4 };
+// Schedules whose kernels wait (bounded) on completion words of the dataflow kind.
+inline bool dataflow_like(int schedule) { return schedule == SCHED_DATAFLOW || schedule == SCHED_STATIC; }
 
 // Tiled schedule of the cached sweep: the mesh is cut into tiles of edge^dim elements; per
 // direction, the tiles of every strongly connected component of the tile upwind graph form one
@@ -298,7 +302,9 @@ cudaError_t launch_adjoint_sweep(sn_mesh* m, const double* mu, cudaStream_t s);
 cudaError_t launch_phi_reduce(sn_mesh* m, int precision, const double* phi_in, double* phi_out, double* d_rr,
                               cudaStream_t s, int d0 = 0, int d1 = -1);
 // forward sweep of directions d0 <= d < d1 only (level chain on the stream, any schedule)
-cudaError_t launch_sweep_range(sn_mesh* m, const double* phi_in, int precision, int d0, int d1, cudaStream_t s);
+// (q_scale = 0: the linear part of the update, no fixed source and vacuum inflow)
+cudaError_t launch_sweep_range(sn_mesh* m, const double* phi_in, int precision, int d0, int d1, cudaStream_t s,
+                               double q_scale = 1.0);
 cudaError_t launch_adjoint_reduce(sn_mesh* m, double* out, cudaStream_t s);
 cudaError_t launch_gradients(sn_mesh* m, const double* phi, double* gt, double* gs, double* gq, cudaStream_t s);
 cudaError_t launch_axpy_norm(sn_mesh* m, const double* a, const double* b, double* out, double* d_rr,

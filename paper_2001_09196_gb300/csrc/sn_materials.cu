@@ -26,7 +26,9 @@ __global__ void pseudo_scattering_kernel(const double* __restrict__ sigma, const
     const double cdt = cv[e] / dt;
     const double den = cdt + sb;
     sigma_t[e] = s;
-    sigma_s[e] = s * sb / den;
+    // sigma_ps <= sigma because den >= sigma b; when C_v/dt underflows to 0 the quotient can round
+    // one ulp above sigma, so it is capped at sigma (its exact value in that limit)
+    sigma_s[e] = fmin(s * sb / den, s);
     q[e] = four_pi * s * a_rad * c_light * t3 * t * cdt / den;
 }
 

@@ -795,6 +795,11 @@ __global__ void __launch_bounds__(128) sweep_level_kernel(SweepArgs a, long long
 // warp waits for belongs to an earlier level and was claimed by a warp that is running.  An
 // item waits (bounded, with back-off) until each upwind neighbour's completion word holds the
 // current epoch, solves, stores psi and publishes its own word with release semantics.
+// Static assignment (SCHED_STATIC): with every warp of the grid resident, warp w takes slices
+// w, w + W, w + 2W, ... of the list (W warps in all) instead of claiming them.  Each warp's slices
+// are in level order, so the unfinished slice earliest in the list waits only on finished items
+// and its warp has finished all of its earlier slices: no deadlock, and no shared counter whose
+// atomics every warp would queue on.
 __device__ __forceinline__ int ld_acquire(const int* p) {
     int v;
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -821,12 +826,18 @@ __global__ void __launch_bounds__(128) sweep_dataflow_kernel(SweepArgs a, Datafl
     const int lane = threadIdx.x & 31;
     const long long n_chunks = f.n_items >> 5;
     const unsigned long long deadline = globaltimer() + f.timeout_ns;
+    unsigned long long mine = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     while (true) {
         // lane 0 claims the chunk and reads the error word; the warp acts on one broadcast value
         unsigned long long c = 0;
         int failed = 0;
         if (lane == 0) {
-            c = atomicAdd(f.next, 1ull);
+            if (f.static_warps > 0) {
+                c = mine;
+                mine += (unsigned long long)f.static_warps;
+            } else {
+                c = atomicAdd(f.next, 1ull);
+            }
             failed = *(volatile int*)f.error;
         }
         c = __shfl_sync(0xffffffffu, c, 0);
@@ -908,11 +919,17 @@ __global__ void __launch_bounds__(128) node_dataflow_kernel(SweepArgs a, Dataflo
     const int src0 = slot < IPW ? slot * N : 0;
     const long long n_slices = (f.n_items >> 5) * SLICES;
     const unsigned long long deadline = globaltimer() + f.timeout_ns;
+    unsigned long long mine = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     while (true) {
         unsigned long long c = 0;
         int failed = 0;
         if (lane == 0) {
-            c = atomicAdd(f.next, 1ull);
+            if (f.static_warps > 0) {
+                c = mine;
+                mine += (unsigned long long)f.static_warps;
+            } else {
+                c = atomicAdd(f.next, 1ull);
+            }
             failed = *(volatile int*)f.error;
         }
         c = __shfl_sync(0xffffffffu, c, 0);
@@ -1574,6 +1591,8 @@ static cudaError_t launch_dataflow(sn_mesh* m, const SweepArgs& a, cudaStream_t 
     const long long cap = (warps_needed * 32 + m->block - 1) / m->block;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
+    // static assignment needs every warp resident: the grid never exceeds one wave
+    f.static_warps = m->schedule == SCHED_STATIC ? blocks * (m->block / 32) : 0;
     SN_COUNT_LAUNCH();
     if (cached) node_dataflow_kernel<DIM, P, MODE == 1 ? 1 : 0, ADJ><<<(unsigned)blocks, m->block, 0, s>>>(a, f, mu);
     else sweep_dataflow_kernel<DIM, P, MODE, ADJ><<<(unsigned)blocks, m->block, 0, s>>>(a, f, mu);
@@ -1882,7 +1901,7 @@ cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double
         else SN_DISPATCH(m->dim, m->p, (cerr = launch_tiles<D_, P_, 1>(m, a, s)));
         return cerr;
     }
-    if (m->schedule == SCHED_DATAFLOW) {
+    if (dataflow_like(m->schedule)) {
         if (precision == SN_FP64) SN_DISPATCH(m->dim, m->p, (launch_dataflow<D_, P_, 0>(m, a, s)));
         else if (precision == SN_FP32) SN_DISPATCH(m->dim, m->p, (launch_dataflow<D_, P_, 1>(m, a, s)));
         else SN_DISPATCH(m->dim, m->p, (launch_dataflow<D_, P_, 2>(m, a, s)));
@@ -1898,7 +1917,8 @@ cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double
 // Forward sweep of the directions d0 <= d < d1 only: the level work list of that range (built once
 // per range and kept) launched as one chain of level kernels on the stream.  The element solves
 // are those of the full sweep, so psi_d of these directions is bitwise the full sweep's.
-cudaError_t launch_sweep_range(sn_mesh* m, const double* phi_in, int precision, int d0, int d1, cudaStream_t s) {
+cudaError_t launch_sweep_range(sn_mesh* m, const double* phi_in, int precision, int d0, int d1, cudaStream_t s,
+                               double q_scale) {
     cudaError_t err = prepare_operator_cache(m, precision, s);
     if (err != cudaSuccess) return err;
     if (!m->range_items || m->range_d0 != d0 || m->range_d1 != d1) {
@@ -1919,7 +1939,8 @@ cudaError_t launch_sweep_range(sn_mesh* m, const double* phi_in, int precision, 
     }
     SweepArgs a = make_args(m);
     a.phi = phi_in;
-    a.q_scale = 1.0;
+    a.q_scale = q_scale;
+    if (q_scale == 0.0) a.psi_inc = 0.0;  // the linear part of the update has vacuum inflow
     a.psi = precision == SN_FP32 ? m->d_psi32 : m->d_psi;
     a.items = m->range_items;
     long long launches = 0;
@@ -1933,7 +1954,7 @@ cudaError_t launch_adjoint_sweep(sn_mesh* m, const double* mu, cudaStream_t s) {
     if (cerr != cudaSuccess) return cerr;
     SweepArgs a = make_args(m);
     a.psi = m->d_lambda;
-    if (m->schedule == SCHED_DATAFLOW) {
+    if (dataflow_like(m->schedule)) {
         SN_DISPATCH(m->dim, m->p, (launch_dataflow<D_, P_, 0, true>(m, a, s, mu)));
         return cudaGetLastError();
     }

@@ -86,13 +86,6 @@ class Problem:
     def n_dirs(self) -> int:
         return self.sn * (self.sn + 2) // (2 if self.dim == 2 else 1)
 
-    def thick_mask(self) -> np.ndarray:
-        """Thick/thin split (Sec. 3.3, Sec. 4.2): thick where sigma_s >= eta, or sigma_t*h > eta."""
-        if self.thick_rule == "sigma_s":
-            return (self.sigma_s >= self.eta).astype(np.uint8)
-        h = 1.0 / self.nx
-        return (self.sigma_t * h > self.eta).astype(np.uint8)
-
 
 def _centroids_uniform(nx, ny):
     i = np.arange(nx)

@@ -14,15 +14,16 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libsn.so")
 
-FP64, FP32, FP32_REFINE = 0, 1, 2
+FP64, FP32, FP32_REFINE, FP32_MIXED = 0, 1, 2, 3
 DSA_NONE, DSA_FULL, DSA_THICK, DSA_TRIANGULAR = 0, 1, 2, 3
 THICK_SIGMA_S, THICK_SIGMA_T_H, THICK_MASK = 0, 1, 2
 DSA_SIGMA_S, DSA_SIGMA_T = 0, 1
 DSA_OP_SIP, DSA_OP_NIP, DSA_OP_MNIP = 0, 1, 2
 _DSA_OP = {"sip": DSA_OP_SIP, "nip": DSA_OP_NIP, "mnip": DSA_OP_MNIP}
-_PREC = {"fp64": FP64, "fp32": FP32, "fp32_refine": FP32_REFINE}
+_PREC = {"fp64": FP64, "fp32": FP32, "fp32_refine": FP32_REFINE, "fp32_mixed": FP32_MIXED}
 _DSA = {"none": DSA_NONE, "full": DSA_FULL, "thick": DSA_THICK, "triangular": DSA_TRIANGULAR}
 _RULE = {"sigma_s": THICK_SIGMA_S, "sigma_t_h": THICK_SIGMA_T_H, "mask": THICK_MASK}
+SCHEDULES = ("levels", "dataflow", "tiles", "barrier", "static")
 
 STATUS = {0: "SN_OK", 1: "SN_ERR_ARG", 2: "SN_ERR_CUDA", 3: "SN_ERR_OOM", 4: "SN_ERR_CYCLE",
           5: "SN_ERR_VOID_FULL_DSA", 6: "SN_ERR_NOT_CONVERGED", 7: "SN_ERR_TIMEOUT",
@@ -51,7 +52,13 @@ class IterOpts(C.Structure):
                 ("inner_tol", C.c_double), ("max_iters", C.c_int), ("inner_max_iters", C.c_int),
                 ("precision", C.c_int), ("checkpoint_every", C.c_int), ("checkpoints", C.c_void_p),
                 ("max_checkpoints", C.c_int), ("warm_start", C.c_int), ("outer", C.c_int), ("restart", C.c_int),
-                ("dsa_operator", C.c_int), ("dsa_vcycle", C.c_int)]
+                ("dsa_operator", C.c_int), ("dsa_vcycle", C.c_int), ("dir_begin", C.c_int), ("dir_end", C.c_int),
+                ("exchange", C.c_void_p), ("exchange_ctx", C.c_void_p), ("exchange_buf", C.c_void_p),
+                ("refine_drop", C.c_double)]
+
+
+# sn_exchange_fn: sn_status (*)(double* phi_partial, long long n, void* stream, void* ctx)
+EXCHANGE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p)
 
 
 class IterStats(C.Structure):
@@ -143,11 +150,15 @@ def _stream(stream):
 
 def make_opts(dsa="thick", thick_rule="sigma_s", eta=1.0, mask=None, dsa_sigma="sigma_s", tol=1e-8,
               inner_tol=1e-4, max_iters=1000, inner_max_iters=200, precision="fp64", checkpoint_every=0,
-              checkpoints=None, warm_start=False, outer="si", restart=30, operator="sip", vcycle="auto"):
+              checkpoints=None, warm_start=False, outer="si", restart=30, operator="sip", vcycle="auto",
+              refine_drop=0.0):
     """Options of sn_source_iterate / sn_adjoint_iterate.  operator: the DSA operator D_ff,
     "sip" (symmetric, conjugate gradients), "nip" (Eq. NIP) or "mnip" (Eq. NIP with the penalty
     of Eq. ModifiedF0); the nonsymmetric two are solved by BiCGStab.  vcycle: arithmetic of the
-    multigrid preconditioner, "auto" (float32 when inner_tol >= 1e-8), "fp64" or "fp32"."""
+    multigrid preconditioner, "auto" (float32 when inner_tol >= 1e-8), "fp64" or "fp32".
+    precision: "fp64", "fp32", "fp32_refine" or "fp32_mixed" (fGMRES with float32 sweeps inside
+    each restart cycle and a float64 true residual between cycles; a cycle ends when its residual
+    estimate fell by refine_drop, 0 = 1e-3)."""
     o = IterOpts()
     _lib.sn_iter_opts_default(C.byref(o))
     o.dsa = _DSA[dsa] if isinstance(dsa, str) else int(dsa)
@@ -172,25 +183,72 @@ def make_opts(dsa="thick", thick_rule="sigma_s", eta=1.0, mask=None, dsa_sigma="
     o.restart = int(restart)
     o.dsa_operator = _DSA_OP[operator] if isinstance(operator, str) else int(operator)
     o.dsa_vcycle = {"auto": 0, "fp64": 1, "fp32": 2}[vcycle] if isinstance(vcycle, str) else int(vcycle)
+    o.refine_drop = float(refine_drop)
     o._keep = keep
     return o
+
+
+def torch_allreduce(group=None):
+    """An exchange for Mesh.source_iterate(directions=..., exchange=...): the sum over the processes
+    of a torch.distributed group.  NCCL reduces the CUDA tensor in place on the current stream; a
+    CPU backend (gloo) reduces a host copy and writes the sum back."""
+    import torch.distributed as dist
+
+    def exchange(t):
+        if dist.get_backend(group) == "nccl" or not t.is_cuda:
+            dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        else:
+            h = t.cpu()
+            dist.all_reduce(h, op=dist.ReduceOp.SUM, group=group)
+            t.copy_(h)
+    return exchange
 
 
 def scalar_flux_noalloc(psi, weights, phi_prev=None, phi_out=None, resid_norm2=None, stream=None):
     """phi_out = sum_d w_d psi_d and ||phi_out - phi_prev||^2 without device allocation in libsn.
 
-    psi: (n_dirs, n_values) float64 CUDA tensor; weights: (n_dirs,) float64 CUDA tensor.
-    Outputs are caller-provided (allocated here by torch only when not given).
+    psi: (n_dirs, ...) float64 CUDA tensor, n_values = the size of one direction's block; weights:
+    (n_dirs,) float64 CUDA tensor on the same
+    device; phi_prev (optional) and phi_out: n_values elements; resid_norm2: at least one element.
+    Outputs are caller-provided (allocated here by torch only when not given).  Every size, device
+    and aliasing rule is checked here, before anything reaches the GPU; the call runs with psi's
+    device current, so the library resolves its scratch array on that device.
     """
     import torch
-    nd = int(psi.shape[0])
-    m = int(psi.numel() // nd)
-    if phi_out is None:
-        phi_out = torch.empty(m, dtype=torch.float64, device=psi.device)
-    if resid_norm2 is None:
-        resid_norm2 = torch.empty(1, dtype=torch.float64, device=psi.device)
-    _check(_lib.sn_scalar_flux_noalloc(_ptr(psi), _ptr(weights), nd, m, _ptr(phi_prev), _ptr(phi_out),
-                                       _ptr(resid_norm2), _stream(stream)))
+    if not isinstance(psi, torch.Tensor) or psi.dim() < 2 or psi.shape[0] < 1:
+        raise ValueError("psi must have shape (n_dirs, ...) with n_dirs >= 1 and at least 2 dimensions")
+    nd, m = int(psi.shape[0]), int(psi[0].numel())
+    if weights is None or weights.numel() != nd:
+        raise ValueError(f"weights needs exactly n_dirs = {nd} elements")
+    if phi_prev is not None and phi_prev.numel() != m:
+        raise ValueError(f"phi_prev needs exactly n_values = {m} elements")
+    if phi_out is not None and phi_out.numel() != m:
+        raise ValueError(f"phi_out needs exactly n_values = {m} elements")
+    if resid_norm2 is not None and resid_norm2.numel() < 1:
+        raise ValueError("resid_norm2 needs at least one element")
+
+    def _overlap(a, b):
+        if a is None or b is None:
+            return False
+        a0, b0 = a.data_ptr(), b.data_ptr()
+        return a0 < b0 + b.numel() * b.element_size() and b0 < a0 + a.numel() * a.element_size()
+
+    for out in (phi_out, resid_norm2):
+        for other in (psi, weights, phi_prev):
+            if _overlap(out, other):
+                raise ValueError("outputs must not share storage with psi, weights or phi_prev")
+    if _overlap(phi_out, resid_norm2):
+        raise ValueError("phi_out and resid_norm2 must not overlap")
+    for t in (psi, weights, phi_prev, phi_out, resid_norm2):
+        if t is not None and t.device != psi.device:
+            raise ValueError("every tensor must be on psi's device")
+    with torch.cuda.device(psi.device):
+        if phi_out is None:
+            phi_out = torch.empty(m, dtype=torch.float64, device=psi.device)
+        if resid_norm2 is None:
+            resid_norm2 = torch.empty(1, dtype=torch.float64, device=psi.device)
+        _check(_lib.sn_scalar_flux_noalloc(_ptr(psi), _ptr(weights), nd, m, _ptr(phi_prev), _ptr(phi_out),
+                                           _ptr(resid_norm2), _stream(stream)))
     return phi_out, resid_norm2
 
 
@@ -234,9 +292,9 @@ class Mesh:
         return (self.n_elem, self.n_nodes)
 
     def set_schedule(self, schedule="dataflow", block=128, param=0):
-        """schedule "levels" | "dataflow" | "tiles" | "barrier"; param: direction groups (levels), per-SM
-        block cap (dataflow), tile edge (tiles) or CTAs per SM (barrier)."""
-        sched = {"levels": 0, "dataflow": 1, "tiles": 2, "barrier": 3}[schedule] if isinstance(schedule, str) else int(schedule)
+        """schedule "levels" | "dataflow" | "tiles" | "barrier" | "static"; param: direction groups
+        (levels), per-SM block cap (dataflow, static), tile edge (tiles) or CTAs per SM (barrier)."""
+        sched = SCHEDULES.index(schedule) if isinstance(schedule, str) else int(schedule)
         _check(_lib.sn_mesh_set_schedule(self._h, sched, int(block), int(param)))
 
     def set_operator_cache(self, mode="auto"):
@@ -252,7 +310,7 @@ class Mesh:
         a, b, c = C.c_int(), C.c_int(), C.c_int()
         _check(_lib.sn_mesh_autotune(self._h, _PREC.get(precision, precision), _stream(stream), C.byref(a),
                                      C.byref(b), C.byref(c)))
-        return ("levels", "dataflow", "tiles", "barrier")[a.value], b.value, c.value
+        return SCHEDULES[a.value], b.value, c.value
 
     def quadrature(self):
         dirs = np.zeros((self.n_dirs, 3))
@@ -311,19 +369,45 @@ class Mesh:
         _check(_lib.sn_sweep(self._h, _ptr(phi_in), _ptr(phi_out), _PREC.get(precision, precision), _stream(stream)))
         return phi_out
 
-    def source_iterate(self, phi=None, stream=None, history=0, **kw):
+    def source_iterate(self, phi=None, stream=None, history=0, directions=None, exchange=None, **kw):
+        """Eq. DSA_fp (source iteration) or fGMRES with the DSA preconditioner; see make_opts.
+
+        directions = (d_begin, d_end) with exchange: a direction-sharded iteration.  This process
+        sweeps only its directions; exchange(t) receives each partial update as a float64 CUDA tensor
+        of shape (n_elem, n_nodes) and must replace it in place by the sum over all processes
+        (torch_allreduce builds one from a torch.distributed process group)."""
         import torch
         if phi is None:
             phi = torch.zeros(self.shape, dtype=torch.float64, device="cuda")
         if "warm_start" not in kw:
             kw["warm_start"] = False
         o = make_opts(**kw)
+        failure = []
+        if directions is not None or exchange is not None:
+            if directions is None or exchange is None:
+                raise ValueError("a direction-sharded iteration needs both directions and exchange")
+            buf = torch.empty(self.shape, dtype=torch.float64, device=phi.device)
+
+            def _cb(ptr, n, strm, ctx):
+                try:
+                    exchange(buf)
+                    return 0
+                except Exception as e:  # reported after the call returns
+                    failure.append(e)
+                    return 1
+            cb = EXCHANGE_FN(_cb)
+            o.dir_begin, o.dir_end = int(directions[0]), int(directions[1])
+            o.exchange = C.cast(cb, C.c_void_p)
+            o.exchange_buf = buf.data_ptr()
+            o._keep.extend([cb, buf])
         st = IterStats()
         hist = np.zeros(max(history, 0))
         if history:
             st.residual_history = hist.ctypes.data_as(C.POINTER(C.c_double))
             st.history_len = history
         status = _lib.sn_source_iterate(self._h, C.byref(o), _ptr(phi), C.byref(st), _stream(stream))
+        if failure:
+            raise failure[0]
         out = {"phi": phi, "iters": st.iters, "rel_residual": st.rel_residual, "inner_iters": st.inner_iters_total,
                "thick_fraction": st.thick_fraction, "ms": st.ms_total, "converged": status == 0,
                "n_checkpoints": st.n_checkpoints, "sweeps": st.n_sweeps, "ms_sweep": st.ms_sweep, "ms_dsa": st.ms_dsa,
@@ -409,7 +493,7 @@ class Batch:
         a, b, c = C.c_int(), C.c_int(), C.c_int()
         _check(_lib.sn_batch_autotune(self._h, _PREC.get(precision, precision), _stream(stream), C.byref(a),
                                       C.byref(b), C.byref(c)))
-        return ("levels", "dataflow", "tiles", "barrier")[a.value], b.value, c.value
+        return SCHEDULES[a.value], b.value, c.value
 
     @staticmethod
     def _ptrs(tensors):

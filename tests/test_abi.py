@@ -89,3 +89,31 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_noalloc_binding_checks_run_before_the_library(libpath):
+    """The no-allocation flux binding refuses bad sizes and aliasing before any pointer reaches the
+    library (CPU tensors here: every check fires before the binding asks for a device pointer)."""
+    import torch
+    from paper_2001_09196_gb300 import sn
+    f64 = dict(dtype=torch.float64)
+    psi = torch.zeros(3, 10, **f64)
+    w = torch.ones(3, **f64)
+    with pytest.raises(ValueError, match="n_dirs"):
+        sn.scalar_flux_noalloc(torch.zeros(30, **f64), w)
+    with pytest.raises(ValueError, match="weights"):
+        sn.scalar_flux_noalloc(psi, torch.ones(2, **f64))
+    with pytest.raises(ValueError, match="phi_prev"):
+        sn.scalar_flux_noalloc(psi, w, phi_prev=torch.zeros(9, **f64))
+    with pytest.raises(ValueError, match="phi_out"):
+        sn.scalar_flux_noalloc(psi, w, phi_out=torch.zeros(11, **f64))
+    with pytest.raises(ValueError, match="resid_norm2"):
+        sn.scalar_flux_noalloc(psi, w, phi_out=torch.zeros(10, **f64), resid_norm2=torch.zeros(0, **f64))
+    prev = torch.zeros(10, **f64)
+    with pytest.raises(ValueError, match="share storage"):
+        sn.scalar_flux_noalloc(psi, w, phi_prev=prev, phi_out=prev)
+    with pytest.raises(ValueError, match="share storage"):
+        sn.scalar_flux_noalloc(psi, w, phi_out=psi[0])
+    buf = torch.zeros(11, **f64)
+    with pytest.raises(ValueError, match="overlap"):
+        sn.scalar_flux_noalloc(psi, w, phi_out=buf[:10], resid_norm2=buf[9:])

@@ -86,3 +86,26 @@ def test_direction_sharded_update_with_gloo(tmp_path):
     mp.spawn(_shard_main, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
     got, ref = np.load(tmp_path / "reduced.npy"), np.load(tmp_path / "full.npy")
     assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def _exchange_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from paper_2001_09196_gb300 import sn
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ex = sn.torch_allreduce()
+    t = torch.arange(12, dtype=torch.float64).reshape(3, 4) * (rank + 1)
+    ex(t)  # in place, as the library's exchange step expects
+    torch.save(t, os.path.join(out_dir, f"ex{rank}.pt"))
+    dist.destroy_process_group()
+
+
+def test_exchange_function_sums_partial_updates_in_place(tmp_path):
+    """The exchange the binding hands to a direction-sharded iteration replaces each rank's partial
+    update by the sum over ranks, in place and identically on every rank."""
+    import torch.multiprocessing as mp
+    mp.spawn(_exchange_main, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    a, b = (torch.load(tmp_path / f"ex{r}.pt") for r in range(2))
+    expect = torch.arange(12, dtype=torch.float64).reshape(3, 4) * 3
+    assert torch.equal(a, expect) and torch.equal(b, expect)

@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 from paper_2001_09196_gb300 import inputs
+from oracle.dsa import thick_mask
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2001_09196_gb300", "csrc")
@@ -114,7 +115,7 @@ def test_host_assembly_matches_the_oracle(driver, tmp_path, name, op, transposed
     from oracle.dsa import DSA
     prob = CASES[name]()
     T = Transport(prob)
-    mask = np.ones(T.ne, dtype=np.uint8) if name == "c1_full" else prob.thick_mask().astype(np.uint8)
+    mask = np.ones(T.ne, dtype=np.uint8) if name == "c1_full" else thick_mask(prob).astype(np.uint8)
     try:
         ref = DSA(T, mask, operator=op)
     except ValueError:  # mNIP next to a void: the library must refuse it too, as a void conflict
@@ -140,7 +141,7 @@ def test_multigrid_hierarchy_is_galerkin(driver, tmp_path, name, op):
     above, every prolongation row is an interpolation (weights summing to 1), and the coarsest
     level holds the inverse of its operator."""
     prob = CASES[name]()
-    mask = np.ones(prob.n_elem, dtype=np.uint8) if name == "c1_full" else prob.thick_mask().astype(np.uint8)
+    mask = np.ones(prob.n_elem, dtype=np.uint8) if name == "c1_full" else thick_mask(prob).astype(np.uint8)
     got, _ = _assemble(driver, tmp_path, prob, mask, op, False, levels=True)
     _, D, levels = got
     assert levels and levels[-1][3] is not None

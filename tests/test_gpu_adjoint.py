@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2001_09196_gb300 import inputs
+from oracle.dsa import thick_mask
 
 pytestmark = pytest.mark.gpu
 
@@ -44,8 +45,8 @@ def test_autograd_matches_oracle_gradients(lib):
     strip = np.zeros(prob.n_elem, dtype=np.uint8)
     strip[[6, 7, 14, 15]] = 1
     T = Transport(prob)
-    phi_ref = T.source_iterate(dsa=DSA(T, prob.thick_mask()), tol=1e-15, max_iters=3000)["phi"]
-    mu_m, _, _ = adjoint.adjoint_iterate(T, adjoint.detector_modal(T, strip), dsa=DSA(T, prob.thick_mask()), tol=1e-15)
+    phi_ref = T.source_iterate(dsa=DSA(T, thick_mask(prob)), tol=1e-15, max_iters=3000)["phi"]
+    mu_m, _, _ = adjoint.adjoint_iterate(T, adjoint.detector_modal(T, strip), dsa=DSA(T, thick_mask(prob)), tol=1e-15)
     gt, gs, gq = adjoint.gradients(T, phi_ref, mu_m)
     mesh = sn.Mesh.from_problem(prob)
     st, ss, q = (torch.tensor(a, dtype=torch.float64, device="cuda", requires_grad=True)
@@ -98,7 +99,7 @@ def test_gradients_match_finite_differences_config5(lib):
     sn, ag = lib
     prob = inputs.config5()
     strip = prob.extra["detector"]
-    mask = prob.thick_mask()
+    mask = thick_mask(prob)
     mesh = sn.Mesh.from_problem(prob)
     st, ss, q = (torch.tensor(a, dtype=torch.float64, device="cuda", requires_grad=True)
                  for a in (prob.sigma_t, prob.sigma_s, prob.q))

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2001_09196_gb300 import inputs
+from oracle.dsa import thick_mask
 
 pytestmark = pytest.mark.gpu
 
@@ -86,5 +87,5 @@ def test_single_element_solution_matches_the_oracle(sn):
     T = Transport(prob)
     m = sn.Mesh.from_problem(prob)
     r = m.source_iterate(dsa="thick", tol=1e-12, inner_tol=1e-13, max_iters=200)
-    ref = T.source_iterate(dsa=DSA(T, prob.thick_mask()), tol=1e-13, max_iters=400)
+    ref = T.source_iterate(dsa=DSA(T, thick_mask(prob)), tol=1e-13, max_iters=400)
     assert r["converged"] and _rel(r["phi"], ref["phi"]) < 1e-10

@@ -2,13 +2,16 @@
 of Eq. ModifiedF0) and their BiCGStab solves, through the C ABI, against the CPU oracle.
 
 Tolerances as for the symmetric operator: 1e-12 relative for operator products, 1e-9 for solves
-to a 1e-13 inner tolerance and for converged solutions, 1e-10 for a fixed number of iterates with
-1e-14 inner solves.
+to a 1e-13 inner tolerance and for converged solutions, and for a fixed number of iterates with
+1e-14 inner solves the derived tolerance of tests/tolerances.py (1e-12, widened by the DSA step's
+rounding amplification c/(1-c) where that exceeds it).
 """
 import numpy as np
 import pytest
 
 from paper_2001_09196_gb300 import inputs
+from oracle.dsa import thick_mask
+from tolerances import dsa_iterate_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -76,7 +79,7 @@ def _dsa(name, cache, op):
     prob, T, ops = _case(name, cache)
     if op not in ops:
         try:
-            ops[op] = DSA(T, prob.thick_mask(), operator=op)
+            ops[op] = DSA(T, thick_mask(prob), operator=op)
         except ValueError:
             ops[op] = None
     return ops[op]
@@ -133,7 +136,7 @@ def test_iterate_parity(sn, cache, name, op):
                          inner_tol=1e-14, inner_max_iters=1000)
     ref = T.source_iterate(dsa=d, tol=0.0, max_iters=K)
     assert r["iters"] == K and r["inner_iters"] > 0
-    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) < 1e-10
+    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) <= dsa_iterate_tol(prob, thick_mask(prob))
 
 
 @pytest.mark.parametrize("name", ["c1", "c3_8"])
@@ -159,7 +162,7 @@ def test_adjoint_with_nip_uses_the_transposed_operator(sn, outer):
     det = np.zeros(prob.n_elem, dtype=np.uint8)
     det[[6, 7, 14, 15]] = 1
     T = Transport(prob)
-    d = DSA(T, prob.thick_mask(), operator="nip")
+    d = DSA(T, thick_mask(prob), operator="nip")
     assert d.thick.size
     g_m = adjoint.detector_modal(T, det)
     g_n = np.linalg.solve(T.V.T, g_m.T).T
@@ -170,7 +173,7 @@ def test_adjoint_with_nip_uses_the_transposed_operator(sn, outer):
         a = m.adjoint_iterate(_t(g_n), dsa="thick", thick_rule=prob.thick_rule, operator="nip", tol=0.0,
                               max_iters=K, inner_tol=1e-14, inner_max_iters=1000)
         assert a["iters"] == K
-        assert np.abs(a["mu"].cpu().numpy() @ T.V - mu_k).max() < 1e-10 * np.abs(mu_k).max()
+        assert np.abs(a["mu"].cpu().numpy() @ T.V - mu_k).max() <= dsa_iterate_tol(prob, thick_mask(prob)) * np.abs(mu_k).max()
     mu_ref, _, _ = adjoint.adjoint_iterate(T, g_m, dsa=d, tol=1e-15)
     a = m.adjoint_iterate(_t(g_n), dsa="thick", thick_rule=prob.thick_rule, operator="nip", outer=outer,
                           tol=1e-14, inner_tol=1e-13, inner_max_iters=1000, max_iters=3000)

@@ -1,12 +1,16 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same seeded inputs.
 
 Tolerances (float64 path): 1e-12 relative to the largest |value| of the oracle's result, the
-bar the method sets for the FP64 form; 1e-5 for the FP32 element-solve form.
+bar the method sets for the FP64 form; 1e-5 for the FP32 element-solve form.  DSA-accelerated
+iterates use the derived tolerance of tests/tolerances.py (the bar, widened by the rounding
+amplification c/(1-c) of the DSA step only where that exceeds it).
 """
 import numpy as np
 import pytest
 
 from paper_2001_09196_gb300 import inputs
+from oracle.dsa import thick_mask
+from tolerances import BAR, dsa_iterate_tol, fp32_fixed_point_tol, FP32_BAR
 
 pytestmark = pytest.mark.gpu
 
@@ -131,8 +135,99 @@ def test_iterate_parity_with_dsa(sn, oracle_cache, name, dsa):
     rule = prob.thick_rule
     K = 6
     r = m.source_iterate(dsa=dsa, thick_rule=rule, tol=0.0, max_iters=K, inner_tol=1e-14, inner_max_iters=500)
-    ref = T.source_iterate(dsa=DSA(T, prob.thick_mask()), tol=0.0, max_iters=K)
-    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) < 1e-10
+    ref = T.source_iterate(dsa=DSA(T, thick_mask(prob)), tol=0.0, max_iters=K)
+    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) <= dsa_iterate_tol(prob, thick_mask(prob))
+
+
+def _c2_with_thick_ratio(c):
+    prob = inputs.config2(n=32, block=8)
+    thick = prob.sigma_t == 1.0e3
+    prob.sigma_s[thick] = c * prob.sigma_t[thick]
+    return prob
+
+
+def test_dsa_iterate_gap_is_rounding_amplification(sn, oracle_cache):
+    """Reading of the iterate tolerance: on configuration 2 the gap between library and oracle
+    iterates comes from the DSA step amplifying rounding differences by c/(1-c), not from the
+    inexact inner solve.  (1) The inner solve itself matches a sparse direct solve to 1e-13.
+    (2) The iterate gap does not shrink when the inner tolerance drops from 1e-12 to 1e-15.
+    (3) With the thick blocks' c lowered from 0.9999 to 0.99 (c/(1-c) from 9999 to 99) the same
+    iterates meet the 1e-12 bar."""
+    import scipy.sparse.linalg as spla
+    from oracle import Transport
+    from oracle.dsa import DSA
+    prob, T = _oracle("c2_32", oracle_cache)
+    op = DSA(T, thick_mask(prob))
+    m = sn.Mesh.from_problem(prob)
+    b = inputs.random_phi(prob, 23)
+    x, _ = m.dsa_solve(_t(b), thick_rule=prob.thick_rule, inner_tol=1e-15, inner_max_iters=2000, vcycle="fp64")
+    ref = np.zeros_like(b)
+    ref[op.thick] = spla.spsolve(op.nodal_matrix().tocsc(), b[op.thick].ravel()).reshape(-1, T.n)
+    assert _rel(x.cpu().numpy(), ref) < 1e-13
+    K = 6
+    ref_k = T.source_iterate(dsa=op, tol=0.0, max_iters=K)["phi"]
+    gaps = [_rel(m.source_iterate(dsa="thick", tol=0.0, max_iters=K, inner_tol=t, inner_max_iters=2000,
+                                  vcycle="fp64")["phi"].cpu().numpy(), ref_k) for t in (1e-12, 1e-15)]
+    assert gaps[1] > gaps[0] / 3.0
+    low = _c2_with_thick_ratio(0.99)
+    T2 = Transport(low)
+    m2 = sn.Mesh.from_problem(low)
+    r2 = m2.source_iterate(dsa="thick", tol=0.0, max_iters=K, inner_tol=1e-15, inner_max_iters=2000, vcycle="fp64")
+    ref2 = T2.source_iterate(dsa=DSA(T2, thick_mask(low)), tol=0.0, max_iters=K)["phi"]
+    assert dsa_iterate_tol(low, thick_mask(low)) == BAR
+    assert _rel(r2["phi"].cpu().numpy(), ref2) <= BAR
+
+
+@pytest.mark.parametrize("name", ["c1", "c2_32", "c3_8"])
+def test_fp32_refine_iterates(sn, oracle_cache, name):
+    """FP32 element solves with float64 residual corrections: the DSA-accelerated iterates match
+    the oracle's float64 iterates to the float64 tolerance."""
+    from oracle.dsa import DSA
+    prob, T = _oracle(name, oracle_cache)
+    m = sn.Mesh.from_problem(prob)
+    K = 6
+    r = m.source_iterate(dsa="thick", thick_rule=prob.thick_rule, tol=0.0, max_iters=K, inner_tol=1e-14,
+                         inner_max_iters=500, precision="fp32_refine")
+    ref = T.source_iterate(dsa=DSA(T, thick_mask(prob)), tol=0.0, max_iters=K)
+    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) <= dsa_iterate_tol(prob, thick_mask(prob))
+
+
+@pytest.mark.parametrize("name", ["c1", "c2_32", "c3_8"])
+def test_fp32_mixed_refinement_reaches_the_fp64_fixed_point(sn, oracle_cache, name):
+    """SN_FP32_MIXED: float32 element solves in every Arnoldi step, a float64 true residual between
+    restart cycles.  It converges to the float64 fixed point (same bound as float64 fGMRES to the
+    same tolerance), which plain float32 solves cannot reach on configuration 2."""
+    from oracle.dsa import DSA
+    prob, T = _oracle(name, oracle_cache)
+    m = sn.Mesh.from_problem(prob)
+    r = m.source_iterate(dsa="thick", thick_rule=prob.thick_rule, outer="fgmres", restart=30, tol=1e-13,
+                         inner_tol=1e-10, max_iters=600, precision="fp32_mixed")
+    ref = T.source_iterate(dsa=DSA(T, thick_mask(prob)), tol=1e-14, max_iters=3000)
+    assert r["converged"] and r["rel_residual"] <= 1e-13
+    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) < 1e-9
+    r64 = m.source_iterate(dsa="thick", thick_rule=prob.thick_rule, outer="fgmres", restart=30, tol=1e-13,
+                           inner_tol=1e-10, max_iters=600)
+    assert _rel(r["phi"].cpu().numpy(), r64["phi"].cpu().numpy()) < 1e-9
+
+
+@pytest.mark.parametrize("name", ["c1", "c2_32", "c3_8"])
+def test_fp32_iteration_against_the_fp64_fixed_point(sn, oracle_cache, name):
+    """The FP32 element-solve form (float64 flux, residual and DSA) iterated by fGMRES to the
+    residual float32 solves can reach, against the oracle's float64 fixed point: within 1e-5 where
+    the scattering ratio leaves the fixed point well conditioned (configurations 1 and 3); on
+    configuration 2, whose c = 0.9999 blocks amplify the float32 perturbation by up to c/(1-c),
+    within the derived bound (measured 4e-5, above the 1e-5 target)."""
+    from oracle.dsa import DSA
+    prob, T = _oracle(name, oracle_cache)
+    m = sn.Mesh.from_problem(prob)
+    r = m.source_iterate(dsa="thick", thick_rule=prob.thick_rule, outer="fgmres", tol=1e-6, inner_tol=1e-10,
+                         max_iters=400, precision="fp32")
+    fixed = T.source_iterate(dsa=DSA(T, thick_mask(prob)), tol=1e-14, max_iters=3000)["phi"]
+    assert r["converged"]
+    err = _rel(r["phi"].cpu().numpy(), fixed)
+    assert err <= fp32_fixed_point_tol(prob)
+    if name != "c2_32":
+        assert err <= FP32_BAR
 
 
 def test_converged_solution_c1(sn, oracle_cache):
@@ -140,9 +235,9 @@ def test_converged_solution_c1(sn, oracle_cache):
     prob, T = _oracle("c1", oracle_cache)
     m = sn.Mesh.from_problem(prob)
     r = m.source_iterate(dsa="thick", tol=1e-8, inner_tol=1e-12)
-    ref = T.source_iterate(dsa=DSA(T, prob.thick_mask()), tol=1e-8)
+    ref = T.source_iterate(dsa=DSA(T, thick_mask(prob)), tol=1e-8)
     assert r["converged"] and r["iters"] == ref["iters"]
-    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) < 1e-10
+    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) <= dsa_iterate_tol(prob, thick_mask(prob))
 
 
 def test_full_dsa_rejects_voids(sn, oracle_cache):
@@ -164,7 +259,7 @@ def test_full_dsa_parity_void_free(sn):
     K = 5
     r = m.source_iterate(dsa="full", tol=0.0, max_iters=K, inner_tol=1e-14, inner_max_iters=500)
     ref = T.source_iterate(dsa=DSA(T, np.ones(T.ne)), tol=0.0, max_iters=K)
-    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) < 1e-10
+    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) <= dsa_iterate_tol(prob, np.ones(T.ne))
 
 
 @pytest.mark.parametrize("name", ["c1", "c2_32", "c3_8"])
@@ -172,7 +267,7 @@ def test_dsa_operator_parity(sn, oracle_cache, name):
     from oracle.dsa import DSA
     prob, T = _oracle(name, oracle_cache)
     m = sn.Mesh.from_problem(prob)
-    mask = prob.thick_mask().astype(bool)
+    mask = thick_mask(prob).astype(bool)
     op = DSA(T, mask)
     Dn = op.nodal_matrix()
     x = inputs.random_phi(prob, 21) - 1.0
@@ -187,14 +282,14 @@ def test_dsa_pcg_solve(sn, oracle_cache, name):
     from oracle.dsa import DSA
     prob, T = _oracle(name, oracle_cache)
     m = sn.Mesh.from_problem(prob)
-    op = DSA(T, prob.thick_mask())
+    op = DSA(T, thick_mask(prob))
     b = inputs.random_phi(prob, 22)
     x, its = m.dsa_solve(_t(b), thick_rule=prob.thick_rule, inner_tol=1e-13, inner_max_iters=1000)
     ref = np.zeros_like(b)
     import scipy.sparse.linalg as spla
     ref[op.thick] = spla.spsolve(op.nodal_matrix().tocsc(), b[op.thick].ravel()).reshape(-1, T.n)
     assert its < 200
-    assert _rel(x.cpu().numpy(), ref) < 1e-9
+    assert _rel(x.cpu().numpy(), ref) < 1e-12
 
 
 @pytest.mark.parametrize("name", ["c1", "c2_32", "c3_8"])
@@ -228,9 +323,9 @@ def test_gradients_parity(sn):
     det = np.zeros(prob.n_elem, dtype=np.uint8)
     det[[6, 7, 14, 15]] = 1
     T = Transport(prob)
-    ref_phi = T.source_iterate(dsa=DSA(T, prob.thick_mask()), tol=1e-15, max_iters=3000)["phi"]
+    ref_phi = T.source_iterate(dsa=DSA(T, thick_mask(prob)), tol=1e-15, max_iters=3000)["phi"]
     g_m = adjoint.detector_modal(T, det)
-    mu_m, _, _ = adjoint.adjoint_iterate(T, g_m, dsa=DSA(T, prob.thick_mask()), tol=1e-15)
+    mu_m, _, _ = adjoint.adjoint_iterate(T, g_m, dsa=DSA(T, thick_mask(prob)), tol=1e-15)
     gt, gs, gq = adjoint.gradients(T, ref_phi, mu_m)
     m = sn.Mesh.from_problem(prob)
     r = m.source_iterate(dsa="thick", tol=1e-14, inner_tol=1e-13, inner_max_iters=500)
@@ -251,7 +346,7 @@ def test_fgmres_reaches_the_oracle_fixed_point(sn, oracle_cache, name):
     m = sn.Mesh.from_problem(prob)
     r = m.source_iterate(dsa="thick", thick_rule=prob.thick_rule, outer="fgmres", restart=30, tol=1e-13,
                          inner_tol=1e-10, max_iters=400)
-    ref = T.source_iterate(dsa=DSA(T, prob.thick_mask()), tol=1e-14, max_iters=2000)
+    ref = T.source_iterate(dsa=DSA(T, thick_mask(prob)), tol=1e-14, max_iters=2000)
     assert r["converged"]
     assert _rel(r["phi"].cpu().numpy(), ref["phi"]) < 1e-9
     si = m.source_iterate(dsa="thick", thick_rule=prob.thick_rule, tol=1e-13, inner_tol=1e-10, max_iters=2000)
@@ -267,9 +362,9 @@ def test_iterate_parity_triangular_dsa(sn, oracle_cache, name):
     K = 5
     r = m.source_iterate(dsa="triangular", thick_rule=prob.thick_rule, tol=0.0, max_iters=K, inner_tol=1e-14,
                          inner_max_iters=500)
-    ref = T.source_iterate(dsa=TriangularDSA(DSA(T, prob.thick_mask())), tol=0.0, max_iters=K)
+    ref = T.source_iterate(dsa=TriangularDSA(DSA(T, thick_mask(prob))), tol=0.0, max_iters=K)
     assert r["sweeps"] == 2 * K
-    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) < 1e-10
+    assert _rel(r["phi"].cpu().numpy(), ref["phi"]) <= dsa_iterate_tol(prob, thick_mask(prob))
 
 
 @pytest.mark.parametrize("name", ["c1", "c2_32"])
@@ -279,7 +374,7 @@ def test_fgmres_triangular_dsa_reaches_the_oracle_fixed_point(sn, oracle_cache, 
     m = sn.Mesh.from_problem(prob)
     r = m.source_iterate(dsa="triangular", thick_rule=prob.thick_rule, outer="fgmres", restart=30, tol=1e-13,
                          inner_tol=1e-10, max_iters=400)
-    ref = T.source_iterate(dsa=DSA(T, prob.thick_mask()), tol=1e-14, max_iters=2000)
+    ref = T.source_iterate(dsa=DSA(T, thick_mask(prob)), tol=1e-14, max_iters=2000)
     assert r["converged"]
     assert _rel(r["phi"].cpu().numpy(), ref["phi"]) < 1e-9
 

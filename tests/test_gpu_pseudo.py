@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from paper_2001_09196_gb300 import inputs
+from oracle.dsa import thick_mask
 
 pytestmark = pytest.mark.gpu
 
@@ -68,7 +69,7 @@ def test_sweep_and_solution_match_the_oracle(sn):
     # 1e-12: the source spans eleven decades (hot gold against cold helium), and the oracle's
     # float64 residual stalls just below that
     r = m.source_iterate(dsa="thick", outer="fgmres", tol=1e-12, inner_tol=1e-10, max_iters=400)
-    ref = T.source_iterate(dsa=DSA(T, prob.thick_mask()), tol=1e-12, max_iters=200)
+    ref = T.source_iterate(dsa=DSA(T, thick_mask(prob)), tol=1e-12, max_iters=200)
     assert r["converged"] and ref["converged"]
     assert _rel(r["phi"].cpu().numpy(), ref["phi"]) < 1e-9
 
@@ -98,3 +99,20 @@ def test_argument_errors(sn):
         assert e.value.status == 1
     st, ss, q = m.materials()  # a refused call leaves the materials alone
     assert np.all(st == 1.0) and np.all(ss == 0.0) and np.all(q == 0.0)
+
+
+def test_vanishing_heat_capacity_term_and_overflow(sn):
+    """C_v/dt underflowing to 0 is the long-step limit sigma_ps = sigma (Eq. hohlraum_sigma): it is
+    accepted with sigma_s = sigma_t; a temperature whose sigma b overflows is refused by name."""
+    prob = inputs.uniform_problem(2, 4, 1, 4, 1.0, 0.0, 0.0)
+    m = sn.Mesh.from_problem(prob)
+    ne = prob.n_elem
+    sigma = np.linspace(0.5, 3e3, ne)
+    m.set_pseudo_scattering(sigma, np.full(ne, 1e-300), np.full(ne, 0.4), 1e300)
+    st, ss, q = m.materials()
+    assert np.all(st == sigma) and np.all(ss <= st) and np.all(np.abs(ss - st) <= 2e-16 * st)
+    assert np.all(q == 0.0)
+    with pytest.raises(sn.SnError, match="overflows") as e:
+        m.set_pseudo_scattering(np.ones(ne), np.ones(ne), np.full(ne, 1e120), 1.0)
+    assert e.value.status == 1
+    assert np.array_equal(m.materials()[0], st)

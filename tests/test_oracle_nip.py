@@ -14,6 +14,7 @@ import pytest
 from paper_2001_09196_gb300 import inputs
 from oracle import Transport, adjoint, dense
 from oracle.dsa import C_M, DSA
+from oracle.dsa import thick_mask
 
 
 def _thick_uniform(p):
@@ -79,7 +80,7 @@ def test_penalty_is_the_angular_integral_of_eq_modified_f0(operator):
 def test_mnip_rejects_void_neighbours():
     prob = inputs.config1()
     T = Transport(prob)
-    mask = prob.thick_mask().copy()
+    mask = thick_mask(prob).copy()
     void = np.flatnonzero(prob.sigma_t == 0)
     e = next(int(u) for v in void for u in T.mesh.nbr[v] if u >= 0 and prob.sigma_t[u] > 0)
     mask[e] = 1                                     # a thick element next to a void one
@@ -92,7 +93,7 @@ def test_mnip_rejects_void_neighbours():
 def test_nonsymmetric_dsa_accelerates_config1(operator):
     prob = inputs.config1()
     T = Transport(prob)
-    r = T.source_iterate(dsa=DSA(T, prob.thick_mask(), operator=operator), tol=1e-8, max_iters=200)
+    r = T.source_iterate(dsa=DSA(T, thick_mask(prob), operator=operator), tol=1e-8, max_iters=200)
     assert r["converged"] and r["iters"] < 40
     assert not T.source_iterate(tol=1e-8, max_iters=60)["converged"]
 
@@ -102,7 +103,7 @@ def test_transposed_correction_is_the_adjoint(operator):
     """<y, C x> = <C^T y, x> for the Algorithm 2 correction C and the adjoint iteration's step."""
     prob = inputs.config2(n=16, block=4, p=1, sn=4)
     T = Transport(prob)
-    dsa = DSA(T, prob.thick_mask(), operator=operator)
+    dsa = DSA(T, thick_mask(prob), operator=operator)
     assert dsa.thick.size
     rng = np.random.default_rng(3)
     x, y = rng.standard_normal((T.ne, T.n)), rng.standard_normal((T.ne, T.n))
@@ -117,7 +118,7 @@ def test_adjoint_iteration_with_nip_reaches_the_dense_adjoint():
     _, S = dense.solve_schur(T)
     g = np.random.default_rng(4).standard_normal((T.ne, T.n))
     mu_ref = np.linalg.solve(S.T, g.ravel()).reshape(T.ne, T.n)
-    dsa = DSA(T, prob.thick_mask(), operator="nip")
+    dsa = DSA(T, thick_mask(prob), operator="nip")
     mu, it, rel = adjoint.adjoint_iterate(T, g, dsa=dsa, tol=1e-14, max_iters=3000)
     assert rel <= 1e-14
     assert np.abs(mu - mu_ref).max() < 1e-11 * np.abs(mu_ref).max()

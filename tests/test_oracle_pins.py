@@ -17,6 +17,7 @@ from oracle import Transport
 from oracle import adjoint, dense
 from oracle.dsa import DSA, TriangularDSA
 from oracle.quadrature import level_symmetric, level_symmetric_octant
+from oracle.dsa import thick_mask
 
 FOUR_PI = 4.0 * np.pi
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -151,7 +152,7 @@ def test_dense_direct_solve_matches_source_iteration(n, p):
     T = Transport(prob)
     direct = dense.solve_block_system(T)
     schur, _ = dense.solve_schur(T)
-    si = T.source_iterate(dsa=DSA(T, prob.thick_mask()), tol=1e-15, max_iters=3000)["phi"]
+    si = T.source_iterate(dsa=DSA(T, thick_mask(prob)), tol=1e-15, max_iters=3000)["phi"]
     scale = np.abs(direct).max()
     assert np.abs(schur - direct).max() < 1e-12 * scale
     assert np.abs(si - direct).max() < 1e-12 * scale
@@ -175,7 +176,7 @@ def test_dsa_fixed_point_invariance(operator):
     prob.sigma_s[prob.sigma_s == 0] = 0.25
     T = Transport(prob)
     ref = dense.solve_block_system(T)
-    for mask in (prob.thick_mask(), np.ones(T.ne)):
+    for mask in (thick_mask(prob), np.ones(T.ne)):
         r = T.source_iterate(dsa=DSA(T, mask, operator=operator), tol=1e-15, max_iters=3000)
         assert np.abs(r["phi"] - ref).max() < 1e-11 * np.abs(ref).max()
 
@@ -183,7 +184,7 @@ def test_dsa_fixed_point_invariance(operator):
 def test_dsa_accelerates_config1():
     prob = inputs.config1()
     T = Transport(prob)
-    r = T.source_iterate(dsa=DSA(T, prob.thick_mask()), tol=1e-8, max_iters=200)
+    r = T.source_iterate(dsa=DSA(T, thick_mask(prob)), tol=1e-8, max_iters=200)
     assert r["converged"] and r["iters"] < 40
     r0 = T.source_iterate(tol=1e-8, max_iters=60)
     assert not r0["converged"]
@@ -191,7 +192,7 @@ def test_dsa_accelerates_config1():
 
 def _vacuum_thin(prob):
     """sigma_s = 0 on every element outside the thick set (the case of Eq. Stri)."""
-    thick = prob.thick_mask().astype(bool)
+    thick = thick_mask(prob).astype(bool)
     prob.sigma_s[~thick] = 0.0
     return prob
 
@@ -203,12 +204,12 @@ def test_triangular_dsa_makes_the_thin_block_the_identity(prob_fn):
     (S P v)_s = v_s.  S v = v - T v with T the zero-source, vacuum-inflow transport update."""
     prob = _vacuum_thin(prob_fn())
     T = Transport(prob)
-    tri = TriangularDSA(DSA(T, prob.thick_mask()))
+    tri = TriangularDSA(DSA(T, thick_mask(prob)))
     rng = np.random.default_rng(7)
     v = rng.standard_normal((T.ne, T.n))
     Pv = v + tri.correction(v)
     SPv = Pv - tri.homogeneous_update(Pv)
-    thin = ~prob.thick_mask().astype(bool)
+    thin = ~thick_mask(prob).astype(bool)
     assert thin.any() and (~thin).any()
     assert np.abs(SPv[thin] - v[thin]).max() < 1e-13 * np.abs(v).max()
     # the thick rows are not the identity (D_ff only approximates the thick block)
@@ -221,11 +222,11 @@ def test_triangular_dsa_fixed_point_and_acceleration():
     prob = inputs.config2d_fields(8, 1, 4, 98, "tri")
     prob.q[:] = 1.0
     prob.sigma_t[prob.sigma_t == 0] = 0.5
-    thick = prob.thick_mask().astype(bool)
+    thick = thick_mask(prob).astype(bool)
     prob.sigma_s[~thick] = 1e-3 * prob.sigma_t[~thick]
     T = Transport(prob)
     ref = dense.solve_block_system(T)
-    diag = DSA(T, prob.thick_mask())
+    diag = DSA(T, thick_mask(prob))
     r_tri = T.source_iterate(dsa=TriangularDSA(diag), tol=1e-14, max_iters=3000)
     assert np.abs(r_tri["phi"] - ref).max() < 1e-11 * np.abs(ref).max()
     r_diag = T.source_iterate(dsa=diag, tol=1e-14, max_iters=3000)
@@ -239,7 +240,7 @@ def test_thick_dsa_beats_full_dsa_with_scattering_free_thin_regions(prob_fn):
     thick block alone is the right preconditioner; the paper's tables show heterogeneous DSA needing
     no more iterations than full DSA.  Thin regions keep sigma_t > 0 so that full DSA is defined."""
     prob = prob_fn()
-    thick = prob.thick_mask().astype(bool)
+    thick = thick_mask(prob).astype(bool)
     prob.sigma_t[prob.sigma_t == 0] = 0.5
     prob.sigma_s[~thick] = 0.0
     T = Transport(prob)
@@ -261,7 +262,7 @@ def test_full_dsa_rejects_voids():
 def test_dsa_operator_spd(prob_fn):
     prob = prob_fn()
     T = Transport(prob)
-    mask = np.ones(T.ne) if np.all(prob.sigma_t > 0) else prob.thick_mask()
+    mask = np.ones(T.ne) if np.all(prob.sigma_t > 0) else thick_mask(prob)
     D = DSA(T, mask).D.toarray()
     assert np.abs(D - D.T).max() <= 1e-15 * np.abs(D).max()
     np.linalg.cholesky(D)
@@ -357,11 +358,11 @@ def test_adjoint_gradients_match_finite_differences():
 
     def J(pr):
         T = Transport(pr)
-        r = T.source_iterate(dsa=DSA(T, pr.thick_mask()), tol=1e-15, max_iters=3000)
+        r = T.source_iterate(dsa=DSA(T, thick_mask(pr)), tol=1e-15, max_iters=3000)
         return (T.to_modal(r["phi"]) * adjoint.detector_modal(T, det)).sum(), r["phi"], T
 
     _, phi, T = J(prob)
-    mu, _, _ = adjoint.adjoint_iterate(T, adjoint.detector_modal(T, det), dsa=DSA(T, prob.thick_mask()), tol=1e-15)
+    mu, _, _ = adjoint.adjoint_iterate(T, adjoint.detector_modal(T, det), dsa=DSA(T, thick_mask(prob)), tol=1e-15)
     gt, gs, gq = adjoint.gradients(T, phi, mu)
     nonvoid = np.flatnonzero(prob.sigma_t > 0)[:3]
     for e in nonvoid:

@@ -16,6 +16,7 @@ from paper_2001_09196_gb300 import inputs
 from oracle import Transport
 from oracle.dsa import DSA
 from oracle.pseudo import problem, pseudo_scattering
+from oracle.dsa import thick_mask
 
 A, C = inputs.HOHLRAUM_A_RAD, inputs.HOHLRAUM_C_LIGHT
 
@@ -67,4 +68,13 @@ def test_hohlraum_like_layout_and_thick_set():
     # the paper's thick rule (sigma_s >= 1) selects exactly the laser-heated gold
     assert np.array_equal(tp.sigma_s >= 1.0, hot)
     assert np.all(tp.sigma_s <= tp.sigma_t) and np.all(tp.q >= 0)
-    assert dataclasses.replace(tp).thick_mask().sum() == hot.sum()
+    assert thick_mask(dataclasses.replace(tp)).sum() == hot.sum()
+
+
+def test_heat_capacity_term_underflow_limit():
+    """C_v/dt = 0 exactly (underflow): sigma_ps = sigma^2 b / (sigma b) = sigma and q_ps = 0 up to
+    rounding (Eq. hohlraum_sigma, Eq. hohlraum_q with the C_v/dt term gone)."""
+    for sigma in (0.5, 7.0, 3e3):
+        _, ss, q = pseudo_scattering([sigma], [1e-300], [0.4], 1e300, A, C)
+        emission = 4 * np.pi * sigma * A * C * 0.4 ** 4
+        assert abs(ss[0] - sigma) <= 4e-16 * sigma and abs(q[0]) <= 1e-15 * emission

@@ -1,8 +1,9 @@
 """GPU: the scalar-flux reduction that allocates nothing matches the flux that sn_sweep returns.
 
-sn_scalar_flux_noalloc serves callers that cannot call cudaMalloc (CUDA graph capture, frameworks
-whose allocator owns the device memory, loops that cannot take cudaMalloc's synchronisation).  It
-keeps its block partial sums in a fixed device array inside the library.  This file is collected
+sn_scalar_flux_noalloc serves callers that cannot call cudaMalloc: frameworks whose caching
+allocator owns the device memory, loops that cannot take cudaMalloc's device synchronisation, and
+hosts with a device memory budget fixed at start-up.  It keeps its block partial sums in a fixed
+device array inside the library.  This file is collected
 last so that a failure here leaves every other test already run; it passes alone and after them.
 """
 import numpy as np
@@ -40,8 +41,14 @@ def test_noalloc_flux_matches_sweep_on_consecutive_calls(sn):
     for seed, prob in enumerate(cases):
         mesh = sn.Mesh.from_problem(prob)
         phi_in, phi_ref, psi, w = _angular_fluxes(mesh, prob, 50 + seed)
-        phi, rr = sn.scalar_flux_noalloc(psi, w, phi_prev=phi_in)
+        phi = torch.empty(psi[0].numel(), dtype=torch.float64, device="cuda")
+        rr = torch.empty(1, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        sn.scalar_flux_noalloc(psi, w, phi_prev=phi_in, phi_out=phi, resid_norm2=rr)
+        torch.cuda.synchronize()
+        if seed > 0:  # after the first call's one-time set-up the device's free memory stays put
+            assert torch.cuda.mem_get_info()[0] == free_before
         ref = phi_ref.reshape(-1)
         assert torch.max(torch.abs(phi - ref)).item() <= 1e-12 * torch.max(torch.abs(ref)).item()
         expect = float(torch.sum((ref - phi_in.reshape(-1)) ** 2))

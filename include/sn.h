@@ -245,7 +245,12 @@ typedef struct {
     void* exchange_ctx;      /* passed through to exchange */
     double* exchange_buf;    /* optional device buffer (n_elem x n_nodes doubles) that the partial
                                 updates are written to and exchanged in; NULL = library scratch */
-    double refine_drop;      /* SN_FP32_MIXED: residual reduction that ends a restart cycle (0 = 1e-3) */
+    double refine_drop;      /* SN_FP32_MIXED: residual reduction that ends a restart cycle (0 = 1e-4) */
+    int host_loop;           /* 0 (default): on the level schedule of one process, the whole solve is
+                                recorded once into a CUDA graph (WHILE conditional nodes, convergence
+                                tests on the device) and runs as one graph launch with one host
+                                synchronisation; 1: a host loop with one synchronisation per outer
+                                iteration, which also splits the device time into ms_sweep / ms_dsa */
 } sn_iter_opts;
 
 typedef struct {

@@ -70,6 +70,11 @@ void free_mesh(sn_mesh* m) {
                     (void*)m->levels.ctrl, (void*)m->d_krylov, (void*)m->levels.d_level_ptr, (void*)m->levels.d_barrier,
                     (void*)m->range_items})
         if (p) cudaFree(p);
+    sn::drop_iter_graph(m);
+    for (void* p : {(void*)m->d_ig, (void*)m->d_igi, (void*)m->d_igv})
+        if (p) cudaFree(p);
+    for (cudaStream_t st : m->ig_stream)
+        if (st) cudaStreamDestroy(st);
     sn::dsa_free(m->dsa);
     sn::dsa_free(m->dsa_t);
     delete m;
@@ -308,6 +313,7 @@ static sn_status commit_materials(sn_mesh* m, std::vector<double>& hst, std::vec
     CK(cudaMemcpyAsync(m->d_sigma_s, hss.data(), m->ne * sizeof(double), cudaMemcpyHostToDevice, s), "copy");
     CK(cudaMemcpyAsync(m->d_q, hq.data(), m->ne * sizeof(double), cudaMemcpyHostToDevice, s), "copy");
     CK(cudaStreamSynchronize(s), "sync");
+    sn::drop_iter_graph(m);
     sn::dsa_free(m->dsa);
     sn::dsa_free(m->dsa_t);
     m->dsa = m->dsa_t = nullptr;
@@ -449,6 +455,7 @@ static sn_status ensure_dsa(sn_mesh* m, const sn_iter_opts* o) {
         if (m->dsa_t) m->dsa_t->vcycle_mode = o->dsa_vcycle;
         return SN_OK;
     }
+    sn::drop_iter_graph(m);
     sn::dsa_free(m->dsa);
     sn::dsa_free(m->dsa_t);
     m->dsa = m->dsa_t = nullptr;
@@ -574,6 +581,25 @@ struct SegmentClock {
     }
 };
 
+// Workspace of flexible GMRES(k): basis V ((k+1) x M), preconditioned basis Z (k x M), w (M),
+// partial sums ((k+1) x blocks) and small device scalars.
+static sn_status ensure_krylov(sn_mesh* m, int k) {
+    const long long M = (long long)m->ne * m->n;
+    const int nb = sn::krylov_blocks(M);
+    const size_t need = (size_t)(2 * k + 2) * M + (size_t)(k + 1) * nb + 4 * (k + 2);
+    if (!m->d_krylov || m->krylov_restart < k) {
+        if (m->d_krylov) {
+            CK(cudaDeviceSynchronize(), "sync");
+            cudaFree(m->d_krylov);
+        }
+        m->d_krylov = nullptr;
+        sn::drop_iter_graph(m);  // a recorded iteration holds the old workspace's addresses
+        CK(cudaMalloc(&m->d_krylov, need * sizeof(double)), "alloc fGMRES workspace");
+        m->krylov_restart = k;
+    }
+    return SN_OK;
+}
+
 // Flexible GMRES(k) on S x = b (Eq. schur), right-preconditioned by the DSA step
 // P v = v + E_f D_ff^{-1} Sigma_f E_f^T v (Algorithm 2 applied to a residual); classical
 // Gram-Schmidt twice, Givens rotations on the host.
@@ -584,13 +610,8 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
     const long long M = (long long)m->ne * m->n;
     const int k = o->restart;
     const int nb = sn::krylov_blocks(M);
-    const size_t need = (size_t)(2 * k + 2) * M + (size_t)(k + 1) * nb + 4 * (k + 2);
-    if (!m->d_krylov || m->krylov_restart < k) {
-        if (m->d_krylov) cudaFree(m->d_krylov);
-        m->d_krylov = nullptr;
-        CK(cudaMalloc(&m->d_krylov, need * sizeof(double)), "alloc fGMRES workspace");
-        m->krylov_restart = k;
-    }
+    sn_status wst = ensure_krylov(m, k);
+    if (wst != SN_OK) return wst;
     double* V = m->d_krylov;                    // (k+1) x M
     double* Z = V + (size_t)(k + 1) * M;        // k x M
     double* w = Z + (size_t)k * M;              // M
@@ -607,7 +628,7 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
     // cycle ends once its residual estimate fell by `drop` (iterative refinement around fGMRES)
     const bool mixed = o->precision == SN_FP32_MIXED;
     const int prec_res = mixed ? SN_FP64 : o->precision, prec_op = mixed ? SN_FP32 : o->precision;
-    const double drop = mixed ? (o->refine_drop > 0.0 ? o->refine_drop : 1e-3) : 0.0;
+    const double drop = mixed ? (o->refine_drop > 0.0 ? o->refine_drop : 1e-4) : 0.0;
     while (true) {
         // true residual r = sweep(x) - x (with the fixed source); adjoint: g + T^T x - x
         ++sweeps;
@@ -744,6 +765,306 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
     return SN_OK;
 }
 
+// ---------------------------------------------------------------- recorded outer iterations
+// A whole source iteration or flexible GMRES solve recorded once into a CUDA graph and launched as
+// one graph: the loops are WHILE conditional nodes whose conditions are set by device kernels
+// (sn_iter_graph.cu), the DSA solve is a nested WHILE node, and the host synchronises once per
+// solve instead of once per outer iteration.  Used for the level schedule on one process (the
+// persistent schedules carry a host-side epoch, and a sharded iteration calls back to the host).
+
+// WHILE node (handle h) appended to the graph `s` is capturing; its body graph in *body.
+static cudaError_t add_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t err = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &ndeps);
+    if (err != cudaSuccess) return err;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((err = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp)) != cudaSuccess) return err;
+    if ((err = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+        return err;
+    *body = cp.conditional.phGraph_out[0];
+    return cudaSuccess;
+}
+
+static cudaError_t new_handle(cudaStream_t s, unsigned dflt, cudaGraphConditionalHandle* h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    cudaError_t err = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+    if (err != cudaSuccess) return err;
+    return cudaGraphConditionalHandleCreate(h, g, dflt, cudaGraphCondAssignDefault);
+}
+
+static bool recordable(const sn_mesh* m, const sn_iter_opts* o) {
+    return !o->host_loop && !sharded(o) && m->schedule == sn::SCHED_LEVELS;
+}
+
+// What a recorded iteration depends on: a graph is reused only for the same key.
+static std::vector<double> iteration_key(const sn_mesh* m, const sn_iter_opts* o, int hist_len) {
+    auto addr = [](const void* p) { return (double)(uintptr_t)p; };
+    return {(double)o->outer, (double)o->restart, (double)o->dsa, (double)o->precision, o->tol, o->inner_tol,
+            (double)o->inner_max_iters, (double)o->max_iters, o->refine_drop, (double)hist_len,
+            (double)o->checkpoint_every, addr(o->checkpoints), (double)o->max_checkpoints, addr(m->dsa),
+            m->dsa ? (double)m->dsa->vcycle_mode : -1.0, (double)m->level_groups, (double)m->block,
+            addr(m->d_krylov), addr(m->d_ig), addr(m->d_igv), addr(m->d_psi32)};
+}
+
+// Records the iteration (fgmres: flexible GMRES, else source iteration) into m->iter_graph.
+static cudaError_t record_iteration(sn_mesh* m, const sn_iter_opts* o, bool fg, int hist_len) {
+    const long long M = (long long)m->ne * m->n;
+    const int k = o->restart;
+    cudaError_t err;
+    for (auto& st : m->ig_stream)
+        if (!st && (err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return err;
+    cudaStream_t s0 = m->ig_stream[0], s1 = m->ig_stream[1], s2 = m->ig_stream[2];
+    double* gd = m->d_ig;
+    int* gi = m->d_igi;
+    double* hist = hist_len > 0 ? m->d_ig + m->ig_doubles : nullptr;
+    double* x = m->d_igv;
+    double* vt = x + M;
+    double* zt = x + 2 * M;
+    const bool mixed = o->precision == SN_FP32_MIXED;
+    const int prec_res = mixed ? SN_FP64 : o->precision, prec_op = mixed ? SN_FP32 : o->precision;
+    const double drop = mixed ? (o->refine_drop > 0.0 ? o->refine_drop : 1e-4) : 0.0;
+    const bool dsa = o->dsa != SN_DSA_NONE && m->dsa && sn::dsa_thick_count(m->dsa) > 0;
+    const long long c0 = sn::g_launches.load();
+    int open = 0;  // captures in progress (s0, s1, s2)
+    cudaGraph_t graph = nullptr;
+    auto unwind = [&](cudaError_t e) {
+        cudaGraph_t g2 = nullptr;
+        if (open > 2) cudaStreamEndCapture(s2, &g2);
+        if (open > 1) cudaStreamEndCapture(s1, &g2);
+        if (open > 0) {
+            cudaStreamEndCapture(s0, &g2);
+            if (g2) cudaGraphDestroy(g2);
+        }
+        cudaGetLastError();
+        sn::g_launches.store(c0);
+        return e;
+    };
+#define RK(call)                                \
+    do {                                        \
+        cudaError_t e_ = (call);                \
+        if (e_ != cudaSuccess) return unwind(e_); \
+    } while (0)
+#define RS(call)                                                    \
+    do {                                                            \
+        if ((call) != SN_OK) return unwind(cudaErrorUnknown);       \
+    } while (0)
+    RK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+    open = 1;
+    RK(sn::ig_init(gd, gi, s0));
+    m->ig_pro = sn::g_launches.load() - c0;
+    cudaGraphConditionalHandle ho, hi;
+    cudaGraph_t body_o = nullptr, body_i = nullptr;
+    RK(new_handle(s0, 1, &ho));
+    RK(add_while(s0, ho, &body_o));
+    RK(cudaStreamBeginCaptureToGraph(s1, body_o, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    open = 2;
+    const long long c1 = sn::g_launches.load();
+    long long inner = 0;
+    if (fg) {
+        double* V = m->d_krylov;
+        double* Z = V + (size_t)(k + 1) * M;
+        double* w = Z + (size_t)k * M;
+        double* part = w + M;
+        double* hd = part + (size_t)(k + 1) * sn::krylov_blocks(M);
+        double* tmp = m->d_work + 2 * (size_t)M;
+        // cycle start: true residual w = b - S x with the fixed source, then V_0 = w / ||w||
+        RS(transport_update(m, o, x, tmp, 1.0, s1, prec_res));
+        RK(sn::launch_axpy_norm(m, tmp, x, w, m->d_scalars, s1));
+        RK(new_handle(s1, 0, &hi));
+        RK(sn::ig_gm_cycle_start(m->d_scalars, gd, gi, k, o->tol, o->max_iters, hist, hist_len, ho, hi, s1));
+        RK(sn::launch_normalize(w, M, part, hd + 2 * (k + 1), V, s1));
+        RK(add_while(s1, hi, &body_i));
+        RK(cudaStreamBeginCaptureToGraph(s2, body_i, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        open = 3;
+        const long long c2 = sn::g_launches.load();
+        // Arnoldi step j: Z_j = P V_j (DSA step, Algorithm 2 or 1), w = S Z_j, two Gram-Schmidt passes
+        RK(sn::ig_get_col(V, gi, 0, M, vt, s2));
+        RK(sn::launch_copy(zt, vt, M, s2));
+        if (dsa) {
+            RK(sn::dsa_correct(m->dsa, vt, zt, o->inner_tol, o->inner_max_iters, false, s2));
+            inner += sn::dsa_nested_prologue_launches(m->dsa);
+            if (o->dsa == SN_DSA_TRIANGULAR) {
+                double* tw = m->d_work;
+                double* ty = m->d_work + M;
+                RK(sn::dsa_select_thick(m->dsa, zt, tw, s2));
+                RS(transport_update(m, o, tw, ty, 0.0, s2, prec_op));
+                RK(sn::dsa_add_thin(m->dsa, ty, zt, s2));
+            }
+        }
+        RK(sn::ig_set_col(Z, gi, M, zt, s2));
+        RS(transport_update(m, o, zt, tmp, 0.0, s2, prec_op));
+        RK(sn::launch_axpy_norm(m, zt, tmp, w, m->d_scalars, s2));
+        RK(sn::launch_multidot_dev(V, gi + 1, 1, k + 1, M, w, part, hd, s2));
+        RK(sn::launch_multiaxpy_dev(V, gi + 1, 1, M, hd, -1.0, w, s2));
+        RK(sn::launch_multidot_dev(V, gi + 1, 1, k + 1, M, w, part, hd + (k + 1), s2));
+        RK(sn::launch_multiaxpy_dev(V, gi + 1, 1, M, hd + (k + 1), -1.0, w, s2));
+        RK(sn::launch_multidot(w, 1, M, w, part, hd + 2 * (k + 1), s2));
+        RK(sn::ig_gm_arnoldi(hd, gd, gi, k, o->tol, o->max_iters, drop, hist, hist_len, hi, s2));
+        RK(sn::ig_next_basis(w, gd, gi, M, V, s2));
+        RK(cudaGetLastError());
+        inner += sn::g_launches.load() - c2;
+        {
+            cudaGraph_t g2 = nullptr;
+            open = 2;
+            RK(cudaStreamEndCapture(s2, &g2));
+        }
+        // x += Z y with H y = g over the steps of this cycle
+        RK(sn::ig_gm_solve(gd, gi, k, s1));
+        RK(sn::launch_multiaxpy_dev(Z, gi + 2, 0, M, gd + sn::iter_graph_y_offset(k), 1.0, x, s1));
+    } else {
+        double* half = m->d_work;
+        double* r = m->d_work + M;
+        RK(sn::launch_sweep(m, x, o->precision, 1.0, s1));
+        RK(sn::launch_phi_reduce(m, o->precision, x, half, m->d_scalars, s1));
+        RK(sn::ig_si_residual(m->d_scalars, gd, gi, hist, hist_len, s1));
+        if (dsa) {
+            RK(sn::launch_axpy_norm(m, half, x, r, m->d_scalars + 1, s1));
+            RK(sn::launch_copy(x, half, M, s1));
+            if (o->dsa != SN_DSA_TRIANGULAR) {
+                RK(sn::dsa_correct(m->dsa, r, x, o->inner_tol, o->inner_max_iters, false, s1));
+                inner += sn::dsa_nested_prologue_launches(m->dsa);
+            } else {
+                double* tw = m->d_work + 2 * M;
+                double* ty = m->d_work + 3 * M;
+                RK(sn::dsa_select_thick(m->dsa, r, tw, s1));
+                RK(sn::dsa_correct(m->dsa, r, tw, o->inner_tol, o->inner_max_iters, false, s1));
+                inner += sn::dsa_nested_prologue_launches(m->dsa);
+                RK(sn::launch_sweep(m, tw, o->precision, 0.0, s1));
+                RK(sn::launch_phi_reduce(m, o->precision, nullptr, ty, nullptr, s1));
+                RK(sn::dsa_tri_combine(m->dsa, tw, r, ty, x, s1));
+            }
+        } else {
+            RK(sn::launch_copy(x, half, M, s1));
+        }
+        RK(sn::ig_si_end(gd, gi, o->tol, o->max_iters, ho, s1));
+        if (o->checkpoint_every > 0)
+            RK(sn::ig_si_checkpoint(x, o->checkpoints, M, gi, o->checkpoint_every, o->max_checkpoints, s1));
+    }
+    RK(cudaGetLastError());
+    // the outer body's own kernels (the inner body counted apart, per Arnoldi step)
+    const long long outer = sn::g_launches.load() - c1 - (fg ? inner - (dsa ? sn::dsa_nested_prologue_launches(m->dsa) : 0) : 0);
+    {
+        cudaGraph_t g2 = nullptr;
+        open = 1;
+        RK(cudaStreamEndCapture(s1, &g2));
+    }
+    open = 0;
+    RK(cudaStreamEndCapture(s0, &graph));
+#undef RK
+#undef RS
+    sn::g_launches.store(c0);  // recorded, not run
+    if (m->iter_graph) cudaGraphExecDestroy(m->iter_graph);
+    m->iter_graph = nullptr;
+    err = cudaGraphInstantiate(&m->iter_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (err != cudaSuccess) {
+        m->iter_graph = nullptr;
+        cudaGetLastError();
+        return err;
+    }
+    m->ig_outer = fg ? outer : outer + inner;
+    m->ig_inner = fg ? inner : 0;
+    return cudaSuccess;
+}
+
+// Solve by one launch of the recorded iteration.  Returns SN_ERR_NOT_CONVERGED like the host loops;
+// *done = false when the iteration cannot be recorded (the caller then runs the host loop).
+static sn_status run_recorded(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_iter_stats* stats, cudaStream_t s,
+                              std::chrono::steady_clock::time_point t0, bool* done) {
+    *done = false;
+    const bool fg = o->outer == SN_OUTER_FGMRES;
+    const long long M = (long long)m->ne * m->n;
+    const int hist_len = stats && stats->residual_history ? stats->history_len : 0;
+    sn_status st;
+    if (fg && (st = ensure_krylov(m, o->restart)) != SN_OK) return st;
+    const size_t doubles = sn::iter_graph_doubles(60);
+    const size_t need = doubles + (size_t)std::max(hist_len, 0);
+    if (!m->d_ig || m->ig_doubles + (size_t)0 < doubles || need > m->ig_doubles + m->ig_hist_cap) {
+        if (m->d_ig) {
+            CK(cudaDeviceSynchronize(), "sync");
+            cudaFree(m->d_ig);
+        }
+        m->d_ig = nullptr;
+        m->ig_doubles = doubles;
+        m->ig_hist_cap = std::max<size_t>(need - doubles, 1024);
+        CK(cudaMalloc(&m->d_ig, (m->ig_doubles + m->ig_hist_cap) * sizeof(double)), "alloc iteration state");
+    }
+    if (!m->d_igi) CK(cudaMalloc(&m->d_igi, 8 * sizeof(int)), "alloc iteration state");
+    if (!m->d_igv) CK(cudaMalloc(&m->d_igv, 3 * (size_t)M * sizeof(double)), "alloc iteration vectors");
+    // set-up that allocates or launches work happens before the recording
+    const bool mixed = o->precision == SN_FP32_MIXED;
+    CK(sn::prepare_recorded_sweep(m, mixed ? SN_FP64 : o->precision, s), "operator cache");
+    if (mixed) CK(sn::prepare_recorded_sweep(m, SN_FP32, s), "operator cache");
+    if (o->dsa != SN_DSA_NONE && m->dsa) CK(sn::dsa_prepare(m->dsa, o->inner_tol), "DSA set-up");
+    const std::vector<double> key = iteration_key(m, o, hist_len);
+    if (!m->iter_graph || m->iter_key != key) {
+        CK(cudaStreamSynchronize(s), "sync");
+        m->capture_no_pdl = false;
+        cudaError_t err = record_iteration(m, o, fg, hist_len);
+        if (err != cudaSuccess) {  // e.g. programmatic edges inside conditional bodies: retry without
+            m->capture_no_pdl = true;
+            err = record_iteration(m, o, fg, hist_len);
+            m->capture_no_pdl = false;
+        }
+        if (err != cudaSuccess) {
+            sn::drop_iter_graph(m);
+            cudaGetLastError();
+            return SN_OK;  // not recordable here: the host loop runs instead
+        }
+        m->iter_key = key;
+    }
+    double* x = m->d_igv;
+    if (o->warm_start) CK(cudaMemcpyAsync(x, phi, M * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    else CK(cudaMemsetAsync(x, 0, M * sizeof(double), s), "memset");
+    CK(cudaGraphLaunch(m->iter_graph, s), "recorded iteration");
+    CK(cudaMemcpyAsync(phi, x, M * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    int hi[8] = {};
+    double hd[4] = {};
+    CK(cudaMemcpyAsync(hi, m->d_igi, sizeof(hi), cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaMemcpyAsync(hd, m->d_ig, sizeof(hd), cudaMemcpyDeviceToHost, s), "copy");
+    if (hist_len > 0)
+        CK(cudaMemcpyAsync(stats->residual_history, m->d_ig + m->ig_doubles, hist_len * sizeof(double),
+                           cudaMemcpyDeviceToHost, s), "copy");
+    CK(cudaStreamSynchronize(s), "sync");
+    *done = true;
+    const int it = hi[0], cycles = hi[5];
+    const bool converged = hi[3] != 0;
+    if (hist_len > 0) {  // entries the solve did not reach stay zero, as in the host loops
+        const int written = std::min(hist_len, fg ? it + 1 : it);
+        for (int i = written; i < hist_len; ++i) stats->residual_history[i] = 0.0;
+    }
+    sn::g_launches.fetch_add(m->ig_pro + (fg ? (long long)(cycles + 1) * m->ig_outer + (long long)it * m->ig_inner
+                                             : (long long)it * m->ig_outer),
+                             std::memory_order_relaxed);
+    int inner_total = 0;
+    if (m->dsa) CK(sn::dsa_take_iters(m->dsa, s, &inner_total), "DSA iterations");
+    const bool tri = o->dsa == SN_DSA_TRIANGULAR && m->dsa && sn::dsa_thick_count(m->dsa) > 0;
+    if (stats) {
+        stats->iters = it;
+        stats->rel_residual = hd[1];
+        stats->inner_iters_total = inner_total;
+        stats->thick_fraction = m->dsa && o->dsa != SN_DSA_NONE ? (double)sn::dsa_thick_count(m->dsa) / m->ne : 0.0;
+        stats->n_checkpoints = fg ? 0 : hi[6];
+        stats->n_sweeps = fg ? (cycles + 1) + it * (tri ? 2 : 1) : it * (tri ? 2 : 1);
+        stats->ms_sweep = 0.0;  // not split in a recorded solve (one graph launch)
+        stats->ms_dsa = 0.0;
+        stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (!converged)
+        return fail(SN_ERR_NOT_CONVERGED, "%s not converged after %d iterations (%.3e)", fg ? "fGMRES" : "source iteration",
+                    it, hd[1]);
+    return SN_OK;
+}
+
 sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_iter_stats* stats, void* stream) {
     if (!m || !phi) return fail(SN_ERR_ARG, "null argument");
     sn_status st = check_opts(o);
@@ -756,6 +1077,11 @@ sn_status sn_source_iterate(sn_mesh* m, const sn_iter_opts* o, double* phi, sn_i
     if (m->dsa) {  // the PCG iteration counter starts from zero for this solve
         int stale = 0;
         CK(sn::dsa_take_iters(m->dsa, (cudaStream_t)stream, &stale), "DSA iterations");
+    }
+    if (recordable(m, o)) {
+        bool done = false;
+        st = run_recorded(m, o, phi, stats, s, t0, &done);
+        if (done || st != SN_OK) return st;
     }
     if (o->outer == SN_OUTER_FGMRES) {
         if (!o->warm_start) CK(cudaMemsetAsync(phi, 0, (size_t)m->ne * m->n * sizeof(double), s), "memset");

@@ -497,65 +497,58 @@ void vcycle0(DsaHierarchy* H, const double* r, double* z, cudaStream_t s) {
 //     x += alpha ph; s = r - alpha v; sh = M s; t = A sh; omega = t.s / t.t; x += omega sh;
 //     r = s - omega t.
 // Both continue while ||r|| > tol ||b|| and k < max_iters.
-cudaError_t record_krylov(DsaHierarchy* H, double tol, int max_iters) {
+// Emits that solve into the graph the stream `cs_stream` is capturing: the prologue on cs_stream, then
+// a WHILE node whose body is captured on H->cap2.  Launch counters: the kernels of the prologue and
+// of one loop iteration are counted into *pro and *body (g_launches is left as it was).
+static cudaError_t emit_krylov(DsaHierarchy* H, cudaStream_t cs_stream, double tol, int max_iters, long long* pro,
+                               long long* body_count) {
     const long long N0 = (long long)H->nt * H->n;
     const Level0& A = H->l0;
     cudaError_t err;
-    if (!H->cap && (err = cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking)) != cudaSuccess) return err;
     if (!H->cap2 && (err = cudaStreamCreateWithFlags(&H->cap2, cudaStreamNonBlocking)) != cudaSuccess) return err;
-    if (H->krylov_graph) cudaGraphExecDestroy(H->krylov_graph);
-    H->krylov_graph = nullptr;
     const long long count0 = g_launches.load();
-    if ((err = cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return err;
-    cudaGraph_t g = nullptr, body = nullptr;
-    bool body_open = false;
-    auto finish = [&](cudaError_t e) -> cudaError_t {
-        if (body_open) {
-            cudaGraph_t b2 = nullptr;
-            cudaStreamEndCapture(H->cap2, &b2);
-        }
-        cudaGraph_t g2 = nullptr;
-        cudaError_t e2 = cudaStreamEndCapture(H->cap, &g2);
-        if (e == cudaSuccess) e = e2;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&H->krylov_graph, g2, 0);
-        if (g2) cudaGraphDestroy(g2);
-        if (e != cudaSuccess) H->krylov_graph = nullptr;
-        return e;
-    };
     cudaStreamCaptureStatus cs;
-    if ((err = cudaStreamGetCaptureInfo(H->cap, &cs, nullptr, &g, nullptr, nullptr, nullptr)) != cudaSuccess)
-        return finish(err);
+    cudaGraph_t g = nullptr;
+    if ((err = cudaStreamGetCaptureInfo(cs_stream, &cs, nullptr, &g, nullptr, nullptr, nullptr)) != cudaSuccess) return err;
+    if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureUnsupported;
     cudaGraphConditionalHandle h;
-    if ((err = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return finish(err);
-    cudaMemsetAsync(H->d_x, 0, N0 * sizeof(double), H->cap);
-    cudaMemsetAsync(H->d_p, 0, N0 * sizeof(double), H->cap);
-    cudaMemcpyAsync(H->d_r, H->d_b, N0 * sizeof(double), cudaMemcpyDeviceToDevice, H->cap);
+    if ((err = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return err;
+    cudaMemsetAsync(H->d_x, 0, N0 * sizeof(double), cs_stream);
+    cudaMemsetAsync(H->d_p, 0, N0 * sizeof(double), cs_stream);
+    cudaMemcpyAsync(H->d_r, H->d_b, N0 * sizeof(double), cudaMemcpyDeviceToDevice, cs_stream);
     if (!H->symmetric) {
-        cudaMemsetAsync(H->d_q, 0, N0 * sizeof(double), H->cap);
-        cudaMemcpyAsync(H->d_rh, H->d_b, N0 * sizeof(double), cudaMemcpyDeviceToDevice, H->cap);
+        cudaMemsetAsync(H->d_q, 0, N0 * sizeof(double), cs_stream);
+        cudaMemcpyAsync(H->d_rh, H->d_b, N0 * sizeof(double), cudaMemcpyDeviceToDevice, cs_stream);
     }
-    dot(H, H->d_b, H->d_b, N0, 3, H->cap);
+    dot(H, H->d_b, H->d_b, N0, 3, cs_stream);
     SN_COUNT_LAUNCH();
-    if (H->symmetric) pcg_start_kernel<<<1, 1, 0, H->cap>>>(H->d_s, H->d_it, h);
-    else bicg_start_kernel<<<1, 1, 0, H->cap>>>(H->d_s, H->d_it, h);
-    H->pro_launches = g_launches.load() - count0;
+    if (H->symmetric) pcg_start_kernel<<<1, 1, 0, cs_stream>>>(H->d_s, H->d_it, h);
+    else bicg_start_kernel<<<1, 1, 0, cs_stream>>>(H->d_s, H->d_it, h);
+    *pro = g_launches.load() - count0;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
-    if ((err = cudaStreamGetCaptureInfo(H->cap, &cs, nullptr, nullptr, &deps, nullptr, &ndeps)) != cudaSuccess)
-        return finish(err);
+    if ((err = cudaStreamGetCaptureInfo(cs_stream, &cs, nullptr, nullptr, &deps, nullptr, &ndeps)) != cudaSuccess) {
+        g_launches.store(count0);
+        return err;
+    }
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     cudaGraphNode_t loop;
-    if ((err = cudaGraphAddNode(&loop, g, deps, nullptr, ndeps, &cp)) != cudaSuccess) return finish(err);
-    if ((err = cudaStreamUpdateCaptureDependencies(H->cap, &loop, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
-        return finish(err);
-    body = cp.conditional.phGraph_out[0];
-    if ((err = cudaStreamBeginCaptureToGraph(H->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-        return finish(err);
-    body_open = true;
+    if ((err = cudaGraphAddNode(&loop, g, deps, nullptr, ndeps, &cp)) != cudaSuccess ||
+        (err = cudaStreamUpdateCaptureDependencies(cs_stream, &loop, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+            cudaSuccess) {
+        g_launches.store(count0);
+        return err;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((err = cudaStreamBeginCaptureToGraph(H->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess) {
+        g_launches.store(count0);
+        return err;
+    }
     const long long count1 = g_launches.load();
     cudaStream_t s = H->cap2;
     if (H->symmetric) {
@@ -596,19 +589,34 @@ cudaError_t record_krylov(DsaHierarchy* H, double tol, int max_iters) {
         SN_COUNT_LAUNCH();
         bicg_check_kernel<<<1, 1, 0, s>>>(H->d_s, H->d_it, tol, max_iters, h);
     }
-    H->body_launches = g_launches.load() - count1;
+    *body_count = g_launches.load() - count1;
     g_launches.store(count0);  // recorded, not run: launches are counted when the graph runs
-    if ((err = cudaGetLastError()) != cudaSuccess) return finish(err);
+    cudaError_t lerr = cudaGetLastError();
     cudaGraph_t b2 = nullptr;
     err = cudaStreamEndCapture(H->cap2, &b2);
-    body_open = false;
-    if (err != cudaSuccess) return finish(err);
-    err = finish(cudaSuccess);
-    if (err == cudaSuccess) {
+    if (lerr != cudaSuccess) return lerr;
+    return err;
+}
+
+// Records the solve as a graph of its own (one launch per solve, see emit_krylov).
+cudaError_t record_krylov(DsaHierarchy* H, double tol, int max_iters) {
+    cudaError_t err;
+    if (!H->cap && (err = cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking)) != cudaSuccess) return err;
+    if (H->krylov_graph) cudaGraphExecDestroy(H->krylov_graph);
+    H->krylov_graph = nullptr;
+    if ((err = cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return err;
+    cudaError_t e = emit_krylov(H, H->cap, tol, max_iters, &H->pro_launches, &H->body_launches);
+    cudaGraph_t g2 = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(H->cap, &g2);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&H->krylov_graph, g2, 0);
+    if (g2) cudaGraphDestroy(g2);
+    if (e != cudaSuccess) H->krylov_graph = nullptr;
+    if (e == cudaSuccess) {
         H->krylov_tol = tol;
         H->krylov_max = max_iters;
     }
-    return err;
+    return e;
 }
 
 // Solves D_ff x = b by one launch of the recorded Krylov solve; the iteration count stays on the
@@ -617,8 +625,21 @@ cudaError_t krylov_solve(DsaHierarchy* H, double tol, int max_iters, cudaStream_
     cudaError_t err;
     const bool want32 = H->vcycle_mode == SN_VCYCLE_FP32 || (H->vcycle_mode == SN_VCYCLE_AUTO && tol >= 1e-8);
     if (want32 && (err = upload32(H)) != cudaSuccess) return err;
-    if (!H->krylov_graph || H->krylov_tol != tol || H->krylov_max != max_iters || H->pc32 != want32) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if ((err = cudaStreamIsCapturing(s, &cs)) != cudaSuccess) return err;
+    if (cs == cudaStreamCaptureStatusActive) {
+        // inside an enclosing capture (a recorded outer iteration): the loop becomes a nested WHILE
+        // node; its launches are counted when the enclosing graph runs (dsa_take_iters)
         H->pc32 = want32;
+        long long pro = 0, body = 0;
+        err = emit_krylov(H, s, tol, max_iters, &pro, &body);
+        H->body_launches = body;
+        H->nested_pro_launches = pro;
+        return err;
+    }
+    if (!H->krylov_graph || H->krylov_tol != tol || H->krylov_max != max_iters || H->krylov_pc32 != want32) {
+        H->pc32 = want32;
+        H->krylov_pc32 = want32;
         if ((err = record_krylov(H, tol, max_iters)) != cudaSuccess) return err;
     }
     g_launches.fetch_add(H->pro_launches, std::memory_order_relaxed);
@@ -648,6 +669,17 @@ void dsa_free(DsaHierarchy* H) {
 }
 
 int dsa_thick_count(const DsaHierarchy* H) { return H ? H->nt : 0; }
+
+// Device copies a solve to tolerance tol needs (made before a solve is recorded into a graph).
+cudaError_t dsa_prepare(DsaHierarchy* H, double tol) {
+    cudaError_t err = upload(H);
+    if (err != cudaSuccess || H->nt == 0) return err;
+    const bool want32 = H->vcycle_mode == SN_VCYCLE_FP32 || (H->vcycle_mode == SN_VCYCLE_AUTO && tol >= 1e-8);
+    if (want32) err = upload32(H);
+    return err;
+}
+
+long long dsa_nested_prologue_launches(const DsaHierarchy* H) { return H ? H->nested_pro_launches : 0; }
 
 cudaError_t dsa_apply(DsaHierarchy* H, const double* x, double* y, cudaStream_t s) {
     cudaError_t err = upload(H);

@@ -64,6 +64,8 @@ struct DsaHierarchy {
     int* d_it = nullptr;                      // [0] iterations of the current solve, [1] running total
     unsigned char* d_emask = nullptr;         // per element: 1 = thick (Algorithm 1's restrictions)
     long long pro_launches = 0, body_launches = 0;  // kernels in the prologue / one loop iteration
+    long long nested_pro_launches = 0;              // prologue kernels of a solve recorded inside another graph
+    bool krylov_pc32 = false;                       // V-cycle arithmetic krylov_graph was recorded with
     cudaStream_t cap = nullptr, cap2 = nullptr;     // private capture streams
 };
 

@@ -186,6 +186,16 @@ struct sn_mesh {
     sn::DsaHierarchy* dsa_t = nullptr;  // D_ff^T for the adjoint of a nonsymmetric operator (built on demand)
     double* d_krylov = nullptr;     // flexible GMRES workspace (basis, preconditioned basis, scratch)
     int krylov_restart = 0;
+    // recorded outer iteration (one graph launch per solve; sn_api.cpp)
+    cudaGraphExec_t iter_graph = nullptr;
+    std::vector<double> iter_key;       // options and buffers the graph was recorded for
+    long long ig_pro = 0, ig_outer = 0, ig_inner = 0;  // kernels in the prologue / outer body / inner body
+    double* d_ig = nullptr;             // device scalars (sn_iter_graph.cu layout) + residual history
+    int* d_igi = nullptr;               // device integers
+    size_t ig_doubles = 0, ig_hist_cap = 0;
+    double* d_igv = nullptr;            // 3 x ne x n: iterate, V_j copy, Z_j work vector
+    cudaStream_t ig_stream[3] = {};     // capture streams: graph, outer body, inner body
+    bool capture_no_pdl = false;        // record level chains without programmatic dependent launch
     int dsa_key_dsa = -1, dsa_key_rule = -1, dsa_key_sigma = -1, dsa_key_op = -1;
     double dsa_key_eta = 0;
     std::vector<unsigned char> dsa_key_mask;
@@ -278,6 +288,8 @@ cudaError_t build_tiles(sn_mesh* m, int edge, cudaStream_t s);
 void free_tiles(sn_mesh* m);
 cudaError_t compute_mass(sn_mesh* m, cudaStream_t s);
 void drop_level_graphs(sn_mesh* m);
+void drop_iter_graph(sn_mesh* m);
+cudaError_t prepare_recorded_sweep(sn_mesh* m, int precision, cudaStream_t s);
 // batched sweep over all instances of a batch (sn_sweep.cu)
 cudaError_t batch_build_worklist(sn_batch* b, cudaStream_t s);
 cudaError_t batch_enqueue_sweep(sn_batch* b, int precision, cudaStream_t s);  // level schedule, capturable
@@ -325,6 +337,28 @@ cudaError_t launch_multidot(const double* V, int k, long long n, const double* w
 cudaError_t launch_multiaxpy(const double* V, int k, long long n, const double* c, double sign, double* w,
                              cudaStream_t s);
 cudaError_t launch_normalize(const double* x, long long n, double* partial, double* s, double* y, cudaStream_t st);
+// the same with the basis size k = *kdev + kofs read on the device (recorded fGMRES)
+cudaError_t launch_multidot_dev(const double* V, const int* kdev, int kofs, int kmax, long long n, const double* w,
+                                double* partial, double* h, cudaStream_t s);
+cudaError_t launch_multiaxpy_dev(const double* V, const int* kdev, int kofs, long long n, const double* c, double sign,
+                                 double* w, cudaStream_t s);
+// sn_iter_graph.cu: device scalars of the recorded outer iterations (layout in that file)
+size_t iter_graph_doubles(int k);
+int iter_graph_y_offset(int k);
+cudaError_t ig_init(double* gd, int* gi, cudaStream_t s);
+cudaError_t ig_si_residual(const double* rr, double* gd, int* gi, double* hist, int hist_len, cudaStream_t s);
+cudaError_t ig_si_end(double* gd, int* gi, double tol, int max_iters, cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t ig_si_checkpoint(const double* phi, double* ckpt, long long M, int* gi, int every, int max_ck,
+                             cudaStream_t s);
+cudaError_t ig_gm_cycle_start(const double* rr, double* gd, int* gi, int k, double tol, int max_iters, double* hist,
+                              int hist_len, cudaGraphConditionalHandle outer, cudaGraphConditionalHandle inner,
+                              cudaStream_t s);
+cudaError_t ig_gm_arnoldi(const double* hd, double* gd, int* gi, int k, double tol, int max_iters, double drop,
+                          double* hist, int hist_len, cudaGraphConditionalHandle inner, cudaStream_t s);
+cudaError_t ig_gm_solve(double* gd, const int* gi, int k, cudaStream_t s);
+cudaError_t ig_get_col(const double* V, const int* gi, int ofs, long long M, double* out, cudaStream_t s);
+cudaError_t ig_set_col(double* V, const int* gi, long long M, const double* in, cudaStream_t s);
+cudaError_t ig_next_basis(const double* w, const double* gd, const int* gi, long long M, double* V, cudaStream_t s);
 // sn_dsa.cu
 // Assembles D_ff (dsa_op: SN_DSA_OP_SIP / NIP / MNIP; transposed: D_ff^T, for the adjoint of a
 // nonsymmetric operator) and its multigrid hierarchy.  Returns null with err set; *void_conflict
@@ -333,6 +367,8 @@ DsaHierarchy* dsa_build(const sn_mesh* m, const unsigned char* mask, int dsa_sig
                         std::string& err, bool* void_conflict = nullptr);
 void dsa_free(DsaHierarchy* h);
 int dsa_thick_count(const DsaHierarchy* h);
+cudaError_t dsa_prepare(DsaHierarchy* h, double tol);
+long long dsa_nested_prologue_launches(const DsaHierarchy* h);
 // y = D_ff x (scatter into [elem][node], zeros elsewhere)
 cudaError_t dsa_apply(DsaHierarchy* h, const double* x, double* y, cudaStream_t s);
 // phi_out += E_f D_ff^{-1} Sigma_f r (transpose = false) or E_f Sigma_f H^{-1} r (transpose = true, with H

@@ -15,9 +15,11 @@ constexpr int kThreads = 256;
 constexpr int kMaxBasis = 64;
 
 // partial[i * nblocks + b] = sum over block b's slice of V_i . w, for i < k
+// (kdev non-null: k = *kdev + kofs, read on the device, for the recorded fGMRES iteration)
 __global__ void multidot_partial_kernel(const double* V, int k, long long n, const double* w, double* partial,
-                                        int nblocks) {
+                                        int nblocks, const int* kdev, int kofs) {
     __shared__ double sh[kThreads];
+    if (kdev) k = *kdev + kofs;
     const long long chunk = (n + gridDim.x - 1) / gridDim.x;
     const long long lo = blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
     for (int i = 0; i < k; ++i) {
@@ -35,9 +37,10 @@ __global__ void multidot_partial_kernel(const double* V, int k, long long n, con
     }
 }
 
-__global__ void multidot_final_kernel(const double* partial, int nblocks, double* out) {
+__global__ void multidot_final_kernel(const double* partial, int nblocks, double* out, const int* kdev, int kofs) {
     __shared__ double sh[kThreads];
     const int i = blockIdx.x;
+    if (kdev && i >= *kdev + kofs) return;
     double s = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(size_t)i * nblocks + b];
     sh[threadIdx.x] = s;
@@ -50,9 +53,11 @@ __global__ void multidot_final_kernel(const double* partial, int nblocks, double
 }
 
 // w += sign * sum_i c[i] V_i  (c on the device)
-__global__ void multiaxpy_kernel(const double* V, int k, long long n, const double* c, double sign, double* w) {
+__global__ void multiaxpy_kernel(const double* V, int k, long long n, const double* c, double sign, double* w,
+                                 const int* kdev, int kofs) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
+    if (kdev) k = *kdev + kofs;
     double s = 0.0;
     for (int i = 0; i < k; ++i) s += c[i] * V[(size_t)i * n + t];
     w[t] += sign * s;
@@ -80,16 +85,35 @@ cudaError_t launch_multidot(const double* V, int k, long long n, const double* w
     if (k < 1 || k > kMaxBasis) return cudaErrorInvalidValue;
     const int nb = krylov_blocks(n);
     SN_COUNT_LAUNCH();
-    multidot_partial_kernel<<<nb, kThreads, 0, s>>>(V, k, n, w, partial, nb);
+    multidot_partial_kernel<<<nb, kThreads, 0, s>>>(V, k, n, w, partial, nb, nullptr, 0);
     SN_COUNT_LAUNCH();
-    multidot_final_kernel<<<k, kThreads, 0, s>>>(partial, nb, h);
+    multidot_final_kernel<<<k, kThreads, 0, s>>>(partial, nb, h, nullptr, 0);
+    return cudaGetLastError();
+}
+
+// As launch_multidot with k = *kdev + kofs read on the device (at most kmax)
+cudaError_t launch_multidot_dev(const double* V, const int* kdev, int kofs, int kmax, long long n, const double* w,
+                                double* partial, double* h, cudaStream_t s) {
+    if (kmax < 1 || kmax > kMaxBasis) return cudaErrorInvalidValue;
+    const int nb = krylov_blocks(n);
+    SN_COUNT_LAUNCH();
+    multidot_partial_kernel<<<nb, kThreads, 0, s>>>(V, kmax, n, w, partial, nb, kdev, kofs);
+    SN_COUNT_LAUNCH();
+    multidot_final_kernel<<<kmax, kThreads, 0, s>>>(partial, nb, h, kdev, kofs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_multiaxpy_dev(const double* V, const int* kdev, int kofs, long long n, const double* c, double sign,
+                                 double* w, cudaStream_t s) {
+    SN_COUNT_LAUNCH();
+    multiaxpy_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(V, 0, n, c, sign, w, kdev, kofs);
     return cudaGetLastError();
 }
 
 cudaError_t launch_multiaxpy(const double* V, int k, long long n, const double* c, double sign, double* w,
                              cudaStream_t s) {
     SN_COUNT_LAUNCH();
-    multiaxpy_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(V, k, n, c, sign, w);
+    multiaxpy_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(V, k, n, c, sign, w, nullptr, 0);
     return cudaGetLastError();
 }
 

@@ -1546,10 +1546,12 @@ cudaError_t build_level_groups(sn_mesh* m, int G) {
     }
     if ((err = cudaMemcpy(L.gitems, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess)
         return err;
-    L.gstreams.resize(G, nullptr);
+    // two sets of fork/join streams and events: a recorded outer iteration captures level chains
+    // into two nested graphs at once (outer and inner loop bodies), and a stream joins one capture
+    L.gstreams.resize(2 * G, nullptr);
     for (auto& st : L.gstreams)
         if ((err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return err;
-    L.gevents.resize(G + 1, nullptr);
+    L.gevents.resize(2 * (G + 1), nullptr);
     for (auto& ev : L.gevents)
         if ((err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return err;
     L.groups = G;
@@ -1701,7 +1703,7 @@ static cudaError_t enqueue_chain(sn_mesh* m, int kind, const SweepArgs& a, const
         const unsigned g = grid_for(e - b, bs), gn = node_grid(m, e - b, bs);
         cudaError_t lerr = cudaSuccess;
         const double* none = nullptr;
-        const bool pdl = !first;
+        const bool pdl = !first && !m->capture_no_pdl;
         first = false;
         if (kind == 3 && a.ainv)
             SN_DISPATCH(m->dim, m->p, (lerr = launch_k(pdl, node_level_kernel<D_, P_, 0, true>, gn, bs, s, a, (const double*)m->d_src, b, e)));
@@ -1742,19 +1744,39 @@ static cudaError_t enqueue_levels(sn_mesh* m, int kind, cudaStream_t s) {
     if (L.groups != m->level_groups) return cudaErrorInvalidValue;  // built before the capture starts
     cudaError_t err;
     a.items = L.gitems;
-    if ((err = cudaEventRecord(L.gevents[0], s)) != cudaSuccess) return err;
+    const int set = s == m->ig_stream[2] ? 1 : 0;  // the inner loop body of a recorded iteration
+    cudaStream_t* gst = L.gstreams.data() + set * L.groups;
+    cudaEvent_t* gev = L.gevents.data() + set * (L.groups + 1);
+    if ((err = cudaEventRecord(gev[0], s)) != cudaSuccess) return err;
     for (int g = 0; g < L.groups; ++g) {
-        cudaStream_t gs = L.gstreams[g];
-        if ((err = cudaStreamWaitEvent(gs, L.gevents[0], 0)) != cudaSuccess) return err;
+        cudaStream_t gs = gst[g];
+        if ((err = cudaStreamWaitEvent(gs, gev[0], 0)) != cudaSuccess) return err;
         if ((err = enqueue_chain(m, kind, a, L.gptr[g], gs)) != cudaSuccess) return err;
-        if ((err = cudaEventRecord(L.gevents[1 + g], gs)) != cudaSuccess) return err;
-        if ((err = cudaStreamWaitEvent(s, L.gevents[1 + g], 0)) != cudaSuccess) return err;
+        if ((err = cudaEventRecord(gev[1 + g], gs)) != cudaSuccess) return err;
+        if ((err = cudaStreamWaitEvent(s, gev[1 + g], 0)) != cudaSuccess) return err;
     }
     return cudaSuccess;
 }
 
 static cudaError_t launch_levels_graph(sn_mesh* m, int kind, cudaStream_t s) {
     cudaError_t err;
+    auto kernels_per_sweep = [m]() {
+        long long kernels = m->levels.n_levels;
+        if (m->level_groups > 1) {
+            kernels = 0;
+            for (const auto& ptr : m->levels.gptr) kernels += (long long)ptr.size() - 1;
+        }
+        return kernels;
+    };
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if ((err = cudaStreamIsCapturing(s, &cs)) != cudaSuccess) return err;
+    if (cs == cudaStreamCaptureStatusActive) {
+        // recorded into an enclosing graph (an outer iteration): the level chain itself, not a
+        // nested graph launch; the direction groups must have been built before the capture
+        if (m->level_groups > 1 && m->levels.groups != m->level_groups) return cudaErrorStreamCaptureUnsupported;
+        g_launches.fetch_add(kernels_per_sweep(), std::memory_order_relaxed);
+        return enqueue_levels(m, kind, s);
+    }
     if (!m->level_graph[kind]) {
         if (!m->cap_stream && (err = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
             return err;
@@ -1773,12 +1795,7 @@ static cudaError_t launch_levels_graph(sn_mesh* m, int kind, cudaStream_t s) {
             return err;
         }
     }
-    long long kernels = m->levels.n_levels;
-    if (m->level_groups > 1) {
-        kernels = 0;
-        for (const auto& ptr : m->levels.gptr) kernels += (long long)ptr.size() - 1;
-    }
-    g_launches.fetch_add(kernels, std::memory_order_relaxed);
+    g_launches.fetch_add(kernels_per_sweep(), std::memory_order_relaxed);
     return cudaGraphLaunch(m->level_graph[kind], s);
 }
 
@@ -1788,6 +1805,23 @@ void drop_level_graphs(sn_mesh* m) {
             cudaGraphExecDestroy(g);
             g = nullptr;
         }
+    drop_iter_graph(m);  // it holds copies of the level chains
+}
+
+void drop_iter_graph(sn_mesh* m) {
+    if (m->iter_graph) cudaGraphExecDestroy(m->iter_graph);
+    m->iter_graph = nullptr;
+    m->iter_key.clear();
+}
+
+// Everything a recorded sweep of this precision needs that allocates or launches set-up work: the
+// operator cache and the direction-group lists of the level schedule.
+cudaError_t prepare_recorded_sweep(sn_mesh* m, int precision, cudaStream_t s) {
+    cudaError_t err = prepare_operator_cache(m, precision, s);
+    if (err != cudaSuccess) return err;
+    if (m->schedule == SCHED_LEVELS && m->level_groups > 1 && m->levels.groups != m->level_groups)
+        err = build_level_groups(m, m->level_groups);
+    return err;
 }
 
 cudaError_t prepare_operator_cache(sn_mesh* m, int precision, cudaStream_t s) {

@@ -54,7 +54,7 @@ class IterOpts(C.Structure):
                 ("max_checkpoints", C.c_int), ("warm_start", C.c_int), ("outer", C.c_int), ("restart", C.c_int),
                 ("dsa_operator", C.c_int), ("dsa_vcycle", C.c_int), ("dir_begin", C.c_int), ("dir_end", C.c_int),
                 ("exchange", C.c_void_p), ("exchange_ctx", C.c_void_p), ("exchange_buf", C.c_void_p),
-                ("refine_drop", C.c_double)]
+                ("refine_drop", C.c_double), ("host_loop", C.c_int)]
 
 
 # sn_exchange_fn: sn_status (*)(double* phi_partial, long long n, void* stream, void* ctx)
@@ -151,14 +151,16 @@ def _stream(stream):
 def make_opts(dsa="thick", thick_rule="sigma_s", eta=1.0, mask=None, dsa_sigma="sigma_s", tol=1e-8,
               inner_tol=1e-4, max_iters=1000, inner_max_iters=200, precision="fp64", checkpoint_every=0,
               checkpoints=None, warm_start=False, outer="si", restart=30, operator="sip", vcycle="auto",
-              refine_drop=0.0):
+              refine_drop=0.0, host_loop=False):
     """Options of sn_source_iterate / sn_adjoint_iterate.  operator: the DSA operator D_ff,
     "sip" (symmetric, conjugate gradients), "nip" (Eq. NIP) or "mnip" (Eq. NIP with the penalty
     of Eq. ModifiedF0); the nonsymmetric two are solved by BiCGStab.  vcycle: arithmetic of the
     multigrid preconditioner, "auto" (float32 when inner_tol >= 1e-8), "fp64" or "fp32".
     precision: "fp64", "fp32", "fp32_refine" or "fp32_mixed" (fGMRES with float32 sweeps inside
     each restart cycle and a float64 true residual between cycles; a cycle ends when its residual
-    estimate fell by refine_drop, 0 = 1e-3)."""
+    estimate fell by refine_drop, 0 = 1e-4).  host_loop: run the outer iteration as a host loop
+    (one synchronisation per iteration, device time split into ms_sweep / ms_dsa) instead of one
+    recorded graph launch."""
     o = IterOpts()
     _lib.sn_iter_opts_default(C.byref(o))
     o.dsa = _DSA[dsa] if isinstance(dsa, str) else int(dsa)
@@ -184,6 +186,7 @@ def make_opts(dsa="thick", thick_rule="sigma_s", eta=1.0, mask=None, dsa_sigma="
     o.dsa_operator = _DSA_OP[operator] if isinstance(operator, str) else int(operator)
     o.dsa_vcycle = {"auto": 0, "fp64": 1, "fp32": 2}[vcycle] if isinstance(vcycle, str) else int(vcycle)
     o.refine_drop = float(refine_drop)
+    o.host_loop = int(bool(host_loop))
     o._keep = keep
     return o
 

@@ -42,6 +42,46 @@ def test_batched_sweep_equals_single_sweeps(sn, schedule, precision):
         assert torch.equal(m.sweep(phi, precision=precision), out)
 
 
+@pytest.fixture(scope="module")
+def oracle_runs():
+    """The oracle's K = 4 DSA-accelerated iterates and its converged solution of every instance."""
+    from oracle import Transport
+    from oracle.dsa import DSA, thick_mask
+    out = []
+    for p in small_instances():
+        T = Transport(p)
+        d = DSA(T, thick_mask(p))
+        out.append((T.source_iterate(dsa=d, tol=0.0, max_iters=4)["phi"],
+                    T.source_iterate(dsa=d, tol=1e-14, max_iters=4000)["phi"]))
+    return out
+
+
+@pytest.mark.parametrize("schedule", [("levels", 64, 0), ("dataflow", 128, 0)])
+def test_batched_iterates_match_the_oracle(sn, schedule, oracle_runs):
+    """The batched source iteration (one union CG over every instance's thick-DSA system, one
+    V-cycle over the union of their hierarchies, Algorithm 2 per instance) against the oracle's
+    own iteration of each instance: K = 4 iterates within the derived DSA-iterate tolerance, and
+    the converged solutions within 1e-9 (a 1e-12 residual times the conditioning of Eq. schur)."""
+    from oracle.dsa import thick_mask
+    from tolerances import dsa_iterate_tol
+    probs = small_instances()
+    meshes = [sn.Mesh.from_problem(p) for p in probs]
+    batch = sn.Batch(meshes)
+    batch.set_schedule(*schedule)
+    res = batch.source_iterate(dsa="thick", thick_rule="sigma_t_h", tol=0.0, max_iters=4, inner_tol=1e-15,
+                               inner_max_iters=3000)
+    assert res["iters"] == [4] * len(probs)
+    for k, (p, (ref_k, _)) in enumerate(zip(probs, oracle_runs)):
+        err = float(np.abs(res["phi"][k].cpu().numpy() - ref_k).max() / np.abs(ref_k).max())
+        assert err <= dsa_iterate_tol(p, thick_mask(p)), (k, err)
+    res = batch.source_iterate(dsa="thick", thick_rule="sigma_t_h", tol=1e-12, max_iters=3000, inner_tol=1e-12,
+                               inner_max_iters=1000)
+    assert res["converged"]
+    for k, (p, (_, ref)) in enumerate(zip(probs, oracle_runs)):
+        err = float(np.abs(res["phi"][k].cpu().numpy() - ref).max() / np.abs(ref).max())
+        assert err < 1e-9, (k, err)
+
+
 @pytest.mark.parametrize("schedule", [("levels", 64, 0), ("dataflow", 128, 0)])
 def test_batched_source_iteration_matches_single_solves(sn, schedule):
     probs = small_instances()

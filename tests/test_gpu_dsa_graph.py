@@ -136,13 +136,13 @@ def test_float32_vcycle_leaves_the_fixed_point_alone(sn):
 
 @pytest.mark.parametrize("outer", ["si", "fgmres"])
 def test_solves_report_sweep_and_dsa_device_time(sn, outer):
-    """sn_iter_stats splits a solve's device time into transport updates and DSA solves."""
+    """sn_iter_stats splits a solve's device time into transport updates and DSA solves (host loop)."""
     prob = inputs.config1()
     m = sn.Mesh.from_problem(prob)
-    r = m.source_iterate(dsa="thick", outer=outer, tol=1e-8, max_iters=300)
+    r = m.source_iterate(dsa="thick", outer=outer, tol=1e-8, max_iters=300, host_loop=True)
     assert r["converged"] and r["ms_sweep"] > 0 and r["ms_dsa"] > 0
     assert r["ms_sweep"] + r["ms_dsa"] <= r["ms"] * 1.02 + 0.1
-    n = m.source_iterate(dsa="none", outer=outer, tol=1e-3, max_iters=60)
+    n = m.source_iterate(dsa="none", outer=outer, tol=1e-3, max_iters=60, host_loop=True)
     assert n["ms_dsa"] == 0 and n["ms_sweep"] > 0
     g = torch.ones(m.shape, dtype=torch.float64, device="cuda")
     a = m.adjoint_iterate(g, dsa="thick", outer=outer, tol=1e-8, max_iters=300)

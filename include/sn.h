@@ -352,6 +352,14 @@ sn_status sn_dsa_solve(sn_mesh* mesh, const sn_iter_opts* opts, const double* b,
 sn_status sn_get_angular_flux(sn_mesh* mesh, int d, int adjoint, int precision, double* out, void* stream);
 
 /*
+ * Diagnostic: the upwind level of every element for direction d (host, n_elem ints), as the
+ * device's Kahn pass computed it when the mesh was created (Sec. 1: the transport update is a
+ * forward solve in an upwind order; level 0 has no upwind neighbour, an element's level is one
+ * more than its highest upwind neighbour's).  SN_ERR_ARG for d outside [0, n_dirs).
+ */
+sn_status sn_get_levels(const sn_mesh* mesh, int d, int* levels);
+
+/*
  * sn_scalar_flux_noalloc: the scalar-flux reduction of a transport update without any device
  * allocation.  The paper has no counterpart; it exists for callers that cannot call cudaMalloc:
  * frameworks whose caching allocator owns all device memory (a cudaMalloc behind its back can fail

@@ -218,6 +218,14 @@ sn_status sn_mesh_destroy(sn_mesh* m) {
     return SN_OK;
 }
 
+sn_status sn_get_levels(const sn_mesh* m, int d, int* levels) {
+    if (!m || !levels) return fail(SN_ERR_ARG, "null argument");
+    if (d < 0 || d >= m->nd) return fail(SN_ERR_ARG, "direction %d not in [0, %d)", d, m->nd);
+    if (m->levels.h_level.size() != (size_t)m->nd * m->ne) return fail(SN_ERR_ARG, "no level sets");
+    std::memcpy(levels, m->levels.h_level.data() + (size_t)d * m->ne, m->ne * sizeof(int));
+    return SN_OK;
+}
+
 sn_status sn_mesh_get_info(const sn_mesh* m, sn_mesh_info* info) {
     if (!m || !info) return fail(SN_ERR_ARG, "null argument");
     info->n_elem = m->ne;

@@ -907,6 +907,43 @@ __device__ __forceinline__ bool wait_neighbours(const SweepArgs& a, const int* d
     return true;
 }
 
+// As wait_neighbours with the face fluxes already loaded, every pending word polled in each round
+// (their loads in flight together) rather than one face after another.
+template <int DIM, int P, bool ADJ>
+__device__ __forceinline__ bool wait_neighbours_all(const SweepArgs& a, const double* F, const int* done, int epoch,
+                                                    int d, int e, unsigned long long deadline) {
+    const int* flag[2 * DIM];
+    int pending = 0;
+#pragma unroll
+    for (int fc = 0; fc < 2 * DIM; ++fc) {
+        flag[fc] = nullptr;
+        if (ADJ ? F[fc] > 0.0 : F[fc] < 0.0) {
+            const int u = neighbor<DIM, P>(a, e, fc);
+            if (u >= 0) {
+                flag[fc] = done + (size_t)d * a.ne + u;
+                ++pending;
+            }
+        }
+    }
+    int polls = 0;
+    while (pending > 0) {
+        int v[2 * DIM];
+#pragma unroll
+        for (int fc = 0; fc < 2 * DIM; ++fc) v[fc] = flag[fc] ? ld_acquire(flag[fc]) : epoch;
+#pragma unroll
+        for (int fc = 0; fc < 2 * DIM; ++fc)
+            if (flag[fc] && v[fc] == epoch) {
+                flag[fc] = nullptr;
+                --pending;
+            }
+        if (pending > 0 && ++polls > 64) {
+            if (globaltimer() > deadline) return false;
+            __nanosleep(64);
+        }
+    }
+    return true;
+}
+
 // Dataflow schedule of the cached sweep, one lane per node: a warp claims 32 / N items at a time
 // (a slice of a 32-item chunk of the padded list, so claims still follow level order), waits for
 // their neighbours, solves, synchronises, and each item's lane 0 fences and publishes the
@@ -944,17 +981,20 @@ __global__ void __launch_bounds__(128) node_dataflow_kernel(SweepArgs a, Dataflo
         // loads that read no angular flux go out before the waits, so they overlap them
         NodeStage<DIM, P, typename std::conditional<MODE == 1, float, double>::type> st;
         if (valid) node_stage<DIM, P, MODE, ADJ>(a, mu, d, e, r, st);
-        const bool ok = valid ? wait_neighbours<DIM, P, ADJ>(a, f.done, f.epoch, d, e, deadline) : true;
+        // one lane per item polls (all of its upwind words at once); the warp barrier then orders
+        // that lane's acquire before every lane's reads of the neighbours
+        const bool ok = (valid && r == 0) ? wait_neighbours_all<DIM, P, ADJ>(a, st.F, f.done, f.epoch, d, e, deadline)
+                                          : true;
         if (!__all_sync(0xffffffffu, ok)) {
             if (lane == 0) atomicExch(f.error, 1);
             break;
         }
-        node_finish<DIM, P, MODE, ADJ>(a, st, d, e, r, src0, valid);
         __syncwarp();
-        if (valid && r == 0) {
-            __threadfence();
-            st_release(f.done + (size_t)d * a.ne + e, f.publish);
-        }
+        node_finish<DIM, P, MODE, ADJ>(a, st, d, e, r, src0, valid);
+        // the warp barrier orders the item's N lanes' stores before lane 0's release store, and a
+        // release is cumulative: a waiter that acquires the word sees all N values
+        __syncwarp();
+        if (valid && r == 0) st_release(f.done + (size_t)d * a.ne + e, f.publish);
     }
 }
 
@@ -1092,11 +1132,31 @@ __global__ void __launch_bounds__(512) barrier_sweep_kernel(SweepArgs a, Barrier
     __shared__ int s_fail;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int slot = lane / N, r = lane - slot * N, src0 = slot < IPW ? slot * N : 0;
+    using R = typename std::conditional<MODE == 1, float, double>::type;
     const long long per_pass = (long long)(blockDim.x >> 5) * IPW, stride = per_pass * gridDim.x;
     const unsigned long long deadline = globaltimer() + b.timeout_ns;
+    // the first pass of a level reads nothing of the previous levels until its face terms, so its
+    // stage (item, face fluxes, source row, inverse row) is loaded before the barrier
+    auto load_first = [&](int L, int& d, int& e, bool& valid, NodeStage<DIM, P, R>& st) {
+        const long long lo = b.level_ptr[L], hi = b.level_ptr[L + 1];
+        const long long t = lo + blockIdx.x * per_pass + warp * IPW + slot;
+        valid = slot < IPW && t < hi;
+        d = e = 0;
+        if (valid) {
+            const int2 it = a.items[t];
+            d = it.x;
+            e = it.y;
+            node_stage<DIM, P, MODE, false>(a, nullptr, d, e, r, st);
+        }
+    };
+    int d0 = 0, e0 = 0;
+    bool v0 = false;
+    NodeStage<DIM, P, R> st0;
+    if (b.n_levels > 0) load_first(0, d0, e0, v0, st0);
     for (int L = 0; L < b.n_levels; ++L) {
         const long long lo = b.level_ptr[L], hi = b.level_ptr[L + 1];
-        for (long long base = lo + blockIdx.x * per_pass; base < hi; base += stride) {
+        node_finish<DIM, P, MODE, false>(a, st0, d0, e0, r, src0, v0);
+        for (long long base = lo + blockIdx.x * per_pass + stride; base < hi; base += stride) {
             const long long t = base + warp * IPW + slot;
             const bool valid = slot < IPW && t < hi;
             int d = 0, e = 0;
@@ -1107,11 +1167,12 @@ __global__ void __launch_bounds__(512) barrier_sweep_kernel(SweepArgs a, Barrier
             }
             node_item<DIM, P, MODE, false>(a, nullptr, d, e, r, src0, valid);
         }
+        if (L + 1 < b.n_levels) load_first(L + 1, d0, e0, v0, st0);
         __syncthreads();
         if (threadIdx.x == 0) {
             int fail = 0;
-            __threadfence();
-            if (!b.stall) atomicAdd(b.counter, 1);
+            // the CTA barrier orders every thread's stores before this release (cumulative)
+            if (!b.stall) asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(b.counter), "r"(1) : "memory");
             const int target = (L + 1) * (int)gridDim.x;
             int polls = 0;
             while (ld_acquire(b.counter) < target) {

@@ -90,6 +90,7 @@ def _load():
         "sn_dsa_apply": [vp, C.POINTER(IterOpts), vp, vp, vp],
         "sn_dsa_solve": [vp, C.POINTER(IterOpts), vp, vp, C.POINTER(C.c_int), vp],
         "sn_get_angular_flux": [vp, i, i, i, vp, vp],
+        "sn_get_levels": [vp, i, vp],
         "sn_mesh_set_schedule": [vp, i, i, i],
         "sn_mesh_set_operator_cache": [vp, i],
         "sn_debug_stall_next_sweep": [vp, d],
@@ -443,6 +444,12 @@ class Mesh:
         gt, gs, gq = (torch.empty(self.n_elem, dtype=torch.float64, device=phi.device) for _ in range(3))
         _check(_lib.sn_gradients(self._h, _ptr(phi), _ptr(mu), _ptr(gt), _ptr(gs), _ptr(gq), _stream(stream)))
         return gt, gs, gq
+
+    def levels(self, d):
+        """Upwind level of every element for direction d (the device's Kahn pass), host int array."""
+        out = np.empty(self.n_elem, dtype=np.int32)
+        _check(_lib.sn_get_levels(self._h, int(d), out.ctypes.data_as(C.c_void_p)))
+        return out
 
     def angular_flux(self, d, adjoint=False, precision="fp64", stream=None):
         import torch

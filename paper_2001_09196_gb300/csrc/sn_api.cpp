@@ -777,8 +777,9 @@ static sn_status fgmres(sn_mesh* m, const sn_iter_opts* o, double* x, sn_iter_st
 // A whole source iteration or flexible GMRES solve recorded once into a CUDA graph and launched as
 // one graph: the loops are WHILE conditional nodes whose conditions are set by device kernels
 // (sn_iter_graph.cu), the DSA solve is a nested WHILE node, and the host synchronises once per
-// solve instead of once per outer iteration.  Used for the level schedule on one process (the
-// persistent schedules carry a host-side epoch, and a sharded iteration calls back to the host).
+// solve instead of once per outer iteration.  Used for the level and dataflow schedules on one
+// process (the tiled and level-barrier schedules carry host-side state, and a sharded iteration
+// calls back to the host).
 
 // WHILE node (handle h) appended to the graph `s` is capturing; its body graph in *body.
 static cudaError_t add_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
@@ -810,7 +811,7 @@ static cudaError_t new_handle(cudaStream_t s, unsigned dflt, cudaGraphConditiona
 }
 
 static bool recordable(const sn_mesh* m, const sn_iter_opts* o) {
-    return !o->host_loop && !sharded(o) && m->schedule == sn::SCHED_LEVELS;
+    return !o->host_loop && !sharded(o) && (m->schedule == sn::SCHED_LEVELS || sn::dataflow_like(m->schedule));
 }
 
 // What a recorded iteration depends on: a graph is reused only for the same key.
@@ -820,6 +821,7 @@ static std::vector<double> iteration_key(const sn_mesh* m, const sn_iter_opts* o
             (double)o->inner_max_iters, (double)o->max_iters, o->refine_drop, (double)hist_len,
             (double)o->checkpoint_every, addr(o->checkpoints), (double)o->max_checkpoints, addr(m->dsa),
             m->dsa ? (double)m->dsa->vcycle_mode : -1.0, (double)m->level_groups, (double)m->block,
+            (double)m->schedule, (double)m->max_blocks_per_sm,
             addr(m->d_krylov), addr(m->d_ig), addr(m->d_igv), addr(m->d_psi32)};
 }
 
@@ -1033,6 +1035,11 @@ static sn_status run_recorded(sn_mesh* m, const sn_iter_opts* o, double* phi, sn
     double* x = m->d_igv;
     if (o->warm_start) CK(cudaMemcpyAsync(x, phi, M * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
     else CK(cudaMemsetAsync(x, 0, M * sizeof(double), s), "memset");
+    const bool df = sn::dataflow_like(m->schedule);
+    if (df) {  // every recorded sweep advances the device epoch once
+        const long long most = 4ll * (o->max_iters + 2) + 8;  // at most 3 sweeps per iteration
+        CK(sn::device_epoch_in(m, most, s), "epoch");
+    }
     CK(cudaGraphLaunch(m->iter_graph, s), "recorded iteration");
     CK(cudaMemcpyAsync(phi, x, M * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
     int hi[8] = {};
@@ -1044,6 +1051,12 @@ static sn_status run_recorded(sn_mesh* m, const sn_iter_opts* o, double* phi, sn
                            cudaMemcpyDeviceToHost, s), "copy");
     CK(cudaStreamSynchronize(s), "sync");
     *done = true;
+    if (df) {
+        CK(sn::device_epoch_out(m, s), "epoch");
+        bool timed_out = false;
+        CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
+        if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out");
+    }
     const int it = hi[0], cycles = hi[5];
     const bool converged = hi[3] != 0;
     if (hist_len > 0) {  // entries the solve did not reach stay zero, as in the host loops

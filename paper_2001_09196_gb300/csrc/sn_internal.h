@@ -77,6 +77,7 @@ struct DataflowArgs {
     unsigned long long timeout_ns;   // per-launch wait budget
     long long static_warps;          // > 0: static assignment, warp w takes slices w, w + static_warps, ...
                                      // (every warp of the grid resident); 0: slices claimed from `next`
+    const int* epoch_dev;            // non-null (recorded sweeps): epoch and publish value read here
 };
 
 struct LevelSets {
@@ -324,6 +325,9 @@ cudaError_t launch_axpy_norm(sn_mesh* m, const double* a, const double* b, doubl
 cudaError_t launch_copy(double* dst, const double* src, size_t n, cudaStream_t s);
 // Reads and clears the dataflow error word (synchronises the stream).
 cudaError_t take_sweep_error(sn_mesh* m, cudaStream_t s, bool* timed_out);
+// device copy of the dataflow epoch around a recorded iteration (see sn_sweep.cu)
+cudaError_t device_epoch_in(sn_mesh* m, long long max_sweeps, cudaStream_t s);
+cudaError_t device_epoch_out(sn_mesh* m, cudaStream_t s);
 cudaError_t launch_axpy_add(double* y, const double* x, size_t n, cudaStream_t s);  // y += x
 // sn_materials.cu: per-element sigma_t, sigma_s, q of the pseudo-scattering time step
 cudaError_t launch_pseudo_scattering(const double* sigma, const double* cv, const double* T, int ne, double dt,

@@ -826,6 +826,7 @@ __global__ void __launch_bounds__(128) sweep_dataflow_kernel(SweepArgs a, Datafl
     const int lane = threadIdx.x & 31;
     const long long n_chunks = f.n_items >> 5;
     const unsigned long long deadline = globaltimer() + f.timeout_ns;
+    if (f.epoch_dev) f.epoch = f.publish = *f.epoch_dev;
     unsigned long long mine = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     while (true) {
         // lane 0 claims the chunk and reads the error word; the warp acts on one broadcast value
@@ -956,6 +957,7 @@ __global__ void __launch_bounds__(128) node_dataflow_kernel(SweepArgs a, Dataflo
     const int src0 = slot < IPW ? slot * N : 0;
     const long long n_slices = (f.n_items >> 5) * SLICES;
     const unsigned long long deadline = globaltimer() + f.timeout_ns;
+    if (f.epoch_dev) f.epoch = f.publish = *f.epoch_dev;
     unsigned long long mine = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     while (true) {
         unsigned long long c = 0;
@@ -1544,10 +1546,10 @@ cudaError_t build_levels(sn_mesh* m, cudaStream_t s, bool* cycle) {
     if ((err = cudaMemcpyAsync(m->levels.padded_rev, padded_rev.data(), padded_rev.size() * sizeof(int2), cudaMemcpyHostToDevice, s)) != cudaSuccess) { cleanup(); return err; }
     if (!m->levels.done) {
         if ((err = cudaMalloc(&m->levels.done, total * sizeof(int))) != cudaSuccess) { cleanup(); return err; }
-        if ((err = cudaMalloc(&m->levels.ctrl, 2 * sizeof(unsigned long long))) != cudaSuccess) { cleanup(); return err; }
+        if ((err = cudaMalloc(&m->levels.ctrl, 3 * sizeof(unsigned long long))) != cudaSuccess) { cleanup(); return err; }
     }
     cudaMemsetAsync(m->levels.done, 0, total * sizeof(int), s);
-    cudaMemsetAsync(m->levels.ctrl, 0, 2 * sizeof(unsigned long long), s);
+    cudaMemsetAsync(m->levels.ctrl, 0, 3 * sizeof(unsigned long long), s);
     m->levels.epoch = 0;
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) { cleanup(); return err; }
     cleanup();
@@ -1619,15 +1621,29 @@ cudaError_t build_level_groups(sn_mesh* m, int G) {
     return cudaSuccess;
 }
 
+__global__ void bump_device_epoch_kernel(unsigned long long* ctrl) { ctrl[2] += 1; }
+
 template <int DIM, int P, int MODE, bool ADJ = false>
 static cudaError_t launch_dataflow(sn_mesh* m, const SweepArgs& a, cudaStream_t s, const double* mu = nullptr) {
     LevelSets& L = m->levels;
-    if (++L.epoch == 0x7fffffff) {  // epochs wrap: start over from a cleared table
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t cerr = cudaStreamIsCapturing(s, &cs);
+    if (cerr != cudaSuccess) return cerr;
+    const bool recorded = cs == cudaStreamCaptureStatusActive;
+    if (!recorded && ++L.epoch == 0x7fffffff) {  // epochs wrap: start over from a cleared table
         cudaMemsetAsync(L.done, 0, (size_t)m->nd * m->ne * sizeof(int), s);
         L.epoch = 1;
     }
     cudaMemsetAsync(L.ctrl, 0, sizeof(unsigned long long), s);
     DataflowArgs f;
+    f.epoch_dev = nullptr;
+    if (recorded) {
+        // inside a recorded iteration the epoch lives on the device (ctrl[2], set from the host's
+        // before the graph runs and read back after it): a one-thread kernel advances it per sweep
+        SN_COUNT_LAUNCH();
+        bump_device_epoch_kernel<<<1, 1, 0, s>>>(L.ctrl);
+        f.epoch_dev = reinterpret_cast<const int*>(L.ctrl + 2);
+    }
     f.items = ADJ ? L.padded_rev : L.padded;
     f.n_items = L.n_padded;
     f.done = L.done;
@@ -2484,6 +2500,32 @@ cudaError_t take_sweep_error(sn_mesh* m, cudaStream_t s, bool* timed_out) {
         err = cudaMemsetAsync(m->levels.ctrl + 1, 0, sizeof(w), s);
         if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     }
+    return err;
+}
+
+// The device copy of the dataflow epoch (ctrl[2]) follows the host's around a recorded iteration:
+// set before the graph runs (after clearing the completion words if the recorded sweeps could run
+// past the wrap point), read back after it.
+cudaError_t device_epoch_in(sn_mesh* m, long long max_sweeps, cudaStream_t s) {
+    LevelSets& L = m->levels;
+    if (!L.ctrl) return cudaSuccess;
+    cudaError_t err;
+    if ((long long)L.epoch + max_sweeps >= 0x7fffffffll) {
+        if ((err = cudaMemsetAsync(L.done, 0, (size_t)m->nd * m->ne * sizeof(int), s)) != cudaSuccess) return err;
+        L.epoch = 0;
+    }
+    const unsigned long long e = (unsigned long long)L.epoch;
+    if ((err = cudaMemcpyAsync(L.ctrl + 2, &e, sizeof(e), cudaMemcpyHostToDevice, s)) != cudaSuccess) return err;
+    return cudaStreamSynchronize(s);  // e lives on this stack frame
+}
+
+cudaError_t device_epoch_out(sn_mesh* m, cudaStream_t s) {
+    LevelSets& L = m->levels;
+    if (!L.ctrl) return cudaSuccess;
+    unsigned long long e = 0;
+    cudaError_t err = cudaMemcpyAsync(&e, L.ctrl + 2, sizeof(e), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err == cudaSuccess) L.epoch = (int)e;
     return err;
 }
 

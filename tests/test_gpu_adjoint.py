@@ -158,14 +158,13 @@ def test_resolvable_gradients_match_finite_differences_to_1e6(lib):
     """All three gradients of 32 seeded elements within 1e-6 relative of central differences with
     relative step 1e-6, with no noise floor.
 
-    A central difference resolves dJ/dp to 1e-6 only where the rounding noise of J, about 1e-13 |J|
-    here (the fixed point of Eq. schur is conditioned by 1/(1 - c) with c up to 0.9999), divided by
-    the step 1e-6 p is below 1e-6 |dJ/dp|, i.e. where |p dJ/dp| >= 0.1 |J|.  The elements are drawn
-    in seeded random order from the non-void elements near the detector and kept when all three
-    relative sensitivities (|sigma_t dJ/dsigma_t|, |sigma_s dJ/dsigma_s| and |q dJ/dq| / |J|, with q
-    read as 1 where it is 0) reach 0.1; the first 32 are checked.  The finite differences use fixed
-    iteration counts (fGMRES K, 40 PCG iterations per DSA solve), so J_K is a smooth function of
-    the data; a q of 0 is differenced one-sided (J is linear in q).
+    A central difference resolves dJ/dp to 1e-6 only where the rounding noise of J divided by the
+    step 1e-6 p stays below 1e-6 |dJ/dp|.  J is evaluated by source iteration run to its float64
+    fixed point (a fixed number of iterations past a 1e-14 residual, each DSA solve to 1e-14), whose
+    rounding noise is a few 1e-15 |J|; so the elements are drawn in seeded random order from the
+    non-void elements and kept when all three relative sensitivities (|sigma_t dJ/dsigma_t|,
+    |sigma_s dJ/dsigma_s| and |q dJ/dq| over |J|, q read as 1 where it is 0) reach 0.03; the first
+    32 are checked.  A q of 0 is differenced one-sided (J is linear in q).
     """
     sn, ag = lib
     prob = inputs.config5()
@@ -183,25 +182,22 @@ def test_resolvable_gradients_match_finite_differences_to_1e6(lib):
     base = [prob.sigma_t.copy(), prob.sigma_s.copy(), prob.q.copy()]
     scale = [np.abs(base[0]), np.abs(base[1]), np.where(base[2] != 0, np.abs(base[2]), 1.0)]
     rel = np.min([np.abs(scale[i] * grads[i]) / abs(J0) for i in range(3)], axis=0)
-    n = prob.nx
-    jj, ii = np.divmod(np.arange(prob.n_elem), n)
-    near = (ii >= n - 24) & (jj >= 7 * n // 16 - 16) & (jj < 7 * n // 16 + n // 8 + 16) & (prob.sigma_t > 0)
     order = np.argsort(inputs.uniform(inputs.MASTER_SEED + 4, 33, prob.n_elem), kind="stable")
-    chosen = [int(e) for e in order if near[e] and rel[e] >= 0.1][:32]
+    chosen = [int(e) for e in order if prob.sigma_t[e] > 0 and rel[e] >= 0.03][:32]
     assert len(chosen) == 32, len(chosen)
     mesh.set_materials(prob.sigma_t, prob.sigma_s, prob.q)
-    probe = mesh.source_iterate(dsa="thick", mask=mask, outer="fgmres", tol=1e-14, inner_tol=1e-13, max_iters=400)
-    K = probe["iters"] + 5
+    si = dict(dsa="thick", mask=mask, outer="si", inner_tol=1e-14, inner_max_iters=400)
+    probe = mesh.source_iterate(tol=1e-14, max_iters=2000, **si)
+    assert probe["converged"]
+    K = probe["iters"] + 10
 
     def J_of(st_h, ss_h, q_h):
         mesh.set_materials(st_h, ss_h, q_h)
-        r = mesh.source_iterate(dsa="thick", mask=mask, outer="fgmres", tol=0.0, max_iters=K, inner_tol=1e-300,
-                                inner_max_iters=40)
+        r = mesh.source_iterate(tol=0.0, max_iters=K, **si)
         return float((g * r["phi"]).sum())
 
     JK = J_of(*base)
-    assert abs(JK - J0) < 1e-8 * abs(J0)
-    worst = 0.0
+    assert abs(JK - J0) < 1e-12 * abs(J0)
     for e in chosen:
         for idx in range(3):
             p = base[idx][e]
@@ -215,6 +211,5 @@ def test_resolvable_gradients_match_finite_differences_to_1e6(lib):
             else:
                 fd = (J_of(*plus) - JK) / h
             err = abs(grads[idx][e] - fd) / abs(fd)
-            worst = max(worst, err)
             assert err <= 1e-6, (e, idx, grads[idx][e], fd, err)
     mesh.set_materials(prob.sigma_t, prob.sigma_s, prob.q)

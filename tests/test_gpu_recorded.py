@@ -39,11 +39,13 @@ RUNS = [dict(outer="si", dsa="thick", tol=1e-8, inner_tol=1e-4, max_iters=300),
         dict(outer="fgmres", dsa="thick", tol=1e-12, inner_tol=1e-4, max_iters=7)]   # stops at max_iters
 
 
+@pytest.mark.parametrize("schedule", [("levels", 32, 2), ("static", 32, 0), ("dataflow", 128, 0)])
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("k", range(len(RUNS)))
-def test_recorded_iteration_equals_the_host_loop(sn, case, k):
+def test_recorded_iteration_equals_the_host_loop(sn, case, k, schedule):
     prob = CASES[case]()
     m = sn.Mesh.from_problem(prob)
+    m.set_schedule(*schedule)
     kw = dict(RUNS[k], thick_rule=prob.thick_rule)
     hist = 400
     a = m.source_iterate(history=hist, **kw)                       # recorded (level schedule)

@@ -603,9 +603,14 @@ def profile_sweeps(args):
     mesh = sn.Mesh.from_problem(prob)
     choice = mesh.autotune(args.precision)
     phi = torch.as_tensor(inputs.random_phi(prob, 3), device="cuda")
-    for _ in range(args.warmup + args.steps):
+    for _ in range(args.warmup):
         mesh.sweep(phi, precision=args.precision)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("sweeps")  # the captured sweeps
+    for _ in range(args.steps):
+        mesh.sweep(phi, precision=args.precision)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     print(json.dumps({"profile_sweeps": args.profile_sweeps, "schedule": list(choice), "elements": mesh.n_elem,
                       "dirs": mesh.n_dirs, "levels": mesh.n_levels}), flush=True)
 

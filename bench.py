@@ -404,7 +404,7 @@ def run_ours(args, rank, ws):
     units_per_sweep = mesh.n_elem * n * mesh.n_dirs
     stream = torch.cuda.current_stream()
     opts = dict(dsa="thick", thick_rule="sigma_s", tol=1e-8, inner_tol=1e-4, max_iters=500, precision="fp64",
-                outer="fgmres", restart=30)
+                outer="fgmres", restart=30, host_loop=args.host_loop)
     phi = torch.zeros(mesh.shape, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
 
@@ -451,7 +451,7 @@ def run_ours(args, rank, ws):
     launches = sn.launch_count() - n0
     # the timed solves run as one recorded graph each; the split of device time into transport
     # updates and DSA solves comes from one more solve run as a host loop (CUDA events per segment)
-    rh = mesh.source_iterate(phi=phi, host_loop=True, **shard, **opts)
+    rh = mesh.source_iterate(phi=phi, **shard, **dict(opts, host_loop=True))
     breakdown = {"sweep_ms": rh["ms_sweep"], "dsa_ms": rh["ms_dsa"], "host_loop_total_ms": rh["ms"],
                  "recorded_total_ms": step_ms_last(ev), "sweeps": rh["sweeps"],
                  "what": "one solve run as a host loop (one synchronisation per iteration): device time of the "
@@ -628,6 +628,9 @@ def main():
     ap.add_argument("--profile-sweeps", default=None, metavar="c2|c3[:n]",
                     help="only run --warmup + --steps sweeps of that mesh (for ncu captures)")
     ap.add_argument("--precision", default="fp64", help="precision of --profile-sweeps")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="run the timed solves as host loops instead of recorded graphs (ncu cannot profile the "
+                         "kernel nodes of graphs with conditional nodes one by one; for launch lists)")
     args = ap.parse_args()
     if args.profile_sweeps:
         profile_sweeps(args)

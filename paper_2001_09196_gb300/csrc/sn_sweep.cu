@@ -908,6 +908,134 @@ __device__ __forceinline__ bool wait_neighbours(const SweepArgs& a, const int* d
     return true;
 }
 
+// ---- data-polled dataflow (forward sweeps): before the launch every angular flux of the sweep
+// is set to the all-ones bit pattern (a NaN no element solve produces), and a consumer polls the
+// upwind values it needs until none is that pattern.  Each value is one 8- (4-) byte word written
+// once by a relaxed store and read by relaxed loads, so a value that is seen is the final one; no
+// completion words, no fences, and the flag round trip of the completion-word scheme disappears.
+__device__ __forceinline__ double ld_relaxed(const double* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return __longlong_as_double((long long)v);
+}
+__device__ __forceinline__ float ld_relaxed(const float* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return __int_as_float((int)v);
+}
+__device__ __forceinline__ void st_relaxed(double* p, double x) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"((unsigned long long)__double_as_longlong(x)) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(float* p, float x) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"((unsigned)__float_as_int(x)) : "memory");
+}
+__device__ __forceinline__ bool is_unset(double v) { return __double_as_longlong(v) == -1ll; }
+__device__ __forceinline__ bool is_unset(float v) { return __float_as_int(v) == -1; }
+__device__ __forceinline__ double unset_value(double) { return __longlong_as_double(-1ll); }
+__device__ __forceinline__ float unset_value(float) { return __int_as_float(-1); }
+
+// node_faces with the upwind values polled (bounded); *ok = false when the deadline passed.
+template <int DIM, int P, typename R>
+__device__ __forceinline__ R node_faces_polled(const SweepArgs& a, const double* F, int d, int e, int r, R rhs,
+                                               unsigned long long deadline, bool* ok) {
+    constexpr int Q = P + 1, N = Shape<DIM, P>::N;
+    constexpr int FAM = DIM == 3 ? FAM_3D_P1 : P - 1;
+    using K = GLT<R>;
+    const int ri[3] = {r % Q, (r / Q) % Q, r / (Q * Q)};
+    const R* psi = static_cast<const R*>(a.psi);
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f) {
+        if (!(F[f] < 0.0)) continue;
+        const int ax = f >> 1;
+        const bool hi = f & 1;
+        const int u = neighbor<DIM, P>(a, e, f);
+        const int tt = DIM == 2 ? ri[1 - ax] : (ax == 0 ? ri[1] + Q * ri[2] : (ax == 1 ? ri[0] + Q * ri[2] : ri[0] + Q * ri[1]));
+        R tr;
+        if (u >= 0) {
+            const R* pu = psi + ((size_t)d * a.ne + u) * N;
+            R v[Q];
+            int polls = 0;
+            while (true) {
+                bool all = true;
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    v[k] = ld_relaxed(pu + node_of<DIM, P>(ax, k, tt));
+                    all = all && !is_unset(v[k]);
+                }
+                if (all) break;
+                if (++polls > 64) {
+                    if (globaltimer() > deadline) {
+                        *ok = false;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            tr = R(0);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) tr += (hi ? K::lm(P, k) : K::lp(P, k)) * v[k];
+        } else {
+            tr = (R)a.psi_inc;
+        }
+        const R c = -(R)F[f] * fcoef<R>(FAM, r, f);
+        rhs += c * tr;
+    }
+    return rhs;
+}
+
+// Data-polled dataflow item loop of the cached forward sweep (schedules 1 and 4 with
+// DataflowArgs::poll_data): claim or take slices as node_dataflow_kernel does, stage, then the
+// face terms poll their upwind values; the store of x is the publication.
+template <int DIM, int P, int MODE>
+__global__ void __launch_bounds__(128) node_datapoll_kernel(SweepArgs a, DataflowArgs f) {
+    using R = typename std::conditional<MODE == 1, float, double>::type;
+    constexpr int N = Shape<DIM, P>::N, IPW = 32 / N, SLICES = (32 + IPW - 1) / IPW;
+    const int lane = threadIdx.x & 31;
+    const int slot = lane / N, r = lane - slot * N;
+    const int src0 = slot < IPW ? slot * N : 0;
+    const long long n_slices = (f.n_items >> 5) * SLICES;
+    const unsigned long long deadline = globaltimer() + f.timeout_ns;
+    const bool withhold = f.publish == -1;  // test hook: store the unset pattern, every wait times out
+    unsigned long long mine = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    while (true) {
+        unsigned long long c = 0;
+        int failed = 0;
+        if (lane == 0) {
+            if (f.static_warps > 0) {
+                c = mine;
+                mine += (unsigned long long)f.static_warps;
+            } else {
+                c = atomicAdd(f.next, 1ull);
+            }
+            failed = *(volatile int*)f.error;
+        }
+        c = __shfl_sync(0xffffffffu, c, 0);
+        failed = __shfl_sync(0xffffffffu, failed, 0);
+        if ((long long)c >= n_slices || failed) break;
+        const long long chunk = (long long)c / SLICES;
+        const int k = (int)((long long)c - chunk * SLICES) * IPW + slot;
+        int2 it = make_int2(-1, -1);
+        if (slot < IPW && k < 32) it = f.items[(chunk << 5) + k];
+        const bool valid = it.x >= 0;
+        const int d = valid ? it.x : 0, e = valid ? it.y : 0;
+        NodeStage<DIM, P, R> st;
+        if (valid) node_stage<DIM, P, MODE, false>(a, nullptr, d, e, r, st);
+        bool ok = true;
+        const R rhs = valid ? node_faces_polled<DIM, P, R>(a, st.F, d, e, r, st.rhs, deadline, &ok) : R(0);
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) atomicExch(f.error, 1);
+            break;
+        }
+        R x = R(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const R rj = __shfl_sync(0xffffffffu, rhs, src0 + j);
+            if (valid) x += st.inv[j] * rj;
+        }
+        if (valid) st_relaxed(static_cast<R*>(a.psi) + ((size_t)d * a.ne + e) * N + r, withhold ? unset_value(x) : x);
+    }
+}
+
 // As wait_neighbours with the face fluxes already loaded, every pending word polled in each round
 // (their loads in flight together) rather than one face after another.
 template <int DIM, int P, bool ADJ>
@@ -1661,7 +1789,10 @@ static cudaError_t launch_dataflow(sn_mesh* m, const SweepArgs& a, cudaStream_t 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool cached = MODE == 1 ? a.ainv32 != nullptr : (MODE == 0 && a.ainv != nullptr);
-    if (cached) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, node_dataflow_kernel<DIM, P, MODE == 1 ? 1 : 0, ADJ>, m->block, 0);
+    // cached forward sweeps poll the upwind angular fluxes themselves (node_datapoll_kernel)
+    const bool datapoll = cached && !ADJ;
+    if (datapoll) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, node_datapoll_kernel<DIM, P, MODE == 1 ? 1 : 0>, m->block, 0);
+    else if (cached) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, node_dataflow_kernel<DIM, P, MODE == 1 ? 1 : 0, ADJ>, m->block, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_dataflow_kernel<DIM, P, MODE, ADJ>, m->block, 0);
     if (m->max_blocks_per_sm > 0 && m->max_blocks_per_sm < per_sm) per_sm = m->max_blocks_per_sm;
     per_sm = per_sm < 1 ? 1 : per_sm;
@@ -1672,6 +1803,15 @@ static cudaError_t launch_dataflow(sn_mesh* m, const SweepArgs& a, cudaStream_t 
     if (blocks < 1) blocks = 1;
     // static assignment needs every warp resident: the grid never exceeds one wave
     f.static_warps = m->schedule == SCHED_STATIC ? blocks * (m->block / 32) : 0;
+    if (datapoll) {
+        // every angular flux of the sweep starts as the unset pattern (all bits one)
+        const size_t bytes = (size_t)m->nd * m->ne * m->n * (MODE == 1 ? sizeof(float) : sizeof(double));
+        cudaError_t merr = cudaMemsetAsync(a.psi, 0xFF, bytes, s);
+        if (merr != cudaSuccess) return merr;
+        SN_COUNT_LAUNCH();
+        node_datapoll_kernel<DIM, P, MODE == 1 ? 1 : 0><<<(unsigned)blocks, m->block, 0, s>>>(a, f);
+        return cudaGetLastError();
+    }
     SN_COUNT_LAUNCH();
     if (cached) node_dataflow_kernel<DIM, P, MODE == 1 ? 1 : 0, ADJ><<<(unsigned)blocks, m->block, 0, s>>>(a, f, mu);
     else sweep_dataflow_kernel<DIM, P, MODE, ADJ><<<(unsigned)blocks, m->block, 0, s>>>(a, f, mu);

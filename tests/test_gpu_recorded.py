@@ -39,7 +39,8 @@ RUNS = [dict(outer="si", dsa="thick", tol=1e-8, inner_tol=1e-4, max_iters=300),
         dict(outer="fgmres", dsa="thick", tol=1e-12, inner_tol=1e-4, max_iters=7)]   # stops at max_iters
 
 
-@pytest.mark.parametrize("schedule", [("levels", 32, 2), ("static", 32, 0), ("dataflow", 128, 0)])
+@pytest.mark.parametrize("schedule", [("levels", 32, 2), ("static", 32, 0), ("dataflow", 128, 0)],
+                         ids=["levels", "static", "dataflow"])
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("k", range(len(RUNS)))
 def test_recorded_iteration_equals_the_host_loop(sn, case, k, schedule):

@@ -38,7 +38,8 @@ def test_schedules_agree_bitwise(sn, name, precision):
     for sched, block, param in (("levels", 32, 4), ("levels", 64, 3), ("levels", 32, 1000), ("dataflow", 128, 0),
                                 ("dataflow", 64, 0), ("dataflow", 32, 1), ("dataflow", 96, 2), ("tiles", 128, 4),
                                 ("tiles", 256, 8), ("tiles", 64, 3), ("tiles", 32, 16), ("barrier", 256, 1),
-                                ("barrier", 512, 1), ("barrier", 128, 3)):
+                                ("barrier", 512, 1), ("barrier", 128, 3), ("static", 128, 0), ("static", 32, 0),
+                                ("static", 64, 2)):
         if sched == "levels" and param > m.n_dirs:
             param = m.n_dirs  # one chain per direction
         m.set_schedule(sched, block, param)
@@ -46,7 +47,7 @@ def test_schedules_agree_bitwise(sn, name, precision):
         assert torch.equal(got, ref), (sched, block, param)
 
 
-@pytest.mark.parametrize("schedule", [("dataflow", 128, 0), ("tiles", 128, 8), ("barrier", 256, 1)])
+@pytest.mark.parametrize("schedule", [("dataflow", 128, 0), ("static", 32, 0), ("tiles", 128, 8), ("barrier", 256, 1)])
 def test_dependency_wait_timeout_is_reported_and_recoverable(sn, schedule):
     prob = CASES["c2_32"]()
     m = sn.Mesh.from_problem(prob)
@@ -69,7 +70,8 @@ def test_adjoint_schedules_agree_bitwise(sn, name):
     mu = torch.as_tensor(inputs.random_phi(prob, 8) - 0.7, device="cuda")
     m.set_schedule("levels", 128)
     ref = m.adjoint_sweep(mu)
-    for sched, block, param in (("levels", 32, 4), ("dataflow", 128, 0), ("dataflow", 32, 1), ("tiles", 128, 8)):
+    for sched, block, param in (("levels", 32, 4), ("dataflow", 128, 0), ("dataflow", 32, 1), ("tiles", 128, 8),
+                                ("static", 32, 0)):
         m.set_schedule(sched, block, param)
         assert torch.equal(m.adjoint_sweep(mu), ref), (sched, block, param)
 
@@ -78,7 +80,8 @@ CANDIDATES = {("levels", 32, 0), ("levels", 64, 0), ("levels", 128, 0), ("levels
               ("levels", 64, 8), ("levels", 32, 16), ("dataflow", 128, 0), ("dataflow", 128, 1),
               ("dataflow", 64, 2), ("dataflow", 32, 4), ("tiles", 128, 8), ("tiles", 128, 16), ("tiles", 256, 16),
               ("tiles", 256, 32), ("levels", 32, 2), ("tiles", 256, 16), ("barrier", 256, 1), ("barrier", 512, 1),
-              ("barrier", 256, 2), ("barrier", 128, 4)}
+              ("barrier", 256, 2), ("barrier", 128, 4), ("static", 128, 0), ("static", 64, 0), ("static", 128, 4),
+              ("static", 128, 2), ("static", 32, 0)}
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

@@ -85,9 +85,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per element-direction of the dominant sweep kernel, from an ncu
 # metrics-only capture (dram__bytes_read.sum + dram__bytes_write.sum) of the bench's own launch, per
 # (schedule, workload).  A schedule or kernel changed since its capture has no entry (traffic null).
-SWEEP_DRAM_BYTES_PER_ITEM = {}
+SWEEP_DRAM_BYTES_PER_ITEM = {("static", "c2"): (2129648128 + 154235392) / (65536 * 40)}  # node_datapoll_kernel
 
-SCHEDULE_KERNEL = {"levels": "node_level_kernel", "dataflow": "node_dataflow_kernel", "static": "node_dataflow_kernel",
+SCHEDULE_KERNEL = {"levels": "node_level_kernel", "dataflow": "node_datapoll_kernel", "static": "node_datapoll_kernel",
                    "tiles": "tile_sweep_kernel", "barrier": "barrier_sweep_kernel"}
 
 
@@ -494,6 +494,7 @@ def run_ours(args, rank, ws):
         forms = {}
         phi64 = phi.clone()  # the FP64 fGMRES solution of the last timed step
         for prec, outer, dsa, op in (("fp32", "fgmres", "thick", "sip"), ("fp32_refine", "fgmres", "thick", "sip"),
+                                     ("fp32_mixed", "fgmres", "thick", "sip"), ("fp32_mixed", "fgmres", "thick", "nip"),
                                      ("fp64", "si", "thick", "sip"), ("fp64", "fgmres", "triangular", "sip"),
                                      ("fp64", "fgmres", "thick", "nip"), ("fp64", "fgmres", "thick", "mnip")):
             name = f"{prec}_{outer}" + {"triangular": "_triangular_dsa", "thick": ""}[dsa] + ("" if op == "sip" else f"_{op}_dsa")

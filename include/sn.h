@@ -101,6 +101,10 @@ sn_status sn_mesh_get_info(const sn_mesh* mesh, sn_mesh_info* info);
  *   schedule 4: as schedule 1, but with every warp of the grid resident and the work list dealt
  *   out statically (warp w takes slices w, w + W, w + 2W, ... of the level-ordered list, W warps in
  *   all) instead of claimed through a shared counter.
+ *   In schedules 1 and 4 with the operator cache, the angular fluxes of the sweep are first set to
+ *   the all-ones bit pattern and each element solve polls the upwind (adjoint: downwind) values it
+ *   needs until none is that pattern (relaxed loads and stores; the stored values are their own
+ *   completion signal); uncached solves wait on per-element completion words.
  *   Uncached solves (SN_FP32_REFINE, cache off) and the adjoint use schedule 0 instead of 2 or 3.
  * block: threads per block, a multiple of 32 in [32, 128] (schedules 0, 1, 4), [32, 256] (2),
  * [32, 512] (3).
@@ -391,8 +395,12 @@ long long sn_launch_count(void);
  * one work list of every instance's (direction, element) items ordered by (upwind level, element
  * family, instance); a level never mixes element templates inside a warp.
  * sn_batch_sweep: one transport update of every instance, phi_out[i] = sweep_i(phi_in[i]) (arrays of
- * count device pointers; phi_in may be NULL), as one persistent launch (schedule 1) or one set of
- * level launches (schedule 0).  Synchronises the stream.
+ * count device pointers; phi_in may be NULL), as one persistent launch (schedule 1: warps claim
+ * 32-item chunks; schedule 4: chunks dealt out statically to resident warps) or one set of level
+ * launches (schedule 0).  In the persistent launches with cached operators every instance's angular
+ * fluxes are reset to an unset bit pattern before the sweep and consumers poll the upwind values
+ * (see sn_mesh_set_schedule); an instance that has converged in a batched iteration keeps its
+ * iterate, but its stored angular fluxes are then not those of a sweep.  Synchronises the stream.
  * sn_batch_source_iterate: Eq. (DSA_fp) with Algorithm 2 for every instance at once: the batched sweep,
  * per-instance flux reductions and residual norms, and one conjugate-gradient solve of the union of
  * the instances' thick-DSA systems (block diagonal, one multigrid V-cycle over the union of their

@@ -1402,7 +1402,7 @@ sn_status sn_batch_destroy(sn_batch* b) {
 
 sn_status sn_batch_set_schedule(sn_batch* b, int schedule, int block, int max_blocks_per_sm) {
     if (!b) return fail(SN_ERR_ARG, "null batch");
-    if (schedule != sn::SCHED_LEVELS && schedule != sn::SCHED_DATAFLOW) return fail(SN_ERR_ARG, "bad schedule");
+    if (schedule != sn::SCHED_LEVELS && !sn::dataflow_like(schedule)) return fail(SN_ERR_ARG, "bad schedule");
     if (block < 32 || block > 128 || block % 32) return fail(SN_ERR_ARG, "block must be 32, 64, 96 or 128");
     if (max_blocks_per_sm < 0) return fail(SN_ERR_ARG, "max_blocks_per_sm must be >= 0");
     if (b->schedule != schedule || b->block != block || b->max_blocks_per_sm != max_blocks_per_sm) {
@@ -1452,14 +1452,14 @@ sn_status sn_batch_sweep(sn_batch* b, const double* const* phi_in, double* const
     }
     std::vector<int> ones(b->count, 1);
     CK(cudaMemcpyAsync(b->d_active, ones.data(), b->count * sizeof(int), cudaMemcpyHostToDevice, s), "copy");
-    if (b->schedule == sn::SCHED_DATAFLOW) {
+    if (sn::dataflow_like(b->schedule)) {
         CK(sn::batch_launch_dataflow(b, precision, s), "batched sweep");
     } else {
         CK(sn::batch_enqueue_sweep(b, precision, s), "batched sweep");
     }
     for (int i = 0; i < b->count; ++i)
         CK(sn::launch_phi_reduce(b->meshes[i], precision, nullptr, phi_out[i], nullptr, s), "phi reduce");
-    if (b->schedule == sn::SCHED_DATAFLOW) return batch_timeout_check(b, s);
+    if (sn::dataflow_like(b->schedule)) return batch_timeout_check(b, s);
     CK(cudaStreamSynchronize(s), "sync");
     return SN_OK;
 }
@@ -1569,7 +1569,7 @@ sn_status sn_batch_source_iterate(sn_batch* b, const sn_iter_opts* o, double* co
             for (int a : active) any |= a != 0;
         }
     }
-    if (b->schedule == sn::SCHED_DATAFLOW && (st = batch_timeout_check(b, s)) != SN_OK) return st;
+    if (sn::dataflow_like(b->schedule) && (st = batch_timeout_check(b, s)) != SN_OK) return st;
     for (int i = 0; i < b->count; ++i) {
         const size_t M = (size_t)b->meshes[i]->ne * b->meshes[i]->n;
         CK(cudaMemcpyAsync(phis[i], b->d_phi + b->dof_off[i], M * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
@@ -1616,7 +1616,8 @@ struct TuneChoice {
 };
 std::map<TuneKey, TuneChoice> g_tune_cache;
 std::mutex g_tune_mutex;
-const TuneChoice kCandidates[] = {{0, 32, 0, 0}, {0, 64, 0, 0}, {0, 128, 0, 0}, {1, 128, 0, 0},
+const TuneChoice kCandidates[] = {{0, 32, 0, 0}, {0, 64, 0, 0}, {0, 128, 0, 0}, {4, 32, 0, 0}, {4, 64, 0, 0},
+                                  {4, 128, 0, 0}, {1, 128, 0, 0},
                                   {1, 128, 1, 0}, {1, 64, 2, 0}, {1, 32, 4, 0}};
 // meshes also try the tiled schedule (cached solves) with a few tile edges and CTA sizes
 const TuneChoice kMeshCandidates[] = {{0, 32, 0, 0}, {0, 64, 0, 0}, {0, 128, 0, 0}, {0, 32, 2, 0},
@@ -1708,11 +1709,11 @@ sn_status sn_batch_autotune(sn_batch* b, int precision, void* stream, int* sched
         cudaError_t err = cudaSuccess;
         const float ms = time_ms([&] {
             if (err != cudaSuccess) return;
-            err = b->schedule == sn::SCHED_DATAFLOW ? sn::batch_launch_dataflow(b, precision, s)
+            err = sn::dataflow_like(b->schedule) ? sn::batch_launch_dataflow(b, precision, s)
                                                     : sn::batch_enqueue_sweep(b, precision, s);
         }, s, 2);
         CK(err, "autotune batched sweep");
-        if (b->schedule == sn::SCHED_DATAFLOW && (st = batch_timeout_check(b, s)) != SN_OK) return st;
+        if (sn::dataflow_like(b->schedule) && (st = batch_timeout_check(b, s)) != SN_OK) return st;
         if (ms < best.ms) best = {c.schedule, c.block, c.cap, ms};
     }
     if ((st = sn_batch_set_schedule(b, best.schedule, best.block, best.cap)) != SN_OK) return st;

@@ -659,7 +659,7 @@ struct BatchIterState {
 // One outer iteration of every active instance (Eq. DSA_fp with Algorithm 2), capturable.
 cudaError_t batch_enqueue_iteration(sn_batch* b, const sn_iter_opts* o, int* d_next, const int* d_dof_inst,
                                     cudaStream_t s) {
-    cudaError_t err = b->schedule == SCHED_DATAFLOW ? batch_launch_dataflow(b, o->precision, s)
+    cudaError_t err = dataflow_like(b->schedule) ? batch_launch_dataflow(b, o->precision, s)
                                                     : batch_enqueue_sweep(b, o->precision, s);
     if (err != cudaSuccess) return err;
     for (int i = 0; i < b->count; ++i) {

@@ -908,7 +908,7 @@ __device__ __forceinline__ bool wait_neighbours(const SweepArgs& a, const int* d
     return true;
 }
 
-// ---- data-polled dataflow (forward sweeps): before the launch every angular flux of the sweep
+// ---- data-polled dataflow (cached sweeps): before the launch every angular flux of the sweep
 // is set to the all-ones bit pattern (a NaN no element solve produces), and a consumer polls the
 // upwind values it needs until none is that pattern.  Each value is one 8- (4-) byte word written
 // once by a relaxed store and read by relaxed loads, so a value that is seen is the final one; no
@@ -934,8 +934,9 @@ __device__ __forceinline__ bool is_unset(float v) { return __float_as_int(v) == 
 __device__ __forceinline__ double unset_value(double) { return __longlong_as_double(-1ll); }
 __device__ __forceinline__ float unset_value(float) { return __int_as_float(-1); }
 
-// node_faces with the upwind values polled (bounded); *ok = false when the deadline passed.
-template <int DIM, int P, typename R>
+// node_faces with the upwind (adjoint: downwind) values polled (bounded); *ok = false when the
+// deadline passed.
+template <int DIM, int P, typename R, bool ADJ>
 __device__ __forceinline__ R node_faces_polled(const SweepArgs& a, const double* F, int d, int e, int r, R rhs,
                                                unsigned long long deadline, bool* ok) {
     constexpr int Q = P + 1, N = Shape<DIM, P>::N;
@@ -945,7 +946,7 @@ __device__ __forceinline__ R node_faces_polled(const SweepArgs& a, const double*
     const R* psi = static_cast<const R*>(a.psi);
 #pragma unroll
     for (int f = 0; f < 2 * DIM; ++f) {
-        if (!(F[f] < 0.0)) continue;
+        if (ADJ ? !(F[f] > 0.0) : !(F[f] < 0.0)) continue;
         const int ax = f >> 1;
         const bool hi = f & 1;
         const int u = neighbor<DIM, P>(a, e, f);
@@ -975,19 +976,21 @@ __device__ __forceinline__ R node_faces_polled(const SweepArgs& a, const double*
 #pragma unroll
             for (int k = 0; k < Q; ++k) tr += (hi ? K::lm(P, k) : K::lp(P, k)) * v[k];
         } else {
+            if (ADJ) continue;
             tr = (R)a.psi_inc;
         }
-        const R c = -(R)F[f] * fcoef<R>(FAM, r, f);
+        const R c = (ADJ ? (R)F[f] : -(R)F[f]) * fcoef<R>(FAM, r, f);
         rhs += c * tr;
     }
     return rhs;
 }
 
-// Data-polled dataflow item loop of the cached forward sweep (schedules 1 and 4 with
-// DataflowArgs::poll_data): claim or take slices as node_dataflow_kernel does, stage, then the
-// face terms poll their upwind values; the store of x is the publication.
-template <int DIM, int P, int MODE>
-__global__ void __launch_bounds__(128) node_datapoll_kernel(SweepArgs a, DataflowArgs f) {
+// Data-polled dataflow item loop of the cached sweeps (schedules 1 and 4; ADJ: the transposed
+// solve of the adjoint in reverse level order): claim or take slices as node_dataflow_kernel does,
+// stage, then the face terms poll their upwind (downwind) values; the store of x is the
+// publication.
+template <int DIM, int P, int MODE, bool ADJ>
+__global__ void __launch_bounds__(128) node_datapoll_kernel(SweepArgs a, DataflowArgs f, const double* mu) {
     using R = typename std::conditional<MODE == 1, float, double>::type;
     constexpr int N = Shape<DIM, P>::N, IPW = 32 / N, SLICES = (32 + IPW - 1) / IPW;
     const int lane = threadIdx.x & 31;
@@ -1019,9 +1022,9 @@ __global__ void __launch_bounds__(128) node_datapoll_kernel(SweepArgs a, Dataflo
         const bool valid = it.x >= 0;
         const int d = valid ? it.x : 0, e = valid ? it.y : 0;
         NodeStage<DIM, P, R> st;
-        if (valid) node_stage<DIM, P, MODE, false>(a, nullptr, d, e, r, st);
+        if (valid) node_stage<DIM, P, MODE, ADJ>(a, mu, d, e, r, st);
         bool ok = true;
-        const R rhs = valid ? node_faces_polled<DIM, P, R>(a, st.F, d, e, r, st.rhs, deadline, &ok) : R(0);
+        const R rhs = valid ? node_faces_polled<DIM, P, R, ADJ>(a, st.F, d, e, r, st.rhs, deadline, &ok) : R(0);
         if (!__all_sync(0xffffffffu, ok)) {
             if (lane == 0) atomicExch(f.error, 1);
             break;
@@ -1789,9 +1792,9 @@ static cudaError_t launch_dataflow(sn_mesh* m, const SweepArgs& a, cudaStream_t 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool cached = MODE == 1 ? a.ainv32 != nullptr : (MODE == 0 && a.ainv != nullptr);
-    // cached forward sweeps poll the upwind angular fluxes themselves (node_datapoll_kernel)
-    const bool datapoll = cached && !ADJ;
-    if (datapoll) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, node_datapoll_kernel<DIM, P, MODE == 1 ? 1 : 0>, m->block, 0);
+    // cached sweeps poll the upwind (adjoint: downwind) angular fluxes themselves (node_datapoll_kernel)
+    const bool datapoll = cached;
+    if (datapoll) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, node_datapoll_kernel<DIM, P, MODE == 1 ? 1 : 0, ADJ>, m->block, 0);
     else if (cached) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, node_dataflow_kernel<DIM, P, MODE == 1 ? 1 : 0, ADJ>, m->block, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_dataflow_kernel<DIM, P, MODE, ADJ>, m->block, 0);
     if (m->max_blocks_per_sm > 0 && m->max_blocks_per_sm < per_sm) per_sm = m->max_blocks_per_sm;
@@ -1809,7 +1812,7 @@ static cudaError_t launch_dataflow(sn_mesh* m, const SweepArgs& a, cudaStream_t 
         cudaError_t merr = cudaMemsetAsync(a.psi, 0xFF, bytes, s);
         if (merr != cudaSuccess) return merr;
         SN_COUNT_LAUNCH();
-        node_datapoll_kernel<DIM, P, MODE == 1 ? 1 : 0><<<(unsigned)blocks, m->block, 0, s>>>(a, f);
+        node_datapoll_kernel<DIM, P, MODE == 1 ? 1 : 0, ADJ><<<(unsigned)blocks, m->block, 0, s>>>(a, f, mu);
         return cudaGetLastError();
     }
     SN_COUNT_LAUNCH();
@@ -2354,6 +2357,80 @@ __global__ void __launch_bounds__(128) batch_node_dataflow_kernel(const SweepArg
     }
 }
 
+// Data-polled chunk of the batched cached sweep (as node_datapoll_kernel for one mesh): stage, poll
+// the upwind angular fluxes (reset to the unset pattern before the launch), solve, store.
+template <int DIM, int P, int MODE>
+__device__ __forceinline__ bool batch_node_chunk_polled(const SweepArgs* args, const BatchItem* items, long long chunk,
+                                                        const int* active, unsigned long long deadline) {
+    using R = typename std::conditional<MODE == 1, float, double>::type;
+    constexpr int N = Shape<DIM, P>::N, IPW = 32 / N, ROUNDS = (32 + IPW - 1) / IPW;
+    const int lane = threadIdx.x & 31;
+    const int slot = lane / N, r = lane - slot * N;
+    const int src0 = slot < IPW ? slot * N : 0;
+#pragma unroll 1
+    for (int round = 0; round < ROUNDS; ++round) {
+        const int k = round * IPW + slot;
+        BatchItem it{-1, 0, 0, 0};
+        if (slot < IPW && k < 32) it = items[(chunk << 5) + k];
+        const bool valid = it.inst >= 0 && active[it.inst];
+        const int inst = valid ? it.inst : 0, d = valid ? it.dir : 0, e = valid ? it.elem : 0;
+        const SweepArgs& a = args[inst];
+        NodeStage<DIM, P, R> st;
+        if (valid) node_stage<DIM, P, MODE, false>(a, nullptr, d, e, r, st);
+        bool ok = true;
+        const R rhs = valid ? node_faces_polled<DIM, P, R, false>(a, st.F, d, e, r, st.rhs, deadline, &ok) : R(0);
+        if (!__all_sync(0xffffffffu, ok)) return false;
+        R x = R(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const R rj = __shfl_sync(0xffffffffu, rhs, src0 + j);
+            if (valid) x += st.inv[j] * rj;
+        }
+        if (valid) st_relaxed(static_cast<R*>(a.psi) + ((size_t)d * a.ne + e) * N + r, x);
+    }
+    return true;
+}
+
+// Batched data-polled sweep: warps claim 32-item chunks (static_warps > 0: take chunks w, w + W, ...).
+template <int MODE>
+__global__ void __launch_bounds__(128) batch_node_datapoll_kernel(const SweepArgs* args, const BatchItem* items,
+                                                                 const int* chunk_fam, long long n_items,
+                                                                 unsigned long long* ctrl, const int* active,
+                                                                 unsigned long long timeout_ns, long long static_warps) {
+    const int lane = threadIdx.x & 31;
+    const long long n_chunks = n_items >> 5;
+    const unsigned long long deadline = globaltimer() + timeout_ns;
+    int* error = reinterpret_cast<int*>(ctrl + 1);
+    unsigned long long mine = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    while (true) {
+        unsigned long long c = 0;
+        int failed = 0;
+        if (lane == 0) {
+            if (static_warps > 0) {
+                c = mine;
+                mine += (unsigned long long)static_warps;
+            } else {
+                c = atomicAdd(ctrl, 1ull);
+            }
+            failed = *(volatile int*)error;
+        }
+        c = __shfl_sync(0xffffffffu, c, 0);
+        failed = __shfl_sync(0xffffffffu, failed, 0);
+        if ((long long)c >= n_chunks || failed) break;
+        bool ok;
+        switch (chunk_fam[c]) {  // uniform across the warp
+            case FAM_2D_P1: ok = batch_node_chunk_polled<2, 1, MODE>(args, items, c, active, deadline); break;
+            case FAM_2D_P2: ok = batch_node_chunk_polled<2, 2, MODE>(args, items, c, active, deadline); break;
+            case FAM_2D_P3: ok = batch_node_chunk_polled<2, 3, MODE>(args, items, c, active, deadline); break;
+            default: ok = batch_node_chunk_polled<3, 1, MODE>(args, items, c, active, deadline); break;
+        }
+        if (!ok) {
+            if (lane == 0) atomicExch(error, 1);
+            break;
+        }
+    }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(128) batch_dataflow_kernel(const SweepArgs* args, const BatchItem* items,
                                                             const int* chunk_fam, long long n_items, int* done,
@@ -2527,8 +2604,8 @@ cudaError_t batch_launch_dataflow(sn_batch* b, int precision, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool node = b->cached && precision != SN_FP32_REFINE;
-    if (node && precision == SN_FP64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_node_dataflow_kernel<0>, b->block, 0);
-    else if (node) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_node_dataflow_kernel<1>, b->block, 0);
+    if (node && precision == SN_FP64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_node_datapoll_kernel<0>, b->block, 0);
+    else if (node) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_node_datapoll_kernel<1>, b->block, 0);
     else if (precision == SN_FP64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_dataflow_kernel<0>, b->block, 0);
     else if (precision == SN_FP32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_dataflow_kernel<1>, b->block, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_dataflow_kernel<2>, b->block, 0);
@@ -2538,16 +2615,27 @@ cudaError_t batch_launch_dataflow(sn_batch* b, int precision, cudaStream_t s) {
     blocks = std::max<long long>(blocks, 1);
     const unsigned long long timeout = 4000000000ull;
     const int* epoch = reinterpret_cast<const int*>(b->d_ctrl + 2);
+    if (node) {
+        // cached (node-per-lane) solves poll the upwind angular fluxes: every instance's starts unset
+        for (int i = 0; i < b->count; ++i) {
+            sn_mesh* m = b->meshes[i];
+            const size_t bytes = (size_t)m->nd * m->ne * m->n * (precision == SN_FP32 ? sizeof(float) : sizeof(double));
+            if ((err = cudaMemsetAsync(b->h_args[i].psi, 0xFF, bytes, s)) != cudaSuccess) return err;
+        }
+        const long long warps = b->schedule == SCHED_STATIC ? blocks * (b->block / 32) : 0;
+        SN_COUNT_LAUNCH();
+        if (precision == SN_FP64)
+            batch_node_datapoll_kernel<0><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam,
+                                                                               b->n_items, b->d_ctrl, b->d_active,
+                                                                               timeout, warps);
+        else
+            batch_node_datapoll_kernel<1><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam,
+                                                                               b->n_items, b->d_ctrl, b->d_active,
+                                                                               timeout, warps);
+        return cudaGetLastError();
+    }
     SN_COUNT_LAUNCH();
-    if (node && precision == SN_FP64)
-        batch_node_dataflow_kernel<0><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam, b->n_items,
-                                                                           b->d_done, b->d_done_off, epoch, b->d_ctrl,
-                                                                           b->d_active, timeout);
-    else if (node)
-        batch_node_dataflow_kernel<1><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam, b->n_items,
-                                                                           b->d_done, b->d_done_off, epoch, b->d_ctrl,
-                                                                           b->d_active, timeout);
-    else if (precision == SN_FP64)
+    if (precision == SN_FP64)
         batch_dataflow_kernel<0><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam, b->n_items,
                                                                       b->d_done, b->d_done_off, epoch, b->d_ctrl,
                                                                       b->d_active, timeout);

@@ -496,7 +496,7 @@ class Batch:
             pass
 
     def set_schedule(self, schedule="levels", block=64, max_blocks_per_sm=0):
-        sched = {"levels": 0, "dataflow": 1}[schedule] if isinstance(schedule, str) else int(schedule)
+        sched = SCHEDULES.index(schedule) if isinstance(schedule, str) else int(schedule)
         _check(_lib.sn_batch_set_schedule(self._h, sched, int(block), int(max_blocks_per_sm)))
 
     def autotune(self, precision="fp64", stream=None):

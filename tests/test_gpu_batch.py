@@ -29,7 +29,8 @@ def small_instances():
     return out
 
 
-@pytest.mark.parametrize("schedule", [("levels", 64, 0), ("dataflow", 128, 0), ("dataflow", 32, 1)])
+@pytest.mark.parametrize("schedule", [("levels", 64, 0), ("dataflow", 128, 0), ("dataflow", 32, 1), ("static", 32, 0),
+                                      ("static", 128, 0)])
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_refine"])
 def test_batched_sweep_equals_single_sweeps(sn, schedule, precision):
     probs = small_instances()
@@ -56,7 +57,7 @@ def oracle_runs():
     return out
 
 
-@pytest.mark.parametrize("schedule", [("levels", 64, 0), ("dataflow", 128, 0)])
+@pytest.mark.parametrize("schedule", [("levels", 64, 0), ("dataflow", 128, 0), ("static", 32, 0)])
 def test_batched_iterates_match_the_oracle(sn, schedule, oracle_runs):
     """The batched source iteration (one union CG over every instance's thick-DSA system, one
     V-cycle over the union of their hierarchies, Algorithm 2 per instance) against the oracle's

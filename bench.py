@@ -272,9 +272,9 @@ def run_reference(args, rank, ws):
 
 
 def batched_form(torch, sn, inputs, stream, flush, args):
-    """64 ragged 2D instances (N 32..192, Q1..Q3, S4..S8) solved together by one batched
-    thick-DSA source iteration to 1e-8, against the same instances solved one after another
-    with the single-mesh fGMRES solver (the faster single-mesh outer iteration on them)."""
+    """64 ragged 2D instances (N 32..192, Q1..Q3, S4..S8) solved together to 1e-8 by the batched
+    thick-DSA source iteration and by the batched fGMRES(30), each against the same instances
+    solved one after another with the single-mesh solver of the same kind (like for like)."""
     probs = inputs.config4()
     meshes = [sn.Mesh.from_problem(p) for p in probs]
     batch = sn.Batch(meshes)
@@ -292,27 +292,32 @@ def batched_form(torch, sn, inputs, stream, flush, args):
         return a.elapsed_time(b), out
 
     sweep_ms = min(timed(lambda: batch.sweep(None))[0] for _ in range(3))
-    batch.source_iterate(**opts)  # records the iteration graph
-    solve_ms, r = timed(lambda: batch.source_iterate(**opts))
-    assert r["converged"], "the batched solve did not reach 1e-8"
-    seq, seq_si = [], []
+    solved = {}
+    for outer in ("si", "fgmres"):
+        batch.source_iterate(outer=outer, **opts)  # records the graphs
+        ms, r = timed(lambda: batch.source_iterate(outer=outer, **opts))
+        assert r["converged"], f"the batched {outer} solve did not reach 1e-8"
+        solved[outer] = (ms, r)
+    seq = {"si": [], "fgmres": []}
     for m in meshes:
-        t, rr = timed(lambda: m.source_iterate(outer="fgmres", **opts))
-        assert rr["converged"]
-        seq.append(t)
-        m.source_iterate(outer="si", **opts)  # records this instance's source-iteration graph
-        t, rr = timed(lambda: m.source_iterate(outer="si", **opts))
-        assert rr["converged"]
-        seq_si.append(t)
+        for outer in ("si", "fgmres"):
+            m.source_iterate(outer=outer, **opts)  # records this instance's iteration graph
+            t, rr = timed(lambda: m.source_iterate(outer=outer, **opts))
+            assert rr["converged"]
+            seq[outer].append(t)
+    best = min(solved, key=lambda k: solved[k][0])
+    per = {outer: {"batched_ms": solved[outer][0], "sequential_ms": sum(seq[outer]),
+                   "speedup_vs_sequential": sum(seq[outer]) / solved[outer][0],
+                   "iters_min_max": [min(solved[outer][1]["iters"]), max(solved[outer][1]["iters"])]}
+           for outer in ("si", "fgmres")}
     return {"workload": "64 ragged 2D instances, N 32..192, Q1..Q3, S4..S8, random fields, thick DSA "
                         "(sigma_t h > 1), tol 1e-8",
             "schedule": list(choice), "dof_dirs_per_sweep": units,
             "sweep_ms": sweep_ms, "sweep_dof_dirs_per_s": units / (sweep_ms / 1e3),
-            "ms_to_tol": solve_ms, "iters_min_max": [min(r["iters"]), max(r["iters"])],
-            "sequential_si_ms": sum(seq_si), "speedup_vs_sequential_si": sum(seq_si) / solve_ms,
-            "sequential_fgmres_ms": sum(seq), "speedup_vs_sequential": sum(seq) / solve_ms,
-            "what": "batched source iteration against the 64 instances solved one after another with the same "
-                    "outer solver (source iteration, like for like) and with single-mesh fGMRES"}
+            "ms_to_tol": solved[best][0], "outer": best, "si": per["si"], "fgmres": per["fgmres"],
+            "speedup_vs_best_sequential": min(sum(seq["si"]), sum(seq["fgmres"])) / solved[best][0],
+            "what": "each batched outer solver against the 64 instances solved one after another with the same "
+                    "outer solver (like for like); ms_to_tol is the faster batched solver"}
 
 
 def other_workloads(torch, sn, inputs, stream, flush, time_sweeps):

@@ -405,10 +405,18 @@ long long sn_launch_count(void);
  * per-instance flux reductions and residual norms, and one conjugate-gradient solve of the union of
  * the instances' thick-DSA systems (block diagonal, one multigrid V-cycle over the union of their
  * hierarchies), with per-instance convergence masks (a converged instance's items become no-ops).
- * One whole outer iteration is recorded once into a CUDA graph and replayed; the host checks the
- * masks every 4 iterations.  phis: count device pointers (warm start if opts->warm_start), receive
- * the results; stats: count entries or NULL.  opts->outer must be SN_OUTER_SI; no checkpoints; the
- * thick rule must not be SN_THICK_MASK.  SN_ERR_NOT_CONVERGED if any instance stops at max_iters.
+ * With opts->outer = SN_OUTER_SI one whole outer iteration is recorded once into a CUDA graph and
+ * replayed; the host checks the masks every 4 iterations.  With SN_OUTER_FGMRES every instance runs
+ * its own flexible GMRES(opts->restart) on Eq. (schur), right-preconditioned by the same union DSA
+ * step, in lock step: one recorded graph per Arnoldi step of all instances (the batched homogeneous
+ * sweep, the union DSA solve, Gram-Schmidt with inner products segmented by instance, the Givens
+ * updates on the device) and one per restart (true residuals with the fixed source); the host reads
+ * two flags after each.  An instance stops extending its basis at the tolerance or its iteration
+ * budget and leaves the batch when its true residual is below opts->tol; stats[i].iters counts its
+ * Arnoldi steps.  phis: count device pointers (warm start if opts->warm_start), receive the
+ * results; stats: count entries or NULL.  Precision SN_FP64, SN_FP32 or SN_FP32_REFINE (not
+ * SN_FP32_MIXED); no checkpoints, no direction sharding; the thick rule must not be SN_THICK_MASK.
+ * SN_ERR_NOT_CONVERGED if any instance stops at max_iters.
  */
 typedef struct sn_batch sn_batch;
 sn_status sn_batch_create(sn_mesh* const* meshes, int count, sn_batch** out);

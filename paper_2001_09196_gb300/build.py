@@ -19,7 +19,7 @@ OBJ_DIR = os.path.join(HERE, "lib", "obj")
 LIB = os.path.join(OUT_DIR, "libsn.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["sn_setup.cpp", "sn_dsa_setup.cpp", "sn_api.cpp", "sn_sweep.cu", "sn_dsa.cu", "sn_noalloc.cu", "sn_krylov.cu", "sn_batch.cu",
-           "sn_tiles.cpp", "sn_materials.cu", "sn_iter_graph.cu"]
+           "sn_tiles.cpp", "sn_materials.cu", "sn_iter_graph.cu", "sn_batch_krylov.cu"]
 
 
 def nvcc() -> str:

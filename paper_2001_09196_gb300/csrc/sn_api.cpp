@@ -1354,6 +1354,7 @@ static void free_batch(sn_batch* b) {
                     (void*)b->d_dof_inst})
         if (p) cudaFree(p);
     sn::union_dsa_free(b->dsa);
+    sn::batch_krylov_free(b->kry);
     delete b;
 }
 
@@ -1409,6 +1410,7 @@ sn_status sn_batch_set_schedule(sn_batch* b, int schedule, int block, int max_bl
         if (b->sweep_graph) cudaGraphExecDestroy(b->sweep_graph);
         if (b->iter_graph) cudaGraphExecDestroy(b->iter_graph);
         b->sweep_graph = b->iter_graph = nullptr;
+        ++b->graph_gen;
     }
     b->schedule = schedule;
     b->block = block;
@@ -1499,6 +1501,42 @@ static sn_status batch_ensure_dsa(sn_batch* b, const sn_iter_opts* o) {
         cudaGraphExecDestroy(b->iter_graph);
         b->iter_graph = nullptr;
     }
+    ++b->graph_gen;
+    return SN_OK;
+}
+
+// Flexible GMRES(restart) of every instance at once (sn_batch_krylov.cu) from the iterates in
+// b->d_phi; the solutions are copied to phis.
+static sn_status batch_fgmres_solve(sn_batch* b, const sn_iter_opts* o, double* const* phis, sn_iter_stats* stats,
+                                    cudaStream_t s, std::chrono::steady_clock::time_point t0) {
+    std::vector<int> iters, sweeps, conv;
+    std::vector<double> rel;
+    CK(sn::batch_fgmres(b, o, s, iters, rel, sweeps, conv), "batched fGMRES");
+    if (sn::dataflow_like(b->schedule)) {
+        sn_status st = batch_timeout_check(b, s);
+        if (st != SN_OK) return st;
+    }
+    for (int i = 0; i < b->count; ++i) {
+        const size_t M = (size_t)b->meshes[i]->ne * b->meshes[i]->n;
+        CK(cudaMemcpyAsync(phis[i], b->d_phi + b->dof_off[i], M * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    }
+    CK(cudaStreamSynchronize(s), "sync");
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    bool all = true;
+    for (int i = 0; i < b->count; ++i) {
+        all &= conv[i] != 0;
+        if (stats) {
+            stats[i].iters = iters[i];
+            stats[i].rel_residual = rel[i];
+            stats[i].inner_iters_total = 0;
+            stats[i].thick_fraction = 0.0;
+            stats[i].n_checkpoints = 0;
+            stats[i].n_sweeps = sweeps[i];
+            stats[i].ms_total = ms;
+            stats[i].ms_sweep = stats[i].ms_dsa = 0.0;
+        }
+    }
+    if (!all) return fail(SN_ERR_NOT_CONVERGED, "some batch instances did not converge in %d iterations", o->max_iters);
     return SN_OK;
 }
 
@@ -1507,7 +1545,7 @@ sn_status sn_batch_source_iterate(sn_batch* b, const sn_iter_opts* o, double* co
     if (!b || !phis) return fail(SN_ERR_ARG, "null argument");
     sn_status st = check_opts(o);
     if (st != SN_OK) return st;
-    if (o->outer != SN_OUTER_SI) return fail(SN_ERR_ARG, "batches iterate with source iteration (SN_OUTER_SI)");
+    if (o->precision == SN_FP32_MIXED) return fail(SN_ERR_ARG, "SN_FP32_MIXED is for single meshes");
     if (sharded(o)) return fail(SN_ERR_ARG, "batches shard by instance, not by direction");
     if (o->checkpoint_every > 0) return fail(SN_ERR_ARG, "checkpoints are not supported for batches");
     const auto t0 = std::chrono::steady_clock::now();
@@ -1521,6 +1559,7 @@ sn_status sn_batch_source_iterate(sn_batch* b, const sn_iter_opts* o, double* co
         else
             CK(cudaMemsetAsync(b->d_phi + b->dof_off[i], 0, M * sizeof(double), s), "memset");
     }
+    if (o->outer == SN_OUTER_FGMRES) return batch_fgmres_solve(b, o, phis, stats, s, t0);
     std::vector<int> ones(b->count, 1);
     CK(cudaMemcpyAsync(b->d_active, ones.data(), b->count * sizeof(int), cudaMemcpyHostToDevice, s), "copy");
     CK(cudaMemsetAsync(b->d_iters, 0, b->count * sizeof(int), s), "memset");

@@ -126,6 +126,7 @@ constexpr int kTileWaitMask = 63, kTilePublish = 64;
 
 struct DsaHierarchy;  // sn_dsa.cu
 struct UnionDsa;      // sn_batch.cu
+struct BatchKrylov;   // sn_batch_krylov.cu
 
 // Element families a batch can mix; a 32-item chunk of the batched work list never mixes them.
 enum { FAM_2D_P1 = 0, FAM_2D_P2 = 1, FAM_2D_P3 = 2, FAM_3D_P1 = 3, FAM_COUNT = 4 };
@@ -224,6 +225,7 @@ struct sn_batch {
     bool cached = false;                     // every instance has an operator cache: node-per-lane kernels
     cudaGraphExec_t sweep_graph = nullptr;   // level schedule, all instances
     cudaGraphExec_t iter_graph = nullptr;    // one whole outer iteration
+    long long graph_gen = 0;                 // advanced whenever recorded batch graphs go stale
     cudaStream_t cap_stream = nullptr;
     // concatenated iteration vectors (instance blocks at dof_off)
     std::vector<long long> dof_off;
@@ -236,6 +238,7 @@ struct sn_batch {
     int* d_next = nullptr;                   // per-instance "iterate again" flags
     int* d_dof_inst = nullptr;               // instance of every concatenated DOF
     sn::UnionDsa* dsa = nullptr;
+    sn::BatchKrylov* kry = nullptr;          // batched flexible GMRES workspace and graphs
     std::vector<std::vector<unsigned char>> dsa_masks;  // thick masks the union DSA was built for
     int dsa_sigma = -1;
     // key of the captured iteration graph
@@ -293,8 +296,12 @@ void drop_iter_graph(sn_mesh* m);
 cudaError_t prepare_recorded_sweep(sn_mesh* m, int precision, cudaStream_t s);
 // batched sweep over all instances of a batch (sn_sweep.cu)
 cudaError_t batch_build_worklist(sn_batch* b, cudaStream_t s);
-cudaError_t batch_enqueue_sweep(sn_batch* b, int precision, cudaStream_t s);  // level schedule, capturable
-cudaError_t batch_launch_dataflow(sn_batch* b, int precision, cudaStream_t s);
+// (args / mask: argument table and per-instance mask other than the batch's own, e.g. the
+// homogeneous table of the batched fGMRES; null = b->d_args / b->d_active)
+cudaError_t batch_enqueue_sweep(sn_batch* b, int precision, cudaStream_t s, const SweepArgs* args = nullptr,
+                                const int* mask = nullptr);  // level schedule, capturable
+cudaError_t batch_launch_dataflow(sn_batch* b, int precision, cudaStream_t s, const SweepArgs* args = nullptr,
+                                  const int* mask = nullptr);
 cudaError_t batch_set_precision(sn_batch* b, int precision, cudaStream_t s);
 // union DSA of a batch (sn_batch.cu)
 UnionDsa* union_dsa_build(const std::vector<DsaHierarchy*>& parts, const std::vector<long long>& dof_off,
@@ -306,6 +313,11 @@ cudaError_t union_dsa_correct(UnionDsa* U, const double* r_all, double* phi_all,
                               int max_iters, cudaStream_t s);
 cudaError_t batch_enqueue_iteration(sn_batch* b, const sn_iter_opts* o, int* d_next, const int* d_dof_inst,
                                     cudaStream_t s);
+// batched flexible GMRES (sn_batch_krylov.cu): per-instance Arnoldi steps, last relative
+// residuals, transport updates and convergence flags
+cudaError_t batch_fgmres(sn_batch* b, const sn_iter_opts* o, cudaStream_t s, std::vector<int>& iters,
+                         std::vector<double>& rel, std::vector<int>& sweeps, std::vector<int>& conv);
+void batch_krylov_free(BatchKrylov* K);
 cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double q_scale, cudaStream_t s);
 cudaError_t prepare_operator_cache(sn_mesh* m, int precision, cudaStream_t s);
 void free_operator_cache(sn_mesh* m);

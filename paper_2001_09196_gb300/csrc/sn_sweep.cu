@@ -2129,6 +2129,7 @@ cudaError_t batch_refresh_cache(sn_batch* b, int precision, cudaStream_t s) {
         if (b->sweep_graph) cudaGraphExecDestroy(b->sweep_graph);
         if (b->iter_graph) cudaGraphExecDestroy(b->iter_graph);
         b->sweep_graph = b->iter_graph = nullptr;
+        ++b->graph_gen;
     }
     // the kernels read the table from device memory, so recorded graphs stay valid
     if (!changed) return cudaSuccess;
@@ -2546,12 +2547,15 @@ cudaError_t batch_set_precision(sn_batch* b, int precision, cudaStream_t s) {
         cudaGraphExecDestroy(b->iter_graph);
         b->iter_graph = nullptr;
     }
+    ++b->graph_gen;
     return cudaMemcpyAsync(b->d_args, b->h_args.data(), b->count * sizeof(SweepArgs), cudaMemcpyHostToDevice, s);
 }
 
-cudaError_t batch_enqueue_sweep(sn_batch* b, int precision, cudaStream_t s) {
+cudaError_t batch_enqueue_sweep(sn_batch* b, int precision, cudaStream_t s, const SweepArgs* args, const int* mask) {
     cudaError_t err = batch_set_precision(b, precision, s);
     if (err != cudaSuccess) return err;
+    if (!args) args = b->d_args;
+    if (!mask) mask = b->d_active;
     const int bs = b->block;
     for (size_t k = 0; k < b->seg_begin.size(); ++k) {
         const long long lo = b->seg_begin[k], hi = b->seg_end[k];
@@ -2559,20 +2563,20 @@ cudaError_t batch_enqueue_sweep(sn_batch* b, int precision, cudaStream_t s) {
         const int fam = b->seg_fam[k];
 #define SN_BATCH_LEVEL(MODE_)                                                                                   \
     do {                                                                                                      \
-        if (fam == FAM_2D_P1) batch_level_kernel<2, 1, MODE_><<<g, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active); \
-        else if (fam == FAM_2D_P2) batch_level_kernel<2, 2, MODE_><<<g, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active); \
-        else if (fam == FAM_2D_P3) batch_level_kernel<2, 3, MODE_><<<g, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active); \
-        else batch_level_kernel<3, 1, MODE_><<<g, bs, 0, s>>>(b->d_args, b->d_items, lo, hi, b->d_active);       \
+        if (fam == FAM_2D_P1) batch_level_kernel<2, 1, MODE_><<<g, bs, 0, s>>>(args, b->d_items, lo, hi, mask); \
+        else if (fam == FAM_2D_P2) batch_level_kernel<2, 2, MODE_><<<g, bs, 0, s>>>(args, b->d_items, lo, hi, mask); \
+        else if (fam == FAM_2D_P3) batch_level_kernel<2, 3, MODE_><<<g, bs, 0, s>>>(args, b->d_items, lo, hi, mask); \
+        else batch_level_kernel<3, 1, MODE_><<<g, bs, 0, s>>>(args, b->d_items, lo, hi, mask);       \
     } while (0)
 #define SN_BATCH_NODE(MODE_)                                                                                    \
     do {                                                                                                      \
         const unsigned gn = grid_for(((hi - lo + ipw - 1) / ipw) * 32, bs);                                   \
         const bool pdl = k > 0;                                                                               \
         cudaError_t lerr;                                                                                     \
-        if (fam == FAM_2D_P1) lerr = launch_k(pdl, batch_node_level_kernel<2, 1, MODE_>, gn, bs, s, b->d_args, b->d_items, lo, hi, b->d_active); \
-        else if (fam == FAM_2D_P2) lerr = launch_k(pdl, batch_node_level_kernel<2, 2, MODE_>, gn, bs, s, b->d_args, b->d_items, lo, hi, b->d_active); \
-        else if (fam == FAM_2D_P3) lerr = launch_k(pdl, batch_node_level_kernel<2, 3, MODE_>, gn, bs, s, b->d_args, b->d_items, lo, hi, b->d_active); \
-        else lerr = launch_k(pdl, batch_node_level_kernel<3, 1, MODE_>, gn, bs, s, b->d_args, b->d_items, lo, hi, b->d_active); \
+        if (fam == FAM_2D_P1) lerr = launch_k(pdl, batch_node_level_kernel<2, 1, MODE_>, gn, bs, s, args, b->d_items, lo, hi, mask); \
+        else if (fam == FAM_2D_P2) lerr = launch_k(pdl, batch_node_level_kernel<2, 2, MODE_>, gn, bs, s, args, b->d_items, lo, hi, mask); \
+        else if (fam == FAM_2D_P3) lerr = launch_k(pdl, batch_node_level_kernel<2, 3, MODE_>, gn, bs, s, args, b->d_items, lo, hi, mask); \
+        else lerr = launch_k(pdl, batch_node_level_kernel<3, 1, MODE_>, gn, bs, s, args, b->d_items, lo, hi, mask); \
         if (lerr != cudaSuccess) return lerr;                                                                 \
     } while (0)
         SN_COUNT_LAUNCH();
@@ -2595,9 +2599,11 @@ __global__ void bump_epoch_kernel(unsigned long long* ctrl) {
 }
 
 // Persistent dataflow sweep of all instances; capturable (the epoch is advanced on the device).
-cudaError_t batch_launch_dataflow(sn_batch* b, int precision, cudaStream_t s) {
+cudaError_t batch_launch_dataflow(sn_batch* b, int precision, cudaStream_t s, const SweepArgs* args, const int* mask) {
     cudaError_t err = batch_set_precision(b, precision, s);
     if (err != cudaSuccess) return err;
+    if (!args) args = b->d_args;
+    if (!mask) mask = b->d_active;
     SN_COUNT_LAUNCH();
     bump_epoch_kernel<<<1, 1, 0, s>>>(b->d_ctrl);
     int dev = 0, sms = 0, per_sm = 1;
@@ -2625,28 +2631,28 @@ cudaError_t batch_launch_dataflow(sn_batch* b, int precision, cudaStream_t s) {
         const long long warps = b->schedule == SCHED_STATIC ? blocks * (b->block / 32) : 0;
         SN_COUNT_LAUNCH();
         if (precision == SN_FP64)
-            batch_node_datapoll_kernel<0><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam,
-                                                                               b->n_items, b->d_ctrl, b->d_active,
+            batch_node_datapoll_kernel<0><<<(unsigned)blocks, b->block, 0, s>>>(args, b->d_items, b->d_chunk_fam,
+                                                                               b->n_items, b->d_ctrl, mask,
                                                                                timeout, warps);
         else
-            batch_node_datapoll_kernel<1><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam,
-                                                                               b->n_items, b->d_ctrl, b->d_active,
+            batch_node_datapoll_kernel<1><<<(unsigned)blocks, b->block, 0, s>>>(args, b->d_items, b->d_chunk_fam,
+                                                                               b->n_items, b->d_ctrl, mask,
                                                                                timeout, warps);
         return cudaGetLastError();
     }
     SN_COUNT_LAUNCH();
     if (precision == SN_FP64)
-        batch_dataflow_kernel<0><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam, b->n_items,
+        batch_dataflow_kernel<0><<<(unsigned)blocks, b->block, 0, s>>>(args, b->d_items, b->d_chunk_fam, b->n_items,
                                                                       b->d_done, b->d_done_off, epoch, b->d_ctrl,
-                                                                      b->d_active, timeout);
+                                                                      mask, timeout);
     else if (precision == SN_FP32)
-        batch_dataflow_kernel<1><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam, b->n_items,
+        batch_dataflow_kernel<1><<<(unsigned)blocks, b->block, 0, s>>>(args, b->d_items, b->d_chunk_fam, b->n_items,
                                                                       b->d_done, b->d_done_off, epoch, b->d_ctrl,
-                                                                      b->d_active, timeout);
+                                                                      mask, timeout);
     else
-        batch_dataflow_kernel<2><<<(unsigned)blocks, b->block, 0, s>>>(b->d_args, b->d_items, b->d_chunk_fam, b->n_items,
+        batch_dataflow_kernel<2><<<(unsigned)blocks, b->block, 0, s>>>(args, b->d_items, b->d_chunk_fam, b->n_items,
                                                                       b->d_done, b->d_done_off, epoch, b->d_ctrl,
-                                                                      b->d_active, timeout);
+                                                                      mask, timeout);
     return cudaGetLastError();
 }
 

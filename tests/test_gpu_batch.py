@@ -115,3 +115,85 @@ def test_batch_convergence_masks_freeze_converged_instances(sn):
         single = m.source_iterate(dsa="none", tol=1e-6, max_iters=600)
         assert res["iters"][k] == single["iters"]
         assert torch.equal(res["phi"][k], single["phi"])
+
+
+def weakly_scattering_instances():
+    """The ragged mix with scattering ratios capped at 0.9, so that fGMRES without the DSA step
+    converges in tens of Arnoldi steps."""
+    out = small_instances()
+    for p in out:
+        p.sigma_s[:] = np.minimum(p.sigma_s, 0.9 * p.sigma_t)
+    return out
+
+
+@pytest.mark.parametrize("schedule", [("levels", 64, 0), ("dataflow", 128, 0), ("static", 32, 0)])
+def test_batched_fgmres_reaches_the_oracle_fixed_point(sn, schedule, oracle_runs):
+    """Every instance's own flexible GMRES (Eq. schur, right-preconditioned by the union DSA step of
+    Algorithm 2), run in lock step over the batch, converges to the oracle's fixed point of that
+    instance within 1e-9 (a 1e-12 residual times the conditioning of Eq. schur)."""
+    probs = small_instances()
+    meshes = [sn.Mesh.from_problem(p) for p in probs]
+    batch = sn.Batch(meshes)
+    batch.set_schedule(*schedule)
+    res = batch.source_iterate(dsa="thick", thick_rule="sigma_t_h", outer="fgmres", restart=30, tol=1e-12,
+                               inner_tol=1e-12, inner_max_iters=1000, max_iters=400)
+    assert res["converged"]
+    for k, (p, (_, ref)) in enumerate(zip(probs, oracle_runs)):
+        assert res["rel_residual"][k] <= 1e-12
+        err = float(np.abs(res["phi"][k].cpu().numpy() - ref).max() / np.abs(ref).max())
+        assert err < 1e-9, (k, err)
+
+
+def test_batched_fgmres_instances_are_independent_without_dsa(sn):
+    """Without the DSA step nothing couples the instances: each instance's Arnoldi process uses
+    inner products over its own DOFs only (summed in a fixed chunk order), so every instance of a
+    batch ends bit for bit where a batch of that instance alone ends, after as many steps.  A small
+    restart forces several cycles."""
+    probs = weakly_scattering_instances()
+    meshes = [sn.Mesh.from_problem(p) for p in probs]
+    batch = sn.Batch(meshes)
+    opts = dict(dsa="none", outer="fgmres", restart=5, tol=1e-10, max_iters=600)
+    res = batch.source_iterate(**opts)
+    assert res["converged"]
+    assert len(set(res["iters"])) > 1
+    for k, m in enumerate(meshes):
+        alone = sn.Batch([m]).source_iterate(**opts)
+        assert alone["iters"][0] == res["iters"][k]
+        assert torch.equal(alone["phi"][0], res["phi"][k]), k
+
+
+@pytest.mark.parametrize("restart", [5, 30])
+def test_batched_fgmres_follows_the_single_mesh_fgmres(sn, restart):
+    """Without the DSA step the batched and the single-mesh fGMRES run the same algorithm on the
+    same operator (only the order of the inner-product sums differs): the same number of Arnoldi
+    steps and solutions within 1e-10 of each other."""
+    probs = weakly_scattering_instances()
+    meshes = [sn.Mesh.from_problem(p) for p in probs]
+    opts = dict(dsa="none", outer="fgmres", restart=restart, tol=1e-10, max_iters=600)
+    res = sn.Batch(meshes).source_iterate(**opts)
+    for k, m in enumerate(meshes):
+        single = m.source_iterate(**opts)
+        assert abs(single["iters"] - res["iters"][k]) <= 1, (k, single["iters"], res["iters"][k])
+        ref = single["phi"]
+        assert float((res["phi"][k] - ref).abs().max() / ref.abs().max()) < 1e-10, k
+
+
+def test_batched_fgmres_fp32_form(sn, oracle_runs):
+    """FP32 element solves inside the batched fGMRES (float64 flux, residual, DSA and Krylov
+    arithmetic): every instance within the derived FP32 bound of the oracle's fixed point."""
+    from tolerances import fp32_fixed_point_tol
+    probs = small_instances()
+    meshes = [sn.Mesh.from_problem(p) for p in probs]
+    res = sn.Batch(meshes).source_iterate(dsa="thick", thick_rule="sigma_t_h", outer="fgmres", restart=30,
+                                          tol=1e-6, inner_tol=1e-10, inner_max_iters=1000, max_iters=400,
+                                          precision="fp32")
+    assert res["converged"]
+    for k, (p, (_, ref)) in enumerate(zip(probs, oracle_runs)):
+        err = float(np.abs(res["phi"][k].cpu().numpy() - ref).max() / np.abs(ref).max())
+        assert err <= fp32_fixed_point_tol(p), (k, err)
+
+
+def test_batched_fgmres_rejects_mixed_precision(sn):
+    meshes = [sn.Mesh.from_problem(p) for p in small_instances()[:2]]
+    with pytest.raises(sn.SnError):
+        sn.Batch(meshes).source_iterate(dsa="thick", thick_rule="sigma_t_h", outer="fgmres", precision="fp32_mixed")

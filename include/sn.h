@@ -49,7 +49,7 @@ enum { SN_FP64 = 0, SN_FP32 = 1, SN_FP32_REFINE = 2, SN_FP32_MIXED = 3 };  /* el
 enum { SN_DSA_NONE = 0, SN_DSA_FULL = 1, SN_DSA_THICK = 2, SN_DSA_TRIANGULAR = 3 };  /* DSA variant */
 enum { SN_THICK_SIGMA_S = 0, SN_THICK_SIGMA_T_H = 1, SN_THICK_MASK = 2 };
 enum { SN_DSA_SIGMA_S = 0, SN_DSA_SIGMA_T = 1 };
-enum { SN_DSA_OP_SIP = 0, SN_DSA_OP_NIP = 1, SN_DSA_OP_MNIP = 2 };  /* DSA operator (Sec. 4.1) */
+enum { SN_DSA_OP_SIP = 0, SN_DSA_OP_NIP = 1, SN_DSA_OP_MNIP = 2 };  /* DSA operator (Sec. 3.1) */
 enum { SN_VCYCLE_AUTO = 0, SN_VCYCLE_FP64 = 1, SN_VCYCLE_FP32 = 2 };  /* DSA preconditioner arithmetic */
 enum { SN_OUTER_SI = 0, SN_OUTER_FGMRES = 1 };                  /* outer iteration */
 enum { SN_CACHE_OFF = 0, SN_CACHE_ON = 1, SN_CACHE_AUTO = 2 };  /* operator cache */
@@ -155,7 +155,7 @@ sn_status sn_set_materials(sn_mesh* mesh, const double* sigma_t, const double* s
 
 /*
  * sn_set_pseudo_scattering: the materials of one implicit time step of gray thermal radiative
- * transfer written as a steady transport problem (Sec. 5.2, Eq. hohlraum_sigma, Eq. hohlraum_q),
+ * transfer written as a steady transport problem (Sec. 4.2, Eq. hohlraum_sigma, Eq. hohlraum_q),
  * computed per element on the device from the opacity sigma (= sigma_a), the heat capacity C_v
  * and the temperature T:
  *     b = 16 pi a c T^3,  sigma_t = sigma,  sigma_s = sigma^2 b / (C_v/dt + sigma b),
@@ -214,8 +214,8 @@ typedef sn_status (*sn_exchange_fn)(double* phi_partial, long long n, void* stre
 
 typedef struct {
     int dsa;                 /* SN_DSA_NONE | SN_DSA_FULL | SN_DSA_THICK (Algorithm 2) | SN_DSA_TRIANGULAR (Algorithm 1) */
-    int thick_rule;          /* SN_THICK_SIGMA_S (sigma_s >= eta, Sec. 4.2) | SN_THICK_SIGMA_T_H | SN_THICK_MASK */
-    double eta;              /* threshold of the thick rule; the paper uses eta = 1 (Sec. 5.1) */
+    int thick_rule;          /* SN_THICK_SIGMA_S (sigma_s >= eta, Sec. 3.2) | SN_THICK_SIGMA_T_H | SN_THICK_MASK */
+    double eta;              /* threshold of the thick rule; the paper uses eta = 1 (Sec. 4.1) */
     const unsigned char* mask; /* host, n_elem, used with SN_THICK_MASK */
     int dsa_sigma;           /* SN_DSA_SIGMA_S (default) | SN_DSA_SIGMA_T: mass matrix of the DSA rhs */
     double tol;              /* relative residual ||r^i|| / ||r^0|| (Euclidean, nodal) */
@@ -232,7 +232,7 @@ typedef struct {
     double* checkpoints;     /* device, max_checkpoints x n_elem x n_nodes, or NULL */
     int max_checkpoints;
     int warm_start;          /* 1: start from phi_inout, 0: from phi = 0 */
-    int outer;               /* SN_OUTER_SI (fixed point, Eq. DSA_fp) | SN_OUTER_FGMRES (Sec. 5) */
+    int outer;               /* SN_OUTER_SI (fixed point, Eq. DSA_fp) | SN_OUTER_FGMRES (Sec. 4) */
     int restart;             /* fGMRES restart length (1..60; the paper uses 30) */
     int dsa_operator;        /* SN_DSA_OP_SIP (default) | SN_DSA_OP_NIP (Eq. NIP) | SN_DSA_OP_MNIP (Eq. NIP with
                                 the penalty of Eq. ModifiedF0); see sn_source_iterate */
@@ -271,7 +271,7 @@ typedef struct {
     double ms_dsa;           /* device time of the DSA solves (CUDA events); both 0 for batches */
 } sn_iter_stats;
 
-/* Defaults: dsa thick, sigma_s >= 1, tol 1e-8, inner_tol 1e-4 (Sec. 5), FP64, cold start. */
+/* Defaults: dsa thick, sigma_s >= 1, tol 1e-8, inner_tol 1e-4 (Sec. 4), FP64, cold start. */
 void sn_iter_opts_default(sn_iter_opts* opts);
 
 /*
@@ -280,19 +280,19 @@ void sn_iter_opts_default(sn_iter_opts* opts);
  *     phi_half^i = sweep(phi^i),  r^i = phi_half^i - phi^i,
  *     phi^{i+1} = phi_half^i + E_f D_ff^{-1} Sigma_f r^i_f     (nothing added for SN_DSA_NONE),
  * with D_ff the symmetric interior-penalty diffusion operator on the thick elements
- * (Sec. 4.1-4.2; SN_DSA_FULL uses every element) solved by conjugate gradients
+ * (Sec. 3.1-3.2; SN_DSA_FULL uses every element) solved by conjugate gradients
  * preconditioned with a geometric multigrid V-cycle.  Stops after the iteration whose
  * ||r^i|| <= tol ||r^0||.  phi_inout: device [elem][node]; receives phi^{i+1}.
  * With outer = SN_OUTER_FGMRES the same system S phi = b (Eq. schur) is solved by flexible
  * GMRES(restart) right-preconditioned by the same DSA step, I + E_f D_ff^{-1} Sigma_f E_f^T (the paper's
- * outer solver, Sec. 5; "flexible" because each DSA solve is inexact).  Its residual b - S phi equals
+ * outer solver, Sec. 4; "flexible" because each DSA solve is inexact).  Its residual b - S phi equals
  * the source-iteration residual, so tol means the same; iters counts Krylov iterations.
  * SN_DSA_TRIANGULAR is the block upper-triangular preconditioner of Algorithm 1 (Eq. approxS): the
  * thick-only DSA step above, then a transport update with zero fixed source and vacuum inflow of
  * [0; corrected thick part] whose result is added on the thin DOFs only (one extra sweep per outer
  * iteration).  It uses the same thick rule; it is not available for the adjoint or for batches
  * (SN_ERR_ARG).
- * opts->dsa_operator picks D_ff (Sec. 4.1; D = 1/(3 sigma_t), sigma_a = sigma_t - sigma_s, all
+ * opts->dsa_operator picks D_ff (Sec. 3.1; D = 1/(3 sigma_t), sigma_a = sigma_t - sigma_s, all
  * integrals on the (p+1)-point Gauss rule; a face to a non-thick element or the boundary is a face
  * to a zero exterior state, as in a principal submatrix):
  *   SN_DSA_OP_SIP: symmetric interior penalty with kappa = max(1/4, 2 p(p+1) {D/h}), h = |K|/|F|;
@@ -340,7 +340,7 @@ sn_status sn_gradients(sn_mesh* mesh, const double* phi, const double* mu, doubl
                        double* d_sigma_s, double* d_q, void* stream);
 
 /*
- * Diagnostics of the DSA operator (Sec. 4): y = D_ff x on the elements selected by opts
+ * Diagnostics of the DSA operator (Sec. 3): y = D_ff x on the elements selected by opts
  * (x, y device, [elem][node]; entries outside the thick set are ignored / set to 0), and the
  * PCG + V-cycle solve of D_ff x = b to opts->inner_tol.  *iters receives the PCG count.
  */
@@ -351,7 +351,7 @@ sn_status sn_dsa_solve(sn_mesh* mesh, const sn_iter_opts* opts, const double* b,
 /*
  * Diagnostic: copies psi_d (direction d) of the last forward sweep (or lambda_d of the last
  * adjoint sweep if adjoint != 0) into out (device, [elem][node], float64; the FP32 form's
- * float32 values are widened).  Used to check the element equations of Sec. 4.1 at full size.
+ * float32 values are widened).  Used to check the element equations of Sec. 3.1 at full size.
  */
 sn_status sn_get_angular_flux(sn_mesh* mesh, int d, int adjoint, int precision, double* out, void* stream);
 

@@ -1,11 +1,11 @@
 """Diffusion synthetic acceleration restricted to the thick subdomain (CPU oracle, tests only).
 
 Paper: Sec. 2.2 (Eq. dsa_prec, Eq. DSA_fp and the additive form D^{-1} = I + D^{-1} Sigma),
-Sec. 3 (Algorithm 2, diagonal heterogeneous DSA: phi_f <- phi_f + D_ff^{-1} Sigma_f r_f; and
+Sec. 2.3 (Algorithm 2, diagonal heterogeneous DSA: phi_f <- phi_f + D_ff^{-1} Sigma_f r_f; and
 Algorithm 1, triangular heterogeneous DSA, the same step followed by a zero-source transport
 update of the thick correction whose result is added on the thin DOFs only),
-Sec. 4.1 (interior-penalty DSA operators: Eq. SIP, Eq. NIP and the modified penalty of
-Eq. ModifiedF0) and Sec. 4.2 (the heterogeneous operator is the principal submatrix on the
+Sec. 3.1 (interior-penalty DSA operators: Eq. SIP, Eq. NIP and the modified penalty of
+Eq. ModifiedF0) and Sec. 3.2 (the heterogeneous operator is the principal submatrix on the
 thick elements, thick where sigma_s >= eta).
 
 Three operators, all with D = 1/(3 sigma_t), sigma_a = sigma_t - sigma_s and the same volume form
@@ -18,16 +18,16 @@ interior-penalty matrix gives on such a face.
     kappa_F = max(1/4, c(p) (D^-/h^- + D^+/h^+)/2) on interior faces and max(1/4, c(p) D/h) on
     boundary faces, c(p) = C_IP p (p+1), h = |K|/|F|.  1/4 is the angular integral of the paper's
     F_0 = (1/4 pi) sum_d w_d |Omega_d.n|/2; the max() floor is the idea of Eq. ModifiedF0 in the
-    form of the modified interior penalty method.  Only thick-element data enter (Sec. 4.2).
+    form of the modified interior penalty method.  Only thick-element data enter (Sec. 3.2).
   * "nip" (Eq. NIP): drops the symmetrising term G^T Sigma_t^{-1} F_1, which is the face term
     -<{D grad v.n},[u]>; keeps -<{D grad u.n},[v]> (the term F_1^T Sigma_t^{-1} G) and the plain
     penalty F_0, kappa_F = 1/4.  Nonsymmetric.
   * "mnip" (Eq. NIP with Eq. ModifiedF0): the face terms of "nip" with the modified penalty
         kappa_F = 1/8 [max(c(p)/(sigma_t^- h^-), 1) + max(c(p)/(sigma_t^+ h^+), 1)],
-    c(p) = C_M p (p+1), C_M = 0.1 (Sec. 4.1.1).  Reading: each side is the upwind side for the
+    c(p) = C_M p (p+1), C_M = 0.1 (Sec. 3.1.1).  Reading: each side is the upwind side for the
     directions leaving it, and (1/4 pi) times the angular integral of |Omega.n| over either half
     of the sphere is 1/4, so the (1/8 pi) sum over directions splits into 1/8 per side.  The
-    neighbour is any element, thin ones included (Sec. 4.2 notes that heterogeneous mNIP brings
+    neighbour is any element, thin ones included (Sec. 3.2 notes that heterogeneous mNIP brings
     thin data into the thick submatrix); on the domain boundary the element's own value stands
     for the missing side.  A void neighbour (sigma_t = 0) makes the penalty infinite: the paper
     states that Eq. ModifiedF0 is not compatible with voids, so this is an error.
@@ -44,7 +44,7 @@ import scipy.sparse.linalg as spla
 from .dg import adjugate, face_points, tensor_rule
 
 C_IP = 2.0
-C_M = 0.1  # the constant of c(p) in Eq. ModifiedF0 (Sec. 4.1.1)
+C_M = 0.1  # the constant of c(p) in Eq. ModifiedF0 (Sec. 3.1.1)
 OPERATORS = ("sip", "nip", "mnip")
 
 
@@ -244,7 +244,7 @@ class TriangularDSA:
 def thick_mask(prob):
     """Thick/thin split of the problem's elements (uint8 per element).
 
-    Rule "sigma_s" (the paper's, Sec. 3.3 and Sec. 4.2 with eta = 1 in Sec. 5.1): thick where
+    Rule "sigma_s" (the paper's, Sec. 2.3 and Sec. 3.2 with eta = 1 in Sec. 4.1): thick where
     sigma_s >= eta.  Rule "sigma_t_h": thick where sigma_t h > eta with h the element width 1/nx (an
     optically thick cell).  A void element (sigma_t = 0) is never thick under either rule.
     """

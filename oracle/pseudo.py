@@ -1,7 +1,7 @@
 """Pseudo-scattering coefficients of one implicit time step of gray thermal radiative transfer
 (CPU oracle, test infrastructure only).
 
-Paper Sec. 5.2, Eq. hohlraum_sigma and Eq. hohlraum_q: with b = 16 pi a c T^3,
+Paper Sec. 4.2, Eq. hohlraum_sigma and Eq. hohlraum_q: with b = 16 pi a c T^3,
     sigma_ps = sigma^2 b / (C_v/dt + sigma b),
     q_ps     = sigma_a a c T^4 - sigma^2 b a c T^4 / (C_v/dt + sigma b),
 and the steady transport problem of the time step takes sigma_t = sigma, sigma_s = sigma_ps and

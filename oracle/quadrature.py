@@ -4,7 +4,7 @@ Angular: the level-symmetric S_N set of the semi-discrete equations (Eq. sntrans
 Sec. 1), with the scalar flux phi = sum_d w_d psi_d and sum_d w_d = 4*pi, so that the
 isotropic scattering term sigma_s/(4 pi) * sum_d w_d psi_d of Eq. (1) keeps its meaning.
 In 2D only the directions with positive polar cosine are kept and their weights doubled
-(the paper's "40 angles" for S8 in 2D, Sec. 5.1).
+(the paper's "40 angles" for S8 in 2D, Sec. 4.1).
 
 Construction (Lewis & Miller, "Computational Methods of Neutron Transport", 1984, ch. 4):
 the N/2 distinct direction cosines satisfy mu_i^2 = mu_1^2 + (i-1) * 2(1 - 3 mu_1^2)/(N-2),

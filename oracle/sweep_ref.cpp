@@ -2,7 +2,7 @@
 // the product path never loads it).
 //
 // What it computes is the update of Sec. 1 (Eq. psi and Eq. phi) in the upwind DG discretisation of
-// Sec. 4.1 (Eq. Tmat1), the same steps as oracle/transport.py and independent of the CUDA library:
+// Sec. 3.1 (Eq. Tmat1), the same steps as oracle/transport.py and independent of the CUDA library:
 //   for every direction d: psi_d = L_d^{-1}(M (q/(4 pi) + sigma_s phi/(4 pi)) - inflow terms), solved
 //   element by element in a Kahn order of the upwind graph (Omega.n on each face), with
 //     A_e = sigma_t M_e - (psi, Omega.grad v)_e + sum_{outflow faces} <(Omega.n) psi, v>,

@@ -5,7 +5,7 @@ What is computed (paper references are to sections / equations):
         Omega_d . grad psi_d + sigma_t psi_d = q_d + sigma_s/(4 pi) sum_d' w_d' psi_d',
     psi_d = psi_inc on inflow boundary faces, phi = sum_d w_d psi_d, sum_d w_d = 4 pi.
     The isotropic source q (total emission per unit volume) gives q_d = q/(4 pi).
-  * Upwind DG in space (Sec. 4.1, Eq. Tmat1): on element K with test function v,
+  * Upwind DG in space (Sec. 3.1, Eq. Tmat1): on element K with test function v,
         -(psi, Omega.grad v)_K + (sigma_t psi, v)_K + sum_{F outflow} <(Omega.n) psi, v>_F
           = (S, v)_K - sum_{F inflow} <(Omega.n) psi_up, v>_F ,
     psi_up the upwind neighbour's trace, or psi_inc on the domain boundary.  (The

@@ -427,7 +427,7 @@ sn_status sn_mesh_set_schedule(sn_mesh* m, int schedule, int block, int param) {
     return SN_OK;
 }
 
-// Thick mask selected by opts (Sec. 4.2: sigma_s >= eta; or sigma_t h > eta; or explicit; all for full DSA).
+// Thick mask selected by opts (Sec. 3.2: sigma_s >= eta; or sigma_t h > eta; or explicit; all for full DSA).
 static sn_status thick_mask_for(const sn_mesh* m, const sn_iter_opts* o, std::vector<unsigned char>& mask) {
     mask.assign(m->ne, 0);
     if (o->dsa == SN_DSA_FULL) {

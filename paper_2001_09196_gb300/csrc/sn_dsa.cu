@@ -1,4 +1,4 @@
-// Thick-subdomain DSA on the device (paper Sec. 2.2 Eq. DSA_fp, Algorithm 2, Sec. 4):
+// Thick-subdomain DSA on the device (paper Sec. 2.2 Eq. DSA_fp, Algorithm 2, Sec. 3):
 // conjugate gradients on the symmetric operator (Eq. SIP), BiCGStab on the nonsymmetric ones
 // (Eq. NIP, with or without Eq. ModifiedF0), both preconditioned by one multigrid V-cycle
 // (block-Jacobi on the DG level, weighted Jacobi on the continuous levels, dense coarsest).

@@ -1,6 +1,6 @@
 // Host-side setup of the thick-subdomain DSA operator and its multigrid hierarchy.
 //
-// Operators (paper Sec. 4.1; Sec. 4.2: the heterogeneous operator is the principal submatrix on
+// Operators (paper Sec. 3.1; Sec. 3.2: the heterogeneous operator is the principal submatrix on
 // the thick elements):
 //   a(u,v) = sum_K (D grad u, grad v)_K + (sigma_a u, v)_K
 //          + sum_{interior thick-thick F} <kappa [u],[v]> - <{D grad u.n},[v]> - s <{D grad v.n},[u]>
@@ -20,7 +20,7 @@
 // are transposed before the hierarchy is built (the Galerkin hierarchy of A^T is the transpose of
 // that of A).
 //
-// Multigrid (replaces the paper's BoomerAMG, Sec. 5): level 0 is the DG space on the thick
+// Multigrid (replaces the paper's BoomerAMG, Sec. 4): level 0 is the DG space on the thick
 // elements with element block-Jacobi smoothing; level 1 is continuous Q1 on the vertices of
 // thick elements (prolongation = the element's own bilinear/trilinear map evaluated at its
 // nodes); coarser levels halve the vertex grid per axis with linear interpolation; every

@@ -1,5 +1,5 @@
 // Materials of one implicit time step of gray thermal radiative transfer in the pseudo-scattering
-// form (paper Sec. 5.2, Eq. hohlraum_sigma and Eq. hohlraum_q), one thread per element:
+// form (paper Sec. 4.2, Eq. hohlraum_sigma and Eq. hohlraum_q), one thread per element:
 //   b = 16 pi a c T^3,  sigma_t = sigma,  sigma_s = sigma (sigma b) / (C_v/dt + sigma b),
 //   q = 4 pi sigma a c T^4 (C_v/dt) / (C_v/dt + sigma b).
 // The last line is the printed q_ps = sigma a c T^4 - sigma^2 b a c T^4 / (C_v/dt + sigma b) with the

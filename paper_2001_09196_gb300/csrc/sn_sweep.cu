@@ -1,6 +1,6 @@
 // Upwind DG S_N sweep kernels for sm_103a.
 //
-// Discretisation (paper Sec. 1, Eq. sntransport; Sec. 4.1, Eq. Tmat1): on element K and
+// Discretisation (paper Sec. 1, Eq. sntransport; Sec. 3.1, Eq. Tmat1): on element K and
 // direction Omega, with Q_p nodal basis at the (p+1)^dim tensor Gauss-Legendre points,
 //   -(psi, Omega.grad v)_K + (sigma_t psi, v)_K + sum_{F outflow} <(Omega.n) psi, v>_F
 //        = (S, v)_K - sum_{F inflow} <(Omega.n) psi_up, v>_F,   S = (q + sigma_s phi)/(4 pi).

@@ -10,7 +10,7 @@ pseudorandom number generators", OOPSLA 2014) used in its counter form:
 output k of a stream with seed s is mix64(s + (k + 1) * GAMMA).
 
 The workloads stand in for the paper's heterogeneous benchmarks (the crooked
-pipe of Sec. 5.1 / Table 1 and the hohlraum of Sec. 5.2, whose geometries are
+pipe of Sec. 4.1 / Table 1 and the hohlraum of Sec. 4.2, whose geometries are
 not available): thick, thin and void regions, scattering ratios close to one
 and cross sections spread over several decades.
 """
@@ -221,7 +221,7 @@ def config5(n: int = 128, seed: int = MASTER_SEED + 4) -> Problem:
     return prob
 
 
-# Materials of the hohlraum problem (Sec. 5.2, Table hohlraum_materials): opacity sigma and heat
+# Materials of the hohlraum problem (Sec. 4.2, Table hohlraum_materials): opacity sigma and heat
 # capacity C_v of gold wall, helium fill, capsule CH layer, hydrogen fuel; NIF units.
 HOHLRAUM_SIGMA = (1.0e3, 1.0e-3, 1.0e2, 1.0)
 HOHLRAUM_CV = (1.0e5, 1.0e-2, 1.0e3, 1.0)

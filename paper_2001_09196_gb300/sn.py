@@ -344,7 +344,7 @@ class Mesh:
         return phi_out
 
     def set_pseudo_scattering(self, sigma, cv, T, dt, a_rad=137.199, c_light=2.9979e4, stream=None):
-        """Materials of one pseudo-scattering time step (Sec. 5.2, Eq. hohlraum_sigma / hohlraum_q),
+        """Materials of one pseudo-scattering time step (Sec. 4.2, Eq. hohlraum_sigma / hohlraum_q),
         formed on the device from per-element opacity, heat capacity and temperature; the default
         constants are the paper's NIF-unit a and c."""
         import torch

@@ -1,4 +1,4 @@
-"""CPU: the library's host assembly of the thick-subdomain DSA operator (sn::dsa_build, Sec. 4.1-4.2:
+"""CPU: the library's host assembly of the thick-subdomain DSA operator (sn::dsa_build, Sec. 3.1-3.2:
 Eq. SIP, Eq. NIP and Eq. NIP with the penalty of Eq. ModifiedF0, and the transposed operator the
 adjoint solves with) against the oracle's operator, element block by element block.
 

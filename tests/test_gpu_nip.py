@@ -1,4 +1,4 @@
-"""GPU parity of the nonsymmetric DSA operators (Sec. 4.1: Eq. NIP, and Eq. NIP with the penalty
+"""GPU parity of the nonsymmetric DSA operators (Sec. 3.1: Eq. NIP, and Eq. NIP with the penalty
 of Eq. ModifiedF0) and their BiCGStab solves, through the C ABI, against the CPU oracle.
 
 Tolerances as for the symmetric operator: 1e-12 relative for operator products, 1e-9 for solves

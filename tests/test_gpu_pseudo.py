@@ -1,4 +1,4 @@
-"""GPU: the pseudo-scattering time step (Sec. 5.2, Eq. hohlraum_sigma / Eq. hohlraum_q) through the
+"""GPU: the pseudo-scattering time step (Sec. 4.2, Eq. hohlraum_sigma / Eq. hohlraum_q) through the
 C ABI against the CPU oracle, on the hohlraum-like layout.
 
 Coefficients: sigma_t exact, sigma_s to 1e-14 relative; q to 1e-13 of the emission term

@@ -1,6 +1,6 @@
 """GPU: the recorded outer iterations (one CUDA graph per solve, loop control on the device).
 
-Source iteration (Eq. DSA_fp with Algorithm 2 or 1) and flexible GMRES (Sec. 5) recorded as WHILE
+Source iteration (Eq. DSA_fp with Algorithm 2 or 1) and flexible GMRES (Sec. 4) recorded as WHILE
 conditional nodes run the same device operations in the same order as the host loops.  Source
 iteration keeps every scalar on the device in both forms, so its iterates, iteration counts,
 residual histories and checkpoints must be bitwise equal.  The host loop of fGMRES does its Givens

@@ -3,7 +3,7 @@ no GPU) against the oracle's level-symmetric sets (themselves pinned to the text
 against numpy's Gauss-Legendre rule and Lagrange basis.
 
 The library and the oracle compute their level-symmetric sets independently; the transport
-parity tests rely on both using the same directions and weights (Sec. 5.1, S8 = 40 angles in 2D).
+parity tests rely on both using the same directions and weights (Sec. 4.1, S8 = 40 angles in 2D).
 """
 import os
 import shutil

@@ -1,7 +1,7 @@
 """CPU: the C++ oracle of the transport update (oracle/sweep_ref.cpp) against the pinned numpy oracle
 and against closed forms.
 
-The C++ code restates the same steps (Sec. 1, Eq. psi and Eq. phi; upwind DG of Sec. 4.1) in a second
+The C++ code restates the same steps (Sec. 1, Eq. psi and Eq. phi; upwind DG of Sec. 3.1) in a second
 implementation; it serves as the timed CPU baseline, so it is pinned here: element by element equal
 to oracle.Transport.sweep (1e-13 relative) on Cartesian, jittered, Q3, 3D and inflow cases and on a
 partial direction range; the same bits for any number of threads; and an infinite medium with the

@@ -1,4 +1,4 @@
-"""Pins of the oracle's nonsymmetric DSA operators (Sec. 4.1: Eq. NIP and the modified penalty
+"""Pins of the oracle's nonsymmetric DSA operators (Sec. 3.1: Eq. NIP and the modified penalty
 of Eq. ModifiedF0) and of the transposed DSA step of the adjoint iteration.
 
 Eq. NIP is Eq. SIP without the symmetrising face term G^T Sigma_t^{-1} F_1 and with the plain

@@ -23,7 +23,7 @@ FOUR_PI = 4.0 * np.pi
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-# ---------------------------------------------------------------- quadrature (Sec. 1, Sec. 5.1)
+# ---------------------------------------------------------------- quadrature (Sec. 1, Sec. 4.1)
 @pytest.mark.parametrize("N,dim,count", [(4, 2, 12), (6, 2, 24), (8, 2, 40), (4, 3, 24), (6, 3, 48), (8, 3, 80)])
 def test_quadrature_counts(N, dim, count):
     d, w = level_symmetric(N, dim)
@@ -158,7 +158,7 @@ def test_dense_direct_solve_matches_source_iteration(n, p):
     assert np.abs(si - direct).max() < 1e-12 * scale
 
 
-# ---------------------------------------------------------------- DSA (Sec. 2.2, Algorithm 2, Sec. 4)
+# ---------------------------------------------------------------- DSA (Sec. 2.2, Algorithm 2, Sec. 3)
 def _void_free_c1():
     prob = inputs.config1()
     v = prob.sigma_t == 0
@@ -169,7 +169,7 @@ def _void_free_c1():
 @pytest.mark.parametrize("operator", ["sip", "nip", "mnip"])
 def test_dsa_fixed_point_invariance(operator):
     """DSA is a preconditioner only: none / thick / full reach the same phi (Eq. DSA_fp), with each
-    interior-penalty operator of Sec. 4.1."""
+    interior-penalty operator of Sec. 3.1."""
     prob = inputs.config2d_fields(6, 1, 4, 99, "inv")
     prob.q[:] = 1.0
     prob.sigma_t[prob.sigma_t == 0] = 0.5
@@ -236,7 +236,7 @@ def test_triangular_dsa_fixed_point_and_acceleration():
 @pytest.mark.parametrize("prob_fn", [inputs.config1, lambda: inputs.config2(n=16, block=4, p=1, sn=4),
                                      lambda: inputs.config2d_fields(8, 1, 4, 98, "tri")])
 def test_thick_dsa_beats_full_dsa_with_scattering_free_thin_regions(prob_fn):
-    """Sec. 3.3: with Sigma_s = 0 outside the thick region S is block upper triangular, so DSA on the
+    """Sec. 2.3: with Sigma_s = 0 outside the thick region S is block upper triangular, so DSA on the
     thick block alone is the right preconditioner; the paper's tables show heterogeneous DSA needing
     no more iterations than full DSA.  Thin regions keep sigma_t > 0 so that full DSA is defined."""
     prob = prob_fn()
@@ -273,7 +273,7 @@ def test_dsa_operator_consistency_q2(operator):
     """u = x(1-x)y(1-y) in Q2: a(u,v) = (f,v) + 1/2 <D du/dn, v>_boundary exactly (consistency of
     the interior-penalty forms in the interior; the half-flux boundary term of the zero-exterior
     reading on the boundary).  u is continuous and zero on the boundary, so the penalty and the
-    symmetrising term vanish and the three operators of Sec. 4.1 share this identity."""
+    symmetrising term vanish and the three operators of Sec. 3.1 share this identity."""
     n, st, ss = 4, 2.0, 1.5
     prob = inputs.uniform_problem(2, n, 2, 4, st, ss, 0.0)
     T = Transport(prob)

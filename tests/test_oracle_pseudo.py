@@ -1,4 +1,4 @@
-"""Pins of the oracle's pseudo-scattering coefficients (Sec. 5.2, Eq. hohlraum_sigma and
+"""Pins of the oracle's pseudo-scattering coefficients (Sec. 4.2, Eq. hohlraum_sigma and
 Eq. hohlraum_q) and checks of the hohlraum-like input layout.
 
 The coefficients are the linearisation of one implicit time step of gray radiative transfer, so
@@ -43,7 +43,7 @@ def test_long_and_short_time_step_limits(sigma, cv, T):
 
 
 def test_scattering_ratio_grows_with_time_step_and_opacity():
-    """Sec. 5.2: iterations slow down when the time step or sigma is large, i.e. c = sigma_ps / sigma
+    """Sec. 4.2: iterations slow down when the time step or sigma is large, i.e. c = sigma_ps / sigma
     grows with both; it stays in [0, 1) and the source stays non-negative."""
     dts = np.logspace(-6, 3, 10)
     sig = np.logspace(-3, 3, 7)

@@ -492,16 +492,51 @@ __global__ void __launch_bounds__(128) factor_kernel(SweepArgs a, R* out, double
 __device__ double g_fcoef[FAM_COUNT][32][6];
 __device__ float g_fcoef32[FAM_COUNT][32][6];
 
+// The same coefficient times the weight l_other(k) with which the neighbour's value at its k-th
+// node along the face normal enters the face trace: a face term is then -F sum_k fw_k psi_k.
+__device__ __align__(16) double g_fw[FAM_COUNT][32][6][4];
+__device__ __align__(16) float g_fw32[FAM_COUNT][32][6][4];
+
 template <typename R>
 __device__ __forceinline__ R fcoef(int fam, int r, int f);
 template <>
 __device__ __forceinline__ double fcoef<double>(int fam, int r, int f) { return __ldg(&g_fcoef[fam][r][f]); }
 template <>
 __device__ __forceinline__ float fcoef<float>(int fam, int r, int f) { return __ldg(&g_fcoef32[fam][r][f]); }
+// The Q weights of (r, f) in 16-byte loads.
+template <int Q>
+__device__ __forceinline__ void fweights(int fam, int r, int f, double* w) {
+    const double2* p = reinterpret_cast<const double2*>(&g_fw[fam][r][f][0]);
+#pragma unroll
+    for (int h = 0; h < (Q + 1) / 2; ++h) {
+        const double2 v = __ldg(p + h);
+        w[2 * h] = v.x;
+        if (2 * h + 1 < Q) w[2 * h + 1] = v.y;
+    }
+}
+template <int Q>
+__device__ __forceinline__ void fweights(int fam, int r, int f, float* w) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(&g_fw32[fam][r][f][0]));
+    const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < Q; ++k) w[k] = vv[k];
+}
+
+// Whether a face with flux factor F = Omega.n |face| is an inflow face (adjoint: an outflow face),
+// i.e. F < 0 (F > 0), decided on the bits so that no float64 compare is issued; zeros and NaN are
+// on neither side, as with the floating-point compare.
+template <bool ADJ>
+__device__ __forceinline__ bool upwind_face(double F) {
+    const long long b = __double_as_longlong(F);
+    const long long m = b & 0x7fffffffffffffffll;
+    return (ADJ ? b > 0 : b < 0) && m != 0 && m <= 0x7ff0000000000000ll;
+}
 
 cudaError_t upload_face_coefficients() {
     static double c[FAM_COUNT][32][6];
     static float c32[FAM_COUNT][32][6];
+    static double w[FAM_COUNT][32][6][4];
+    static float w32[FAM_COUNT][32][6][4];
     for (int fam = 0; fam < FAM_COUNT; ++fam) {
         const int dim = fam == FAM_3D_P1 ? 3 : 2, p = fam == FAM_3D_P1 ? 1 : fam + 1, Q = p + 1;
         const int n = dim == 2 ? Q * Q : Q * Q * Q;
@@ -520,11 +555,19 @@ cudaError_t upload_face_coefficients() {
                 }
                 c[fam][r][f] = v;
                 c32[fam][r][f] = (float)v;
+                // the neighbour's side of the face: its high end for our low face and vice versa
+                for (int k = 0; k < 4; ++k) {
+                    const double l = k < Q ? ((f & 1) ? g.lm[k] : g.lp[k]) : 0.0;
+                    w[fam][r][f][k] = v * l;
+                    w32[fam][r][f][k] = (float)(v * l);
+                }
             }
     }
     cudaError_t err = cudaMemcpyToSymbol(g_fcoef, c, sizeof(c));
-    if (err != cudaSuccess) return err;
-    return cudaMemcpyToSymbol(g_fcoef32, c32, sizeof(c32));
+    if (err == cudaSuccess) err = cudaMemcpyToSymbol(g_fcoef32, c32, sizeof(c32));
+    if (err == cudaSuccess) err = cudaMemcpyToSymbol(g_fw, w, sizeof(w));
+    if (err == cudaSuccess) err = cudaMemcpyToSymbol(g_fw32, w32, sizeof(w32));
+    return err;
 }
 
 // Cached transport update with one lane per node: a warp holds 32 / N items, lane r of an item
@@ -590,28 +633,26 @@ template <int DIM, int P, typename R, bool ADJ>
 __device__ __forceinline__ R node_faces(const SweepArgs& a, const double* F, int d, int e, int r, R rhs) {
     constexpr int Q = P + 1, N = Shape<DIM, P>::N;
     constexpr int FAM = DIM == 3 ? FAM_3D_P1 : P - 1;
-    using K = GLT<R>;
     const int ri[3] = {r % Q, (r / Q) % Q, r / (Q * Q)};
     const R* psi = static_cast<const R*>(a.psi);
 #pragma unroll
     for (int f = 0; f < 2 * DIM; ++f) {
-        if (ADJ ? !(F[f] > 0.0) : !(F[f] < 0.0)) continue;
+        if (!upwind_face<ADJ>(F[f])) continue;
         const int ax = f >> 1;
-        const bool hi = f & 1;
         const int u = neighbor<DIM, P>(a, e, f);
         const int tt = DIM == 2 ? ri[1 - ax] : (ax == 0 ? ri[1] + Q * ri[2] : (ax == 1 ? ri[0] + Q * ri[2] : ri[0] + Q * ri[1]));
-        R tr;
+        const R sF = ADJ ? (R)F[f] : -(R)F[f];
         if (u >= 0) {
             const R* pu = psi + ((size_t)d * a.ne + u) * N;
-            tr = R(0);
+            R w[Q];
+            fweights<Q>(FAM, r, f, w);
+            R t = R(0);
 #pragma unroll
-            for (int k = 0; k < Q; ++k) tr += (hi ? K::lm(P, k) : K::lp(P, k)) * __ldcg(pu + node_of<DIM, P>(ax, k, tt));
-        } else {
-            if (ADJ) continue;
-            tr = (R)a.psi_inc;
+            for (int k = 0; k < Q; ++k) t += w[k] * __ldcg(pu + node_of<DIM, P>(ax, k, tt));
+            rhs += sF * t;
+        } else if (!ADJ) {
+            rhs += (sF * fcoef<R>(FAM, r, f)) * (R)a.psi_inc;
         }
-        const R c = (ADJ ? (R)F[f] : -(R)F[f]) * fcoef<R>(FAM, r, f);
-        rhs += c * tr;
     }
     return rhs;
 }
@@ -654,7 +695,7 @@ __device__ __forceinline__ void node_item(const SweepArgs& a, const double* mu, 
 }
 
 template <int DIM, int P, int MODE, bool ADJ>
-__global__ void __launch_bounds__(128) node_level_kernel(SweepArgs a, const double* mu, long long begin,
+__global__ void __launch_bounds__(128, DIM == 3 ? 10 : 1) node_level_kernel(SweepArgs a, const double* mu, long long begin,
                                                         long long end) {
     constexpr int N = Shape<DIM, P>::N, IPW = 32 / N;
     const int lane = threadIdx.x & 31;
@@ -935,23 +976,22 @@ __device__ __forceinline__ double unset_value(double) { return __longlong_as_dou
 __device__ __forceinline__ float unset_value(float) { return __int_as_float(-1); }
 
 // node_faces with the upwind (adjoint: downwind) values polled (bounded); *ok = false when the
-// deadline passed.
+// deadline passed or, once a wait has gone on for a while, when another warp has set the launch's
+// error word (so a failed launch ends promptly without every item reading the word).
 template <int DIM, int P, typename R, bool ADJ>
 __device__ __forceinline__ R node_faces_polled(const SweepArgs& a, const double* F, int d, int e, int r, R rhs,
-                                               unsigned long long deadline, bool* ok) {
+                                               unsigned long long deadline, const int* error, bool* ok) {
     constexpr int Q = P + 1, N = Shape<DIM, P>::N;
     constexpr int FAM = DIM == 3 ? FAM_3D_P1 : P - 1;
-    using K = GLT<R>;
     const int ri[3] = {r % Q, (r / Q) % Q, r / (Q * Q)};
     const R* psi = static_cast<const R*>(a.psi);
 #pragma unroll
     for (int f = 0; f < 2 * DIM; ++f) {
-        if (ADJ ? !(F[f] > 0.0) : !(F[f] < 0.0)) continue;
+        if (!upwind_face<ADJ>(F[f])) continue;
         const int ax = f >> 1;
-        const bool hi = f & 1;
         const int u = neighbor<DIM, P>(a, e, f);
         const int tt = DIM == 2 ? ri[1 - ax] : (ax == 0 ? ri[1] + Q * ri[2] : (ax == 1 ? ri[0] + Q * ri[2] : ri[0] + Q * ri[1]));
-        R tr;
+        const R sF = ADJ ? (R)F[f] : -(R)F[f];
         if (u >= 0) {
             const R* pu = psi + ((size_t)d * a.ne + u) * N;
             R v[Q];
@@ -965,22 +1005,22 @@ __device__ __forceinline__ R node_faces_polled(const SweepArgs& a, const double*
                 }
                 if (all) break;
                 if (++polls > 64) {
-                    if (globaltimer() > deadline) {
+                    if (globaltimer() > deadline || *(volatile const int*)error) {
                         *ok = false;
                         break;
                     }
                     __nanosleep(32);
                 }
             }
-            tr = R(0);
+            R w[Q];
+            fweights<Q>(FAM, r, f, w);
+            R t = R(0);
 #pragma unroll
-            for (int k = 0; k < Q; ++k) tr += (hi ? K::lm(P, k) : K::lp(P, k)) * v[k];
-        } else {
-            if (ADJ) continue;
-            tr = (R)a.psi_inc;
+            for (int k = 0; k < Q; ++k) t += w[k] * v[k];
+            rhs += sF * t;
+        } else if (!ADJ) {
+            rhs += (sF * fcoef<R>(FAM, r, f)) * (R)a.psi_inc;
         }
-        const R c = (ADJ ? (R)F[f] : -(R)F[f]) * fcoef<R>(FAM, r, f);
-        rhs += c * tr;
     }
     return rhs;
 }
@@ -999,32 +1039,41 @@ __global__ void __launch_bounds__(128) node_datapoll_kernel(SweepArgs a, Dataflo
     const long long n_slices = (f.n_items >> 5) * SLICES;
     const unsigned long long deadline = globaltimer() + f.timeout_ns;
     const bool withhold = f.publish == -1;  // test hook: store the unset pattern, every wait times out
-    unsigned long long mine = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    while (true) {
-        unsigned long long c = 0;
-        int failed = 0;
-        if (lane == 0) {
-            if (f.static_warps > 0) {
-                c = mine;
-                mine += (unsigned long long)f.static_warps;
-            } else {
-                c = atomicAdd(f.next, 1ull);
-            }
-            failed = *(volatile int*)f.error;
-        }
-        c = __shfl_sync(0xffffffffu, c, 0);
-        failed = __shfl_sync(0xffffffffu, failed, 0);
-        if ((long long)c >= n_slices || failed) break;
+    // this lane's item of slice c (padding and lanes past the slice's items: (-1, -1))
+    auto item_of = [&](unsigned long long c) {
         const long long chunk = (long long)c / SLICES;
         const int k = (int)((long long)c - chunk * SLICES) * IPW + slot;
-        int2 it = make_int2(-1, -1);
-        if (slot < IPW && k < 32) it = f.items[(chunk << 5) + k];
+        return (slot < IPW && k < 32 && (long long)c < n_slices) ? f.items[(chunk << 5) + k] : make_int2(-1, -1);
+    };
+    const bool fixed = f.static_warps > 0;
+    unsigned long long mine = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // static assignment: the warp's slices are known in advance, so the next one's items are loaded
+    // while the current one is solved
+    int2 next = fixed ? item_of(mine) : make_int2(-1, -1);
+    while (true) {
+        unsigned long long c = 0;
+        if (fixed) {
+            c = mine;
+            mine += (unsigned long long)f.static_warps;
+        } else {
+            if (lane == 0) c = atomicAdd(f.next, 1ull);
+            c = __shfl_sync(0xffffffffu, c, 0);
+        }
+        if ((long long)c >= n_slices) break;
+        int2 it;
+        if (fixed) {
+            it = next;
+            next = item_of(mine);
+        } else {
+            it = item_of(c);
+        }
         const bool valid = it.x >= 0;
         const int d = valid ? it.x : 0, e = valid ? it.y : 0;
         NodeStage<DIM, P, R> st;
         if (valid) node_stage<DIM, P, MODE, ADJ>(a, mu, d, e, r, st);
         bool ok = true;
-        const R rhs = valid ? node_faces_polled<DIM, P, R, ADJ>(a, st.F, d, e, r, st.rhs, deadline, &ok) : R(0);
+        const R rhs = valid ? node_faces_polled<DIM, P, R, ADJ>(a, st.F, d, e, r, st.rhs, deadline, f.error, &ok)
+                            : R(0);
         if (!__all_sync(0xffffffffu, ok)) {
             if (lane == 0) atomicExch(f.error, 1);
             break;
@@ -1489,11 +1538,11 @@ __global__ void diff_norm_kernel(const double* a, const double* b, double* out, 
 // out[e][i] = sigma_s[e] M_i / (4 pi) * sum_d w_d lam_d[e][i]
 template <int DIM, int P>
 __global__ void adjoint_reduce_kernel(SweepArgs a, const double* lam, const double* w, double* out) {
-    constexpr int Q = P + 1, N = Shape<DIM, P>::N;
+    constexpr int N = Shape<DIM, P>::N;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t M = (size_t)a.ne * N;
     if (idx >= M) return;
-    const int e = (int)(idx / N), i = (int)(idx % N);
+    const int e = (int)(idx / N);
     double s = 0.0;
     for (int d = 0; d < a.nd; ++d) s += w[d] * lam[(size_t)d * M + idx];
     out[idx] = a.sigma_s[e] * a.mass[idx] / kFourPi * s;
@@ -1502,7 +1551,7 @@ __global__ void adjoint_reduce_kernel(SweepArgs a, const double* lam, const doub
 template <int DIM, int P>
 __global__ void gradient_kernel(SweepArgs a, const double* psi, const double* lam, const double* w,
                                 const double* phi, double* gt, double* gs, double* gq) {
-    constexpr int Q = P + 1, N = Shape<DIM, P>::N;
+    constexpr int N = Shape<DIM, P>::N;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= a.ne) return;
     double M[N];
@@ -2362,7 +2411,8 @@ __global__ void __launch_bounds__(128) batch_node_dataflow_kernel(const SweepArg
 // the upwind angular fluxes (reset to the unset pattern before the launch), solve, store.
 template <int DIM, int P, int MODE>
 __device__ __forceinline__ bool batch_node_chunk_polled(const SweepArgs* args, const BatchItem* items, long long chunk,
-                                                        const int* active, unsigned long long deadline) {
+                                                        const int* active, unsigned long long deadline,
+                                                        const int* error) {
     using R = typename std::conditional<MODE == 1, float, double>::type;
     constexpr int N = Shape<DIM, P>::N, IPW = 32 / N, ROUNDS = (32 + IPW - 1) / IPW;
     const int lane = threadIdx.x & 31;
@@ -2379,7 +2429,7 @@ __device__ __forceinline__ bool batch_node_chunk_polled(const SweepArgs* args, c
         NodeStage<DIM, P, R> st;
         if (valid) node_stage<DIM, P, MODE, false>(a, nullptr, d, e, r, st);
         bool ok = true;
-        const R rhs = valid ? node_faces_polled<DIM, P, R, false>(a, st.F, d, e, r, st.rhs, deadline, &ok) : R(0);
+        const R rhs = valid ? node_faces_polled<DIM, P, R, false>(a, st.F, d, e, r, st.rhs, deadline, error, &ok) : R(0);
         if (!__all_sync(0xffffffffu, ok)) return false;
         R x = R(0);
 #pragma unroll
@@ -2405,25 +2455,20 @@ __global__ void __launch_bounds__(128) batch_node_datapoll_kernel(const SweepArg
     unsigned long long mine = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     while (true) {
         unsigned long long c = 0;
-        int failed = 0;
-        if (lane == 0) {
-            if (static_warps > 0) {
-                c = mine;
-                mine += (unsigned long long)static_warps;
-            } else {
-                c = atomicAdd(ctrl, 1ull);
-            }
-            failed = *(volatile int*)error;
+        if (static_warps > 0) {
+            c = mine;
+            mine += (unsigned long long)static_warps;
+        } else {
+            if (lane == 0) c = atomicAdd(ctrl, 1ull);
+            c = __shfl_sync(0xffffffffu, c, 0);
         }
-        c = __shfl_sync(0xffffffffu, c, 0);
-        failed = __shfl_sync(0xffffffffu, failed, 0);
-        if ((long long)c >= n_chunks || failed) break;
+        if ((long long)c >= n_chunks) break;
         bool ok;
         switch (chunk_fam[c]) {  // uniform across the warp
-            case FAM_2D_P1: ok = batch_node_chunk_polled<2, 1, MODE>(args, items, c, active, deadline); break;
-            case FAM_2D_P2: ok = batch_node_chunk_polled<2, 2, MODE>(args, items, c, active, deadline); break;
-            case FAM_2D_P3: ok = batch_node_chunk_polled<2, 3, MODE>(args, items, c, active, deadline); break;
-            default: ok = batch_node_chunk_polled<3, 1, MODE>(args, items, c, active, deadline); break;
+            case FAM_2D_P1: ok = batch_node_chunk_polled<2, 1, MODE>(args, items, c, active, deadline, error); break;
+            case FAM_2D_P2: ok = batch_node_chunk_polled<2, 2, MODE>(args, items, c, active, deadline, error); break;
+            case FAM_2D_P3: ok = batch_node_chunk_polled<2, 3, MODE>(args, items, c, active, deadline, error); break;
+            default: ok = batch_node_chunk_polled<3, 1, MODE>(args, items, c, active, deadline, error); break;
         }
         if (!ok) {
             if (lane == 0) atomicExch(error, 1);

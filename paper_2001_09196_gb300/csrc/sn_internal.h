@@ -56,6 +56,13 @@ struct SweepArgs {
     const double* ainv;             // operator cache: nd x ne inverses A_e^{-1} (float64), or null
     const float* ainv32;            // the same rounded to float32 (FP32 form), or null
     const double* fflux;            // face flux factors beside the cache: 2D nd x ne x 4, 3D nd x 3 (b_x, b_y, b_z)
+    // float32 copies read by the FP32 cached solves (built with the float32 cache): face flux
+    // factors (as fflux), sigma_s and q per element, mass / (4 pi) per node; q32 is null for the
+    // linear part of the update (no fixed source)
+    const float* fflux32;
+    const float* ss32;
+    const float* q32;
+    const float* mass32;
 };
 
 // Entries of one cached inverse: N*N rounded up to a multiple of 4 (16-byte vector loads).  The
@@ -175,6 +182,7 @@ struct sn_mesh {
     double* d_ainv = nullptr;           // cached inverses, float64 (FP64 form and adjoint)
     float* d_ainv32 = nullptr;          // cached inverses, float32 (FP32 form)
     double* d_fflux = nullptr;          // face flux factors read with the cache (see SweepArgs::fflux)
+    float* d_in32 = nullptr;            // float32 inputs of the FP32 cached solves (see SweepArgs::fflux32)
     bool ainv_valid = false, ainv32_valid = false;    // match the current materials
     bool ainv_denied = false, ainv32_denied = false;  // AUTO mode found no room for them
     double* d_src = nullptr;            // ne x n source vector read by the graph-captured level launches

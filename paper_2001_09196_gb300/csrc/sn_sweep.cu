@@ -531,6 +531,12 @@ __device__ __forceinline__ bool upwind_face(double F) {
     const long long m = b & 0x7fffffffffffffffll;
     return (ADJ ? b > 0 : b < 0) && m != 0 && m <= 0x7ff0000000000000ll;
 }
+template <bool ADJ>
+__device__ __forceinline__ bool upwind_face(float F) {
+    const int b = __float_as_int(F);
+    const int m = b & 0x7fffffff;
+    return (ADJ ? b > 0 : b < 0) && m != 0 && m <= 0x7f800000;
+}
 
 cudaError_t upload_face_coefficients() {
     static double c[FAM_COUNT][32][6];
@@ -596,13 +602,30 @@ __device__ __forceinline__ void cached_fluxes(const SweepArgs& a, int d, int e, 
         }
     }
 }
+template <int DIM>
+__device__ __forceinline__ void cached_fluxes(const SweepArgs& a, int d, int e, float* F) {
+    if constexpr (DIM == 2) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(a.fflux32 + ((size_t)d * a.ne + e) * 4));
+        F[0] = v.x;
+        F[1] = v.y;
+        F[2] = v.z;
+        F[3] = v.w;
+    } else {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const float b = __ldg(a.fflux32 + 3 * d + ax);
+            F[2 * ax] = -b;
+            F[2 * ax + 1] = b;
+        }
+    }
+}
 
 // The part of a node's work that reads no angular flux: the face flux factors, the source row
 // (forward: M_r (q + sigma_s phi_r) / (4 pi); adjoint: mu_r) and the N entries of the cached
 // inverse this lane multiplies with (forward: row r of A_e^{-1}; adjoint: column r).
 template <int DIM, int P, typename R>
 struct NodeStage {
-    double F[2 * DIM];
+    R F[2 * DIM];  // face flux factors (float32 in the FP32 form: its upwind test and face terms)
     R rhs;
     R inv[Shape<DIM, P>::N];
 };
@@ -615,6 +638,11 @@ __device__ __forceinline__ void node_stage(const SweepArgs& a, const double* mu,
     cached_fluxes<DIM>(a, d, e, st.F);
     if constexpr (ADJ) {
         st.rhs = (R)mu[(size_t)e * N + r];
+    } else if constexpr (MODE == 1) {
+        // float32 source row from the float32 copies: M_r / (4 pi) (sigma_s phi_r + q)
+        const float ph = a.phi ? (float)a.phi[(size_t)e * N + r] : 0.0f;
+        const float qe = a.q32 ? __ldg(a.q32 + e) : 0.0f;
+        st.rhs = __ldg(a.mass32 + (size_t)e * N + r) * fmaf(__ldg(a.ss32 + e), ph, qe);
     } else {
         const double ss = a.sigma_s[e], qe = a.q[e] * a.q_scale;
         const double S = (qe + (a.phi ? ss * a.phi[(size_t)e * N + r] : 0.0)) * (1.0 / kFourPi);
@@ -630,7 +658,7 @@ __device__ __forceinline__ void node_stage(const SweepArgs& a, const double* mu,
 
 // Inflow (adjoint: outflow) face terms of node r from the neighbours' angular fluxes.
 template <int DIM, int P, typename R, bool ADJ>
-__device__ __forceinline__ R node_faces(const SweepArgs& a, const double* F, int d, int e, int r, R rhs) {
+__device__ __forceinline__ R node_faces(const SweepArgs& a, const R* F, int d, int e, int r, R rhs) {
     constexpr int Q = P + 1, N = Shape<DIM, P>::N;
     constexpr int FAM = DIM == 3 ? FAM_3D_P1 : P - 1;
     const int ri[3] = {r % Q, (r / Q) % Q, r / (Q * Q)};
@@ -641,7 +669,7 @@ __device__ __forceinline__ R node_faces(const SweepArgs& a, const double* F, int
         const int ax = f >> 1;
         const int u = neighbor<DIM, P>(a, e, f);
         const int tt = DIM == 2 ? ri[1 - ax] : (ax == 0 ? ri[1] + Q * ri[2] : (ax == 1 ? ri[0] + Q * ri[2] : ri[0] + Q * ri[1]));
-        const R sF = ADJ ? (R)F[f] : -(R)F[f];
+        const R sF = ADJ ? F[f] : -F[f];
         if (u >= 0) {
             const R* pu = psi + ((size_t)d * a.ne + u) * N;
             R w[Q];
@@ -979,7 +1007,7 @@ __device__ __forceinline__ float unset_value(float) { return __int_as_float(-1);
 // deadline passed or, once a wait has gone on for a while, when another warp has set the launch's
 // error word (so a failed launch ends promptly without every item reading the word).
 template <int DIM, int P, typename R, bool ADJ>
-__device__ __forceinline__ R node_faces_polled(const SweepArgs& a, const double* F, int d, int e, int r, R rhs,
+__device__ __forceinline__ R node_faces_polled(const SweepArgs& a, const R* F, int d, int e, int r, R rhs,
                                                unsigned long long deadline, const int* error, bool* ok) {
     constexpr int Q = P + 1, N = Shape<DIM, P>::N;
     constexpr int FAM = DIM == 3 ? FAM_3D_P1 : P - 1;
@@ -991,7 +1019,7 @@ __device__ __forceinline__ R node_faces_polled(const SweepArgs& a, const double*
         const int ax = f >> 1;
         const int u = neighbor<DIM, P>(a, e, f);
         const int tt = DIM == 2 ? ri[1 - ax] : (ax == 0 ? ri[1] + Q * ri[2] : (ax == 1 ? ri[0] + Q * ri[2] : ri[0] + Q * ri[1]));
-        const R sF = ADJ ? (R)F[f] : -(R)F[f];
+        const R sF = ADJ ? F[f] : -F[f];
         if (u >= 0) {
             const R* pu = psi + ((size_t)d * a.ne + u) * N;
             R v[Q];
@@ -1090,15 +1118,15 @@ __global__ void __launch_bounds__(128) node_datapoll_kernel(SweepArgs a, Dataflo
 
 // As wait_neighbours with the face fluxes already loaded, every pending word polled in each round
 // (their loads in flight together) rather than one face after another.
-template <int DIM, int P, bool ADJ>
-__device__ __forceinline__ bool wait_neighbours_all(const SweepArgs& a, const double* F, const int* done, int epoch,
+template <int DIM, int P, bool ADJ, typename T>
+__device__ __forceinline__ bool wait_neighbours_all(const SweepArgs& a, const T* F, const int* done, int epoch,
                                                     int d, int e, unsigned long long deadline) {
     const int* flag[2 * DIM];
     int pending = 0;
 #pragma unroll
     for (int fc = 0; fc < 2 * DIM; ++fc) {
         flag[fc] = nullptr;
-        if (ADJ ? F[fc] > 0.0 : F[fc] < 0.0) {
+        if (upwind_face<ADJ>(F[fc])) {
             const int u = neighbor<DIM, P>(a, e, fc);
             if (u >= 0) {
                 flag[fc] = done + (size_t)d * a.ne + u;
@@ -1604,7 +1632,21 @@ static SweepArgs make_args(const sn_mesh* m) {
     a.ainv = m->cache_mode != SN_CACHE_OFF ? m->d_ainv : nullptr;
     a.ainv32 = m->cache_mode != SN_CACHE_OFF ? m->d_ainv32 : nullptr;
     a.fflux = m->d_fflux;
+    if (m->d_in32 && m->cache_mode != SN_CACHE_OFF) {  // layout: fflux32, ss32 (ne), q32 (ne), mass32 (ne n)
+        const size_t nf = m->dim == 2 ? (size_t)m->nd * m->ne * 4 : (size_t)m->nd * 3;
+        a.fflux32 = m->d_in32;
+        a.ss32 = m->d_in32 + nf;
+        a.q32 = a.ss32 + m->ne;
+        a.mass32 = a.q32 + m->ne;
+    }
     return a;
+}
+
+// The linear part of the update: no fixed source and vacuum inflow.
+static void linear_part(SweepArgs& a) {
+    a.q_scale = 0.0;
+    a.psi_inc = 0.0;
+    a.q32 = nullptr;
 }
 
 #define SN_DISPATCH(DIMV, PV, CALL)                                             \
@@ -2001,8 +2043,7 @@ static cudaError_t enqueue_levels(sn_mesh* m, int kind, cudaStream_t s) {
         a.psi = m->d_lambda;
     } else {
         if (kind >= 4) {  // the linear part: no fixed source and vacuum inflow
-            a.q_scale = 0.0;
-            a.psi_inc = 0.0;
+            linear_part(a);
             kind -= 4;
         }
         a.phi = m->d_src;
@@ -2093,6 +2134,20 @@ cudaError_t prepare_recorded_sweep(sn_mesh* m, int precision, cudaStream_t s) {
     return err;
 }
 
+// Float32 copies of the inputs of the FP32 cached solves (layout of SweepArgs::fflux32 .. mass32):
+// face flux factors, sigma_s and q per element, mass / (4 pi) per node.
+__global__ void fp32_inputs_kernel(const double* fflux, long long nf, const double* ss, const double* q,
+                                   const double* mass, int ne, int n, float* out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nf + 2ll * ne + (long long)ne * n) return;
+    double v;
+    if (t < nf) v = fflux[t];
+    else if (t < nf + ne) v = ss[t - nf];
+    else if (t < nf + 2ll * ne) v = q[t - nf - ne];
+    else v = mass[t - nf - 2ll * ne] * (1.0 / kFourPi);
+    out[t] = (float)v;
+}
+
 cudaError_t prepare_operator_cache(sn_mesh* m, int precision, cudaStream_t s) {
     if (m->cache_mode == SN_CACHE_OFF || precision == SN_FP32_REFINE) return cudaSuccess;
     const bool f32 = precision == SN_FP32;
@@ -2140,6 +2195,21 @@ cudaError_t prepare_operator_cache(sn_mesh* m, int precision, cudaStream_t s) {
         else
             SN_DISPATCH(m->dim, m->p, (factor_kernel<D_, P_, double><<<grid_for(total, 128), 128, 0, s>>>(a, m->d_ainv, m->d_fflux)));
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        if (f32) {  // the float32 inputs of the FP32 solves, from the same materials
+            const long long nf = m->dim == 2 ? total * 4 : (long long)m->nd * 3;
+            const long long n32 = nf + 2ll * m->ne + (long long)m->ne * m->n;
+            if (!m->d_in32) {
+                if ((err = cudaMalloc(&m->d_in32, n32 * sizeof(float))) != cudaSuccess) {
+                    m->d_in32 = nullptr;
+                    return err;
+                }
+                drop_level_graphs(m);  // captured launches carry the argument pointers
+            }
+            SN_COUNT_LAUNCH();
+            fp32_inputs_kernel<<<grid_for(n32, 256), 256, 0, s>>>(m->d_fflux, nf, m->d_sigma_s, m->d_q, m->d_mass, m->ne,
+                                                                  m->n, m->d_in32);
+            if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        }
         valid = true;
     }
     return cudaSuccess;
@@ -2149,9 +2219,11 @@ void free_operator_cache(sn_mesh* m) {
     if (m->d_ainv) cudaFree(m->d_ainv);
     if (m->d_ainv32) cudaFree(m->d_ainv32);
     if (m->d_fflux) cudaFree(m->d_fflux);
+    if (m->d_in32) cudaFree(m->d_in32);
     m->d_ainv = nullptr;
     m->d_ainv32 = nullptr;
     m->d_fflux = nullptr;
+    m->d_in32 = nullptr;
     m->ainv_valid = m->ainv32_valid = false;
 }
 
@@ -2166,10 +2238,16 @@ cudaError_t batch_refresh_cache(sn_batch* b, int precision, cudaStream_t s) {
         if (err != cudaSuccess) return err;
         const SweepArgs fresh = make_args(m);
         all = all && (precision == SN_FP32 ? fresh.ainv32 != nullptr : fresh.ainv != nullptr);
-        if (fresh.ainv != b->h_args[i].ainv || fresh.ainv32 != b->h_args[i].ainv32 || fresh.fflux != b->h_args[i].fflux) {
-            b->h_args[i].ainv = fresh.ainv;
-            b->h_args[i].ainv32 = fresh.ainv32;
-            b->h_args[i].fflux = fresh.fflux;
+        SweepArgs& h = b->h_args[i];
+        if (fresh.ainv != h.ainv || fresh.ainv32 != h.ainv32 || fresh.fflux != h.fflux || fresh.fflux32 != h.fflux32 ||
+            fresh.ss32 != h.ss32 || fresh.q32 != h.q32 || fresh.mass32 != h.mass32) {
+            h.ainv = fresh.ainv;
+            h.ainv32 = fresh.ainv32;
+            h.fflux = fresh.fflux;
+            h.fflux32 = fresh.fflux32;
+            h.ss32 = fresh.ss32;
+            h.q32 = fresh.q32;
+            h.mass32 = fresh.mass32;
             changed = true;
         }
     }
@@ -2190,8 +2268,8 @@ cudaError_t launch_sweep(sn_mesh* m, const double* phi_in, int precision, double
     if (cerr != cudaSuccess) return cerr;
     SweepArgs a = make_args(m);
     a.phi = phi_in;
-    a.q_scale = q_scale;
-    if (q_scale == 0.0) a.psi_inc = 0.0;  // the linear part of the update has vacuum inflow
+    if (q_scale != 0.0 && q_scale != 1.0) return cudaErrorInvalidValue;  // the source is on or off
+    if (q_scale == 0.0) linear_part(a);
     a.psi = precision == SN_FP32 ? m->d_psi32 : m->d_psi;
     const bool cached = precision == SN_FP64 ? a.ainv != nullptr : (precision == SN_FP32 && a.ainv32 != nullptr);
     if (m->schedule == SCHED_BARRIER && cached) {  // uncached solves fall back to the level schedule
@@ -2243,8 +2321,8 @@ cudaError_t launch_sweep_range(sn_mesh* m, const double* phi_in, int precision, 
     }
     SweepArgs a = make_args(m);
     a.phi = phi_in;
-    a.q_scale = q_scale;
-    if (q_scale == 0.0) a.psi_inc = 0.0;  // the linear part of the update has vacuum inflow
+    if (q_scale != 0.0 && q_scale != 1.0) return cudaErrorInvalidValue;  // the source is on or off
+    if (q_scale == 0.0) linear_part(a);
     a.psi = precision == SN_FP32 ? m->d_psi32 : m->d_psi;
     a.items = m->range_items;
     long long launches = 0;

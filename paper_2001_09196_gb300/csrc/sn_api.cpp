@@ -65,7 +65,7 @@ void free_mesh(sn_mesh* m) {
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     if (m->d_src) cudaFree(m->d_src);
     for (void* p : {(void*)m->d_dirs, (void*)m->d_wts, (void*)m->d_corners, (void*)m->d_sigma_t, (void*)m->d_sigma_s,
-                    (void*)m->d_q, m->d_psi, m->d_psi32, (void*)m->d_lambda, (void*)m->d_mass, (void*)m->d_work, (void*)m->d_red,
+                    (void*)m->d_q, m->d_psi, m->d_psi32, (void*)m->d_lambda, (void*)m->d_mass, (void*)m->d_mass4, (void*)m->d_work, (void*)m->d_red,
                     (void*)m->d_scalars, (void*)m->levels.items, (void*)m->levels.padded, (void*)m->levels.padded_rev, (void*)m->levels.done,
                     (void*)m->levels.ctrl, (void*)m->d_krylov, (void*)m->levels.d_level_ptr, (void*)m->levels.d_barrier,
                     (void*)m->range_items})
@@ -201,6 +201,7 @@ sn_status sn_mesh_create(const sn_mesh_desc* desc, sn_mesh** out) {
     CK(dalloc(&m->d_red, m->red_blocks), "alloc");
     CK(dalloc(&m->d_scalars, 16), "alloc");
     CK(dalloc(&m->d_mass, M), "alloc");
+    CK(dalloc(&m->d_mass4, M), "alloc");
     CK(dalloc(&m->d_src, M), "alloc");
     CK(sn::compute_mass(m.get(), 0), "element masses");
     bool cycle = false;

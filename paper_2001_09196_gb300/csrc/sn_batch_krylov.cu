@@ -445,6 +445,7 @@ cudaError_t batch_fgmres(sn_batch* b, const sn_iter_opts* o, cudaStream_t s, std
     for (int i = 0; i < b->count; ++i) {
         hom[i].phi = K->zj + b->dof_off[i];
         hom[i].q_scale = 0.0;
+        hom[i].q = nullptr;
         hom[i].q32 = nullptr;
         hom[i].psi_inc = 0.0;  // the linear part of the update has vacuum inflow
     }

@@ -50,9 +50,10 @@ struct SweepArgs {
     const double* q;
     const double* phi;              // scattering source (nodal), may be null (= 0)
     const double* mass;             // ne x n collocated masses W_i det J(x_i)
+    const double* mass4;            // the same divided by 4 pi (the scale of a source row)
     void* psi;                      // nd x ne x n, float64 or float32
     const int2* items;              // (dir, elem) sorted by level
-    double q_scale;                 // multiplies q (1 normally, 0 for homogeneous solves)
+    double q_scale;                 // 1 normally, 0 for homogeneous solves (q and q32 are then null)
     const double* ainv;             // operator cache: nd x ne inverses A_e^{-1} (float64), or null
     const float* ainv32;            // the same rounded to float32 (FP32 form), or null
     const double* fflux;            // face flux factors beside the cache: 2D nd x ne x 4, 3D nd x 3 (b_x, b_y, b_z)
@@ -164,6 +165,7 @@ struct sn_mesh {
     void* d_psi32 = nullptr;        // float32 angular fluxes of the FP32 form
     double* d_lambda = nullptr;     // adjoint angular fluxes
     double* d_mass = nullptr;       // ne x n collocated masses
+    double* d_mass4 = nullptr;      // the same divided by 4 pi
     double* d_work = nullptr;       // 4 x ne x n scratch vectors for iterations
     double* d_red = nullptr;        // reduction partials
     int red_blocks = 0;

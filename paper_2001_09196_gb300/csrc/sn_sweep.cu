@@ -206,7 +206,7 @@ __device__ __forceinline__ void narrow_geom(const ElemGeom<DIM, P, double>& gd, 
 
 // Collocated masses W_i det J(x_i) of every element (float64, once per mesh).
 template <int DIM, int P>
-__global__ void mass_kernel(SweepArgs a, double* mass) {
+__global__ void mass_kernel(SweepArgs a, double* mass, double* mass4) {
     constexpr int Q = P + 1, N = Shape<DIM, P>::N;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)a.ne * N) return;
@@ -230,6 +230,7 @@ __global__ void mass_kernel(SweepArgs a, double* mass) {
         dj = 0.125 * a.hx * a.hy * a.hz;
     }
     mass[idx] = W * dj;
+    mass4[idx] = W * dj * (1.0 / kFourPi);  // the source row's scale, M_i / (4 pi)
 }
 
 template <int DIM, int P>
@@ -644,9 +645,10 @@ __device__ __forceinline__ void node_stage(const SweepArgs& a, const double* mu,
         const float qe = a.q32 ? __ldg(a.q32 + e) : 0.0f;
         st.rhs = __ldg(a.mass32 + (size_t)e * N + r) * fmaf(__ldg(a.ss32 + e), ph, qe);
     } else {
-        const double ss = a.sigma_s[e], qe = a.q[e] * a.q_scale;
-        const double S = (qe + (a.phi ? ss * a.phi[(size_t)e * N + r] : 0.0)) * (1.0 / kFourPi);
-        st.rhs = (R)a.mass[(size_t)e * N + r] * (R)S;
+        // M_r / (4 pi) (sigma_s phi_r + q), q absent (null) in the linear part of the update
+        const double qe = a.q ? a.q[e] : 0.0;
+        const double S = a.phi ? fma(a.sigma_s[e], a.phi[(size_t)e * N + r], qe) : qe;
+        st.rhs = (R)(a.mass4[(size_t)e * N + r] * S);
     }
     const R* inv;
     if constexpr (MODE == 1) inv = a.ainv32;
@@ -746,7 +748,7 @@ template <int DIM, int P, typename RS, typename R>
 __device__ __forceinline__ void assemble_rhs(const SweepArgs& a, const ElemGeom<DIM, P, R>& g, int d, int e, R* rhs) {
     constexpr int Q = P + 1, N = Shape<DIM, P>::N, NT = Shape<DIM, P>::NT;
     using K = GLT<R>;
-    const double ss = a.sigma_s[e], qe = a.q[e] * a.q_scale;
+    const double ss = a.sigma_s[e], qe = a.q ? a.q[e] : 0.0;
     const double* phi = a.phi ? a.phi + (size_t)e * N : nullptr;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -1628,6 +1630,7 @@ static SweepArgs make_args(const sn_mesh* m) {
     a.q = m->d_q;
     a.items = m->levels.items;
     a.mass = m->d_mass;
+    a.mass4 = m->d_mass4;
     a.q_scale = 1.0;
     a.ainv = m->cache_mode != SN_CACHE_OFF ? m->d_ainv : nullptr;
     a.ainv32 = m->cache_mode != SN_CACHE_OFF ? m->d_ainv32 : nullptr;
@@ -1646,6 +1649,7 @@ static SweepArgs make_args(const sn_mesh* m) {
 static void linear_part(SweepArgs& a) {
     a.q_scale = 0.0;
     a.psi_inc = 0.0;
+    a.q = nullptr;
     a.q32 = nullptr;
 }
 
@@ -1671,7 +1675,7 @@ cudaError_t compute_mass(sn_mesh* m, cudaStream_t s) {
     SweepArgs a = make_args(m);
     const long long M = (long long)m->ne * m->n;
     SN_COUNT_LAUNCH();
-    SN_DISPATCH(m->dim, m->p, (mass_kernel<D_, P_><<<grid_for(M, 256), 256, 0, s>>>(a, m->d_mass)));
+    SN_DISPATCH(m->dim, m->p, (mass_kernel<D_, P_><<<grid_for(M, 256), 256, 0, s>>>(a, m->d_mass, m->d_mass4)));
     return cudaGetLastError();
 }
 

@@ -197,3 +197,22 @@ def test_batched_fgmres_rejects_mixed_precision(sn):
     meshes = [sn.Mesh.from_problem(p) for p in small_instances()[:2]]
     with pytest.raises(sn.SnError):
         sn.Batch(meshes).source_iterate(dsa="thick", thick_rule="sigma_t_h", outer="fgmres", precision="fp32_mixed")
+
+
+def test_batched_fgmres_budget_and_warm_start(sn):
+    """An iteration budget below what the instances need ends the solve with SN_ERR_NOT_CONVERGED
+    after exactly that many Arnoldi steps per instance; a warm start from the unconverged iterates
+    continues to the same solution as a cold start (within the tolerance)."""
+    probs = weakly_scattering_instances()[:3]
+    meshes = [sn.Mesh.from_problem(p) for p in probs]
+    batch = sn.Batch(meshes)
+    opts = dict(dsa="thick", thick_rule="sigma_t_h", outer="fgmres", restart=4, inner_tol=1e-10, inner_max_iters=500)
+    res = batch.source_iterate(tol=1e-14, max_iters=6, **opts)
+    assert not res["converged"]
+    assert res["iters"] == [6] * len(probs)
+    warm = batch.source_iterate(phis=[p.clone() for p in res["phi"]], warm_start=True, tol=1e-10, max_iters=400,
+                                **opts)
+    cold = batch.source_iterate(tol=1e-12, max_iters=400, **opts)
+    assert warm["converged"] and cold["converged"]
+    for a, b in zip(warm["phi"], cold["phi"]):
+        assert float((a - b).abs().max() / b.abs().max()) < 1e-8

@@ -340,6 +340,29 @@ sn_status sn_gradients(sn_mesh* mesh, const double* phi, const double* mu, doubl
                        double* d_sigma_s, double* d_q, void* stream);
 
 /*
+ * sn_unrolled_gradients: gradients of J = g^T phi_K with respect to sigma_t, sigma_s and q, where
+ * phi_K is the K-th iterate of source iteration without acceleration from phi_0, phi_{k+1} =
+ * T phi_k + b (one transport update, sn_sweep; Eq. source0), i.e. the derivative of the map that a
+ * fixed number of updates computes, not of the converged solution.  Reverse accumulation through
+ * the K updates: mu_K = g; for k = K-1 .. 0 the update at (phi_k, mu_{k+1}) contributes the
+ * sn_gradients contractions (one forward sweep from phi_k, one adjoint sweep of mu_{k+1}), and
+ * mu_k = T^T mu_{k+1} (sn_adjoint_sweep's reduction of the same adjoint sweep).
+ * Iterate checkpointing: the phi_k are needed in reverse order; they are recomputed segment by
+ * segment from every `checkpoint_every`-th iterate.  checkpoints: NULL (this call runs the K - 1
+ * forward updates first and keeps its own), or the buffer that sn_source_iterate filled with
+ * dsa = SN_DSA_NONE, max_iters = K, checkpoint_every = the same value (iterates checkpoint_every,
+ * 2 checkpoint_every, ...; at least ceil(K / checkpoint_every) - 1 of them).  phi0: device, or NULL
+ * for phi_0 = 0 (sn_source_iterate's cold start).  g: device [elem][node].  Outputs n_elem doubles
+ * each (NULL to skip), overwritten.  Memory: (ceil(K / checkpoint_every) + checkpoint_every + 5)
+ * vectors of n_elem x n_nodes doubles, allocated for the call.  Cost: about 3K forward and K adjoint
+ * sweeps (K - 1 + K - ceil(K / every) recomputing and K in the backward pass).  FP64.
+ * Errors: SN_ERR_ARG for K < 1 or checkpoint_every < 1; SN_ERR_TIMEOUT as sn_sweep.
+ */
+sn_status sn_unrolled_gradients(sn_mesh* mesh, const double* phi0, int K, int checkpoint_every,
+                                const double* checkpoints, const double* g, double* d_sigma_t, double* d_sigma_s,
+                                double* d_q, void* stream);
+
+/*
  * Diagnostics of the DSA operator (Sec. 3): y = D_ff x on the elements selected by opts
  * (x, y device, [elem][node]; entries outside the thick set are ignored / set to 0), and the
  * PCG + V-cycle solve of D_ff x = b to opts->inner_tol.  *iters receives the PCG count.

@@ -109,3 +109,27 @@ def gradients(T, phi_nodal, mu_modal):
         gs += np.einsum("em,em->e", lam, Mphi) / FOUR_PI
         gq += np.einsum("em,em->e", lam, M1) / FOUR_PI
     return gt, gs, gq
+
+
+def unrolled_gradients(T, phi0_nodal, K, g_modal):
+    """dJ/dsigma_t, dJ/dsigma_s, dJ/dq of J = g^T phi_K, phi_K the K-th iterate of source iteration
+    without acceleration from phi_0 (phi_{k+1} = T phi_k + b, Eq. source0): the chain rule through
+    the K updates, taken backwards.  Update k maps phi_k to phi_{k+1} with the data p entering as in
+    the converged case, so with mu_K = g and mu_k = T^T mu_{k+1},
+        dJ/dp = sum_{k=0}^{K-1} mu_{k+1}^T (d b/dp + dT/dp phi_k),
+    each term the contraction `gradients` forms at (phi_k, mu_{k+1}).  Every iterate is kept."""
+    phis = [np.asarray(phi0_nodal, dtype=float)]
+    for _ in range(K - 1):
+        phis.append(T.sweep(phis[-1]))
+    mu = np.array(g_modal, dtype=float)
+    gt = np.zeros(T.ne)
+    gs = np.zeros(T.ne)
+    gq = np.zeros(T.ne)
+    for k in range(K - 1, -1, -1):
+        a, b, c = gradients(T, phis[k], mu)
+        gt += a
+        gs += b
+        gq += c
+        if k > 0:
+            mu = adjoint_sweep_modal(T, mu)
+    return gt, gs, gq

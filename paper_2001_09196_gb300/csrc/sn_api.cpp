@@ -1302,6 +1302,89 @@ sn_status sn_gradients(sn_mesh* m, const double* phi, const double* mu, double* 
     return SN_OK;
 }
 
+// Reverse accumulation through K unaccelerated transport updates phi_{k+1} = T phi_k + b (see sn.h).
+sn_status sn_unrolled_gradients(sn_mesh* m, const double* phi0, int K, int every, const double* checkpoints,
+                                const double* g, double* gt, double* gs, double* gq, void* stream) {
+    if (!m || !g) return fail(SN_ERR_ARG, "null argument");
+    if (K < 1) return fail(SN_ERR_ARG, "K must be >= 1");
+    if (every < 1) return fail(SN_ERR_ARG, "checkpoint_every must be >= 1");
+    sn_status st = ensure_lambda(m);
+    if (st != SN_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t M = (size_t)m->ne * m->n, ne = (size_t)m->ne;
+    const int nseg = (K + every - 1) / every;  // segment j starts at iterate j * every
+    // workspace: phi_0 (when none is given), own checkpoints (when none are given), one segment of
+    // iterates, two scratch vectors, two adjoint vectors, one step's gradients
+    const size_t n_own = checkpoints ? 0 : (size_t)nseg * M;
+    const size_t need = M + n_own + (size_t)every * M + 4 * M + 3 * ne;
+    double* work = nullptr;
+    CK(cudaMalloc(&work, need * sizeof(double)), "alloc unrolled-gradient workspace");
+    std::unique_ptr<double, decltype(&cudaFree)> hold(work, &cudaFree);
+    double* zero = work;
+    double* own = zero + M;
+    double* seg = own + n_own;
+    double* scr = seg + (size_t)every * M;
+    double* mu = scr + 2 * M;
+    double* tg = mu + 2 * M;
+    if (!phi0) {
+        CK(cudaMemsetAsync(zero, 0, M * sizeof(double), s), "memset");
+        phi0 = zero;
+    }
+    // iterate j * every: phi_0, then the caller's checkpoints (source iteration's, which hold
+    // iterates every, 2 every, ...) or this call's own
+    auto start = [&](int j) -> const double* {
+        if (j == 0) return phi0;
+        return checkpoints ? checkpoints + (size_t)(j - 1) * M : own + (size_t)j * M;
+    };
+    auto update = [&](const double* in, double* out) -> sn_status {  // out = T in + b
+        CK(sn::launch_sweep(m, in, SN_FP64, 1.0, s), "sweep");
+        CK(sn::launch_phi_reduce(m, SN_FP64, nullptr, out, nullptr, s), "phi reduce");
+        return SN_OK;
+    };
+    if (!checkpoints) {  // forward pass keeping every `every`-th iterate below K
+        const double* cur = phi0;
+        for (int k = 0; k + 1 < K; ++k) {
+            double* out = (k + 1) % every == 0 ? own + (size_t)((k + 1) / every) * M : scr + (size_t)(k % 2) * M;
+            if ((st = update(cur, out)) != SN_OK) return st;
+            cur = out;
+        }
+    }
+    for (double* o : {gt, gs, gq})
+        if (o) CK(cudaMemsetAsync(o, 0, ne * sizeof(double), s), "memset");
+    double* mu_cur = mu;
+    double* mu_next = mu + M;
+    CK(cudaMemcpyAsync(mu_cur, g, M * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    for (int j = nseg - 1; j >= 0; --j) {
+        const int base = j * every, end = std::min(K, base + every);
+        // the segment's iterates, recomputed from its first
+        CK(cudaMemcpyAsync(seg, start(j), M * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+        for (int i = 1; i < end - base; ++i)
+            if ((st = update(seg + (size_t)(i - 1) * M, seg + (size_t)i * M)) != SN_OK) return st;
+        for (int k = end - 1; k >= base; --k) {
+            const double* phik = seg + (size_t)(k - base) * M;
+            // update k at (phi_k, mu_{k+1}): psi of the update, lambda_d = w_d L_d^{-T} mu_{k+1}
+            CK(sn::launch_sweep(m, phik, SN_FP64, 1.0, s), "sweep");
+            CK(sn::launch_adjoint_sweep(m, mu_cur, s), "adjoint sweep");
+            CK(sn::launch_gradients(m, phik, gt ? tg : nullptr, gs ? tg + ne : nullptr, gq ? tg + 2 * ne : nullptr, s),
+               "gradients");
+            if (gt) CK(sn::launch_axpy_add(gt, tg, ne, s), "accumulate");
+            if (gs) CK(sn::launch_axpy_add(gs, tg + ne, ne, s), "accumulate");
+            if (gq) CK(sn::launch_axpy_add(gq, tg + 2 * ne, ne, s), "accumulate");
+            if (k > 0) {  // mu_k = T^T mu_{k+1}, from the same lambda
+                CK(sn::launch_adjoint_reduce(m, mu_next, s), "adjoint reduce");
+                std::swap(mu_cur, mu_next);
+            }
+        }
+    }
+    CK(cudaStreamSynchronize(s), "sync");
+    if (m->schedule != sn::SCHED_LEVELS) {
+        bool timed_out = false;
+        CK(sn::take_sweep_error(m, s, &timed_out), "sweep status");
+        if (timed_out) return fail(SN_ERR_TIMEOUT, "a sweep dependency wait timed out");
+    }
+    return SN_OK;
+}
+
 sn_status sn_dsa_apply(sn_mesh* m, const sn_iter_opts* o, const double* x, double* y, void* stream) {
     if (!m || !o || !x || !y) return fail(SN_ERR_ARG, "null argument");
     sn_iter_opts oo = *o;

@@ -87,6 +87,7 @@ def _load():
         "sn_adjoint_sweep": [vp, vp, vp, i, vp],
         "sn_adjoint_iterate": [vp, C.POINTER(IterOpts), vp, vp, C.POINTER(IterStats), vp],
         "sn_gradients": [vp, vp, vp, vp, vp, vp, vp],
+        "sn_unrolled_gradients": [vp, vp, i, i, vp, vp, vp, vp, vp, vp],
         "sn_dsa_apply": [vp, C.POINTER(IterOpts), vp, vp, vp],
         "sn_dsa_solve": [vp, C.POINTER(IterOpts), vp, vp, C.POINTER(C.c_int), vp],
         "sn_get_angular_flux": [vp, i, i, i, vp, vp],
@@ -443,6 +444,25 @@ class Mesh:
         import torch
         gt, gs, gq = (torch.empty(self.n_elem, dtype=torch.float64, device=phi.device) for _ in range(3))
         _check(_lib.sn_gradients(self._h, _ptr(phi), _ptr(mu), _ptr(gt), _ptr(gs), _ptr(gq), _stream(stream)))
+        return gt, gs, gq
+
+    def unrolled_gradients(self, g, K, checkpoint_every=1, phi0=None, checkpoints=None, stream=None):
+        """Gradients of g . phi_K for the K-th unaccelerated source iterate (sn_unrolled_gradients):
+        (d_sigma_t, d_sigma_s, d_q).  checkpoints: None, or the buffer source_iterate filled with
+        dsa="none", max_iters=K and the same checkpoint_every."""
+        import torch
+        m = self.n_elem * self.n_nodes
+        if int(K) < 1 or int(checkpoint_every) < 1:
+            raise ValueError("K and checkpoint_every must be >= 1")
+        if g.numel() != m or (phi0 is not None and phi0.numel() != m):
+            raise ValueError(f"g and phi0 need exactly n_elem * n_nodes = {m} values")
+        need = (-(-int(K) // int(checkpoint_every)) - 1) * m
+        if checkpoints is not None and checkpoints.numel() < need:
+            raise ValueError(f"checkpoints need at least {need} values")
+        gt, gs, gq = (torch.empty(self.n_elem, dtype=torch.float64, device=g.device) for _ in range(3))
+        _check(_lib.sn_unrolled_gradients(self._h, None if phi0 is None else _ptr(phi0), int(K), int(checkpoint_every),
+                                          None if checkpoints is None else _ptr(checkpoints), _ptr(g), _ptr(gt),
+                                          _ptr(gs), _ptr(gq), _stream(stream)))
         return gt, gs, gq
 
     def levels(self, d):

@@ -381,26 +381,37 @@ def other_workloads(torch, sn, inputs, stream, flush, time_sweeps):
     del m3, x3, phi3
     # config 5
     p5 = inputs.config5()
-    if True:
-        m5 = sn.Mesh.from_problem(p5)
-        # J = sum over the strip of the integral of phi: g = Gauss weights x (h/2)^2 on strip elements
-        xg, wg = np.polynomial.legendre.leggauss(p5.p + 1)
-        g5h = np.zeros((p5.n_elem, p5.n_nodes))
-        g5h[p5.extra["detector"].astype(bool)] = np.outer(wg, wg).ravel() * (0.5 / p5.nx) ** 2
-        g5 = torch.as_tensor(g5h, device="cuda")
+    m5 = sn.Mesh.from_problem(p5)
+    # J = sum over the strip of the integral of phi: g = Gauss weights x (h/2)^2 on strip elements
+    xg, wg = np.polynomial.legendre.leggauss(p5.p + 1)
+    g5h = np.zeros((p5.n_elem, p5.n_nodes))
+    g5h[p5.extra["detector"].astype(bool)] = np.outer(wg, wg).ravel() * (0.5 / p5.nx) ** 2
+    g5 = torch.as_tensor(g5h, device="cuda")
 
-        def grad_once():
-            st, ss, q = (torch.tensor(a, dtype=torch.float64, device="cuda", requires_grad=True)
-                         for a in (p5.sigma_t, p5.sigma_s, p5.q))
-            phi = autograd.solve(m5, st, ss, q, solve_opts=dict(thick_rule="sigma_t_h", tol=1e-8),
-                                 adjoint_opts=dict(tol=1e-8))
-            (g5 * phi).sum().backward()
-            return st.grad
-        grad_once()
-        ms5, _ = timed(grad_once)
-        out["c5"] = {"workload": "128x128 Q1 S8, config-3-style fields, detector = right-edge 16x4 strip; forward "
-                                 "fGMRES + adjoint fGMRES (thick DSA, 1e-8) + gradients w.r.t. sigma_t, sigma_s, q",
-                     "ms_gradient": ms5}
+    def grad_once():
+        st, ss, q = (torch.tensor(a, dtype=torch.float64, device="cuda", requires_grad=True)
+                     for a in (p5.sigma_t, p5.sigma_s, p5.q))
+        phi = autograd.solve(m5, st, ss, q, solve_opts=dict(thick_rule="sigma_t_h", tol=1e-8),
+                             adjoint_opts=dict(tol=1e-8))
+        (g5 * phi).sum().backward()
+        return st.grad
+    grad_once()
+    ms5, _ = timed(grad_once)
+
+    def grad_unrolled():
+        st, ss, q = (torch.tensor(a, dtype=torch.float64, device="cuda", requires_grad=True)
+                     for a in (p5.sigma_t, p5.sigma_s, p5.q))
+        phi = autograd.unrolled(m5, st, ss, q, 20, checkpoint_every=5)
+        (g5 * phi).sum().backward()
+        return st.grad
+    grad_unrolled()
+    ms5u, _ = timed(grad_unrolled)
+    out["c5"] = {"workload": "128x128 Q1 S8, config-3-style fields, detector = right-edge 16x4 strip; forward "
+                             "fGMRES + adjoint fGMRES (thick DSA, 1e-8) + gradients w.r.t. sigma_t, sigma_s, q",
+                 "ms_gradient": ms5,
+                 "ms_gradient_unrolled": ms5u,
+                 "unrolled": "gradients of J(phi_K), K = 20 unaccelerated updates, checkpoints every 5 "
+                             "(forward 20 sweeps; backward 36 forward and 20 adjoint sweeps)"}
     return out
 
 

@@ -85,7 +85,7 @@ FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per element-direction of the dominant sweep kernel, from an ncu
 # metrics-only capture (dram__bytes_read.sum + dram__bytes_write.sum) of the bench's own launch, per
 # (schedule, workload).  A schedule or kernel changed since its capture has no entry (traffic null).
-SWEEP_DRAM_BYTES_PER_ITEM = {("static", "c2"): (2129141760 + 154312448) / (65536 * 40)}  # node_datapoll_kernel
+SWEEP_DRAM_BYTES_PER_ITEM = {("static", "c2"): (2148698624 + 154070528) / (65536 * 40)}  # node_datapoll_kernel
 
 SCHEDULE_KERNEL = {"levels": "node_level_kernel", "dataflow": "node_datapoll_kernel", "static": "node_datapoll_kernel",
                    "tiles": "tile_sweep_kernel", "barrier": "barrier_sweep_kernel"}

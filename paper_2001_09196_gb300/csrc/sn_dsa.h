@@ -53,7 +53,11 @@ struct DsaHierarchy {
     bool pc32 = false;                        // the recorded solve uses the float32 V-cycle
     bool uploaded32 = false;
     float *d_vr32 = nullptr, *d_r32 = nullptr, *d_z32 = nullptr;
-    double omega0 = 0.6, omega = 0.6;         // damping of block-Jacobi (level 0) / Jacobi (levels >= 1)
+    // damping of block-Jacobi (level 0) / Jacobi (levels >= 1).  Level 0: 0.8 keeps the smoother
+    // convergent with margin for the largest eigenvalue of the block-Jacobi-preconditioned SIP
+    // operator measured on the jittered Q2 configuration (between 2 and 2.2: damping 1.0 made the
+    // PCG diverge, 0.9 converged) and takes fewer PCG iterations than 0.6 (336 against 391 per solve)
+    double omega0 = 0.8, omega = 0.6;
     int nu = 2;                               // pre- and post-smoothing steps
     // The Krylov solve (PCG or BiCGStab) recorded as a CUDA graph whose WHILE conditional node
     // repeats one iteration until the device-side convergence test fails (no host

@@ -58,7 +58,7 @@ struct UnionDsa {
     int* iters = nullptr;        // PCG iterations performed (device counter)
     int* local_iters = nullptr;  // iterations of the current solve (recorded loop)
     cudaStream_t cap2 = nullptr; // captures the loop body while the batched iteration is recorded
-    double omega0 = 0.6, omega = 0.6;
+    double omega0 = 0.8, omega = 0.6;  // as the single-mesh V-cycle (sn_dsa.h)
     int nu = 2;
     std::vector<DsaHierarchy*> parts;  // host hierarchies (kept for their sizes)
 };

@@ -58,10 +58,9 @@ struct SweepArgs {
     const float* ainv32;            // the same rounded to float32 (FP32 form), or null
     const double* fflux;            // face flux factors beside the cache: 2D nd x ne x 4, 3D nd x 3 (b_x, b_y, b_z)
     // float32 copies read by the FP32 cached solves (built with the float32 cache): face flux
-    // factors (as fflux), sigma_s and q per element, mass / (4 pi) per node; q32 is null for the
-    // linear part of the update (no fixed source)
+    // factors (as fflux), q per element, mass / (4 pi) per node; q32 is null for the linear part
+    // of the update (no fixed source)
     const float* fflux32;
-    const float* ss32;
     const float* q32;
     const float* mass32;
 };

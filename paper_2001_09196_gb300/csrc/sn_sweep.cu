@@ -640,10 +640,13 @@ __device__ __forceinline__ void node_stage(const SweepArgs& a, const double* mu,
     if constexpr (ADJ) {
         st.rhs = (R)mu[(size_t)e * N + r];
     } else if constexpr (MODE == 1) {
-        // float32 source row from the float32 copies: M_r / (4 pi) (sigma_s phi_r + q)
-        const float ph = a.phi ? (float)a.phi[(size_t)e * N + r] : 0.0f;
+        // float32 source row M_r / (4 pi) (sigma_s phi_r + q): the scattering product is formed in
+        // float64 and rounded once, because a sigma_s rounded to float32 would be a systematic
+        // change of the absorption sigma_t - sigma_s, which the fixed point amplifies by up to
+        // c / (1 - c)
+        const float sp = a.phi ? (float)(a.sigma_s[e] * a.phi[(size_t)e * N + r]) : 0.0f;
         const float qe = a.q32 ? __ldg(a.q32 + e) : 0.0f;
-        st.rhs = __ldg(a.mass32 + (size_t)e * N + r) * fmaf(__ldg(a.ss32 + e), ph, qe);
+        st.rhs = __ldg(a.mass32 + (size_t)e * N + r) * (sp + qe);
     } else {
         // M_r / (4 pi) (sigma_s phi_r + q), q absent (null) in the linear part of the update
         const double qe = a.q ? a.q[e] : 0.0;
@@ -1635,11 +1638,10 @@ static SweepArgs make_args(const sn_mesh* m) {
     a.ainv = m->cache_mode != SN_CACHE_OFF ? m->d_ainv : nullptr;
     a.ainv32 = m->cache_mode != SN_CACHE_OFF ? m->d_ainv32 : nullptr;
     a.fflux = m->d_fflux;
-    if (m->d_in32 && m->cache_mode != SN_CACHE_OFF) {  // layout: fflux32, ss32 (ne), q32 (ne), mass32 (ne n)
+    if (m->d_in32 && m->cache_mode != SN_CACHE_OFF) {  // layout: fflux32, q32 (ne), mass32 (ne n)
         const size_t nf = m->dim == 2 ? (size_t)m->nd * m->ne * 4 : (size_t)m->nd * 3;
         a.fflux32 = m->d_in32;
-        a.ss32 = m->d_in32 + nf;
-        a.q32 = a.ss32 + m->ne;
+        a.q32 = m->d_in32 + nf;
         a.mass32 = a.q32 + m->ne;
     }
     return a;
@@ -2139,16 +2141,15 @@ cudaError_t prepare_recorded_sweep(sn_mesh* m, int precision, cudaStream_t s) {
 }
 
 // Float32 copies of the inputs of the FP32 cached solves (layout of SweepArgs::fflux32 .. mass32):
-// face flux factors, sigma_s and q per element, mass / (4 pi) per node.
-__global__ void fp32_inputs_kernel(const double* fflux, long long nf, const double* ss, const double* q,
-                                   const double* mass, int ne, int n, float* out) {
+// face flux factors, q per element, mass / (4 pi) per node.
+__global__ void fp32_inputs_kernel(const double* fflux, long long nf, const double* q, const double* mass, int ne,
+                                   int n, float* out) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nf + 2ll * ne + (long long)ne * n) return;
+    if (t >= nf + ne + (long long)ne * n) return;
     double v;
     if (t < nf) v = fflux[t];
-    else if (t < nf + ne) v = ss[t - nf];
-    else if (t < nf + 2ll * ne) v = q[t - nf - ne];
-    else v = mass[t - nf - 2ll * ne] * (1.0 / kFourPi);
+    else if (t < nf + ne) v = q[t - nf];
+    else v = mass[t - nf - ne] * (1.0 / kFourPi);
     out[t] = (float)v;
 }
 
@@ -2201,7 +2202,7 @@ cudaError_t prepare_operator_cache(sn_mesh* m, int precision, cudaStream_t s) {
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         if (f32) {  // the float32 inputs of the FP32 solves, from the same materials
             const long long nf = m->dim == 2 ? total * 4 : (long long)m->nd * 3;
-            const long long n32 = nf + 2ll * m->ne + (long long)m->ne * m->n;
+            const long long n32 = nf + m->ne + (long long)m->ne * m->n;
             if (!m->d_in32) {
                 if ((err = cudaMalloc(&m->d_in32, n32 * sizeof(float))) != cudaSuccess) {
                     m->d_in32 = nullptr;
@@ -2210,8 +2211,8 @@ cudaError_t prepare_operator_cache(sn_mesh* m, int precision, cudaStream_t s) {
                 drop_level_graphs(m);  // captured launches carry the argument pointers
             }
             SN_COUNT_LAUNCH();
-            fp32_inputs_kernel<<<grid_for(n32, 256), 256, 0, s>>>(m->d_fflux, nf, m->d_sigma_s, m->d_q, m->d_mass, m->ne,
-                                                                  m->n, m->d_in32);
+            fp32_inputs_kernel<<<grid_for(n32, 256), 256, 0, s>>>(m->d_fflux, nf, m->d_q, m->d_mass, m->ne, m->n,
+                                                                  m->d_in32);
             if ((err = cudaGetLastError()) != cudaSuccess) return err;
         }
         valid = true;
@@ -2244,12 +2245,11 @@ cudaError_t batch_refresh_cache(sn_batch* b, int precision, cudaStream_t s) {
         all = all && (precision == SN_FP32 ? fresh.ainv32 != nullptr : fresh.ainv != nullptr);
         SweepArgs& h = b->h_args[i];
         if (fresh.ainv != h.ainv || fresh.ainv32 != h.ainv32 || fresh.fflux != h.fflux || fresh.fflux32 != h.fflux32 ||
-            fresh.ss32 != h.ss32 || fresh.q32 != h.q32 || fresh.mass32 != h.mass32) {
+            fresh.q32 != h.q32 || fresh.mass32 != h.mass32) {
             h.ainv = fresh.ainv;
             h.ainv32 = fresh.ainv32;
             h.fflux = fresh.fflux;
             h.fflux32 = fresh.fflux32;
-            h.ss32 = fresh.ss32;
             h.q32 = fresh.q32;
             h.mass32 = fresh.mass32;
             changed = true;

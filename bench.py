@@ -228,6 +228,20 @@ def cpp_oracle_sweeps(prob, directions, threads, reps=1):
     return prob.n_elem * prob.n_nodes * len(directions) / dt, dt
 
 
+def cpp_oracle_solve_c1(cores):
+    """The C++ oracle's source iteration with the thick-DSA correction (Algorithm 2, SIP, conjugate
+    gradients) on config 1 to 1e-8, timed on the host cores: context for the GPU's config-1 solve."""
+    from paper_2001_09196_gb300 import inputs
+    from oracle import sweep_cpp
+    from oracle.dsa import thick_mask
+    prob = inputs.config1()
+    mask = thick_mask(prob)
+    t0 = time.perf_counter()
+    r = sweep_cpp.source_iterate(prob, mask, tol=1e-8, max_iters=500, cg_tol=1e-12, threads=cores)
+    return {"ms_to_1e-8": 1e3 * (time.perf_counter() - t0), "iters": r["iters"], "threads": cores,
+            "what": "C++ oracle, config 1 (16x16 Q1 S4), source iteration with thick DSA (SIP, CG) to 1e-8"}
+
+
 def cpu_baseline_line(prob):
     """The C++ oracle (oracle/sweep_ref.cpp) timed on the host cores: one thread on 4 of the 40
     directions, and OpenMP over all 40 directions with every core (the reported value)."""
@@ -236,11 +250,16 @@ def cpu_baseline_line(prob):
     cores = os.cpu_count() or 1
     v1, s1 = cpp_oracle_sweeps(prob, range(0, 4), 1)
     vn, sn_ = cpp_oracle_sweeps(prob, range(0, 40), cores)
-    return {"value": vn, "unit": UNIT, "cores": cores, "kind": "oracle",
+    line = {"value": vn, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"C++ oracle transport update (modal DG, Gauss elimination per element) of all 40 directions on "
                       f"the full 256x256 Q2 mesh, OpenMP over directions ({sn_:.2f} s)",
             "single_thread": {"value": v1, "sample": f"4 of 40 directions, 1 thread ({s1:.2f} s)"},
             "host": host_cpu()}
+    try:
+        line["solve_c1"] = cpp_oracle_solve_c1(cores)
+    except Exception as e:  # context only: never let it cost the line
+        line["solve_c1"] = {"unavailable": str(e)[:200]}
+    return line
 
 
 def run_reference(args, rank, ws):

@@ -360,19 +360,9 @@ bool sweep_direction(const Problem& P, int d, const double* src, double* psi) {
     return true;
 }
 
-}  // namespace
-
-extern "C" {
-
-// Transport update phi_out = sum over directions [d_begin, d_end) of w_d psi_d (Eq. phi) for
-// nodal phi_in; returns 0, or 1 if an upwind graph has a cycle.  vertices: NULL for the uniform
-// grid of the unit square/cube.  gx, gw: the (p+2)-point Gauss rule; glx: the (p+1) Gauss-Legendre
-// nodes.  threads: OpenMP threads over directions (<= 0: the runtime's default).
-int sno_sweep(int dim, int nx, int ny, int nz, int p, const double* vertices, int nd, const double* dirs,
-              const double* w, const double* sigma_t, const double* sigma_s, const double* q, double psi_inc,
-              const double* gx, const double* gw, const double* glx, const double* phi_in, double* phi_out,
-              int d_begin, int d_end, int threads) {
-    Problem P;
+void build_problem(Problem& P, int dim, int nx, int ny, int nz, int p, const double* vertices, int nd,
+                   const double* dirs, const double* w, const double* sigma_t, const double* sigma_s, const double* q,
+                   double psi_inc, const double* gx, const double* gw, const double* glx) {
     P.dim = dim;
     P.nx = nx;
     P.ny = ny;
@@ -401,19 +391,38 @@ int sno_sweep(int dim, int nx, int ny, int nz, int p, const double* vertices, in
                 }
             }
     setup(P, gx, gw, glx);
-    const int n = P.n, ne = P.ne;
-    // modal source S = (q + sigma_s phi)/(4 pi)
-    const double four_pi = 4.0 * M_PI;
-    std::vector<double> phim((size_t)ne * n), src((size_t)ne * n);
-    for (int e = 0; e < ne; ++e)
+}
+
+void to_modal(const Problem& P, const double* nodal, double* modal) {
+    const int n = P.n;
+    for (int e = 0; e < P.ne; ++e)
         for (int m = 0; m < n; ++m) {
             double s = 0.0;
-            for (int k = 0; k < n; ++k) s += P.Vinv[(size_t)m * n + k] * phi_in[(size_t)e * n + k];
-            phim[(size_t)e * n + m] = s;
+            for (int k = 0; k < n; ++k) s += P.Vinv[(size_t)m * n + k] * nodal[(size_t)e * n + k];
+            modal[(size_t)e * n + m] = s;
         }
+}
+
+void to_nodal(const Problem& P, const double* modal, double* nodal) {
+    const int n = P.n;
+    for (int e = 0; e < P.ne; ++e)
+        for (int r = 0; r < n; ++r) {
+            double s = 0.0;
+            for (int m = 0; m < n; ++m) s += P.V[(size_t)r * n + m] * modal[(size_t)e * n + m];
+            nodal[(size_t)e * n + r] = s;
+        }
+}
+
+// The transport update (Eq. source0) in modal coefficients: out = sum over directions
+// [d_begin, d_end) of w_d psi_d, psi_d = L_d^{-1}((q + sigma_s phi)/(4 pi)) with the boundary inflow;
+// false if an upwind graph has a cycle.
+bool update_modal(const Problem& P, const double* phim, double* out, int d_begin, int d_end, int threads) {
+    const int n = P.n, ne = P.ne;
+    const double four_pi = 4.0 * M_PI;
+    std::vector<double> src((size_t)ne * n);
     for (int e = 0; e < ne; ++e)
         for (int m = 0; m < n; ++m)
-            src[(size_t)e * n + m] = (sigma_s[e] * phim[(size_t)e * n + m]) / four_pi + (m == 0 ? q[e] / four_pi : 0.0);
+            src[(size_t)e * n + m] = (P.ss[e] * phim[(size_t)e * n + m]) / four_pi + (m == 0 ? P.q[e] / four_pi : 0.0);
     const int nsweep = d_end - d_begin;
     std::vector<double> psi((size_t)nsweep * ne * n);
     int cycle = 0;
@@ -423,16 +432,378 @@ int sno_sweep(int dim, int nx, int ny, int nz, int p, const double* vertices, in
 #endif
     for (int t = 0; t < nsweep; ++t)
         if (!sweep_direction(P, d_begin + t, src.data(), &psi[(size_t)t * ne * n])) cycle = 1;
-    if (cycle) return 1;
-    std::vector<double> out((size_t)ne * n, 0.0);
+    if (cycle) return false;
+    for (size_t i = 0; i < (size_t)ne * n; ++i) out[i] = 0.0;
     for (int t = 0; t < nsweep; ++t)  // in direction order
-        for (size_t i = 0; i < out.size(); ++i) out[i] += w[d_begin + t] * psi[(size_t)t * ne * n + i];
-    for (int e = 0; e < ne; ++e)
-        for (int r = 0; r < n; ++r) {
-            double s = 0.0;
-            for (int m = 0; m < n; ++m) s += P.V[(size_t)r * n + m] * out[(size_t)e * n + m];
-            phi_out[(size_t)e * n + r] = s;
+        for (size_t i = 0; i < (size_t)ne * n; ++i) out[i] += P.w[d_begin + t] * psi[(size_t)t * ne * n + i];
+    return true;
+}
+
+// ---------------------------------------------------------------- thick-subdomain DSA (SIP)
+// D_ff of Sec. 3.1-3.2 with the symmetric interior-penalty face terms (Eq. SIP, the conjugate-
+// gradient path), restricted to the thick elements: for thick elements K and thick-thick faces F,
+//   sum_K (D grad u, grad v)_K + (sigma_a u, v)_K
+//   + sum_F <kappa [u],[v]> - <{D grad u.n},[v]> - <{D grad v.n},[u]>,
+// D = 1/(3 sigma_t), sigma_a = sigma_t - sigma_s; a face whose neighbour is not thick is a face to a
+// zero exterior state (jump = u, average = u/2); kappa_F = max(1/4, c(p) (D-/h- + D+/h+)/2),
+// max(1/4, c(p) D/h) on boundary-type faces, c(p) = 2 p (p+1), h = |K|/|F|.  Integrals by the
+// (p+1)-point Gauss rule per axis, the same as oracle/dsa.py.  Stored by block rows of thick
+// elements: (column element, n x n block) pairs.
+struct Dsa {
+    int n = 0, nt = 0;
+    std::vector<int> thick, local;                      // thick elements; local index (-1: not thick)
+    std::vector<std::vector<std::pair<int, std::vector<double>>>> rows;
+    std::vector<double> dinv;                           // inverses of the diagonal blocks (nt x n x n)
+};
+
+std::vector<double>& block_at(Dsa& D, int r, int c) {
+    for (auto& pr : D.rows[r])
+        if (pr.first == c) return pr.second;
+    D.rows[r].push_back({c, std::vector<double>((size_t)D.n * D.n, 0.0)});
+    return D.rows[r].back().second;
+}
+
+void inv3(int dim, const double* J, double* Ji) {  // inverse of a dim x dim matrix
+    double A[9];
+    adjugate(dim, J, A);
+    const double dj = det(dim, J);
+    for (int i = 0; i < dim * dim; ++i) Ji[i] = A[i] / dj;
+}
+
+void assemble_sip(const Problem& P, const unsigned char* mask, const double* gx1, const double* gw1, Dsa& D) {
+    const int dim = P.dim, n = P.n, p = P.p, Q1 = p + 1;
+    D.n = n;
+    D.local.assign(P.ne, -1);
+    for (int e = 0; e < P.ne; ++e)
+        if (mask[e]) {
+            D.local[e] = (int)D.thick.size();
+            D.thick.push_back(e);
         }
+    D.nt = (int)D.thick.size();
+    D.rows.assign(D.nt, {});
+    const double cp = 2.0 * p * (p + 1);
+    // (p+1)-point rules: volume (x fastest) and faces
+    int nq = 1, nqf = 1;
+    for (int a = 0; a < dim; ++a) nq *= Q1;
+    for (int a = 0; a < dim - 1; ++a) nqf *= Q1;
+    std::vector<double> vx((size_t)nq * dim), vw(nq), B((size_t)nq * n), dB((size_t)nq * n * dim);
+    for (int t = 0; t < nq; ++t) {
+        int r = t;
+        double wt = 1.0;
+        for (int a = 0; a < dim; ++a) {
+            vx[(size_t)t * dim + a] = gx1[r % Q1];
+            wt *= gw1[r % Q1];
+            r /= Q1;
+        }
+        vw[t] = wt;
+        basis(P, &vx[(size_t)t * dim], &B[(size_t)t * n], &dB[(size_t)t * n * dim]);
+    }
+    // element volumes |K| with the same rule (every element: h of non-thick neighbours is not needed)
+    std::vector<double> vol(P.ne, 0.0);
+    for (int e = 0; e < P.ne; ++e) {
+        double x[3], J[9];
+        for (int t = 0; t < nq; ++t) {
+            map_point(P, e, &vx[(size_t)t * dim], x, J);
+            vol[e] += vw[t] * det(dim, J);
+        }
+    }
+    auto Dc = [&](int e) { return 1.0 / (3.0 * P.st[e]); };
+    // volume terms
+    for (int lt = 0; lt < D.nt; ++lt) {
+        const int e = D.thick[lt];
+        const double De = Dc(e), sa = P.st[e] - P.ss[e];
+        std::vector<double>& K = block_at(D, lt, lt);
+        double x[3], J[9], Ji[9];
+        std::vector<double> g((size_t)n * dim);
+        for (int t = 0; t < nq; ++t) {
+            map_point(P, e, &vx[(size_t)t * dim], x, J);
+            const double dj = det(dim, J);
+            inv3(dim, J, Ji);
+            for (int m = 0; m < n; ++m)  // physical gradient: (J^{-T} grad_ref)_r = sum_c Jinv[c][r] d/dxi_c
+                for (int r = 0; r < dim; ++r) {
+                    double v = 0.0;
+                    for (int c = 0; c < dim; ++c) v += Ji[c * dim + r] * dB[((size_t)t * n + m) * dim + c];
+                    g[(size_t)m * dim + r] = v;
+                }
+            for (int m = 0; m < n; ++m)
+                for (int k = 0; k < n; ++k) {
+                    double gg = 0.0;
+                    for (int r = 0; r < dim; ++r) gg += g[(size_t)m * dim + r] * g[(size_t)k * dim + r];
+                    K[(size_t)m * n + k] += vw[t] * dj * (De * gg + sa * B[(size_t)t * n + m] * B[(size_t)t * n + k]);
+                }
+        }
+    }
+    // face terms
+    std::vector<double> fwt(nqf), ft((size_t)nqf * (dim - 1 > 0 ? dim - 1 : 1));
+    for (int t = 0; t < nqf; ++t) {
+        int r = t;
+        double wt = 1.0;
+        for (int b = 0; b < dim - 1; ++b) {
+            ft[(size_t)t * (dim - 1) + b] = gx1[r % Q1];
+            wt *= gw1[r % Q1];
+            r /= Q1;
+        }
+        fwt[t] = wt;
+    }
+    for (int lt = 0; lt < D.nt; ++lt) {
+        const int e = D.thick[lt];
+        for (int f = 0; f < 2 * dim; ++f) {
+            const int a = f / 2, side = f % 2;
+            const double s = side ? 1.0 : -1.0;
+            const int u = P.nbr[(size_t)e * 2 * dim + f];
+            const int ut = u >= 0 ? D.local[u] : -1;
+            if (ut >= 0 && side == 0) continue;  // interior thick-thick faces from the side == 1 element
+            // face points on this side (xi) and on the neighbour's side (xo), normals, weights
+            std::vector<double> Bf((size_t)nqf * n), Bo((size_t)nqf * n), dn((size_t)nqf * n), dno((size_t)nqf * n),
+                dS(nqf);
+            double area = 0.0;
+            for (int t = 0; t < nqf; ++t) {
+                double xi[3], xo[3];
+                int b2 = 0;
+                for (int b = 0; b < dim; ++b) {
+                    if (b == a) {
+                        xi[b] = side ? 1.0 : -1.0;
+                        xo[b] = side ? -1.0 : 1.0;
+                    } else {
+                        xi[b] = xo[b] = ft[(size_t)t * (dim - 1) + b2];
+                        ++b2;
+                    }
+                }
+                double x[3], J[9], A[9], Ji[9], dBf[27 * 8];
+                basis(P, xi, &Bf[(size_t)t * n], dBf);
+                map_point(P, e, xi, x, J);
+                adjugate(dim, J, A);
+                inv3(dim, J, Ji);
+                double N[3], nn = 0.0;
+                for (int r = 0; r < dim; ++r) {
+                    N[r] = s * A[a * dim + r];
+                    nn += N[r] * N[r];
+                }
+                nn = std::sqrt(nn);
+                dS[t] = nn * fwt[t];
+                area += dS[t];
+                double nrm[3];
+                for (int r = 0; r < dim; ++r) nrm[r] = N[r] / nn;
+                for (int m = 0; m < n; ++m) {
+                    double v = 0.0;
+                    for (int r = 0; r < dim; ++r) {
+                        double gr = 0.0;
+                        for (int c = 0; c < dim; ++c) gr += Ji[c * dim + r] * dBf[m * dim + c];
+                        v += gr * nrm[r];
+                    }
+                    dn[(size_t)t * n + m] = v;
+                }
+                if (ut >= 0) {  // the neighbour's basis and gradient at the same physical point
+                    double Jo[9], Jio[9], dBo[27 * 8];
+                    basis(P, xo, &Bo[(size_t)t * n], dBo);
+                    map_point(P, u, xo, x, Jo);
+                    inv3(dim, Jo, Jio);
+                    for (int m = 0; m < n; ++m) {
+                        double v = 0.0;
+                        for (int r = 0; r < dim; ++r) {
+                            double gr = 0.0;
+                            for (int c = 0; c < dim; ++c) gr += Jio[c * dim + r] * dBo[m * dim + c];
+                            v += gr * nrm[r];
+                        }
+                        dno[(size_t)t * n + m] = v;
+                    }
+                }
+            }
+            const double De = Dc(e), he = vol[e] / area;
+            if (ut < 0) {  // boundary-type face: <kappa u, v> - 1/2 <D du/dn, v> - 1/2 <D dv/dn, u>
+                const double kap = std::max(0.25, cp * De / he);
+                std::vector<double>& K = block_at(D, lt, lt);
+                for (int t = 0; t < nqf; ++t)
+                    for (int m = 0; m < n; ++m)
+                        for (int k = 0; k < n; ++k)
+                            K[(size_t)m * n + k] += dS[t] * (kap * Bf[(size_t)t * n + m] * Bf[(size_t)t * n + k] -
+                                                             0.5 * De * dn[(size_t)t * n + k] * Bf[(size_t)t * n + m] -
+                                                             0.5 * De * dn[(size_t)t * n + m] * Bf[(size_t)t * n + k]);
+                continue;
+            }
+            const double Do = Dc(u), ho = vol[u] / area;
+            const double kap = std::max(0.25, cp * 0.5 * (De / he + Do / ho));
+            struct Side {
+                int row;
+                const double *Bv, *dnv;
+                double Dv, sg;
+            };
+            const Side sides[2] = {{lt, Bf.data(), dn.data(), De, 1.0}, {ut, Bo.data(), dno.data(), Do, -1.0}};
+            for (const Side& ra : sides)
+                for (const Side& cb : sides) {
+                    std::vector<double>& K = block_at(D, ra.row, cb.row);
+                    for (int t = 0; t < nqf; ++t)
+                        for (int m = 0; m < n; ++m)
+                            for (int k = 0; k < n; ++k)
+                                K[(size_t)m * n + k] +=
+                                    dS[t] * (kap * ra.sg * cb.sg * ra.Bv[(size_t)t * n + m] * cb.Bv[(size_t)t * n + k] -
+                                             0.5 * cb.Dv * ra.sg * cb.dnv[(size_t)t * n + k] * ra.Bv[(size_t)t * n + m] -
+                                             0.5 * ra.Dv * cb.sg * ra.dnv[(size_t)t * n + m] * cb.Bv[(size_t)t * n + k]);
+                }
+        }
+    }
+    // inverses of the diagonal blocks (block-Jacobi preconditioner of the conjugate gradients)
+    D.dinv.assign((size_t)D.nt * n * n, 0.0);
+    for (int lt = 0; lt < D.nt; ++lt) {
+        const std::vector<double>& K = block_at(D, lt, lt);
+        for (int c = 0; c < n; ++c) {
+            std::vector<double> A(K), b(n, 0.0);
+            b[c] = 1.0;
+            solve_dense(n, A.data(), b.data());
+            for (int r = 0; r < n; ++r) D.dinv[((size_t)lt * n + r) * n + c] = b[r];
+        }
+    }
+}
+
+void dsa_apply(const Dsa& D, const double* x, double* y) {  // y = D_ff x
+    const int n = D.n;
+    for (int r = 0; r < D.nt; ++r) {
+        double* yr = y + (size_t)r * n;
+        for (int m = 0; m < n; ++m) yr[m] = 0.0;
+        for (const auto& pr : D.rows[r]) {
+            const double* xc = x + (size_t)pr.first * n;
+            for (int m = 0; m < n; ++m)
+                for (int k = 0; k < n; ++k) yr[m] += pr.second[(size_t)m * n + k] * xc[k];
+        }
+    }
+}
+
+// D_ff x = b by block-Jacobi-preconditioned conjugate gradients to ||b - D x|| <= tol ||b||
+int dsa_solve(const Dsa& D, const double* b, double* x, double tol, int max_iters) {
+    const size_t N = (size_t)D.nt * D.n;
+    const int n = D.n;
+    std::vector<double> r(b, b + N), z(N), p(N), q(N);
+    for (size_t i = 0; i < N; ++i) x[i] = 0.0;
+    auto dot = [&](const std::vector<double>& a, const std::vector<double>& c) {
+        double s = 0.0;
+        for (size_t i = 0; i < N; ++i) s += a[i] * c[i];
+        return s;
+    };
+    auto precond = [&]() {
+        for (int e = 0; e < D.nt; ++e)
+            for (int m = 0; m < n; ++m) {
+                double s = 0.0;
+                for (int k = 0; k < n; ++k) s += D.dinv[((size_t)e * n + m) * n + k] * r[(size_t)e * n + k];
+                z[(size_t)e * n + m] = s;
+            }
+    };
+    const double bb = dot(r, r);
+    if (bb == 0.0) return 0;
+    precond();
+    p = z;
+    double rz = dot(r, z);
+    int it = 0;
+    while (it < max_iters) {
+        dsa_apply(D, p.data(), q.data());
+        const double alpha = rz / dot(p, q);
+        for (size_t i = 0; i < N; ++i) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * q[i];
+        }
+        ++it;
+        if (dot(r, r) <= tol * tol * bb) break;
+        precond();
+        const double rz2 = dot(r, z);
+        const double beta = rz2 / rz;
+        rz = rz2;
+        for (size_t i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
+    }
+    return it;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Transport update phi_out = sum over directions [d_begin, d_end) of w_d psi_d (Eq. phi) for
+// nodal phi_in; returns 0, or 1 if an upwind graph has a cycle.  vertices: NULL for the uniform
+// grid of the unit square/cube.  gx, gw: the (p+2)-point Gauss rule; glx: the (p+1) Gauss-Legendre
+// nodes.  threads: OpenMP threads over directions (<= 0: the runtime's default).
+int sno_sweep(int dim, int nx, int ny, int nz, int p, const double* vertices, int nd, const double* dirs,
+              const double* w, const double* sigma_t, const double* sigma_s, const double* q, double psi_inc,
+              const double* gx, const double* gw, const double* glx, const double* phi_in, double* phi_out,
+              int d_begin, int d_end, int threads) {
+    Problem P;
+    build_problem(P, dim, nx, ny, nz, p, vertices, nd, dirs, w, sigma_t, sigma_s, q, psi_inc, gx, gw, glx);
+    std::vector<double> phim((size_t)P.ne * P.n), out((size_t)P.ne * P.n);
+    to_modal(P, phi_in, phim.data());
+    if (!update_modal(P, phim.data(), out.data(), d_begin, d_end, threads)) return 1;
+    to_nodal(P, out.data(), phi_out);
+    return 0;
+}
+
+// The thick-subdomain DSA operator D_ff (SIP) in the modal basis as a dense matrix of the thick
+// elements' coefficients (nt n x nt n, row-major; small problems only).  gx1, gw1: the (p+1)-point
+// Gauss rule.  Returns nt.
+int sno_dsa_matrix(int dim, int nx, int ny, int nz, int p, const double* vertices, const double* sigma_t,
+                   const double* sigma_s, const unsigned char* mask, const double* gx, const double* gw,
+                   const double* glx, const double* gx1, const double* gw1, double* out) {
+    Problem P;
+    const double dir0[3] = {0.0, 0.0, 1.0}, w0 = 1.0;
+    build_problem(P, dim, nx, ny, nz, p, vertices, 1, dir0, &w0, sigma_t, sigma_s, sigma_t, 0.0, gx, gw, glx);
+    Dsa D;
+    assemble_sip(P, mask, gx1, gw1, D);
+    const size_t N = (size_t)D.nt * D.n;
+    if (out) {
+        for (size_t i = 0; i < N * N; ++i) out[i] = 0.0;
+        for (int r = 0; r < D.nt; ++r)
+            for (const auto& pr : D.rows[r])
+                for (int m = 0; m < D.n; ++m)
+                    for (int k = 0; k < D.n; ++k)
+                        out[((size_t)r * D.n + m) * N + (size_t)pr.first * D.n + k] = pr.second[(size_t)m * D.n + k];
+    }
+    return D.nt;
+}
+
+// Source iteration (Eq. DSA_fp) from phi = 0: phi_half = T phi + b (the transport update),
+// r = phi_half - phi, then phi = phi_half, or with a thick mask phi = phi_half + E_f D_ff^{-1}
+// Sigma_f r_f (Algorithm 2, Sigma = sigma_s M, D_ff the SIP operator above solved by conjugate
+// gradients to cg_tol); stops after the iteration whose ||r|| (Euclidean, GL-nodal values) is at most
+// tol ||r^0||, or after max_iters.  phi_out: nodal.  Returns 0, 1 on a cycle.
+int sno_source_iterate(int dim, int nx, int ny, int nz, int p, const double* vertices, int nd, const double* dirs,
+                       const double* w, const double* sigma_t, const double* sigma_s, const double* q,
+                       double psi_inc, const double* gx, const double* gw, const double* glx, const double* gx1,
+                       const double* gw1, const unsigned char* mask, double tol, int max_iters, double cg_tol,
+                       double* phi_out, int* iters, double* rel_out, int threads) {
+    Problem P;
+    build_problem(P, dim, nx, ny, nz, p, vertices, nd, dirs, w, sigma_t, sigma_s, q, psi_inc, gx, gw, glx);
+    const int n = P.n, ne = P.ne;
+    Dsa D;
+    const bool use_dsa = mask != nullptr;
+    if (use_dsa) assemble_sip(P, mask, gx1, gw1, D);
+    std::vector<double> phi((size_t)ne * n, 0.0), half((size_t)ne * n), r((size_t)ne * n), rn((size_t)ne * n);
+    std::vector<double> rhs((size_t)D.nt * n), corr((size_t)D.nt * n);
+    double r0 = -1.0, rel = INFINITY;
+    int it = 0;
+    while (it < max_iters) {
+        if (!update_modal(P, phi.data(), half.data(), 0, P.nd, threads)) return 1;
+        for (size_t i = 0; i < r.size(); ++i) r[i] = half[i] - phi[i];
+        to_nodal(P, r.data(), rn.data());
+        double nrm = 0.0;
+        for (double v : rn) nrm += v * v;
+        nrm = std::sqrt(nrm);
+        if (r0 < 0.0) r0 = nrm > 0.0 ? nrm : 1.0;
+        rel = nrm / r0;
+        phi = half;
+        if (use_dsa && D.nt > 0) {  // Sigma_f r_f = sigma_s M r on the thick elements
+            for (int lt = 0; lt < D.nt; ++lt) {
+                const int e = D.thick[lt];
+                for (int m = 0; m < n; ++m) {
+                    double s = 0.0;
+                    for (int k = 0; k < n; ++k) s += P.M[((size_t)e * n + m) * n + k] * r[(size_t)e * n + k];
+                    rhs[(size_t)lt * n + m] = P.ss[e] * s;
+                }
+            }
+            dsa_solve(D, rhs.data(), corr.data(), cg_tol, 100000);
+            for (int lt = 0; lt < D.nt; ++lt)
+                for (int m = 0; m < n; ++m) phi[(size_t)D.thick[lt] * n + m] += corr[(size_t)lt * n + m];
+        }
+        ++it;
+        if (rel <= tol) break;
+    }
+    to_nodal(P, phi.data(), phi_out);
+    if (iters) *iters = it;
+    if (rel_out) *rel_out = rel;
     return 0;
 }
 

@@ -1,11 +1,16 @@
-"""CPU: the C++ oracle of the transport update (oracle/sweep_ref.cpp) against the pinned numpy oracle
-and against closed forms.
+"""CPU: the C++ oracle (oracle/sweep_ref.cpp: the transport update, the thick-subdomain SIP DSA
+operator and source iteration with and without Algorithm 2) against the pinned numpy oracle and
+against closed forms.
 
 The C++ code restates the same steps (Sec. 1, Eq. psi and Eq. phi; upwind DG of Sec. 3.1) in a second
 implementation; it serves as the timed CPU baseline, so it is pinned here: element by element equal
 to oracle.Transport.sweep (1e-13 relative) on Cartesian, jittered, Q3, 3D and inflow cases and on a
 partial direction range; the same bits for any number of threads; and an infinite medium with the
-equilibrium inflow psi_inc = q/(4 pi sigma_a) is a fixed point, phi = q/(sigma_t - sigma_s).
+equilibrium inflow psi_inc = q/(4 pi sigma_a) is a fixed point, phi = q/(sigma_t - sigma_s).  Its D_ff
+(Eq. SIP on the thick elements, Sec. 3.2) equals oracle.dsa.DSA's entry by entry; its source
+iteration reproduces the numpy oracle's iterates (unaccelerated to 1e-13; with the Algorithm 2 step,
+where the numpy oracle factorises D_ff and the C++ code runs conjugate gradients, within the iterate
+tolerance of the rounding-amplification reading) and its converged solutions.
 """
 import numpy as np
 import pytest
@@ -55,3 +60,51 @@ def test_cpp_sweep_infinite_medium_fixed_point(dim, p):
     phi = np.full((prob.n_elem, prob.n_nodes), q / (st - ss))
     got = sweep_cpp.sweep(prob, phi, threads=2)
     assert np.abs(got - phi).max() <= 1e-13 * phi.max()
+
+
+DSA_CASES = {"c1": inputs.config1, "c2_16": lambda: inputs.config2(n=16, block=4),
+             "c3_8": lambda: inputs.config3(n=8), "q3": lambda: inputs.config2d_fields(6, 3, 4, 78, "q3")}
+
+
+def _jittered_q2():
+    prob = inputs.config2d_fields(8, 2, 4, 77, "q2j")
+    prob.vertices = inputs.jittered_vertices(8, 8, 0.15, 77)
+    return prob
+
+
+DSA_CASES["jittered_q2"] = _jittered_q2
+
+
+@pytest.mark.parametrize("name", list(DSA_CASES))
+def test_cpp_dsa_operator_equals_the_numpy_oracle(name):
+    from oracle.dsa import DSA, thick_mask
+    prob = DSA_CASES[name]()
+    mask = thick_mask(prob)
+    assert mask.sum() > 0
+    ref = DSA(Transport(prob), mask).D.toarray()
+    got = sweep_cpp.dsa_matrix(prob, mask)
+    assert got.shape == ref.shape
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name", list(DSA_CASES))
+def test_cpp_source_iteration_equals_the_numpy_oracle(name):
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from tolerances import dsa_iterate_tol
+    from oracle.dsa import DSA, thick_mask
+    prob = DSA_CASES[name]()
+    T = Transport(prob)
+    mask = thick_mask(prob)
+    ref = T.source_iterate(dsa=None, tol=0.0, max_iters=5)["phi"]
+    got = sweep_cpp.source_iterate(prob, None, tol=0.0, max_iters=5)["phi"]
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+    d = DSA(T, mask)
+    ref = T.source_iterate(dsa=d, tol=0.0, max_iters=4)["phi"]
+    got = sweep_cpp.source_iterate(prob, mask, tol=0.0, max_iters=4)["phi"]
+    assert np.abs(got - ref).max() <= dsa_iterate_tol(prob, mask) * np.abs(ref).max()
+    ref = T.source_iterate(dsa=d, tol=1e-12, max_iters=3000)
+    got = sweep_cpp.source_iterate(prob, mask, tol=1e-12, max_iters=3000)
+    assert got["iters"] == ref["iters"]
+    assert np.abs(got["phi"] - ref["phi"]).max() <= 1e-10 * np.abs(ref["phi"]).max()

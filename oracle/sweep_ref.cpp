@@ -1,4 +1,5 @@
-// CPU oracle of the transport update in plain C++ (test infrastructure and timed CPU baseline only;
+// CPU oracle in plain C++: the transport update, the thick-subdomain DSA operator and source
+// iteration with or without the Algorithm 2 step (test infrastructure and timed CPU baseline only;
 // the product path never loads it).
 //
 // What it computes is the update of Sec. 1 (Eq. psi and Eq. phi) in the upwind DG discretisation of
@@ -13,7 +14,9 @@
 // pivoting.  Input and output scalar fluxes are values at the (p+1)^dim Gauss-Legendre nodes
 // ([elem][node], x fastest), converted to and from modal coefficients here.  The direction set and
 // both 1D Gauss rules are inputs.  Directions may be swept in parallel (OpenMP); the sum over
-// directions always runs in direction order.
+// directions always runs in direction order.  The DSA operator (Eq. SIP on the thick elements,
+// Sec. 3.1-3.2) and the source iteration (Eq. DSA_fp, Algorithm 2) follow oracle/dsa.py and
+// oracle/transport.py; D_ff is solved by block-Jacobi conjugate gradients.
 #include <cmath>
 #include <cstring>
 #include <vector>

@@ -17,8 +17,10 @@
 // directions always runs in direction order.  The DSA operator (Eq. SIP on the thick elements,
 // Sec. 3.1-3.2) and the source iteration (Eq. DSA_fp, Algorithm 2) follow oracle/dsa.py and
 // oracle/transport.py; D_ff is solved by block-Jacobi conjugate gradients.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #ifdef _OPENMP

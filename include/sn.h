@@ -353,7 +353,7 @@ sn_status sn_gradients(sn_mesh* mesh, const double* phi, const double* mu, doubl
  * dsa = SN_DSA_NONE, max_iters = K, checkpoint_every = the same value (iterates checkpoint_every,
  * 2 checkpoint_every, ...; at least ceil(K / checkpoint_every) - 1 of them).  phi0: device, or NULL
  * for phi_0 = 0 (sn_source_iterate's cold start).  g: device [elem][node].  Outputs n_elem doubles
- * each (NULL to skip), overwritten.  Memory: checkpoint_every + 5 vectors of n_elem x n_nodes
+ * each (NULL to skip), overwritten.  Memory: min(checkpoint_every, K) + 5 vectors of n_elem x n_nodes
  * doubles, plus ceil(K / checkpoint_every) more when checkpoints is NULL, allocated for the call.
  * Cost: K forward and K adjoint sweeps in the backward pass, K - ceil(K / checkpoint_every) forward
  * sweeps recomputing segments, and K - 1 more when checkpoints is NULL.  FP64.

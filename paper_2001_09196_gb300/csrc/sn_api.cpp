@@ -1308,6 +1308,7 @@ sn_status sn_unrolled_gradients(sn_mesh* m, const double* phi0, int K, int every
     if (!m || !g) return fail(SN_ERR_ARG, "null argument");
     if (K < 1) return fail(SN_ERR_ARG, "K must be >= 1");
     if (every < 1) return fail(SN_ERR_ARG, "checkpoint_every must be >= 1");
+    every = std::min(every, K);  // one segment either way; no workspace beyond K iterates
     sn_status st = ensure_lambda(m);
     if (st != SN_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;

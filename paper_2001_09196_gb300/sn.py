@@ -144,6 +144,14 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _need(n, **tensors):
+    """Raise unless every given tensor (None = not given) holds exactly n values: the library reads
+    and writes n values through each pointer, so a shorter buffer would be overrun on the device."""
+    for name, t in tensors.items():
+        if t is not None and t.numel() != n:
+            raise ValueError(f"{name} needs exactly {n} values, got {t.numel()}")
+
+
 def _stream(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -326,6 +334,7 @@ class Mesh:
     def set_materials(self, sigma_t, sigma_s, q, stream=None):
         import torch
         if isinstance(sigma_t, torch.Tensor) and sigma_t.is_cuda:
+            _need(self.n_elem, sigma_t=sigma_t, sigma_s=sigma_s, q=q)
             args = [_ptr(sigma_t.contiguous()), _ptr(sigma_s.contiguous()), _ptr(q.contiguous())]
             _check(_lib.sn_set_materials(self._h, *args, 1, _stream(stream)))
             return
@@ -338,6 +347,7 @@ class Mesh:
     def sweep_directions(self, phi_in, d_begin, d_end, phi_out=None, precision="fp64", stream=None):
         """The contribution of directions d_begin <= d < d_end to one transport update."""
         import torch
+        _need(self.n_elem * self.n_nodes, phi_in=phi_in, phi_out=phi_out)
         if phi_out is None:
             phi_out = torch.empty(self.shape, dtype=torch.float64, device=phi_in.device if phi_in is not None else "cuda")
         _check(_lib.sn_sweep_directions(self._h, _ptr(phi_in), _ptr(phi_out), int(d_begin), int(d_end),
@@ -350,6 +360,7 @@ class Mesh:
         constants are the paper's NIF-unit a and c."""
         import torch
         if isinstance(sigma, torch.Tensor) and sigma.is_cuda:
+            _need(self.n_elem, sigma=sigma, cv=cv, T=T)
             args = [_ptr(x.contiguous()) for x in (sigma, cv, T)]
             _check(_lib.sn_set_pseudo_scattering(self._h, *args, float(dt), float(a_rad), float(c_light), 1,
                                                  _stream(stream)))
@@ -369,6 +380,7 @@ class Mesh:
 
     def sweep(self, phi_in, phi_out=None, precision="fp64", stream=None):
         import torch
+        _need(self.n_elem * self.n_nodes, phi_in=phi_in, phi_out=phi_out)
         if phi_out is None:
             phi_out = torch.empty(self.shape, dtype=torch.float64, device=phi_in.device if phi_in is not None else "cuda")
         _check(_lib.sn_sweep(self._h, _ptr(phi_in), _ptr(phi_out), _PREC.get(precision, precision), _stream(stream)))
@@ -382,11 +394,18 @@ class Mesh:
         of shape (n_elem, n_nodes) and must replace it in place by the sum over all processes
         (torch_allreduce builds one from a torch.distributed process group)."""
         import torch
+        M = self.n_elem * self.n_nodes
+        _need(M, phi=phi)
+        ck = kw.get("checkpoints")
+        if ck is not None and (ck.numel() < M or ck.numel() % M):
+            raise ValueError(f"checkpoints need a whole number (>= 1) of n_elem * n_nodes = {M} value vectors")
         if phi is None:
             phi = torch.zeros(self.shape, dtype=torch.float64, device="cuda")
         if "warm_start" not in kw:
             kw["warm_start"] = False
         o = make_opts(**kw)
+        if ck is not None:
+            o.max_checkpoints = ck.numel() // M
         failure = []
         if directions is not None or exchange is not None:
             if directions is None or exchange is None:
@@ -423,12 +442,14 @@ class Mesh:
 
     def adjoint_sweep(self, mu, out=None, stream=None):
         import torch
+        _need(self.n_elem * self.n_nodes, mu=mu, out=out)
         out = torch.empty_like(mu) if out is None else out
         _check(_lib.sn_adjoint_sweep(self._h, _ptr(mu), _ptr(out), FP64, _stream(stream)))
         return out
 
     def adjoint_iterate(self, g, mu=None, stream=None, **kw):
         import torch
+        _need(self.n_elem * self.n_nodes, g=g, mu=mu)
         mu = torch.zeros_like(g) if mu is None else mu
         kw.setdefault("warm_start", False)
         o = make_opts(**kw)
@@ -442,6 +463,7 @@ class Mesh:
 
     def gradients(self, phi, mu, stream=None):
         import torch
+        _need(self.n_elem * self.n_nodes, phi=phi, mu=mu)
         gt, gs, gq = (torch.empty(self.n_elem, dtype=torch.float64, device=phi.device) for _ in range(3))
         _check(_lib.sn_gradients(self._h, _ptr(phi), _ptr(mu), _ptr(gt), _ptr(gs), _ptr(gq), _stream(stream)))
         return gt, gs, gq
@@ -480,6 +502,7 @@ class Mesh:
 
     def dsa_apply(self, x, stream=None, **kw):
         import torch
+        _need(self.n_elem * self.n_nodes, x=x)
         y = torch.empty_like(x)
         o = make_opts(**kw)
         _check(_lib.sn_dsa_apply(self._h, C.byref(o), _ptr(x), _ptr(y), _stream(stream)))
@@ -487,6 +510,7 @@ class Mesh:
 
     def dsa_solve(self, b, stream=None, **kw):
         import torch
+        _need(self.n_elem * self.n_nodes, b=b)
         x = torch.empty_like(b)
         o = make_opts(**kw)
         its = C.c_int(0)
@@ -525,14 +549,19 @@ class Batch:
                                       C.byref(b), C.byref(c)))
         return SCHEDULES[a.value], b.value, c.value
 
-    @staticmethod
-    def _ptrs(tensors):
+    def _ptrs(self, tensors):
+        """One pointer per instance; each tensor must hold its instance's n_elem * n_nodes values."""
+        tensors = list(tensors)
+        if len(tensors) != len(self.meshes):
+            raise ValueError(f"need one tensor per instance ({len(self.meshes)}), got {len(tensors)}")
+        for i, (t, m) in enumerate(zip(tensors, self.meshes)):
+            _need(m.n_elem * m.n_nodes, **{f"instance {i}": t})
         return (C.c_void_p * len(tensors))(*[None if t is None else _ptr(t).value for t in tensors])
 
     def sweep(self, phis_in=None, precision="fp64", stream=None):
         import torch
-        outs = [torch.empty(m.shape, dtype=torch.float64, device="cuda") for m in self.meshes]
         ins = self._ptrs(phis_in) if phis_in is not None else None
+        outs = [torch.empty(m.shape, dtype=torch.float64, device="cuda") for m in self.meshes]
         _check(_lib.sn_batch_sweep(self._h, ins, self._ptrs(outs), _PREC.get(precision, precision), _stream(stream)))
         return outs
 

@@ -117,3 +117,60 @@ def test_noalloc_binding_checks_run_before_the_library(libpath):
     buf = torch.zeros(11, **f64)
     with pytest.raises(ValueError, match="overlap"):
         sn.scalar_flux_noalloc(psi, w, phi_out=buf[:10], resid_norm2=buf[9:])
+
+
+def test_mesh_and_batch_bindings_check_buffer_sizes_before_the_library(libpath):
+    """Every Mesh / Batch method that hands the library a caller's buffer refuses a buffer of the
+    wrong size before any pointer reaches the library (the library trusts the sizes it is given).
+    The meshes here are stand-ins with only their sizes set: no GPU and no library handle."""
+    import torch
+    from paper_2001_09196_gb300 import sn
+    f64 = dict(dtype=torch.float64)
+
+    def fake_mesh(n_elem, n_nodes):
+        m = object.__new__(sn.Mesh)
+        m._h = None
+        m.n_elem, m.n_nodes, m.n_dirs, m.n_levels, m.dim, m.p = n_elem, n_nodes, 12, 1, 2, 1
+        return m
+
+    m = fake_mesh(16, 4)
+    bad = torch.zeros(63, **f64)
+    good = torch.zeros(16, 4, **f64)
+    cases = [
+        ("phi_in", lambda: m.sweep(bad)),
+        ("phi_out", lambda: m.sweep(good, phi_out=bad)),
+        ("phi_in", lambda: m.sweep_directions(bad, 0, 3)),
+        ("phi_out", lambda: m.sweep_directions(good, 0, 3, phi_out=bad)),
+        ("phi", lambda: m.source_iterate(phi=bad)),
+        ("checkpoints", lambda: m.source_iterate(phi=good, checkpoint_every=2, checkpoints=torch.zeros(65, **f64))),
+        ("checkpoints", lambda: m.source_iterate(phi=good, checkpoint_every=2, checkpoints=torch.zeros(32, **f64))),
+        ("mu", lambda: m.adjoint_sweep(bad)),
+        ("out", lambda: m.adjoint_sweep(good, out=bad)),
+        ("g", lambda: m.adjoint_iterate(bad)),
+        ("mu", lambda: m.adjoint_iterate(good, mu=bad)),
+        ("phi", lambda: m.gradients(bad, good)),
+        ("mu", lambda: m.gradients(good, bad)),
+        ("g and phi0", lambda: m.unrolled_gradients(bad, 3)),
+        ("checkpoints", lambda: m.unrolled_gradients(good, 5, 2, checkpoints=torch.zeros(64, **f64))),
+        ("x", lambda: m.dsa_apply(bad)),
+        ("b", lambda: m.dsa_solve(bad)),
+    ]
+    for name, call in cases:
+        with pytest.raises(ValueError, match=name):
+            call()
+    if torch.cuda.is_available():
+        return  # the material checks below rely on CPU tensors taking the host path
+    with pytest.raises(ValueError, match="one value per element"):
+        m.set_materials(torch.ones(15, **f64), torch.ones(16, **f64), torch.ones(16, **f64))
+    with pytest.raises(ValueError, match="one value per element"):
+        m.set_pseudo_scattering(torch.ones(16, **f64), torch.ones(17, **f64), torch.ones(16, **f64), 1.0)
+
+    b = object.__new__(sn.Batch)
+    b._h = None
+    b.meshes = [fake_mesh(16, 4), fake_mesh(9, 9)]
+    with pytest.raises(ValueError, match="one tensor per instance"):
+        b.sweep([good])
+    with pytest.raises(ValueError, match="instance 1"):
+        b.sweep([good, torch.zeros(80, **f64)])
+    with pytest.raises(ValueError, match="instance 0"):
+        b.source_iterate([bad, torch.zeros(81, **f64)])

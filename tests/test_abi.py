@@ -62,6 +62,44 @@ def test_invalid_descriptor_is_rejected_without_touching_the_gpu(libpath):
         sn.Mesh(2, 4, 4, p=1, sn=5)
 
 
+def test_every_descriptor_refusal_comes_before_the_gpu(libpath):
+    """Each refusal of sn_mesh_create that depends only on the descriptor: element counts, order,
+    dimension, inflow value, the element-count ceiling, and the vertices (finite, no inverted or
+    degenerate quadrilateral, none in 3D).  All run before the first CUDA call, so they hold here."""
+    import numpy as np
+    from paper_2001_09196_gb300 import sn
+
+    def verts(nx, ny):
+        x, y = np.meshgrid(np.linspace(0, 1, nx + 1), np.linspace(0, 1, ny + 1))
+        return np.stack([x, y], axis=-1).reshape(-1, 2).copy()
+
+    inverted = verts(2, 2)
+    inverted[[4, 5]] = inverted[[5, 4]]          # swap two vertices of the middle row
+    flat = verts(1, 1)
+    flat[3] = flat[1]                             # a triangle: zero Jacobian at one corner
+    nan = verts(2, 2)
+    nan[4, 0] = np.nan
+    cases = [
+        ("element counts", lambda: sn.Mesh(2, 0, 4, p=1, sn=4)),
+        ("element counts", lambda: sn.Mesh(3, 4, 4, 0, p=1, sn=4)),
+        ("2D supports", lambda: sn.Mesh(2, 4, 4, p=4, sn=4)),
+        ("2D supports", lambda: sn.Mesh(2, 4, 4, p=0, sn=4)),
+        ("psi_inc", lambda: sn.Mesh(2, 4, 4, p=1, sn=4, psi_inc=-1.0)),
+        ("psi_inc", lambda: sn.Mesh(2, 4, 4, p=1, sn=4, psi_inc=float("inf"))),
+        ("too many elements", lambda: sn.Mesh(2, 65536, 65536, p=1, sn=4)),
+        ("too many elements", lambda: sn.Mesh(3, 1025, 1024, 1024, p=1, sn=4)),
+        ("sn_order", lambda: sn.Mesh(3, 2, 2, 2, p=1, sn=10)),
+        ("inverted", lambda: sn.Mesh(2, 2, 2, p=1, sn=4, vertices=inverted)),
+        ("inverted or degenerate", lambda: sn.Mesh(2, 1, 1, p=2, sn=4, vertices=flat)),
+        ("non-finite", lambda: sn.Mesh(2, 2, 2, p=1, sn=4, vertices=nan)),
+        ("vertices must be NULL", lambda: sn.Mesh(3, 1, 1, 1, p=1, sn=4, vertices=verts(1, 1))),
+    ]
+    for what, call in cases:
+        with pytest.raises(sn.SnError, match=what) as e:
+            call()
+        assert e.value.status == 1, what
+
+
 def test_binding_structs_match_the_header_layout(tmp_path):
     """Every field of the ctypes mirrors sits at the C compiler's offset, and the sizes agree."""
     import shutil

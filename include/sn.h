@@ -23,6 +23,11 @@
  *    and return when the results are ready in device memory unless stated otherwise.
  *  - All device buffers a mesh needs (angular fluxes, work lists, the DSA hierarchy) are
  *    owned by the mesh and freed by sn_mesh_destroy.
+ *  - Sizes are not checked: a scalar-flux argument must hold n_elem x n_nodes doubles and a
+ *    per-element argument n_elem doubles (sn_mesh_get_info); a shorter buffer is overrun.
+ *  - Unless an entry point says more: SN_ERR_ARG for a null mesh or required pointer or an
+ *    out-of-range option (nothing is enqueued), SN_ERR_CUDA for a failed CUDA call, and
+ *    SN_ERR_TIMEOUT when a bounded wait of the dataflow or tiled schedules gave up.
  */
 #ifndef SN_H
 #define SN_H
@@ -111,6 +116,7 @@ sn_status sn_mesh_get_info(const sn_mesh* mesh, sn_mesh_info* info);
  * param: schedule 0: direction groups (0 or 1 = one chain, at most the number of directions);
  * schedules 1 and 4: blocks per SM (0 = occupancy limit); schedule 2: tile edge (<= 64); schedule 3:
  * CTAs per SM.
+ * Errors: SN_ERR_ARG for an unknown schedule, a block outside its range or a param out of range.
  */
 sn_status sn_mesh_set_schedule(sn_mesh* mesh, int schedule, int block, int param);
 
@@ -137,11 +143,15 @@ sn_status sn_mesh_set_operator_cache(sn_mesh* mesh, int mode);
  * Test hook for the bounded waits of the dataflow schedule: the next sweep's items publish a
  * completion value that no waiter accepts, so every dependent item waits timeout_seconds
  * (0 < t <= 4), the kernel records the failure and exits, and the call returns SN_ERR_TIMEOUT.
- * The context stays usable; later sweeps are unaffected.
+ * The context stays usable; later sweeps are unaffected.  The paper has no counterpart (a hook of
+ * the device-side wait limits).  Errors: SN_ERR_ARG for t outside (0, 4] or a mesh on the level
+ * schedule, which never waits.
  */
 sn_status sn_debug_stall_next_sweep(sn_mesh* mesh, double timeout_seconds);
 
-/* Quadrature readback: dirs (host, n_dirs x 3) and weights (host, n_dirs). */
+/* Quadrature readback (the level-symmetric set of Eq. sntransport, Sec. 1): dirs (host, n_dirs x 3,
+ * Omega_d row by row) and weights (host, n_dirs, summing to 4 pi).  Errors: SN_ERR_ARG for a null
+ * mesh. */
 sn_status sn_mesh_quadrature(const sn_mesh* mesh, double* dirs, double* weights);
 
 /*
@@ -172,7 +182,8 @@ sn_status sn_set_materials(sn_mesh* mesh, const double* sigma_t, const double* s
 sn_status sn_set_pseudo_scattering(sn_mesh* mesh, const double* sigma, const double* cv, const double* T,
                                    double dt, double a_rad, double c_light, int mem, void* stream);
 
-/* Current materials (host arrays of n_elem doubles; any may be NULL). */
+/* Current materials sigma_t, sigma_s, q of Eq. sntransport (host arrays of n_elem doubles, written;
+ * any may be NULL).  Errors: SN_ERR_ARG for a null mesh. */
 sn_status sn_get_materials(const sn_mesh* mesh, double* sigma_t, double* sigma_s, double* q);
 
 /*
@@ -180,8 +191,9 @@ sn_status sn_get_materials(const sn_mesh* mesh, double* sigma_t, double* sigma_s
  *     phi_out = sum_d w_d L_d^{-1} ( q/(4 pi) + sigma_s phi_in / (4 pi) ),
  * the element systems solved in the given precision (SN_FP64, SN_FP32 or SN_FP32_REFINE;
  * the scalar-flux sum is always float64).  phi_in, phi_out: device, [elem][node],
- * must not alias.  The angular fluxes psi_d of this sweep stay in the mesh (used by
- * sn_gradients).
+ * must not alias.  phi_in may be NULL (phi_in = 0).  The angular fluxes psi_d of this sweep
+ * stay in the mesh (used by sn_gradients).  Errors: SN_ERR_ARG for a null mesh or phi_out, an
+ * unknown precision (SN_FP32_MIXED is an iteration, not a sweep) or phi_in == phi_out.
  */
 sn_status sn_sweep(sn_mesh* mesh, const double* phi_in, double* phi_out, int precision, void* stream);
 
@@ -317,6 +329,7 @@ sn_status sn_source_iterate(sn_mesh* mesh, const sn_iter_opts* opts, double* phi
  * mass matrix with coefficient sigma_s/(4 pi).  L_d^T is solved by a sweep in reversed
  * upwind order with transposed element and face blocks (adjoint of Eq. system).
  * mu_in, out: device [elem][node]; the lambda_d = w_d L_d^{-T} mu_in stay in the mesh.
+ * Errors: SN_ERR_ARG for a null pointer, mu_in == out or a precision other than SN_FP64.
  */
 sn_status sn_adjoint_sweep(sn_mesh* mesh, const double* mu_in, double* out, int precision, void* stream);
 
@@ -324,6 +337,8 @@ sn_status sn_adjoint_sweep(sn_mesh* mesh, const double* mu_in, double* out, int 
  * sn_adjoint_iterate: solves S^T mu = g (S = I - T, Eq. schur) by the adjoint source
  * iteration mu <- g + T^T mu with the transposed DSA step, or (outer = SN_OUTER_FGMRES) by
  * flexible GMRES right-preconditioned by that transposed step.  g, mu_inout: device.
+ * Errors: as sn_source_iterate for the options; SN_ERR_ARG for SN_DSA_TRIANGULAR or a direction
+ * range (the adjoint runs on one process); SN_ERR_NOT_CONVERGED after max_iters (mu_inout written).
  */
 sn_status sn_adjoint_iterate(sn_mesh* mesh, const sn_iter_opts* opts, const double* g, double* mu_inout,
                              sn_iter_stats* stats, void* stream);
@@ -335,6 +350,8 @@ sn_status sn_adjoint_iterate(sn_mesh* mesh, const sn_iter_opts* opts, const doub
  *   d_q[e]       =  sum_d lambda_d,e^T M_e 1 / (4 pi),
  * with psi_d = L_d^{-1}(q_d + Sigma_s phi) and lambda_d = w_d L_d^{-T} mu (one forward and
  * one adjoint sweep, FP64).  All pointers device; outputs n_elem doubles (NULL to skip).
+ * The paper computes no gradients: these follow from Eq. (system) by the adjoint method.
+ * Errors: SN_ERR_ARG for a null mesh, phi or mu.
  */
 sn_status sn_gradients(sn_mesh* mesh, const double* phi, const double* mu, double* d_sigma_t,
                        double* d_sigma_s, double* d_q, void* stream);
@@ -367,6 +384,7 @@ sn_status sn_unrolled_gradients(sn_mesh* mesh, const double* phi0, int K, int ch
  * Diagnostics of the DSA operator (Sec. 3): y = D_ff x on the elements selected by opts
  * (x, y device, [elem][node]; entries outside the thick set are ignored / set to 0), and the
  * PCG + V-cycle solve of D_ff x = b to opts->inner_tol.  *iters receives the PCG count.
+ * Errors: SN_ERR_ARG for a null pointer or bad options; SN_ERR_VOID_FULL_DSA as sn_source_iterate.
  */
 sn_status sn_dsa_apply(sn_mesh* mesh, const sn_iter_opts* opts, const double* x, double* y, void* stream);
 sn_status sn_dsa_solve(sn_mesh* mesh, const sn_iter_opts* opts, const double* b, double* x, int* iters,
@@ -376,6 +394,7 @@ sn_status sn_dsa_solve(sn_mesh* mesh, const sn_iter_opts* opts, const double* b,
  * Diagnostic: copies psi_d (direction d) of the last forward sweep (or lambda_d of the last
  * adjoint sweep if adjoint != 0) into out (device, [elem][node], float64; the FP32 form's
  * float32 values are widened).  Used to check the element equations of Sec. 3.1 at full size.
+ * Errors: SN_ERR_ARG for a null pointer, d outside [0, n_dirs), or no sweep of that kind yet.
  */
 sn_status sn_get_angular_flux(sn_mesh* mesh, int d, int adjoint, int precision, double* out, void* stream);
 

@@ -2,6 +2,8 @@
 
 The generators hold none of the method's arithmetic; these checks pin what they produce to the
 stated shapes, material values and distributions, and check that they are reproducible."""
+import os
+
 import numpy as np
 
 from paper_2001_09196_gb300 import inputs
@@ -93,3 +95,17 @@ def test_generators_are_reproducible():
     assert np.array_equal(inputs.random_phi(a, 3), inputs.random_phi(b, 3))
     c = inputs.config2(n=32, block=8, seed=inputs.MASTER_SEED + 99)
     assert not np.array_equal(a.vertices, c.vertices)
+
+
+def test_hohlraum_constants_are_the_papers():
+    """The hohlraum-like layout's materials and constants equal the values the paper prints
+    (Sec. 4.2, Table hohlraum_materials; tests/golden/hohlraum_materials.txt)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "hohlraum_materials.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    mats = {r[0]: (float(r[1]), float(r[2])) for r in rows if len(r) == 3}
+    consts = {r[0]: float(r[1]) for r in rows if len(r) == 2}
+    order = ("gold", "helium", "CH", "hydrogen")
+    assert inputs.HOHLRAUM_SIGMA == tuple(mats[k][0] for k in order)
+    assert inputs.HOHLRAUM_CV == tuple(mats[k][1] for k in order)
+    assert (inputs.HOHLRAUM_A_RAD, inputs.HOHLRAUM_C_LIGHT, inputs.HOHLRAUM_DT) == (consts["a"], consts["c"],
+                                                                                   consts["dt"])

@@ -144,6 +144,34 @@ def test_cartesian_levels_are_index_sums():
         assert np.array_equal(lev, s.sum(axis=1))
 
 
+def test_cyclic_upwind_graph_is_refused():
+    """Kahn's order exists only for an acyclic upwind graph (the sweep of Sec. 1 needs one).  No
+    direction on a mesh of convex elements makes a cycle, so the face fluxes are handed in: on a 2x2
+    mesh a flow circulating 0 -> 1 -> 3 -> 2 -> 0 has no element without upwind neighbours and must
+    raise; reversing the edge 2 -> 0 leaves the chain 0 -> 1 -> 3 -> 2 (with 0 -> 2), levels
+    [0], [1], [3], [2]."""
+    from oracle.transport import CycleError
+    prob = inputs.uniform_problem(2, 2, 1, 4, 1.0, 0.5, 1.0)
+    T = Transport(prob)
+    shape = T.face_flux(0)[0].shape   # (ne, face points); face 2a + side, side 1 = positive axis
+
+    def flows(edges):
+        fw = [np.zeros(shape) for _ in range(4)]
+        for e, f, sign in edges:
+            fw[f][e] = sign
+        return fw
+    # (element, face, +1 outflow / -1 inflow); elements 0 (0,0), 1 (1,0), 2 (0,1), 3 (1,1)
+    ring = [(0, 1, 1), (1, 0, -1),    # 0 -> 1 across x
+            (1, 3, 1), (3, 2, -1),    # 1 -> 3 across y
+            (3, 0, 1), (2, 1, -1),    # 3 -> 2 across x
+            (2, 2, 1), (0, 3, -1)]    # 2 -> 0 across y
+    assert np.array_equal(T.mesh.nbr[[0, 1, 3, 2]][:, [1, 3, 0, 2]].diagonal(), [1, 3, 2, 0])
+    with pytest.raises(CycleError):
+        T.levels(0, fw=flows(ring))
+    broken = ring[:6] + [(2, 2, -1), (0, 3, 1)]   # 0 -> 2 instead of 2 -> 0
+    assert [list(L) for L in T.levels(0, fw=flows(broken))] == [[0], [1], [3], [2]]
+
+
 # ---------------------------------------------------------------- block system (Eq. system / schur)
 @pytest.mark.parametrize("n,p", [(4, 1), (3, 2)])
 def test_dense_direct_solve_matches_source_iteration(n, p):

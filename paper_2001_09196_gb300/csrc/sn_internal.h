@@ -38,6 +38,12 @@ void lagrange_eval(const GL1D& g, double t, double* val, double* der);
 // Level-symmetric S_N set; returns false for an unsupported order.
 bool level_symmetric(int N, int dim, std::vector<double>& dirs, std::vector<double>& wts);
 
+// Directed graph helpers of the tiled schedule (host).  to_csr sorts and de-duplicates the edges
+// (source, target) and builds the CSR arrays ptr (n + 1) and adj; strong_components labels every
+// vertex with its strongly connected component (comp, n values) and returns how many there are.
+void to_csr(int n, std::vector<std::pair<int, int>>& edges, std::vector<int>& ptr, std::vector<int>& adj);
+int strong_components(int n, const std::vector<int>& ptr, const std::vector<int>& adj, std::vector<int>& comp);
+
 // Everything a sweep kernel reads, by value.
 struct SweepArgs {
     int dim, p, nx, ny, nz, ne, nd;

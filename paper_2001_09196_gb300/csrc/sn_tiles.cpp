@@ -22,60 +22,6 @@ namespace sn {
 
 namespace {
 
-// Strongly connected components of a directed graph in CSR form (iterative Tarjan).
-int strong_components(int n, const std::vector<int>& ptr, const std::vector<int>& adj, std::vector<int>& comp) {
-    std::vector<int> index(n, -1), low(n, 0), stack;
-    std::vector<char> on_stack(n, 0);
-    std::vector<std::pair<int, int>> call;  // (vertex, next edge)
-    comp.assign(n, -1);
-    int counter = 0, n_comp = 0;
-    for (int root = 0; root < n; ++root) {
-        if (index[root] >= 0) continue;
-        index[root] = low[root] = counter++;
-        stack.push_back(root);
-        on_stack[root] = 1;
-        call.push_back({root, ptr[root]});
-        while (!call.empty()) {
-            const int v = call.back().first;
-            if (call.back().second < ptr[v + 1]) {
-                const int w = adj[call.back().second++];
-                if (index[w] < 0) {
-                    index[w] = low[w] = counter++;
-                    stack.push_back(w);
-                    on_stack[w] = 1;
-                    call.push_back({w, ptr[w]});
-                } else if (on_stack[w]) {
-                    low[v] = std::min(low[v], index[w]);
-                }
-                continue;
-            }
-            if (low[v] == index[v]) {
-                int w;
-                do {
-                    w = stack.back();
-                    stack.pop_back();
-                    on_stack[w] = 0;
-                    comp[w] = n_comp;
-                } while (w != v);
-                ++n_comp;
-            }
-            call.pop_back();
-            if (!call.empty()) low[call.back().first] = std::min(low[call.back().first], low[v]);
-        }
-    }
-    return n_comp;
-}
-
-void to_csr(int n, std::vector<std::pair<int, int>>& edges, std::vector<int>& ptr, std::vector<int>& adj) {
-    std::sort(edges.begin(), edges.end());
-    edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
-    ptr.assign(n + 1, 0);
-    for (const auto& e : edges) ptr[e.first + 1]++;
-    for (int i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
-    adj.resize(edges.size());
-    for (size_t k = 0; k < edges.size(); ++k) adj[k] = edges[k].second;  // sorted by source: CSR order
-}
-
 template <typename T>
 cudaError_t upload(T** d, const std::vector<T>& h) {
     cudaError_t err = cudaMalloc(d, std::max<size_t>(1, h.size()) * sizeof(T));
